@@ -1,0 +1,187 @@
+"""Multiresolution encodings in FP64 (test infrastructure only; see ``oracle``).
+
+* ``simplex_encode`` / ``simplex_encode_bwd``: the paper's pipeline of Sec. 5,
+  steps (a) hash the simplex vertices at L levels, (b) look up the feature
+  vectors of table H_l, (c) barycentric interpolation (Sec. 4.3), (d) concatenate
+  the levels; (e) the backward pass accumulates the loss gradient into the
+  looked-up entries.
+* ``grid_encode`` / ``grid_encode_bwd``: the baseline the paper compares
+  against (Instant-NGP's 2^n-vertex grid), interpolated by repeated linear
+  interpolation one axis at a time as in Algorithm 1 (trilinear interpolation
+  by recursion on the dimension), with the same hash and tables.
+
+Tables are [L, T, F] arrays of any float dtype (the values are upcast to FP64);
+the output layout is [P, L*F] with level-major feature groups.  The first
+level-scaling step is evaluated in binary32 (see ``lattice``), everything after
+the floor is FP64.
+
+Parity pins: the simplex path is pinned by weights >= 0, sum 1, exact
+reconstruction of the point, agreement with a brute-force point-in-simplex
+search, exact interpolation of affine fields and the memory-usage figure of
+Sec. 5.2; the grid path by exact interpolation of multilinear fields.  The
+backward passes are pinned by adjointness and by exact finite differences
+(both encodings are linear in the tables).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+from . import lattice
+
+
+def _level_params(kind, n, n_levels, base_res, growth, res_mode):
+    if kind == "simplex":
+        return lattice.simplex_level_scales_fp32(n, n_levels, base_res, growth, res_mode)
+    return lattice.grid_level_scales_fp32(n_levels, base_res, growth)
+
+
+# --------------------------------------------------------------------------
+# simplex encoding, Sec. 5 (a)-(d)
+# --------------------------------------------------------------------------
+def simplex_level_vertices(x32: np.ndarray, level_scale: np.float32, log2_T: int):
+    """Steps (a) for one level: returns (slots int64 [P, n+1], weights FP64 [P, n+1],
+    vertices int64 [P, n+1, n])."""
+    q = lattice.scaled_skewed_fp32(x32, level_scale)
+    c, order, f = lattice.subdivide(q)
+    V = lattice.simplex_vertices(c, order)
+    w = lattice.barycentric_weights(f, order)
+    slots = lattice.hash_slot(V, log2_T)
+    return slots, w, V
+
+
+def simplex_encode(x32, tables, *, base_res, growth, res_mode=lattice.RES_RAW, with_denominator=False):
+    """Forward simplex encoding of points ``x32`` ([P, n], binary32) with tables [L, T, F].
+
+    Returns FP64 [P, L*F]; with ``with_denominator`` also returns sum_k |w_k H_k|
+    per output, the scale against which a relative tolerance is measured.
+    """
+    x32 = np.asarray(x32, dtype=np.float32)
+    P, n = x32.shape
+    L, T, F = tables.shape
+    log2_T = int(T).bit_length() - 1
+    scales = _level_params("simplex", n, L, base_res, growth, res_mode)
+    out = np.zeros((P, L * F), dtype=np.float64)
+    den = np.zeros((P, L * F), dtype=np.float64)
+    for l in range(L):
+        slots, w, _ = simplex_level_vertices(x32, scales[l], log2_T)
+        H = np.asarray(tables[l], dtype=np.float64)[slots]            # (b) lookup [P, n+1, F]
+        out[:, l * F:(l + 1) * F] = np.einsum("pk,pkf->pf", w, H)      # (c) interpolate, (d) concat
+        den[:, l * F:(l + 1) * F] = np.einsum("pk,pkf->pf", np.abs(w), np.abs(H))
+    return (out, den) if with_denominator else out
+
+
+def simplex_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, growth,
+                       res_mode=lattice.RES_RAW, levels=None, with_denominator=False):
+    """Step (e): dH_l[slot(v_k)][f] += w_k * dout[p][l*F + f], FP64.
+
+    Returns a dict level -> FP64 [T, F] gradient (only the levels asked for), and
+    with ``with_denominator`` a second dict of sum |w_k * dout| per entry.
+    """
+    x32 = np.asarray(x32, dtype=np.float32)
+    dout = np.asarray(dout, dtype=np.float64)
+    P, n = x32.shape
+    F = n_features
+    T = 1 << log2_T
+    scales = _level_params("simplex", n, n_levels, base_res, growth, res_mode)
+    grads, dens = {}, {}
+    for l in (range(n_levels) if levels is None else levels):
+        slots, w, _ = simplex_level_vertices(x32, scales[l], log2_T)
+        terms = w[:, :, None] * dout[:, None, l * F:(l + 1) * F]       # [P, n+1, F]
+        g = np.zeros((T, F), dtype=np.float64)
+        np.add.at(g, slots.ravel(), terms.reshape(-1, F))
+        grads[l] = g
+        if with_denominator:
+            a = np.zeros((T, F), dtype=np.float64)
+            np.add.at(a, slots.ravel(), np.abs(terms).reshape(-1, F))
+            dens[l] = a
+    return (grads, dens) if with_denominator else grads
+
+
+# --------------------------------------------------------------------------
+# 2^n grid comparator, Algorithm 1
+# --------------------------------------------------------------------------
+def grid_level_cell(x32, level_res: np.float32):
+    """p = x * N_l in binary32, c = floor(p), f = p - c (FP64)."""
+    p = np.asarray(x32, dtype=np.float32) * np.float32(level_res)
+    p = p.astype(np.float64)
+    c = np.floor(p)
+    return c.astype(np.int64), p - c
+
+
+def _corner_offsets(n):
+    """All b in {0,1}^n, in the order of a C-ordered [2]*n array (axis 0 slowest)."""
+    return np.array(list(itertools.product((0, 1), repeat=n)), dtype=np.int64)
+
+
+def grid_level_corner_weights(f: np.ndarray) -> np.ndarray:
+    """Weight of every corner as the adjoint of the axis-by-axis linear interpolation.
+
+    Runs the recursion of Algorithm 1 backwards: a unit output is split by
+    (1 - f_i, f_i) along each axis in turn, giving [P, 2^n] weights in the
+    corner order of ``_corner_offsets``.
+    """
+    P, n = f.shape
+    w = np.ones((P, 1))
+    for i in range(n):                       # split along axes 0..n-1 (axis 0 slowest)
+        lo = w * (1.0 - f[:, i])[:, None]
+        hi = w * f[:, i][:, None]
+        w = np.stack([lo, hi], axis=2).reshape(P, -1)
+    return w
+
+
+def grid_encode(x32, tables, *, base_res, growth):
+    """Forward 2^n grid encoding, [P, L*F] FP64.
+
+    Per level: look up the 2^n corner values, then (Algorithm 1) interpolate
+    linearly along the last remaining axis and recurse on the others until a
+    single value is left.
+    """
+    x32 = np.asarray(x32, dtype=np.float32)
+    P, n = x32.shape
+    L, T, F = tables.shape
+    log2_T = int(T).bit_length() - 1
+    res = _level_params("grid", n, L, base_res, growth, None)
+    offs = _corner_offsets(n)
+    out = np.zeros((P, L * F), dtype=np.float64)
+    for l in range(L):
+        c, f = grid_level_cell(x32, res[l])
+        corners = c[:, None, :] + offs[None, :, :]                       # [P, 2^n, n]
+        vals = np.asarray(tables[l], dtype=np.float64)[lattice.hash_slot(corners, log2_T)]
+        vals = vals.reshape((P,) + (2,) * n + (F,))
+        for i in reversed(range(n)):                                   # lerp along axis i
+            t = f[:, i].reshape((P,) + (1,) * i + (1,))
+            v0 = np.take(vals, 0, axis=1 + i)
+            v1 = np.take(vals, 1, axis=1 + i)
+            vals = v0 * (1.0 - t) + v1 * t
+        out[:, l * F:(l + 1) * F] = vals.reshape(P, F)
+    return out
+
+
+def grid_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, growth, levels=None):
+    """Backward of ``grid_encode``: dH_l[slot(c+b)] += w_b * dout, FP64 dict level -> [T, F]."""
+    x32 = np.asarray(x32, dtype=np.float32)
+    dout = np.asarray(dout, dtype=np.float64)
+    P, n = x32.shape
+    F = n_features
+    T = 1 << log2_T
+    res = _level_params("grid", n, n_levels, base_res, growth, None)
+    offs = _corner_offsets(n)
+    grads = {}
+    for l in (range(n_levels) if levels is None else levels):
+        c, f = grid_level_cell(x32, res[l])
+        w = grid_level_corner_weights(f)                                 # [P, 2^n]
+        slots = lattice.hash_slot(c[:, None, :] + offs[None, :, :], log2_T)
+        terms = w[:, :, None] * dout[:, None, l * F:(l + 1) * F]
+        g = np.zeros((T, F), dtype=np.float64)
+        np.add.at(g, slots.ravel(), terms.reshape(-1, F))
+        grads[l] = g
+    return grads
+
+
+def grid_level_vertices(x32, level_res, log2_T):
+    """Slots int64 [P, 2^n] and weights FP64 [P, 2^n] of one grid level."""
+    c, f = grid_level_cell(x32, level_res)
+    offs = _corner_offsets(c.shape[1])
+    return lattice.hash_slot(c[:, None, :] + offs[None, :, :], log2_T), grid_level_corner_weights(f)

@@ -1,0 +1,158 @@
+"""Seeded synthetic inputs for the encoding workloads.
+
+This module holds none of the encoding's arithmetic: it only draws points,
+table values, upstream gradients and procedural targets from numpy's PCG64
+generator, so that the CUDA path and the FP64 oracle can be fed the same bits.
+All arrays are host numpy arrays; callers move them to the device.
+
+Workload recipes (shapes and distributions of the paper's tasks, Sec. 6):
+
+* ``uniform_points``   -- P points uniform in [0, 1)^d, binary32.
+* ``edge_points``      -- points on the faces x = 0 and x = 1, on lattice
+  planes and with tied coordinates (the degenerate cases of the subdivision).
+* ``sdf_points``       -- half uniform in [0,1)^3, half within 0.01 of the
+  surface of a seeded union of spheres and tori (SDF-style sampling).
+* ``uniform_tables``   -- [L, T, F] values U(-a, a) stored as fp32 / fp16 /
+  bf16 (bf16 is returned as the binary32 values it represents plus its raw
+  uint16 bits).
+* ``normal_grads``     -- upstream gradients N(0, 1).
+* ``ProceduralImage``  -- an RGB image defined analytically as a seeded sum of
+  sinusoids plus bilinear value noise on a coarse lattice; it stands in for the
+  gigapixel photograph of Sec. 6.1, which is not available here.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def uniform_points(P: int, d: int, seed: int) -> np.ndarray:
+    return rng(seed).random((P, d), dtype=np.float32)
+
+
+def edge_points(d: int, seed: int, per_kind: int = 64) -> np.ndarray:
+    """Degenerate inputs: corners/faces of the unit cube, ties, tiny and near-1 values."""
+    g = rng(seed)
+    pts = []
+    # faces x_i = 0 and x_i = 1
+    for i in range(d):
+        for val in (0.0, 1.0):
+            p = g.random((per_kind, d), dtype=np.float32)
+            p[:, i] = val
+            pts.append(p)
+    # corners
+    for bits in range(1 << d):
+        pts.append(np.array([[(bits >> i) & 1 for i in range(d)]], dtype=np.float32))
+    # all coordinates tied
+    t = g.random((per_kind, 1), dtype=np.float32)
+    pts.append(np.repeat(t, d, axis=1))
+    # pairs tied
+    p = g.random((per_kind, d), dtype=np.float32)
+    p[:, 1] = p[:, 0]
+    pts.append(p)
+    # coordinates on coarse dyadic values (land exactly on lattice planes at many levels)
+    k = g.integers(0, 65, size=(per_kind, d))
+    pts.append((k / 64.0).astype(np.float32))
+    # values just below 1 and just above 0
+    pts.append(np.full((1, d), np.nextafter(np.float32(1), np.float32(0)), dtype=np.float32))
+    pts.append(np.full((1, d), np.float32(1e-30), dtype=np.float32))
+    return np.concatenate(pts, axis=0)
+
+
+def fp32_to_bf16_bits(a: np.ndarray) -> np.ndarray:
+    """Round binary32 to bfloat16 (nearest, ties to even); returns the uint16 bits."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    rounding = ((u >> 16) & 1) + np.uint32(0x7FFF)
+    return ((u + rounding) >> 16).astype(np.uint16)
+
+
+def bf16_bits_to_fp32(b: np.ndarray) -> np.ndarray:
+    return (np.asarray(b, dtype=np.uint32) << 16).view(np.float32)
+
+
+def uniform_tables(L: int, T: int, F: int, seed: int, dtype: str = "f32", scale: float = 1e-4):
+    """Returns (values, storage): values as binary32 exactly equal to what is stored,
+    storage as the array to copy to the device (float32, float16 or uint16 bf16 bits)."""
+    v = rng(seed).uniform(-scale, scale, size=(L, T, F)).astype(np.float32)
+    if dtype == "f32":
+        return v, v
+    if dtype == "f16":
+        h = v.astype(np.float16)
+        return h.astype(np.float32), h
+    if dtype == "bf16":
+        bits = fp32_to_bf16_bits(v)
+        return bf16_bits_to_fp32(bits), bits
+    raise ValueError(dtype)
+
+
+def normal_grads(P: int, n: int, seed: int) -> np.ndarray:
+    return rng(seed).standard_normal((P, n), dtype=np.float32)
+
+
+def sdf_points(P: int, seed: int, n_shapes: int = 32, band: float = 0.01) -> np.ndarray:
+    """Half uniform in [0,1)^3, half within ``band`` of a seeded union of spheres and tori."""
+    g = rng(seed)
+    n_uni = P // 2
+    n_sur = P - n_uni
+    pts = [g.random((n_uni, 3))]
+    kinds = g.integers(0, 2, size=n_shapes)
+    centres = g.uniform(0.2, 0.8, size=(n_shapes, 3))
+    radii = g.uniform(0.03, 0.15, size=n_shapes)
+    which = g.integers(0, n_shapes, size=n_sur)
+    u = g.standard_normal((n_sur, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    off = g.uniform(-band, band, size=(n_sur, 1))
+    angle = g.uniform(0.0, 2 * np.pi, size=n_sur)
+    tube = g.uniform(0.0, 2 * np.pi, size=n_sur)
+    sur = np.empty((n_sur, 3))
+    sph = kinds[which] == 0
+    r = radii[which][:, None]
+    sur[sph] = centres[which][sph] + (r[sph] + off[sph]) * u[sph]
+    # torus in the xy plane: major radius r, minor radius r/3
+    tor = ~sph
+    rr, rm = r[tor, 0], r[tor, 0] / 3.0 + off[tor, 0]
+    sur[tor, 0] = centres[which][tor, 0] + (rr + rm * np.cos(tube[tor])) * np.cos(angle[tor])
+    sur[tor, 1] = centres[which][tor, 1] + (rr + rm * np.cos(tube[tor])) * np.sin(angle[tor])
+    sur[tor, 2] = centres[which][tor, 2] + rm * np.sin(tube[tor])
+    pts.append(np.clip(sur, 0.0, np.nextafter(1.0, 0.0)))
+    out = np.concatenate(pts).astype(np.float32)
+    return out[g.permutation(P)]
+
+
+class ProceduralImage:
+    """RGB image of ``size`` x ``size`` pixels defined analytically (no pixel array):
+    a seeded sum of ``n_waves`` sinusoids per channel plus bilinear value noise on
+    a 64 x 64 lattice, mapped to [0, 1].  ``sample(x)`` evaluates it at points
+    x in [0,1)^2 (pixel-centre snapped), returning float32 [P, 3]."""
+
+    def __init__(self, seed: int, size: int = 16384, n_waves: int = 64):
+        g = rng(seed)
+        self.size = size
+        self.freq = g.uniform(1.0, 400.0, size=(3, n_waves, 1)) * g.choice([-1, 1], size=(3, n_waves, 2))
+        self.dirs = g.standard_normal((3, n_waves, 2))
+        self.dirs /= np.linalg.norm(self.dirs, axis=2, keepdims=True)
+        self.phase = g.uniform(0, 2 * np.pi, size=(3, n_waves))
+        self.amp = g.uniform(0.2, 1.0, size=(3, n_waves)) / n_waves
+        self.noise = g.random((3, 65, 65))
+
+    def sample(self, x: np.ndarray) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64)
+        px = (np.floor(x * self.size) + 0.5) / self.size
+        out = np.empty((x.shape[0], 3))
+        gx = px[:, 0] * 64.0
+        gy = px[:, 1] * 64.0
+        ix = np.minimum(gx.astype(np.int64), 63)
+        iy = np.minimum(gy.astype(np.int64), 63)
+        fx, fy = gx - ix, gy - iy
+        for ch in range(3):
+            k = self.dirs[ch] * np.abs(self.freq[ch])                # [W, 2]
+            arg = px @ k.T + self.phase[ch]                          # [P, W]
+            s = np.sin(arg) @ self.amp[ch]
+            nz = self.noise[ch]
+            vn = ((1 - fx) * (1 - fy) * nz[ix, iy] + fx * (1 - fy) * nz[ix + 1, iy]
+                  + (1 - fx) * fy * nz[ix, iy + 1] + fx * fy * nz[ix + 1, iy + 1])
+            out[:, ch] = 0.5 + 0.35 * s + 0.3 * (vn - 0.5)
+        return np.clip(out, 0.0, 1.0).astype(np.float32)
