@@ -1,0 +1,394 @@
+"""Benchmark: simplex-encoding training step throughput (points/s) on one GB300.
+
+Workload (the image-fitting configuration): d = 2, L = 16 levels, F = 2 features,
+T = 2^22 entries per level in fp16, base resolution 16, growth 2.0, 64-wide network
+32 -> 64 -> 64 -> 3 (fp16 tensor cores, fp32 accumulation), L2 loss against a
+procedural 16384^2 RGB image, Adam on fp32 master copies, 2^18 uniformly drawn points
+per step.  A step is one pass of the whole path: encode forward, network forward +
+loss + backward, encode backward (scatter into the tables), Adam on the touched table
+entries and on the network.
+
+Prints one JSON line.  ``value`` is device-timed (inputs resident in HBM), ``e2e`` the
+same metric through the public API with the batch copied from pinned host memory and
+the loss read back every step.  ``--impl reference`` times the FP64 oracle on the
+host cores instead.  Under torchrun every rank trains its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFG = dict(d=2, n_levels=16, n_features=2, log2_T=22, base_res=16.0, growth=2.0)
+BATCH = 1 << 18
+N_OUT = 3
+WORKLOAD = "image_fit_2d_L16_F2_T2^22_fp16_mlp64x2_P2^18"
+METRIC = "simplex encode fwd+bwd training-step throughput"
+N_POOL = 8   # distinct resident batches cycled through the timed steps
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while active."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[3 + i]
+                          and "Not" not in r[3 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+def make_batches(n, seed0=1000):
+    from paper_2311_15439_gb300 import synth
+    img = synth.ProceduralImage(seed=7, size=16384, n_waves=64)
+    xs, ts = [], []
+    for i in range(n):
+        x = synth.uniform_points(BATCH, 2, seed0 + i)
+        xs.append(x)
+        ts.append(img.sample(x))
+    return xs, ts
+
+
+def _kernel_bytes(F=2, L=16, d=2):
+    """Algorithmic bytes per point of each launch of the step (stated in the design notes)."""
+    V = d + 1
+    return {
+        "encode_fwd": 4 * d + L * V * 2 * F + L * F * 2,              # x, fp16 gathers, fp16 encoding
+        "mlp_train_l2": L * F * 2 + 4 * N_OUT + 4 * L * F,            # encoding, target, dL/d(encoding)
+        "encode_bwd": 4 * d + 4 * L * F + L * V * 2 * 4 * F,          # x, dL/d(enc), fp32 RMW per vertex
+    }
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2311_15439_gb300 import build as B
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    B.build()   # no-op when up to date
+
+    enc = Encoder(**CFG, kind=args.kind, table_dtype="f16")
+    mlp = Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16")
+    tr = Trainer(enc, mlp, BATCH, seed=rank, device=dev)
+    xs, ts = make_batches(N_POOL, seed0=1000 + 100 * rank)
+    xd = [torch.from_numpy(x).to(dev) for x in xs]
+    td = [torch.from_numpy(t).to(dev) for t in ts]
+    stream = torch.cuda.current_stream(dev)
+
+    for i in range(args.warmup):
+        tr.step(xd[i % N_POOL], td[i % N_POOL])
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed region: K steps, per-kernel events on the launching stream
+    names = ["encode_fwd", "mlp_train_l2", "encode_bwd", "adam_tables", "adam_mlp"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    F = enc.n_features
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for k in range(args.steps):
+            x, t = xd[k % N_POOL], td[k % N_POOL]
+            e = ev[k]
+            tr.t += 1
+            e[0].record(stream)
+            tr.enc.encode_fwd(x, tr.tables, tr.enc_out)
+            e[1].record(stream)
+            tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, t, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
+                                workspace=tr.ws)
+            e[2].record(stream)
+            tr.enc.encode_bwd(x, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
+            e[3].record(stream)
+            tr.adam_tables.step_touched(tr.t, tr.state, tr.touched, tr.tables, F)
+            e[4].record(stream)
+            tr.adam_mlp.step(tr.t, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
+            e[5].record(stream)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+    ms = start.elapsed_time(stop)
+    per_kernel = {n: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)]))
+                  for i, n in enumerate(names)}
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    loss = tr.loss()
+
+    # ---- end to end through the public API: pinned host batch -> device, step, loss -> host
+    hx = [torch.from_numpy(x).pin_memory() for x in xs]
+    ht = [torch.from_numpy(t).pin_memory() for t in ts]
+    bx = torch.empty_like(xd[0])
+    bt = torch.empty_like(td[0])
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s2.record(stream)
+    for k in range(e2e_steps):
+        bx.copy_(hx[k % N_POOL], non_blocking=True)
+        bt.copy_(ht[k % N_POOL], non_blocking=True)
+        tr.step(bx, bt)
+        tr.loss()                                   # device -> host read of the step's loss
+    e2.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = s2.elapsed_time(e2)
+    if world > 1:
+        tt = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_e2e = float(tt.item())
+
+    # ---- comparators on the same GPU (encode forward + backward only, equal L, F, T)
+    comparators = encode_sweep(dev) if (rank == 0 and not args.no_sweep) else None
+
+    if rank == 0:
+        value = BATCH * args.steps * world / (ms / 1e3)
+        dom = max(("encode_fwd", "mlp_train_l2", "encode_bwd"), key=lambda n: per_kernel[n])
+        kb = _kernel_bytes()
+        peak, peak_src = _peaks()
+        achieved = kb[dom] * BATCH / (per_kernel[dom] / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "kind": args.kind, "global_batch": BATCH * world,
+                       "points_per_step_per_gpu": BATCH, "parallelism": "replicas (one per GPU)",
+                       "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state, no flush",
+                       "batches": "%d resident distinct batches cycled" % N_POOL},
+            "e2e": {"value": BATCH * e2e_steps * world / (ms_e2e / 1e3), "unit": "points/s",
+                    "h2d_bytes_per_step": BATCH * (2 + N_OUT) * 4, "d2h_bytes_per_step": 4},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "bytes_per_point": kb[dom]},
+            "per_kernel_ms": per_kernel,
+            "gpu_launches": args.steps * tr.n_launches_per_step,
+            "clocks": clk.summary(),
+            "final_loss": loss,
+        }
+        if comparators is not None:
+            line["comparators"] = comparators
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline_subprocess(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def encode_sweep(dev, reps=20):
+    """Encode forward+backward points/s of the simplex encoder vs the 2^d grid at d = 2..5
+    (L = 16, F = 2, T = 2^19, fp16 tables, 2^20 points), and the binary32 path."""
+    import torch
+    from paper_2311_15439_gb300 import synth
+    from paper_2311_15439_gb300.api import Encoder
+    P = 1 << 20
+    out = {}
+    for d in (2, 3, 4, 5):
+        x = torch.from_numpy(synth.uniform_points(P, d, 50 + d)).to(dev)
+        dout = torch.randn((P, 32), device=dev)
+        row = {}
+        for kind, tdt in (("simplex", "f16"), ("grid", "f16"), ("simplex", "f32")):
+            enc = Encoder(d, 16, 2, 19, 16.0, 1.38, kind=kind, table_dtype=tdt, out_dtype=tdt)
+            tab = torch.zeros(enc.table_shape(), dtype=torch.float16 if tdt == "f16" else torch.float32, device=dev)
+            grad = torch.zeros(enc.table_shape(), dtype=torch.float32, device=dev)
+            o = torch.empty((P, 32), dtype=tab.dtype, device=dev)
+            for _ in range(3):
+                enc.encode_fwd(x, tab, o)
+                enc.encode_bwd(x, dout, grad)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            s.record()
+            for _ in range(reps):
+                enc.encode_fwd(x, tab, o)
+                enc.encode_bwd(x, dout, grad)
+            e.record()
+            torch.cuda.synchronize(dev)
+            row["%s_%s" % (kind, tdt)] = P * reps / (s.elapsed_time(e) / 1e3)
+        out["d%d" % d] = row
+    return {"encode_fwd_bwd_points_per_s": out, "config": "L=16 F=2 T=2^19 base 16 growth 1.38, 2^20 points"}
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle arm (the reference of this benchmark)
+# ----------------------------------------------------------------------------------------
+def oracle_step(x, tgt, H, W, state, t):
+    """One training step of the FP64 oracle: encode, network + L2 loss, backward, scatter,
+    Adam on every table parameter (zero-gradient skip) and on the network."""
+    from oracle import adam, encoding, mlp
+    L, T, F = H.shape
+    e = encoding.simplex_encode(x, H, base_res=CFG["base_res"], growth=CFG["growth"])
+    y, acts = mlp.mlp_forward(W, e)
+    loss, dy = mlp.l2_loss(y, tgt)
+    dW, de = mlp.mlp_backward(W, acts, dy)
+    g = encoding.simplex_encode_bwd(x, de, n_levels=L, log2_T=int(T).bit_length() - 1, n_features=F,
+                                    base_res=CFG["base_res"], growth=CFG["growth"])
+    hp = dict(lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15)
+    for l in range(L):
+        H[l], state["m"][l], state["v"][l] = adam.adam_step(H[l], g[l], state["m"][l], state["v"][l], t,
+                                                            skip_zero_grad=True, **hp)
+    for i in range(len(W)):
+        W[i], state["mW"][i], state["vW"][i] = adam.adam_step(W[i], dW[i], state["mW"][i], state["vW"][i], t,
+                                                              skip_zero_grad=False, **hp)
+    return loss
+
+
+def time_oracle(sample_points, steps, seconds_cap):
+    from paper_2311_15439_gb300 import synth
+    L, T, F = CFG["n_levels"], 1 << CFG["log2_T"], CFG["n_features"]
+    H = synth.uniform_tables(L, T, F, 0, dtype="f32", scale=1e-4)[0].astype(np.float64)
+    g = np.random.Generator(np.random.PCG64(1))
+    dims = [(64, 32), (64, 64), (3, 64)]
+    W = [g.uniform(-math.sqrt(6 / fi), math.sqrt(6 / fi), size=(fo, fi)) for fo, fi in dims]
+    state = {"m": np.zeros_like(H), "v": np.zeros_like(H), "mW": [np.zeros_like(w) for w in W],
+             "vW": [np.zeros_like(w) for w in W]}
+    img = synth.ProceduralImage(seed=7, size=16384, n_waves=64)
+    done, t0 = 0, time.perf_counter()
+    times = []
+    for k in range(steps):
+        x = synth.uniform_points(sample_points, 2, 5000 + k)
+        tgt = img.sample(x)
+        s = time.perf_counter()
+        oracle_step(x, tgt, H, W, state, k + 1)
+        times.append(time.perf_counter() - s)
+        done += 1
+        if time.perf_counter() - t0 > seconds_cap:
+            break
+    return sample_points * done / sum(times), done, times
+
+
+def cpu_baseline_subprocess(seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--cpu-seconds", str(seconds)]
+    try:
+        res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+        return json.loads(res.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # report, do not fail the GPU line
+        return {"value": None, "error": repr(exc)[:200]}
+
+
+def cpu_baseline_only(seconds):
+    sample = 1 << 13
+    v, done, _ = time_oracle(sample, 1000, seconds)
+    print(json.dumps({"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
+                      "sample": "%d oracle steps of %d points each on the full workload tables "
+                               "(L=16, T=2^22, F=2; Adam over all 134M table parameters)" % (done, sample)}))
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    sample = 1 << 12
+    _, done, times = time_oracle(sample, args.warmup + args.steps, 1e9)
+    t = times[args.warmup:]
+    value = sample * len(t) / sum(t)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+        "steps": len(t), "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d-point steps of the full workload (tables L=16, T=2^22)" % sample},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kind", default="simplex", choices=["simplex", "grid"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-baseline-only", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.cpu_baseline_only:
+        cpu_baseline_only(args.cpu_seconds)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

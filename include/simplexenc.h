@@ -1,0 +1,245 @@
+/*
+ * simplexenc.h -- C ABI of the GB300 (sm_103a) simplex-grid hash encoding library.
+ *
+ * The library computes the multiresolution simplex-lattice hash encoding of
+ * Wen & Yang, "Efficient Encoding of Graphics Primitives with Simplex-based
+ * Structures" (arXiv 2311.15439), its backward pass, the tiny fully connected
+ * network that consumes it, the L2 loss of the image-fitting task and the Adam
+ * update that trains tables and network, plus the 2^d multilinear hash-grid
+ * encoder that the paper compares against.
+ *
+ * Conventions for every entry point:
+ *   - Every buffer argument is a DEVICE pointer owned by the caller unless its
+ *     comment says "host".  The library never allocates device memory and never
+ *     frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  All device work is enqueued asynchronously on that stream; the
+ *     call returns without synchronising.
+ *   - Arguments are validated on the host before anything is enqueued.  A bad
+ *     argument returns SXE_EINVAL (or SXE_EUNSUPPORTED for a valid but
+ *     unimplemented combination) and enqueues nothing.  A CUDA launch error
+ *     returns SXE_ECUDA.  No call aborts the process.  sxe_last_error() gives a
+ *     message for the last failing call on the calling thread.
+ *   - Gradient outputs accumulate (+=); the caller zeroes them when needed.
+ *   - Layouts are row-major with the last index fastest.
+ *   - Dimensions d = 2..5 are supported (the paper's n, Sec. 6.3 studies up to 7).
+ *   - Points are meant to lie in [0,1]^d (Sec. 4.2 footnote).  Points outside
+ *     it are still encoded (their lattice vertices hash like any other) as long
+ *     as every scaled, skewed coordinate stays below 2^31 in magnitude; NaN
+ *     input gives unspecified output but never an out-of-bounds access.
+ */
+#ifndef SIMPLEXENC_H
+#define SIMPLEXENC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SXE_OK = 0,
+  SXE_EINVAL = -1,        /* an argument is out of range or NULL where required */
+  SXE_EUNSUPPORTED = -2,  /* valid but not implemented (e.g. d = 7)            */
+  SXE_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed        */
+  SXE_ENOMEM = -4         /* a caller-provided workspace is too small           */
+} sxe_status;
+
+typedef enum { SXE_SIMPLEX = 0, SXE_GRID = 1 } sxe_kind;
+typedef enum { SXE_F32 = 0, SXE_F16 = 1, SXE_BF16 = 2 } sxe_dtype;
+typedef enum { SXE_RES_RAW = 0, SXE_RES_EQUAL_MEM = 1 } sxe_res_mode;
+
+#define SXE_MAX_LEVELS 32
+
+/*
+ * Encoding description (Sec. 5, Sec. 5.1, Sec. 5.2).
+ *   d            input dimension n of the paper, 2..5
+ *   n_levels     L, 1..SXE_MAX_LEVELS
+ *   n_features   F features per table entry: 1, 2, 4 or 8
+ *   log2_T       table size T = 2^log2_T entries per level, 4..26
+ *   base_res     resolution of level 0; level l has N_l = floor(base_res * growth^l)
+ *   growth       per-level growth factor (>= 1)
+ *   kind         SXE_SIMPLEX (the paper's method, n+1 vertices per level) or
+ *                SXE_GRID (the 2^n-corner multilinear comparator, Algorithm 1)
+ *   res_mode     SXE_RES_RAW, or SXE_RES_EQUAL_MEM to multiply N_l by
+ *                (n+1)^((n-1)/(2n)) as Sec. 5.2 does for equal-memory comparisons
+ *                (simplex only)
+ *   table_dtype  storage type of the feature tables read by the forward pass
+ *   out_dtype    type of the encoded output
+ */
+typedef struct {
+  int32_t d;
+  int32_t n_levels;
+  int32_t n_features;
+  int32_t log2_T;
+  double base_res;
+  double growth;
+  int32_t kind;
+  int32_t res_mode;
+  int32_t table_dtype;
+  int32_t out_dtype;
+} sxe_encoding_desc;
+
+typedef struct sxe_encoder sxe_encoder;  /* opaque: level constants only, no device memory */
+
+/* Validates `desc` and computes the per-level constants on the host (Sec. 5.1):
+ * the input multiplier N_l * m / sqrt(n+1) for the simplex (m = 1 or the Sec. 5.2
+ * factor) or N_l for the grid, in FP64 rounded once to binary32, and the skew
+ * factor F_n = (sqrt(n+1)-1)/n of Eq. 2.  *out receives a handle the caller
+ * releases with sxe_encoder_destroy.  Thread-safe; the handle is immutable. */
+sxe_status sxe_encoder_create(const sxe_encoding_desc* desc, sxe_encoder** out);
+sxe_status sxe_encoder_destroy(sxe_encoder* enc);
+
+/* Copies the binary32 per-level multipliers (host float[L]) and the integer level
+ * resolutions N_l (host int32[L]) into caller arrays; either may be NULL. */
+sxe_status sxe_encoder_level_params(const sxe_encoder* enc, float* level_scale, int32_t* level_res);
+
+/* Forward encoding, Sec. 5 steps (a)-(d): for every point and level, scale and skew
+ * (Eq. 2) the point, find its simplex by sorting the fractional parts (Sec. 4.2),
+ * weight its n+1 vertices barycentrically (Sec. 4.3), hash each vertex into that
+ * level's table and interpolate; levels are concatenated.
+ *   x       [n_points][d] binary32
+ *   tables  [L][T][F] of desc.table_dtype
+ *   out     [n_points][L*F] of desc.out_dtype (fully overwritten)
+ * n_points may be 0 (nothing is enqueued).  The binary32 scale and skew use one
+ * rounding per operation in a fixed order (p_i = x_i*s, sigma = sum left to right,
+ * t = F_n*sigma, q_i = p_i + t); ties between equal fractional parts list the
+ * lower axis first. */
+sxe_status sxe_encode_fwd(const sxe_encoder* enc, const float* x, int64_t n_points,
+                          const void* tables, void* out, void* stream);
+
+/* Backward encoding, Sec. 5 step (e): for every point, level, vertex k and feature f,
+ *   grad[(l*T + slot_k) * grad_stride + f] += w_k * dout[p][l*F + f]
+ * with the same vertices and weights as the forward pass (recomputed).
+ *   dout         [n_points][L*F] binary32
+ *   grad         binary32 gradient storage; entry (l, slot) starts at float index
+ *                (l*T + slot) * grad_stride.  grad_stride = F gives a dense [L][T][F]
+ *                array; larger strides let the gradient live inside an
+ *                interleaved optimiser-state record.  grad_stride must be a
+ *                multiple of F and the byte address of every entry a multiple of
+ *                4*F bytes (for F <= 4) or 16 bytes (F = 8).
+ *   touched      optional bitmap of L*T bits (uint32 words, bit e%32 of word e/32
+ *                for entry e = l*T + slot); every entry that receives a term gets
+ *                its bit set.  NULL disables marking.
+ * Accumulation order is unspecified (atomic adds), so results agree with the
+ * exact sum to within floating-point reassociation. */
+sxe_status sxe_encode_bwd(const sxe_encoder* enc, const float* x, int64_t n_points,
+                          const float* dout, float* grad, int64_t grad_stride,
+                          uint32_t* touched, void* stream);
+
+/* The lattice vertices the encoding reads, for testing and inspection:
+ *   slots    [n_points][L][V] uint32 table slots (0..T-1) of each vertex
+ *   weights  [n_points][L][V] binary32 interpolation weights
+ * with V = d+1 (simplex, in the walk order of Sec. 4.2: base vertex first) or
+ * V = 2^d (grid, corner b at index sum_i b_i 2^(d-1-i)).  Either pointer may be NULL. */
+sxe_status sxe_encode_vertices(const sxe_encoder* enc, const float* x, int64_t n_points,
+                               uint32_t* slots, float* weights, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Tiny fully connected network (Sec. 5 d-e; about 7k weights, Sec. 6.1).     */
+/* ------------------------------------------------------------------------ */
+
+/* n_in inputs -> n_hidden hidden layers of `width` ReLU units -> n_out linear
+ * outputs, no biases.  Supported: width = 64, n_in in {16, 32, 64},
+ * 1 <= n_hidden <= 3, 1 <= n_out <= 16, dtype SXE_F16 or SXE_BF16 (tensor-core
+ * operands; accumulation is binary32).
+ * Weight layout (`weights`, dtype; `dweights`, binary32): the matrices
+ * W_0 [width][n_in], W_1..W_{n_hidden-1} [width][width], W_out [n_out][width]
+ * stored back to back, each row-major [fan_out][fan_in]. */
+typedef struct {
+  int32_t n_in;
+  int32_t width;
+  int32_t n_hidden;
+  int32_t n_out;
+  int32_t dtype;
+} sxe_mlp_desc;
+
+/* Number of weights of the network (host). */
+int64_t sxe_mlp_n_params(const sxe_mlp_desc* desc);
+
+/* Forward pass.
+ *   in   [n_points][n_in] of desc.dtype
+ *   out  [n_points][n_out] binary32
+ *   act  optional [n_hidden][n_points][width] of desc.dtype receiving the
+ *        post-ReLU hidden activations; NULL skips. */
+sxe_status sxe_mlp_fwd(const sxe_mlp_desc* desc, const void* weights, const void* in,
+                       int64_t n_points, float* out, void* act, void* stream);
+
+/* Size in bytes of the workspace sxe_mlp_bwd needs for n_points (host). */
+int64_t sxe_mlp_bwd_workspace_bytes(const sxe_mlp_desc* desc, int64_t n_points);
+
+/* Backward pass for upstream gradient dout [n_points][n_out] (binary32).  The
+ * hidden activations are recomputed on chip from `in` (no activation buffer).
+ * The gradient is multiplied by `loss_scale` (a power of two keeps this exact)
+ * before it is rounded to desc.dtype for the tensor cores, and every binary32
+ * result is divided by it again.
+ *   din        optional [n_points][n_in] binary32, overwritten with dL/din
+ *   dweights   binary32, same layout as the weights, accumulated (+=)
+ *   workspace  device scratch of sxe_mlp_bwd_workspace_bytes() bytes; the
+ *              per-block weight-gradient partials are summed in a fixed order,
+ *              so dweights is deterministic.  SXE_ENOMEM if it is too small. */
+sxe_status sxe_mlp_bwd(const sxe_mlp_desc* desc, const void* weights, const void* in,
+                       const float* dout, float loss_scale, int64_t n_points,
+                       float* din, float* dweights, void* workspace, int64_t workspace_bytes,
+                       void* stream);
+
+/* Forward pass, L2 loss and backward pass in one sweep over the points (Sec. 6.1
+ * image fitting): with y the network output, the upstream gradient is
+ * dy = 2 (y - target) / (n_points*n_out); *sq_sum (one binary32 device
+ * scalar) is overwritten with the batch's sum of squared residuals, summed in a
+ * fixed order.  Other arguments as sxe_mlp_bwd. */
+sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* desc, const void* weights, const void* in,
+                            const float* target, float loss_scale, int64_t n_points,
+                            float* din, float* dweights, float* sq_sum,
+                            void* workspace, int64_t workspace_bytes, void* stream);
+
+/* L2 loss of the image-fitting task (Sec. 6.1): mean over n_points*n_out of
+ * (y - target)^2.  Writes dy = 2 (y - target) / (n_points*n_out) (binary32,
+ * overwritten) and adds the batch's sum of squared residuals to *sq_sum
+ * (one binary32 device scalar). */
+sxe_status sxe_loss_l2(const float* y, const float* target, int64_t n_points, int32_t n_out,
+                       float* dy, float* sq_sum, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Adam (Kingma & Ba, Algorithm 1), binary32 master copy                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  float lr;
+  float beta1;
+  float beta2;
+  float eps;
+  int32_t skip_zero_grad;  /* 1: a parameter whose gradient is exactly 0 keeps its
+                              value and moments (rule used for hash-table entries) */
+} sxe_adam_desc;
+
+/* Dense step over n parameters at 1-based step t:
+ *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *   param -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
+ * param, m, v, grad: [n] binary32 (grad is read, then zeroed).  param_lowp:
+ * optional [n] of lowp_dtype (SXE_F16 / SXE_BF16 / SXE_F32) receiving the
+ * rounded new parameters; NULL skips. */
+sxe_status sxe_step(const sxe_adam_desc* desc, int64_t t, int64_t n, float* param, float* m,
+                    float* v, float* grad, void* param_lowp, int32_t lowp_dtype, void* stream);
+
+/* Table step over the entries marked in `touched` (n_entries bits), for the
+ * interleaved state layout state[e] = {param[F], m[F], v[F], grad[F]} (binary32,
+ * 16*F bytes per entry; its gradient is what sxe_encode_bwd writes with
+ * grad = state + 3F and grad_stride = 4F).  Each marked entry takes the update
+ * of sxe_step with skip_zero_grad forced on (entries never marked have gradient
+ * zero and are skipped by the same rule), writes table_lowp[e*F..] in
+ * lowp_dtype, zeroes its gradient and clears its bit. */
+sxe_status sxe_step_touched(const sxe_adam_desc* desc, int64_t t, int64_t n_entries,
+                            int32_t n_features, float* state, uint32_t* touched,
+                            void* table_lowp, int32_t lowp_dtype, void* stream);
+
+/* Thread-local message describing the last failing call on this thread ("" if none). */
+const char* sxe_last_error(void);
+
+/* Library version string. */
+const char* sxe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMPLEXENC_H */

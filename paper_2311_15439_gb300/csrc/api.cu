@@ -1,0 +1,261 @@
+// C ABI of libsimplexenc: argument validation, level constants, dispatch.
+// Every entry point checks its arguments on the host, enqueues nothing on error and
+// returns a status; the message of the last failure is kept per thread.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sxe_internal.cuh"
+
+namespace sxe {
+
+static thread_local char g_err[512] = "";
+
+sxe_status set_error(sxe_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+sxe_status check_launch(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(SXE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return SXE_OK;
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+static size_t dtype_size(int32_t dt) { return dt == SXE_F32 ? 4 : 2; }
+static bool valid_dtype(int32_t dt) { return dt == SXE_F32 || dt == SXE_F16 || dt == SXE_BF16; }
+
+}  // namespace sxe
+
+using namespace sxe;
+
+extern "C" {
+
+const char* sxe_last_error(void) { return g_err; }
+
+const char* sxe_version(void) { return "simplexenc 0.1 (sm_103a)"; }
+
+sxe_status sxe_encoder_create(const sxe_encoding_desc* d, sxe_encoder** out) {
+  g_err[0] = 0;
+  if (!d || !out) return set_error(SXE_EINVAL, "encoder_create: NULL argument");
+  if (d->d < 1 || d->d > 16) return set_error(SXE_EINVAL, "encoder_create: d=%d out of range", d->d);
+  if (d->d < 2 || d->d > 5) return set_error(SXE_EUNSUPPORTED, "encoder_create: d=%d not built (2..5)", d->d);
+  if (d->n_levels < 1 || d->n_levels > SXE_MAX_LEVELS)
+    return set_error(SXE_EINVAL, "encoder_create: n_levels=%d out of 1..%d", d->n_levels, SXE_MAX_LEVELS);
+  if (!(d->n_features == 1 || d->n_features == 2 || d->n_features == 4 || d->n_features == 8))
+    return set_error(SXE_EINVAL, "encoder_create: n_features=%d not in {1,2,4,8}", d->n_features);
+  if (d->log2_T < 4 || d->log2_T > 26) return set_error(SXE_EINVAL, "encoder_create: log2_T=%d out of 4..26", d->log2_T);
+  if (!(d->base_res >= 1.0) || !(d->growth >= 1.0) || !std::isfinite(d->base_res) || !std::isfinite(d->growth))
+    return set_error(SXE_EINVAL, "encoder_create: base_res and growth must be finite and >= 1");
+  if (d->kind != SXE_SIMPLEX && d->kind != SXE_GRID) return set_error(SXE_EINVAL, "encoder_create: bad kind");
+  if (d->res_mode != SXE_RES_RAW && d->res_mode != SXE_RES_EQUAL_MEM)
+    return set_error(SXE_EINVAL, "encoder_create: bad res_mode");
+  if (d->kind == SXE_GRID && d->res_mode != SXE_RES_RAW)
+    return set_error(SXE_EINVAL, "encoder_create: res_mode applies to the simplex encoder only");
+  if (!valid_dtype(d->table_dtype) || !valid_dtype(d->out_dtype))
+    return set_error(SXE_EINVAL, "encoder_create: bad dtype");
+  const int64_t elems = ((int64_t)d->n_levels << d->log2_T) * d->n_features;
+  if (elems >= ((int64_t)1 << 34)) return set_error(SXE_EINVAL, "encoder_create: tables too large");
+
+  sxe_encoder* e = new (std::nothrow) sxe_encoder;
+  if (!e) return set_error(SXE_ENOMEM, "encoder_create: out of host memory");
+  std::memset(e, 0, sizeof(*e));
+  e->desc = *d;
+  const double n = (double)d->d;
+  // Eq. 2: F_n = (sqrt(n+1) - 1) / n.  Sec. 5.1: simplex input multiplier N_l * m / sqrt(n+1),
+  // m = 1 or (n+1)^((n-1)/(2n)) (Sec. 5.2); grid multiplier N_l.  FP64, rounded once.
+  const double m = d->res_mode == SXE_RES_EQUAL_MEM ? std::pow(n + 1.0, (n - 1.0) / (2.0 * n)) : 1.0;
+  for (int l = 0; l < d->n_levels; ++l) {
+    const double N = std::floor(d->base_res * std::pow(d->growth, (double)l));
+    if (N > 1.0e9) {
+      delete e;
+      return set_error(SXE_EINVAL, "encoder_create: level %d resolution %.0f too large", l, N);
+    }
+    e->level_res[l] = (int32_t)N;
+    e->prm.scale[l] = d->kind == SXE_SIMPLEX ? (float)(N * m / std::sqrt(n + 1.0)) : (float)N;
+  }
+  e->prm.n_levels = d->n_levels;
+  e->prm.log2_T = d->log2_T;
+  e->prm.out_dtype = d->out_dtype;
+  e->prm.skew_F = (float)((std::sqrt(n + 1.0) - 1.0) / n);
+  *out = e;
+  return SXE_OK;
+}
+
+sxe_status sxe_encoder_destroy(sxe_encoder* e) {
+  delete e;
+  return SXE_OK;
+}
+
+sxe_status sxe_encoder_level_params(const sxe_encoder* e, float* scale, int32_t* res) {
+  if (!e) return set_error(SXE_EINVAL, "encoder_level_params: NULL encoder");
+  for (int l = 0; l < e->desc.n_levels; ++l) {
+    if (scale) scale[l] = e->prm.scale[l];
+    if (res) res[l] = e->level_res[l];
+  }
+  return SXE_OK;
+}
+
+static sxe_status check_points(const char* fn, const sxe_encoder* e, const float* x, int64_t P) {
+  if (!e) return set_error(SXE_EINVAL, "%s: NULL encoder", fn);
+  if (P < 0 || P > ((int64_t)1 << 40) / e->desc.n_levels) return set_error(SXE_EINVAL, "%s: n_points=%lld out of range", fn, (long long)P);
+  if (P > 0 && !x) return set_error(SXE_EINVAL, "%s: NULL x", fn);
+  const size_t xa = e->desc.d == 2 ? 8 : e->desc.d == 4 ? 16 : 4;
+  if (!aligned(x, xa)) return set_error(SXE_EINVAL, "%s: x must be %zu-byte aligned for d=%d", fn, xa, e->desc.d);
+  return SXE_OK;
+}
+
+sxe_status sxe_encode_fwd(const sxe_encoder* e, const float* x, int64_t P, const void* tables, void* out,
+                          void* stream) {
+  sxe_status st = check_points("encode_fwd", e, x, P);
+  if (st != SXE_OK) return st;
+  if (P == 0) return SXE_OK;
+  if (!tables || !out) return set_error(SXE_EINVAL, "encode_fwd: NULL tables or out");
+  const int F = e->desc.n_features;
+  const size_t ta = std::min<size_t>(16, F * dtype_size(e->desc.table_dtype));
+  if (!aligned(tables, ta)) return set_error(SXE_EINVAL, "encode_fwd: tables must be %zu-byte aligned", ta);
+  const size_t oa = F == 2 ? 2 * dtype_size(e->desc.out_dtype) : dtype_size(e->desc.out_dtype);
+  if (!aligned(out, oa)) return set_error(SXE_EINVAL, "encode_fwd: out must be %zu-byte aligned", oa);
+  return launch_encode_fwd(e, x, P, tables, out, (cudaStream_t)stream);
+}
+
+sxe_status sxe_encode_bwd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* grad,
+                          int64_t grad_stride, uint32_t* touched, void* stream) {
+  sxe_status st = check_points("encode_bwd", e, x, P);
+  if (st != SXE_OK) return st;
+  if (P == 0) return SXE_OK;
+  if (!dout || !grad) return set_error(SXE_EINVAL, "encode_bwd: NULL dout or grad");
+  const int F = e->desc.n_features;
+  if (grad_stride < F || grad_stride % F != 0 || grad_stride > (1 << 16))
+    return set_error(SXE_EINVAL, "encode_bwd: grad_stride=%lld must be a multiple of F=%d", (long long)grad_stride, F);
+  const size_t ga = F == 1 ? 4 : F == 2 ? 8 : 16;
+  if (!aligned(grad, ga) || ((grad_stride * 4) % ga) != 0)
+    return set_error(SXE_EINVAL, "encode_bwd: gradient entries must be %zu-byte aligned", ga);
+  if (!aligned(dout, F == 2 ? 8 : 4)) return set_error(SXE_EINVAL, "encode_bwd: dout misaligned");
+  if (touched && !aligned(touched, 4)) return set_error(SXE_EINVAL, "encode_bwd: touched misaligned");
+  return launch_encode_bwd(e, x, P, dout, grad, grad_stride, touched, (cudaStream_t)stream);
+}
+
+sxe_status sxe_encode_vertices(const sxe_encoder* e, const float* x, int64_t P, uint32_t* slots, float* weights,
+                               void* stream) {
+  sxe_status st = check_points("encode_vertices", e, x, P);
+  if (st != SXE_OK) return st;
+  if (P == 0 || (!slots && !weights)) return SXE_OK;
+  return launch_encode_vertices(e, x, P, slots, weights, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+static sxe_status check_mlp(const char* fn, const sxe_mlp_desc* d) {
+  if (!d) return set_error(SXE_EINVAL, "%s: NULL desc", fn);
+  if (d->width != 64) return set_error(SXE_EUNSUPPORTED, "%s: width=%d (only 64 is built)", fn, d->width);
+  if (!(d->n_in == 16 || d->n_in == 32 || d->n_in == 64))
+    return set_error(SXE_EUNSUPPORTED, "%s: n_in=%d not in {16,32,64}", fn, d->n_in);
+  if (d->n_hidden < 1 || d->n_hidden > 3) return set_error(SXE_EUNSUPPORTED, "%s: n_hidden=%d not in 1..3", fn, d->n_hidden);
+  if (d->n_out < 1 || d->n_out > 16) return set_error(SXE_EINVAL, "%s: n_out=%d not in 1..16", fn, d->n_out);
+  if (d->dtype != SXE_F16 && d->dtype != SXE_BF16) return set_error(SXE_EINVAL, "%s: dtype must be F16 or BF16", fn);
+  return SXE_OK;
+}
+
+int64_t sxe_mlp_n_params(const sxe_mlp_desc* d) {
+  if (!d) return 0;
+  return (int64_t)d->width * d->n_in + (int64_t)(d->n_hidden - 1) * d->width * d->width + (int64_t)d->n_out * d->width;
+}
+
+sxe_status sxe_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,
+                       void* stream) {
+  sxe_status st = check_mlp("mlp_fwd", d);
+  if (st != SXE_OK) return st;
+  if (P < 0) return set_error(SXE_EINVAL, "mlp_fwd: n_points < 0");
+  if (P == 0) return SXE_OK;
+  if (!W || !in || !out) return set_error(SXE_EINVAL, "mlp_fwd: NULL weights, in or out");
+  if (!aligned(in, 16) || !aligned(W, 4) || (act && !aligned(act, 4)))
+    return set_error(SXE_EINVAL, "mlp_fwd: in must be 16-byte aligned, weights/act 4-byte aligned");
+  return launch_mlp_fwd(d, W, in, P, out, act, (cudaStream_t)stream);
+}
+
+int64_t sxe_mlp_bwd_workspace_bytes(const sxe_mlp_desc* d, int64_t P) {
+  if (!d || P <= 0) return 0;
+  return (int64_t)mlp_grid_blocks(P) * (sxe_mlp_n_params(d) + 1) * (int64_t)sizeof(float);
+}
+
+static sxe_status mlp_bwd_common(const char* fn, const sxe_mlp_desc* d, const void* W, const void* in,
+                                 const float* dout, const float* target, float loss_scale, int64_t P, float* din,
+                                 float* dW, float* sq_sum, void* ws, int64_t ws_bytes, void* stream) {
+  sxe_status st = check_mlp(fn, d);
+  if (st != SXE_OK) return st;
+  if (P < 0) return set_error(SXE_EINVAL, "%s: n_points < 0", fn);
+  if (P == 0) return SXE_OK;
+  if (!W || !in || !dW || !ws) return set_error(SXE_EINVAL, "%s: NULL weights, in, dweights or workspace", fn);
+  if (!(loss_scale > 0.f) || !std::isfinite(loss_scale)) return set_error(SXE_EINVAL, "%s: loss_scale must be > 0", fn);
+  if (!aligned(in, 16) || !aligned(W, 4) || !aligned(ws, 4) || (din && !aligned(din, 8)))
+    return set_error(SXE_EINVAL, "%s: misaligned buffer", fn);
+  const int64_t need = sxe_mlp_bwd_workspace_bytes(d, P);
+  if (ws_bytes < need) return set_error(SXE_ENOMEM, "%s: workspace %lld < %lld bytes", fn, (long long)ws_bytes, (long long)need);
+  return launch_mlp_bwd(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, (float*)ws, mlp_grid_blocks(P),
+                        (cudaStream_t)stream);
+}
+
+sxe_status sxe_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, float loss_scale,
+                       int64_t P, float* din, float* dW, void* ws, int64_t ws_bytes, void* stream) {
+  if (P > 0 && !dout) return set_error(SXE_EINVAL, "mlp_bwd: NULL dout");
+  return mlp_bwd_common("mlp_bwd", d, W, in, dout, nullptr, loss_scale, P, din, dW, nullptr, ws, ws_bytes, stream);
+}
+
+sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* d, const void* W, const void* in, const float* target,
+                            float loss_scale, int64_t P, float* din, float* dW, float* sq_sum, void* ws,
+                            int64_t ws_bytes, void* stream) {
+  if (P > 0 && (!target || !sq_sum)) return set_error(SXE_EINVAL, "mlp_train_l2: NULL target or sq_sum");
+  return mlp_bwd_common("mlp_train_l2", d, W, in, nullptr, target, loss_scale, P, din, dW, sq_sum, ws, ws_bytes,
+                        stream);
+}
+
+sxe_status sxe_loss_l2(const float* y, const float* target, int64_t P, int32_t n_out, float* dy, float* sq_sum,
+                       void* stream) {
+  if (P < 0 || n_out < 1) return set_error(SXE_EINVAL, "loss_l2: bad sizes");
+  if (P == 0) return SXE_OK;
+  if (!y || !target || !dy || !sq_sum) return set_error(SXE_EINVAL, "loss_l2: NULL argument");
+  return launch_loss_l2(y, target, P, n_out, dy, sq_sum, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+static sxe_status check_adam(const char* fn, const sxe_adam_desc* a, int64_t t) {
+  if (!a) return set_error(SXE_EINVAL, "%s: NULL desc", fn);
+  if (t < 1) return set_error(SXE_EINVAL, "%s: step t must be >= 1", fn);
+  if (!(a->lr >= 0.f) || !(a->beta1 >= 0.f && a->beta1 < 1.f) || !(a->beta2 >= 0.f && a->beta2 < 1.f) ||
+      !(a->eps >= 0.f))
+    return set_error(SXE_EINVAL, "%s: bad hyper-parameters", fn);
+  return SXE_OK;
+}
+
+sxe_status sxe_step(const sxe_adam_desc* a, int64_t t, int64_t n, float* p, float* m, float* v, float* g,
+                    void* lowp, int32_t lowp_dtype, void* stream) {
+  sxe_status st = check_adam("step", a, t);
+  if (st != SXE_OK) return st;
+  if (n < 0) return set_error(SXE_EINVAL, "step: n < 0");
+  if (n == 0) return SXE_OK;
+  if (!p || !m || !v || !g) return set_error(SXE_EINVAL, "step: NULL param, m, v or grad");
+  if (lowp && !valid_dtype(lowp_dtype)) return set_error(SXE_EINVAL, "step: bad lowp dtype");
+  return launch_adam_dense(a, t, n, p, m, v, g, lowp, lowp_dtype, (cudaStream_t)stream);
+}
+
+sxe_status sxe_step_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries, int32_t F, float* state,
+                            uint32_t* touched, void* lowp, int32_t lowp_dtype, void* stream) {
+  sxe_status st = check_adam("step_touched", a, t);
+  if (st != SXE_OK) return st;
+  if (n_entries < 0) return set_error(SXE_EINVAL, "step_touched: n_entries < 0");
+  if (!(F == 1 || F == 2 || F == 4 || F == 8)) return set_error(SXE_EINVAL, "step_touched: F=%d", F);
+  if (n_entries == 0) return SXE_OK;
+  if (!state || !touched || !lowp) return set_error(SXE_EINVAL, "step_touched: NULL state, touched or table");
+  if (!valid_dtype(lowp_dtype)) return set_error(SXE_EINVAL, "step_touched: bad lowp dtype");
+  if (!aligned(state, 16) || !aligned(touched, 4)) return set_error(SXE_EINVAL, "step_touched: misaligned buffer");
+  return launch_adam_touched(a, t, n_entries, F, state, touched, lowp, lowp_dtype, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+// Multiresolution simplex / grid hash encoding kernels (Sec. 5 a-e of arXiv 2311.15439,
+// and the 2^d grid of Algorithm 1 as comparator).
+//
+// Work item = one (point, level) pair, flattened as i = p * L + l so that consecutive
+// threads write consecutive F-feature groups of the [P][L*F] output (coalesced) and
+// read consecutive groups of dout.  Every item issues its V = d+1 (simplex) or 2^d
+// (grid) independent gathers before it consumes any of them.
+#include "sxe_internal.cuh"
+
+namespace sxe {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <bool SIMPLEX, int D> struct Verts { static constexpr int V = SIMPLEX ? D + 1 : (1 << D); };
+
+template <bool SIMPLEX, int D>
+__device__ __forceinline__ void lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
+                                        uint32_t (&slot)[Verts<SIMPLEX, D>::V], float (&w)[Verts<SIMPLEX, D>::V]) {
+  if constexpr (SIMPLEX) simplex_lattice<D>(x, s, skewF, mask, slot, w);
+  else grid_lattice<D>(x, s, mask, slot, w);
+}
+
+// Decode work item i into (point, level) with small 32-bit divisions.
+struct Item { int64_t p; int l; };
+__device__ __forceinline__ Item item_of(int L) {
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int64_t p0 = base / L;
+  const int j = (int)(base - p0 * L) + (int)threadIdx.x;
+  const int q = j / L;
+  return Item{p0 + q, j - q * L};
+}
+
+template <int D>
+__device__ __forceinline__ void load_point(const float* __restrict__ x, int64_t p, float (&v)[D]) {
+  if constexpr (D == 2) {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(x) + p);
+    v[0] = a.x; v[1] = a.y;
+  } else if constexpr (D == 4) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(x) + p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = __ldg(x + p * D + i);
+  }
+}
+
+template <bool SIMPLEX, int D, int F, typename TT>
+__global__ void __launch_bounds__(kThreads)
+encode_fwd_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__ tables,
+                  void* __restrict__ out, const EncParams prm) {
+  constexpr int V = Verts<SIMPLEX, D>::V;
+  __shared__ float s_scale[SXE_MAX_LEVELS];
+  if (threadIdx.x < SXE_MAX_LEVELS) s_scale[threadIdx.x] = prm.scale[threadIdx.x];
+  __syncthreads();
+  const int L = prm.n_levels;
+  const Item it = item_of(L);
+  if (it.p >= P) return;
+  float xv[D];
+  load_point<D>(x, it.p, xv);
+  const uint32_t mask = (1u << prm.log2_T) - 1u;
+  uint32_t slot[V];
+  float w[V];
+  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
+  const TT* tab = tables + ((int64_t)it.l << prm.log2_T) * F;
+  float val[V][F];
+#pragma unroll
+  for (int k = 0; k < V; ++k) load_entry<TT, F>(tab + (int64_t)slot[k] * F, val[k]);
+  float acc[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) acc[f] = 0.f;
+#pragma unroll
+  for (int k = 0; k < V; ++k)
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = fmaf(w[k], val[k][f], acc[f]);
+  const int64_t o = (it.p * L + it.l) * F;
+  if (prm.out_dtype == SXE_F32) {
+    float* po = reinterpret_cast<float*>(out) + o;
+    if constexpr (F == 2) *reinterpret_cast<float2*>(po) = make_float2(acc[0], acc[1]);
+    else {
+#pragma unroll
+      for (int f = 0; f < F; ++f) po[f] = acc[f];
+    }
+  } else if (prm.out_dtype == SXE_F16) {
+    __half* po = reinterpret_cast<__half*>(out) + o;
+    if constexpr (F == 2) *reinterpret_cast<__half2*>(po) = __floats2half2_rn(acc[0], acc[1]);
+    else {
+#pragma unroll
+      for (int f = 0; f < F; ++f) po[f] = __float2half_rn(acc[f]);
+    }
+  } else {
+    __nv_bfloat16* po = reinterpret_cast<__nv_bfloat16*>(out) + o;
+    if constexpr (F == 2) *reinterpret_cast<__nv_bfloat162*>(po) = __floats2bfloat162_rn(acc[0], acc[1]);
+    else {
+#pragma unroll
+      for (int f = 0; f < F; ++f) po[f] = __float2bfloat16_rn(acc[f]);
+    }
+  }
+}
+
+template <bool SIMPLEX, int D, int F>
+__global__ void __launch_bounds__(kThreads)
+encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restrict__ dout,
+                  float* __restrict__ grad, int64_t stride, uint32_t* __restrict__ touched,
+                  const EncParams prm) {
+  constexpr int V = Verts<SIMPLEX, D>::V;
+  __shared__ float s_scale[SXE_MAX_LEVELS];
+  if (threadIdx.x < SXE_MAX_LEVELS) s_scale[threadIdx.x] = prm.scale[threadIdx.x];
+  __syncthreads();
+  const int L = prm.n_levels;
+  const Item it = item_of(L);
+  if (it.p >= P) return;
+  float g[F];
+  const float* pd = dout + (it.p * L + it.l) * F;
+  if constexpr (F == 2) {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(pd));
+    g[0] = a.x; g[1] = a.y;
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) g[f] = __ldg(pd + f);
+  }
+  float xv[D];
+  load_point<D>(x, it.p, xv);
+  const uint32_t mask = (1u << prm.log2_T) - 1u;
+  uint32_t slot[V];
+  float w[V];
+  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
+  const int64_t lbase = (int64_t)it.l << prm.log2_T;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    float c[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) c[f] = w[k] * g[f];
+    const int64_t e = lbase + slot[k];
+    atomic_add_entry<F>(grad + e * stride, c);
+    if (touched) {
+      const uint32_t bit = 1u << (uint32_t)(e & 31);
+      uint32_t* word = touched + (e >> 5);
+      if (!(__ldcg(word) & bit)) atomicOr(word, bit);
+    }
+  }
+}
+
+template <bool SIMPLEX, int D>
+__global__ void __launch_bounds__(kThreads)
+encode_vertices_kernel(const float* __restrict__ x, int64_t P, uint32_t* __restrict__ slots,
+                       float* __restrict__ weights, const EncParams prm) {
+  constexpr int V = Verts<SIMPLEX, D>::V;
+  const int L = prm.n_levels;
+  const Item it = item_of(L);
+  if (it.p >= P) return;
+  float xv[D];
+  load_point<D>(x, it.p, xv);
+  uint32_t slot[V];
+  float w[V];
+  lattice<SIMPLEX, D>(xv, prm.scale[it.l], prm.skew_F, (1u << prm.log2_T) - 1u, slot, w);
+  const int64_t o = (it.p * L + it.l) * V;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (slots) slots[o + k] = slot[k];
+    if (weights) weights[o + k] = w[k];
+  }
+}
+
+inline unsigned grid_for(int64_t P, int L) { return (unsigned)((P * L + kThreads - 1) / kThreads); }
+
+// ---- dispatch ---------------------------------------------------------------
+template <bool SIMPLEX, int D, int F>
+sxe_status fwd_tt(const sxe_encoder* enc, const float* x, int64_t P, const void* tab, void* out, cudaStream_t s) {
+  const unsigned g = grid_for(P, enc->prm.n_levels);
+  switch (enc->desc.table_dtype) {
+    case SXE_F32: encode_fwd_kernel<SIMPLEX, D, F, float><<<g, kThreads, 0, s>>>(x, P, (const float*)tab, out, enc->prm); break;
+    case SXE_F16: encode_fwd_kernel<SIMPLEX, D, F, __half><<<g, kThreads, 0, s>>>(x, P, (const __half*)tab, out, enc->prm); break;
+    default: encode_fwd_kernel<SIMPLEX, D, F, __nv_bfloat16><<<g, kThreads, 0, s>>>(x, P, (const __nv_bfloat16*)tab, out, enc->prm); break;
+  }
+  return check_launch("encode_fwd");
+}
+
+template <bool SIMPLEX, int D>
+sxe_status fwd_f(const sxe_encoder* e, const float* x, int64_t P, const void* t, void* o, cudaStream_t s) {
+  switch (e->desc.n_features) {
+    case 1: return fwd_tt<SIMPLEX, D, 1>(e, x, P, t, o, s);
+    case 2: return fwd_tt<SIMPLEX, D, 2>(e, x, P, t, o, s);
+    case 4: return fwd_tt<SIMPLEX, D, 4>(e, x, P, t, o, s);
+    default: return fwd_tt<SIMPLEX, D, 8>(e, x, P, t, o, s);
+  }
+}
+
+template <bool SIMPLEX>
+sxe_status fwd_d(const sxe_encoder* e, const float* x, int64_t P, const void* t, void* o, cudaStream_t s) {
+  switch (e->desc.d) {
+    case 2: return fwd_f<SIMPLEX, 2>(e, x, P, t, o, s);
+    case 3: return fwd_f<SIMPLEX, 3>(e, x, P, t, o, s);
+    case 4: return fwd_f<SIMPLEX, 4>(e, x, P, t, o, s);
+    default: return fwd_f<SIMPLEX, 5>(e, x, P, t, o, s);
+  }
+}
+
+template <bool SIMPLEX, int D, int F>
+sxe_status bwd_f(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
+                 uint32_t* touched, cudaStream_t s) {
+  encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, e->prm.n_levels), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm);
+  return check_launch("encode_bwd");
+}
+
+template <bool SIMPLEX, int D>
+sxe_status bwd_fd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
+                  uint32_t* t, cudaStream_t s) {
+  switch (e->desc.n_features) {
+    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, s);
+    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, s);
+    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, s);
+    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, s);
+  }
+}
+
+template <bool SIMPLEX>
+sxe_status bwd_d(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
+                 uint32_t* t, cudaStream_t s) {
+  switch (e->desc.d) {
+    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, s);
+    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, s);
+    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, s);
+    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, s);
+  }
+}
+
+template <bool SIMPLEX>
+sxe_status verts_d(const sxe_encoder* e, const float* x, int64_t P, uint32_t* sl, float* w, cudaStream_t s) {
+  const unsigned g = grid_for(P, e->prm.n_levels);
+  switch (e->desc.d) {
+    case 2: encode_vertices_kernel<SIMPLEX, 2><<<g, kThreads, 0, s>>>(x, P, sl, w, e->prm); break;
+    case 3: encode_vertices_kernel<SIMPLEX, 3><<<g, kThreads, 0, s>>>(x, P, sl, w, e->prm); break;
+    case 4: encode_vertices_kernel<SIMPLEX, 4><<<g, kThreads, 0, s>>>(x, P, sl, w, e->prm); break;
+    default: encode_vertices_kernel<SIMPLEX, 5><<<g, kThreads, 0, s>>>(x, P, sl, w, e->prm); break;
+  }
+  return check_launch("encode_vertices");
+}
+
+}  // namespace
+
+sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables, void* out,
+                             cudaStream_t s) {
+  return enc->desc.kind == SXE_SIMPLEX ? fwd_d<true>(enc, x, P, tables, out, s)
+                                       : fwd_d<false>(enc, x, P, tables, out, s);
+}
+
+sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout, float* grad,
+                             int64_t stride, uint32_t* touched, cudaStream_t s) {
+  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, s)
+                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, s);
+}
+
+sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,
+                                  float* weights, cudaStream_t s) {
+  return enc->desc.kind == SXE_SIMPLEX ? verts_d<true>(enc, x, P, slots, weights, s)
+                                       : verts_d<false>(enc, x, P, slots, weights, s);
+}
+
+}  // namespace sxe

@@ -1,0 +1,562 @@
+// Tiny fully connected ReLU network on the tensor cores (Sec. 5 d-e, Sec. 6.1 of
+// arXiv 2311.15439: the encoding feeds a ~7k-weight network; the loss gradient flows
+// back through it into the encoding).
+//
+// Shapes: n_in -> NH hidden layers of 64 ReLU units -> n_out (<= 16) linear outputs,
+// no biases.  One CTA = 8 warps works on tiles of 128 points (16 per warp); the whole
+// network lives in shared memory, activations stay in registers between layers (the
+// C fragment of one m16n8k16 product is the A fragment of the next).
+//
+// The backward kernel recomputes the forward pass of its tile (cheaper than writing
+// and re-reading activations), stages inputs, activations and deltas of the tile in
+// shared memory and accumulates the weight gradients dW_l = Delta_l^T In_l for the
+// whole persistent loop in registers; per-CTA partials go to a workspace and a second
+// kernel sums them in a fixed order (deterministic).
+#include <algorithm>
+#include <type_traits>
+
+#include "sxe_internal.cuh"
+
+namespace sxe {
+namespace {
+
+constexpr int kWidth = 64;
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kTile = kWarps * 16;   // points per tile
+constexpr int kSW = kWidth + 8;      // padded row stride (halves) of 64-wide tiles
+constexpr int kSO = 16 + 8;          // padded row stride of 16-wide tiles
+
+template <typename T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+  __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+template <typename T> __device__ __forceinline__ float2 unpack2(uint32_t u);
+template <> __device__ __forceinline__ float2 unpack2<__half>(uint32_t u) {
+  return __half22float2(*reinterpret_cast<__half2*>(&u));
+}
+template <> __device__ __forceinline__ float2 unpack2<__nv_bfloat16>(uint32_t u) {
+  return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u));
+}
+
+template <typename T>
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  } else {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  }
+}
+
+__device__ __forceinline__ uint32_t lds32(const void* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ void sts32(void* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t& r0, uint32_t& r1, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+// B fragment (k16 x n8) of a row-major [n][k] shared array with row stride `ld` (halves).
+template <typename T>
+__device__ __forceinline__ void bfrag(const T* W, int ld, int nt, int kk, int g, int t, uint32_t& b0, uint32_t& b1) {
+  const T* row = W + (nt * 8 + g) * ld + kk * 16 + 2 * t;
+  b0 = lds32(row);
+  b1 = lds32(row + 8);
+}
+
+// Shared-memory plan of one CTA (offsets in halves).
+template <int N_IN, int NH>
+struct Smem {
+  static constexpr int SX = N_IN + 8;
+  static constexpr int W0 = 0;                                  // [64][SX]      W_0
+  static constexpr int W0T = W0 + kWidth * SX;                  // [N_IN][kSW]   W_0^T
+  static constexpr int WH = W0T + N_IN * kSW;                   // (NH-1) x [64][kSW]  W_h
+  static constexpr int WHT = WH + (NH - 1) * kWidth * kSW;      // (NH-1) x [64][kSW]  W_h^T
+  static constexpr int WO = WHT + (NH - 1) * kWidth * kSW;      // [16][kSW]     W_out (zero padded)
+  static constexpr int WOT = WO + 16 * kSW;                     // [64][kSO]     W_out^T
+  static constexpr int X = WOT + kWidth * kSO;                  // [128][SX]     inputs of the tile
+  static constexpr int A = X + kTile * SX;                      // NH x [128][kSW] hidden activations
+  static constexpr int D = A + NH * kTile * kSW;                // NH x [128][kSW] hidden deltas
+  static constexpr int DY = D + NH * kTile * kSW;               // [128][kSO]    output delta
+  static constexpr int FWD_END = A;                             // forward-only kernels stop here
+  static constexpr int END = DY + kTile * kSO;
+  // weight-gradient tiles: output layer 1x8, hidden 4x8 each, first layer 4x(N_IN/8)
+  static constexpr int N_WTILES = 8 + (NH - 1) * 32 + 4 * (N_IN / 8);
+  static constexpr int TILES_PER_WARP = (N_WTILES + kWarps - 1) / kWarps;
+};
+
+// Load W (global, [fan_out][fan_in] back to back) into the padded shared copies.
+template <typename T, int N_IN, int NH>
+__device__ void load_weights(const T* __restrict__ W, int n_out, T* sm, bool transposed) {
+  using S = Smem<N_IN, NH>;
+  const T zero = from_f32<T>(0.f);
+  for (int i = threadIdx.x; i < kWidth * N_IN; i += blockDim.x) {
+    const int r = i / N_IN, c = i % N_IN;
+    const T v = W[i];
+    sm[S::W0 + r * S::SX + c] = v;
+    if (transposed) sm[S::W0T + c * kSW + r] = v;
+  }
+  const T* Wh = W + kWidth * N_IN;
+  for (int h = 0; h < NH - 1; ++h) {
+    for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
+      const int r = i / kWidth, c = i % kWidth;
+      const T v = Wh[h * kWidth * kWidth + i];
+      sm[S::WH + h * kWidth * kSW + r * kSW + c] = v;
+      if (transposed) sm[S::WHT + h * kWidth * kSW + c * kSW + r] = v;
+    }
+  }
+  const T* Wo = Wh + (NH - 1) * kWidth * kWidth;
+  for (int i = threadIdx.x; i < 16 * kWidth; i += blockDim.x) {
+    const int r = i / kWidth, c = i % kWidth;
+    const T v = r < n_out ? Wo[r * kWidth + c] : zero;
+    sm[S::WO + r * kSW + c] = v;
+    if (transposed) sm[S::WOT + c * kSO + r] = v;
+  }
+}
+
+// Stage the tile's inputs [128][N_IN] into shared memory (zero rows past P).
+template <typename T, int N_IN, int NH>
+__device__ __forceinline__ void load_inputs(const T* __restrict__ in, int64_t row0, int64_t P, T* sm) {
+  using S = Smem<N_IN, NH>;
+  constexpr int VPR = N_IN * 2 / 16;  // 16-byte vectors per row
+  for (int i = threadIdx.x; i < kTile * VPR; i += blockDim.x) {
+    const int r = i / VPR, c = i % VPR;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (row0 + r < P) v = __ldg(reinterpret_cast<const uint4*>(in + (row0 + r) * N_IN) + c);
+    *reinterpret_cast<uint4*>(sm + S::X + r * S::SX + c * 8) = v;
+  }
+}
+
+// Forward pass of the warp's 16 rows.  Writes hidden activations to sm (if `keep`)
+// and returns the 16 output columns as two C fragments.
+template <typename T, int N_IN, int NH>
+__device__ __forceinline__ void forward_rows(T* sm, int r0, int g, int t, bool keep, float (&y)[2][4],
+                                             uint32_t (&hfr)[NH][4][4]) {
+  using S = Smem<N_IN, NH>;
+  uint32_t afr[4][4];
+  // input fragments
+#pragma unroll
+  for (int kk = 0; kk < N_IN / 16; ++kk) {
+    const T* base = sm + S::X + (r0 + g) * S::SX + kk * 16 + 2 * t;
+    afr[kk][0] = lds32(base);
+    afr[kk][1] = lds32(base + 8 * S::SX);
+    afr[kk][2] = lds32(base + 8);
+    afr[kk][3] = lds32(base + 8 * S::SX + 8);
+  }
+#pragma unroll
+  for (int h = 0; h < NH; ++h) {
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+      if (h == 0) {
+#pragma unroll
+        for (int kk = 0; kk < N_IN / 16; ++kk) {
+          uint32_t b0, b1;
+          bfrag<T>(sm + S::W0, S::SX, nt, kk, g, t, b0, b1);
+          mma16816<T>(acc[nt], afr[kk], b0, b1);
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          uint32_t b0, b1;
+          bfrag<T>(sm + S::WH + (h - 1) * kWidth * kSW, kSW, nt, kk, g, t, b0, b1);
+          mma16816<T>(acc[nt], afr[kk], b0, b1);
+        }
+      }
+    }
+    // ReLU, round to the operand type; the rounded values are both the next layer's
+    // input and what the backward pass sees.
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      afr[kk][0] = pack2<T>(fmaxf(acc[2 * kk][0], 0.f), fmaxf(acc[2 * kk][1], 0.f));
+      afr[kk][1] = pack2<T>(fmaxf(acc[2 * kk][2], 0.f), fmaxf(acc[2 * kk][3], 0.f));
+      afr[kk][2] = pack2<T>(fmaxf(acc[2 * kk + 1][0], 0.f), fmaxf(acc[2 * kk + 1][1], 0.f));
+      afr[kk][3] = pack2<T>(fmaxf(acc[2 * kk + 1][2], 0.f), fmaxf(acc[2 * kk + 1][3], 0.f));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) hfr[h][kk][j] = afr[kk][j];
+      if (keep) {
+        T* a = sm + S::A + h * kTile * kSW;
+        sts32(a + (r0 + g) * kSW + kk * 16 + 2 * t, afr[kk][0]);
+        sts32(a + (r0 + g + 8) * kSW + kk * 16 + 2 * t, afr[kk][1]);
+        sts32(a + (r0 + g) * kSW + kk * 16 + 8 + 2 * t, afr[kk][2]);
+        sts32(a + (r0 + g + 8) * kSW + kk * 16 + 8 + 2 * t, afr[kk][3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    y[nt][0] = y[nt][1] = y[nt][2] = y[nt][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      uint32_t b0, b1;
+      bfrag<T>(sm + S::WO, kSW, nt, kk, g, t, b0, b1);
+      mma16816<T>(y[nt], afr[kk], b0, b1);
+    }
+  }
+}
+
+template <typename T, int N_IN, int NH>
+__global__ void __launch_bounds__(kThreads)
+mlp_fwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out, float* __restrict__ out,
+               T* __restrict__ act) {
+  using S = Smem<N_IN, NH>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  load_weights<T, N_IN, NH>(W, n_out, sm, false);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = warp * 16;
+  const int64_t n_tiles = (P + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kTile;
+    __syncthreads();
+    load_inputs<T, N_IN, NH>(in, row0, P, sm);
+    __syncthreads();
+    float y[2][4];
+    uint32_t hfr[NH][4][4];
+    forward_rows<T, N_IN, NH>(sm, r0, g, t, false, y, hfr);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int64_t row = row0 + r0 + g + half * 8;
+      if (row >= P) continue;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int o = nt * 8 + 2 * t + j;
+          if (o < n_out) out[row * n_out + o] = y[nt][half * 2 + j];
+        }
+      if (act) {
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            T* a = act + ((int64_t)h * P + row) * kWidth + kk * 16 + 2 * t;
+            sts32(a, hfr[h][kk][half]);
+            sts32(a + 8, hfr[h][kk][2 + half]);
+          }
+      }
+    }
+  }
+}
+
+// MODE 0: dy = dout * loss_scale.  MODE 1: dy = loss_scale * 2 (y - target) / (P n_out),
+// and the squared residuals are summed into *sq_sum.
+template <typename T, int N_IN, int NH, int MODE>
+__global__ void __launch_bounds__(kThreads)
+mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
+               const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
+               float* __restrict__ din, float* __restrict__ ws, int64_t n_params, float* __restrict__ sq_sum) {
+  using S = Smem<N_IN, NH>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  load_weights<T, N_IN, NH>(W, n_out, sm, true);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = warp * 16;
+  const int64_t n_tiles = (P + kTile - 1) / kTile;
+  const float inv_count = 2.f / (float)((double)P * n_out);
+  float dw[S::TILES_PER_WARP][4];
+#pragma unroll
+  for (int i = 0; i < S::TILES_PER_WARP; ++i) dw[i][0] = dw[i][1] = dw[i][2] = dw[i][3] = 0.f;
+  float sq = 0.f;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kTile;
+    __syncthreads();
+    load_inputs<T, N_IN, NH>(in, row0, P, sm);
+    __syncthreads();
+    float y[2][4];
+    uint32_t hfr[NH][4][4];
+    forward_rows<T, N_IN, NH>(sm, r0, g, t, true, y, hfr);
+    // ---- output delta
+    uint32_t afr[4][4];
+    {
+      float dy[2][4];
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t row = row0 + r0 + g + (e >> 1) * 8;
+          const int o = nt * 8 + 2 * t + (e & 1);
+          float v = 0.f;
+          if (row < P && o < n_out) {
+            if (MODE == 0) {
+              v = dout[row * n_out + o] * loss_scale;
+            } else {
+              const float r = y[nt][e] - target[row * n_out + o];
+              sq = fmaf(r, r, sq);
+              v = r * inv_count * loss_scale;
+            }
+          }
+          dy[nt][e] = v;
+        }
+      afr[0][0] = pack2<T>(dy[0][0], dy[0][1]);
+      afr[0][1] = pack2<T>(dy[0][2], dy[0][3]);
+      afr[0][2] = pack2<T>(dy[1][0], dy[1][1]);
+      afr[0][3] = pack2<T>(dy[1][2], dy[1][3]);
+      T* d = sm + S::DY;
+      sts32(d + (r0 + g) * kSO + 2 * t, afr[0][0]);
+      sts32(d + (r0 + g + 8) * kSO + 2 * t, afr[0][1]);
+      sts32(d + (r0 + g) * kSO + 8 + 2 * t, afr[0][2]);
+      sts32(d + (r0 + g + 8) * kSO + 8 + 2 * t, afr[0][3]);
+    }
+    // ---- hidden deltas, top layer down: dH_h = (dH_{h+1} W_{h+1}) * [a_h > 0]
+#pragma unroll
+    for (int h = NH - 1; h >= 0; --h) {
+      float acc[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+        if (h == NH - 1) {
+          uint32_t b0, b1;
+          bfrag<T>(sm + S::WOT, kSO, nt, 0, g, t, b0, b1);
+          mma16816<T>(acc[nt], afr[0], b0, b1);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            uint32_t b0, b1;
+            bfrag<T>(sm + S::WHT + h * kWidth * kSW, kSW, nt, kk, g, t, b0, b1);
+            mma16816<T>(acc[nt], afr[kk], b0, b1);
+          }
+        }
+      }
+      // mask by the ReLU derivative and round to the operand type
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int nt = 2 * kk + (j >> 1);
+          const float2 a = unpack2<T>(hfr[h][kk][j]);
+          const float lo = a.x > 0.f ? acc[nt][(j & 1) * 2] : 0.f;
+          const float hi = a.y > 0.f ? acc[nt][(j & 1) * 2 + 1] : 0.f;
+          afr[kk][j] = pack2<T>(lo, hi);
+        }
+        T* d = sm + S::D + h * kTile * kSW;
+        sts32(d + (r0 + g) * kSW + kk * 16 + 2 * t, afr[kk][0]);
+        sts32(d + (r0 + g + 8) * kSW + kk * 16 + 2 * t, afr[kk][1]);
+        sts32(d + (r0 + g) * kSW + kk * 16 + 8 + 2 * t, afr[kk][2]);
+        sts32(d + (r0 + g + 8) * kSW + kk * 16 + 8 + 2 * t, afr[kk][3]);
+      }
+    }
+    // ---- input gradient dX = dH_0 W_0
+    if (din) {
+      const float inv_scale = 1.f / loss_scale;
+#pragma unroll
+      for (int nt = 0; nt < N_IN / 8; ++nt) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          uint32_t b0, b1;
+          bfrag<T>(sm + S::W0T, kSW, nt, kk, g, t, b0, b1);
+          mma16816<T>(acc, afr[kk], b0, b1);
+        }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int64_t row = row0 + r0 + g + half * 8;
+          if (row < P)
+            *reinterpret_cast<float2*>(din + row * N_IN + nt * 8 + 2 * t) =
+                make_float2(acc[half * 2] * inv_scale, acc[half * 2 + 1] * inv_scale);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- weight gradients of the tile: dW_l += Delta_l^T In_l, K = 128 rows
+#pragma unroll
+    for (int i = 0; i < S::TILES_PER_WARP; ++i) {
+      const int id = warp + i * kWarps;
+      if (id >= S::N_WTILES) break;
+      const T* Dl; int ldd; const T* In; int ldi; int mt, nt;
+      if (id < 8) {                                       // output layer: [16][64]
+        Dl = sm + S::DY; ldd = kSO; In = sm + S::A + (NH - 1) * kTile * kSW; ldi = kSW; mt = 0; nt = id;
+      } else if (id < 8 + (NH - 1) * 32) {                // hidden h: [64][64]
+        const int j = id - 8, h = 1 + j / 32, r = j % 32;
+        Dl = sm + S::D + h * kTile * kSW; ldd = kSW; In = sm + S::A + (h - 1) * kTile * kSW; ldi = kSW;
+        mt = r / 8; nt = r % 8;
+      } else {                                            // first layer: [64][N_IN]
+        const int j = id - 8 - (NH - 1) * 32;
+        Dl = sm + S::D; ldd = kSW; In = sm + S::X; ldi = S::SX; mt = j / (N_IN / 8); nt = j % (N_IN / 8);
+      }
+      const int q = lane >> 3, rr = lane & 7;
+#pragma unroll
+      for (int ks = 0; ks < kTile / 16; ++ks) {
+        uint32_t a[4], b0, b1;
+        ldsm_x4_trans(a, Dl + (ks * 16 + (q >> 1) * 8 + rr) * ldd + mt * 16 + (q & 1) * 8);
+        ldsm_x2_trans(b0, b1, In + (ks * 16 + (q & 1) * 8 + rr) * ldi + nt * 8);
+        mma16816<T>(dw[i], a, b0, b1);
+      }
+    }
+  }
+  // ---- per-CTA partials to the workspace
+  float* wsb = ws + (int64_t)blockIdx.x * n_params;
+  const int off_h = kWidth * N_IN;
+  const int off_o = off_h + (NH - 1) * kWidth * kWidth;
+#pragma unroll
+  for (int i = 0; i < S::TILES_PER_WARP; ++i) {
+    const int id = warp + i * kWarps;
+    if (id >= S::N_WTILES) break;
+    int base, fan_in, mt, nt, rows;
+    if (id < 8) { base = off_o; fan_in = kWidth; mt = 0; nt = id; rows = n_out; }
+    else if (id < 8 + (NH - 1) * 32) {
+      const int j = id - 8, h = 1 + j / 32, r = j % 32;
+      base = off_h + (h - 1) * kWidth * kWidth; fan_in = kWidth; mt = r / 8; nt = r % 8; rows = kWidth;
+    } else {
+      const int j = id - 8 - (NH - 1) * 32;
+      base = 0; fan_in = N_IN; mt = j / (N_IN / 8); nt = j % (N_IN / 8); rows = kWidth;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int m = mt * 16 + g + (e >> 1) * 8, n = nt * 8 + 2 * t + (e & 1);
+      if (m < rows) wsb[base + m * fan_in + n] = dw[i][e];
+    }
+  }
+  if (MODE == 1) {   // per-CTA sum of squared residuals after the weight partials
+    __shared__ float sq_part[kWarps];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) sq_part[warp] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s = 0.f;
+      for (int w = 0; w < kWarps; ++w) s += sq_part[w];
+      ws[(int64_t)gridDim.x * n_params + blockIdx.x] = s;
+    }
+  }
+}
+
+// dW[j] += (sum_b ws[b][j]) / loss_scale, summed over b in increasing order; the loss
+// partials (after the nb x n weight partials) are summed the same way into *sq_sum.
+__global__ void reduce_partials_kernel(const float* __restrict__ ws, int nb, int64_t n, float inv_scale,
+                                       float* __restrict__ dW, float* __restrict__ sq_sum) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < nb; ++b) s += ws[(int64_t)b * n + j];
+    dW[j] += s * inv_scale;
+  }
+  if (sq_sum && blockIdx.x == 0 && threadIdx.x == 0) {
+    float s = 0.f;
+    for (int b = 0; b < nb; ++b) s += ws[(int64_t)nb * n + b];
+    *sq_sum = s;
+  }
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms = n > 0 ? n : 148;
+  }
+  return g_num_sms;
+}
+
+template <typename T, int N_IN, int NH>
+sxe_status fwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,
+                      cudaStream_t s) {
+  using S = Smem<N_IN, NH>;
+  const size_t bytes = (size_t)S::FWD_END * sizeof(T);   // weights + input tile
+  auto k = mlp_fwd_kernel<T, N_IN, NH>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const int64_t n_tiles = (P + kTile - 1) / kTile;
+  const int grid = (int)std::min<int64_t>(n_tiles, 2 * num_sms());
+  k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, out, (T*)act);
+  return check_launch("mlp_fwd");
+}
+
+template <typename T, int N_IN, int NH>
+sxe_status bwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                      float loss_scale, int64_t P, float* din, float* dW, float* sq_sum, float* ws, int grid,
+                      cudaStream_t s) {
+  using S = Smem<N_IN, NH>;
+  const size_t bytes = (size_t)S::END * sizeof(T);
+  const int64_t n_params = sxe_mlp_n_params(d);
+  if (target) {
+    auto k = mlp_bwd_kernel<T, N_IN, NH, 1>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale, din, ws,
+                                    n_params, sq_sum);
+  } else {
+    auto k = mlp_bwd_kernel<T, N_IN, NH, 0>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale, din, ws,
+                                    n_params, sq_sum);
+  }
+  sxe_status st = check_launch("mlp_bwd");
+  if (st != SXE_OK) return st;
+  const int rb = (int)std::min<int64_t>((n_params + 255) / 256, 1024);
+  reduce_partials_kernel<<<rb, 256, 0, s>>>(ws, grid, n_params, 1.f / loss_scale, dW, target ? sq_sum : nullptr);
+  return check_launch("mlp_bwd_reduce");
+}
+
+template <typename T, int N_IN>
+sxe_status fwd_nh(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act, cudaStream_t s) {
+  switch (d->n_hidden) {
+    case 1: return fwd_launch<T, N_IN, 1>(d, W, in, P, out, act, s);
+    case 2: return fwd_launch<T, N_IN, 2>(d, W, in, P, out, act, s);
+    default: return fwd_launch<T, N_IN, 3>(d, W, in, P, out, act, s);
+  }
+}
+template <typename T>
+sxe_status fwd_in(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act, cudaStream_t s) {
+  switch (d->n_in) {
+    case 16: return fwd_nh<T, 16>(d, W, in, P, out, act, s);
+    case 32: return fwd_nh<T, 32>(d, W, in, P, out, act, s);
+    default: return fwd_nh<T, 64>(d, W, in, P, out, act, s);
+  }
+}
+template <typename T, int N_IN>
+sxe_status bwd_nh(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+  switch (d->n_hidden) {
+    case 1: return bwd_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
+    case 2: return bwd_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
+    default: return bwd_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
+  }
+}
+template <typename T>
+sxe_status bwd_in(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+  switch (d->n_in) {
+    case 16: return bwd_nh<T, 16>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
+    case 32: return bwd_nh<T, 32>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
+    default: return bwd_nh<T, 64>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
+  }
+}
+
+}  // namespace
+
+int mlp_grid_blocks(int64_t P) {
+  const int64_t n_tiles = (P + kTile - 1) / kTile;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, num_sms()));
+}
+
+sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,
+                          cudaStream_t s) {
+  return d->dtype == SXE_F16 ? fwd_in<__half>(d, W, in, P, out, act, s)
+                             : fwd_in<__nv_bfloat16>(d, W, in, P, out, act, s);
+}
+
+sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
+                          const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
+                          float* ws, int grid, cudaStream_t s) {
+  return d->dtype == SXE_F16 ? bwd_in<__half>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s)
+                             : bwd_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s);
+}
+
+}  // namespace sxe

@@ -1,0 +1,137 @@
+// Adam (Kingma & Ba, Algorithm 1) on a binary32 master copy, and the L2 loss of the
+// image-fitting task (Sec. 6.1 of arXiv 2311.15439).
+//
+// Two layouts:
+//   * dense SoA arrays (network weights): one thread per parameter;
+//   * table entries in an interleaved record {param[F], m[F], v[F], grad[F]} plus a
+//     bitmap of entries that received a gradient in this step.  One warp covers the 32
+//     entries of one bitmap word: the warp reads the word once, only its marked lanes
+//     touch their (consecutive, coalesced) records, and lane 0 clears the word.  An
+//     entry that was never marked has gradient zero and is skipped, which is exactly the
+//     zero-gradient skip rule applied to every entry.
+#include <cmath>
+
+#include "sxe_internal.cuh"
+
+namespace sxe {
+namespace {
+
+struct AdamConst {
+  float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+  int skip;
+};
+
+AdamConst make_const(const sxe_adam_desc* a, int64_t t) {
+  AdamConst k;
+  k.lr = a->lr; k.b1 = a->beta1; k.b2 = a->beta2; k.eps = a->eps;
+  k.c1 = (float)(1.0 / (1.0 - std::pow((double)a->beta1, (double)t)));
+  k.c2 = (float)(1.0 / (1.0 - std::pow((double)a->beta2, (double)t)));
+  k.skip = a->skip_zero_grad;
+  return k;
+}
+
+__device__ __forceinline__ void adam_one(const AdamConst& k, float g, float& p, float& m, float& v) {
+  m = fmaf(k.b1, m, (1.f - k.b1) * g);
+  v = fmaf(k.b2, v, (1.f - k.b2) * g * g);
+  const float mh = m * k.c1;
+  const float vh = v * k.c2;
+  p = p - k.lr * mh / (sqrtf(vh) + k.eps);
+}
+
+__global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p, float* __restrict__ m,
+                                  float* __restrict__ v, float* __restrict__ g, void* __restrict__ lowp, int ldt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    float pi = p[i];
+    if (!(k.skip && gi == 0.f)) {
+      float mi = m[i], vi = v[i];
+      adam_one(k, gi, pi, mi, vi);
+      p[i] = pi; m[i] = mi; v[i] = vi;
+      g[i] = 0.f;
+    }
+    if (lowp) store_as(lowp, i, ldt, pi);
+  }
+}
+
+template <int F>
+__global__ void adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state,
+                                    uint32_t* __restrict__ touched, void* __restrict__ lowp, int ldt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_words = (n_entries + 31) >> 5;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = warp0; w < n_words; w += n_warps) {
+    const uint32_t bits = touched[w];            // uniform across the warp
+    if (bits == 0u) continue;
+    const int64_t e = (w << 5) + lane;
+    if (((bits >> lane) & 1u) && e < n_entries) {
+      float* rec = state + e * (4 * F);
+      float p[F], m[F], v[F], g[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) { p[f] = rec[f]; m[f] = rec[F + f]; v[f] = rec[2 * F + f]; g[f] = rec[3 * F + f]; }
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        if (g[f] != 0.f) adam_one(k, g[f], p[f], m[f], v[f]);
+        rec[f] = p[f]; rec[F + f] = m[f]; rec[2 * F + f] = v[f]; rec[3 * F + f] = 0.f;
+        store_as(lowp, e * F + f, ldt, p[f]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) touched[w] = 0u;
+  }
+}
+
+__global__ void loss_l2_kernel(const float* __restrict__ y, const float* __restrict__ tgt, int64_t n, float scale,
+                               float* __restrict__ dy, float* __restrict__ sq_sum) {
+  float sq = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float r = y[i] - tgt[i];
+    dy[i] = r * scale;
+    sq = fmaf(r, r, sq);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += part[i];
+    if (s != 0.f) atomicAdd(sq_sum, s);
+  }
+}
+
+unsigned blocks_for(int64_t n, int threads, unsigned cap) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+sxe_status launch_adam_dense(const sxe_adam_desc* a, int64_t t, int64_t n, float* p, float* m, float* v, float* g,
+                             void* lowp, int32_t ldt, cudaStream_t s) {
+  adam_dense_kernel<<<blocks_for(n, 256, 1u << 16), 256, 0, s>>>(make_const(a, t), n, p, m, v, g, lowp, ldt);
+  return check_launch("adam_dense");
+}
+
+sxe_status launch_adam_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries, int32_t F, float* state,
+                               uint32_t* touched, void* lowp, int32_t ldt, cudaStream_t s) {
+  const AdamConst k = make_const(a, t);
+  const unsigned nb = blocks_for(((n_entries + 31) >> 5) * 32, 256, 1u << 20);
+  switch (F) {
+    case 1: adam_touched_kernel<1><<<nb, 256, 0, s>>>(k, n_entries, state, touched, lowp, ldt); break;
+    case 2: adam_touched_kernel<2><<<nb, 256, 0, s>>>(k, n_entries, state, touched, lowp, ldt); break;
+    case 4: adam_touched_kernel<4><<<nb, 256, 0, s>>>(k, n_entries, state, touched, lowp, ldt); break;
+    default: adam_touched_kernel<8><<<nb, 256, 0, s>>>(k, n_entries, state, touched, lowp, ldt); break;
+  }
+  return check_launch("adam_touched");
+}
+
+sxe_status launch_loss_l2(const float* y, const float* target, int64_t P, int32_t n_out, float* dy, float* sq_sum,
+                          cudaStream_t s) {
+  const int64_t n = P * n_out;
+  loss_l2_kernel<<<blocks_for(n, 256, 4096), 256, 0, s>>>(y, target, n, (float)(2.0 / (double)n), dy, sq_sum);
+  return check_launch("loss_l2");
+}
+
+}  // namespace sxe

@@ -1,0 +1,226 @@
+// Internal declarations shared by the CUDA translation units of libsimplexenc.
+//
+// The lattice arithmetic here is the GPU side of the simplex-grid hash encoding
+// (Wen & Yang, arXiv 2311.15439): scale + skew (Eq. 2, Sec. 5.1), simplicial
+// subdivision by ranking the fractional parts (Sec. 4.2, Remark 2), barycentric
+// weights (Sec. 4.3) and the vertex hash (Sec. 5 a); plus the 2^d grid corners of
+// the comparator (Algorithm 1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/simplexenc.h"
+
+namespace sxe {
+
+// ---------------------------------------------------------------------------
+// host-side handle
+// ---------------------------------------------------------------------------
+struct EncParams {
+  int32_t n_levels;
+  int32_t log2_T;
+  int32_t out_dtype;
+  float skew_F;                    // F_n of Eq. 2 rounded to binary32 (simplex only)
+  float scale[SXE_MAX_LEVELS];     // per-level input multiplier (binary32)
+};
+
+}  // namespace sxe
+
+struct sxe_encoder {
+  sxe_encoding_desc desc;
+  int32_t level_res[SXE_MAX_LEVELS];
+  sxe::EncParams prm;
+};
+
+namespace sxe {
+
+// error reporting (defined in api.cu)
+sxe_status set_error(sxe_status st, const char* fmt, ...);
+sxe_status check_launch(const char* what);
+
+// launchers (defined in encode.cu / mlp.cu / optim.cu); arguments already validated
+sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
+                             void* out, cudaStream_t s);
+sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
+                             float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s);
+sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,
+                                  float* weights, cudaStream_t s);
+
+int mlp_grid_blocks(int64_t P);
+sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out,
+                          void* act, cudaStream_t s);
+sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
+                          const float* target, float loss_scale, int64_t P, float* din, float* dW,
+                          float* sq_sum, float* ws, int grid, cudaStream_t s);
+sxe_status launch_loss_l2(const float* y, const float* target, int64_t P, int32_t n_out, float* dy,
+                          float* sq_sum, cudaStream_t s);
+sxe_status launch_adam_dense(const sxe_adam_desc* a, int64_t t, int64_t n, float* p, float* m, float* v,
+                             float* g, void* lowp, int32_t lowp_dtype, cudaStream_t s);
+sxe_status launch_adam_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries, int32_t F,
+                               float* state, uint32_t* touched, void* lowp, int32_t lowp_dtype,
+                               cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// Hash multipliers per axis: 1, 2654435761, 805459861 (the Instant-NGP spatial hash
+// the paper's backbone uses) and, for axes 4 and 5, the smallest primes not below
+// frac(sqrt(5)) * 2^32 and frac(sqrt(7)) * 2^32.
+__host__ __device__ constexpr uint32_t hash_prime(int axis) {
+  return axis == 0 ? 1u : axis == 1 ? 2654435761u : axis == 2 ? 805459861u
+       : axis == 3 ? 1013904263u : 2773480771u;
+}
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Store `n` binary32 values as dtype `dt` at element offset `off` of `base`.
+__device__ __forceinline__ void store_as(void* base, int64_t off, int32_t dt, float v) {
+  if (dt == SXE_F32) reinterpret_cast<float*>(base)[off] = v;
+  else if (dt == SXE_F16) reinterpret_cast<__half*>(base)[off] = __float2half_rn(v);
+  else reinterpret_cast<__nv_bfloat16*>(base)[off] = __float2bfloat16_rn(v);
+}
+
+// Raw aligned vector of B bytes.
+template <int B> struct RawVec;
+template <> struct RawVec<2> { using type = unsigned short; };
+template <> struct RawVec<4> { using type = unsigned int; };
+template <> struct RawVec<8> { using type = uint2; };
+template <> struct RawVec<16> { using type = uint4; };
+
+// Gather the F features of one table entry through the read-only path.
+template <typename T, int F>
+__device__ __forceinline__ void load_entry(const T* __restrict__ p, float (&o)[F]) {
+  constexpr int B = F * (int)sizeof(T);
+  if constexpr (B <= 16) {
+    using V = typename RawVec<B>::type;
+    union { V v; T t[F]; } u;
+    u.v = __ldg(reinterpret_cast<const V*>(p));
+#pragma unroll
+    for (int f = 0; f < F; ++f) o[f] = to_f32(u.t[f]);
+  } else {
+    union { uint4 v[B / 16]; T t[F]; } u;
+#pragma unroll
+    for (int j = 0; j < B / 16; ++j) u.v[j] = __ldg(reinterpret_cast<const uint4*>(p) + j);
+#pragma unroll
+    for (int f = 0; f < F; ++f) o[f] = to_f32(u.t[f]);
+  }
+}
+
+// Vector atomic add of F binary32 values (8/16-byte vector atomics on sm_90+).
+template <int F>
+__device__ __forceinline__ void atomic_add_entry(float* p, const float (&v)[F]) {
+  if constexpr (F == 1) {
+    atomicAdd(p, v[0]);
+  } else if constexpr (F == 2) {
+    atomicAdd(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < F / 4; ++j)
+      atomicAdd(reinterpret_cast<float4*>(p) + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Simplex lattice of one point at one level.
+//   Sec. 5.1 + Eq. 2: p_i = x_i * s, sigma = sum_i p_i (left to right), t = F * sigma,
+//   q_i = p_i + t; each operation rounded once (no contraction).
+//   Sec. 4.2: c = floor(q), f = q - c (exact).  rank_i = number of axes j whose f_j is
+//   larger, or equal with j < i: the stable decreasing order of the paper's sort.
+//   Remark 2: vertex k = c + sum of e_i over axes with rank_i < k.
+//   Sec. 4.3: w_0 = 1 - s_0, w_k = s_{k-1} - s_k, w_d = s_{d-1} on the sorted s.
+//   Sec. 5 (a): slot = XOR_i (uint32(v_i) * prime_i) mod T.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
+                                                uint32_t (&slot)[D + 1], float (&w)[D + 1]) {
+  float p[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) p[i] = __fmul_rn(x[i], s);
+  float sigma = p[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) sigma = __fadd_rn(sigma, p[i]);
+  const float t = __fmul_rn(skewF, sigma);
+  float f[D];
+  uint32_t h0[D], h1[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const float q = __fadd_rn(p[i], t);
+    const float fl = floorf(q);
+    f[i] = __fsub_rn(q, fl);
+    const uint32_t c = (uint32_t)__float2int_rz(fl);
+    h0[i] = c * hash_prime(i);
+    h1[i] = (c + 1u) * hash_prime(i);
+  }
+  int rank[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    int r = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+      if (j != i) r += (f[j] > f[i]) || (j < i && f[j] == f[i]);
+    rank[i] = r;
+  }
+  float srt[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    float v = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) v = (rank[i] == k) ? f[i] : v;
+    srt[k] = v;
+  }
+  w[0] = __fsub_rn(1.f, srt[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) w[k] = __fsub_rn(srt[k - 1], srt[k]);
+  w[D] = srt[D - 1];
+#pragma unroll
+  for (int k = 0; k <= D; ++k) {
+    uint32_t h = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) h ^= (rank[i] < k) ? h1[i] : h0[i];
+    slot[k] = h & mask;
+  }
+}
+
+// 2^D grid corners of one point at one level (Algorithm 1's multilinear weights):
+// p_i = x_i * N (binary32), c = floor(p), f = p - c; corner b (axis 0 = most
+// significant bit) has weight prod_i (b_i ? f_i : 1 - f_i), multiplied in axis order.
+template <int D>
+__device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint32_t mask,
+                                             uint32_t (&slot)[1 << D], float (&w)[1 << D]) {
+  float f[D];
+  uint32_t h0[D], h1[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const float p = __fmul_rn(x[i], N);
+    const float fl = floorf(p);
+    f[i] = __fsub_rn(p, fl);
+    const uint32_t c = (uint32_t)__float2int_rz(fl);
+    h0[i] = c * hash_prime(i);
+    h1[i] = (c + 1u) * hash_prime(i);
+  }
+#pragma unroll
+  for (int b = 0; b < (1 << D); ++b) {
+    float wt = 1.f;
+    uint32_t h = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const bool bi = (b >> (D - 1 - i)) & 1;
+      wt = __fmul_rn(wt, bi ? f[i] : __fsub_rn(1.f, f[i]));
+      h ^= bi ? h1[i] : h0[i];
+    }
+    w[b] = wt;
+    slot[b] = h & mask;
+  }
+}
+
+}  // namespace sxe

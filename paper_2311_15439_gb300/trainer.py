@@ -1,0 +1,90 @@
+"""Training step of the image-fitting and SDF-style workloads (Sec. 6.1 of arXiv 2311.15439).
+
+One ``step(x, target)`` runs, on the caller's stream and entirely in libsimplexenc
+kernels:
+
+1. ``sxe_encode_fwd``   -- multiresolution encoding of the batch from the low-precision
+                           tables (Sec. 5 a-d);
+2. ``sxe_mlp_train_l2`` -- network forward, L2 loss, network backward, dL/d(encoding)
+                           (Sec. 5 d-e);
+3. ``sxe_encode_bwd``   -- scatter-add of dL/d(encoding) into the gradient field of the
+                           interleaved table state, marking touched entries (Sec. 5 e);
+4. ``sxe_step_touched`` -- Adam on the marked table entries (zero-gradient skip rule),
+                           refreshing the low-precision tables;
+5. ``sxe_step``         -- Adam on the network weights, refreshing their low-precision copy.
+
+Table state layout in HBM: one binary32 record {param[F], m[F], v[F], grad[F]} per entry
+(32 bytes for F = 2: one DRAM sector), entries ordered [level][slot]; a separate dense
+[L][T][F] low-precision copy is what the forward pass gathers from; a bitmap of L*T bits
+marks the entries that received a gradient in the current step.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import synth
+from .api import Adam, Encoder, Mlp, torch_dtype
+
+
+def default_loss_scale(P: int, n_out: int) -> float:
+    """Power of two near P*n_out/2 so that the scaled L2 gradient 2 r / (P n_out) is O(r)."""
+    return float(2.0 ** max(0, math.floor(math.log2(max(1.0, P * n_out / 2.0)))))
+
+
+class Trainer:
+    def __init__(self, encoder: Encoder, mlp: Mlp, batch: int, *, seed: int = 0, device="cuda",
+                 table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15):
+        if mlp.n_in != encoder.n_out:
+            raise ValueError("network input %d != encoding width %d" % (mlp.n_in, encoder.n_out))
+        self.enc, self.mlp, self.P = encoder, mlp, batch
+        self.device = torch.device(device)
+        F = encoder.n_features
+        n_entries = encoder.n_levels * encoder.T
+        # seeded host values U(-table_init, table_init), so any checker can regenerate them
+        vals = synth.uniform_tables(encoder.n_levels, encoder.T, F, seed, dtype="f32", scale=table_init)[0]
+        init = torch.from_numpy(vals.reshape(n_entries, F)).to(self.device)
+        self.state = torch.zeros((n_entries, 4 * F), dtype=torch.float32, device=self.device)
+        self.state[:, :F] = init
+        self.tables = init.to(torch_dtype(encoder.table_dtype)).reshape(encoder.table_shape()).contiguous()
+        self.touched = torch.zeros(((n_entries + 31) // 32,), dtype=torch.int32, device=self.device)
+        W0 = torch.from_numpy(mlp.init_weights(seed + 1)).to(self.device)
+        self.W = W0.clone()
+        self.W_lowp = W0.to(torch_dtype(mlp.dtype))
+        self.mW = torch.zeros_like(W0)
+        self.vW = torch.zeros_like(W0)
+        self.dW = torch.zeros_like(W0)
+        self.enc_out = torch.empty((batch, encoder.n_out), dtype=torch_dtype(encoder.out_dtype), device=self.device)
+        self.d_enc = torch.empty((batch, encoder.n_out), dtype=torch.float32, device=self.device)
+        self.sq_sum = torch.zeros((1,), dtype=torch.float32, device=self.device)
+        self.ws = mlp.workspace(batch, self.device)
+        self.loss_scale = default_loss_scale(batch, mlp.n_out)
+        self.adam_tables = Adam(lr, betas[0], betas[1], eps, skip_zero_grad=True)
+        self.adam_mlp = Adam(lr, betas[0], betas[1], eps, skip_zero_grad=False)
+        self.t = 0
+
+    @property
+    def n_launches_per_step(self) -> int:
+        return 6   # encode_fwd, mlp train, its partial reduction, encode_bwd, table Adam, network Adam
+
+    def step(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
+        """One optimisation step on batch (x [P, d] float32, target [P, n_out] float32); asynchronous."""
+        F = self.enc.n_features
+        self.t += 1
+        self.enc.encode_fwd(x, self.tables, self.enc_out, stream=stream)
+        self.mlp.mlp_train_l2(self.W_lowp, self.enc_out, target, self.dW, self.sq_sum, din=self.d_enc,
+                              loss_scale=self.loss_scale, workspace=self.ws, stream=stream)
+        self.enc.encode_bwd(x, self.d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F, touched=self.touched,
+                            stream=stream)
+        self.adam_tables.step_touched(self.t, self.state, self.touched, self.tables, F, stream=stream)
+        self.adam_mlp.step(self.t, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=stream)
+
+    def loss(self) -> float:
+        """Mean squared error of the last step (synchronises)."""
+        return float(self.sq_sum.item()) / (self.P * self.mlp.n_out)
+
+    def table_params(self) -> torch.Tensor:
+        """binary32 master table parameters as [L, T, F]."""
+        F = self.enc.n_features
+        return self.state[:, :F].reshape(self.enc.table_shape())

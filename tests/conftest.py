@@ -21,3 +21,31 @@ def read_golden(name):
             if line and not line.startswith("#"):
                 rows.append(line.split())
     return rows
+
+
+import pytest  # noqa: E402
+
+
+@pytest.fixture(scope="session")
+def cuda_lib():
+    """Build (if needed) and load libsimplexenc on the GPU; fails loudly without CUDA."""
+    import torch
+    from paper_2311_15439_gb300 import build, _lib
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    _lib.lib()
+    return _lib
+
+
+def rel_err(got, want, den, floor=1e-30):
+    """max |got - want| / (den + floor): error measured against the sum of absolute terms."""
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    return float(np.max(np.abs(got - want) / (np.asarray(den, dtype=np.float64) + floor))) if got.size else 0.0
+
+
+#: tolerance of an encoding value against sum_k |w_k H_k|, by output dtype: binary32
+#: accumulation of at most 32 terms (1e-5, the stated FP32 bar), or one final rounding
+#: to fp16 (unit roundoff 2^-11 -> 2e-3) / bf16 (2^-8 -> 5e-3).
+ENC_TOL = {"f32": 1e-5, "f16": 2e-3, "bf16": 5e-3}

@@ -1,0 +1,123 @@
+"""C ABI: the library builds, loads without a GPU, exports every declared symbol, and its
+host-side logic (argument validation, level constants) is right.  No device calls."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import lattice
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2311_15439_gb300 import build, _lib
+    build.build()
+    return _lib
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "simplexenc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sxe_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_lists_every_binding(L):
+    assert sorted(L.EXPORTS) == _declared_functions()
+
+
+def test_library_exports_every_declared_symbol(L):
+    lib = L.lib()
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert b"sm_103a" in lib.sxe_version()
+
+
+def _desc(L, **kw):
+    base = dict(d=2, n_levels=8, n_features=2, log2_T=14, base_res=16.0, growth=1.5, kind=L.SXE_SIMPLEX,
+                res_mode=L.SXE_RES_RAW, table_dtype=L.SXE_F32, out_dtype=L.SXE_F32)
+    base.update(kw)
+    return L.EncodingDesc(**base)
+
+
+def _create(L, **kw):
+    h = ctypes.c_void_p()
+    st = L.lib().sxe_encoder_create(ctypes.byref(_desc(L, **kw)), ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(d=7), -2), (dict(d=0), -1), (dict(n_levels=0), -1), (dict(n_levels=33), -1),
+    (dict(n_features=3), -1), (dict(log2_T=3), -1), (dict(log2_T=27), -1), (dict(base_res=0.5), -1),
+    (dict(growth=0.9), -1), (dict(kind=5), -1), (dict(res_mode=2), -1), (dict(table_dtype=9), -1),
+    (dict(kind=1, res_mode=1), -1), (dict(base_res=float("nan")), -1),
+])
+def test_encoder_create_rejects_bad_descriptions(L, bad, status):
+    st, h = _create(L, **bad)
+    assert st == status
+    assert L.lib().sxe_last_error()
+
+
+def test_entry_points_validate_before_launch(L):
+    lib = L.lib()
+    st, h = _create(L)
+    assert st == 0
+    try:
+        # NULL encoder / negative sizes / NULL buffers are refused on the host
+        assert lib.sxe_encode_fwd(None, 16, 10, 16, 16, None) == -1
+        assert lib.sxe_encode_fwd(h, 16, -1, 16, 16, None) == -1
+        assert lib.sxe_encode_fwd(h, None, 10, 16, 16, None) == -1
+        assert lib.sxe_encode_fwd(h, 16, 10, None, 16, None) == -1
+        assert lib.sxe_encode_fwd(h, 12, 10, 16, 16, None) == -1            # x misaligned for d = 2
+        assert lib.sxe_encode_bwd(h, 16, 10, 16, 16, 3, None, None) == -1    # stride not a multiple of F
+        assert lib.sxe_encode_bwd(h, 16, 10, 16, 20, 2, None, None) == -1    # grad entries misaligned
+        # zero points: nothing to do, no pointer needed
+        assert lib.sxe_encode_fwd(h, None, 0, None, None, None) == 0
+        assert lib.sxe_encode_bwd(h, None, 0, None, None, 2, None, None) == 0
+    finally:
+        lib.sxe_encoder_destroy(h)
+    m = L.MlpDesc(32, 64, 2, 3, L.SXE_F16)
+    assert lib.sxe_mlp_n_params(ctypes.byref(m)) == 32 * 64 + 64 * 64 + 3 * 64
+    assert lib.sxe_mlp_fwd(ctypes.byref(L.MlpDesc(32, 128, 2, 3, L.SXE_F16)), 16, 16, 8, 16, None, None) == -2
+    assert lib.sxe_mlp_fwd(ctypes.byref(L.MlpDesc(32, 64, 2, 17, L.SXE_F16)), 16, 16, 8, 16, None, None) == -1
+    assert lib.sxe_mlp_fwd(ctypes.byref(L.MlpDesc(32, 64, 2, 3, L.SXE_F32)), 16, 16, 8, 16, None, None) == -1
+    assert lib.sxe_mlp_bwd(ctypes.byref(m), 16, 16, 16, ctypes.c_float(1.0), 8, None, 16, 16, 4, None) == -4  # workspace too small
+    a = L.AdamDesc(1e-2, 0.9, 0.99, 1e-15, 0)
+    assert lib.sxe_step(ctypes.byref(a), 0, 4, 16, 16, 16, 16, None, 0, None) == -1                         # t = 0
+    assert lib.sxe_step(ctypes.byref(L.AdamDesc(1e-2, 1.0, 0.99, 1e-15, 0)), 1, 4, 16, 16, 16, 16, None, 0, None) == -1
+
+
+@pytest.mark.parametrize("kind", ["simplex", "grid"])
+@pytest.mark.parametrize("cfg", [(2, 8, 16.0, 1.5), (2, 16, 16.0, 2.0), (3, 16, 16.0, 1.38), (4, 16, 16.0, 1.38),
+                                 (5, 12, 8.0, 1.6)])
+def test_level_constants_match_oracle(L, kind, cfg):
+    """The library's binary32 level multipliers and resolutions equal the oracle's bit for bit."""
+    d, nl, base, growth = cfg
+    for res_mode in ([0, 1] if kind == "simplex" else [0]):
+        st, h = _create(L, d=d, n_levels=nl, base_res=base, growth=growth,
+                        kind=L.SXE_SIMPLEX if kind == "simplex" else L.SXE_GRID, res_mode=res_mode)
+        assert st == 0
+        s = np.zeros(nl, np.float32)
+        r = np.zeros(nl, np.int32)
+        assert L.lib().sxe_encoder_level_params(h, s.ctypes.data, r.ctypes.data) == 0
+        L.lib().sxe_encoder_destroy(h)
+        assert r.tolist() == lattice.level_resolutions(nl, base, growth)
+        if kind == "simplex":
+            want = lattice.simplex_level_scales_fp32(d, nl, base, growth, res_mode)
+        else:
+            want = lattice.grid_level_scales_fp32(nl, base, growth)
+        assert np.array_equal(s.view(np.uint32), want.view(np.uint32))
+
+
+def test_product_path_refuses_to_run_without_library(tmp_path):
+    """The binding raises (no CPU fallback) when the shared library is missing."""
+    from paper_2311_15439_gb300 import _lib
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            _lib.lib(str(tmp_path / "missing.so"))
+    finally:
+        _lib._lib = saved

@@ -1,0 +1,185 @@
+"""GPU parity of the encoding kernels against the FP64 oracle (through the C ABI).
+
+Slots are compared bit for bit; weights, encodings and table gradients within the
+tolerances of ``conftest.ENC_TOL`` measured against the sum of absolute terms."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import ENC_TOL, rel_err
+from oracle import encoding as O
+from oracle import lattice
+from paper_2311_15439_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+# (d, L, F, log2_T, base, growth, table dtype, out dtype, P)
+CASES = [
+    (2, 8, 2, 14, 16.0, 1.5, "f32", "f32", 65536),       # plain FP32 workload, full size
+    (2, 16, 2, 22, 16.0, 2.0, "f16", "f16", 1 << 14),     # image-style tables
+    (3, 16, 2, 19, 16.0, 1.38, "bf16", "bf16", 1 << 13),  # SDF-style tables
+    (3, 16, 2, 19, 16.0, 1.38, "f16", "f32", 5000),
+    (4, 16, 2, 19, 16.0, 1.38, "f16", "f16", 3000),
+    (5, 16, 2, 19, 16.0, 1.38, "f16", "f16", 3000),
+    (2, 4, 1, 12, 8.0, 2.0, "f32", "f32", 4999),
+    (3, 5, 4, 12, 8.0, 2.0, "f32", "bf16", 3001),
+    (4, 3, 8, 10, 4.0, 1.5, "f32", "f32", 777),
+]
+
+
+def _ids(c):
+    return "d%d_L%d_F%d_T%d_%s_%s_P%d" % (c[0], c[1], c[2], c[3], c[6], c[7], c[8])
+
+
+def _points(d, P, seed):
+    return np.concatenate([synth.uniform_points(P, d, seed), synth.edge_points(d, seed + 1, per_kind=8)])
+
+
+def _setup(cuda_lib, case, kind, seed=0):
+    from paper_2311_15439_gb300.api import Encoder
+    d, L, F, log2_T, base, growth, tdt, odt, P = case
+    enc = Encoder(d, L, F, log2_T, base, growth, kind=kind, table_dtype=tdt, out_dtype=odt)
+    vals, store = synth.uniform_tables(L, 1 << log2_T, F, seed + 2, dtype=tdt, scale=1e-4)
+    t = torch.from_numpy(store.astype(np.int16) if tdt == "bf16" else store).cuda()
+    if tdt == "bf16":
+        t = t.view(torch.bfloat16)
+    x = _points(d, P, seed + 3)
+    return enc, vals, t, x
+
+
+@pytest.mark.parametrize("kind", ["simplex", "grid"])
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_vertices_bit_exact(cuda_lib, case, kind):
+    """Lattice slots equal the oracle's bit for bit (given the same binary32 skewed point);
+    weights agree to binary32 rounding."""
+    enc, _, _, x = _setup(cuda_lib, case, kind)
+    d, L, F, log2_T, base, growth = case[:6]
+    slots, w = enc.encode_vertices(torch.from_numpy(x).cuda())
+    slots, w = slots.cpu().numpy(), w.cpu().numpy()
+    if kind == "simplex":
+        scales = lattice.simplex_level_scales_fp32(d, L, base, growth)
+        for l in range(L):
+            s_ref, w_ref, _ = O.simplex_level_vertices(x, scales[l], log2_T)
+            assert np.array_equal(slots[:, l, :].astype(np.int64), s_ref), "level %d" % l
+            assert np.max(np.abs(w[:, l, :] - w_ref)) <= 2.0 ** -23
+    else:
+        res = lattice.grid_level_scales_fp32(L, base, growth)
+        for l in range(L):
+            s_ref, w_ref = O.grid_level_vertices(x, res[l], log2_T)
+            assert np.array_equal(slots[:, l, :].astype(np.int64), s_ref), "level %d" % l
+            assert np.max(np.abs(w[:, l, :] - w_ref)) <= (2 * d + 1) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("kind", ["simplex", "grid"])
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_forward_matches_oracle(cuda_lib, case, kind):
+    enc, vals, t, x = _setup(cuda_lib, case, kind)
+    base, growth = case[4], case[5]
+    out = enc.encode_fwd(torch.from_numpy(x).cuda(), t).float().cpu().numpy()
+    if kind == "simplex":
+        ref, den = O.simplex_encode(x, vals, base_res=base, growth=growth, with_denominator=True)
+    else:
+        ref = O.grid_encode(x, vals, base_res=base, growth=growth)
+        den = O.grid_encode(x, np.abs(vals), base_res=base, growth=growth)   # weights are >= 0
+    assert rel_err(out, ref, den) <= ENC_TOL[case[7]]
+
+
+@pytest.mark.parametrize("kind", ["simplex", "grid"])
+@pytest.mark.parametrize("case", [c for c in CASES if c[3] <= 19], ids=_ids)
+def test_backward_matches_oracle(cuda_lib, case, kind):
+    """Table gradients (binary32 atomics) agree with the FP64 scatter-add within 1e-5 of
+    sum |w_k dout|; untouched entries stay exactly zero."""
+    enc, _, _, x = _setup(cuda_lib, case, kind)
+    d, L, F, log2_T, base, growth = case[:6]
+    dout = synth.normal_grads(len(x), L * F, 7)
+    grad = torch.zeros((L, 1 << log2_T, F), dtype=torch.float32, device="cuda")
+    enc.encode_bwd(torch.from_numpy(x).cuda(), torch.from_numpy(dout).cuda(), grad)
+    g = grad.cpu().numpy()
+    kw = dict(n_levels=L, log2_T=log2_T, n_features=F, base_res=base, growth=growth)
+    if kind == "simplex":
+        ref, den = O.simplex_encode_bwd(x, dout, with_denominator=True, **kw)
+    else:
+        ref = O.grid_encode_bwd(x, dout, **kw)
+        den = O.grid_encode_bwd(x, np.abs(dout), **kw)
+    for l in range(L):
+        assert rel_err(g[l], ref[l], den[l]) <= 1e-5, "level %d" % l
+        assert np.all(g[l][den[l] == 0] == 0)
+
+
+def test_full_size_image_workload(cuda_lib):
+    """2^18 points, L = 16, T = 2^22 fp16 tables, the launch the benchmark times: every output
+    against the oracle, and the gradients of three levels (coarse, middle, finest)."""
+    case = (2, 16, 2, 22, 16.0, 2.0, "f16", "f16", 1 << 18)
+    enc, vals, t, x = _setup(cuda_lib, case, "simplex", seed=11)
+    x = x[: 1 << 18]
+    xd = torch.from_numpy(x).cuda()
+    out = enc.encode_fwd(xd, t).float().cpu().numpy()
+    ref, den = O.simplex_encode(x, vals, base_res=16.0, growth=2.0, with_denominator=True)
+    assert rel_err(out, ref, den) <= ENC_TOL["f16"]
+    dout = synth.normal_grads(len(x), 32, 12)
+    grad = torch.zeros((16, 1 << 22, 2), dtype=torch.float32, device="cuda")
+    enc.encode_bwd(xd, torch.from_numpy(dout).cuda(), grad)
+    levels = [0, 7, 15]
+    ref, den = O.simplex_encode_bwd(x, dout, n_levels=16, log2_T=22, n_features=2, base_res=16.0, growth=2.0,
+                                    levels=levels, with_denominator=True)
+    for l in levels:
+        assert rel_err(grad[l].cpu().numpy(), ref[l], den[l]) <= 1e-5
+
+
+def test_strided_gradient_and_touched_bitmap(cuda_lib):
+    """Gradients written into interleaved records (stride 4F, offset 3F) equal the dense ones,
+    nothing else in the records changes, and exactly the entries with a term are marked."""
+    case = (3, 6, 2, 12, 8.0, 1.7, "f16", "f16", 3000)
+    enc, _, _, x = _setup(cuda_lib, case, "simplex")
+    L, F, T = 6, 2, 1 << 12
+    xd = torch.from_numpy(x).cuda()
+    dout = torch.from_numpy(synth.normal_grads(len(x), L * F, 3)).cuda()
+    dense = torch.zeros((L, T, F), dtype=torch.float32, device="cuda")
+    enc.encode_bwd(xd, dout, dense)
+    state = torch.randn((L * T, 4 * F), device="cuda")
+    state[:, 3 * F:] = 0
+    before = state.clone()
+    touched = torch.zeros(((L * T + 31) // 32,), dtype=torch.int32, device="cuda")
+    enc.encode_bwd(xd, dout, state, grad_stride=4 * F, grad_offset=3 * F, touched=touched)
+    torch.cuda.synchronize()
+    assert torch.equal(state[:, :3 * F], before[:, :3 * F])
+    g_dense = dense.reshape(L * T, F).cpu().numpy()
+    g_rec = state[:, 3 * F:].cpu().numpy()
+    assert np.max(np.abs(g_dense - g_rec)) <= 1e-5 * np.max(np.abs(g_dense))
+    bits = touched.cpu().numpy().view(np.uint32)
+    marked = ((bits[:, None] >> np.arange(32, dtype=np.uint32)[None, :]) & 1).ravel()[: L * T].astype(bool)
+    scales = lattice.simplex_level_scales_fp32(3, L, 8.0, 1.7)
+    want = np.zeros(L * T, dtype=bool)
+    for l in range(L):
+        s, _, _ = O.simplex_level_vertices(x, scales[l], 12)
+        want[l * T + s.ravel()] = True
+    assert np.array_equal(marked, want)
+
+
+def test_zero_points_and_errors(cuda_lib):
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300._lib import SxeError
+    enc = Encoder(2, 4, 2, 10, 8.0, 1.5, table_dtype="f32")
+    t = torch.zeros((4, 1024, 2), device="cuda")
+    out = enc.encode_fwd(torch.zeros((0, 2), device="cuda"), t)
+    assert out.shape == (0, 8)
+    with pytest.raises(TypeError):
+        enc.encode_fwd(torch.zeros((4, 2), device="cuda", dtype=torch.float64), t)
+    with pytest.raises(SxeError):
+        enc.encode_bwd(torch.zeros((4, 2), device="cuda"), torch.zeros((4, 8), device="cuda"),
+                       torch.zeros((4 * 1024 * 3,), device="cuda"), grad_stride=3)
+
+
+def test_out_of_domain_points_stay_in_bounds(cuda_lib):
+    """Points outside [0,1]^d (negative, > 1, huge) and NaN still produce slots inside the
+    table (defined behaviour for finite points, no out-of-bounds access for NaN)."""
+    from paper_2311_15439_gb300.api import Encoder
+    enc = Encoder(3, 8, 2, 12, 16.0, 1.5, table_dtype="f32")
+    x = np.array([[-0.5, 2.0, 0.3], [1e4, -1e4, 5.0], [np.nan, 0.2, 0.3], [1.0, 1.0, 1.0]], dtype=np.float32)
+    slots, w = enc.encode_vertices(torch.from_numpy(x).cuda())
+    s = slots.cpu().numpy()
+    assert s.min() >= 0 and s.max() < 4096
+    scales = lattice.simplex_level_scales_fp32(3, 8, 16.0, 1.5)
+    for l in range(8):
+        ref, _, _ = O.simplex_level_vertices(x[[0, 1, 3]], scales[l], 12)
+        assert np.array_equal(s[[0, 1, 3], l, :].astype(np.int64), ref)

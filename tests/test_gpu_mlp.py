@@ -1,0 +1,199 @@
+"""GPU parity of the tensor-core network, its backward pass, the L2 loss and Adam.
+
+Network results are compared with the FP64 oracle run on the same fp16/bf16 weights and
+inputs, against an upper bound of the magnitudes involved (absolute weights and
+activations propagated through the network, no ReLU masking).  The kernel rounds each
+hidden activation and each delta to the operand type once, so a chain of at most
+2*NH + 2 roundings of unit roundoff u (2^-11 fp16, 2^-8 bf16) bounds the relative error:
+tolerance = (2*NH + 2) * u."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_err
+from oracle import adam as OA
+from oracle import mlp as OM
+from paper_2311_15439_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+U = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+NP = {"f16": np.float16}
+
+
+def _round(a, dt):
+    t = torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.float16 if dt == "f16" else torch.bfloat16)
+    return t, t.float().numpy().astype(np.float64)
+
+
+def _dens(Ws, x, dy):
+    """Magnitude bounds: forward |y| <= |W_L| ... |W_1| |x|; backward likewise."""
+    h = [np.abs(x)]
+    for W in Ws:
+        h.append(h[-1] @ np.abs(W).T)
+    d = np.abs(dy)
+    dW = [None] * len(Ws)
+    for i in reversed(range(len(Ws))):
+        dW[i] = d.T @ h[i]
+        d = d @ np.abs(Ws[i])
+    return h[-1], dW, d
+
+
+# (n_in, n_hidden, n_out, dtype, P)
+NETS = [(32, 2, 3, "f16", 4099), (32, 2, 3, "bf16", 2000), (32, 1, 1, "bf16", 3333), (16, 3, 16, "f16", 1000),
+        (64, 1, 5, "f16", 257), (32, 2, 3, "f16", 1 << 16)]
+
+
+def _setup(net, seed=0):
+    from paper_2311_15439_gb300.api import Mlp
+    n_in, nh, n_out, dt, P = net
+    mlp = Mlp(n_in, n_out, n_hidden=nh, dtype=dt)
+    W_t, W = _round(mlp.init_weights(seed), dt)
+    x_t, x = _round(synth.rng(seed + 1).uniform(-1, 1, size=(P, n_in)), dt)
+    return mlp, W_t.cuda(), mlp.split(W), x_t.cuda(), x
+
+
+@pytest.mark.parametrize("net", NETS, ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
+def test_forward(cuda_lib, net):
+    mlp, Wd, Ws, xd, x = _setup(net)
+    nh, dt = net[1], net[3]
+    act = torch.empty((nh, x.shape[0], 64), dtype=Wd.dtype, device="cuda")
+    y = mlp.mlp_fwd(Wd, xd, act=act).cpu().numpy()
+    ref, acts = OM.mlp_forward(Ws, x)
+    yden, _, _ = _dens(Ws, x, np.zeros_like(ref))
+    tol = (2 * nh + 2) * U[dt]
+    assert rel_err(y, ref, yden) <= tol
+    h = [np.abs(x)]
+    for W in Ws[:-1]:
+        h.append(h[-1] @ np.abs(W).T)
+    for i in range(nh):
+        assert rel_err(act[i].float().cpu().numpy(), acts[i + 1], h[i + 1]) <= tol
+
+
+@pytest.mark.parametrize("net", NETS, ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
+def test_backward(cuda_lib, net):
+    mlp, Wd, Ws, xd, x = _setup(net, seed=5)
+    nh, dt = net[1], net[3]
+    dy = synth.normal_grads(x.shape[0], net[2], 9).astype(np.float64)
+    dW = torch.zeros((mlp.n_params,), device="cuda")
+    din = torch.empty((x.shape[0], net[0]), device="cuda")
+    mlp.mlp_bwd(Wd, xd, torch.from_numpy(dy.astype(np.float32)).cuda(), dW, din=din, loss_scale=1.0)
+    _, acts = OM.mlp_forward(Ws, x)
+    dW_ref, din_ref = OM.mlp_backward(Ws, acts, dy)
+    _, dW_den, din_den = _dens(Ws, x, dy)
+    tol = (2 * nh + 2) * U[dt]
+    got = mlp.split(dW.cpu().numpy())
+    for i in range(len(Ws)):
+        assert rel_err(got[i], dW_ref[i], dW_den[i]) <= tol, "layer %d" % i
+    assert rel_err(din.cpu().numpy(), din_ref, din_den) <= tol
+
+
+def test_backward_accumulates_and_is_deterministic(cuda_lib):
+    mlp, Wd, Ws, xd, x = _setup((32, 2, 3, "f16", 5000), seed=3)
+    dy = torch.from_numpy(synth.normal_grads(5000, 3, 4)).cuda()
+    a = torch.zeros((mlp.n_params,), device="cuda")
+    b = torch.zeros((mlp.n_params,), device="cuda")
+    mlp.mlp_bwd(Wd, xd, dy, a)
+    mlp.mlp_bwd(Wd, xd, dy, b)
+    assert torch.equal(a, b)                       # fixed-order reduction: bitwise repeatable
+    mlp.mlp_bwd(Wd, xd, dy, a)
+    torch.testing.assert_close(a, 2 * b, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("net", [NETS[0], NETS[2], NETS[5]], ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
+def test_train_l2(cuda_lib, net):
+    """Fused forward + L2 loss + backward equals the oracle's loss and gradients, with the
+    gradient scaled by a power of two before the fp16 rounding and unscaled after."""
+    from paper_2311_15439_gb300.trainer import default_loss_scale
+    mlp, Wd, Ws, xd, x = _setup(net, seed=21)
+    n_in, nh, n_out, dt, P = net
+    tgt = synth.rng(22).random((P, n_out)).astype(np.float32)
+    dW = torch.zeros((mlp.n_params,), device="cuda")
+    din = torch.empty((P, n_in), device="cuda")
+    sq = torch.full((1,), 123.0, device="cuda")     # overwritten, not accumulated
+    ls = default_loss_scale(P, n_out)
+    mlp.mlp_train_l2(Wd, xd, torch.from_numpy(tgt).cuda(), dW, sq, din=din, loss_scale=ls)
+    y, acts = OM.mlp_forward(Ws, x)
+    loss, dy = OM.l2_loss(y, tgt)
+    dW_ref, din_ref = OM.mlp_backward(Ws, acts, dy)
+    tol = (2 * nh + 2) * U[dt]
+    yden = _dens(Ws, x, dy)[0]
+    # |dy| is bounded by 2 (|y| + |t|) / (P n_out); the squared residual's error by 3 tol (|y| + |t|)^2
+    dy_bound = 2.0 * (yden + np.abs(tgt)) / dy.size
+    _, dW_den, din_den = _dens(Ws, x, dy_bound)
+    assert abs(sq.item() / (P * n_out) - loss) <= 3 * tol * np.mean((yden + np.abs(tgt)) ** 2)
+    got = mlp.split(dW.cpu().numpy())
+    for i in range(len(Ws)):
+        assert rel_err(got[i], dW_ref[i], dW_den[i]) <= tol, "layer %d" % i
+    assert rel_err(din.cpu().numpy(), din_ref, din_den) <= tol
+
+
+def test_loss_kernel(cuda_lib):
+    from paper_2311_15439_gb300.api import loss_l2
+    g = synth.rng(3)
+    y = g.standard_normal((1000, 3)).astype(np.float32)
+    t = g.random((1000, 3)).astype(np.float32)
+    dy = torch.empty((1000, 3), device="cuda")
+    sq = torch.zeros((1,), device="cuda")
+    loss_l2(torch.from_numpy(y).cuda(), torch.from_numpy(t).cuda(), dy, sq)
+    ref_loss, ref_dy = OM.l2_loss(y, t)
+    assert sq.item() / 3000 == pytest.approx(ref_loss, rel=1e-5)
+    np.testing.assert_allclose(dy.cpu().numpy(), ref_dy, rtol=1e-6, atol=1e-12)
+
+
+def _hp32():
+    # the kernel works with the binary32 values of the hyper-parameters
+    return dict(lr=float(np.float32(1e-2)), beta1=float(np.float32(0.9)), beta2=float(np.float32(0.99)),
+                eps=float(np.float32(1e-15)))
+
+
+@pytest.mark.parametrize("skip", [False, True])
+def test_adam_dense(cuda_lib, skip):
+    from paper_2311_15439_gb300.api import Adam
+    g = synth.rng(4)
+    n = 10007
+    p = g.standard_normal(n).astype(np.float32)
+    m = (g.standard_normal(n) * 0.1).astype(np.float32)
+    v = (g.random(n) * 0.01).astype(np.float32)
+    gr = (g.standard_normal(n) * (g.random(n) < 0.8)).astype(np.float32)
+    dev = [torch.from_numpy(a.copy()).cuda() for a in (p, m, v, gr)]
+    low = torch.empty(n, dtype=torch.float16, device="cuda")
+    Adam(1e-2, 0.9, 0.99, 1e-15, skip_zero_grad=skip).step(3, *dev, lowp=low)
+    rp, rm, rv = OA.adam_step(p, gr, m, v, 3, skip_zero_grad=skip, **_hp32())
+    for got, want in zip(dev[:3], (rp, rm, rv)):
+        np.testing.assert_allclose(got.cpu().numpy(), want, rtol=2e-6, atol=1e-7)
+    assert torch.equal(low, dev[0].half())
+    if skip:
+        assert torch.all(dev[3] == 0)
+
+
+@pytest.mark.parametrize("F,dt", [(2, "f16"), (2, "bf16"), (1, "f32"), (4, "f16"), (8, "f32")])
+def test_adam_touched(cuda_lib, F, dt):
+    """The bitmap-driven table step equals dense Adam with the zero-gradient skip rule."""
+    from paper_2311_15439_gb300.api import Adam
+    g = synth.rng(5 + F)
+    n_entries = 4096 + 17
+    marked = g.random(n_entries) < 0.3
+    p = g.standard_normal((n_entries, F)).astype(np.float32)
+    m = (g.standard_normal((n_entries, F)) * 0.1).astype(np.float32)
+    v = (g.random((n_entries, F)) * 0.01).astype(np.float32)
+    gr = (g.standard_normal((n_entries, F)) * marked[:, None]).astype(np.float32)
+    gr[::7] = 0.0                                   # marked entries whose gradient is exactly zero
+    state = torch.from_numpy(np.concatenate([p, m, v, gr], axis=1).copy()).cuda()
+    words = np.zeros((n_entries + 31) // 32, dtype=np.uint32)
+    for e in np.nonzero(marked)[0]:
+        words[e >> 5] |= np.uint32(1 << (e & 31))
+    touched = torch.from_numpy(words.view(np.int32).copy()).cuda()
+    tdt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[dt]
+    table = torch.from_numpy(p.copy()).to(tdt).cuda()
+    Adam(1e-2, 0.9, 0.99, 1e-15).step_touched(5, state, touched, table, F)
+    rp, rm, rv = OA.adam_step(p, gr, m, v, 5, skip_zero_grad=True, **_hp32())
+    s = state.cpu().numpy()
+    np.testing.assert_allclose(s[:, :F], rp, rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(s[:, F:2 * F], rm, rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(s[:, 2 * F:3 * F], rv, rtol=2e-6, atol=1e-9)
+    assert np.all(s[:, 3 * F:] == 0)
+    assert torch.all(touched == 0)
+    assert torch.equal(table[torch.from_numpy(marked).cuda()], state[:, :F][torch.from_numpy(marked).cuda()].to(tdt))

@@ -1,0 +1,166 @@
+"""GPU parity of the full training step (encode -> network + L2 -> encode backward -> Adam)
+and of the autograd wrappers."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_err
+from oracle import adam as OA
+from oracle import encoding as OE
+from oracle import mlp as OM
+from paper_2311_15439_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CFG = dict(d=2, n_levels=8, n_features=2, log2_T=12, base_res=16.0, growth=1.5)
+
+
+def _make(P=4096, seed=0, table_dtype="f16"):
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+    enc = Encoder(**CFG, table_dtype=table_dtype)
+    mlp = Mlp(16, 3, n_hidden=2, dtype="f16")
+    return Trainer(enc, mlp, P, seed=seed)
+
+
+def test_one_step_matches_oracle():
+    """Gradients of one step against the oracle pipeline: encode (FP64, rounded to the fp16
+    encoding the network consumes), network + L2 loss and backward (FP64), scatter-add of
+    dL/d(encoding) into the tables (FP64); then the Adam step of every table entry whose
+    gradient sign is unambiguous, and of every network weight likewise."""
+    from paper_2311_15439_gb300.build import build
+    build()
+    P = 4096
+    tr = _make(P)
+    x = synth.uniform_points(P, 2, 5)
+    tgt = synth.ProceduralImage(6, size=4096, n_waves=16).sample(x)
+    F, L, T = 2, 8, 1 << 12
+    # the oracle regenerates the seeded initial values on the host and rounds them itself
+    p_tab0 = synth.uniform_tables(L, T, F, 0, dtype="f32", scale=1e-4)[0].reshape(L * T, F).astype(np.float64)
+    tables = p_tab0.astype(np.float16).astype(np.float64).reshape(L, T, F)
+    W0 = tr.mlp.init_weights(1).astype(np.float64)
+    W = [w.astype(np.float16).astype(np.float64) for w in tr.mlp.split(W0)]
+
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda()
+    # run the first three stages of the step and stop before the optimiser
+    tr.enc.encode_fwd(xd, tr.tables, tr.enc_out)
+    tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, td, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
+                        workspace=tr.ws)
+    tr.enc.encode_bwd(xd, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
+    g_tab = tr.state[:, 3 * F:].cpu().numpy().copy()
+    g_W = tr.dW.cpu().numpy().copy()
+    loss_gpu = tr.loss()
+
+    enc = OE.simplex_encode(x, tables, base_res=16.0, growth=1.5)
+    enc16 = enc.astype(np.float16).astype(np.float64)          # the encoding dtype the network reads
+    y, acts = OM.mlp_forward(W, enc16)
+    loss, dy = OM.l2_loss(y, tgt)
+    dW_ref, denc = OM.mlp_backward(W, acts, dy)
+    g_ref, g_den = OE.simplex_encode_bwd(x, denc, n_levels=L, log2_T=12, n_features=F, base_res=16.0,
+                                         growth=1.5, with_denominator=True)
+    # magnitude bound of dL/d(encoding): |dy| through |W|
+    d = 2 * (np.abs(y) + np.abs(tgt)) / dy.size
+    for Wi in reversed(W):
+        d = d @ np.abs(Wi)
+    _, den_bound = OE.simplex_encode_bwd(x, d, n_levels=L, log2_T=12, n_features=F, base_res=16.0, growth=1.5,
+                                         with_denominator=True)
+    tol = 6 * 2.0 ** -11
+    assert abs(loss_gpu - loss) <= 3 * tol * loss + 1e-6
+    for l in range(L):
+        assert rel_err(g_tab[l * T:(l + 1) * T], g_ref[l], den_bound[l]) <= tol, "level %d" % l
+
+    # optimiser: Adam at t = 1 moves each parameter by -lr * g / (|g| + eps); compare where the
+    # sign of the gradient is unambiguous (|g_ref| well above the tolerance)
+    tr.adam_tables.step_touched(1, tr.state, tr.touched, tr.tables, F)
+    tr.adam_mlp.step(1, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
+    hp = dict(lr=float(np.float32(1e-2)), beta1=float(np.float32(0.9)), beta2=float(np.float32(0.99)),
+              eps=float(np.float32(1e-15)))
+    g_all = np.concatenate([g_ref[l] for l in range(L)])
+    den_all = np.concatenate([den_bound[l] for l in range(L)])
+    p_ref, _, _ = OA.adam_step(p_tab0, g_all, np.zeros_like(g_all), np.zeros_like(g_all), 1, skip_zero_grad=True, **hp)
+    clear = (np.abs(g_all) > 4 * tol * den_all) | (den_all == 0)
+    p_gpu = tr.state[:, :F].cpu().numpy()
+    np.testing.assert_allclose(p_gpu[clear], p_ref[clear], rtol=0, atol=2e-6)
+    assert clear.mean() > 0.5
+    gW_ref = np.concatenate([a.ravel() for a in dW_ref])
+    W_ref, _, _ = OA.adam_step(W0, gW_ref, np.zeros_like(W0), np.zeros_like(W0), 1, skip_zero_grad=False, **hp)
+    clearW = np.abs(gW_ref) > 1e-2 * np.abs(gW_ref).max()
+    np.testing.assert_allclose(tr.W.cpu().numpy()[clearW], W_ref[clearW], rtol=0, atol=1e-5)
+    assert np.abs(g_W - gW_ref).max() <= tol * np.abs(gW_ref).max() * 4
+
+
+def test_training_reduces_loss():
+    """Fitting the procedural image with the full step drives the L2 loss down."""
+    P = 1 << 14
+    tr = _make(P, seed=3)
+    img = synth.ProceduralImage(7, size=2048, n_waves=8)
+    losses = []
+    for it in range(60):
+        x = synth.uniform_points(P, 2, 100 + it)
+        tr.step(torch.from_numpy(x).cuda(), torch.from_numpy(img.sample(x)).cuda())
+        if it in (0, 59):
+            losses.append(tr.loss())
+    assert losses[1] < 0.5 * losses[0]
+
+
+def test_step_is_repeatable():
+    """Two trainers with the same seed and batches end bitwise identical (forward has no
+    atomics; the table gradient atomics may reorder, so compare the parameters within the
+    Adam step's sensitivity and the loss exactly for the first step)."""
+    P = 2048
+    a, b = _make(P, seed=9), _make(P, seed=9)
+    x = synth.uniform_points(P, 2, 1)
+    tgt = synth.ProceduralImage(2, size=1024, n_waves=4).sample(x)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda()
+    a.step(xd, td)
+    b.step(xd, td)
+    assert a.loss() == b.loss()
+    assert torch.equal(a.W, b.W)
+
+
+def test_autograd_encoding_matches_oracle_and_fd():
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.autograd import encode
+    enc = Encoder(3, 6, 2, 12, 8.0, 1.5, table_dtype="f32")
+    vals = synth.uniform_tables(6, 1 << 12, 2, 4, scale=1.0)[0]
+    H = torch.from_numpy(vals).cuda().requires_grad_(True)
+    x = synth.uniform_points(1500, 3, 5)
+    D = synth.normal_grads(1500, 12, 6)
+    out = encode(torch.from_numpy(x).cuda(), H, enc)
+    (out * torch.from_numpy(D).cuda()).sum().backward()
+    g = H.grad.cpu().numpy()
+    ref, den = OE.simplex_encode_bwd(x, D, n_levels=6, log2_T=12, n_features=2, base_res=8.0, growth=1.5,
+                                     with_denominator=True)
+    for l in range(6):
+        assert rel_err(g[l], ref[l], den[l]) <= 1e-5
+    # finite differences of the CUDA forward in binary32 (exact up to rounding: linear in H)
+    rng = synth.rng(7)
+    Dt = torch.from_numpy(D).cuda()
+    xd = torch.from_numpy(x).cuda()
+    for _ in range(10):
+        l, s, f = int(rng.integers(6)), int(ref[0].shape[0] * 0 + rng.integers(1 << 12)), int(rng.integers(2))
+        if den[l][s, f] == 0:
+            continue
+        Hp, Hm = H.detach().clone(), H.detach().clone()
+        Hp[l, s, f] += 0.5
+        Hm[l, s, f] -= 0.5
+        fd = ((enc.encode_fwd(xd, Hp) * Dt).double().sum() - (enc.encode_fwd(xd, Hm) * Dt).double().sum()).item()
+        assert abs(fd - g[l, s, f]) <= 1e-4 * max(1.0, den[l][s, f])
+
+
+def test_autograd_mlp_matches_oracle():
+    from paper_2311_15439_gb300.api import Mlp
+    from paper_2311_15439_gb300.autograd import mlp_apply
+    mlp = Mlp(32, 3, n_hidden=2, dtype="f16")
+    W = torch.from_numpy(mlp.init_weights(1)).half().cuda().requires_grad_(True)
+    x = torch.from_numpy(synth.rng(2).uniform(-1, 1, (600, 32)).astype(np.float32)).half().cuda().requires_grad_(True)
+    y = mlp_apply(x, W, mlp)
+    dy = torch.from_numpy(synth.normal_grads(600, 3, 3)).cuda()
+    (y * dy).sum().backward()
+    Ws = [w.astype(np.float64) for w in mlp.split(W.detach().float().cpu().numpy())]
+    _, acts = OM.mlp_forward(Ws, x.detach().float().cpu().numpy().astype(np.float64))
+    dW_ref, din_ref = OM.mlp_backward(Ws, acts, dy.cpu().numpy().astype(np.float64))
+    gW = mlp.split(W.grad.float().cpu().numpy())
+    for a, b in zip(gW, dW_ref):
+        assert np.abs(a - b).max() <= 1e-2 * np.abs(b).max()
+    assert np.abs(x.grad.float().cpu().numpy() - din_ref).max() <= 1e-2 * np.abs(din_ref).max()
