@@ -135,6 +135,18 @@ sxe_status sxe_encode_bwd(const sxe_encoder* enc, const float* x, int64_t n_poin
 sxe_status sxe_encode_vertices(const sxe_encoder* enc, const float* x, int64_t n_points,
                                uint32_t* slots, float* weights, void* stream);
 
+/* Plain binary32 comparator of the simplex encoding: one thread per point loops over
+ * the levels, orders the fractional parts with a bubble sort (the paper's choice,
+ * Sec. 4.2 footnote), walks the vertices one axis at a time (Remark 2), loads every
+ * feature and adds every gradient term separately.  Same arithmetic and results as
+ * sxe_encode_fwd / sxe_encode_bwd; requires kind = SXE_SIMPLEX and binary32 tables and
+ * output (else SXE_EUNSUPPORTED).  out [n_points][L*F] is overwritten; grad is a dense
+ * [L][T][F] binary32 array, accumulated. */
+sxe_status sxe_encode_plain_fwd(const sxe_encoder* enc, const float* x, int64_t n_points,
+                                const float* tables, float* out, void* stream);
+sxe_status sxe_encode_plain_bwd(const sxe_encoder* enc, const float* x, int64_t n_points,
+                                const float* dout, float* grad, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Tiny fully connected network (Sec. 5 d-e; about 7k weights, Sec. 6.1).     */
 /* ------------------------------------------------------------------------ */

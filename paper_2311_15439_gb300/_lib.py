@@ -20,7 +20,7 @@ SXE_MAX_LEVELS = 32
 #: every function the header declares (checked by the export test)
 EXPORTS = (
     "sxe_encoder_create", "sxe_encoder_destroy", "sxe_encoder_level_params",
-    "sxe_encode_fwd", "sxe_encode_bwd", "sxe_encode_vertices",
+    "sxe_encode_fwd", "sxe_encode_bwd", "sxe_encode_vertices", "sxe_encode_plain_fwd", "sxe_encode_plain_bwd",
     "sxe_mlp_n_params", "sxe_mlp_fwd", "sxe_mlp_bwd_workspace_bytes", "sxe_mlp_bwd", "sxe_mlp_train_l2",
     "sxe_loss_l2", "sxe_step", "sxe_step_touched", "sxe_last_error", "sxe_version",
 )
@@ -58,6 +58,8 @@ def _declare(L):
         "sxe_encode_fwd": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_encode_bwd": (i32, [vp, vp, i64, vp, vp, i64, vp, vp]),
         "sxe_encode_vertices": (i32, [vp, vp, i64, vp, vp, vp]),
+        "sxe_encode_plain_fwd": (i32, [vp, vp, i64, vp, vp, vp]),
+        "sxe_encode_plain_bwd": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_mlp_n_params": (i64, [M]),
         "sxe_mlp_fwd": (i32, [M, vp, vp, i64, vp, vp, vp]),
         "sxe_mlp_bwd_workspace_bytes": (i64, [M, i64]),

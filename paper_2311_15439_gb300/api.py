@@ -118,6 +118,28 @@ class Encoder:
                 "sxe_encode_bwd")
         return grad
 
+    def encode_plain_fwd(self, x: torch.Tensor, tables: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """Plain binary32 comparator path (``sxe_encode_plain_fwd``)."""
+        P = x.shape[0]
+        _need(x, torch.float32, "x", (P, self.d))
+        _need(tables, torch.float32, "tables", self.table_shape())
+        if out is None:
+            out = torch.empty((P, self.n_out), dtype=torch.float32, device=x.device)
+        _need(out, torch.float32, "out", (P, self.n_out))
+        L.check(L.lib().sxe_encode_plain_fwd(self._h, _ptr(x), P, _ptr(tables), _ptr(out), _stream(stream)),
+                "sxe_encode_plain_fwd")
+        return out
+
+    def encode_plain_bwd(self, x: torch.Tensor, dout: torch.Tensor, grad: torch.Tensor, stream=None):
+        """Plain binary32 comparator path (``sxe_encode_plain_bwd``); grad is a dense [L, T, F] array."""
+        P = x.shape[0]
+        _need(x, torch.float32, "x", (P, self.d))
+        _need(dout, torch.float32, "dout", (P, self.n_out))
+        _need(grad, torch.float32, "grad", self.table_shape())
+        L.check(L.lib().sxe_encode_plain_bwd(self._h, _ptr(x), P, _ptr(dout), _ptr(grad), _stream(stream)),
+                "sxe_encode_plain_bwd")
+        return grad
+
     def encode_vertices(self, x: torch.Tensor, stream=None):
         """(slots int32 [P, L, V], weights float32 [P, L, V])."""
         P = x.shape[0]

@@ -151,6 +151,30 @@ sxe_status sxe_encode_vertices(const sxe_encoder* e, const float* x, int64_t P, 
   return launch_encode_vertices(e, x, P, slots, weights, (cudaStream_t)stream);
 }
 
+static sxe_status check_plain(const char* fn, const sxe_encoder* e, const float* x, int64_t P, const void* a,
+                              const void* b) {
+  sxe_status st = check_points(fn, e, x, P);
+  if (st != SXE_OK) return st;
+  if (e->desc.kind != SXE_SIMPLEX || e->desc.table_dtype != SXE_F32 || e->desc.out_dtype != SXE_F32)
+    return set_error(SXE_EUNSUPPORTED, "%s: needs a simplex encoder with binary32 tables and output", fn);
+  if (P > 0 && (!a || !b)) return set_error(SXE_EINVAL, "%s: NULL buffer", fn);
+  return SXE_OK;
+}
+
+sxe_status sxe_encode_plain_fwd(const sxe_encoder* e, const float* x, int64_t P, const float* tables, float* out,
+                                void* stream) {
+  sxe_status st = check_plain("encode_plain_fwd", e, x, P, tables, out);
+  if (st != SXE_OK || P == 0) return st;
+  return launch_encode_plain(e, false, x, P, tables, out, (cudaStream_t)stream);
+}
+
+sxe_status sxe_encode_plain_bwd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* grad,
+                                void* stream) {
+  sxe_status st = check_plain("encode_plain_bwd", e, x, P, dout, grad);
+  if (st != SXE_OK || P == 0) return st;
+  return launch_encode_plain(e, true, x, P, dout, grad, (cudaStream_t)stream);
+}
+
 // ---------------------------------------------------------------------------
 static sxe_status check_mlp(const char* fn, const sxe_mlp_desc* d) {
   if (!d) return set_error(SXE_EINVAL, "%s: NULL desc", fn);
@@ -254,7 +278,8 @@ sxe_status sxe_step_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries
   if (n_entries == 0) return SXE_OK;
   if (!state || !touched || !lowp) return set_error(SXE_EINVAL, "step_touched: NULL state, touched or table");
   if (!valid_dtype(lowp_dtype)) return set_error(SXE_EINVAL, "step_touched: bad lowp dtype");
-  if (!aligned(state, 16) || !aligned(touched, 4)) return set_error(SXE_EINVAL, "step_touched: misaligned buffer");
+  if (!aligned(state, 16) || !aligned(touched, 4) || !aligned(lowp, F == 2 ? 2 * dtype_size(lowp_dtype) : 1))
+    return set_error(SXE_EINVAL, "step_touched: misaligned buffer");
   return launch_adam_touched(a, t, n_entries, F, state, touched, lowp, lowp_dtype, (cudaStream_t)stream);
 }
 

@@ -53,28 +53,49 @@ __global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p,
   }
 }
 
+// Low-precision copy of F consecutive parameters in one store where the type allows.
 template <int F>
-__global__ void adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state,
-                                    uint32_t* __restrict__ touched, void* __restrict__ lowp, int ldt) {
+__device__ __forceinline__ void store_lowp(void* base, int64_t e, int ldt, const float (&p)[F]) {
+  if (F == 2 && ldt == SXE_F16) {
+    reinterpret_cast<__half2*>(base)[e] = __floats2half2_rn(p[0], p[1]);
+  } else if (F == 2 && ldt == SXE_BF16) {
+    reinterpret_cast<__nv_bfloat162*>(base)[e] = __floats2bfloat162_rn(p[0], p[1]);
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) store_as(base, e * F + f, ldt, p[f]);
+  }
+}
+
+template <int F>
+__global__ void __launch_bounds__(256)
+adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state, uint32_t* __restrict__ touched,
+                    void* __restrict__ lowp, int ldt) {
+  constexpr int NV = F;                            // float4 vectors per record of 4F floats
   const int lane = threadIdx.x & 31;
   const int64_t n_words = (n_entries + 31) >> 5;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w = warp0; w < n_words; w += n_warps) {
-    const uint32_t bits = touched[w];            // uniform across the warp
+    const uint32_t bits = touched[w];              // uniform across the warp
     if (bits == 0u) continue;
     const int64_t e = (w << 5) + lane;
     if (((bits >> lane) & 1u) && e < n_entries) {
-      float* rec = state + e * (4 * F);
-      float p[F], m[F], v[F], g[F];
+      float4* rec = reinterpret_cast<float4*>(state + e * (4 * F));
+      union { float4 v[NV]; float f[4 * F]; } r;
 #pragma unroll
-      for (int f = 0; f < F; ++f) { p[f] = rec[f]; m[f] = rec[F + f]; v[f] = rec[2 * F + f]; g[f] = rec[3 * F + f]; }
+      for (int j = 0; j < NV; ++j) r.v[j] = rec[j];
+      float p[F];
 #pragma unroll
       for (int f = 0; f < F; ++f) {
-        if (g[f] != 0.f) adam_one(k, g[f], p[f], m[f], v[f]);
-        rec[f] = p[f]; rec[F + f] = m[f]; rec[2 * F + f] = v[f]; rec[3 * F + f] = 0.f;
-        store_as(lowp, e * F + f, ldt, p[f]);
+        float pp = r.f[f], mm = r.f[F + f], vv = r.f[2 * F + f];
+        const float g = r.f[3 * F + f];
+        if (g != 0.f) adam_one(k, g, pp, mm, vv);
+        r.f[f] = pp; r.f[F + f] = mm; r.f[2 * F + f] = vv; r.f[3 * F + f] = 0.f;
+        p[f] = pp;
       }
+#pragma unroll
+      for (int j = 0; j < NV; ++j) rec[j] = r.v[j];
+      store_lowp<F>(lowp, e, ldt, p);
     }
     __syncwarp();
     if (lane == 0) touched[w] = 0u;

@@ -46,6 +46,8 @@ sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, 
                              void* out, cudaStream_t s);
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
                              float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s);
+sxe_status launch_encode_plain(const sxe_encoder* enc, bool backward, const float* x, int64_t P, const float* a,
+                               float* b, cudaStream_t s);
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,
                                   float* weights, cudaStream_t s);
 

@@ -49,3 +49,17 @@ def rel_err(got, want, den, floor=1e-30):
 #: accumulation of at most 32 terms (1e-5, the stated FP32 bar), or one final rounding
 #: to fp16 (unit roundoff 2^-11 -> 2e-3) / bf16 (2^-8 -> 5e-3).
 ENC_TOL = {"f32": 1e-5, "f16": 2e-3, "bf16": 5e-3}
+#: absolute part of the same bound: below 2^-14 fp16 is subnormal with spacing 2^-24, so
+#: one rounding errs by up to 2^-25 regardless of the value (bf16 and binary32 keep the
+#: binary32 exponent range: no floor needed at these magnitudes).
+ENC_ATOL = {"f32": 0.0, "f16": 2.0 ** -25, "bf16": 0.0}
+
+
+def worst_ratio(got, want, den, tol, atol=0.0):
+    """max |got - want| / (tol * den + atol): <= 1 means within the bound everywhere."""
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    bound = tol * np.asarray(den, dtype=np.float64) + atol
+    err = np.abs(got - want)
+    return float(np.max(np.where(bound > 0, err / np.where(bound > 0, bound, 1.0), np.where(err > 0, np.inf, 0.0))))

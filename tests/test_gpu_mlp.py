@@ -41,6 +41,22 @@ def _dens(Ws, x, dy):
     return h[-1], dW, d
 
 
+def ambiguous_rows(Ws, x, tol):
+    """Points for which some hidden pre-activation lies within the rounding band of zero
+    (|z| <= tol * its magnitude bound): there the ReLU decision, and the backward pass below
+    it, may legitimately come out either way at the kernel's precision."""
+    h = np.asarray(x, dtype=np.float64)
+    habs = np.abs(h)
+    amb = np.zeros(len(h), dtype=bool)
+    for W in Ws[:-1]:
+        z = h @ W.T
+        zden = habs @ np.abs(W).T
+        amb |= np.any(np.abs(z) <= tol * zden, axis=1)
+        h = np.maximum(z, 0.0)
+        habs = zden
+    return amb
+
+
 # (n_in, n_hidden, n_out, dtype, P)
 NETS = [(32, 2, 3, "f16", 4099), (32, 2, 3, "bf16", 2000), (32, 1, 1, "bf16", 3333), (16, 3, 16, "f16", 1000),
         (64, 1, 5, "f16", 257), (32, 2, 3, "f16", 1 << 16)]
@@ -87,7 +103,9 @@ def test_backward(cuda_lib, net):
     got = mlp.split(dW.cpu().numpy())
     for i in range(len(Ws)):
         assert rel_err(got[i], dW_ref[i], dW_den[i]) <= tol, "layer %d" % i
-    assert rel_err(din.cpu().numpy(), din_ref, din_den) <= tol
+    amb = ambiguous_rows(Ws, x, tol)
+    assert amb.mean() < 0.05
+    assert rel_err(din.cpu().numpy()[~amb], din_ref[~amb], din_den[~amb]) <= tol
 
 
 def test_backward_accumulates_and_is_deterministic(cuda_lib):
@@ -127,7 +145,9 @@ def test_train_l2(cuda_lib, net):
     got = mlp.split(dW.cpu().numpy())
     for i in range(len(Ws)):
         assert rel_err(got[i], dW_ref[i], dW_den[i]) <= tol, "layer %d" % i
-    assert rel_err(din.cpu().numpy(), din_ref, din_den) <= tol
+    amb = ambiguous_rows(Ws, x, tol)
+    assert amb.mean() < 0.05
+    assert rel_err(din.cpu().numpy()[~amb], din_ref[~amb], din_den[~amb]) <= tol
 
 
 def test_loss_kernel(cuda_lib):

@@ -66,8 +66,21 @@ def test_one_step_matches_oracle():
                                          with_denominator=True)
     tol = 6 * 2.0 ** -11
     assert abs(loss_gpu - loss) <= 3 * tol * loss + 1e-6
+    # entries fed by a point whose ReLU decisions are ambiguous at fp16 are checked only for
+    # being finite; all others against the bound
+    from test_gpu_mlp import ambiguous_rows
+    from oracle import lattice
+    amb = ambiguous_rows(W, enc16, tol)
+    assert amb.mean() < 0.05
+    scales = lattice.simplex_level_scales_fp32(2, L, 16.0, 1.5)
+    shaky = np.zeros(L * T, dtype=bool)
     for l in range(L):
-        assert rel_err(g_tab[l * T:(l + 1) * T], g_ref[l], den_bound[l]) <= tol, "level %d" % l
+        s_amb, _, _ = OE.simplex_level_vertices(x[amb], scales[l], 12)
+        shaky[l * T + s_amb.ravel()] = True
+    assert np.all(np.isfinite(g_tab))
+    for l in range(L):
+        ok = ~shaky[l * T:(l + 1) * T]
+        assert rel_err(g_tab[l * T:(l + 1) * T][ok], g_ref[l][ok], den_bound[l][ok]) <= tol, "level %d" % l
 
     # optimiser: Adam at t = 1 moves each parameter by -lr * g / (|g| + eps); compare where the
     # sign of the gradient is unambiguous (|g_ref| well above the tolerance)
@@ -78,7 +91,7 @@ def test_one_step_matches_oracle():
     g_all = np.concatenate([g_ref[l] for l in range(L)])
     den_all = np.concatenate([den_bound[l] for l in range(L)])
     p_ref, _, _ = OA.adam_step(p_tab0, g_all, np.zeros_like(g_all), np.zeros_like(g_all), 1, skip_zero_grad=True, **hp)
-    clear = (np.abs(g_all) > 4 * tol * den_all) | (den_all == 0)
+    clear = ((np.abs(g_all) > 4 * tol * den_all) | (den_all == 0)) & ~shaky[:, None]
     p_gpu = tr.state[:, :F].cpu().numpy()
     np.testing.assert_allclose(p_gpu[clear], p_ref[clear], rtol=0, atol=2e-6)
     assert clear.mean() > 0.5
@@ -160,7 +173,18 @@ def test_autograd_mlp_matches_oracle():
     Ws = [w.astype(np.float64) for w in mlp.split(W.detach().float().cpu().numpy())]
     _, acts = OM.mlp_forward(Ws, x.detach().float().cpu().numpy().astype(np.float64))
     dW_ref, din_ref = OM.mlp_backward(Ws, acts, dy.cpu().numpy().astype(np.float64))
-    gW = mlp.split(W.grad.float().cpu().numpy())
-    for a, b in zip(gW, dW_ref):
-        assert np.abs(a - b).max() <= 1e-2 * np.abs(b).max()
-    assert np.abs(x.grad.float().cpu().numpy() - din_ref).max() <= 1e-2 * np.abs(din_ref).max()
+    # the Function returns exactly what the C ABI computes, cast to the parameter dtypes
+    dW_direct = torch.zeros((mlp.n_params,), device="cuda")
+    din_direct = torch.empty((600, 32), device="cuda")
+    mlp.mlp_bwd(W.detach(), x.detach(), dy, dW_direct, din=din_direct)
+    assert torch.equal(W.grad, dW_direct.half())
+    assert torch.equal(x.grad, din_direct.half())
+    # and agrees with the oracle within the network tolerance plus the final fp16 rounding
+    from test_gpu_mlp import _dens, ambiguous_rows
+    xs = x.detach().float().cpu().numpy().astype(np.float64)
+    _, dW_den, din_den = _dens(Ws, xs, dy.cpu().numpy().astype(np.float64))
+    tol = 6 * 2.0 ** -11 + 2.0 ** -11
+    for a, b, den in zip(mlp.split(W.grad.float().cpu().numpy()), dW_ref, dW_den):
+        assert rel_err(a, b, den) <= tol
+    amb = ambiguous_rows(Ws, xs, tol)
+    assert rel_err(x.grad.float().cpu().numpy()[~amb], din_ref[~amb], din_den[~amb]) <= tol
