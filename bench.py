@@ -216,6 +216,7 @@ def run_gpu(args):
 
     # ---- comparators on the same GPU (encode forward + backward only, equal L, F, T)
     comparators = encode_sweep(dev) if (rank == 0 and not args.no_sweep) else None
+    serving = serve_bench(dev) if (rank == 0 and not args.no_serve) else None
 
     if rank == 0:
         value = BATCH * args.steps * world / (ms / 1e3)
@@ -243,6 +244,8 @@ def run_gpu(args):
         }
         if comparators is not None:
             line["comparators"] = comparators
+        if serving is not None:
+            line["serve"] = serving
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline_subprocess(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -281,6 +284,30 @@ def encode_sweep(dev, reps=20):
             row["%s_%s" % (kind, tdt)] = P * reps / (s.elapsed_time(e) / 1e3)
         out["d%d" % d] = row
     return {"encode_fwd_bwd_points_per_s": out, "config": "L=16 F=2 T=2^19 base 16 growth 1.38, 2^20 points"}
+
+
+def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5):
+    """Poisson-arriving field queries of 4K..4M points (log-uniform), d uniform in 2..5, served
+    by the continuous-batching loop; simplex fields vs 2^d grid fields (L=16, F=2, T=2^19, fp16)."""
+    import torch
+    from paper_2311_15439_gb300 import synth
+    from paper_2311_15439_gb300.serve import FieldServer, make_field, poisson_load, run_load
+    arrivals, ds, sizes = poisson_load(rate_hz, n_requests, (2, 3, 4, 5), 4096, 4 << 20, seed)
+    pools = {d: torch.from_numpy(synth.uniform_points(4 << 20, d, 900 + d)).pin_memory() for d in (2, 3, 4, 5)}
+    out = {"load": "%d Poisson requests at %.0f/s, sizes log-uniform 4K..4M points, d in {2,3,4,5}" % (n_requests, rate_hz)}
+    for kind in ("simplex", "grid"):
+        fields = {d: make_field(d, kind=kind, seed=d, device=dev) for d in (2, 3, 4, 5)}
+        srv = FieldServer(fields, mem_budget_bytes=4 << 30, n_slots=4, max_batch_points=4 << 20, device=dev).start()
+        # warm-up: one request per d (allocator, pinned buffers, kernel load)
+        for d in (2, 3, 4, 5):
+            srv.submit(d, pools[d][:65536]).wait()
+        reqs, wall = run_load(srv, arrivals, ds, sizes, pools, seed)
+        srv.stop()
+        lat = np.array([r.latency for r in reqs]) * 1e3
+        out[kind] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "points_per_s": float(sizes.sum() / wall), "batches": srv.n_batches,
+                     "errors": sum(r.error is not None for r in reqs)}
+    return out
 
 
 # ----------------------------------------------------------------------------------------
@@ -377,6 +404,7 @@ def main():
     ap.add_argument("--kind", default="simplex", choices=["simplex", "grid"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-baseline-only", action="store_true")
     args = ap.parse_args()

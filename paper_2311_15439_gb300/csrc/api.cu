@@ -206,7 +206,7 @@ sxe_status sxe_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int
 
 int64_t sxe_mlp_bwd_workspace_bytes(const sxe_mlp_desc* d, int64_t P) {
   if (!d || P <= 0) return 0;
-  return (int64_t)mlp_grid_blocks(P) * (sxe_mlp_n_params(d) + 1) * (int64_t)sizeof(float);
+  return (int64_t)mlp_grid_blocks(d, P) * (sxe_mlp_n_params(d) + 1) * (int64_t)sizeof(float);
 }
 
 static sxe_status mlp_bwd_common(const char* fn, const sxe_mlp_desc* d, const void* W, const void* in,
@@ -222,7 +222,7 @@ static sxe_status mlp_bwd_common(const char* fn, const sxe_mlp_desc* d, const vo
     return set_error(SXE_EINVAL, "%s: misaligned buffer", fn);
   const int64_t need = sxe_mlp_bwd_workspace_bytes(d, P);
   if (ws_bytes < need) return set_error(SXE_ENOMEM, "%s: workspace %lld < %lld bytes", fn, (long long)ws_bytes, (long long)need);
-  return launch_mlp_bwd(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, (float*)ws, mlp_grid_blocks(P),
+  return launch_mlp_bwd(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, (float*)ws, mlp_grid_blocks(d, P),
                         (cudaStream_t)stream);
 }
 

@@ -110,6 +110,18 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
   const int L = prm.n_levels;
   const Item it = item_of(L);
   if (it.p >= P) return;
+  float xv[D];
+  load_point<D>(x, it.p, xv);
+  const uint32_t mask = (1u << prm.log2_T) - 1u;
+  uint32_t slot[V];
+  float w[V];
+  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
+  const int64_t lbase = (int64_t)it.l << prm.log2_T;
+  // Pull the gradient entries into L2 through the load path before the atomics reach them:
+  // atomics that miss L2 are processed far more slowly than plain-load misses.
+#pragma unroll
+  for (int k = 0; k < V; ++k)
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(grad + (lbase + slot[k]) * stride));
   float g[F];
   const float* pd = dout + (it.p * L + it.l) * F;
   if constexpr (F == 2) {
@@ -119,13 +131,6 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
 #pragma unroll
     for (int f = 0; f < F; ++f) g[f] = __ldg(pd + f);
   }
-  float xv[D];
-  load_point<D>(x, it.p, xv);
-  const uint32_t mask = (1u << prm.log2_T) - 1u;
-  uint32_t slot[V];
-  float w[V];
-  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
-  const int64_t lbase = (int64_t)it.l << prm.log2_T;
 #pragma unroll
   for (int k = 0; k < V; ++k) {
     float c[F];

@@ -85,12 +85,9 @@ template <int N_IN, int NH>
 struct Smem {
   static constexpr int SX = N_IN + 8;
   static constexpr int W0 = 0;                                  // [64][SX]      W_0
-  static constexpr int W0T = W0 + kWidth * SX;                  // [N_IN][kSW]   W_0^T
-  static constexpr int WH = W0T + N_IN * kSW;                   // (NH-1) x [64][kSW]  W_h
-  static constexpr int WHT = WH + (NH - 1) * kWidth * kSW;      // (NH-1) x [64][kSW]  W_h^T
-  static constexpr int WO = WHT + (NH - 1) * kWidth * kSW;      // [16][kSW]     W_out (zero padded)
-  static constexpr int WOT = WO + 16 * kSW;                     // [64][kSO]     W_out^T
-  static constexpr int X = WOT + kWidth * kSO;                  // [128][SX]     inputs of the tile
+  static constexpr int WH = W0 + kWidth * SX;                   // (NH-1) x [64][kSW]  W_h
+  static constexpr int WO = WH + (NH - 1) * kWidth * kSW;       // [16][kSW]     W_out (zero padded)
+  static constexpr int X = WO + 16 * kSW;                       // [128][SX]     inputs of the tile
   static constexpr int A = X + kTile * SX;                      // NH x [128][kSW] hidden activations
   static constexpr int D = A + NH * kTile * kSW;                // NH x [128][kSW] hidden deltas
   static constexpr int DY = D + NH * kTile * kSW;               // [128][kSO]    output delta
@@ -101,33 +98,31 @@ struct Smem {
   static constexpr int TILES_PER_WARP = (N_WTILES + kWarps - 1) / kWarps;
 };
 
-// Load W (global, [fan_out][fan_in] back to back) into the padded shared copies.
+// Load W (global, [fan_out][fan_in] back to back) into padded row-major shared copies.
+// The forward pass reads B fragments from them directly (k contiguous); the backward
+// pass needs the transposed operand and reads it with ldmatrix.trans.
 template <typename T, int N_IN, int NH>
-__device__ void load_weights(const T* __restrict__ W, int n_out, T* sm, bool transposed) {
+__device__ void load_weights(const T* __restrict__ W, int n_out, T* sm) {
   using S = Smem<N_IN, NH>;
   const T zero = from_f32<T>(0.f);
-  for (int i = threadIdx.x; i < kWidth * N_IN; i += blockDim.x) {
-    const int r = i / N_IN, c = i % N_IN;
-    const T v = W[i];
-    sm[S::W0 + r * S::SX + c] = v;
-    if (transposed) sm[S::W0T + c * kSW + r] = v;
-  }
+  for (int i = threadIdx.x; i < kWidth * N_IN; i += blockDim.x) sm[S::W0 + (i / N_IN) * S::SX + i % N_IN] = W[i];
   const T* Wh = W + kWidth * N_IN;
-  for (int h = 0; h < NH - 1; ++h) {
-    for (int i = threadIdx.x; i < kWidth * kWidth; i += blockDim.x) {
-      const int r = i / kWidth, c = i % kWidth;
-      const T v = Wh[h * kWidth * kWidth + i];
-      sm[S::WH + h * kWidth * kSW + r * kSW + c] = v;
-      if (transposed) sm[S::WHT + h * kWidth * kSW + c * kSW + r] = v;
-    }
+  for (int i = threadIdx.x; i < (NH - 1) * kWidth * kWidth; i += blockDim.x) {
+    const int h = i / (kWidth * kWidth), r = (i / kWidth) % kWidth, c = i % kWidth;
+    sm[S::WH + h * kWidth * kSW + r * kSW + c] = Wh[i];
   }
   const T* Wo = Wh + (NH - 1) * kWidth * kWidth;
   for (int i = threadIdx.x; i < 16 * kWidth; i += blockDim.x) {
     const int r = i / kWidth, c = i % kWidth;
-    const T v = r < n_out ? Wo[r * kWidth + c] : zero;
-    sm[S::WO + r * kSW + c] = v;
-    if (transposed) sm[S::WOT + c * kSO + r] = v;
+    sm[S::WO + r * kSW + c] = r < n_out ? Wo[r * kWidth + c] : zero;
   }
+}
+
+// B fragment (k16 x n8) of a row-major [k][n] shared array (n contiguous), via ldmatrix.trans.
+__device__ __forceinline__ void bfrag_kn(const void* base, int ld_halves, int kk, int nt, int lane,
+                                         uint32_t& b0, uint32_t& b1) {
+  const int q = lane >> 3, rr = lane & 7;
+  ldsm_x2_trans(b0, b1, reinterpret_cast<const __half*>(base) + (kk * 16 + (q & 1) * 8 + rr) * ld_halves + nt * 8);
 }
 
 // Stage the tile's inputs [128][N_IN] into shared memory (zero rows past P).
@@ -219,7 +214,7 @@ mlp_fwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
   using S = Smem<N_IN, NH>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  load_weights<T, N_IN, NH>(W, n_out, sm, false);
+  load_weights<T, N_IN, NH>(W, n_out, sm);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int r0 = warp * 16;
   const int64_t n_tiles = (P + kTile - 1) / kTile;
@@ -258,15 +253,19 @@ mlp_fwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
 
 // MODE 0: dy = dout * loss_scale.  MODE 1: dy = loss_scale * 2 (y - target) / (P n_out),
 // and the squared residuals are summed into *sq_sum.
+// Two CTAs per SM where the shared-memory plan allows it (then at most 128 registers).
+template <int N_IN, int NH>
+struct BwdOcc { static constexpr int value = Smem<N_IN, NH>::END * 2 <= 110 * 1024 ? 2 : 1; };
+
 template <typename T, int N_IN, int NH, int MODE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, BwdOcc<N_IN, NH>::value)
 mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
                const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
                float* __restrict__ din, float* __restrict__ ws, int64_t n_params, float* __restrict__ sq_sum) {
   using S = Smem<N_IN, NH>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  load_weights<T, N_IN, NH>(W, n_out, sm, true);
+  load_weights<T, N_IN, NH>(W, n_out, sm);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int r0 = warp * 16;
   const int64_t n_tiles = (P + kTile - 1) / kTile;
@@ -323,15 +322,15 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
 #pragma unroll
       for (int nt = 0; nt < 8; ++nt) {
         acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-        if (h == NH - 1) {
+        if (h == NH - 1) {          // dY W_out: B[k = o][n = j] = W_out[o][j]
           uint32_t b0, b1;
-          bfrag<T>(sm + S::WOT, kSO, nt, 0, g, t, b0, b1);
+          bfrag_kn(sm + S::WO, kSW, 0, nt, lane, b0, b1);
           mma16816<T>(acc[nt], afr[0], b0, b1);
-        } else {
+        } else {                    // dH_{h+1} W_{h+1}: B[k = j][n = j'] = W_{h+1}[j][j']
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             uint32_t b0, b1;
-            bfrag<T>(sm + S::WHT + h * kWidth * kSW, kSW, nt, kk, g, t, b0, b1);
+            bfrag_kn(sm + S::WH + h * kWidth * kSW, kSW, kk, nt, lane, b0, b1);
             mma16816<T>(acc[nt], afr[kk], b0, b1);
           }
         }
@@ -361,9 +360,9 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
       for (int nt = 0; nt < N_IN / 8; ++nt) {
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
+        for (int kk = 0; kk < 4; ++kk) {    // dH_0 W_0: B[k = j][n = i] = W_0[j][i]
           uint32_t b0, b1;
-          bfrag<T>(sm + S::W0T, kSW, nt, kk, g, t, b0, b1);
+          bfrag_kn(sm + S::W0, S::SX, kk, nt, lane, b0, b1);
           mma16816<T>(acc, afr[kk], b0, b1);
         }
 #pragma unroll
@@ -456,6 +455,23 @@ __global__ void reduce_partials_kernel(const float* __restrict__ ws, int nb, int
 }
 
 int g_num_sms = 0;
+int num_sms();
+
+// CTAs of the backward kernel that fit on one SM (shared memory and registers), cached.
+template <typename T, int N_IN, int NH, int MODE>
+int bwd_ctas_per_sm() {
+  static int cached = 0;
+  if (cached == 0) {
+    auto k = mlp_bwd_kernel<T, N_IN, NH, MODE>;
+    const int bytes = Smem<N_IN, NH>::END * (int)sizeof(T);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, bytes) != cudaSuccess || n < 1) n = 1;
+    cached = n;
+  }
+  return cached;
+}
+
 int num_sms() {
   if (g_num_sms == 0) {
     int dev = 0, n = 0;
@@ -539,11 +555,31 @@ sxe_status bwd_in(const sxe_mlp_desc* d, const void* W, const void* in, const fl
   }
 }
 
+template <typename T, int N_IN>
+int ctas_nh(int nh) {
+  switch (nh) {
+    case 1: return std::min(bwd_ctas_per_sm<T, N_IN, 1, 0>(), bwd_ctas_per_sm<T, N_IN, 1, 1>());
+    case 2: return std::min(bwd_ctas_per_sm<T, N_IN, 2, 0>(), bwd_ctas_per_sm<T, N_IN, 2, 1>());
+    default: return std::min(bwd_ctas_per_sm<T, N_IN, 3, 0>(), bwd_ctas_per_sm<T, N_IN, 3, 1>());
+  }
+}
+template <typename T>
+int ctas_in(const sxe_mlp_desc* d) {
+  switch (d->n_in) {
+    case 16: return ctas_nh<T, 16>(d->n_hidden);
+    case 32: return ctas_nh<T, 32>(d->n_hidden);
+    default: return ctas_nh<T, 64>(d->n_hidden);
+  }
+}
+
 }  // namespace
 
-int mlp_grid_blocks(int64_t P) {
+// Persistent grid of the backward kernel: every resident CTA slot of the device, at most
+// one CTA per tile of 128 points.
+int mlp_grid_blocks(const sxe_mlp_desc* d, int64_t P) {
   const int64_t n_tiles = (P + kTile - 1) / kTile;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, num_sms()));
+  const int per_sm = d->dtype == SXE_F16 ? ctas_in<__half>(d) : ctas_in<__nv_bfloat16>(d);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)num_sms() * per_sm));
 }
 
 sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,

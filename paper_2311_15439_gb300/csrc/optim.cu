@@ -67,38 +67,49 @@ __device__ __forceinline__ void store_lowp(void* base, int64_t e, int ldt, const
 }
 
 template <int F>
+__device__ __forceinline__ void adam_record(const AdamConst& k, float* state, int64_t e, void* lowp, int ldt) {
+  constexpr int NV = F;                            // float4 vectors per record of 4F floats
+  float4* rec = reinterpret_cast<float4*>(state + e * (4 * F));
+  union { float4 v[NV]; float f[4 * F]; } r;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) r.v[j] = rec[j];
+  float p[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    float pp = r.f[f], mm = r.f[F + f], vv = r.f[2 * F + f];
+    const float g = r.f[3 * F + f];
+    if (g != 0.f) adam_one(k, g, pp, mm, vv);
+    r.f[f] = pp; r.f[F + f] = mm; r.f[2 * F + f] = vv; r.f[3 * F + f] = 0.f;
+    p[f] = pp;
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) rec[j] = r.v[j];
+  store_lowp<F>(lowp, e, ldt, p);
+}
+
+// A warp reads 32 consecutive bitmap words at once (one per lane, coalesced), then visits
+// only the nonzero ones: for each, the 32 lanes take the word's 32 entries and the marked
+// lanes update their records.  Each lane clears the word it loaded.  Bounded grid.
+template <int F>
 __global__ void __launch_bounds__(256)
 adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state, uint32_t* __restrict__ touched,
                     void* __restrict__ lowp, int ldt) {
-  constexpr int NV = F;                            // float4 vectors per record of 4F floats
   const int lane = threadIdx.x & 31;
   const int64_t n_words = (n_entries + 31) >> 5;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = warp0; w < n_words; w += n_warps) {
-    const uint32_t bits = touched[w];              // uniform across the warp
-    if (bits == 0u) continue;
-    const int64_t e = (w << 5) + lane;
-    if (((bits >> lane) & 1u) && e < n_entries) {
-      float4* rec = reinterpret_cast<float4*>(state + e * (4 * F));
-      union { float4 v[NV]; float f[4 * F]; } r;
-#pragma unroll
-      for (int j = 0; j < NV; ++j) r.v[j] = rec[j];
-      float p[F];
-#pragma unroll
-      for (int f = 0; f < F; ++f) {
-        float pp = r.f[f], mm = r.f[F + f], vv = r.f[2 * F + f];
-        const float g = r.f[3 * F + f];
-        if (g != 0.f) adam_one(k, g, pp, mm, vv);
-        r.f[f] = pp; r.f[F + f] = mm; r.f[2 * F + f] = vv; r.f[3 * F + f] = 0.f;
-        p[f] = pp;
-      }
-#pragma unroll
-      for (int j = 0; j < NV; ++j) rec[j] = r.v[j];
-      store_lowp<F>(lowp, e, ldt, p);
+  for (int64_t w0 = warp0 << 5; w0 < n_words; w0 += n_warps << 5) {
+    const int64_t wi = w0 + lane;
+    const uint32_t mine = wi < n_words ? touched[wi] : 0u;
+    uint32_t todo = __ballot_sync(0xffffffffu, mine != 0u);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1u;
+      const uint32_t bits = __shfl_sync(0xffffffffu, mine, src);
+      const int64_t e = ((w0 + src) << 5) + lane;
+      if (((bits >> lane) & 1u) && e < n_entries) adam_record<F>(k, state, e, lowp, ldt);
     }
-    __syncwarp();
-    if (lane == 0) touched[w] = 0u;
+    if (mine) touched[wi] = 0u;
   }
 }
 
@@ -138,7 +149,12 @@ sxe_status launch_adam_dense(const sxe_adam_desc* a, int64_t t, int64_t n, float
 sxe_status launch_adam_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries, int32_t F, float* state,
                                uint32_t* touched, void* lowp, int32_t ldt, cudaStream_t s) {
   const AdamConst k = make_const(a, t);
-  const unsigned nb = blocks_for(((n_entries + 31) >> 5) * 32, 256, 1u << 20);
+  // one warp per 32 bitmap words, at most 16 blocks of 8 warps per SM
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t chunks = (((n_entries + 31) >> 5) + 31) >> 5;
+  const unsigned nb = blocks_for(chunks * 32, 256, (unsigned)(16 * sms));
   switch (F) {
     case 1: adam_touched_kernel<1><<<nb, 256, 0, s>>>(k, n_entries, state, touched, lowp, ldt); break;
     case 2: adam_touched_kernel<2><<<nb, 256, 0, s>>>(k, n_entries, state, touched, lowp, ldt); break;

@@ -51,7 +51,7 @@ sxe_status launch_encode_plain(const sxe_encoder* enc, bool backward, const floa
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,
                                   float* weights, cudaStream_t s);
 
-int mlp_grid_blocks(int64_t P);
+int mlp_grid_blocks(const sxe_mlp_desc* d, int64_t P);
 sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out,
                           void* act, cudaStream_t s);
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,

@@ -183,3 +183,26 @@ def test_out_of_domain_points_stay_in_bounds(cuda_lib):
     for l in range(8):
         ref, _, _ = O.simplex_level_vertices(x[[0, 1, 3]], scales[l], 12)
         assert np.array_equal(s[[0, 1, 3], l, :].astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_plain_path_matches_oracle(cuda_lib, d):
+    """The plain binary32 comparator path (bubble sort, scalar loads and atomics) computes the
+    same encoding and table gradient as the oracle."""
+    from paper_2311_15439_gb300.api import Encoder
+    L, log2_T = 8, 14
+    enc = Encoder(d, L, 2, log2_T, 16.0, 1.5, table_dtype="f32")
+    vals = synth.uniform_tables(L, 1 << log2_T, 2, 20 + d, scale=1e-4)[0]
+    x = _points(d, 3000, 30 + d)
+    xd = torch.from_numpy(x).cuda()
+    out = enc.encode_plain_fwd(xd, torch.from_numpy(vals).cuda()).cpu().numpy()
+    ref, den = O.simplex_encode(x, vals, base_res=16.0, growth=1.5, with_denominator=True)
+    assert rel_err(out, ref, den) <= 1e-5
+    dout = synth.normal_grads(len(x), L * 2, 40 + d)
+    grad = torch.zeros((L, 1 << log2_T, 2), device="cuda")
+    enc.encode_plain_bwd(xd, torch.from_numpy(dout).cuda(), grad)
+    gref, gden = O.simplex_encode_bwd(x, dout, n_levels=L, log2_T=log2_T, n_features=2, base_res=16.0,
+                                      growth=1.5, with_denominator=True)
+    g = grad.cpu().numpy()
+    for l in range(L):
+        assert rel_err(g[l], gref[l], gden[l]) <= 1e-5

@@ -41,20 +41,42 @@ def _dens(Ws, x, dy):
     return h[-1], dW, d
 
 
-def ambiguous_rows(Ws, x, tol):
-    """Points for which some hidden pre-activation lies within the rounding band of zero
-    (|z| <= tol * its magnitude bound): there the ReLU decision, and the backward pass below
-    it, may legitimately come out either way at the kernel's precision."""
+def flip_slack(Ws, x, dy, u):
+    """Extra error the backward pass may show where a ReLU decision is ambiguous at the
+    kernel's precision.  The kernel feeds each layer the previous activations rounded once
+    to the operand type (unit roundoff u; exact inputs for the first layer), so a
+    pre-activation z can differ from the oracle's by up to 2 u sum_i |h_i W_ji| (+ binary32
+    accumulation); if |z| is inside that band the unit's mask may differ, which changes its
+    delta by at most the full unmasked term |d_pre_j|.  Returns (dW slack list, din slack),
+    propagated through |W| like the magnitude bounds; rows with no ambiguous unit get zero."""
     h = np.asarray(x, dtype=np.float64)
-    habs = np.abs(h)
-    amb = np.zeros(len(h), dtype=bool)
-    for W in Ws[:-1]:
+    habs = [np.abs(h)]
+    amb = []
+    for i, W in enumerate(Ws[:-1]):
         z = h @ W.T
-        zden = habs @ np.abs(W).T
-        amb |= np.any(np.abs(z) <= tol * zden, axis=1)
+        band = ((2.0 * u if i > 0 else 0.0) + 64 * 2.0 ** -24) * (np.abs(h) @ np.abs(W).T)
+        amb.append(np.abs(z) <= band)
         h = np.maximum(z, 0.0)
-        habs = zden
-    return amb
+        habs.append(habs[-1] @ np.abs(W).T)
+    d = np.abs(dy)
+    slack = np.zeros_like(d)
+    dW_slack = [None] * len(Ws)
+    for i in reversed(range(len(Ws))):
+        dW_slack[i] = slack.T @ habs[i]
+        d_pre = d @ np.abs(Ws[i])
+        s_pre = slack @ np.abs(Ws[i])
+        if i > 0:
+            slack = s_pre + d_pre * amb[i - 1]
+            d = d_pre
+        else:
+            return dW_slack, s_pre
+
+
+def within(got, want, den, tol, slack=0.0):
+    """max |got - want| / (tol den + slack); <= 1 means inside the bound everywhere."""
+    bound = tol * np.asarray(den, dtype=np.float64) + slack
+    err = np.abs(np.asarray(got, dtype=np.float64) - np.asarray(want, dtype=np.float64))
+    return float(np.max(err / np.maximum(bound, 1e-300)))
 
 
 # (n_in, n_hidden, n_out, dtype, P)
@@ -99,13 +121,12 @@ def test_backward(cuda_lib, net):
     _, acts = OM.mlp_forward(Ws, x)
     dW_ref, din_ref = OM.mlp_backward(Ws, acts, dy)
     _, dW_den, din_den = _dens(Ws, x, dy)
+    dW_sl, din_sl = flip_slack(Ws, x, dy, U[dt])
     tol = (2 * nh + 2) * U[dt]
     got = mlp.split(dW.cpu().numpy())
     for i in range(len(Ws)):
-        assert rel_err(got[i], dW_ref[i], dW_den[i]) <= tol, "layer %d" % i
-    amb = ambiguous_rows(Ws, x, tol)
-    assert amb.mean() < 0.05
-    assert rel_err(din.cpu().numpy()[~amb], din_ref[~amb], din_den[~amb]) <= tol
+        assert within(got[i], dW_ref[i], dW_den[i], tol, dW_sl[i]) <= 1.0, "layer %d" % i
+    assert within(din.cpu().numpy(), din_ref, din_den, tol, din_sl) <= 1.0
 
 
 def test_backward_accumulates_and_is_deterministic(cuda_lib):
@@ -141,13 +162,12 @@ def test_train_l2(cuda_lib, net):
     # |dy| is bounded by 2 (|y| + |t|) / (P n_out); the squared residual's error by 3 tol (|y| + |t|)^2
     dy_bound = 2.0 * (yden + np.abs(tgt)) / dy.size
     _, dW_den, din_den = _dens(Ws, x, dy_bound)
+    dW_sl, din_sl = flip_slack(Ws, x, dy_bound, U[dt])
     assert abs(sq.item() / (P * n_out) - loss) <= 3 * tol * np.mean((yden + np.abs(tgt)) ** 2)
     got = mlp.split(dW.cpu().numpy())
     for i in range(len(Ws)):
-        assert rel_err(got[i], dW_ref[i], dW_den[i]) <= tol, "layer %d" % i
-    amb = ambiguous_rows(Ws, x, tol)
-    assert amb.mean() < 0.05
-    assert rel_err(din.cpu().numpy()[~amb], din_ref[~amb], din_den[~amb]) <= tol
+        assert within(got[i], dW_ref[i], dW_den[i], tol, dW_sl[i]) <= 1.0, "layer %d" % i
+    assert within(din.cpu().numpy(), din_ref, din_den, tol, din_sl) <= 1.0
 
 
 def test_loss_kernel(cuda_lib):

@@ -1,0 +1,95 @@
+"""Serving loop: answers equal the kernels' answers alone and in the mix, memory admission
+holds, bad requests fail alone, and values match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import encoding as OE
+from oracle import mlp as OM
+from paper_2311_15439_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields(log2_T=14):
+    from paper_2311_15439_gb300.serve import make_field
+    return {d: make_field(d, log2_T=log2_T, seed=10 + d) for d in (2, 3, 4, 5)}
+
+
+def _alone(f, x):
+    enc = f.encoder.encode_fwd(x.cuda(), f.tables)
+    return f.mlp.mlp_fwd(f.weights, enc).cpu()
+
+
+def test_alone_equals_mixed(cuda_lib):
+    """Each request's values are bitwise the same when merged with others (continuous batching
+    over 4 stream slots) as when computed alone."""
+    from paper_2311_15439_gb300.serve import FieldServer
+    fields = _fields()
+    g = synth.rng(1)
+    reqs_in = []
+    for i in range(40):
+        d = int(g.choice([2, 3, 4, 5]))
+        P = int(np.exp(g.uniform(np.log(100), np.log(70000))))
+        reqs_in.append((d, torch.from_numpy(synth.uniform_points(P, d, 100 + i)).pin_memory()))
+    srv = FieldServer(fields, mem_budget_bytes=64 << 20, n_slots=4, max_batch_points=1 << 18).start()
+    reqs = [srv.submit(d, x) for d, x in reqs_in]
+    for r in reqs:
+        assert r.wait(60)
+    srv.stop()
+    assert srv.n_batches < len(reqs)                     # requests were merged
+    for (d, x), r in zip(reqs_in, reqs):
+        assert r.error is None
+        assert torch.equal(r.y, _alone(fields[d], x))
+
+
+def test_memory_admission_and_rejections(cuda_lib):
+    """With a budget that fits about one request, requests wait instead of overcommitting;
+    malformed, unknown-dimension and oversize requests fail without disturbing the rest."""
+    from paper_2311_15439_gb300.serve import FieldServer
+    fields = _fields()
+    budget = 40000 * fields[2].bytes_per_point() + 1024
+    srv = FieldServer(fields, mem_budget_bytes=budget, n_slots=3, max_batch_points=1 << 16).start()
+    good = [(2, torch.from_numpy(synth.uniform_points(30000, 2, i)).pin_memory()) for i in range(6)]
+    bad = [(7, torch.zeros((10, 7)).pin_memory()),                      # no field of that dimension
+           (3, torch.zeros((10, 2)).pin_memory()),                      # wrong width
+           (2, torch.from_numpy(synth.uniform_points(100000, 2, 9)).pin_memory())]   # over the budget
+    reqs = []
+    for i, (d, x) in enumerate(good):
+        reqs.append(srv.submit(d, x))
+        if i < len(bad):
+            reqs.append(srv.submit(*bad[i]))
+    for r in reqs:
+        assert r.wait(60)
+    srv.stop()
+    assert srv.peak_used <= budget
+    errs = [r for r in reqs if r.error is not None]
+    assert len(errs) == len(bad)
+    for r in reqs:
+        if r.error is None:
+            assert torch.equal(r.y, _alone(fields[r.d], r.x))
+
+
+@pytest.mark.parametrize("d", [2, 5])
+def test_served_values_match_oracle(cuda_lib, d):
+    """Served values equal the FP64 oracle's encoding + network on the same fp16 tables and
+    weights (encoding rounded to fp16 as the network reads it), within the network bound."""
+    from paper_2311_15439_gb300.serve import FieldServer
+    from test_gpu_mlp import _dens
+    f = _fields()[d]
+    x = synth.uniform_points(5000, d, 3)
+    srv = FieldServer({d: f}).start()
+    r = srv.submit(d, torch.from_numpy(x).pin_memory())
+    assert r.wait(60)
+    srv.stop()
+    tables = f.tables.float().cpu().numpy()
+    enc = OE.simplex_encode(x, tables, base_res=16.0, growth=1.38)
+    enc16 = enc.astype(np.float16).astype(np.float64)
+    Ws = [w.astype(np.float64) for w in f.mlp.split(f.weights.float().cpu().numpy())]
+    y, _ = OM.mlp_forward(Ws, enc16)
+    yden, _, _ = _dens(Ws, enc16, np.zeros_like(y))
+    tol = 6 * 2.0 ** -11
+    # forward only: a ReLU decision flipped by rounding changes a value by no more than the
+    # rounding itself, so the forward bound needs no slack
+    err = np.abs(r.y.numpy().astype(np.float64) - y)
+    assert np.all(err <= tol * yden)
