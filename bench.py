@@ -292,6 +292,7 @@ def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5):
     import torch
     from paper_2311_15439_gb300 import synth
     from paper_2311_15439_gb300.serve import FieldServer, make_field, poisson_load, run_load
+    sys.setswitchinterval(2e-4)          # let the scheduler thread take the GIL promptly
     arrivals, ds, sizes = poisson_load(rate_hz, n_requests, (2, 3, 4, 5), 4096, 4 << 20, seed)
     pools = {d: torch.from_numpy(synth.uniform_points(4 << 20, d, 900 + d)).pin_memory() for d in (2, 3, 4, 5)}
     out = {"load": "%d Poisson requests at %.0f/s, sizes log-uniform 4K..4M points, d in {2,3,4,5}" % (n_requests, rate_hz)}
@@ -300,7 +301,8 @@ def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5):
         srv = FieldServer(fields, mem_budget_bytes=4 << 30, n_slots=4, max_batch_points=4 << 20, device=dev).start()
         # warm-up: one request per d (allocator, pinned buffers, kernel load)
         for d in (2, 3, 4, 5):
-            srv.submit(d, pools[d][:65536]).wait()
+            if not srv.submit(d, pools[d][:65536]).wait(120.0):
+                raise TimeoutError("serving warm-up request did not complete")
         reqs, wall = run_load(srv, arrivals, ds, sizes, pools, seed)
         srv.stop()
         lat = np.array([r.latency for r in reqs]) * 1e3

@@ -98,18 +98,20 @@ encode_fwd_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__
   }
 }
 
+// Levels [l0, l0 + nl) of every point; work item i = p * nl + (l - l0).
 template <bool SIMPLEX, int D, int F>
 __global__ void __launch_bounds__(kThreads)
 encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restrict__ dout,
                   float* __restrict__ grad, int64_t stride, uint32_t* __restrict__ touched,
-                  const EncParams prm) {
+                  const EncParams prm, int l0, int nl) {
   constexpr int V = Verts<SIMPLEX, D>::V;
   __shared__ float s_scale[SXE_MAX_LEVELS];
   if (threadIdx.x < SXE_MAX_LEVELS) s_scale[threadIdx.x] = prm.scale[threadIdx.x];
   __syncthreads();
   const int L = prm.n_levels;
-  const Item it = item_of(L);
+  Item it = item_of(nl);
   if (it.p >= P) return;
+  it.l += l0;
   float xv[D];
   load_point<D>(x, it.p, xv);
   const uint32_t mask = (1u << prm.log2_T) - 1u;
@@ -117,11 +119,6 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
   float w[V];
   lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
   const int64_t lbase = (int64_t)it.l << prm.log2_T;
-  // Pull the gradient entries into L2 through the load path before the atomics reach them:
-  // atomics that miss L2 are processed far more slowly than plain-load misses.
-#pragma unroll
-  for (int k = 0; k < V; ++k)
-    asm volatile("prefetch.global.L2 [%0];" :: "l"(grad + (lbase + slot[k]) * stride));
   float g[F];
   const float* pd = dout + (it.p * L + it.l) * F;
   if constexpr (F == 2) {
@@ -203,30 +200,30 @@ sxe_status fwd_d(const sxe_encoder* e, const float* x, int64_t P, const void* t,
 
 template <bool SIMPLEX, int D, int F>
 sxe_status bwd_f(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                 uint32_t* touched, cudaStream_t s) {
-  encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, e->prm.n_levels), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm);
+                 uint32_t* touched, int l0, int nl, cudaStream_t s) {
+  encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, nl), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm, l0, nl);
   return check_launch("encode_bwd");
 }
 
 template <bool SIMPLEX, int D>
 sxe_status bwd_fd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                  uint32_t* t, cudaStream_t s) {
+                  uint32_t* t, int l0, int nl, cudaStream_t s) {
   switch (e->desc.n_features) {
-    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, s);
-    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, s);
-    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, s);
-    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, s);
+    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, l0, nl, s);
+    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, l0, nl, s);
+    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, l0, nl, s);
+    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, l0, nl, s);
   }
 }
 
 template <bool SIMPLEX>
 sxe_status bwd_d(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                 uint32_t* t, cudaStream_t s) {
+                 uint32_t* t, int l0, int nl, cudaStream_t s) {
   switch (e->desc.d) {
-    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, s);
-    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, s);
-    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, s);
-    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, s);
+    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, l0, nl, s);
+    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, l0, nl, s);
+    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, l0, nl, s);
+    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, l0, nl, s);
   }
 }
 
@@ -251,9 +248,10 @@ sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, 
 }
 
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout, float* grad,
-                             int64_t stride, uint32_t* touched, cudaStream_t s) {
-  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, s)
-                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, s);
+                             int64_t stride, uint32_t* touched, cudaStream_t s, int l0, int nl) {
+  if (nl < 0) nl = enc->prm.n_levels - l0;
+  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, l0, nl, s)
+                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, l0, nl, s);
 }
 
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,

@@ -12,7 +12,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
-#include "../../include/simplexenc.h"
+#include "simplexenc.h"
 
 namespace sxe {
 
@@ -45,7 +45,8 @@ sxe_status check_launch(const char* what);
 sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
                              void* out, cudaStream_t s);
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
-                             float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s);
+                             float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s,
+                             int level_begin = 0, int n_levels = -1);
 sxe_status launch_encode_plain(const sxe_encoder* enc, bool backward, const float* x, int64_t P, const float* a,
                                float* b, cudaStream_t s);
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,

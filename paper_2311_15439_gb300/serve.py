@@ -46,7 +46,7 @@ class Field:
         return 4 * self.encoder.d + 2 * self.encoder.n_out + 4 * self.mlp.n_out
 
 
-@dataclass
+@dataclass(eq=False)          # identity equality: requests are removed from queues by identity
 class Request:
     d: int
     x: torch.Tensor                        # [P, d] float32, pinned host memory
@@ -93,6 +93,7 @@ class FieldServer:
         self.n_batches = 0
         self.n_launch_kernels = 0
         self.peak_used = 0
+        self.failure = None
         self._next_id = 0
 
     # ---- client side --------------------------------------------------------------
@@ -115,7 +116,7 @@ class FieldServer:
 
     def stop(self, drain: bool = True):
         if drain:
-            while True:
+            while self.thread is not None and self.thread.is_alive():
                 with self.lock:
                     if not self.queue and not self.inflight:
                         break
@@ -204,6 +205,19 @@ class FieldServer:
         self.inflight.append(_Batch(group, slot, need, (x, enc, y), ev))
 
     def _loop(self):
+        try:
+            self._serve()
+        except BaseException as exc:           # never leave a client waiting on a dead scheduler
+            with self.lock:
+                pending = list(self.queue) + [r for b in self.inflight for r in b.reqs]
+                self.queue.clear()
+                self.inflight.clear()
+            for r in pending:
+                if not r.done.is_set():
+                    self._reject(r, "scheduler failed: %r" % (exc,))
+            self.failure = exc
+
+    def _serve(self):
         while self.running or self.queue or self.inflight:
             progressed = False
             with self.lock:
@@ -254,9 +268,13 @@ def run_load(server: FieldServer, arrivals, ds, sizes, host_points: dict[int, to
     for t, d, P in zip(arrivals, ds, sizes):
         src = host_points[int(d)]
         o = int(g.integers(0, src.shape[0] - P + 1))
-        while time.perf_counter() - t0 < t:
-            pass
+        while True:                                     # sleep (releasing the GIL) until just before t
+            ahead = t - (time.perf_counter() - t0)
+            if ahead <= 0:
+                break
+            time.sleep(ahead - 5e-5 if ahead > 1e-4 else 0)
         reqs.append(server.submit(int(d), src[o:o + int(P)]))
     for r in reqs:
-        r.wait()
+        if not r.wait(120.0):
+            raise TimeoutError("request %d (%d points, d=%d) did not complete" % (r.rid, r.n_points, r.d))
     return reqs, time.perf_counter() - t0

@@ -41,20 +41,24 @@ def _dens(Ws, x, dy):
     return h[-1], dW, d
 
 
-def flip_slack(Ws, x, dy, u):
+def flip_slack(Ws, x, dy, u, x_err=0.0):
     """Extra error the backward pass may show where a ReLU decision is ambiguous at the
     kernel's precision.  The kernel feeds each layer the previous activations rounded once
     to the operand type (unit roundoff u; exact inputs for the first layer), so a
     pre-activation z can differ from the oracle's by up to 2 u sum_i |h_i W_ji| (+ binary32
     accumulation); if |z| is inside that band the unit's mask may differ, which changes its
-    delta by at most the full unmasked term |d_pre_j|.  Returns (dW slack list, din slack),
-    propagated through |W| like the magnitude bounds; rows with no ambiguous unit get zero."""
+    delta by at most the full unmasked term |d_pre_j|.  ``x_err`` bounds how far the kernel's
+    inputs may differ from ``x`` (zero when both read the same values).  Returns (dW slack
+    list, din slack), propagated through |W| like the magnitude bounds; rows with no ambiguous
+    unit get zero."""
     h = np.asarray(x, dtype=np.float64)
     habs = [np.abs(h)]
     amb = []
     for i, W in enumerate(Ws[:-1]):
         z = h @ W.T
         band = ((2.0 * u if i > 0 else 0.0) + 64 * 2.0 ** -24) * (np.abs(h) @ np.abs(W).T)
+        if i == 0:
+            band = band + np.broadcast_to(np.asarray(x_err, dtype=np.float64), h.shape) @ np.abs(W).T
         amb.append(np.abs(z) <= band)
         h = np.maximum(z, 0.0)
         habs.append(habs[-1] @ np.abs(W).T)
