@@ -41,6 +41,16 @@ def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def _tensor_peak():
+    """Dense fp16 tensor peak for a kernel timed inside a long step: the measured sustained
+    bf16 figure (fp16 and bf16 run at the same dense rate)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"])
+    except Exception:
+        return 1700.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -111,14 +121,27 @@ def make_batches(n, seed0=1000):
     return xs, ts
 
 
-def _kernel_bytes(F=2, L=16, d=2):
-    """Algorithmic bytes per point of each launch of the step (stated in the design notes)."""
+def _stage_work(n_touched, F=2, L=16, d=2, width=64, n_in=32):
+    """Algorithmic work of each timed stage of one step (stated in the design notes):
+    bytes for the memory-bound stages, FLOPs for the network."""
     V = d + 1
-    return {
-        "encode_fwd": 4 * d + L * V * 2 * F + L * F * 2,              # x, fp16 gathers, fp16 encoding
-        "mlp_train_l2": L * F * 2 + 4 * N_OUT + 4 * L * F,            # encoding, target, dL/d(encoding)
-        "encode_bwd": 4 * d + 4 * L * F + L * V * 2 * 4 * F,          # x, dL/d(enc), fp32 RMW per vertex
-    }
+    per_pt_fwd = 4 * d + L * V * 2 * F + L * F * 2                 # x, fp16 gathers, fp16 encoding
+    table = BATCH * (4 * d + 4 * L * F) + n_touched * (2 * 16 * F)  # x, dL/d(enc); record read + write
+    flops = 2 * (n_in * width + width * width + width * 16)       # forward MACs (output padded to 16)
+    flops = 3 * flops * BATCH                                     # forward + delta + weight-gradient GEMMs
+    return {"encode_fwd": ("hbm", per_pt_fwd * BATCH), "table_step": ("hbm", table),
+            "mlp_train_l2": ("tensor", flops)}
+
+
+def count_touched(tr, x):
+    """Entries that one batch touches (for the table stage's algorithmic bytes)."""
+    import torch
+    enc = tr.enc
+    dense = torch.zeros(enc.table_shape(), dtype=torch.float32, device=x.device)
+    bm = torch.zeros_like(tr.touched)
+    enc.encode_bwd(x, torch.ones((x.shape[0], enc.n_out), device=x.device), dense, touched=bm)
+    bits = bm.cpu().numpy().view(np.uint32)
+    return int(np.unpackbits(bits.view(np.uint8)).sum())
 
 
 def run_gpu(args):
@@ -151,10 +174,9 @@ def run_gpu(args):
         tr.step(xd[i % N_POOL], td[i % N_POOL])
     torch.cuda.synchronize(dev)
 
-    # ---- device-timed region: K steps, per-kernel events on the launching stream
-    names = ["encode_fwd", "mlp_train_l2", "encode_bwd", "adam_tables", "adam_mlp"]
+    # ---- device-timed region: K steps, per-stage events on the launching stream
+    names = ["encode_fwd", "mlp_train_l2", "table_step", "adam_mlp"]
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
-    F = enc.n_features
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         if world > 1:
@@ -166,17 +188,15 @@ def run_gpu(args):
             e = ev[k]
             tr.t += 1
             e[0].record(stream)
-            tr.enc.encode_fwd(x, tr.tables, tr.enc_out)
+            tr.enc.encode_fwd_records(x, tr.state, tr.enc_out)
             e[1].record(stream)
             tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, t, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
                                 workspace=tr.ws)
             e[2].record(stream)
-            tr.enc.encode_bwd(x, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
+            tr.enc.table_step(tr.adam_tables, tr.t, x, tr.d_enc, tr.state, tr.scratch, tr.touched)
             e[3].record(stream)
-            tr.adam_tables.step_touched(tr.t, tr.state, tr.touched, tr.tables, F)
-            e[4].record(stream)
             tr.adam_mlp.step(tr.t, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
-            e[5].record(stream)
+            e[4].record(stream)
         stop.record(stream)
         torch.cuda.synchronize(dev)
         if world > 1:
@@ -189,6 +209,7 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     loss = tr.loss()
+    n_touched = count_touched(tr, xd[0])
 
     # ---- end to end through the public API: pinned host batch -> device, step, loss -> host
     hx = [torch.from_numpy(x).pin_memory() for x in xs]
@@ -220,23 +241,29 @@ def run_gpu(args):
 
     if rank == 0:
         value = BATCH * args.steps * world / (ms / 1e3)
-        dom = max(("encode_fwd", "mlp_train_l2", "encode_bwd"), key=lambda n: per_kernel[n])
-        kb = _kernel_bytes()
-        peak, peak_src = _peaks()
-        achieved = kb[dom] * BATCH / (per_kernel[dom] / 1e3) / 1e9
+        work = _stage_work(n_touched)
+        dom = max(work, key=lambda n: per_kernel[n])
+        bound, amount = work[dom]
+        hbm_peak, peak_src = _peaks()
+        if bound == "hbm":
+            achieved = amount / (per_kernel[dom] / 1e3) / 1e9
+            peak, unit = hbm_peak, "GB/s"
+        else:
+            achieved = amount / (per_kernel[dom] / 1e3) / 1e12
+            peak, unit = _tensor_peak(), "TFLOP/s"
         line = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "kind": args.kind, "global_batch": BATCH * world,
                        "points_per_step_per_gpu": BATCH, "parallelism": "replicas (one per GPU)",
-                       "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state, no flush",
+                       "l2": "working set > L2: 2 GiB fp32 table state records (fp16 copies inside), no flush",
                        "batches": "%d resident distinct batches cycled" % N_POOL},
             "e2e": {"value": BATCH * e2e_steps * world / (ms_e2e / 1e3), "unit": "points/s",
                     "h2d_bytes_per_step": BATCH * (2 + N_OUT) * 4, "d2h_bytes_per_step": 4},
-            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                         "bytes_per_point": kb[dom]},
+                         "work_per_step": amount, "touched_entries_per_step": n_touched},
             "per_kernel_ms": per_kernel,
             "gpu_launches": args.steps * tr.n_launches_per_step,
             "clocks": clk.summary(),
@@ -282,6 +309,18 @@ def encode_sweep(dev, reps=20):
             e.record()
             torch.cuda.synchronize(dev)
             row["%s_%s" % (kind, tdt)] = P * reps / (s.elapsed_time(e) / 1e3)
+            if kind == "simplex" and tdt == "f32":       # the plain binary32 path on the same tables
+                for _ in range(2):
+                    enc.encode_plain_fwd(x, tab, o)
+                    enc.encode_plain_bwd(x, dout, grad)
+                torch.cuda.synchronize(dev)
+                s.record()
+                for _ in range(reps):
+                    enc.encode_plain_fwd(x, tab, o)
+                    enc.encode_plain_bwd(x, dout, grad)
+                e.record()
+                torch.cuda.synchronize(dev)
+                row["simplex_plain_f32"] = P * reps / (s.elapsed_time(e) / 1e3)
         out["d%d" % d] = row
     return {"encode_fwd_bwd_points_per_s": out, "config": "L=16 F=2 T=2^19 base 16 growth 1.38, 2^20 points"}
 

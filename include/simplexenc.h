@@ -108,6 +108,15 @@ sxe_status sxe_encoder_level_params(const sxe_encoder* enc, float* level_scale, 
 sxe_status sxe_encode_fwd(const sxe_encoder* enc, const float* x, int64_t n_points,
                           const void* tables, void* out, void* stream);
 
+/* sxe_encode_fwd reading the tables with an entry stride: entry (l, slot) starts at
+ * element (l*T + slot) * table_stride of `tables` (desc.table_dtype).  table_stride = F
+ * is the dense layout; sxe_table_step's state records are read with table_stride =
+ * 4F binary32 words (8F elements of a 16-bit type) from the start of their copy field.
+ * table_stride * element size must keep every entry aligned to min(16, F * element
+ * size) bytes. */
+sxe_status sxe_encode_fwd_strided(const sxe_encoder* enc, const float* x, int64_t n_points,
+                                  const void* tables, int64_t table_stride, void* out, void* stream);
+
 /* Backward encoding, Sec. 5 step (e): for every point, level, vertex k and feature f,
  *   grad[(l*T + slot_k) * grad_stride + f] += w_k * dout[p][l*F + f]
  * with the same vertices and weights as the forward pass (recomputed).
@@ -243,6 +252,25 @@ sxe_status sxe_step(const sxe_adam_desc* desc, int64_t t, int64_t n, float* para
 sxe_status sxe_step_touched(const sxe_adam_desc* desc, int64_t t, int64_t n_entries,
                             int32_t n_features, float* state, uint32_t* touched,
                             void* table_lowp, int32_t lowp_dtype, void* stream);
+
+/* Table update of one training step, Sec. 5 (e) followed by Adam, processed one level at
+ * a time: for each level l, every point's vertices add w_k * dout[p][l*F + f] into a
+ * dense binary32 scratch [T][F] and mark the entries they touch; then every marked
+ * entry takes the Adam step of sxe_step with the zero-gradient skip rule (per
+ * parameter), refreshes its low-precision copy, and its scratch gradient and bit are
+ * cleared.  The result equals sxe_encode_bwd into a zeroed gradient followed by the
+ * skip-rule Adam step of every table parameter; the scratch (T*F*4 bytes, reused by
+ * every level) stays resident in L2.
+ *   state    L*T records of 4F binary32 words each: [0,F) parameter, [F,2F) first
+ *            moment, [2F,3F) second moment, [3F,4F) the desc.table_dtype copy of the
+ *            parameter packed from its start (rest zero).  16-byte aligned.
+ *   scratch  [T][F] binary32, all zero on entry; zero again on return.
+ *   touched  L*T bits (uint32 words), all zero on entry; zero again on return.
+ *   dout     [n_points][L*F] binary32 dL/d(encoding).
+ * Needs T >= 32.  Launches 2*L kernels on `stream`. */
+sxe_status sxe_table_step(const sxe_encoder* enc, const sxe_adam_desc* adam, int64_t t,
+                          const float* x, int64_t n_points, const float* dout,
+                          float* state, float* scratch, uint32_t* touched, void* stream);
 
 /* Thread-local message describing the last failing call on this thread ("" if none). */
 const char* sxe_last_error(void);

@@ -98,6 +98,32 @@ class Encoder:
                 "sxe_encode_fwd")
         return out
 
+    def encode_fwd_records(self, x: torch.Tensor, state: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """Forward encoding reading the low-precision copies inside ``sxe_table_step`` records
+        (``sxe_encode_fwd_strided`` with entry stride 4F binary32 words)."""
+        P, F = x.shape[0], self.n_features
+        _need(x, torch.float32, "x", (P, self.d))
+        _need(state, torch.float32, "state", (self.n_levels * self.T, 4 * F))
+        if out is None:
+            out = torch.empty((P, self.n_out), dtype=torch_dtype(self.out_dtype), device=x.device)
+        _need(out, torch_dtype(self.out_dtype), "out", (P, self.n_out))
+        esize = torch.empty((), dtype=torch_dtype(self.table_dtype)).element_size()
+        L.check(L.lib().sxe_encode_fwd_strided(self._h, _ptr(x), P, state.data_ptr() + 12 * F, 16 * F // esize,
+                                               _ptr(out), _stream(stream)), "sxe_encode_fwd_strided")
+        return out
+
+    def table_step(self, adam: "Adam", t: int, x: torch.Tensor, dout: torch.Tensor, state: torch.Tensor,
+                   scratch: torch.Tensor, touched: torch.Tensor, stream=None):
+        """Level-by-level table backward + Adam (``sxe_table_step``)."""
+        P, F = x.shape[0], self.n_features
+        _need(x, torch.float32, "x", (P, self.d))
+        _need(dout, torch.float32, "dout", (P, self.n_out))
+        _need(state, torch.float32, "state", (self.n_levels * self.T, 4 * F))
+        _need(scratch, torch.float32, "scratch", (self.T, F))
+        _need(touched, torch.int32, "touched", ((self.n_levels * self.T + 31) // 32,))
+        L.check(L.lib().sxe_table_step(self._h, ctypes.byref(adam.desc), int(t), _ptr(x), P, _ptr(dout), _ptr(state),
+                                       _ptr(scratch), _ptr(touched), _stream(stream)), "sxe_table_step")
+
     def encode_bwd(self, x: torch.Tensor, dout: torch.Tensor, grad: torch.Tensor, grad_stride: int | None = None,
                    touched: torch.Tensor | None = None, grad_offset: int = 0, stream=None):
         """grad += d(out)/d(tables)^T dout.  ``grad`` is a float32 tensor; entry (l, slot) starts at

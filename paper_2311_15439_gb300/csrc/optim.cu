@@ -16,28 +16,6 @@
 namespace sxe {
 namespace {
 
-struct AdamConst {
-  float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
-  int skip;
-};
-
-AdamConst make_const(const sxe_adam_desc* a, int64_t t) {
-  AdamConst k;
-  k.lr = a->lr; k.b1 = a->beta1; k.b2 = a->beta2; k.eps = a->eps;
-  k.c1 = (float)(1.0 / (1.0 - std::pow((double)a->beta1, (double)t)));
-  k.c2 = (float)(1.0 / (1.0 - std::pow((double)a->beta2, (double)t)));
-  k.skip = a->skip_zero_grad;
-  return k;
-}
-
-__device__ __forceinline__ void adam_one(const AdamConst& k, float g, float& p, float& m, float& v) {
-  m = fmaf(k.b1, m, (1.f - k.b1) * g);
-  v = fmaf(k.b2, v, (1.f - k.b2) * g * g);
-  const float mh = m * k.c1;
-  const float vh = v * k.c2;
-  p = p - k.lr * mh / (sqrtf(vh) + k.eps);
-}
-
 __global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p, float* __restrict__ m,
                                   float* __restrict__ v, float* __restrict__ g, void* __restrict__ lowp, int ldt) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -50,19 +28,6 @@ __global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p,
       g[i] = 0.f;
     }
     if (lowp) store_as(lowp, i, ldt, pi);
-  }
-}
-
-// Low-precision copy of F consecutive parameters in one store where the type allows.
-template <int F>
-__device__ __forceinline__ void store_lowp(void* base, int64_t e, int ldt, const float (&p)[F]) {
-  if (F == 2 && ldt == SXE_F16) {
-    reinterpret_cast<__half2*>(base)[e] = __floats2half2_rn(p[0], p[1]);
-  } else if (F == 2 && ldt == SXE_BF16) {
-    reinterpret_cast<__nv_bfloat162*>(base)[e] = __floats2bfloat162_rn(p[0], p[1]);
-  } else {
-#pragma unroll
-    for (int f = 0; f < F; ++f) store_as(base, e * F + f, ldt, p[f]);
   }
 }
 
@@ -142,13 +107,13 @@ unsigned blocks_for(int64_t n, int threads, unsigned cap) {
 
 sxe_status launch_adam_dense(const sxe_adam_desc* a, int64_t t, int64_t n, float* p, float* m, float* v, float* g,
                              void* lowp, int32_t ldt, cudaStream_t s) {
-  adam_dense_kernel<<<blocks_for(n, 256, 1u << 16), 256, 0, s>>>(make_const(a, t), n, p, m, v, g, lowp, ldt);
+  adam_dense_kernel<<<blocks_for(n, 256, 1u << 16), 256, 0, s>>>(make_adam_const(a, t), n, p, m, v, g, lowp, ldt);
   return check_launch("adam_dense");
 }
 
 sxe_status launch_adam_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries, int32_t F, float* state,
                                uint32_t* touched, void* lowp, int32_t ldt, cudaStream_t s) {
-  const AdamConst k = make_const(a, t);
+  const AdamConst k = make_adam_const(a, t);
   // one warp per 32 bitmap words, at most 16 blocks of 8 warps per SM
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "simplexenc.h"
@@ -43,7 +44,10 @@ sxe_status check_launch(const char* what);
 
 // launchers (defined in encode.cu / mlp.cu / optim.cu); arguments already validated
 sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
-                             void* out, cudaStream_t s);
+                             void* out, cudaStream_t s, int64_t table_stride = 0);
+sxe_status launch_table_step(const sxe_encoder* enc, const sxe_adam_desc* adam, int64_t t, const float* x,
+                             int64_t P, const float* dout, float* state, float* scratch, uint32_t* touched,
+                             cudaStream_t s);
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
                              float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s,
                              int level_begin = 0, int n_levels = -1);
@@ -130,6 +134,45 @@ __device__ __forceinline__ void atomic_add_entry(float* p, const float (&v)[F]) 
 #pragma unroll
     for (int j = 0; j < F / 4; ++j)
       atomicAdd(reinterpret_cast<float4*>(p) + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba, Algorithm 1) on binary32 state
+// ---------------------------------------------------------------------------
+struct AdamConst {
+  float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+  int skip;
+};
+
+inline AdamConst make_adam_const(const sxe_adam_desc* a, int64_t t) {
+  AdamConst k;
+  k.lr = a->lr; k.b1 = a->beta1; k.b2 = a->beta2; k.eps = a->eps;
+  k.c1 = (float)(1.0 / (1.0 - pow((double)a->beta1, (double)t)));
+  k.c2 = (float)(1.0 / (1.0 - pow((double)a->beta2, (double)t)));
+  k.skip = a->skip_zero_grad;
+  return k;
+}
+
+// m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr m c1 / (sqrt(v c2) + eps)
+__device__ __forceinline__ void adam_one(const AdamConst& k, float g, float& p, float& m, float& v) {
+  m = fmaf(k.b1, m, (1.f - k.b1) * g);
+  v = fmaf(k.b2, v, (1.f - k.b2) * g * g);
+  const float mh = m * k.c1;
+  const float vh = v * k.c2;
+  p = p - k.lr * mh / (sqrtf(vh) + k.eps);
+}
+
+// Low-precision copy of F consecutive parameters in one store where the type allows.
+template <int F>
+__device__ __forceinline__ void store_lowp(void* base, int64_t e, int ldt, const float (&p)[F]) {
+  if (F == 2 && ldt == SXE_F16) {
+    reinterpret_cast<__half2*>(base)[e] = __floats2half2_rn(p[0], p[1]);
+  } else if (F == 2 && ldt == SXE_BF16) {
+    reinterpret_cast<__nv_bfloat162*>(base)[e] = __floats2bfloat162_rn(p[0], p[1]);
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) store_as(base, e * F + f, ldt, p[f]);
   }
 }
 

@@ -42,12 +42,12 @@ def test_one_step_matches_oracle():
     W = [w.astype(np.float16).astype(np.float64) for w in tr.mlp.split(W0)]
 
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda()
-    # run the first three stages of the step and stop before the optimiser
-    tr.enc.encode_fwd(xd, tr.tables, tr.enc_out)
-    tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, td, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
-                        workspace=tr.ws)
-    tr.enc.encode_bwd(xd, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
-    g_tab = tr.state[:, 3 * F:].cpu().numpy().copy()
+    # encode + network stages; the table gradient they imply is read out with the dense
+    # backward entry point before the optimiser consumes it
+    tr.forward_and_grads(xd, td)
+    dense = torch.zeros((L, T, F), device="cuda")
+    tr.enc.encode_bwd(xd, tr.d_enc, dense)
+    g_tab = dense.reshape(L * T, F).cpu().numpy()
     g_W = tr.dW.cpu().numpy().copy()
     loss_gpu = tr.loss()
 
@@ -81,17 +81,19 @@ def test_one_step_matches_oracle():
 
     # optimiser: Adam at t = 1 moves each parameter by -lr * g / (|g| + eps); compare where the
     # sign of the gradient is unambiguous (|g_ref| well above the tolerance)
-    tr.adam_tables.step_touched(1, tr.state, tr.touched, tr.tables, F)
-    tr.adam_mlp.step(1, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
+    tr.t = 1
+    tr.apply_updates(xd)
+    assert torch.all(tr.scratch == 0) and torch.all(tr.touched == 0)
+    assert torch.equal(tr.table_lowp().reshape(L * T, F), tr.table_params().half())
     hp = dict(lr=float(np.float32(1e-2)), beta1=float(np.float32(0.9)), beta2=float(np.float32(0.99)),
               eps=float(np.float32(1e-15)))
     g_all = np.concatenate([g_ref[l] for l in range(L)])
     den_all = np.concatenate([den_bound[l] for l in range(L)])
     p_ref, _, _ = OA.adam_step(p_tab0, g_all, np.zeros_like(g_all), np.zeros_like(g_all), 1, skip_zero_grad=True, **hp)
     clear = ((np.abs(g_all) > 4 * tol * den_all) | (den_all == 0)) & ~shaky
-    p_gpu = tr.state[:, :F].cpu().numpy()
+    p_gpu = tr.table_params().cpu().numpy()
     np.testing.assert_allclose(p_gpu[clear], p_ref[clear], rtol=0, atol=2e-6)
-    assert clear.mean() > 0.5
+    assert (clear & (den_all > 0)).sum() > 5000          # the comparison covers many updated entries
     gW_ref = np.concatenate([a.ravel() for a in dW_ref])
     W_ref, _, _ = OA.adam_step(W0, gW_ref, np.zeros_like(W0), np.zeros_like(W0), 1, skip_zero_grad=False, **hp)
     clearW = np.abs(gW_ref) > 1e-2 * np.abs(gW_ref).max()
@@ -186,3 +188,66 @@ def test_autograd_mlp_matches_oracle():
     for a, b, den, sl in zip(mlp.split(W.grad.float().cpu().numpy()), dW_ref, dW_den, dW_sl):
         assert within(a, b, den, tol, sl) <= 1.0
     assert within(x.grad.float().cpu().numpy(), din_ref, din_den, tol, din_sl) <= 1.0
+
+
+@pytest.mark.parametrize("kind,d,F,tdt", [("simplex", 2, 2, "f16"), ("simplex", 3, 2, "bf16"), ("grid", 3, 2, "f16"),
+                                          ("simplex", 4, 1, "f32"), ("simplex", 2, 4, "f16"), ("simplex", 5, 8, "f32")])
+def test_table_step_matches_oracle(kind, d, F, tdt):
+    """Level-by-level scatter + Adam equals the oracle's gradient followed by the zero-gradient
+    skip-rule Adam of every table parameter; scratch and bitmap end zero; the low-precision
+    copies are the rounded parameters; untouched records are unchanged."""
+    from paper_2311_15439_gb300.api import Adam, Encoder
+    from paper_2311_15439_gb300.build import build
+    from paper_2311_15439_gb300.trainer import pack_records
+    build()
+    L, log2_T, P = 5, 12, 3000
+    T = 1 << log2_T
+    enc = Encoder(d, L, F, log2_T, 8.0, 1.6, kind=kind, table_dtype=tdt, out_dtype="f32")
+    g = synth.rng(3)
+    p0 = g.standard_normal((L * T, F)).astype(np.float32) * 0.1
+    m0 = (g.standard_normal((L * T, F)) * 0.01).astype(np.float32)
+    v0 = g.uniform(0.01, 0.1, (L * T, F)).astype(np.float32)
+    rec = pack_records(p0, tdt)
+    rec[:, F:2 * F] = m0
+    rec[:, 2 * F:3 * F] = v0
+    state = torch.from_numpy(rec).cuda()
+    scratch = torch.zeros((T, F), device="cuda")
+    touched = torch.zeros((L * T // 32,), dtype=torch.int32, device="cuda")
+    x = synth.uniform_points(P, d, 4)
+    dout = synth.normal_grads(P, L * F, 5)
+    enc.table_step(Adam(1e-2, 0.9, 0.99, 1e-15), 5, torch.from_numpy(x).cuda(), torch.from_numpy(dout).cuda(),
+                   state, scratch, touched)
+    s = state.cpu().numpy()
+    assert torch.all(scratch == 0) and torch.all(touched == 0)
+    kw = dict(n_levels=L, log2_T=log2_T, n_features=F, base_res=8.0, growth=1.6)
+    grads = (OE.simplex_encode_bwd if kind == "simplex" else OE.grid_encode_bwd)(x, dout, **kw)
+    gr = np.concatenate([grads[l] for l in range(L)])
+    hp = dict(lr=float(np.float32(1e-2)), beta1=float(np.float32(0.9)), beta2=float(np.float32(0.99)),
+              eps=float(np.float32(1e-15)))
+    rp, rm, rv = OA.adam_step(p0, gr, m0, v0, 5, skip_zero_grad=True, **hp)
+    # gradients carry binary32 atomic rounding (1e-5 of sum |terms|); Adam maps it smoothly here
+    np.testing.assert_allclose(s[:, :F], rp, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(s[:, F:2 * F], rm, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(s[:, 2 * F:3 * F], rv, rtol=1e-5, atol=1e-9)
+    untouched = np.all(gr == 0, axis=1)
+    assert untouched.any() and (~untouched).sum() > 1000
+    assert np.array_equal(s[untouched, :3 * F], rec[untouched, :3 * F])
+    dt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[tdt]
+    low = state[:, 3 * F:].contiguous().view(dt)[:, :F]
+    assert torch.equal(low, state[:, :F].to(dt))
+
+
+@pytest.mark.parametrize("tdt", ["f16", "bf16", "f32"])
+def test_forward_from_records_equals_dense(tdt):
+    """Gathering the low-precision copies out of the state records gives the same encoding,
+    bit for bit, as the dense table holding the same values."""
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.trainer import pack_records
+    L, log2_T, F = 6, 12, 2
+    enc = Encoder(3, L, F, log2_T, 8.0, 1.7, table_dtype=tdt)
+    vals = synth.uniform_tables(L, 1 << log2_T, F, 6, dtype=tdt, scale=1.0)[0]
+    state = torch.from_numpy(pack_records(vals.reshape(-1, F), tdt)).cuda()
+    dt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[tdt]
+    dense = torch.from_numpy(vals).cuda().to(dt)
+    x = torch.from_numpy(synth.uniform_points(4000, 3, 7)).cuda()
+    assert torch.equal(enc.encode_fwd_records(x, state), enc.encode_fwd(x, dense))
