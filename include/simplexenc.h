@@ -214,6 +214,25 @@ sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* desc, const void* weights, const
                             float* din, float* dweights, float* sq_sum,
                             void* workspace, int64_t workspace_bytes, void* stream);
 
+/* sxe_mlp_train_l2 without a caller-provided workspace, for callers that cannot
+ * allocate device memory: code running under another framework's allocator that owns
+ * all device memory, real-time or embedded loops where an allocation may block or fail,
+ * and code that must not allocate while a stream is being captured.  The paper has no
+ * counterpart; this is an interface convenience of this library.
+ * The per-CTA weight-gradient partials live in a fixed array inside the library's own
+ * device memory: 2^21 binary32 values (8 MiB), held on every GPU that loads the library
+ * until the process exits.  If a network needs more than that per CTA the call returns
+ * SXE_ENOMEM; otherwise the persistent grid is reduced to what the array holds.
+ * The first call on each device looks up the array's device address (with that device
+ * current) and caches it, so make one call before any stream capture begins.
+ * Every call shares the array and leaves its last contents in it; nothing in it needs to
+ * start at zero.  Calls whose kernels overlap on the GPU (unordered streams) race on the
+ * array: serialise them.  Results equal sxe_mlp_train_l2's up to the summation order of
+ * the partials. */
+sxe_status sxe_mlp_train_l2_static(const sxe_mlp_desc* desc, const void* weights, const void* in,
+                                   const float* target, float loss_scale, int64_t n_points,
+                                   float* din, float* dweights, float* sq_sum, void* stream);
+
 /* L2 loss of the image-fitting task (Sec. 6.1): mean over n_points*n_out of
  * (y - target)^2.  Writes dy = 2 (y - target) / (n_points*n_out) (binary32,
  * overwritten) and adds the batch's sum of squared residuals to *sq_sum

@@ -251,6 +251,23 @@ class Mlp:
                                          _stream(stream)), "sxe_mlp_train_l2")
         return dW
 
+    def mlp_train_l2_static(self, W, x, target, dW, sq_sum, din=None, loss_scale: float = 1.0, stream=None):
+        """``sxe_mlp_train_l2_static``: the same computation without a workspace argument, for
+        callers that cannot allocate device memory (the library's own fixed scratch is used)."""
+        dt = torch_dtype(self.dtype)
+        P = x.shape[0]
+        _need(W, dt, "weights", (self.n_params,))
+        _need(x, dt, "in", (P, self.n_in))
+        _need(target, torch.float32, "target", (P, self.n_out))
+        _need(dW, torch.float32, "dweights", (self.n_params,))
+        _need(sq_sum, torch.float32, "sq_sum", (1,))
+        if din is not None:
+            _need(din, torch.float32, "din", (P, self.n_in))
+        L.check(L.lib().sxe_mlp_train_l2_static(ctypes.byref(self.desc), _ptr(W), _ptr(x), _ptr(target),
+                                                float(loss_scale), P, _ptr(din), _ptr(dW), _ptr(sq_sum),
+                                                _stream(stream)), "sxe_mlp_train_l2_static")
+        return dW
+
 
 def loss_l2(y, target, dy, sq_sum, stream=None):
     P, n_out = y.shape
