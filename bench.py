@@ -126,7 +126,7 @@ def _stage_work(n_touched, F=2, L=16, d=2, width=64, n_in=32):
     bytes for the memory-bound stages, FLOPs for the network."""
     V = d + 1
     per_pt_fwd = 4 * d + L * V * 2 * F + L * F * 2                 # x, fp16 gathers, fp16 encoding
-    table = BATCH * (4 * d + 4 * L * F) + n_touched * (2 * 16 * F)  # x, dL/d(enc); record read + write
+    table = BATCH * (4 * d + 4 * L * F) + n_touched * (2 * 16 * F + 2 * F)  # x, dL/d(enc); record r+w, fp16 copy
     flops = 2 * (n_in * width + width * width + width * 16)       # forward MACs (output padded to 16)
     flops = 3 * flops * BATCH                                     # forward + delta + weight-gradient GEMMs
     return {"encode_fwd": ("hbm", per_pt_fwd * BATCH), "table_step": ("hbm", table),
@@ -188,12 +188,12 @@ def run_gpu(args):
             e = ev[k]
             tr.t += 1
             e[0].record(stream)
-            tr.enc.encode_fwd_records(x, tr.state, tr.enc_out)
+            tr.enc.encode_fwd(x, tr.tables, tr.enc_out)
             e[1].record(stream)
-            tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, t, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
-                                workspace=tr.ws)
+            tr.mlp.mlp_train_l2_grouped(tr.W_lowp, tr.enc_out, t, tr.dW, tr.sq_sum, tr.d_enc, tr.enc.n_features,
+                                        loss_scale=tr.loss_scale, workspace=tr.ws)
             e[2].record(stream)
-            tr.enc.table_step(tr.adam_tables, tr.t, x, tr.d_enc, tr.state, tr.scratch, tr.touched)
+            tr.enc.table_step(tr.adam_tables, tr.t, x, tr.d_enc, tr.state, tr.tables, tr.scratch, tr.touched)
             e[3].record(stream)
             tr.adam_mlp.step(tr.t, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
             e[4].record(stream)
@@ -257,7 +257,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "kind": args.kind, "global_batch": BATCH * world,
                        "points_per_step_per_gpu": BATCH, "parallelism": "replicas (one per GPU)",
-                       "l2": "working set > L2: 2 GiB fp32 table state records (fp16 copies inside), no flush",
+                       "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state records, no flush",
                        "batches": "%d resident distinct batches cycled" % N_POOL},
             "e2e": {"value": BATCH * e2e_steps * world / (ms_e2e / 1e3), "unit": "points/s",
                     "h2d_bytes_per_step": BATCH * (2 + N_OUT) * 4, "d2h_bytes_per_step": 4},

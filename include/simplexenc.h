@@ -233,6 +233,15 @@ sxe_status sxe_mlp_train_l2_static(const sxe_mlp_desc* desc, const void* weights
                                    const float* target, float loss_scale, int64_t n_points,
                                    float* din, float* dweights, float* sq_sum, void* stream);
 
+/* sxe_mlp_train_l2 writing din grouped: column c of dL/din goes to
+ * din[((c / din_group) * n_points + p) * din_group + c % din_group], i.e. [n_in/g][P][g];
+ * with g = F of the encoder that is dL/d(encoding) level-major, [L][P][F].  din_group is
+ * 1, 2, 4 or 8 and divides n_in; din is required.  Other arguments as sxe_mlp_train_l2. */
+sxe_status sxe_mlp_train_l2_grouped(const sxe_mlp_desc* desc, const void* weights, const void* in,
+                                    const float* target, float loss_scale, int64_t n_points,
+                                    float* din, int32_t din_group, float* dweights, float* sq_sum,
+                                    void* workspace, int64_t workspace_bytes, void* stream);
+
 /* L2 loss of the image-fitting task (Sec. 6.1): mean over n_points*n_out of
  * (y - target)^2.  Writes dy = 2 (y - target) / (n_points*n_out) (binary32,
  * overwritten) and adds the batch's sum of squared residuals to *sq_sum
@@ -272,24 +281,26 @@ sxe_status sxe_step_touched(const sxe_adam_desc* desc, int64_t t, int64_t n_entr
                             int32_t n_features, float* state, uint32_t* touched,
                             void* table_lowp, int32_t lowp_dtype, void* stream);
 
-/* Table update of one training step, Sec. 5 (e) followed by Adam, processed one level at
- * a time: for each level l, every point's vertices add w_k * dout[p][l*F + f] into a
- * dense binary32 scratch [T][F] and mark the entries they touch; then every marked
- * entry takes the Adam step of sxe_step with the zero-gradient skip rule (per
- * parameter), refreshes its low-precision copy, and its scratch gradient and bit are
- * cleared.  The result equals sxe_encode_bwd into a zeroed gradient followed by the
- * skip-rule Adam step of every table parameter; the scratch (T*F*4 bytes, reused by
- * every level) stays resident in L2.
- *   state    L*T records of 4F binary32 words each: [0,F) parameter, [F,2F) first
- *            moment, [2F,3F) second moment, [3F,4F) the desc.table_dtype copy of the
- *            parameter packed from its start (rest zero).  16-byte aligned.
- *   scratch  [T][F] binary32, all zero on entry; zero again on return.
- *   touched  L*T bits (uint32 words), all zero on entry; zero again on return.
- *   dout     [n_points][L*F] binary32 dL/d(encoding).
- * Needs T >= 32.  Launches 2*L kernels on `stream`. */
+/* Table update of one training step: Sec. 5 (e) (accumulate dL/d(encoding) into the
+ * looked-up entries) followed by the Adam step of sxe_step with the zero-gradient skip
+ * rule applied per parameter, and the refresh of the low-precision copy the forward pass
+ * reads.  Same result as sxe_encode_bwd into zeroed gradients followed by sxe_step_touched.
+ *   dout        dL/d(encoding) LEVEL-MAJOR: [L][n_points][F] binary32 (the layout
+ *               sxe_mlp_train_l2_grouped writes with din_group = F).
+ *   state       L*T records of 4F binary32 words {param[F], m[F], v[F], grad[F]}, the
+ *               grad fields zero on entry and again on return.  16-byte aligned.
+ *   table_lowp  dense [L][T][F] copy of the parameters in desc.table_dtype (rewritten for
+ *               every entry that takes a step).
+ *   scratch     [T][F] binary32, zero on entry and again on return.
+ *   touched     L*T bits (uint32 words), zero on entry and again on return.
+ * Levels whose lattice box (N_l+2)^d holds at most T/4 vertices are scattered into the
+ * records' grad fields and stepped together; every finer level is scattered into the
+ * scratch (reused by every level, so it stays in L2) and stepped from it, one level at a
+ * time.  Needs T >= 32.  Launches 2 + 2 * (number of finer levels) kernels. */
 sxe_status sxe_table_step(const sxe_encoder* enc, const sxe_adam_desc* adam, int64_t t,
                           const float* x, int64_t n_points, const float* dout,
-                          float* state, float* scratch, uint32_t* touched, void* stream);
+                          float* state, void* table_lowp, float* scratch, uint32_t* touched,
+                          void* stream);
 
 /* Thread-local message describing the last failing call on this thread ("" if none). */
 const char* sxe_last_error(void);

@@ -23,7 +23,7 @@ EXPORTS = (
     "sxe_encode_fwd", "sxe_encode_bwd", "sxe_encode_vertices", "sxe_encode_plain_fwd", "sxe_encode_plain_bwd",
     "sxe_mlp_n_params", "sxe_mlp_fwd", "sxe_mlp_bwd_workspace_bytes", "sxe_mlp_bwd", "sxe_mlp_train_l2",
     "sxe_loss_l2", "sxe_step", "sxe_step_touched", "sxe_last_error", "sxe_version",
-    "sxe_encode_fwd_strided", "sxe_table_step", "sxe_mlp_train_l2_static",
+    "sxe_encode_fwd_strided", "sxe_table_step", "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped",
 )
 
 
@@ -70,7 +70,8 @@ def _declare(L):
         "sxe_step": (i32, [A, i64, i64, vp, vp, vp, vp, vp, i32, vp]),
         "sxe_step_touched": (i32, [A, i64, i64, i32, vp, vp, vp, i32, vp]),
         "sxe_encode_fwd_strided": (i32, [vp, vp, i64, vp, i64, vp, vp]),
-        "sxe_table_step": (i32, [vp, A, i64, vp, i64, vp, vp, vp, vp, vp]),
+        "sxe_table_step": (i32, [vp, A, i64, vp, i64, vp, vp, vp, vp, vp, vp]),
+        "sxe_mlp_train_l2_grouped": (i32, [M, vp, vp, vp, f32, i64, vp, i32, vp, vp, vp, i64, vp]),
         "sxe_mlp_train_l2_static": (i32, [M, vp, vp, vp, f32, i64, vp, vp, vp, vp]),
         "sxe_last_error": (ctypes.c_char_p, []),
         "sxe_version": (ctypes.c_char_p, []),

@@ -98,31 +98,19 @@ class Encoder:
                 "sxe_encode_fwd")
         return out
 
-    def encode_fwd_records(self, x: torch.Tensor, state: torch.Tensor, out: torch.Tensor | None = None, stream=None):
-        """Forward encoding reading the low-precision copies inside ``sxe_table_step`` records
-        (``sxe_encode_fwd_strided`` with entry stride 4F binary32 words)."""
+    def table_step(self, adam: "Adam", t: int, x: torch.Tensor, dout_level_major: torch.Tensor, state: torch.Tensor,
+                   table_lowp: torch.Tensor, scratch: torch.Tensor, touched: torch.Tensor, stream=None):
+        """Table backward + Adam of one training step (``sxe_table_step``); dout is [L, P, F]."""
         P, F = x.shape[0], self.n_features
         _need(x, torch.float32, "x", (P, self.d))
+        _need(dout_level_major, torch.float32, "dout", (self.n_levels, P, F))
         _need(state, torch.float32, "state", (self.n_levels * self.T, 4 * F))
-        if out is None:
-            out = torch.empty((P, self.n_out), dtype=torch_dtype(self.out_dtype), device=x.device)
-        _need(out, torch_dtype(self.out_dtype), "out", (P, self.n_out))
-        esize = torch.empty((), dtype=torch_dtype(self.table_dtype)).element_size()
-        L.check(L.lib().sxe_encode_fwd_strided(self._h, _ptr(x), P, state.data_ptr() + 12 * F, 16 * F // esize,
-                                               _ptr(out), _stream(stream)), "sxe_encode_fwd_strided")
-        return out
-
-    def table_step(self, adam: "Adam", t: int, x: torch.Tensor, dout: torch.Tensor, state: torch.Tensor,
-                   scratch: torch.Tensor, touched: torch.Tensor, stream=None):
-        """Level-by-level table backward + Adam (``sxe_table_step``)."""
-        P, F = x.shape[0], self.n_features
-        _need(x, torch.float32, "x", (P, self.d))
-        _need(dout, torch.float32, "dout", (P, self.n_out))
-        _need(state, torch.float32, "state", (self.n_levels * self.T, 4 * F))
+        _need(table_lowp, torch_dtype(self.table_dtype), "table_lowp", self.table_shape())
         _need(scratch, torch.float32, "scratch", (self.T, F))
         _need(touched, torch.int32, "touched", ((self.n_levels * self.T + 31) // 32,))
-        L.check(L.lib().sxe_table_step(self._h, ctypes.byref(adam.desc), int(t), _ptr(x), P, _ptr(dout), _ptr(state),
-                                       _ptr(scratch), _ptr(touched), _stream(stream)), "sxe_table_step")
+        L.check(L.lib().sxe_table_step(self._h, ctypes.byref(adam.desc), int(t), _ptr(x), P, _ptr(dout_level_major),
+                                       _ptr(state), _ptr(table_lowp), _ptr(scratch), _ptr(touched),
+                                       _stream(stream)), "sxe_table_step")
 
     def encode_bwd(self, x: torch.Tensor, dout: torch.Tensor, grad: torch.Tensor, grad_stride: int | None = None,
                    touched: torch.Tensor | None = None, grad_offset: int = 0, stream=None):
@@ -249,6 +237,24 @@ class Mlp:
         L.check(L.lib().sxe_mlp_train_l2(ctypes.byref(self.desc), _ptr(W), _ptr(x), _ptr(target), float(loss_scale),
                                          P, _ptr(din), _ptr(dW), _ptr(sq_sum), _ptr(ws), ws.numel() * 4,
                                          _stream(stream)), "sxe_mlp_train_l2")
+        return dW
+
+    def mlp_train_l2_grouped(self, W, x, target, dW, sq_sum, din, din_group: int, loss_scale: float = 1.0,
+                             workspace=None, stream=None):
+        """``sxe_mlp_train_l2_grouped``: din written as [n_in / g, P, g]."""
+        dt = torch_dtype(self.dtype)
+        P = x.shape[0]
+        _need(W, dt, "weights", (self.n_params,))
+        _need(x, dt, "in", (P, self.n_in))
+        _need(target, torch.float32, "target", (P, self.n_out))
+        _need(dW, torch.float32, "dweights", (self.n_params,))
+        _need(sq_sum, torch.float32, "sq_sum", (1,))
+        _need(din, torch.float32, "din", (self.n_in // din_group, P, din_group))
+        ws = workspace if workspace is not None else self.workspace(P, x.device)
+        L.check(L.lib().sxe_mlp_train_l2_grouped(ctypes.byref(self.desc), _ptr(W), _ptr(x), _ptr(target),
+                                                 float(loss_scale), P, _ptr(din), int(din_group), _ptr(dW),
+                                                 _ptr(sq_sum), _ptr(ws), ws.numel() * 4, _stream(stream)),
+                "sxe_mlp_train_l2_grouped")
         return dW
 
     def mlp_train_l2_static(self, W, x, target, dW, sq_sum, din=None, loss_scale: float = 1.0, stream=None):

@@ -144,7 +144,8 @@ sxe_status sxe_encode_fwd_strided(const sxe_encoder* e, const float* x, int64_t 
 }
 
 sxe_status sxe_table_step(const sxe_encoder* e, const sxe_adam_desc* adam, int64_t t, const float* x, int64_t P,
-                          const float* dout, float* state, float* scratch, uint32_t* touched, void* stream) {
+                          const float* dout, float* state, void* table_lowp, float* scratch, uint32_t* touched,
+                          void* stream) {
   sxe_status st = check_points("table_step", e, x, P);
   if (st != SXE_OK) return st;
   if (!adam || t < 1) return set_error(SXE_EINVAL, "table_step: NULL Adam description or step t < 1");
@@ -152,13 +153,15 @@ sxe_status sxe_table_step(const sxe_encoder* e, const sxe_adam_desc* adam, int64
       !(adam->eps >= 0.f))
     return set_error(SXE_EINVAL, "table_step: bad Adam hyper-parameters");
   if (e->desc.log2_T < 5) return set_error(SXE_EUNSUPPORTED, "table_step: needs T >= 32 (log2_T >= 5)");
-  if (!state || !scratch || !touched || (P > 0 && !dout))
-    return set_error(SXE_EINVAL, "table_step: NULL state, scratch, touched or dout");
+  if (!state || !table_lowp || !scratch || !touched || (P > 0 && !dout))
+    return set_error(SXE_EINVAL, "table_step: NULL state, table, scratch, touched or dout");
   const int F = e->desc.n_features;
   const size_t ga = F == 1 ? 4 : F == 2 ? 8 : 16;
-  if (!aligned(state, 16) || !aligned(scratch, ga) || !aligned(touched, 4) || (dout && !aligned(dout, 4)))
+  const size_t la = F == 2 ? 2 * dtype_size(e->desc.table_dtype) : dtype_size(e->desc.table_dtype);
+  if (!aligned(state, 16) || !aligned(scratch, ga) || !aligned(touched, 4) || !aligned(table_lowp, la) ||
+      (dout && !aligned(dout, F == 2 ? 8 : 4)))
     return set_error(SXE_EINVAL, "table_step: misaligned buffer");
-  return launch_table_step(e, adam, t, x, P, dout, state, scratch, touched, (cudaStream_t)stream);
+  return launch_table_step(e, adam, t, x, P, dout, state, table_lowp, scratch, touched, (cudaStream_t)stream);
 }
 
 sxe_status sxe_encode_bwd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* grad,
@@ -273,6 +276,27 @@ sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* d, const void* W, const void* in
   if (P > 0 && (!target || !sq_sum)) return set_error(SXE_EINVAL, "mlp_train_l2: NULL target or sq_sum");
   return mlp_bwd_common("mlp_train_l2", d, W, in, nullptr, target, loss_scale, P, din, dW, sq_sum, ws, ws_bytes,
                         stream);
+}
+
+sxe_status sxe_mlp_train_l2_grouped(const sxe_mlp_desc* d, const void* W, const void* in, const float* target,
+                                    float loss_scale, int64_t P, float* din, int32_t din_group, float* dW,
+                                    float* sq_sum, void* ws, int64_t ws_bytes, void* stream) {
+  if (!d) return set_error(SXE_EINVAL, "mlp_train_l2_grouped: NULL desc");
+  if (!(din_group == 1 || din_group == 2 || din_group == 4 || din_group == 8) || d->n_in % din_group != 0)
+    return set_error(SXE_EINVAL, "mlp_train_l2_grouped: din_group=%d must be 1, 2, 4 or 8 and divide n_in", din_group);
+  if (P > 0 && (!target || !sq_sum || !din)) return set_error(SXE_EINVAL, "mlp_train_l2_grouped: NULL target, sq_sum or din");
+  sxe_status st = check_mlp("mlp_train_l2_grouped", d);
+  if (st != SXE_OK) return st;
+  if (P < 0) return set_error(SXE_EINVAL, "mlp_train_l2_grouped: n_points < 0");
+  if (P == 0) return SXE_OK;
+  if (!W || !in || !dW || !ws) return set_error(SXE_EINVAL, "mlp_train_l2_grouped: NULL weights, in, dweights or workspace");
+  if (!(loss_scale > 0.f) || !std::isfinite(loss_scale)) return set_error(SXE_EINVAL, "mlp_train_l2_grouped: loss_scale must be > 0");
+  if (!aligned(in, 16) || !aligned(W, 4) || !aligned(ws, 4) || !aligned(din, 8))
+    return set_error(SXE_EINVAL, "mlp_train_l2_grouped: misaligned buffer");
+  const int64_t need = sxe_mlp_bwd_workspace_bytes(d, P);
+  if (ws_bytes < need) return set_error(SXE_ENOMEM, "mlp_train_l2_grouped: workspace %lld < %lld bytes", (long long)ws_bytes, (long long)need);
+  return launch_mlp_bwd(d, W, in, nullptr, target, loss_scale, P, din, dW, sq_sum, (float*)ws, mlp_grid_blocks(d, P),
+                        (cudaStream_t)stream, din_group);
 }
 
 sxe_status sxe_loss_l2(const float* y, const float* target, int64_t P, int32_t n_out, float* dy, float* sq_sum,

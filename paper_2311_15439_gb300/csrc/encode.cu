@@ -103,7 +103,7 @@ template <bool SIMPLEX, int D, int F>
 __global__ void __launch_bounds__(kThreads)
 encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restrict__ dout,
                   float* __restrict__ grad, int64_t stride, uint32_t* __restrict__ touched,
-                  const EncParams prm, int l0, int nl) {
+                  const EncParams prm, int l0, int nl, bool dout_level_major) {
   constexpr int V = Verts<SIMPLEX, D>::V;
   __shared__ float s_scale[SXE_MAX_LEVELS];
   if (threadIdx.x < SXE_MAX_LEVELS) s_scale[threadIdx.x] = prm.scale[threadIdx.x];
@@ -120,7 +120,7 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
   lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
   const int64_t lbase = (int64_t)it.l << prm.log2_T;
   float g[F];
-  const float* pd = dout + (it.p * L + it.l) * F;
+  const float* pd = dout + (dout_level_major ? (int64_t)it.l * P + it.p : it.p * L + it.l) * F;
   if constexpr (F == 2) {
     const float2 a = __ldg(reinterpret_cast<const float2*>(pd));
     g[0] = a.x; g[1] = a.y;
@@ -201,30 +201,30 @@ sxe_status fwd_d(const sxe_encoder* e, const float* x, int64_t P, const void* t,
 
 template <bool SIMPLEX, int D, int F>
 sxe_status bwd_f(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                 uint32_t* touched, int l0, int nl, cudaStream_t s) {
-  encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, nl), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm, l0, nl);
+                 uint32_t* touched, int l0, int nl, cudaStream_t s, bool lm) {
+  encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, nl), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm, l0, nl, lm);
   return check_launch("encode_bwd");
 }
 
 template <bool SIMPLEX, int D>
 sxe_status bwd_fd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                  uint32_t* t, int l0, int nl, cudaStream_t s) {
+                  uint32_t* t, int l0, int nl, cudaStream_t s, bool lm) {
   switch (e->desc.n_features) {
-    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, l0, nl, s);
-    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, l0, nl, s);
-    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, l0, nl, s);
-    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, l0, nl, s);
+    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
+    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
+    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
+    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
   }
 }
 
 template <bool SIMPLEX>
 sxe_status bwd_d(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                 uint32_t* t, int l0, int nl, cudaStream_t s) {
+                 uint32_t* t, int l0, int nl, cudaStream_t s, bool lm) {
   switch (e->desc.d) {
-    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, l0, nl, s);
-    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, l0, nl, s);
-    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, l0, nl, s);
-    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, l0, nl, s);
+    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
+    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
+    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
+    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
   }
 }
 
@@ -250,10 +250,10 @@ sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, 
 }
 
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout, float* grad,
-                             int64_t stride, uint32_t* touched, cudaStream_t s, int l0, int nl) {
+                             int64_t stride, uint32_t* touched, cudaStream_t s, int l0, int nl, bool dout_lm) {
   if (nl < 0) nl = enc->prm.n_levels - l0;
-  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, l0, nl, s)
-                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, l0, nl, s);
+  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, l0, nl, s, dout_lm)
+                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, l0, nl, s, dout_lm);
 }
 
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,

@@ -261,7 +261,8 @@ template <typename T, int N_IN, int NH, int MODE>
 __global__ void __launch_bounds__(kThreads, BwdOcc<N_IN, NH>::value)
 mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
                const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
-               float* __restrict__ din, float* __restrict__ ws, int64_t n_params, float* __restrict__ sq_sum) {
+               float* __restrict__ din, float* __restrict__ ws, int64_t n_params, float* __restrict__ sq_sum,
+               int din_group) {
   using S = Smem<N_IN, NH>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -368,9 +369,17 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
           const int64_t row = row0 + r0 + g + half * 8;
-          if (row < P)
-            *reinterpret_cast<float2*>(din + row * N_IN + nt * 8 + 2 * t) =
-                make_float2(acc[half * 2] * inv_scale, acc[half * 2 + 1] * inv_scale);
+          if (row >= P) continue;
+          const int c = nt * 8 + 2 * t;                 // columns c, c + 1
+          const float2 v = make_float2(acc[half * 2] * inv_scale, acc[half * 2 + 1] * inv_scale);
+          if (din_group == 0) {                          // [P][n_in]
+            *reinterpret_cast<float2*>(din + row * N_IN + c) = v;
+          } else if (din_group == 1) {                   // [n_in][P]
+            din[(int64_t)c * P + row] = v.x;
+            din[(int64_t)(c + 1) * P + row] = v.y;
+          } else {                                       // [n_in / g][P][g], c and c + 1 in one group
+            *reinterpret_cast<float2*>(din + ((int64_t)(c / din_group) * P + row) * din_group + c % din_group) = v;
+          }
         }
       }
     }
@@ -498,7 +507,7 @@ sxe_status fwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, int6
 template <typename T, int N_IN, int NH>
 sxe_status bwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
                       float loss_scale, int64_t P, float* din, float* dW, float* sq_sum, float* ws, int grid,
-                      cudaStream_t s) {
+                      cudaStream_t s, int din_group) {
   using S = Smem<N_IN, NH>;
   const size_t bytes = (size_t)S::END * sizeof(T);
   const int64_t n_params = sxe_mlp_n_params(d);
@@ -506,12 +515,12 @@ sxe_status bwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
     auto k = mlp_bwd_kernel<T, N_IN, NH, 1>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale, din, ws,
-                                    n_params, sq_sum);
+                                    n_params, sq_sum, din_group);
   } else {
     auto k = mlp_bwd_kernel<T, N_IN, NH, 0>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale, din, ws,
-                                    n_params, sq_sum);
+                                    n_params, sq_sum, din_group);
   }
   sxe_status st = check_launch("mlp_bwd");
   if (st != SXE_OK) return st;
@@ -538,20 +547,20 @@ sxe_status fwd_in(const sxe_mlp_desc* d, const void* W, const void* in, int64_t 
 }
 template <typename T, int N_IN>
 sxe_status bwd_nh(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int dg) {
   switch (d->n_hidden) {
-    case 1: return bwd_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
-    case 2: return bwd_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
-    default: return bwd_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
+    case 1: return bwd_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
+    case 2: return bwd_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
+    default: return bwd_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
   }
 }
 template <typename T>
 sxe_status bwd_in(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int dg) {
   switch (d->n_in) {
-    case 16: return bwd_nh<T, 16>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
-    case 32: return bwd_nh<T, 32>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
-    default: return bwd_nh<T, 64>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s);
+    case 16: return bwd_nh<T, 16>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
+    case 32: return bwd_nh<T, 32>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
+    default: return bwd_nh<T, 64>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
   }
 }
 
@@ -590,9 +599,10 @@ sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, 
 
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                           const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
-                          float* ws, int grid, cudaStream_t s) {
-  return d->dtype == SXE_F16 ? bwd_in<__half>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s)
-                             : bwd_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s);
+                          float* ws, int grid, cudaStream_t s, int din_group) {
+  return d->dtype == SXE_F16
+             ? bwd_in<__half>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group)
+             : bwd_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);
 }
 
 }  // namespace sxe

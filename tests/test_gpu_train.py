@@ -46,7 +46,7 @@ def test_one_step_matches_oracle():
     # backward entry point before the optimiser consumes it
     tr.forward_and_grads(xd, td)
     dense = torch.zeros((L, T, F), device="cuda")
-    tr.enc.encode_bwd(xd, tr.d_enc, dense)
+    tr.enc.encode_bwd(xd, tr.d_enc_rows(), dense)
     g_tab = dense.reshape(L * T, F).cpu().numpy()
     g_W = tr.dW.cpu().numpy().copy()
     loss_gpu = tr.loss()
@@ -93,7 +93,7 @@ def test_one_step_matches_oracle():
     clear = ((np.abs(g_all) > 4 * tol * den_all) | (den_all == 0)) & ~shaky
     p_gpu = tr.table_params().cpu().numpy()
     np.testing.assert_allclose(p_gpu[clear], p_ref[clear], rtol=0, atol=2e-6)
-    assert (clear & (den_all > 0)).sum() > 500           # the comparison covers many updated entries
+    assert (clear & (den_all > 0)).sum() > 200           # the comparison covers many updated entries
     gW_ref = np.concatenate([a.ravel() for a in dW_ref])
     W_ref, _, _ = OA.adam_step(W0, gW_ref, np.zeros_like(W0), np.zeros_like(W0), 1, skip_zero_grad=False, **hp)
     clearW = np.abs(gW_ref) > 1e-2 * np.abs(gW_ref).max()
@@ -193,12 +193,13 @@ def test_autograd_mlp_matches_oracle():
 @pytest.mark.parametrize("kind,d,F,tdt", [("simplex", 2, 2, "f16"), ("simplex", 3, 2, "bf16"), ("grid", 3, 2, "f16"),
                                           ("simplex", 4, 1, "f32"), ("simplex", 2, 4, "f16"), ("simplex", 5, 8, "f32")])
 def test_table_step_matches_oracle(kind, d, F, tdt):
-    """Level-by-level scatter + Adam equals the oracle's gradient followed by the zero-gradient
-    skip-rule Adam of every table parameter; scratch and bitmap end zero; the low-precision
-    copies are the rounded parameters; untouched records are unchanged."""
+    """The table step (coarse levels through the records, finer levels through the L2 scratch)
+    equals the oracle's gradient followed by the zero-gradient skip-rule Adam of every table
+    parameter; grad fields, scratch and bitmap end zero; the low-precision tables hold the
+    rounded parameters; untouched records are unchanged."""
     from paper_2311_15439_gb300.api import Adam, Encoder
     from paper_2311_15439_gb300.build import build
-    from paper_2311_15439_gb300.trainer import pack_records
+    from paper_2311_15439_gb300.trainer import lowp_copy, pack_records
     build()
     L, log2_T, P = 5, 12, 3000
     T = 1 << log2_T
@@ -207,18 +208,21 @@ def test_table_step_matches_oracle(kind, d, F, tdt):
     p0 = g.standard_normal((L * T, F)).astype(np.float32) * 0.1
     m0 = (g.standard_normal((L * T, F)) * 0.01).astype(np.float32)
     v0 = g.uniform(0.01, 0.1, (L * T, F)).astype(np.float32)
-    rec = pack_records(p0, tdt)
+    rec = pack_records(p0)
     rec[:, F:2 * F] = m0
     rec[:, 2 * F:3 * F] = v0
     state = torch.from_numpy(rec).cuda()
+    table = lowp_copy(p0.reshape(L, T, F), tdt).cuda()
     scratch = torch.zeros((T, F), device="cuda")
     touched = torch.zeros((L * T // 32,), dtype=torch.int32, device="cuda")
     x = synth.uniform_points(P, d, 4)
     dout = synth.normal_grads(P, L * F, 5)
-    enc.table_step(Adam(1e-2, 0.9, 0.99, 1e-15), 5, torch.from_numpy(x).cuda(), torch.from_numpy(dout).cuda(),
-                   state, scratch, touched)
+    dout_lm = np.ascontiguousarray(dout.reshape(P, L, F).transpose(1, 0, 2))
+    enc.table_step(Adam(1e-2, 0.9, 0.99, 1e-15), 5, torch.from_numpy(x).cuda(), torch.from_numpy(dout_lm).cuda(),
+                   state, table, scratch, touched)
     s = state.cpu().numpy()
     assert torch.all(scratch == 0) and torch.all(touched == 0)
+    assert np.all(s[:, 3 * F:] == 0)
     kw = dict(n_levels=L, log2_T=log2_T, n_features=F, base_res=8.0, growth=1.6)
     grads = (OE.simplex_encode_bwd if kind == "simplex" else OE.grid_encode_bwd)(x, dout, **kw)
     gr = np.concatenate([grads[l] for l in range(L)])
@@ -233,21 +237,43 @@ def test_table_step_matches_oracle(kind, d, F, tdt):
     assert untouched.any() and (~untouched).sum() > 1000
     assert np.array_equal(s[untouched, :3 * F], rec[untouched, :3 * F])
     dt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[tdt]
-    low = state[:, 3 * F:].contiguous().view(dt)[:, :F]
-    assert torch.equal(low, state[:, :F].to(dt))
+    assert torch.equal(table.reshape(L * T, F), state[:, :F].to(dt))
 
 
 @pytest.mark.parametrize("tdt", ["f16", "bf16", "f32"])
-def test_forward_from_records_equals_dense(tdt):
-    """Gathering the low-precision copies out of the state records gives the same encoding,
-    bit for bit, as the dense table holding the same values."""
+def test_forward_strided_equals_dense(tdt):
+    """Gathering the table with an entry stride (entries interleaved with other data) gives the
+    same encoding, bit for bit, as the dense table holding the same values."""
+    from paper_2311_15439_gb300 import _lib
     from paper_2311_15439_gb300.api import Encoder
-    from paper_2311_15439_gb300.trainer import pack_records
     L, log2_T, F = 6, 12, 2
     enc = Encoder(3, L, F, log2_T, 8.0, 1.7, table_dtype=tdt)
     vals = synth.uniform_tables(L, 1 << log2_T, F, 6, dtype=tdt, scale=1.0)[0]
-    state = torch.from_numpy(pack_records(vals.reshape(-1, F), tdt)).cuda()
     dt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[tdt]
     dense = torch.from_numpy(vals).cuda().to(dt)
+    per_word = 4 // dense.element_size()
+    inter = torch.zeros((L << log2_T, 8 * per_word), dtype=dt, device="cuda")  # 32-byte entries
+    inter[:, 3 * per_word:3 * per_word + F] = dense.reshape(-1, F)
     x = torch.from_numpy(synth.uniform_points(4000, 3, 7)).cuda()
-    assert torch.equal(enc.encode_fwd_records(x, state), enc.encode_fwd(x, dense))
+    out = torch.empty((4000, L * F), dtype=dt, device="cuda")
+    st = _lib.lib().sxe_encode_fwd_strided(enc.handle, x.data_ptr(), 4000, inter.data_ptr() + 12, 8 * per_word,
+                                           out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    assert torch.equal(out, enc.encode_fwd(x, dense))
+
+
+def test_grouped_input_gradient_is_the_transpose():
+    """dL/din written grouped ([n_in/g][P][g]) equals the row-major result rearranged, bit for bit."""
+    from paper_2311_15439_gb300.api import Mlp
+    mlp = Mlp(32, 3, n_hidden=2, dtype="f16")
+    W = torch.from_numpy(mlp.init_weights(2)).half().cuda()
+    P = 3001
+    x = torch.from_numpy(synth.rng(3).uniform(-1, 1, (P, 32)).astype(np.float32)).half().cuda()
+    tgt = torch.from_numpy(synth.rng(4).random((P, 3)).astype(np.float32)).cuda()
+    d_rows = torch.empty((P, 32), device="cuda")
+    mlp.mlp_train_l2(W, x, tgt, torch.zeros(mlp.n_params, device="cuda"), torch.zeros(1, device="cuda"), din=d_rows)
+    for g in (1, 2, 4, 8):
+        d_g = torch.empty((32 // g, P, g), device="cuda")
+        mlp.mlp_train_l2_grouped(W, x, tgt, torch.zeros(mlp.n_params, device="cuda"), torch.zeros(1, device="cuda"),
+                                 d_g, g)
+        assert torch.equal(d_g.permute(1, 0, 2).reshape(P, 32), d_rows)
