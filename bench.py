@@ -122,14 +122,15 @@ def make_batches(n, seed0=1000):
 
 
 def _stage_work(n_touched, F=2, L=16, d=2, width=64, n_in=32):
-    """Algorithmic work of each timed stage of one step (stated in the design notes):
-    bytes for the memory-bound stages, FLOPs for the network."""
+    """Algorithmic work of each timed kernel of one step (stated in the design notes):
+    bytes for the memory-bound kernels, FLOPs for the network."""
     V = d + 1
-    per_pt_fwd = 4 * d + L * V * 2 * F + L * F * 2                 # x, fp16 gathers, fp16 encoding
-    table = BATCH * (4 * d + 4 * L * F) + n_touched * (2 * 16 * F + 2 * F)  # x, dL/d(enc); record r+w, fp16 copy
-    flops = 2 * (n_in * width + width * width + width * 16)       # forward MACs (output padded to 16)
-    flops = 3 * flops * BATCH                                     # forward + delta + weight-gradient GEMMs
-    return {"encode_fwd": ("hbm", per_pt_fwd * BATCH), "table_step": ("hbm", table),
+    fwd = BATCH * (4 * d + L * V * 2 * F + L * F * 2)              # x, fp16 gathers, fp16 encoding
+    bwd = BATCH * (4 * d + 4 * L * F + L * V * 2 * 4 * F)           # x, dL/d(enc), fp32 RMW per vertex
+    adam = n_touched * (2 * 16 * F + 2 * F) + L * (1 << 22) // 8    # record r+w, fp16 copy; bitmap scan
+    flops = 2 * (n_in * width + width * width + width * 16)        # forward MACs (output padded to 16)
+    flops = 3 * flops * BATCH                                      # forward + delta + weight-gradient GEMMs
+    return {"encode_fwd": ("hbm", fwd), "encode_bwd": ("hbm", bwd), "adam_tables": ("hbm", adam),
             "mlp_train_l2": ("tensor", flops)}
 
 
@@ -175,8 +176,9 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
 
     # ---- device-timed region: K steps, per-stage events on the launching stream
-    names = ["encode_fwd", "mlp_train_l2", "table_step", "adam_mlp"]
+    names = ["encode_fwd", "mlp_train_l2", "encode_bwd", "adam_tables", "adam_mlp"]
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    F = enc.n_features
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         if world > 1:
@@ -190,13 +192,15 @@ def run_gpu(args):
             e[0].record(stream)
             tr.enc.encode_fwd(x, tr.tables, tr.enc_out)
             e[1].record(stream)
-            tr.mlp.mlp_train_l2_grouped(tr.W_lowp, tr.enc_out, t, tr.dW, tr.sq_sum, tr.d_enc, tr.enc.n_features,
-                                        loss_scale=tr.loss_scale, workspace=tr.ws)
+            tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, t, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
+                                workspace=tr.ws)
             e[2].record(stream)
-            tr.enc.table_step(tr.adam_tables, tr.t, x, tr.d_enc, tr.state, tr.tables, tr.scratch, tr.touched)
+            tr.enc.encode_bwd(x, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
             e[3].record(stream)
-            tr.adam_mlp.step(tr.t, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
+            tr.adam_tables.step_touched(tr.t, tr.state, tr.touched, tr.tables, F)
             e[4].record(stream)
+            tr.adam_mlp.step(tr.t, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
+            e[5].record(stream)
         stop.record(stream)
         torch.cuda.synchronize(dev)
         if world > 1:

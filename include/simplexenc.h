@@ -108,15 +108,6 @@ sxe_status sxe_encoder_level_params(const sxe_encoder* enc, float* level_scale, 
 sxe_status sxe_encode_fwd(const sxe_encoder* enc, const float* x, int64_t n_points,
                           const void* tables, void* out, void* stream);
 
-/* sxe_encode_fwd reading the tables with an entry stride: entry (l, slot) starts at
- * element (l*T + slot) * table_stride of `tables` (desc.table_dtype).  table_stride = F
- * is the dense layout; sxe_table_step's state records are read with table_stride =
- * 4F binary32 words (8F elements of a 16-bit type) from the start of their copy field.
- * table_stride * element size must keep every entry aligned to min(16, F * element
- * size) bytes. */
-sxe_status sxe_encode_fwd_strided(const sxe_encoder* enc, const float* x, int64_t n_points,
-                                  const void* tables, int64_t table_stride, void* out, void* stream);
-
 /* Backward encoding, Sec. 5 step (e): for every point, level, vertex k and feature f,
  *   grad[(l*T + slot_k) * grad_stride + f] += w_k * dout[p][l*F + f]
  * with the same vertices and weights as the forward pass (recomputed).
@@ -281,26 +272,22 @@ sxe_status sxe_step_touched(const sxe_adam_desc* desc, int64_t t, int64_t n_entr
                             int32_t n_features, float* state, uint32_t* touched,
                             void* table_lowp, int32_t lowp_dtype, void* stream);
 
-/* Table update of one training step: Sec. 5 (e) (accumulate dL/d(encoding) into the
- * looked-up entries) followed by the Adam step of sxe_step with the zero-gradient skip
- * rule applied per parameter, and the refresh of the low-precision copy the forward pass
- * reads.  Same result as sxe_encode_bwd into zeroed gradients followed by sxe_step_touched.
- *   dout        dL/d(encoding) LEVEL-MAJOR: [L][n_points][F] binary32 (the layout
- *               sxe_mlp_train_l2_grouped writes with din_group = F).
- *   state       L*T records of 4F binary32 words {param[F], m[F], v[F], grad[F]}, the
- *               grad fields zero on entry and again on return.  16-byte aligned.
- *   table_lowp  dense [L][T][F] copy of the parameters in desc.table_dtype (rewritten for
- *               every entry that takes a step).
- *   scratch     [T][F] binary32, zero on entry and again on return.
- *   touched     L*T bits (uint32 words), zero on entry and again on return.
- * Levels whose lattice box (N_l+2)^d holds at most T/4 vertices are scattered into the
- * records' grad fields and stepped together; every finer level is scattered into the
- * scratch (reused by every level, so it stays in L2) and stepped from it, one level at a
- * time.  Needs T >= 32.  Launches 2 + 2 * (number of finer levels) kernels. */
-sxe_status sxe_table_step(const sxe_encoder* enc, const sxe_adam_desc* adam, int64_t t,
-                          const float* x, int64_t n_points, const float* dout,
-                          float* state, void* table_lowp, float* scratch, uint32_t* touched,
-                          void* stream);
+/* Which kernel runs the network's training pass (sxe_mlp_bwd, sxe_mlp_train_l2*),
+ * process-wide: SXE_MLP_KERNEL_MMA_SYNC (warp-level mma.sync for every product) or
+ * SXE_MLP_KERNEL_TCGEN05 (tcgen05.mma with TMEM accumulators for every product whose rows
+ * are points, mma.sync for the weight gradients).  SXE_MLP_KERNEL_AUTO picks the default.
+ * Both compute the same products in the same precision.  Not thread-safe: set it before
+ * launching work. */
+#define SXE_MLP_KERNEL_AUTO 0
+#define SXE_MLP_KERNEL_MMA_SYNC 1
+#define SXE_MLP_KERNEL_TCGEN05 2
+sxe_status sxe_mlp_set_kernel(int32_t kernel);
+int32_t sxe_mlp_get_kernel(void);
+
+/* Device-side failure word: nonzero once a bounded wait inside a kernel gave up (the
+ * kernel then left its loop, freed its tensor memory and returned; its outputs are not
+ * valid).  Synchronous; clears the word when `clear` is nonzero. */
+sxe_status sxe_device_error(int32_t* flag, int32_t clear);
 
 /* Thread-local message describing the last failing call on this thread ("" if none). */
 const char* sxe_last_error(void);

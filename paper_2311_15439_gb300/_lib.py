@@ -16,6 +16,7 @@ SXE_SIMPLEX, SXE_GRID = 0, 1
 SXE_F32, SXE_F16, SXE_BF16 = 0, 1, 2
 SXE_RES_RAW, SXE_RES_EQUAL_MEM = 0, 1
 SXE_MAX_LEVELS = 32
+SXE_MLP_KERNEL_AUTO, SXE_MLP_KERNEL_MMA_SYNC, SXE_MLP_KERNEL_TCGEN05 = 0, 1, 2
 
 #: every function the header declares (checked by the export test)
 EXPORTS = (
@@ -23,7 +24,8 @@ EXPORTS = (
     "sxe_encode_fwd", "sxe_encode_bwd", "sxe_encode_vertices", "sxe_encode_plain_fwd", "sxe_encode_plain_bwd",
     "sxe_mlp_n_params", "sxe_mlp_fwd", "sxe_mlp_bwd_workspace_bytes", "sxe_mlp_bwd", "sxe_mlp_train_l2",
     "sxe_loss_l2", "sxe_step", "sxe_step_touched", "sxe_last_error", "sxe_version",
-    "sxe_encode_fwd_strided", "sxe_table_step", "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped",
+    "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped",
+    "sxe_mlp_set_kernel", "sxe_mlp_get_kernel", "sxe_device_error",
 )
 
 
@@ -69,10 +71,11 @@ def _declare(L):
         "sxe_loss_l2": (i32, [vp, vp, i64, i32, vp, vp, vp]),
         "sxe_step": (i32, [A, i64, i64, vp, vp, vp, vp, vp, i32, vp]),
         "sxe_step_touched": (i32, [A, i64, i64, i32, vp, vp, vp, i32, vp]),
-        "sxe_encode_fwd_strided": (i32, [vp, vp, i64, vp, i64, vp, vp]),
-        "sxe_table_step": (i32, [vp, A, i64, vp, i64, vp, vp, vp, vp, vp, vp]),
         "sxe_mlp_train_l2_grouped": (i32, [M, vp, vp, vp, f32, i64, vp, i32, vp, vp, vp, i64, vp]),
         "sxe_mlp_train_l2_static": (i32, [M, vp, vp, vp, f32, i64, vp, vp, vp, vp]),
+        "sxe_mlp_set_kernel": (i32, [i32]),
+        "sxe_mlp_get_kernel": (i32, []),
+        "sxe_device_error": (i32, [ctypes.POINTER(i32), i32]),
         "sxe_last_error": (ctypes.c_char_p, []),
         "sxe_version": (ctypes.c_char_p, []),
     }

@@ -98,20 +98,6 @@ class Encoder:
                 "sxe_encode_fwd")
         return out
 
-    def table_step(self, adam: "Adam", t: int, x: torch.Tensor, dout_level_major: torch.Tensor, state: torch.Tensor,
-                   table_lowp: torch.Tensor, scratch: torch.Tensor, touched: torch.Tensor, stream=None):
-        """Table backward + Adam of one training step (``sxe_table_step``); dout is [L, P, F]."""
-        P, F = x.shape[0], self.n_features
-        _need(x, torch.float32, "x", (P, self.d))
-        _need(dout_level_major, torch.float32, "dout", (self.n_levels, P, F))
-        _need(state, torch.float32, "state", (self.n_levels * self.T, 4 * F))
-        _need(table_lowp, torch_dtype(self.table_dtype), "table_lowp", self.table_shape())
-        _need(scratch, torch.float32, "scratch", (self.T, F))
-        _need(touched, torch.int32, "touched", ((self.n_levels * self.T + 31) // 32,))
-        L.check(L.lib().sxe_table_step(self._h, ctypes.byref(adam.desc), int(t), _ptr(x), P, _ptr(dout_level_major),
-                                       _ptr(state), _ptr(table_lowp), _ptr(scratch), _ptr(touched),
-                                       _stream(stream)), "sxe_table_step")
-
     def encode_bwd(self, x: torch.Tensor, dout: torch.Tensor, grad: torch.Tensor, grad_stride: int | None = None,
                    touched: torch.Tensor | None = None, grad_offset: int = 0, stream=None):
         """grad += d(out)/d(tables)^T dout.  ``grad`` is a float32 tensor; entry (l, slot) starts at

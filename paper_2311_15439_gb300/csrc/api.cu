@@ -126,44 +126,6 @@ sxe_status sxe_encode_fwd(const sxe_encoder* e, const float* x, int64_t P, const
   return launch_encode_fwd(e, x, P, tables, out, (cudaStream_t)stream);
 }
 
-sxe_status sxe_encode_fwd_strided(const sxe_encoder* e, const float* x, int64_t P, const void* tables,
-                                  int64_t table_stride, void* out, void* stream) {
-  sxe_status st = check_points("encode_fwd_strided", e, x, P);
-  if (st != SXE_OK) return st;
-  if (P == 0) return SXE_OK;
-  if (!tables || !out) return set_error(SXE_EINVAL, "encode_fwd_strided: NULL tables or out");
-  const int F = e->desc.n_features;
-  const size_t es = dtype_size(e->desc.table_dtype);
-  const size_t ta = std::min<size_t>(16, F * es);
-  if (table_stride < F || table_stride > (1 << 20) || !aligned(tables, ta) || ((size_t)table_stride * es) % ta != 0)
-    return set_error(SXE_EINVAL, "encode_fwd_strided: table_stride=%lld must be >= F and keep entries %zu-byte aligned",
-                     (long long)table_stride, ta);
-  const size_t oa = F == 2 ? 2 * dtype_size(e->desc.out_dtype) : dtype_size(e->desc.out_dtype);
-  if (!aligned(out, oa)) return set_error(SXE_EINVAL, "encode_fwd_strided: out must be %zu-byte aligned", oa);
-  return launch_encode_fwd(e, x, P, tables, out, (cudaStream_t)stream, table_stride);
-}
-
-sxe_status sxe_table_step(const sxe_encoder* e, const sxe_adam_desc* adam, int64_t t, const float* x, int64_t P,
-                          const float* dout, float* state, void* table_lowp, float* scratch, uint32_t* touched,
-                          void* stream) {
-  sxe_status st = check_points("table_step", e, x, P);
-  if (st != SXE_OK) return st;
-  if (!adam || t < 1) return set_error(SXE_EINVAL, "table_step: NULL Adam description or step t < 1");
-  if (!(adam->lr >= 0.f) || !(adam->beta1 >= 0.f && adam->beta1 < 1.f) || !(adam->beta2 >= 0.f && adam->beta2 < 1.f) ||
-      !(adam->eps >= 0.f))
-    return set_error(SXE_EINVAL, "table_step: bad Adam hyper-parameters");
-  if (e->desc.log2_T < 5) return set_error(SXE_EUNSUPPORTED, "table_step: needs T >= 32 (log2_T >= 5)");
-  if (!state || !table_lowp || !scratch || !touched || (P > 0 && !dout))
-    return set_error(SXE_EINVAL, "table_step: NULL state, table, scratch, touched or dout");
-  const int F = e->desc.n_features;
-  const size_t ga = F == 1 ? 4 : F == 2 ? 8 : 16;
-  const size_t la = F == 2 ? 2 * dtype_size(e->desc.table_dtype) : dtype_size(e->desc.table_dtype);
-  if (!aligned(state, 16) || !aligned(scratch, ga) || !aligned(touched, 4) || !aligned(table_lowp, la) ||
-      (dout && !aligned(dout, F == 2 ? 8 : 4)))
-    return set_error(SXE_EINVAL, "table_step: misaligned buffer");
-  return launch_table_step(e, adam, t, x, P, dout, state, table_lowp, scratch, touched, (cudaStream_t)stream);
-}
-
 sxe_status sxe_encode_bwd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* grad,
                           int64_t grad_stride, uint32_t* touched, void* stream) {
   sxe_status st = check_points("encode_bwd", e, x, P);
@@ -297,6 +259,20 @@ sxe_status sxe_mlp_train_l2_grouped(const sxe_mlp_desc* d, const void* W, const 
   if (ws_bytes < need) return set_error(SXE_ENOMEM, "mlp_train_l2_grouped: workspace %lld < %lld bytes", (long long)ws_bytes, (long long)need);
   return launch_mlp_bwd(d, W, in, nullptr, target, loss_scale, P, din, dW, sq_sum, (float*)ws, mlp_grid_blocks(d, P),
                         (cudaStream_t)stream, din_group);
+}
+
+sxe_status sxe_mlp_set_kernel(int32_t k) {
+  if (k != SXE_MLP_KERNEL_AUTO && k != SXE_MLP_KERNEL_MMA_SYNC && k != SXE_MLP_KERNEL_TCGEN05)
+    return set_error(SXE_EINVAL, "mlp_set_kernel: unknown kernel %d", k);
+  g_mlp_kernel = k;
+  return SXE_OK;
+}
+
+int32_t sxe_mlp_get_kernel(void) { return g_mlp_kernel; }
+
+sxe_status sxe_device_error(int32_t* flag, int32_t clear) {
+  if (!flag) return set_error(SXE_EINVAL, "device_error: NULL flag");
+  return read_tc_error(flag, clear != 0);
 }
 
 sxe_status sxe_loss_l2(const float* y, const float* target, int64_t P, int32_t n_out, float* dy, float* sq_sum,

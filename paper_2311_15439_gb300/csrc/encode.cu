@@ -112,13 +112,7 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
   Item it = item_of(nl);
   if (it.p >= P) return;
   it.l += l0;
-  float xv[D];
-  load_point<D>(x, it.p, xv);
-  const uint32_t mask = (1u << prm.log2_T) - 1u;
-  uint32_t slot[V];
-  float w[V];
-  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
-  const int64_t lbase = (int64_t)it.l << prm.log2_T;
+  // issue the gradient and point loads first, the lattice arithmetic overlaps them
   float g[F];
   const float* pd = dout + (dout_level_major ? (int64_t)it.l * P + it.p : it.p * L + it.l) * F;
   if constexpr (F == 2) {
@@ -128,17 +122,32 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
 #pragma unroll
     for (int f = 0; f < F; ++f) g[f] = __ldg(pd + f);
   }
+  float xv[D];
+  load_point<D>(x, it.p, xv);
+  const uint32_t mask = (1u << prm.log2_T) - 1u;
+  uint32_t slot[V];
+  float w[V];
+  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
+  const int64_t lbase = (int64_t)it.l << prm.log2_T;
+  // all bitmap words in flight at once, then the (fire-and-forget) atomics, then the marks
+  uint32_t words[V];
+  if (touched) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) words[k] = __ldcg(touched + ((lbase + slot[k]) >> 5));
+  }
 #pragma unroll
   for (int k = 0; k < V; ++k) {
     float c[F];
 #pragma unroll
     for (int f = 0; f < F; ++f) c[f] = w[k] * g[f];
-    const int64_t e = lbase + slot[k];
-    atomic_add_entry<F>(grad + e * stride, c);
-    if (touched) {
+    atomic_add_entry<F>(grad + (lbase + slot[k]) * stride, c);
+  }
+  if (touched) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int64_t e = lbase + slot[k];
       const uint32_t bit = 1u << (uint32_t)(e & 31);
-      uint32_t* word = touched + (e >> 5);
-      if (!(__ldcg(word) & bit)) atomicOr(word, bit);
+      if (!(words[k] & bit)) atomicOr(touched + (e >> 5), bit);
     }
   }
 }

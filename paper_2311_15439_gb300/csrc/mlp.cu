@@ -463,6 +463,19 @@ __global__ void reduce_partials_kernel(const float* __restrict__ ws, int nb, int
   }
 }
 
+}  // namespace
+
+sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
+                             cudaStream_t s) {
+  const int rb = (int)std::min<int64_t>((n_params + 255) / 256, 1024);
+  reduce_partials_kernel<<<rb, 256, 0, s>>>(ws, nb, n_params, inv_scale, dW, sq_sum);
+  return check_launch("mlp_bwd_reduce");
+}
+
+int g_mlp_kernel = SXE_MLP_KERNEL_AUTO;
+
+namespace {
+
 int g_num_sms = 0;
 int num_sms();
 
@@ -600,6 +613,8 @@ sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, 
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                           const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
                           float* ws, int grid, cudaStream_t s, int din_group) {
+  if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05)
+    return launch_mlp_bwd_tc(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);
   return d->dtype == SXE_F16
              ? bwd_in<__half>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group)
              : bwd_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);

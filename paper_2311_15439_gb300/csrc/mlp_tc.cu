@@ -1,0 +1,485 @@
+// Tiny fully connected network, forward + L2 loss + backward, on the 5th-generation tensor
+// cores (tcgen05) -- Sec. 5 (d)-(e) and Sec. 6.1 of arXiv 2311.15439.
+//
+// One CTA (8 warps) owns one 128-point tile at a time (persistent loop).  The tile's row r is
+// TMEM lane r: every GEMM whose rows are points runs as tcgen05.mma with M = 128, fp16/bf16
+// operands from shared memory (core-matrix layout, see tc_ptx.cuh) and an fp32 accumulator
+// in TMEM, issued by one thread and completed through an mbarrier:
+//   forward   H_0 = relu(X W_0^T), H_h = relu(H_{h-1} W_h^T), Y = H_last W_out^T
+//   loss      dY = 2 (Y - target) / (P n_out) * loss_scale            (per row, in registers)
+//   backward  dH_last = (dY W_out) * [H_last > 0], dH_{h-1} = (dH_h W_h) * [H_{h-1} > 0],
+//             dX = dH_0 W_0
+// The epilogues read the accumulator with tcgen05.ld (warp w reads lanes 32 (w % 4)..+31,
+// half the columns each), apply ReLU / mask / loss, and write the next operand tile.
+// The weight gradients dW_l = Delta_l^T In_l reduce over the points, so their rows are not
+// points; they run as mma.sync m16n8k16 over the same shared-memory tiles (ldmatrix.trans)
+// while the last tcgen05 product of the tile is in flight, and accumulate across the
+// persistent loop in registers (per-CTA partials, summed in a fixed order afterwards).
+//
+// Every mbarrier wait is bounded: on timeout the kernel raises the device error word, all
+// threads leave the loop together, TMEM is freed and the kernel returns.
+#include <algorithm>
+#include <type_traits>
+
+#include "sxe_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace sxe {
+
+__device__ int g_tc_error;   // nonzero once a tensor-core wait timed out
+
+namespace {
+
+constexpr int kW = 64;
+constexpr int kM = 128;
+constexpr int kThreads = 256;
+constexpr uint32_t kWaitPolls = 1u << 26;
+constexpr uint32_t kTmemCols = 64;
+
+template <int N_IN, int NH>
+struct TcSmem {
+  static constexpr int X = 0;                                 // [128][N_IN]
+  static constexpr int H = X + kM * N_IN * 2;                 // NH x [128][64]
+  static constexpr int DH = H + NH * kM * kW * 2;             // NH x [128][64]
+  static constexpr int DY = DH + NH * kM * kW * 2;            // [128][16]
+  static constexpr int W0 = DY + kM * 16 * 2;                 // [64][N_IN]
+  static constexpr int WH = W0 + kW * N_IN * 2;               // (NH-1) x [64][64]
+  static constexpr int WO = WH + (NH - 1) * kW * kW * 2;      // [16][64]
+  static constexpr int WOT = WO + 16 * kW * 2;                // [64][16]
+  static constexpr int WHT = WOT + kW * 16 * 2;               // (NH-1) x [64][64]
+  static constexpr int W0T = WHT + (NH - 1) * kW * kW * 2;    // [N_IN][64]
+  static constexpr int END = W0T + N_IN * kW * 2;
+  static constexpr int N_WTILES = 8 + (NH - 1) * 32 + 4 * (N_IN / 8);
+  static constexpr int TILES_PER_WARP = (N_WTILES + 7) / 8;
+};
+
+template <typename T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+  __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+template <typename T> __device__ __forceinline__ float2 unpack2(uint32_t u);
+template <> __device__ __forceinline__ float2 unpack2<__half>(uint32_t u) {
+  return __half22float2(*reinterpret_cast<__half2*>(&u));
+}
+template <> __device__ __forceinline__ float2 unpack2<__nv_bfloat16>(uint32_t u) {
+  return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u));
+}
+
+template <typename T>
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  if constexpr (std::is_same<T, __half>::value) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  } else {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  }
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], uint32_t saddr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(saddr));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t& r0, uint32_t& r1, uint32_t saddr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(saddr));
+}
+
+// element (n, k) of a [N][K] core-matrix tile at `base`
+template <typename T>
+__device__ __forceinline__ T* cm(unsigned char* base, int n, int k, int K) {
+  return reinterpret_cast<T*>(base + tc::cm_offset(n, k, K));
+}
+
+// Write W (global [fan_out][fan_in]) as B operand [fan_out][fan_in] and its transpose
+// [fan_in][fan_out], rows of the output layer past n_out zero.
+template <typename T, int N_IN, int NH>
+__device__ void load_weights_cm(const T* __restrict__ W, int n_out, unsigned char* sm) {
+  using S = TcSmem<N_IN, NH>;
+  const T zero = from_f32<T>(0.f);
+  for (int i = threadIdx.x; i < kW * N_IN; i += blockDim.x) {
+    const int o = i / N_IN, c = i % N_IN;
+    const T v = W[i];
+    *cm<T>(sm + S::W0, o, c, N_IN) = v;
+    *cm<T>(sm + S::W0T, c, o, kW) = v;
+  }
+  const T* Wh = W + kW * N_IN;
+  for (int i = threadIdx.x; i < (NH - 1) * kW * kW; i += blockDim.x) {
+    const int h = i / (kW * kW), o = (i / kW) % kW, c = i % kW;
+    const T v = Wh[i];
+    *cm<T>(sm + S::WH + h * kW * kW * 2, o, c, kW) = v;
+    *cm<T>(sm + S::WHT + h * kW * kW * 2, c, o, kW) = v;
+  }
+  const T* Wo = Wh + (NH - 1) * kW * kW;
+  for (int i = threadIdx.x; i < 16 * kW; i += blockDim.x) {
+    const int o = i / kW, c = i % kW;
+    const T v = o < n_out ? Wo[o * kW + c] : zero;
+    *cm<T>(sm + S::WO, o, c, kW) = v;
+    *cm<T>(sm + S::WOT, c, o, 16) = v;
+  }
+}
+
+// row r, columns c0..c0+15 of a K-column core-matrix tile from 16 fp32 values
+template <typename T>
+__device__ __forceinline__ void store16(unsigned char* tile, int r, int c0, int K, const float (&v)[16]) {
+  uint4 lo, hi;
+  lo.x = pack2<T>(v[0], v[1]);   lo.y = pack2<T>(v[2], v[3]);   lo.z = pack2<T>(v[4], v[5]);   lo.w = pack2<T>(v[6], v[7]);
+  hi.x = pack2<T>(v[8], v[9]);   hi.y = pack2<T>(v[10], v[11]); hi.z = pack2<T>(v[12], v[13]); hi.w = pack2<T>(v[14], v[15]);
+  *reinterpret_cast<uint4*>(tile + tc::cm_offset(r, c0, K)) = lo;
+  *reinterpret_cast<uint4*>(tile + tc::cm_offset(r, c0 + 8, K)) = hi;
+}
+
+template <typename T>
+__device__ __forceinline__ void load16(const unsigned char* tile, int r, int c0, int K, float (&v)[16]) {
+  const uint4 lo = *reinterpret_cast<const uint4*>(tile + tc::cm_offset(r, c0, K));
+  const uint4 hi = *reinterpret_cast<const uint4*>(tile + tc::cm_offset(r, c0 + 8, K));
+  const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float2 f = unpack2<T>(w[j]);
+    v[2 * j] = f.x;
+    v[2 * j + 1] = f.y;
+  }
+}
+
+// D = A B^T over K (multiple of 16) from two core-matrix tiles (A: [128][K], B: [N][K])
+__device__ __forceinline__ void issue_gemm(uint32_t tmem, const unsigned char* A, const unsigned char* B, int K,
+                                           uint32_t idesc) {
+  const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+  const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B);
+  for (int ks = 0; ks < K / 16; ++ks)
+    tc::mma_f16(tmem, tc::smem_desc(a0 + ks * 256u, 128u, sbo), tc::smem_desc(b0 + ks * 256u, 128u, sbo), idesc,
+                ks > 0);
+}
+
+// MODE 0: dy = dout * loss_scale.  MODE 1: L2 loss against target.
+template <typename T, int N_IN, int NH, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+mlp_train_tc_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
+                    const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
+                    float* __restrict__ din, int din_group, float* __restrict__ ws, int64_t n_params) {
+  using S = TcSmem<N_IN, NH>;
+  constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sq_part[8];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  const int r = quad * 32 + lane;                       // this thread's tile row / TMEM lane
+  const int64_t n_tiles = (P + kM - 1) / kM;
+  const float inv_count = 2.f / (float)((double)P * n_out);
+  const float inv_scale = 1.f / loss_scale;
+
+  load_weights_cm<T, N_IN, NH>(W, n_out, sm);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  tc::fence_smem_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  float dw[S::TILES_PER_WARP][4];
+#pragma unroll
+  for (int i = 0; i < S::TILES_PER_WARP; ++i) dw[i][0] = dw[i][1] = dw[i][2] = dw[i][3] = 0.f;
+  float sq = 0.f;
+
+  // issue (one thread) after all operand writes, then every thread waits for the product
+  auto gemm = [&](const unsigned char* A, const unsigned char* B, int K, int N) -> bool {
+    tc::fence_smem_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      issue_gemm(tmem, A, B, K, tc::idesc_f16(kM, N, BF16));
+      tc::commit(&mbar);
+    }
+    const bool ok = tc::mbar_wait(&mbar, phase, kWaitPolls);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    return ok;
+  };
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kM;
+    // ---- stage the tile's inputs
+    for (int i = tid; i < kM * (N_IN / 8); i += kThreads) {
+      const int rr = i / (N_IN / 8), c = (i % (N_IN / 8)) * 8;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (row0 + rr < P) v = __ldg(reinterpret_cast<const uint4*>(in + (row0 + rr) * N_IN + c));
+      *reinterpret_cast<uint4*>(sm + S::X + tc::cm_offset(rr, c, N_IN)) = v;
+    }
+    // ---- forward
+    bool ok = true;
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      if (h == 0) ok = gemm(sm + S::X, sm + S::W0, N_IN, kW);
+      else ok = gemm(sm + S::H + (h - 1) * kM * kW * 2, sm + S::WH + (h - 1) * kW * kW * 2, kW, kW);
+      if (__syncthreads_or(!ok)) { failed = true; break; }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int c0 = half * 32 + c * 16;
+        float v[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+        store16<T>(sm + S::H + h * kM * kW * 2, r, c0, kW, v);
+      }
+    }
+    if (failed) break;
+    ok = gemm(sm + S::H + (NH - 1) * kM * kW * 2, sm + S::WO, kW, 16);
+    if (__syncthreads_or(!ok)) { failed = true; break; }
+    // ---- output delta (warps 0-3 hold the 16 output columns of their rows)
+    if (half == 0) {
+      float v[16];
+      tc::tmem_ld16(lane_addr, v);
+      const int64_t row = row0 + r;
+#pragma unroll
+      for (int o = 0; o < 16; ++o) {
+        float dyo = 0.f;
+        if (row < P && o < n_out) {
+          if (MODE == 0) {
+            dyo = dout[row * n_out + o] * loss_scale;
+          } else {
+            const float res = v[o] - target[row * n_out + o];
+            sq = fmaf(res, res, sq);
+            dyo = res * inv_count * loss_scale;
+          }
+        }
+        v[o] = dyo;
+      }
+      store16<T>(sm + S::DY, r, 0, 16, v);
+    }
+    // ---- hidden deltas, top layer down
+#pragma unroll
+    for (int h = NH - 1; h >= 0; --h) {
+      if (h == NH - 1) ok = gemm(sm + S::DY, sm + S::WOT, 16, kW);
+      else ok = gemm(sm + S::DH + (h + 1) * kM * kW * 2, sm + S::WHT + h * kW * kW * 2, kW, kW);
+      if (__syncthreads_or(!ok)) { failed = true; break; }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int c0 = half * 32 + c * 16;
+        float v[16], a[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+        load16<T>(sm + S::H + h * kM * kW * 2, r, c0, kW, a);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = a[j] > 0.f ? v[j] : 0.f;
+        store16<T>(sm + S::DH + h * kM * kW * 2, r, c0, kW, v);
+      }
+    }
+    if (failed) break;
+    // ---- dX = dH_0 W_0 on the tensor cores, weight gradients on mma.sync meanwhile
+    tc::fence_smem_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      issue_gemm(tmem, sm + S::DH, sm + S::W0T, kW, tc::idesc_f16(kM, N_IN, BF16));
+      tc::commit(&mbar);
+    }
+    {
+      const int g = lane >> 2, t = lane & 3, q = lane >> 3, rr = lane & 7;
+      (void)g; (void)t;
+#pragma unroll
+      for (int i = 0; i < S::TILES_PER_WARP; ++i) {
+        const int id = warp + i * 8;
+        if (id >= S::N_WTILES) break;
+        const unsigned char *Dl, *In;
+        int Kd, Ki, mt, nt;
+        if (id < 8) {
+          Dl = sm + S::DY; Kd = 16; In = sm + S::H + (NH - 1) * kM * kW * 2; Ki = kW; mt = 0; nt = id;
+        } else if (id < 8 + (NH - 1) * 32) {
+          const int j = id - 8, h = 1 + j / 32, rem = j % 32;
+          Dl = sm + S::DH + h * kM * kW * 2; Kd = kW; In = sm + S::H + (h - 1) * kM * kW * 2; Ki = kW;
+          mt = rem / 8; nt = rem % 8;
+        } else {
+          const int j = id - 8 - (NH - 1) * 32;
+          Dl = sm + S::DH; Kd = kW; In = sm + S::X; Ki = N_IN; mt = j / (N_IN / 8); nt = j % (N_IN / 8);
+        }
+        const uint32_t dl = tc::smem_u32(Dl), il = tc::smem_u32(In);
+#pragma unroll
+        for (int ks = 0; ks < kM / 16; ++ks) {
+          uint32_t a[4], b0, b1;
+          ldsm_x4_trans(a, dl + tc::cm_offset(ks * 16 + (q >> 1) * 8 + rr, mt * 16 + (q & 1) * 8, Kd));
+          ldsm_x2_trans(b0, b1, il + tc::cm_offset(ks * 16 + (q & 1) * 8 + rr, nt * 8, Ki));
+          mma16816<T>(dw[i], a, b0, b1);
+        }
+      }
+    }
+    ok = tc::mbar_wait(&mbar, phase, kWaitPolls);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (__syncthreads_or(!ok)) { failed = true; break; }
+    // ---- input gradient
+    {
+      constexpr int PER_WARP = N_IN / 2;          // columns per warp half (16 or 32; 8 -> one half)
+      const int64_t row = row0 + r;
+      if (N_IN >= 32 || half == 0) {
+#pragma unroll
+        for (int c = 0; c < (N_IN >= 32 ? PER_WARP / 16 : 1); ++c) {
+          const int c0 = (N_IN >= 32 ? half * PER_WARP : 0) + c * 16;
+          float v[16];
+          tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+          if (din && row < P) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+              const int col = c0 + j;
+              const float2 val = make_float2(v[j] * inv_scale, v[j + 1] * inv_scale);
+              if (din_group == 0) {
+                *reinterpret_cast<float2*>(din + row * N_IN + col) = val;
+              } else if (din_group == 1) {
+                din[(int64_t)col * P + row] = val.x;
+                din[(int64_t)(col + 1) * P + row] = val.y;
+              } else {
+                *reinterpret_cast<float2*>(din + ((int64_t)(col / din_group) * P + row) * din_group + col % din_group) = val;
+              }
+            }
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+
+  // ---- per-CTA partials (all threads reach this point together)
+  if (failed && tid == 0) atomicExch(&g_tc_error, 1);
+  float* wsb = ws + (int64_t)blockIdx.x * n_params;
+  const int off_h = kW * N_IN;
+  const int off_o = off_h + (NH - 1) * kW * kW;
+  {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int i = 0; i < S::TILES_PER_WARP; ++i) {
+      const int id = warp + i * 8;
+      if (id >= S::N_WTILES) break;
+      int base, fan_in, mt, nt, rows;
+      if (id < 8) { base = off_o; fan_in = kW; mt = 0; nt = id; rows = n_out; }
+      else if (id < 8 + (NH - 1) * 32) {
+        const int j = id - 8, h = 1 + j / 32, rem = j % 32;
+        base = off_h + (h - 1) * kW * kW; fan_in = kW; mt = rem / 8; nt = rem % 8; rows = kW;
+      } else {
+        const int j = id - 8 - (NH - 1) * 32;
+        base = 0; fan_in = N_IN; mt = j / (N_IN / 8); nt = j % (N_IN / 8); rows = kW;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = mt * 16 + g + (e >> 1) * 8, n = nt * 8 + 2 * t + (e & 1);
+        if (m < rows) wsb[base + m * fan_in + n] = dw[i][e];
+      }
+    }
+  }
+  if (MODE == 1) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) sq_part[warp] = sq;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (MODE == 1 && tid == 0) {
+    float s = 0.f;
+    for (int w = 0; w < 8; ++w) s += sq_part[w];
+    ws[(int64_t)gridDim.x * n_params + blockIdx.x] = s;
+  }
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+}  // namespace
+}  // namespace sxe
+
+namespace sxe {
+namespace {
+
+template <typename T, int N_IN, int NH, int MODE>
+int tc_ctas_per_sm() {
+  static int cached = 0;
+  if (cached == 0) {
+    auto k = mlp_train_tc_kernel<T, N_IN, NH, MODE>;
+    const int bytes = TcSmem<N_IN, NH>::END;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, bytes) != cudaSuccess || n < 1) n = 1;
+    cached = n;
+  }
+  return cached;
+}
+
+template <typename T, int N_IN, int NH>
+sxe_status tc_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                     float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+  const int bytes = TcSmem<N_IN, NH>::END;
+  const int64_t n_params = sxe_mlp_n_params(d);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (target) {
+    grid = std::min(grid, sms * tc_ctas_per_sm<T, N_IN, NH, 1>());
+    mlp_train_tc_kernel<T, N_IN, NH, 1><<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
+                                                                     target, ls, din, dg, ws, n_params);
+  } else {
+    grid = std::min(grid, sms * tc_ctas_per_sm<T, N_IN, NH, 0>());
+    mlp_train_tc_kernel<T, N_IN, NH, 0><<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
+                                                                     target, ls, din, dg, ws, n_params);
+  }
+  sxe_status st = check_launch("mlp_train_tc");
+  if (st != SXE_OK) return st;
+  return launch_mlp_reduce(ws, grid, n_params, 1.f / ls, dW, target ? sq : nullptr, s);
+}
+
+template <typename T, int N_IN>
+sxe_status tc_nh(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+  switch (d->n_hidden) {
+    case 1: return tc_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    case 2: return tc_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    default: return tc_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+  }
+}
+
+template <typename T>
+sxe_status tc_in(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+  switch (d->n_in) {
+    case 16: return tc_nh<T, 16>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    case 32: return tc_nh<T, 32>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    default: return tc_nh<T, 64>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+  }
+}
+
+}  // namespace
+
+sxe_status launch_mlp_bwd_tc(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
+                             const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
+                             float* ws, int grid, cudaStream_t s, int din_group) {
+  return d->dtype == SXE_F16
+             ? tc_in<__half>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s)
+             : tc_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s);
+}
+
+sxe_status read_tc_error(int32_t* flag, bool clear) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int));
+  if (e == cudaSuccess && clear) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
+  }
+  if (e != cudaSuccess) return set_error(SXE_ECUDA, "device_error: %s", cudaGetErrorString(e));
+  *flag = v;
+  return SXE_OK;
+}
+
+}  // namespace sxe

@@ -31,34 +31,15 @@ __global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p,
   }
 }
 
-template <int F>
-__device__ __forceinline__ void adam_record(const AdamConst& k, float* state, int64_t e, void* lowp, int ldt) {
-  constexpr int NV = F;                            // float4 vectors per record of 4F floats
-  float4* rec = reinterpret_cast<float4*>(state + e * (4 * F));
-  union { float4 v[NV]; float f[4 * F]; } r;
-#pragma unroll
-  for (int j = 0; j < NV; ++j) r.v[j] = rec[j];
-  float p[F];
-#pragma unroll
-  for (int f = 0; f < F; ++f) {
-    float pp = r.f[f], mm = r.f[F + f], vv = r.f[2 * F + f];
-    const float g = r.f[3 * F + f];
-    if (g != 0.f) adam_one(k, g, pp, mm, vv);
-    r.f[f] = pp; r.f[F + f] = mm; r.f[2 * F + f] = vv; r.f[3 * F + f] = 0.f;
-    p[f] = pp;
-  }
-#pragma unroll
-  for (int j = 0; j < NV; ++j) rec[j] = r.v[j];
-  store_lowp<F>(lowp, e, ldt, p);
-}
-
-// A warp reads 32 consecutive bitmap words at once (one per lane, coalesced), then visits
-// only the nonzero ones: for each, the 32 lanes take the word's 32 entries and the marked
-// lanes update their records.  Each lane clears the word it loaded.  Bounded grid.
+// A warp reads 32 consecutive bitmap words at once (one per lane, coalesced) and visits
+// only the nonzero ones, the 32 lanes taking a word's 32 entries.  Up to NB nonzero words are
+// handled together: all their marked records are loaded before any is updated, so a warp
+// keeps NB record loads in flight instead of one.  Each lane clears the word it loaded.
 template <int F>
 __global__ void __launch_bounds__(256)
 adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state, uint32_t* __restrict__ touched,
                     void* __restrict__ lowp, int ldt) {
+  constexpr int NB = F <= 2 ? 4 : (F == 4 ? 2 : 1);
   const int lane = threadIdx.x & 31;
   const int64_t n_words = (n_entries + 31) >> 5;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -68,11 +49,42 @@ adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state, u
     const uint32_t mine = wi < n_words ? touched[wi] : 0u;
     uint32_t todo = __ballot_sync(0xffffffffu, mine != 0u);
     while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1u;
-      const uint32_t bits = __shfl_sync(0xffffffffu, mine, src);
-      const int64_t e = ((w0 + src) << 5) + lane;
-      if (((bits >> lane) & 1u) && e < n_entries) adam_record<F>(k, state, e, lowp, ldt);
+      int64_t e[NB];
+      bool on[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int src = todo ? __ffs(todo) - 1 : 0;
+        const uint32_t bits = __shfl_sync(0xffffffffu, mine, src);
+        on[b] = todo != 0u && ((bits >> lane) & 1u);
+        todo &= todo ? todo - 1u : 0u;
+        e[b] = ((w0 + src) << 5) + lane;
+        on[b] = on[b] && e[b] < n_entries;
+      }
+      union Rec { float4 v[F]; float f[4 * F]; } r[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (on[b]) {
+          const float4* rec = reinterpret_cast<const float4*>(state + e[b] * (4 * F));
+#pragma unroll
+          for (int j = 0; j < F; ++j) r[b].v[j] = rec[j];
+        }
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (on[b]) {
+          float p[F];
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            float pp = r[b].f[f], mm = r[b].f[F + f], vv = r[b].f[2 * F + f];
+            const float g = r[b].f[3 * F + f];
+            if (g != 0.f) adam_one(k, g, pp, mm, vv);
+            r[b].f[f] = pp; r[b].f[F + f] = mm; r[b].f[2 * F + f] = vv; r[b].f[3 * F + f] = 0.f;
+            p[f] = pp;
+          }
+          float4* rec = reinterpret_cast<float4*>(state + e[b] * (4 * F));
+#pragma unroll
+          for (int j = 0; j < F; ++j) rec[j] = r[b].v[j];
+          store_lowp<F>(lowp, e[b], ldt, p);
+        }
     }
     if (mine) touched[wi] = 0u;
   }

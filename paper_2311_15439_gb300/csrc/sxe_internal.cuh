@@ -45,10 +45,6 @@ sxe_status check_launch(const char* what);
 // launchers (defined in encode.cu / mlp.cu / optim.cu); arguments already validated
 sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
                              void* out, cudaStream_t s, int64_t table_stride = 0);
-sxe_status launch_table_step(const sxe_encoder* enc, const sxe_adam_desc* adam, int64_t t, const float* x,
-                             int64_t P, const float* dout_lm, float* state, void* table_lowp, float* scratch,
-                             uint32_t* touched, cudaStream_t s);
-int table_step_coarse_levels(const sxe_encoder* enc);
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
                              float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s,
                              int level_begin = 0, int n_levels = -1, bool dout_level_major = false);
@@ -63,6 +59,13 @@ sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, 
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                           const float* target, float loss_scale, int64_t P, float* din, float* dW,
                           float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group = 0);
+sxe_status launch_mlp_bwd_tc(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
+                             const float* target, float loss_scale, int64_t P, float* din, float* dW,
+                             float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group);
+sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
+                             cudaStream_t s);
+sxe_status read_tc_error(int32_t* flag, bool clear);
+extern int g_mlp_kernel;
 sxe_status launch_loss_l2(const float* y, const float* target, int64_t P, int32_t n_out, float* dy,
                           float* sq_sum, cudaStream_t s);
 sxe_status launch_adam_dense(const sxe_adam_desc* a, int64_t t, int64_t n, float* p, float* m, float* v,

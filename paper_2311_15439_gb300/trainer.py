@@ -3,25 +3,25 @@
 One ``step(x, target)`` runs, on the caller's stream and entirely in libsimplexenc
 kernels:
 
-1. ``sxe_encode_fwd``           -- multiresolution encoding of the batch from the dense
-                                   low-precision tables (Sec. 5 a-d);
-2. ``sxe_mlp_train_l2_grouped`` -- network forward, L2 loss, network backward; dL/d(encoding)
-                                   written level-major [L][P][F] (Sec. 5 d-e);
-3. ``sxe_table_step``           -- scatter of dL/d(encoding) into the tables and Adam with the
-                                   zero-gradient skip rule on the touched entries, refreshing the
-                                   low-precision tables (Sec. 5 e);
-4. ``sxe_step``                 -- Adam on the network weights, refreshing their fp16 copy.
+1. ``sxe_encode_fwd``   -- multiresolution encoding of the batch from the low-precision
+                           tables (Sec. 5 a-d);
+2. ``sxe_mlp_train_l2`` -- network forward, L2 loss, network backward, dL/d(encoding)
+                           (Sec. 5 d-e);
+3. ``sxe_encode_bwd``   -- scatter-add of dL/d(encoding) into the gradient field of the
+                           interleaved table state, marking touched entries (Sec. 5 e);
+4. ``sxe_step_touched`` -- Adam on the marked table entries (zero-gradient skip rule),
+                           refreshing the low-precision tables;
+5. ``sxe_step``         -- Adam on the network weights, refreshing their low-precision copy.
 
-Table state in HBM: one record of 4F binary32 words per entry {param[F], m[F], v[F], grad[F]},
-entries ordered [level][slot] (32 bytes = one DRAM sector for F = 2); a dense [L][T][F]
-low-precision copy for the forward gathers; a [T][F] binary32 scratch and an L*T-bit touched
-bitmap, both zero between steps.
+Table state layout in HBM: one binary32 record {param[F], m[F], v[F], grad[F]} per entry
+(32 bytes for F = 2: one DRAM sector), entries ordered [level][slot]; a separate dense
+[L][T][F] low-precision copy is what the forward pass gathers from; a bitmap of L*T bits
+marks the entries that received a gradient in the current step.
 """
 from __future__ import annotations
 
 import math
 
-import numpy as np
 import torch
 
 from . import synth
@@ -31,23 +31,6 @@ from .api import Adam, Encoder, Mlp, torch_dtype
 def default_loss_scale(P: int, n_out: int) -> float:
     """Power of two near P*n_out/2 so that the scaled L2 gradient 2 r / (P n_out) is O(r)."""
     return float(2.0 ** max(0, math.floor(math.log2(max(1.0, P * n_out / 2.0)))))
-
-
-def pack_records(values: np.ndarray) -> np.ndarray:
-    """State records {param, m = 0, v = 0, grad = 0} for binary32 parameters [n, F]."""
-    n, F = values.shape
-    rec = np.zeros((n, 4 * F), dtype=np.float32)
-    rec[:, :F] = values
-    return rec
-
-
-def lowp_copy(values: np.ndarray, table_dtype: str):
-    """The table-dtype rounding of binary32 values as a torch tensor (host)."""
-    if table_dtype == "f32":
-        return torch.from_numpy(values.copy())
-    if table_dtype == "f16":
-        return torch.from_numpy(values.astype(np.float16))
-    return torch.from_numpy(synth.fp32_to_bf16_bits(values).view(np.int16)).view(torch.bfloat16)
 
 
 class Trainer:
@@ -61,10 +44,10 @@ class Trainer:
         n_entries = encoder.n_levels * encoder.T
         # seeded host values U(-table_init, table_init), so any checker can regenerate them
         vals = synth.uniform_tables(encoder.n_levels, encoder.T, F, seed, dtype="f32", scale=table_init)[0]
-        self.state = torch.from_numpy(pack_records(vals.reshape(n_entries, F))).to(self.device)
-        self.tables = lowp_copy(vals, encoder.table_dtype).to(self.device)
-        del vals
-        self.scratch = torch.zeros((encoder.T, F), dtype=torch.float32, device=self.device)
+        init = torch.from_numpy(vals.reshape(n_entries, F)).to(self.device)
+        self.state = torch.zeros((n_entries, 4 * F), dtype=torch.float32, device=self.device)
+        self.state[:, :F] = init
+        self.tables = init.to(torch_dtype(encoder.table_dtype)).reshape(encoder.table_shape()).contiguous()
         self.touched = torch.zeros(((n_entries + 31) // 32,), dtype=torch.int32, device=self.device)
         W0 = torch.from_numpy(mlp.init_weights(seed + 1)).to(self.device)
         self.W = W0.clone()
@@ -73,7 +56,7 @@ class Trainer:
         self.vW = torch.zeros_like(W0)
         self.dW = torch.zeros_like(W0)
         self.enc_out = torch.empty((batch, encoder.n_out), dtype=torch_dtype(encoder.out_dtype), device=self.device)
-        self.d_enc = torch.empty((encoder.n_levels, batch, F), dtype=torch.float32, device=self.device)
+        self.d_enc = torch.empty((batch, encoder.n_out), dtype=torch.float32, device=self.device)
         self.sq_sum = torch.zeros((1,), dtype=torch.float32, device=self.device)
         self.ws = mlp.workspace(batch, self.device)
         self.loss_scale = default_loss_scale(batch, mlp.n_out)
@@ -83,42 +66,25 @@ class Trainer:
 
     @property
     def n_launches_per_step(self) -> int:
-        # encode, network train + its partial reduction, table step, network Adam
-        lc = sum(1 for N in self.enc.level_params()[1] if (int(N) + 2.0) ** self.enc.d <= self.enc.T / 4.0)
-        table = (2 if lc > 0 else 0) + 2 * (self.enc.n_levels - lc)
-        return 4 + table
-
-    def forward_and_grads(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
-        """Encode and run the network with its L2 loss and backward pass (stages 1-2)."""
-        self.enc.encode_fwd(x, self.tables, self.enc_out, stream=stream)
-        self.mlp.mlp_train_l2_grouped(self.W_lowp, self.enc_out, target, self.dW, self.sq_sum, self.d_enc,
-                                      self.enc.n_features, loss_scale=self.loss_scale, workspace=self.ws,
-                                      stream=stream)
-
-    def apply_updates(self, x: torch.Tensor, stream=None) -> None:
-        """Table update and network Adam step (stages 3-4)."""
-        self.enc.table_step(self.adam_tables, self.t, x, self.d_enc, self.state, self.tables, self.scratch,
-                            self.touched, stream=stream)
-        self.adam_mlp.step(self.t, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=stream)
+        return 6   # encode_fwd, mlp train, its partial reduction, encode_bwd, table Adam, network Adam
 
     def step(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
         """One optimisation step on batch (x [P, d] float32, target [P, n_out] float32); asynchronous."""
+        F = self.enc.n_features
         self.t += 1
-        self.forward_and_grads(x, target, stream)
-        self.apply_updates(x, stream)
+        self.enc.encode_fwd(x, self.tables, self.enc_out, stream=stream)
+        self.mlp.mlp_train_l2(self.W_lowp, self.enc_out, target, self.dW, self.sq_sum, din=self.d_enc,
+                              loss_scale=self.loss_scale, workspace=self.ws, stream=stream)
+        self.enc.encode_bwd(x, self.d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F, touched=self.touched,
+                            stream=stream)
+        self.adam_tables.step_touched(self.t, self.state, self.touched, self.tables, F, stream=stream)
+        self.adam_mlp.step(self.t, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=stream)
 
     def loss(self) -> float:
         """Mean squared error of the last step (synchronises)."""
         return float(self.sq_sum.item()) / (self.P * self.mlp.n_out)
 
     def table_params(self) -> torch.Tensor:
-        """binary32 master table parameters as [L*T, F] (a view)."""
-        return self.state[:, :self.enc.n_features]
-
-    def table_lowp(self) -> torch.Tensor:
-        """The dense low-precision tables the forward pass reads, [L, T, F]."""
-        return self.tables
-
-    def d_enc_rows(self) -> torch.Tensor:
-        """dL/d(encoding) of the last step in the [P, L*F] layout of ``sxe_encode_bwd``."""
-        return self.d_enc.permute(1, 0, 2).reshape(self.P, -1).contiguous()
+        """binary32 master table parameters as [L, T, F]."""
+        F = self.enc.n_features
+        return self.state[:, :F].reshape(self.enc.table_shape())

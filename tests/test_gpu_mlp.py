@@ -83,6 +83,25 @@ def within(got, want, den, tol, slack=0.0):
     return float(np.max(err / np.maximum(bound, 1e-300)))
 
 
+@pytest.fixture(params=["mma_sync", "tcgen05"])
+def mlp_kernel(request, cuda_lib):
+    """Run the test with the network's training pass on each kernel; afterwards no bounded
+    device wait may have given up."""
+    import ctypes
+    L = cuda_lib
+    code = {"mma_sync": L.SXE_MLP_KERNEL_MMA_SYNC, "tcgen05": L.SXE_MLP_KERNEL_TCGEN05}[request.param]
+    prev = L.lib().sxe_mlp_get_kernel()
+    assert L.lib().sxe_mlp_set_kernel(code) == 0
+    try:
+        yield request.param
+        torch.cuda.synchronize()
+        flag = ctypes.c_int32(0)
+        assert L.lib().sxe_device_error(ctypes.byref(flag), 1) == 0
+        assert flag.value == 0
+    finally:
+        L.lib().sxe_mlp_set_kernel(prev)
+
+
 # (n_in, n_hidden, n_out, dtype, P)
 NETS = [(32, 2, 3, "f16", 4099), (32, 2, 3, "bf16", 2000), (32, 1, 1, "bf16", 3333), (16, 3, 16, "f16", 1000),
         (64, 1, 5, "f16", 257), (32, 2, 3, "f16", 1 << 16)]
@@ -115,7 +134,7 @@ def test_forward(cuda_lib, net):
 
 
 @pytest.mark.parametrize("net", NETS, ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
-def test_backward(cuda_lib, net):
+def test_backward(cuda_lib, net, mlp_kernel):
     mlp, Wd, Ws, xd, x = _setup(net, seed=5)
     nh, dt = net[1], net[3]
     dy = synth.normal_grads(x.shape[0], net[2], 9).astype(np.float64)
@@ -133,7 +152,7 @@ def test_backward(cuda_lib, net):
     assert within(din.cpu().numpy(), din_ref, din_den, tol, din_sl) <= 1.0
 
 
-def test_backward_accumulates_and_is_deterministic(cuda_lib):
+def test_backward_accumulates_and_is_deterministic(cuda_lib, mlp_kernel):
     mlp, Wd, Ws, xd, x = _setup((32, 2, 3, "f16", 5000), seed=3)
     dy = torch.from_numpy(synth.normal_grads(5000, 3, 4)).cuda()
     a = torch.zeros((mlp.n_params,), device="cuda")
@@ -146,7 +165,7 @@ def test_backward_accumulates_and_is_deterministic(cuda_lib):
 
 
 @pytest.mark.parametrize("net", [NETS[0], NETS[2], NETS[5]], ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
-def test_train_l2(cuda_lib, net):
+def test_train_l2(cuda_lib, net, mlp_kernel):
     """Fused forward + L2 loss + backward equals the oracle's loss and gradients, with the
     gradient scaled by a power of two before the fp16 rounding and unscaled after."""
     from paper_2311_15439_gb300.trainer import default_loss_scale
@@ -241,3 +260,33 @@ def test_adam_touched(cuda_lib, F, dt):
     assert np.all(s[:, 3 * F:] == 0)
     assert torch.all(touched == 0)
     assert torch.equal(table[torch.from_numpy(marked).cuda()], state[:, :F][torch.from_numpy(marked).cuda()].to(tdt))
+
+
+@pytest.mark.parametrize("net", [NETS[0], NETS[1], NETS[3], NETS[4]], ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
+def test_tcgen05_and_mma_sync_agree(cuda_lib, net):
+    """The two kernels compute the same products in the same precision: their gradients
+    differ only by binary32 accumulation order (and the rare ReLU decision at a rounding tie)."""
+    import ctypes
+    L = cuda_lib
+    mlp, Wd, Ws, xd, x = _setup(net, seed=31)
+    dy = torch.from_numpy(synth.normal_grads(x.shape[0], net[2], 32)).cuda()
+    outs = {}
+    prev = L.lib().sxe_mlp_get_kernel()
+    try:
+        for k in (L.SXE_MLP_KERNEL_MMA_SYNC, L.SXE_MLP_KERNEL_TCGEN05):
+            assert L.lib().sxe_mlp_set_kernel(k) == 0
+            dW = torch.zeros((mlp.n_params,), device="cuda")
+            din = torch.empty((x.shape[0], net[0]), device="cuda")
+            mlp.mlp_bwd(Wd, xd, dy, dW, din=din)
+            outs[k] = (dW.cpu().numpy(), din.cpu().numpy())
+    finally:
+        L.lib().sxe_mlp_set_kernel(prev)
+    flag = ctypes.c_int32(0)
+    assert L.lib().sxe_device_error(ctypes.byref(flag), 1) == 0 and flag.value == 0
+    _, dW_den, din_den = _dens(Ws, x, dy.cpu().numpy().astype(np.float64))
+    dW_sl, din_sl = flip_slack(Ws, x, dy.cpu().numpy().astype(np.float64), U[net[3]])
+    tol = (2 * net[1] + 2) * U[net[3]]
+    a, b = outs[L.SXE_MLP_KERNEL_MMA_SYNC], outs[L.SXE_MLP_KERNEL_TCGEN05]
+    for i, (ga, gb) in enumerate(zip(mlp.split(a[0]), mlp.split(b[0]))):
+        assert within(gb, ga, dW_den[i], tol, 2 * dW_sl[i]) <= 1.0, "layer %d" % i
+    assert within(b[1], a[1], din_den, tol, 2 * din_sl) <= 1.0

@@ -42,12 +42,12 @@ def test_one_step_matches_oracle():
     W = [w.astype(np.float16).astype(np.float64) for w in tr.mlp.split(W0)]
 
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda()
-    # encode + network stages; the table gradient they imply is read out with the dense
-    # backward entry point before the optimiser consumes it
-    tr.forward_and_grads(xd, td)
-    dense = torch.zeros((L, T, F), device="cuda")
-    tr.enc.encode_bwd(xd, tr.d_enc_rows(), dense)
-    g_tab = dense.reshape(L * T, F).cpu().numpy()
+    # run the first three stages of the step and stop before the optimiser
+    tr.enc.encode_fwd(xd, tr.tables, tr.enc_out)
+    tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, td, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
+                        workspace=tr.ws)
+    tr.enc.encode_bwd(xd, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
+    g_tab = tr.state[:, 3 * F:].cpu().numpy().copy()
     g_W = tr.dW.cpu().numpy().copy()
     loss_gpu = tr.loss()
 
@@ -81,17 +81,15 @@ def test_one_step_matches_oracle():
 
     # optimiser: Adam at t = 1 moves each parameter by -lr * g / (|g| + eps); compare where the
     # sign of the gradient is unambiguous (|g_ref| well above the tolerance)
-    tr.t = 1
-    tr.apply_updates(xd)
-    assert torch.all(tr.scratch == 0) and torch.all(tr.touched == 0)
-    assert torch.equal(tr.table_lowp().reshape(L * T, F), tr.table_params().half())
+    tr.adam_tables.step_touched(1, tr.state, tr.touched, tr.tables, F)
+    tr.adam_mlp.step(1, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
     hp = dict(lr=float(np.float32(1e-2)), beta1=float(np.float32(0.9)), beta2=float(np.float32(0.99)),
               eps=float(np.float32(1e-15)))
     g_all = np.concatenate([g_ref[l] for l in range(L)])
     den_all = np.concatenate([den_bound[l] for l in range(L)])
     p_ref, _, _ = OA.adam_step(p_tab0, g_all, np.zeros_like(g_all), np.zeros_like(g_all), 1, skip_zero_grad=True, **hp)
     clear = ((np.abs(g_all) > 4 * tol * den_all) | (den_all == 0)) & ~shaky
-    p_gpu = tr.table_params().cpu().numpy()
+    p_gpu = tr.state[:, :F].cpu().numpy()
     np.testing.assert_allclose(p_gpu[clear], p_ref[clear], rtol=0, atol=2e-6)
     assert (clear & (den_all > 0)).sum() > 200           # the comparison covers many updated entries
     gW_ref = np.concatenate([a.ravel() for a in dW_ref])
@@ -188,78 +186,6 @@ def test_autograd_mlp_matches_oracle():
     for a, b, den, sl in zip(mlp.split(W.grad.float().cpu().numpy()), dW_ref, dW_den, dW_sl):
         assert within(a, b, den, tol, sl) <= 1.0
     assert within(x.grad.float().cpu().numpy(), din_ref, din_den, tol, din_sl) <= 1.0
-
-
-@pytest.mark.parametrize("kind,d,F,tdt", [("simplex", 2, 2, "f16"), ("simplex", 3, 2, "bf16"), ("grid", 3, 2, "f16"),
-                                          ("simplex", 4, 1, "f32"), ("simplex", 2, 4, "f16"), ("simplex", 5, 8, "f32")])
-def test_table_step_matches_oracle(kind, d, F, tdt):
-    """The table step (coarse levels through the records, finer levels through the L2 scratch)
-    equals the oracle's gradient followed by the zero-gradient skip-rule Adam of every table
-    parameter; grad fields, scratch and bitmap end zero; the low-precision tables hold the
-    rounded parameters; untouched records are unchanged."""
-    from paper_2311_15439_gb300.api import Adam, Encoder
-    from paper_2311_15439_gb300.build import build
-    from paper_2311_15439_gb300.trainer import lowp_copy, pack_records
-    build()
-    L, log2_T, P = 5, 12, 3000
-    T = 1 << log2_T
-    enc = Encoder(d, L, F, log2_T, 8.0, 1.6, kind=kind, table_dtype=tdt, out_dtype="f32")
-    g = synth.rng(3)
-    p0 = g.standard_normal((L * T, F)).astype(np.float32) * 0.1
-    m0 = (g.standard_normal((L * T, F)) * 0.01).astype(np.float32)
-    v0 = g.uniform(0.01, 0.1, (L * T, F)).astype(np.float32)
-    rec = pack_records(p0)
-    rec[:, F:2 * F] = m0
-    rec[:, 2 * F:3 * F] = v0
-    state = torch.from_numpy(rec).cuda()
-    table = lowp_copy(p0.reshape(L, T, F), tdt).cuda()
-    scratch = torch.zeros((T, F), device="cuda")
-    touched = torch.zeros((L * T // 32,), dtype=torch.int32, device="cuda")
-    x = synth.uniform_points(P, d, 4)
-    dout = synth.normal_grads(P, L * F, 5)
-    dout_lm = np.ascontiguousarray(dout.reshape(P, L, F).transpose(1, 0, 2))
-    enc.table_step(Adam(1e-2, 0.9, 0.99, 1e-15), 5, torch.from_numpy(x).cuda(), torch.from_numpy(dout_lm).cuda(),
-                   state, table, scratch, touched)
-    s = state.cpu().numpy()
-    assert torch.all(scratch == 0) and torch.all(touched == 0)
-    assert np.all(s[:, 3 * F:] == 0)
-    kw = dict(n_levels=L, log2_T=log2_T, n_features=F, base_res=8.0, growth=1.6)
-    grads = (OE.simplex_encode_bwd if kind == "simplex" else OE.grid_encode_bwd)(x, dout, **kw)
-    gr = np.concatenate([grads[l] for l in range(L)])
-    hp = dict(lr=float(np.float32(1e-2)), beta1=float(np.float32(0.9)), beta2=float(np.float32(0.99)),
-              eps=float(np.float32(1e-15)))
-    rp, rm, rv = OA.adam_step(p0, gr, m0, v0, 5, skip_zero_grad=True, **hp)
-    # gradients carry binary32 atomic rounding (1e-5 of sum |terms|); Adam maps it smoothly here
-    np.testing.assert_allclose(s[:, :F], rp, rtol=0, atol=2e-6)
-    np.testing.assert_allclose(s[:, F:2 * F], rm, rtol=0, atol=2e-6)
-    np.testing.assert_allclose(s[:, 2 * F:3 * F], rv, rtol=1e-5, atol=1e-9)
-    untouched = np.all(gr == 0, axis=1)
-    assert untouched.any() and (~untouched).sum() > 1000
-    assert np.array_equal(s[untouched, :3 * F], rec[untouched, :3 * F])
-    dt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[tdt]
-    assert torch.equal(table.reshape(L * T, F), state[:, :F].to(dt))
-
-
-@pytest.mark.parametrize("tdt", ["f16", "bf16", "f32"])
-def test_forward_strided_equals_dense(tdt):
-    """Gathering the table with an entry stride (entries interleaved with other data) gives the
-    same encoding, bit for bit, as the dense table holding the same values."""
-    from paper_2311_15439_gb300 import _lib
-    from paper_2311_15439_gb300.api import Encoder
-    L, log2_T, F = 6, 12, 2
-    enc = Encoder(3, L, F, log2_T, 8.0, 1.7, table_dtype=tdt)
-    vals = synth.uniform_tables(L, 1 << log2_T, F, 6, dtype=tdt, scale=1.0)[0]
-    dt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[tdt]
-    dense = torch.from_numpy(vals).cuda().to(dt)
-    per_word = 4 // dense.element_size()
-    inter = torch.zeros((L << log2_T, 8 * per_word), dtype=dt, device="cuda")  # 32-byte entries
-    inter[:, 3 * per_word:3 * per_word + F] = dense.reshape(-1, F)
-    x = torch.from_numpy(synth.uniform_points(4000, 3, 7)).cuda()
-    out = torch.empty((4000, L * F), dtype=dt, device="cuda")
-    st = _lib.lib().sxe_encode_fwd_strided(enc.handle, x.data_ptr(), 4000, inter.data_ptr() + 12, 8 * per_word,
-                                           out.data_ptr(), torch.cuda.current_stream().cuda_stream)
-    assert st == 0
-    assert torch.equal(out, enc.encode_fwd(x, dense))
 
 
 def test_grouped_input_gradient_is_the_transpose():
