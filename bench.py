@@ -163,6 +163,10 @@ def run_gpu(args):
         dist.barrier()
     B.build()   # no-op when up to date
 
+    from paper_2311_15439_gb300 import _lib
+    _lib.check(_lib.lib().sxe_mlp_set_kernel({"auto": _lib.SXE_MLP_KERNEL_AUTO, "mma_sync": _lib.SXE_MLP_KERNEL_MMA_SYNC,
+                                              "tcgen05": _lib.SXE_MLP_KERNEL_TCGEN05}[args.mlp_kernel]),
+               "sxe_mlp_set_kernel")
     enc = Encoder(**CFG, kind=args.kind, table_dtype="f16")
     mlp = Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16")
     tr = Trainer(enc, mlp, BATCH, seed=rank, device=dev)
@@ -259,7 +263,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "kind": args.kind, "global_batch": BATCH * world,
+            "config": {"workload": WORKLOAD, "kind": args.kind, "mlp_kernel": args.mlp_kernel,
+                       "global_batch": BATCH * world,
                        "points_per_step_per_gpu": BATCH, "parallelism": "replicas (one per GPU)",
                        "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state records, no flush",
                        "batches": "%d resident distinct batches cycled" % N_POOL},
@@ -450,6 +455,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05"],
+                    help="kernel of the network training pass")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-baseline-only", action="store_true")
     args = ap.parse_args()
