@@ -449,26 +449,52 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
 
 // dW[j] += (sum_b ws[b][j]) / loss_scale, summed over b in increasing order; the loss
 // partials (after the nb x n weight partials) are summed the same way into *sq_sum.
-__global__ void reduce_partials_kernel(const float* __restrict__ ws, int nb, int64_t n, float inv_scale,
-                                       float* __restrict__ dW, float* __restrict__ sq_sum) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+// Sums the per-CTA partial weight gradients: one CTA per 32 consecutive parameters, its 8
+// warps take interleaved slices of the partials (coalesced 128-byte rows), and the 8 warp
+// sums are added in a fixed order, so the result does not depend on scheduling.
+constexpr int kReduceCols = 32, kReduceWarps = 8;
+__global__ void __launch_bounds__(kReduceCols * kReduceWarps)
+reduce_partials_kernel(const float* __restrict__ ws, int nb, int64_t n, float inv_scale,
+                       float* __restrict__ dW, float* __restrict__ sq_sum) {
+  __shared__ float part[kReduceWarps][kReduceCols];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * kReduceCols + lane;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  if (j < n) {
+    int b = w;
+    for (; b + 3 * kReduceWarps < nb; b += 4 * kReduceWarps) {
+      s0 += ws[(int64_t)b * n + j];
+      s1 += ws[(int64_t)(b + kReduceWarps) * n + j];
+      s2 += ws[(int64_t)(b + 2 * kReduceWarps) * n + j];
+      s3 += ws[(int64_t)(b + 3 * kReduceWarps) * n + j];
+    }
+    for (; b < nb; b += kReduceWarps) s0 += ws[(int64_t)b * n + j];
+  }
+  part[w][lane] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (w == 0 && j < n) {
     float s = 0.f;
-    for (int b = 0; b < nb; ++b) s += ws[(int64_t)b * n + j];
+#pragma unroll
+    for (int k = 0; k < kReduceWarps; ++k) s += part[k][lane];
     dW[j] += s * inv_scale;
   }
-  if (sq_sum && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sq_sum && blockIdx.x == 0 && w == 1) {
     float s = 0.f;
-    for (int b = 0; b < nb; ++b) s += ws[(int64_t)nb * n + b];
-    *sq_sum = s;
+    for (int b = lane; b < nb; b += 32) s += ws[(int64_t)nb * n + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) *sq_sum = s;
   }
 }
+
+int reduce_blocks(int64_t n_params) { return (int)((n_params + kReduceCols - 1) / kReduceCols); }
 
 }  // namespace
 
 sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
                              cudaStream_t s) {
-  const int rb = (int)std::min<int64_t>((n_params + 255) / 256, 1024);
-  reduce_partials_kernel<<<rb, 256, 0, s>>>(ws, nb, n_params, inv_scale, dW, sq_sum);
+  reduce_partials_kernel<<<reduce_blocks(n_params), kReduceCols * kReduceWarps, 0, s>>>(ws, nb, n_params, inv_scale,
+                                                                                     dW, sq_sum);
   return check_launch("mlp_bwd_reduce");
 }
 
@@ -537,9 +563,7 @@ sxe_status bwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
   }
   sxe_status st = check_launch("mlp_bwd");
   if (st != SXE_OK) return st;
-  const int rb = (int)std::min<int64_t>((n_params + 255) / 256, 1024);
-  reduce_partials_kernel<<<rb, 256, 0, s>>>(ws, grid, n_params, 1.f / loss_scale, dW, target ? sq_sum : nullptr);
-  return check_launch("mlp_bwd_reduce");
+  return launch_mlp_reduce(ws, grid, n_params, 1.f / loss_scale, dW, target ? sq_sum : nullptr, s);
 }
 
 template <typename T, int N_IN>

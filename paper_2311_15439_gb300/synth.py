@@ -92,6 +92,31 @@ def normal_grads(P: int, n: int, seed: int) -> np.ndarray:
     return rng(seed).standard_normal((P, n), dtype=np.float32)
 
 
+class SphereTorusScene:
+    """Seeded union of spheres and tori (the SDF-style workload's surface): centres in
+    [0.2, 0.8]^3, radii 0.03..0.15, tori in the xy plane with minor radius r/3.
+    ``sdf(x)`` is the signed distance of the union (minimum over shapes), float32 [P, 1]."""
+
+    def __init__(self, seed: int, n_shapes: int = 32):
+        g = rng(seed)
+        self.kinds = g.integers(0, 2, size=n_shapes)
+        self.centres = g.uniform(0.2, 0.8, size=(n_shapes, 3))
+        self.radii = g.uniform(0.03, 0.15, size=n_shapes)
+
+    def sdf(self, x: np.ndarray) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64)
+        best = np.full(x.shape[0], np.inf)
+        for kind, c, r in zip(self.kinds, self.centres, self.radii):
+            p = x - c
+            if kind == 0:
+                dist = np.linalg.norm(p, axis=1) - r
+            else:
+                q = np.stack([np.hypot(p[:, 0], p[:, 1]) - r, p[:, 2]], axis=1)
+                dist = np.linalg.norm(q, axis=1) - r / 3.0
+            best = np.minimum(best, dist)
+        return best.astype(np.float32)[:, None]
+
+
 def sdf_points(P: int, seed: int, n_shapes: int = 32, band: float = 0.01) -> np.ndarray:
     """Half uniform in [0,1)^3, half within ``band`` of a seeded union of spheres and tori."""
     g = rng(seed)

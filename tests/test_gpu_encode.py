@@ -206,3 +206,26 @@ def test_plain_path_matches_oracle(cuda_lib, d):
     g = grad.cpu().numpy()
     for l in range(L):
         assert rel_err(g[l], gref[l], gden[l]) <= 1e-5
+
+
+def test_full_size_sdf_workload(cuda_lib):
+    """SDF-style configuration at full size: d = 3, L = 16, F = 2, T = 2^19 bf16 tables and
+    output, growth 1.38, 2^20 points (half near a union of spheres and tori): every output
+    against the oracle, gradients of three levels."""
+    from paper_2311_15439_gb300.api import Encoder
+    enc = Encoder(3, 16, 2, 19, 16.0, 1.38, table_dtype="bf16", out_dtype="bf16")
+    vals, bits = synth.uniform_tables(16, 1 << 19, 2, 70, dtype="bf16", scale=1e-4)
+    t = torch.from_numpy(bits.astype(np.int16)).cuda().view(torch.bfloat16)
+    x = synth.sdf_points(1 << 20, 71)
+    xd = torch.from_numpy(x).cuda()
+    out = enc.encode_fwd(xd, t).float().cpu().numpy()
+    ref, den = O.simplex_encode(x, vals, base_res=16.0, growth=1.38, with_denominator=True)
+    assert worst_ratio(out, ref, den, ENC_TOL["bf16"], ENC_ATOL["bf16"]) <= 1.0
+    dout = synth.normal_grads(len(x), 32, 72)
+    grad = torch.zeros((16, 1 << 19, 2), dtype=torch.float32, device="cuda")
+    enc.encode_bwd(xd, torch.from_numpy(dout).cuda(), grad)
+    levels = [0, 8, 15]
+    gref, gden = O.simplex_encode_bwd(x, dout, n_levels=16, log2_T=19, n_features=2, base_res=16.0, growth=1.38,
+                                      levels=levels, with_denominator=True)
+    for l in levels:
+        assert rel_err(grad[l].cpu().numpy(), gref[l], gden[l]) <= 1e-5

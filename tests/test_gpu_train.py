@@ -203,3 +203,21 @@ def test_grouped_input_gradient_is_the_transpose():
         mlp.mlp_train_l2_grouped(W, x, tgt, torch.zeros(mlp.n_params, device="cuda"), torch.zeros(1, device="cuda"),
                                  d_g, g)
         assert torch.equal(d_g.permute(1, 0, 2).reshape(P, 32), d_rows)
+
+
+def test_sdf_training_reduces_loss():
+    """SDF-style workload (d = 3, bf16 tables and network, one hidden layer, one output):
+    fitting the signed distance of a union of spheres and tori drives the L2 loss down."""
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+    P = 1 << 15
+    enc = Encoder(3, 16, 2, 16, 16.0, 1.38, table_dtype="bf16")
+    tr = Trainer(enc, Mlp(32, 1, n_hidden=1, dtype="bf16"), P, seed=4)
+    scene = synth.SphereTorusScene(5)
+    losses = []
+    for it in range(80):
+        x = synth.sdf_points(P, 200 + it)
+        tr.step(torch.from_numpy(x).cuda(), torch.from_numpy(scene.sdf(x)).cuda())
+        if it in (0, 79):
+            losses.append(tr.loss())
+    assert np.isfinite(losses).all() and losses[1] < 0.5 * losses[0]
