@@ -20,7 +20,10 @@ reconstruction of the point, agreement with a brute-force point-in-simplex
 search, exact interpolation of affine fields and the memory-usage figure of
 Sec. 5.2; the grid path by exact interpolation of multilinear fields.  The
 backward passes are pinned by adjointness and by exact finite differences
-(both encodings are linear in the tables).
+(both encodings are linear in the tables).  The input gradients
+(``simplex_encode_dx`` / ``grid_encode_dx``) are pinned by the exact gradient of
+affine (simplex) and multilinear (grid) fields and by central differences of the
+forward pass inside one cell.
 """
 from __future__ import annotations
 
@@ -97,6 +100,46 @@ def simplex_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, gro
             np.add.at(a, slots.ravel(), np.abs(terms).reshape(-1, F))
             dens[l] = a
     return (grads, dens) if with_denominator else grads
+
+
+def simplex_encode_dx(x32, tables, dout, *, base_res, growth, res_mode=lattice.RES_RAW, with_denominator=False):
+    """Gradient of sum_p,j dout[p][j] * out[p][j] with respect to the points, FP64 [P, n].
+
+    Inside one simplex the output is affine in the fractional parts: by the weights of
+    Sec. 4.3, moving f along axis order[k] shifts weight from vertex v_k to v_{k+1}, so
+    d out / d q_order[k] = H(v_{k+1}) - H(v_k).  The skew of Eq. 2 (q = p + F_n sum p) is
+    symmetric, so d/dp_j = g_j + F_n sum_i g_i, and p = x s_l gives the factor s_l.  The
+    constants are the binary32 s_l and F_n of the forward pass.  Where the point lies on a
+    face (tied fractional parts) the derivative is the one-sided value of the forward
+    pass's simplex.  With ``with_denominator`` also returns the sum of the magnitudes of
+    the terms (the scale of the rounding error of any evaluation order).
+    """
+    x32 = np.asarray(x32, dtype=np.float32)
+    dout = np.asarray(dout, dtype=np.float64)
+    P, n = x32.shape
+    L, T, F = tables.shape
+    log2_T = int(T).bit_length() - 1
+    scales = _level_params("simplex", n, L, base_res, growth, res_mode)
+    Fn = float(np.float32(lattice.skew_factor(n)))
+    dx = np.zeros((P, n))
+    den = np.zeros((P, n))
+    rows = np.arange(P)
+    for l in range(L):
+        q = lattice.scaled_skewed_fp32(x32, scales[l])
+        c, order, _ = lattice.subdivide(q)
+        V = lattice.simplex_vertices(c, order)
+        H = np.asarray(tables[l], dtype=np.float64)[lattice.hash_slot(V, log2_T)]   # [P, n+1, F]
+        dl = dout[:, l * F:(l + 1) * F]
+        g = np.zeros((P, n))
+        a = np.zeros((P, n))
+        for k in range(n):
+            diff = H[:, k + 1] - H[:, k]                                    # [P, F]
+            g[rows, order[:, k]] = np.einsum("pf,pf->p", dl, diff)
+            a[rows, order[:, k]] = np.einsum("pf,pf->p", np.abs(dl), np.abs(H[:, k + 1]) + np.abs(H[:, k]))
+        s = float(scales[l])
+        dx += s * (g + Fn * g.sum(axis=1, keepdims=True))
+        den += s * (a + Fn * a.sum(axis=1, keepdims=True))
+    return (dx, den) if with_denominator else dx
 
 
 # --------------------------------------------------------------------------
@@ -178,6 +221,43 @@ def grid_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, growth
         np.add.at(g, slots.ravel(), terms.reshape(-1, F))
         grads[l] = g
     return grads
+
+
+def grid_level_corner_weight_derivatives(f: np.ndarray, axis: int) -> np.ndarray:
+    """d w_b / d f_axis for every corner b (same order as ``grid_level_corner_weights``): the
+    factor of the differentiated axis becomes -1 (lower corner) or +1 (upper corner)."""
+    P, n = f.shape
+    w = np.ones((P, 1))
+    for i in range(n):
+        lo = w * ((-1.0 + 0.0 * f[:, i]) if i == axis else (1.0 - f[:, i]))[:, None]
+        hi = w * ((1.0 + 0.0 * f[:, i]) if i == axis else f[:, i])[:, None]
+        w = np.stack([lo, hi], axis=2).reshape(P, -1)
+    return w
+
+
+def grid_encode_dx(x32, tables, dout, *, base_res, growth, with_denominator=False):
+    """Gradient of sum dout * out of ``grid_encode`` with respect to the points, FP64 [P, n]:
+    the derivative of the n-linear weights along each axis, times N_l (p = x N_l)."""
+    x32 = np.asarray(x32, dtype=np.float32)
+    dout = np.asarray(dout, dtype=np.float64)
+    P, n = x32.shape
+    L, T, F = tables.shape
+    log2_T = int(T).bit_length() - 1
+    res = _level_params("grid", n, L, base_res, growth, None)
+    offs = _corner_offsets(n)
+    dx = np.zeros((P, n))
+    den = np.zeros((P, n))
+    for l in range(L):
+        c, f = grid_level_cell(x32, res[l])
+        H = np.asarray(tables[l], dtype=np.float64)[lattice.hash_slot(c[:, None, :] + offs[None, :, :], log2_T)]
+        dl = dout[:, l * F:(l + 1) * F]
+        proj = np.einsum("pf,pbf->pb", dl, H)                                # [P, 2^n]
+        aproj = np.einsum("pf,pbf->pb", np.abs(dl), np.abs(H))
+        for j in range(n):
+            dw = grid_level_corner_weight_derivatives(f, j)
+            dx[:, j] += float(res[l]) * np.einsum("pb,pb->p", dw, proj)
+            den[:, j] += float(res[l]) * np.einsum("pb,pb->p", np.abs(dw), aproj)
+    return (dx, den) if with_denominator else dx
 
 
 def grid_level_vertices(x32, level_res, log2_T):

@@ -247,3 +247,91 @@ def test_adam_matches_library_and_skips_zero_grads():
         opt.step()
         th, m, v = adam.adam_step(th, gr, m, v, t, skip_zero_grad=False, **hp)
     np.testing.assert_allclose(th, p.detach().numpy(), rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# input gradients
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_simplex_dx_of_affine_field(n):
+    """On an affine field a.x + b the encoding is a.x + b for every point (Sec. 4.3), so the
+    gradient of sum dout * out with respect to x is sum_l dout_l a, exactly (up to the
+    rounding of the binary32 skew constant), also on faces and ties."""
+    g = synth.rng(140 + n)
+    a, b = g.standard_normal(n), -0.2
+    L, growth = 3, 1.5
+    base, log2_T = (4.0, 20) if n < 4 else (3.0, 22)
+    tables = _collision_free_tables("simplex", n, L, base, growth, log2_T, lambda p: p @ a + b)
+    x = np.concatenate([synth.uniform_points(200, n, 141), synth.edge_points(n, 142, per_kind=4)])
+    dout = synth.normal_grads(len(x), L, 143).astype(np.float64)
+    dx = encoding.simplex_encode_dx(x, tables, dout, base_res=base, growth=growth)
+    want = dout.sum(axis=1)[:, None] * a[None, :]
+    scale = np.abs(dout).sum(axis=1)[:, None] * np.abs(a).sum()
+    assert np.all(np.abs(dx - want) <= 1e-6 * scale)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_grid_dx_of_multilinear_field(n):
+    """The n-linear interpolant of prod_i (1 + c_i x_i) is that function on every cell, so its
+    x-gradient is c_j prod_{i != j} (1 + c_i x_i) at the binary32 point the grid sees."""
+    g = synth.rng(150 + n)
+    cc = g.standard_normal(n)
+    L, base, growth = 3, 4.0, 1.5
+    log2_T = 20 if n < 4 else 22
+    if n == 4:
+        base = 3.0
+    fn = lambda p: np.prod(1.0 + cc * p, axis=-1)
+    tables = _collision_free_tables("grid", n, L, base, growth, log2_T, fn)
+    x = np.concatenate([synth.uniform_points(200, n, 151), synth.edge_points(n, 152, per_kind=4)])
+    dout = synth.normal_grads(len(x), L, 153).astype(np.float64)
+    dx = encoding.grid_encode_dx(x, tables, dout, base_res=base, growth=growth)
+    want = np.zeros_like(dx)
+    for l, N in enumerate(lattice.level_resolutions(L, base, growth)):
+        xs = (x * np.float32(N)).astype(np.float64) / N
+        for j in range(n):
+            others = np.prod(np.delete(1.0 + cc * xs, j, axis=1), axis=1)
+            want[:, j] += dout[:, l] * cc[j] * others
+    np.testing.assert_allclose(dx, want, rtol=1e-9, atol=1e-9)
+
+
+def _same_cells(kind, x, n, L, base, growth, log2_T):
+    """Per level, the slot sets of the cell that contains each point."""
+    out = []
+    if kind == "simplex":
+        scales = lattice.simplex_level_scales_fp32(n, L, base, growth)
+        for l in range(L):
+            out.append(np.sort(encoding.simplex_level_vertices(x, scales[l], log2_T)[0], axis=1))
+    else:
+        for N in lattice.grid_level_scales_fp32(L, base, growth):
+            out.append(encoding.grid_level_vertices(x, N, log2_T)[0])
+    return out
+
+
+@pytest.mark.parametrize("kind,n", [("simplex", 2), ("simplex", 3), ("simplex", 5), ("grid", 2), ("grid", 3)])
+def test_dx_matches_central_differences(kind, n):
+    """Random tables: the input gradient equals the central difference of the forward pass for
+    points whose cell (at every level) is the same at x - h e_j and x + h e_j."""
+    L, base, growth, log2_T, F = 3, 4.0, 1.5, 12, 2
+    tables = synth.uniform_tables(L, 1 << log2_T, F, 160 + n, scale=1.0)[0].astype(np.float64)
+    x = synth.uniform_points(400, n, 161 + n)
+    x = np.clip(x, 0.01, 0.99).astype(np.float32)
+    dout = synth.normal_grads(len(x), L * F, 162).astype(np.float64)
+    enc = encoding.simplex_encode if kind == "simplex" else encoding.grid_encode
+    dxf = encoding.simplex_encode_dx if kind == "simplex" else encoding.grid_encode_dx
+    dx, den = dxf(x, tables, dout, base_res=base, growth=growth, with_denominator=True)
+    h = np.float32(2.0 ** -13)
+    cells = _same_cells(kind, x, n, L, base, growth, log2_T)
+    checked = 0
+    for j in range(n):
+        xp, xm = x.copy(), x.copy()
+        xp[:, j] += h
+        xm[:, j] -= h
+        ok = np.ones(len(x), dtype=bool)
+        for xx in (xp, xm):
+            for c0, c1 in zip(cells, _same_cells(kind, xx, n, L, base, growth, log2_T)):
+                ok &= np.all(c0 == c1, axis=1)
+        fd = ((enc(xp, tables, base_res=base, growth=growth) - enc(xm, tables, base_res=base, growth=growth))
+              * dout).sum(axis=1) / (2.0 * float(h))
+        assert np.all(np.abs(fd - dx[:, j])[ok] <= 2e-3 * den[ok, j] + 1e-12)
+        checked += ok.sum()
+    assert checked > 100 * n
