@@ -40,21 +40,26 @@ def _level_params(kind, n, n_levels, base_res, growth, res_mode):
     return lattice.grid_level_scales_fp32(n_levels, base_res, growth)
 
 
+def _widths(kind, n, scales, log2_T, index_mode):
+    return lattice.level_box_widths(kind, n, scales, log2_T, index_mode)
+
+
 # --------------------------------------------------------------------------
 # simplex encoding, Sec. 5 (a)-(d)
 # --------------------------------------------------------------------------
-def simplex_level_vertices(x32: np.ndarray, level_scale: np.float32, log2_T: int):
+def simplex_level_vertices(x32: np.ndarray, level_scale: np.float32, log2_T: int, width: int = 0):
     """Steps (a) for one level: returns (slots int64 [P, n+1], weights FP64 [P, n+1],
     vertices int64 [P, n+1, n])."""
     q = lattice.scaled_skewed_fp32(x32, level_scale)
     c, order, f = lattice.subdivide(q)
     V = lattice.simplex_vertices(c, order)
     w = lattice.barycentric_weights(f, order)
-    slots = lattice.hash_slot(V, log2_T)
+    slots = lattice.slot_of(V, log2_T, width)
     return slots, w, V
 
 
-def simplex_encode(x32, tables, *, base_res, growth, res_mode=lattice.RES_RAW, with_denominator=False):
+def simplex_encode(x32, tables, *, base_res, growth, res_mode=lattice.RES_RAW, with_denominator=False,
+                   index_mode=lattice.INDEX_HASH):
     """Forward simplex encoding of points ``x32`` ([P, n], binary32) with tables [L, T, F].
 
     Returns FP64 [P, L*F]; with ``with_denominator`` also returns sum_k |w_k H_k|
@@ -65,10 +70,11 @@ def simplex_encode(x32, tables, *, base_res, growth, res_mode=lattice.RES_RAW, w
     L, T, F = tables.shape
     log2_T = int(T).bit_length() - 1
     scales = _level_params("simplex", n, L, base_res, growth, res_mode)
+    widths = _widths("simplex", n, scales, log2_T, index_mode)
     out = np.zeros((P, L * F), dtype=np.float64)
     den = np.zeros((P, L * F), dtype=np.float64)
     for l in range(L):
-        slots, w, _ = simplex_level_vertices(x32, scales[l], log2_T)
+        slots, w, _ = simplex_level_vertices(x32, scales[l], log2_T, widths[l])
         H = np.asarray(tables[l], dtype=np.float64)[slots]            # (b) lookup [P, n+1, F]
         out[:, l * F:(l + 1) * F] = np.einsum("pk,pkf->pf", w, H)      # (c) interpolate, (d) concat
         den[:, l * F:(l + 1) * F] = np.einsum("pk,pkf->pf", np.abs(w), np.abs(H))
@@ -76,7 +82,8 @@ def simplex_encode(x32, tables, *, base_res, growth, res_mode=lattice.RES_RAW, w
 
 
 def simplex_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, growth,
-                       res_mode=lattice.RES_RAW, levels=None, with_denominator=False):
+                       res_mode=lattice.RES_RAW, levels=None, with_denominator=False,
+                       index_mode=lattice.INDEX_HASH):
     """Step (e): dH_l[slot(v_k)][f] += w_k * dout[p][l*F + f], FP64.
 
     Returns a dict level -> FP64 [T, F] gradient (only the levels asked for), and
@@ -88,9 +95,10 @@ def simplex_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, gro
     F = n_features
     T = 1 << log2_T
     scales = _level_params("simplex", n, n_levels, base_res, growth, res_mode)
+    widths = _widths("simplex", n, scales, log2_T, index_mode)
     grads, dens = {}, {}
     for l in (range(n_levels) if levels is None else levels):
-        slots, w, _ = simplex_level_vertices(x32, scales[l], log2_T)
+        slots, w, _ = simplex_level_vertices(x32, scales[l], log2_T, widths[l])
         terms = w[:, :, None] * dout[:, None, l * F:(l + 1) * F]       # [P, n+1, F]
         g = np.zeros((T, F), dtype=np.float64)
         np.add.at(g, slots.ravel(), terms.reshape(-1, F))
@@ -102,7 +110,8 @@ def simplex_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, gro
     return (grads, dens) if with_denominator else grads
 
 
-def simplex_encode_dx(x32, tables, dout, *, base_res, growth, res_mode=lattice.RES_RAW, with_denominator=False):
+def simplex_encode_dx(x32, tables, dout, *, base_res, growth, res_mode=lattice.RES_RAW, with_denominator=False,
+                      index_mode=lattice.INDEX_HASH):
     """Gradient of sum_p,j dout[p][j] * out[p][j] with respect to the points, FP64 [P, n].
 
     Inside one simplex the output is affine in the fractional parts: by the weights of
@@ -120,6 +129,7 @@ def simplex_encode_dx(x32, tables, dout, *, base_res, growth, res_mode=lattice.R
     L, T, F = tables.shape
     log2_T = int(T).bit_length() - 1
     scales = _level_params("simplex", n, L, base_res, growth, res_mode)
+    widths = _widths("simplex", n, scales, log2_T, index_mode)
     Fn = float(np.float32(lattice.skew_factor(n)))
     dx = np.zeros((P, n))
     den = np.zeros((P, n))
@@ -128,7 +138,7 @@ def simplex_encode_dx(x32, tables, dout, *, base_res, growth, res_mode=lattice.R
         q = lattice.scaled_skewed_fp32(x32, scales[l])
         c, order, _ = lattice.subdivide(q)
         V = lattice.simplex_vertices(c, order)
-        H = np.asarray(tables[l], dtype=np.float64)[lattice.hash_slot(V, log2_T)]   # [P, n+1, F]
+        H = np.asarray(tables[l], dtype=np.float64)[lattice.slot_of(V, log2_T, widths[l])]   # [P, n+1, F]
         dl = dout[:, l * F:(l + 1) * F]
         g = np.zeros((P, n))
         a = np.zeros((P, n))
@@ -174,7 +184,7 @@ def grid_level_corner_weights(f: np.ndarray) -> np.ndarray:
     return w
 
 
-def grid_encode(x32, tables, *, base_res, growth):
+def grid_encode(x32, tables, *, base_res, growth, index_mode=lattice.INDEX_HASH):
     """Forward 2^n grid encoding, [P, L*F] FP64.
 
     Per level: look up the 2^n corner values, then (Algorithm 1) interpolate
@@ -186,12 +196,13 @@ def grid_encode(x32, tables, *, base_res, growth):
     L, T, F = tables.shape
     log2_T = int(T).bit_length() - 1
     res = _level_params("grid", n, L, base_res, growth, None)
+    widths = _widths("grid", n, res, log2_T, index_mode)
     offs = _corner_offsets(n)
     out = np.zeros((P, L * F), dtype=np.float64)
     for l in range(L):
         c, f = grid_level_cell(x32, res[l])
         corners = c[:, None, :] + offs[None, :, :]                       # [P, 2^n, n]
-        vals = np.asarray(tables[l], dtype=np.float64)[lattice.hash_slot(corners, log2_T)]
+        vals = np.asarray(tables[l], dtype=np.float64)[lattice.slot_of(corners, log2_T, widths[l])]
         vals = vals.reshape((P,) + (2,) * n + (F,))
         for i in reversed(range(n)):                                   # lerp along axis i
             t = f[:, i].reshape((P,) + (1,) * i + (1,))
@@ -202,7 +213,8 @@ def grid_encode(x32, tables, *, base_res, growth):
     return out
 
 
-def grid_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, growth, levels=None):
+def grid_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, growth, levels=None,
+                    index_mode=lattice.INDEX_HASH):
     """Backward of ``grid_encode``: dH_l[slot(c+b)] += w_b * dout, FP64 dict level -> [T, F]."""
     x32 = np.asarray(x32, dtype=np.float32)
     dout = np.asarray(dout, dtype=np.float64)
@@ -210,12 +222,13 @@ def grid_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, growth
     F = n_features
     T = 1 << log2_T
     res = _level_params("grid", n, n_levels, base_res, growth, None)
+    widths = _widths("grid", n, res, log2_T, index_mode)
     offs = _corner_offsets(n)
     grads = {}
     for l in (range(n_levels) if levels is None else levels):
         c, f = grid_level_cell(x32, res[l])
         w = grid_level_corner_weights(f)                                 # [P, 2^n]
-        slots = lattice.hash_slot(c[:, None, :] + offs[None, :, :], log2_T)
+        slots = lattice.slot_of(c[:, None, :] + offs[None, :, :], log2_T, widths[l])
         terms = w[:, :, None] * dout[:, None, l * F:(l + 1) * F]
         g = np.zeros((T, F), dtype=np.float64)
         np.add.at(g, slots.ravel(), terms.reshape(-1, F))
@@ -235,7 +248,7 @@ def grid_level_corner_weight_derivatives(f: np.ndarray, axis: int) -> np.ndarray
     return w
 
 
-def grid_encode_dx(x32, tables, dout, *, base_res, growth, with_denominator=False):
+def grid_encode_dx(x32, tables, dout, *, base_res, growth, with_denominator=False, index_mode=lattice.INDEX_HASH):
     """Gradient of sum dout * out of ``grid_encode`` with respect to the points, FP64 [P, n]:
     the derivative of the n-linear weights along each axis, times N_l (p = x N_l)."""
     x32 = np.asarray(x32, dtype=np.float32)
@@ -244,12 +257,14 @@ def grid_encode_dx(x32, tables, dout, *, base_res, growth, with_denominator=Fals
     L, T, F = tables.shape
     log2_T = int(T).bit_length() - 1
     res = _level_params("grid", n, L, base_res, growth, None)
+    widths = _widths("grid", n, res, log2_T, index_mode)
     offs = _corner_offsets(n)
     dx = np.zeros((P, n))
     den = np.zeros((P, n))
     for l in range(L):
         c, f = grid_level_cell(x32, res[l])
-        H = np.asarray(tables[l], dtype=np.float64)[lattice.hash_slot(c[:, None, :] + offs[None, :, :], log2_T)]
+        H = np.asarray(tables[l], dtype=np.float64)[lattice.slot_of(c[:, None, :] + offs[None, :, :], log2_T,
+                                                                      widths[l])]
         dl = dout[:, l * F:(l + 1) * F]
         proj = np.einsum("pf,pbf->pb", dl, H)                                # [P, 2^n]
         aproj = np.einsum("pf,pbf->pb", np.abs(dl), np.abs(H))
@@ -260,8 +275,8 @@ def grid_encode_dx(x32, tables, dout, *, base_res, growth, with_denominator=Fals
     return (dx, den) if with_denominator else dx
 
 
-def grid_level_vertices(x32, level_res, log2_T):
+def grid_level_vertices(x32, level_res, log2_T, width=0):
     """Slots int64 [P, 2^n] and weights FP64 [P, 2^n] of one grid level."""
     c, f = grid_level_cell(x32, level_res)
     offs = _corner_offsets(c.shape[1])
-    return lattice.hash_slot(c[:, None, :] + offs[None, :, :], log2_T), grid_level_corner_weights(f)
+    return lattice.slot_of(c[:, None, :] + offs[None, :, :], log2_T, width), grid_level_corner_weights(f)

@@ -27,6 +27,13 @@ Readings where the paper is silent (each also listed in the design notes):
   with one rounding per operation in this order: p_i = x_i*s, sigma = ((p_1 +
   p_2) + p_3) + ..., t = F*sigma, q_i = p_i + t.  Index parity with the GPU is
   conditioned on this binary32 value; everything after it is FP64 here.
+* Optional dense indexing of coarse levels (``INDEX_DENSE_COARSE``; Instant-NGP
+  stores a level directly when its lattice fits the table, the paper hashes every
+  level): the vertices of points in [0,1]^n have coordinates 0..B-1 per axis with
+  B = floor(top) + 2, top = s_l sqrt(n+1) (simplex: q_i <= s_l (1 + n F_n)) or N_l
+  (grid), evaluated from the binary32 scale with a 2^-20 relative margin so that a
+  rounded-up binary32 coordinate stays inside; a level with B^n <= T stores vertex v
+  at sum_i v_i B^i (uint32 arithmetic, then modulo T), other levels hash.
 * Hash: XOR over axes of (uint32 v_i * pi_i) modulo T (a power of two), with
   pi = (1, 2654435761, 805459861) for the first three axes (Instant-NGP's
   spatial hash, which the paper's backbone uses) and, for axes 4 and 5,
@@ -44,6 +51,9 @@ HASH_PRIMES = (1, 2654435761, 805459861, 1013904263, 2773480771)
 
 RES_RAW = 0
 RES_EQUAL_MEM = 1
+
+INDEX_HASH = 0
+INDEX_DENSE_COARSE = 1
 
 
 # --------------------------------------------------------------------------
@@ -184,3 +194,39 @@ def hash_slot(v: np.ndarray, log2_T: int) -> np.ndarray:
         vi = v[..., i].astype(np.uint64) & mask32          # two's complement mod 2^32
         h ^= (vi * np.uint64(HASH_PRIMES[i])) & mask32     # product < 2^64: exact
     return (h & np.uint64((1 << log2_T) - 1)).astype(np.int64)
+
+
+# --------------------------------------------------------------------------
+# optional direct (collision-free) indexing of the coarse levels
+# --------------------------------------------------------------------------
+def dense_box_width(kind: str, n: int, scale_fp32) -> int:
+    """Number of lattice coordinates per axis that the vertices of points in [0,1]^n take."""
+    top = float(scale_fp32) * (math.sqrt(n + 1.0) if kind == "simplex" else 1.0)
+    return int(math.floor(top * (1.0 + 2.0 ** -20))) + 2
+
+
+def level_box_widths(kind: str, n: int, scales, log2_T: int, index_mode: int) -> list[int]:
+    """Per level: the box width B if that level is stored directly (B^n <= T), else 0 (hashed)."""
+    out = []
+    for s in scales:
+        B = dense_box_width(kind, n, s) if index_mode == INDEX_DENSE_COARSE else 0
+        out.append(B if B and B ** n <= (1 << log2_T) else 0)
+    return out
+
+
+def dense_slot(v: np.ndarray, width: int, log2_T: int) -> np.ndarray:
+    """(sum_i (v_i mod 2^32) * width^i mod 2^32) mod T, exact on uint64."""
+    v = np.asarray(v, dtype=np.int64)
+    mask32 = np.uint64(0xFFFFFFFF)
+    h = np.zeros(v.shape[:-1], dtype=np.uint64)
+    stride = 1
+    for i in range(v.shape[-1]):
+        vi = v[..., i].astype(np.uint64) & mask32
+        h = (h + ((vi * np.uint64(stride % (1 << 32))) & mask32)) & mask32
+        stride *= width
+    return (h & np.uint64((1 << log2_T) - 1)).astype(np.int64)
+
+
+def slot_of(v: np.ndarray, log2_T: int, width: int = 0) -> np.ndarray:
+    """Table slot of vertex v: direct index for a stored level (width > 0), else the hash."""
+    return dense_slot(v, width, log2_T) if width else hash_slot(v, log2_T)

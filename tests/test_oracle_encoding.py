@@ -335,3 +335,84 @@ def test_dx_matches_central_differences(kind, n):
         assert np.all(np.abs(fd - dx[:, j])[ok] <= 2e-3 * den[ok, j] + 1e-12)
         checked += ok.sum()
     assert checked > 100 * n
+
+
+# --------------------------------------------------------------------------
+# optional direct indexing of coarse levels
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,n", [("simplex", 2), ("simplex", 3), ("simplex", 5), ("grid", 2), ("grid", 4)])
+def test_dense_box_holds_every_vertex(kind, n):
+    """The box width is N_l + 2 (the skewed unit cube spans [0, N_l]^n, Sec. 5.1) and every
+    vertex of every point of [0,1]^n, faces and corners included, lies inside it."""
+    L, base, growth = 4, 5.0, 1.7
+    x = np.concatenate([synth.uniform_points(3000, n, 170), synth.edge_points(n, 171, per_kind=16)])
+    if kind == "simplex":
+        scales = lattice.simplex_level_scales_fp32(n, L, base, growth)
+    else:
+        scales = lattice.grid_level_scales_fp32(L, base, growth)
+    for l, N in enumerate(lattice.level_resolutions(L, base, growth)):
+        B = lattice.dense_box_width(kind, n, scales[l])
+        assert B == N + 2
+        if kind == "simplex":
+            V = encoding.simplex_level_vertices(x, scales[l], 20)[2]
+        else:
+            c, _ = encoding.grid_level_cell(x, scales[l])
+            V = c[:, None, :] + encoding._corner_offsets(n)[None]
+        assert V.min() >= 0 and V.max() <= B - 1
+        assert V.max() == B - 1                        # the corner x = 1 reaches the far face
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_dense_slots_are_a_bijection_of_the_box(n):
+    B, log2_T = 7, 14
+    box = np.stack(np.meshgrid(*([np.arange(B)] * n), indexing="ij"), -1).reshape(-1, n)
+    s = lattice.dense_slot(box, B, log2_T)
+    assert len(np.unique(s)) == B ** n and s.min() == 0 and s.max() == B ** n - 1
+    # axis 0 fastest
+    e = np.eye(n, dtype=np.int64)
+    assert list(lattice.dense_slot(e, B, log2_T)) == [B ** i for i in range(n)]
+
+
+def test_dense_levels_are_exactly_those_that_fit():
+    L, base, growth, log2_T, n = 8, 16.0, 2.0, 16, 2
+    scales = lattice.simplex_level_scales_fp32(n, L, base, growth)
+    w = lattice.level_box_widths("simplex", n, scales, log2_T, lattice.INDEX_DENSE_COARSE)
+    Ns = lattice.level_resolutions(L, base, growth)
+    assert w == [N + 2 if (N + 2) ** 2 <= (1 << log2_T) else 0 for N in Ns]
+    assert w[:4] == [18, 34, 66, 130] and w[4:] == [0] * 4          # 258^2 > 2^16
+    assert lattice.level_box_widths("simplex", n, scales, log2_T, lattice.INDEX_HASH) == [0] * L
+
+
+@pytest.mark.parametrize("kind,n", [("simplex", 2), ("simplex", 3), ("grid", 2), ("grid", 3)])
+def test_dense_levels_reproduce_fields_with_a_small_table(kind, n):
+    """With T far below what a collision-free hash needs, the directly indexed levels still
+    reproduce affine (simplex) / multilinear (grid) fields exactly."""
+    g = synth.rng(180 + n)
+    a = g.standard_normal(n)
+    fn = (lambda p: p @ a + 0.5) if kind == "simplex" else (lambda p: np.prod(1.0 + a * p, axis=-1))
+    L, base, growth, log2_T = 4, 4.0, 1.5, 12
+    T = 1 << log2_T
+    if kind == "simplex":
+        scales = lattice.simplex_level_scales_fp32(n, L, base, growth)
+    else:
+        scales = lattice.grid_level_scales_fp32(L, base, growth)
+    widths = lattice.level_box_widths(kind, n, scales, log2_T, lattice.INDEX_DENSE_COARSE)
+    assert all(widths)
+    tables = np.zeros((L, T, 1))
+    for l in range(L):
+        B = widths[l]
+        box = np.stack(np.meshgrid(*([np.arange(B)] * n), indexing="ij"), -1).reshape(-1, n)
+        pos = lattice.unskew(box.astype(float)) if kind == "simplex" else box.astype(float)
+        tables[l, lattice.dense_slot(box, B, log2_T), 0] = fn(pos / float(scales[l]))
+    x = np.concatenate([synth.uniform_points(300, n, 181), synth.edge_points(n, 182, per_kind=4)])
+    if kind == "simplex":
+        out = encoding.simplex_encode(x, tables, base_res=base, growth=growth, index_mode=lattice.INDEX_DENSE_COARSE)
+    else:
+        out = encoding.grid_encode(x, tables, base_res=base, growth=growth, index_mode=lattice.INDEX_DENSE_COARSE)
+    for l in range(L):
+        if kind == "simplex":
+            q = lattice.scaled_skewed_fp32(x, scales[l]).astype(np.float64)
+            xs = lattice.unskew(q) / float(scales[l])
+        else:
+            xs = (x * np.float32(scales[l])).astype(np.float64) / float(scales[l])
+        np.testing.assert_allclose(out[:, l], fn(xs), rtol=0, atol=1e-11)
