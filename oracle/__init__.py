@@ -20,6 +20,8 @@ function.  Modules:
 * ``mlp``      -- the tiny fully connected ReLU network, its backward pass and
   the L2 loss (Sec. 5 d-e, Sec. 6.1).
 * ``adam``     -- the Adam update used to train tables and weights.
+* ``render``   -- volumetric rendering with the encodings: ray samples, the
+  quadrature of Eq. 5, spherical harmonics of the view direction (Sec. 6.2).
 * ``geometry`` -- brute-force and closed-form facts used only to pin the
   oracle itself (Theorems 1-5, Lemma 4, Sec. 5.2 volume ratio).
 
