@@ -88,10 +88,12 @@ def composite(sigma, rgb, delta):
     T = np.ones(R)
     w = np.zeros((R, S))
     for i in range(S):
-        alpha = 1.0 - np.exp(-sigma[:, i] * delta)
+        # alpha = 1 - exp(-sigma delta) and the factor 1 - alpha = exp(-sigma delta) (Eq. 5's
+        # T = exp(-integral of sigma)) are formed without cancellation: expm1 and exp directly
+        alpha = -np.expm1(-sigma[:, i] * delta)
         w[:, i] = T * alpha
         C += w[:, i, None] * rgb[:, i]
-        T = T * (1.0 - alpha)
+        T = T * np.exp(-sigma[:, i] * delta)
     return C, T, w
 
 
