@@ -246,6 +246,8 @@ def run_gpu(args):
     # ---- comparators on the same GPU (encode forward + backward only, equal L, F, T)
     comparators = encode_sweep(dev) if (rank == 0 and not args.no_sweep) else None
     serving = serve_bench(dev) if (rank == 0 and not args.no_serve) else None
+    peaks_ra = random_access_peaks(dev, tr.state.numel() * 4, tr.tables) if rank == 0 else None
+    volume = volume_sweep(dev) if (rank == 0 and not args.no_volume) else None
 
     if rank == 0:
         value = BATCH * args.steps * world / (ms / 1e3)
@@ -278,8 +280,18 @@ def run_gpu(args):
             "clocks": clk.summary(),
             "final_loss": loss,
         }
+        contrib = BATCH * CFG["n_levels"] * (CFG["d"] + 1)
+        pred_bwd = n_touched / peaks_ra["red_f2_miss"] + (contrib - n_touched) / peaks_ra["red_f2_l2"]
+        line["random_access_roofline"] = {
+            "kernel": "encode_bwd", "contributions": contrib, "touched_entries": n_touched,
+            "peaks_ops_per_s": peaks_ra,
+            "predicted_ms": pred_bwd * 1e3, "measured_ms": per_kernel["encode_bwd"],
+            "frac": pred_bwd * 1e3 / per_kernel["encode_bwd"],
+            "model": "first touch of an entry = one random float2 reduction missing L2; later ones hit"}
         if comparators is not None:
             line["comparators"] = comparators
+        if volume is not None:
+            line["volume"] = volume
         if serving is not None:
             line["serve"] = serving
         if not args.no_cpu:
@@ -332,6 +344,81 @@ def encode_sweep(dev, reps=20):
                 row["simplex_plain_f32"] = P * reps / (s.elapsed_time(e) / 1e3)
         out["d%d" % d] = row
     return {"encode_fwd_bwd_points_per_s": out, "config": "L=16 F=2 T=2^19 base 16 growth 1.38, 2^20 points"}
+
+
+def random_access_peaks(dev, state_bytes, table, n_ops=1 << 24, reps=5):
+    """Peak rates of the scattered patterns that bound the table kernels, measured on this GPU
+    with the library's probe: float2 reductions into random 32-byte records of a footprint the
+    size of the table state (L2 misses) and of 8 MiB (L2 hits), and 4-byte gathers from the
+    fp16 tables.  Returns ops/s."""
+    import torch
+    from paper_2311_15439_gb300 import _lib as L
+    lib = L.lib()
+    n_rec = 1 << int(math.log2(state_bytes // 32))
+    buf = torch.zeros((n_rec, 8), dtype=torch.float32, device=dev)
+    sink = torch.zeros((1,), dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    tab = table.view(torch.float32).reshape(-1)
+    cases = {"red_f2_miss": (0, buf, n_rec, 8), "red_f2_l2": (0, buf, 1 << 18, 8),
+             "gather_4B_table": (1, tab, 1 << int(math.log2(tab.numel())), 1)}
+    out = {}
+    for name, (kind, b, slots, sf) in cases.items():
+        if sf < 2:          # 4-byte gathers: slots of 2 floats over the first half of the table words
+            slots, sf = slots // 2, 2
+        lib.sxe_probe_random_access(kind, b.data_ptr(), slots, sf, n_ops, 1, sink.data_ptr(), st)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for r in range(reps):
+            L.check(lib.sxe_probe_random_access(kind, b.data_ptr(), slots, sf, n_ops, 2 + r, sink.data_ptr(), st),
+                    "sxe_probe_random_access")
+        e.record()
+        torch.cuda.synchronize(dev)
+        out[name] = n_ops * reps / (s.elapsed_time(e) / 1e3)
+    del buf
+    return out
+
+
+def volume_sweep(dev, n_rays=1 << 16, samples=(1, 4, 16, 64, 256, 1024), reps=3):
+    """Volumetric rendering (Sec. 6.2): 2^16 rays from a sphere around the unit cube, S midpoint
+    samples per ray, encoding (L=16, F=2, T=2^19 fp16, growth 1.38) -> density network -> field
+    head -> colour network -> compositing.  Render time and encoding-stage time per S, simplex vs
+    the 8-corner trilinear grid, and their ratio (the paper's Fig. of kernel run-time vs samples)."""
+    import torch
+    from paper_2311_15439_gb300 import synth
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.render import Renderer
+    rays = [torch.from_numpy(a).to(dev) for a in synth.camera_rays(n_rays, 60)]
+    res = {}
+    for kind in ("simplex", "grid"):
+        enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, table_dtype="f16")
+        vals, store = synth.uniform_tables(16, 1 << 19, 2, 61, dtype="f16", scale=1.0)
+        tab = torch.from_numpy(store).to(dev)
+        for S in samples:
+            rr = Renderer(enc, n_rays, S, dtype="f16", device=dev)
+            Wd, Wc = rr.init_weights(62)
+            color = torch.empty((n_rays, 3), device=dev)
+            rr.render(*rays, tab, Wd, Wc, color=color)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            torch.cuda.synchronize(dev)
+            ev[0].record()
+            for _ in range(reps):
+                rr.render(*rays, tab, Wd, Wc, color=color)
+            ev[1].record()
+            x = rr.x[: n_rays * S]
+            ev[2].record()
+            for _ in range(reps):
+                enc.encode_fwd(x, tab, rr.enc_out[: n_rays * S])
+            ev[3].record()
+            torch.cuda.synchronize(dev)
+            res.setdefault(str(S), {})[kind] = {"render_ms": ev[0].elapsed_time(ev[1]) / reps,
+                                                "encode_ms": ev[2].elapsed_time(ev[3]) / reps}
+            del rr
+            torch.cuda.empty_cache()
+    for S, r in res.items():
+        r["grid_over_simplex_render"] = r["grid"]["render_ms"] / r["simplex"]["render_ms"]
+        r["grid_over_simplex_encode"] = r["grid"]["encode_ms"] / r["simplex"]["encode_ms"]
+    return {"rays": n_rays, "config": "d=3 L=16 F=2 T=2^19 fp16 growth 1.38; nets 32-64-16 and 32-64-64-3",
+            "by_samples_per_ray": res}
 
 
 def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5):
@@ -455,6 +542,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-volume", action="store_true")
     ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05"],
                     help="kernel of the network training pass")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

@@ -48,6 +48,7 @@ typedef enum {
 typedef enum { SXE_SIMPLEX = 0, SXE_GRID = 1 } sxe_kind;
 typedef enum { SXE_F32 = 0, SXE_F16 = 1, SXE_BF16 = 2 } sxe_dtype;
 typedef enum { SXE_RES_RAW = 0, SXE_RES_EQUAL_MEM = 1 } sxe_res_mode;
+typedef enum { SXE_INDEX_HASH = 0, SXE_INDEX_DENSE_COARSE = 1 } sxe_index_mode;
 
 #define SXE_MAX_LEVELS 32
 
@@ -66,6 +67,12 @@ typedef enum { SXE_RES_RAW = 0, SXE_RES_EQUAL_MEM = 1 } sxe_res_mode;
  *                (simplex only)
  *   table_dtype  storage type of the feature tables read by the forward pass
  *   out_dtype    type of the encoded output
+ *   index_mode   SXE_INDEX_HASH: every level hashes its vertices (Sec. 5 a).
+ *                SXE_INDEX_DENSE_COARSE: a level whose lattice box fits the table
+ *                stores vertex v directly at sum_i v_i B^i (uint32, modulo T), where
+ *                B = floor(top (1 + 2^-20)) + 2 coordinates per axis, top = s_l sqrt(n+1)
+ *                (simplex) or N_l (grid), if B^n <= T; the other levels hash.  No
+ *                collisions on those levels for points in [0,1]^n.
  */
 typedef struct {
   int32_t d;
@@ -78,6 +85,7 @@ typedef struct {
   int32_t res_mode;
   int32_t table_dtype;
   int32_t out_dtype;
+  int32_t index_mode;
 } sxe_encoding_desc;
 
 typedef struct sxe_encoder sxe_encoder;  /* opaque: level constants only, no device memory */
@@ -93,6 +101,10 @@ sxe_status sxe_encoder_destroy(sxe_encoder* enc);
 /* Copies the binary32 per-level multipliers (host float[L]) and the integer level
  * resolutions N_l (host int32[L]) into caller arrays; either may be NULL. */
 sxe_status sxe_encoder_level_params(const sxe_encoder* enc, float* level_scale, int32_t* level_res);
+
+/* Copies the per-level box width B of the directly indexed levels into host int32[L]
+ * (0 for a hashed level; all 0 under SXE_INDEX_HASH). */
+sxe_status sxe_encoder_level_index(const sxe_encoder* enc, int32_t* box_width);
 
 /* Forward encoding, Sec. 5 steps (a)-(d): for every point and level, scale and skew
  * (Eq. 2) the point, find its simplex by sorting the fractional parts (Sec. 4.2),
@@ -127,6 +139,22 @@ sxe_status sxe_encode_bwd(const sxe_encoder* enc, const float* x, int64_t n_poin
                           const float* dout, float* grad, int64_t grad_stride,
                           uint32_t* touched, void* stream);
 
+/* Gradient with respect to the points (the chain rule through Sec. 4.3's weights, Eq. 2's
+ * skew and the level scale; the paper does not state it):
+ *   dx[p][i] += sum_{l,f} dout[p][l*F+f] * d out[p][l*F+f] / d x_i
+ * Simplex: inside the point's simplex the output is affine in the fractional parts q - c,
+ * and d out / d q_i = H(v_{k+1}) - H(v_k) for the axis i added between vertices k and k+1
+ * (Remark 2); d/dx = s_l (I + F_n 1 1^T) d/dq.  Grid: the derivative of the n-linear
+ * weights, times N_l.  On faces and ties the value is the one-sided derivative of the
+ * simplex (cell) the forward pass picks.
+ *   tables  [L][T][F] of the encoder's table dtype (dense, as sxe_encode_fwd)
+ *   dout    [n_points][L*F] binary32
+ *   dx      [n_points][d] binary32, accumulated (+=); zero it for a plain gradient.
+ * All device pointers, caller-owned, 4-byte aligned (tables as sxe_encode_fwd).
+ * One kernel on `stream`. */
+sxe_status sxe_encode_bwd_input(const sxe_encoder* enc, const float* x, int64_t n_points,
+                                const void* tables, const float* dout, float* dx, void* stream);
+
 /* The lattice vertices the encoding reads, for testing and inspection:
  *   slots    [n_points][L][V] uint32 table slots (0..T-1) of each vertex
  *   weights  [n_points][L][V] binary32 interpolation weights
@@ -139,13 +167,59 @@ sxe_status sxe_encode_vertices(const sxe_encoder* enc, const float* x, int64_t n
  * the levels, orders the fractional parts with a bubble sort (the paper's choice,
  * Sec. 4.2 footnote), walks the vertices one axis at a time (Remark 2), loads every
  * feature and adds every gradient term separately.  Same arithmetic and results as
- * sxe_encode_fwd / sxe_encode_bwd; requires kind = SXE_SIMPLEX and binary32 tables and
- * output (else SXE_EUNSUPPORTED).  out [n_points][L*F] is overwritten; grad is a dense
+ * sxe_encode_fwd / sxe_encode_bwd; requires kind = SXE_SIMPLEX, SXE_INDEX_HASH and
+ * binary32 tables and output (else SXE_EUNSUPPORTED).  out [n_points][L*F] is overwritten; grad is a dense
  * [L][T][F] binary32 array, accumulated. */
 sxe_status sxe_encode_plain_fwd(const sxe_encoder* enc, const float* x, int64_t n_points,
                                 const float* tables, float* out, void* stream);
 sxe_status sxe_encode_plain_bwd(const sxe_encoder* enc, const float* x, int64_t n_points,
                                 const float* dout, float* grad, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Volumetric rendering with the encodings (Sec. 6.2, Eq. 5).                 */
+/* ------------------------------------------------------------------------ */
+
+/* Ray samples: for ray r with origin o[r][3], direction d[r][3] and interval
+ * [t_near[r], t_far[r]], delta[r] = (t_far - t_near) / S and sample k at
+ * x[r*S + k][3] = o + t_k d, t_k = t_near + (k + 1/2) delta, each binary32 operation
+ * rounded once in this order (no contraction).  The paper does not state its sampling;
+ * this is the midpoint rule on S equal segments.  x [n_rays*S][3] and delta [n_rays]
+ * binary32 are overwritten.  1 <= S <= 2^20. */
+sxe_status sxe_vr_samples(const float* origins, const float* dirs, const float* t_near,
+                          const float* t_far, int64_t n_rays, int32_t n_samples, float* x,
+                          float* delta, void* stream);
+
+/* Field head between the density and the colour network (Instant-NGP's layout, which
+ * Sec. 6.2 builds on): from the density network's 16 binary32 outputs per sample,
+ * density_out [n_rays*S][16] (16-byte aligned), writes sigma [n_rays*S] = exp(min(v_0, 15))
+ * and the colour network's input color_in [n_rays*S][32] of `dtype` (SXE_F16 / SXE_BF16,
+ * 16-byte aligned): the 16 outputs, then the 16 real spherical harmonics of degree <= 3
+ * (l-major, m = -l..l; orthonormal, Condon-Shortley phase folded in) of the ray's unit
+ * direction dirs [n_rays][3]. */
+sxe_status sxe_vr_field(const float* density_out, const float* dirs, int64_t n_rays,
+                        int32_t n_samples, int32_t dtype, float* sigma, void* color_in,
+                        void* stream);
+
+/* Front-to-back compositing of Eq. 5 for a field constant on each segment:
+ *   T_k = exp(-sum_{j<k} sigma_j delta), w_k = T_k (1 - exp(-sigma_k delta)),
+ *   color[r][c] = sum_k w_k sigmoid(rgb_logits[r*S+k][c]).
+ * sigma [n_rays*S] >= 0, rgb_logits [n_rays*S][3], delta [n_rays] binary32.  Writes
+ * color [n_rays][3]; transmittance [n_rays] = exp(-sum_k sigma_k delta) and
+ * weights [n_rays*S] = w_k if not NULL.  One warp per ray (a shuffle scan of sigma delta). */
+sxe_status sxe_vr_composite(const float* sigma, const float* rgb_logits, const float* delta,
+                            int64_t n_rays, int32_t n_samples, float* color,
+                            float* transmittance, float* weights, void* stream);
+
+/* Measurement aid (no counterpart in the paper): n_ops scattered accesses to random slots
+ * of buf [n_slots][slot_floats] binary32 (n_slots a power of two, slot_floats even, 2..64),
+ * slot = mix64(seed ^ i) mod n_slots with a counter-based 64-bit mixer:
+ *   kind 0: a float2 atomic add of (1, 1) into the slot's last two floats
+ *           (the shape of the table backward's reductions into state records);
+ *   kind 1: a 4-byte load of the slot's first float (the shape of the forward gathers);
+ *           sink [1] is written only if the loaded sum is -1.
+ * Timed by the caller to give the peak rate of that pattern for a given footprint. */
+sxe_status sxe_probe_random_access(int32_t kind, float* buf, int64_t n_slots, int32_t slot_floats,
+                                   int64_t n_ops, uint64_t seed, float* sink, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Tiny fully connected network (Sec. 5 d-e; about 7k weights, Sec. 6.1).     */

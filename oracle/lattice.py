@@ -10,13 +10,13 @@ Restates, in the paper's order and notation:
   Sec. 4.2, Remark 2);
 * the barycentric weights w_1 = 1 - s_1, w_k = s_{k-1} - s_k, w_{n+1} = s_n on the
   sorted fractional parts s (Sec. 4.3, from the proof of Theorem 1);
-* the vertex hash of Sec. 5 (a) ("hashing their integer coordinates").
+* the vertex hash of Sec. 5 (a) (each vertex's integer coordinates are hashed).
 
 Readings where the paper is silent (each also listed in the design notes):
 
 * Level resolution N_l = floor(base * growth^l), the Instant-NGP rule the
   backbone of Sec. 5 uses; no +0.5 offset; the point is used as given.
-* "Adjustment scale S_n" (Sec. 5.1) is read as dividing the level-scaled
+* The adjustment scale S_n of Sec. 5.1 is read as dividing the level-scaled
   input by S_n = sqrt(n+1) *before* the skew, so that the skewed image of the
   unit cube fits the lattice box [0, N_l]^n.  (Pinned by the memory-usage
   figure of Sec. 5.2, see tests.)

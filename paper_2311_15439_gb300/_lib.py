@@ -15,13 +15,16 @@ SXE_OK, SXE_EINVAL, SXE_EUNSUPPORTED, SXE_ECUDA, SXE_ENOMEM = 0, -1, -2, -3, -4
 SXE_SIMPLEX, SXE_GRID = 0, 1
 SXE_F32, SXE_F16, SXE_BF16 = 0, 1, 2
 SXE_RES_RAW, SXE_RES_EQUAL_MEM = 0, 1
+SXE_INDEX_HASH, SXE_INDEX_DENSE_COARSE = 0, 1
 SXE_MAX_LEVELS = 32
 SXE_MLP_KERNEL_AUTO, SXE_MLP_KERNEL_MMA_SYNC, SXE_MLP_KERNEL_TCGEN05 = 0, 1, 2
 
 #: every function the header declares (checked by the export test)
 EXPORTS = (
-    "sxe_encoder_create", "sxe_encoder_destroy", "sxe_encoder_level_params",
-    "sxe_encode_fwd", "sxe_encode_bwd", "sxe_encode_vertices", "sxe_encode_plain_fwd", "sxe_encode_plain_bwd",
+    "sxe_encoder_create", "sxe_encoder_destroy", "sxe_encoder_level_params", "sxe_encoder_level_index",
+    "sxe_encode_fwd", "sxe_encode_bwd", "sxe_encode_bwd_input", "sxe_encode_vertices",
+    "sxe_encode_plain_fwd", "sxe_encode_plain_bwd", "sxe_vr_samples", "sxe_vr_field", "sxe_vr_composite",
+    "sxe_probe_random_access",
     "sxe_mlp_n_params", "sxe_mlp_fwd", "sxe_mlp_bwd_workspace_bytes", "sxe_mlp_bwd", "sxe_mlp_train_l2",
     "sxe_loss_l2", "sxe_step", "sxe_step_touched", "sxe_last_error", "sxe_version",
     "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped",
@@ -33,7 +36,7 @@ class EncodingDesc(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("n_features", ctypes.c_int32),
                 ("log2_T", ctypes.c_int32), ("base_res", ctypes.c_double), ("growth", ctypes.c_double),
                 ("kind", ctypes.c_int32), ("res_mode", ctypes.c_int32), ("table_dtype", ctypes.c_int32),
-                ("out_dtype", ctypes.c_int32)]
+                ("out_dtype", ctypes.c_int32), ("index_mode", ctypes.c_int32)]
 
 
 class MlpDesc(ctypes.Structure):
@@ -58,10 +61,16 @@ def _declare(L):
         "sxe_encoder_create": (i32, [E, ctypes.POINTER(vp)]),
         "sxe_encoder_destroy": (i32, [vp]),
         "sxe_encoder_level_params": (i32, [vp, vp, vp]),
+        "sxe_encoder_level_index": (i32, [vp, vp]),
         "sxe_encode_fwd": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_encode_bwd": (i32, [vp, vp, i64, vp, vp, i64, vp, vp]),
+        "sxe_encode_bwd_input": (i32, [vp, vp, i64, vp, vp, vp, vp]),
         "sxe_encode_vertices": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_encode_plain_fwd": (i32, [vp, vp, i64, vp, vp, vp]),
+        "sxe_vr_samples": (i32, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
+        "sxe_probe_random_access": (i32, [i32, vp, i64, i32, i64, ctypes.c_uint64, vp, vp]),
+        "sxe_vr_field": (i32, [vp, vp, i64, i32, i32, vp, vp, vp]),
+        "sxe_vr_composite": (i32, [vp, vp, vp, i64, i32, vp, vp, vp, vp]),
         "sxe_encode_plain_bwd": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_mlp_n_params": (i64, [M]),
         "sxe_mlp_fwd": (i32, [M, vp, vp, i64, vp, vp, vp]),

@@ -20,6 +20,7 @@ _DTYPES = {"f32": (L.SXE_F32, torch.float32), "f16": (L.SXE_F16, torch.float16),
            "bf16": (L.SXE_BF16, torch.bfloat16)}
 _KINDS = {"simplex": L.SXE_SIMPLEX, "grid": L.SXE_GRID}
 _RES = {"raw": L.SXE_RES_RAW, "equal_mem": L.SXE_RES_EQUAL_MEM}
+_INDEX = {"hash": L.SXE_INDEX_HASH, "dense_coarse": L.SXE_INDEX_DENSE_COARSE}
 
 
 def torch_dtype(name: str) -> torch.dtype:
@@ -53,16 +54,19 @@ class Encoder:
     """Multiresolution simplex (or 2^d grid) hash encoding, ``sxe_encoder_*`` / ``sxe_encode_*``."""
 
     def __init__(self, d: int, n_levels: int, n_features: int, log2_T: int, base_res: float, growth: float,
-                 kind: str = "simplex", res_mode: str = "raw", table_dtype: str = "f16", out_dtype: str | None = None):
+                 kind: str = "simplex", res_mode: str = "raw", table_dtype: str = "f16", out_dtype: str | None = None,
+                 index_mode: str = "hash"):
         self.d, self.n_levels, self.n_features, self.log2_T = d, n_levels, n_features, log2_T
         self.base_res, self.growth, self.kind, self.res_mode = base_res, growth, kind, res_mode
+        self.index_mode = index_mode
         self.table_dtype = table_dtype
         self.out_dtype = out_dtype or table_dtype
         self.T = 1 << log2_T
         self.n_out = n_levels * n_features
         self.n_vertices = d + 1 if kind == "simplex" else (1 << d)
         desc = L.EncodingDesc(d, n_levels, n_features, log2_T, float(base_res), float(growth), _KINDS[kind],
-                              _RES[res_mode], _DTYPES[table_dtype][0], _DTYPES[self.out_dtype][0])
+                              _RES[res_mode], _DTYPES[table_dtype][0], _DTYPES[self.out_dtype][0],
+                              _INDEX[index_mode])
         h = ctypes.c_void_p()
         L.check(L.lib().sxe_encoder_create(ctypes.byref(desc), ctypes.byref(h)), "sxe_encoder_create")
         self._h = h
@@ -86,6 +90,12 @@ class Encoder:
         r = np.zeros(self.n_levels, dtype=np.int32)
         L.check(L.lib().sxe_encoder_level_params(self._h, s.ctypes.data, r.ctypes.data), "sxe_encoder_level_params")
         return s, r
+
+    def level_index(self):
+        """int32 box width B per level for directly indexed levels, 0 for hashed ones."""
+        w = np.zeros(self.n_levels, dtype=np.int32)
+        L.check(L.lib().sxe_encoder_level_index(self._h, w.ctypes.data), "sxe_encoder_level_index")
+        return w
 
     def encode_fwd(self, x: torch.Tensor, tables: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         P = x.shape[0]
@@ -117,6 +127,20 @@ class Encoder:
         L.check(L.lib().sxe_encode_bwd(self._h, _ptr(x), P, _ptr(dout), gp, stride, _ptr(touched), _stream(stream)),
                 "sxe_encode_bwd")
         return grad
+
+    def encode_bwd_input(self, x: torch.Tensor, tables: torch.Tensor, dout: torch.Tensor,
+                         dx: torch.Tensor | None = None, stream=None):
+        """dx += d(out)/dx^T dout (``sxe_encode_bwd_input``); returns dx [P, d] float32."""
+        P = x.shape[0]
+        _need(x, torch.float32, "x", (P, self.d))
+        _need(tables, torch_dtype(self.table_dtype), "tables", self.table_shape())
+        _need(dout, torch.float32, "dout", (P, self.n_out))
+        if dx is None:
+            dx = torch.zeros((P, self.d), dtype=torch.float32, device=x.device)
+        _need(dx, torch.float32, "dx", (P, self.d))
+        L.check(L.lib().sxe_encode_bwd_input(self._h, _ptr(x), P, _ptr(tables), _ptr(dout), _ptr(dx),
+                                             _stream(stream)), "sxe_encode_bwd_input")
+        return dx
 
     def encode_plain_fwd(self, x: torch.Tensor, tables: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         """Plain binary32 comparator path (``sxe_encode_plain_fwd``)."""

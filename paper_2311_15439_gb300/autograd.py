@@ -2,7 +2,8 @@
 
 ``SimplexEncodingFunction`` (and the same class for the grid comparator) returns the
 encoding of ``x`` from ``tables`` and, in backward, the table gradient computed by
-``sxe_encode_bwd`` (Sec. 5 e).  The input gradient dL/dx is not provided (None).
+``sxe_encode_bwd`` (Sec. 5 e) and, when ``x`` requires it, the input gradient dL/dx
+computed by ``sxe_encode_bwd_input``.
 ``MlpFunction`` wraps ``sxe_mlp_fwd`` / ``sxe_mlp_bwd`` and returns dL/din and dL/dW.
 """
 from __future__ import annotations
@@ -17,18 +18,23 @@ class EncodingFunction(torch.autograd.Function):
     def forward(ctx, x: torch.Tensor, tables: torch.Tensor, encoder: Encoder):
         x = x.contiguous()
         out = encoder.encode_fwd(x, tables.contiguous())
-        ctx.save_for_backward(x)
+        ctx.save_for_backward(x, tables)
         ctx.encoder = encoder
         ctx.tables_dtype = tables.dtype
         return out
 
     @staticmethod
     def backward(ctx, dout: torch.Tensor):
-        (x,) = ctx.saved_tensors
+        x, tables = ctx.saved_tensors
         enc = ctx.encoder
-        grad = torch.zeros(enc.table_shape(), dtype=torch.float32, device=x.device)
-        enc.encode_bwd(x, dout.to(torch.float32).contiguous(), grad)
-        return None, grad.to(ctx.tables_dtype), None
+        dout = dout.to(torch.float32).contiguous()
+        grad = None
+        if ctx.needs_input_grad[1]:
+            grad = torch.zeros(enc.table_shape(), dtype=torch.float32, device=x.device)
+            enc.encode_bwd(x, dout, grad)
+            grad = grad.to(ctx.tables_dtype)
+        dx = enc.encode_bwd_input(x, tables.contiguous(), dout) if ctx.needs_input_grad[0] else None
+        return dx, grad, None
 
 
 class MlpFunction(torch.autograd.Function):

@@ -61,6 +61,8 @@ sxe_status sxe_encoder_create(const sxe_encoding_desc* d, sxe_encoder** out) {
     return set_error(SXE_EINVAL, "encoder_create: res_mode applies to the simplex encoder only");
   if (!valid_dtype(d->table_dtype) || !valid_dtype(d->out_dtype))
     return set_error(SXE_EINVAL, "encoder_create: bad dtype");
+  if (d->index_mode != SXE_INDEX_HASH && d->index_mode != SXE_INDEX_DENSE_COARSE)
+    return set_error(SXE_EINVAL, "encoder_create: bad index_mode");
   const int64_t elems = ((int64_t)d->n_levels << d->log2_T) * d->n_features;
   if (elems >= ((int64_t)1 << 34)) return set_error(SXE_EINVAL, "encoder_create: tables too large");
 
@@ -80,12 +82,26 @@ sxe_status sxe_encoder_create(const sxe_encoding_desc* d, sxe_encoder** out) {
     }
     e->level_res[l] = (int32_t)N;
     e->prm.scale[l] = d->kind == SXE_SIMPLEX ? (float)(N * m / std::sqrt(n + 1.0)) : (float)N;
+    // Directly indexed level: the vertices of [0,1]^n take B = floor(top) + 2 values per axis,
+    // top = s_l sqrt(n+1) (simplex, q_i <= s_l (1 + n F_n)) or N_l (grid), with a 2^-20
+    // margin for binary32 rounding; used when B^n fits the table.
+    if (d->index_mode == SXE_INDEX_DENSE_COARSE) {
+      const double top = (double)e->prm.scale[l] * (d->kind == SXE_SIMPLEX ? std::sqrt(n + 1.0) : 1.0);
+      const double B = std::floor(top * (1.0 + std::ldexp(1.0, -20))) + 2.0;
+      if (std::pow(B, n) <= std::ldexp(1.0, d->log2_T)) e->prm.width[l] = (uint32_t)B;
+    }
   }
   e->prm.n_levels = d->n_levels;
   e->prm.log2_T = d->log2_T;
   e->prm.out_dtype = d->out_dtype;
   e->prm.skew_F = (float)((std::sqrt(n + 1.0) - 1.0) / n);
   *out = e;
+  return SXE_OK;
+}
+
+sxe_status sxe_encoder_level_index(const sxe_encoder* e, int32_t* width) {
+  if (!e || !width) return set_error(SXE_EINVAL, "encoder_level_index: NULL argument");
+  for (int l = 0; l < e->desc.n_levels; ++l) width[l] = (int32_t)e->prm.width[l];
   return SXE_OK;
 }
 
@@ -143,6 +159,71 @@ sxe_status sxe_encode_bwd(const sxe_encoder* e, const float* x, int64_t P, const
   return launch_encode_bwd(e, x, P, dout, grad, grad_stride, touched, (cudaStream_t)stream);
 }
 
+sxe_status sxe_encode_bwd_input(const sxe_encoder* e, const float* x, int64_t P, const void* tables,
+                                const float* dout, float* dx, void* stream) {
+  sxe_status st = check_points("encode_bwd_input", e, x, P);
+  if (st != SXE_OK) return st;
+  if (P == 0) return SXE_OK;
+  if (!tables || !dout || !dx) return set_error(SXE_EINVAL, "encode_bwd_input: NULL tables, dout or dx");
+  const int F = e->desc.n_features;
+  const size_t ta = std::min<size_t>(16, F * dtype_size(e->desc.table_dtype));
+  if (!aligned(tables, ta)) return set_error(SXE_EINVAL, "encode_bwd_input: tables must be %zu-byte aligned", ta);
+  if (!aligned(dout, 4) || !aligned(dx, 4)) return set_error(SXE_EINVAL, "encode_bwd_input: dout or dx misaligned");
+  return launch_encode_bwd_input(e, x, P, tables, dout, dx, (cudaStream_t)stream);
+}
+
+static sxe_status check_rays(const char* fn, int64_t R, int32_t S) {
+  if (R < 0 || S < 1 || S > (1 << 20) || R > ((int64_t)1 << 36) / S)
+    return set_error(SXE_EINVAL, "%s: n_rays=%lld n_samples=%d out of range", fn, (long long)R, S);
+  return SXE_OK;
+}
+
+sxe_status sxe_vr_samples(const float* origins, const float* dirs, const float* t_near, const float* t_far,
+                          int64_t R, int32_t S, float* x, float* delta, void* stream) {
+  sxe_status st = check_rays("vr_samples", R, S);
+  if (st != SXE_OK || R == 0) return st;
+  if (!origins || !dirs || !t_near || !t_far || !x || !delta)
+    return set_error(SXE_EINVAL, "vr_samples: NULL buffer");
+  if (!aligned(origins, 4) || !aligned(dirs, 4) || !aligned(t_near, 4) || !aligned(t_far, 4) || !aligned(x, 4) ||
+      !aligned(delta, 4))
+    return set_error(SXE_EINVAL, "vr_samples: misaligned buffer");
+  return launch_vr_samples(origins, dirs, t_near, t_far, R, S, x, delta, (cudaStream_t)stream);
+}
+
+sxe_status sxe_vr_field(const float* density_out, const float* dirs, int64_t R, int32_t S, int32_t dtype,
+                        float* sigma, void* color_in, void* stream) {
+  sxe_status st = check_rays("vr_field", R, S);
+  if (st != SXE_OK || R == 0) return st;
+  if (dtype != SXE_F16 && dtype != SXE_BF16) return set_error(SXE_EINVAL, "vr_field: dtype must be f16 or bf16");
+  if (!density_out || !dirs || !sigma || !color_in) return set_error(SXE_EINVAL, "vr_field: NULL buffer");
+  if (!aligned(density_out, 16) || !aligned(color_in, 16) || !aligned(dirs, 4) || !aligned(sigma, 4))
+    return set_error(SXE_EINVAL, "vr_field: density_out and color_in must be 16-byte aligned");
+  return launch_vr_field(density_out, dirs, R, S, dtype, sigma, color_in, (cudaStream_t)stream);
+}
+
+sxe_status sxe_vr_composite(const float* sigma, const float* rgb_logits, const float* delta, int64_t R, int32_t S,
+                            float* color, float* transmittance, float* weights, void* stream) {
+  sxe_status st = check_rays("vr_composite", R, S);
+  if (st != SXE_OK || R == 0) return st;
+  if (!sigma || !rgb_logits || !delta || !color) return set_error(SXE_EINVAL, "vr_composite: NULL buffer");
+  if (!aligned(sigma, 4) || !aligned(rgb_logits, 4) || !aligned(delta, 4) || !aligned(color, 4) ||
+      !aligned(transmittance, 4) || !aligned(weights, 4))
+    return set_error(SXE_EINVAL, "vr_composite: misaligned buffer");
+  return launch_vr_composite(sigma, rgb_logits, delta, R, S, color, transmittance, weights, (cudaStream_t)stream);
+}
+
+sxe_status sxe_probe_random_access(int32_t kind, float* buf, int64_t n_slots, int32_t slot_floats, int64_t n_ops,
+                                   uint64_t seed, float* sink, void* stream) {
+  if (kind != 0 && kind != 1) return set_error(SXE_EINVAL, "probe_random_access: kind must be 0 or 1");
+  if (n_slots < 1 || (n_slots & (n_slots - 1)) != 0 || n_slots > ((int64_t)1 << 34))
+    return set_error(SXE_EINVAL, "probe_random_access: n_slots must be a power of two");
+  if (slot_floats < 2 || slot_floats > 64 || (slot_floats & 1) || n_ops < 0)
+    return set_error(SXE_EINVAL, "probe_random_access: slot_floats must be even in 2..64");
+  if (!buf || !sink || !aligned(buf, 8)) return set_error(SXE_EINVAL, "probe_random_access: NULL or misaligned buffer");
+  if (n_ops == 0) return SXE_OK;
+  return launch_probe(kind, buf, n_slots, slot_floats, n_ops, seed, sink, (cudaStream_t)stream);
+}
+
 sxe_status sxe_encode_vertices(const sxe_encoder* e, const float* x, int64_t P, uint32_t* slots, float* weights,
                                void* stream) {
   sxe_status st = check_points("encode_vertices", e, x, P);
@@ -155,8 +236,9 @@ static sxe_status check_plain(const char* fn, const sxe_encoder* e, const float*
                               const void* b) {
   sxe_status st = check_points(fn, e, x, P);
   if (st != SXE_OK) return st;
-  if (e->desc.kind != SXE_SIMPLEX || e->desc.table_dtype != SXE_F32 || e->desc.out_dtype != SXE_F32)
-    return set_error(SXE_EUNSUPPORTED, "%s: needs a simplex encoder with binary32 tables and output", fn);
+  if (e->desc.kind != SXE_SIMPLEX || e->desc.table_dtype != SXE_F32 || e->desc.out_dtype != SXE_F32 ||
+      e->desc.index_mode != SXE_INDEX_HASH)
+    return set_error(SXE_EUNSUPPORTED, "%s: needs a hashed simplex encoder with binary32 tables and output", fn);
   if (P > 0 && (!a || !b)) return set_error(SXE_EINVAL, "%s: NULL buffer", fn);
   return SXE_OK;
 }

@@ -15,20 +15,22 @@ constexpr int kThreads = 256;
 template <bool SIMPLEX, int D> struct Verts { static constexpr int V = SIMPLEX ? D + 1 : (1 << D); };
 
 template <bool SIMPLEX, int D>
-__device__ __forceinline__ void lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
+__device__ __forceinline__ void lattice(const float (&x)[D], float s, float skewF, uint32_t mask, uint32_t width,
                                         uint32_t (&slot)[Verts<SIMPLEX, D>::V], float (&w)[Verts<SIMPLEX, D>::V]) {
-  if constexpr (SIMPLEX) simplex_lattice<D>(x, s, skewF, mask, slot, w);
-  else grid_lattice<D>(x, s, mask, slot, w);
+  if constexpr (SIMPLEX) simplex_lattice<D>(x, s, skewF, mask, width, slot, w);
+  else grid_lattice<D>(x, s, mask, width, slot, w);
 }
 
-// Decode work item i into (point, level) with small 32-bit divisions.
+// Decode work item i = blockIdx.x * kThreads + threadIdx.x into (point, level) = (i / L, i % L)
+// with 32-bit divisions only: blockIdx.x = qb L + rb gives i = qb kThreads L + j with
+// j = rb kThreads + threadIdx.x < L kThreads, so i / L = qb kThreads + j / L.
 struct Item { int64_t p; int l; };
 __device__ __forceinline__ Item item_of(int L) {
-  const int64_t base = (int64_t)blockIdx.x * kThreads;
-  const int64_t p0 = base / L;
-  const int j = (int)(base - p0 * L) + (int)threadIdx.x;
-  const int q = j / L;
-  return Item{p0 + q, j - q * L};
+  const uint32_t uL = (uint32_t)L;
+  const uint32_t qb = blockIdx.x / uL;
+  const uint32_t j = (blockIdx.x - qb * uL) * kThreads + threadIdx.x;
+  const uint32_t q = j / uL;
+  return Item{(int64_t)qb * kThreads + q, (int)(j - q * uL)};
 }
 
 template <int D>
@@ -51,7 +53,11 @@ encode_fwd_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__
                   void* __restrict__ out, const EncParams prm) {
   constexpr int V = Verts<SIMPLEX, D>::V;
   __shared__ float s_scale[SXE_MAX_LEVELS];
-  if (threadIdx.x < SXE_MAX_LEVELS) s_scale[threadIdx.x] = prm.scale[threadIdx.x];
+  __shared__ uint32_t s_width[SXE_MAX_LEVELS];
+  if (threadIdx.x < SXE_MAX_LEVELS) {
+    s_scale[threadIdx.x] = prm.scale[threadIdx.x];
+    s_width[threadIdx.x] = prm.width[threadIdx.x];
+  }
   __syncthreads();
   const int L = prm.n_levels;
   const Item it = item_of(L);
@@ -61,7 +67,7 @@ encode_fwd_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__
   const uint32_t mask = (1u << prm.log2_T) - 1u;
   uint32_t slot[V];
   float w[V];
-  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
+  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, s_width[it.l], slot, w);
   const TT* tab = tables + ((int64_t)it.l << prm.log2_T) * tstride;
   float val[V][F];
 #pragma unroll
@@ -106,7 +112,11 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
                   const EncParams prm, int l0, int nl, bool dout_level_major) {
   constexpr int V = Verts<SIMPLEX, D>::V;
   __shared__ float s_scale[SXE_MAX_LEVELS];
-  if (threadIdx.x < SXE_MAX_LEVELS) s_scale[threadIdx.x] = prm.scale[threadIdx.x];
+  __shared__ uint32_t s_width[SXE_MAX_LEVELS];
+  if (threadIdx.x < SXE_MAX_LEVELS) {
+    s_scale[threadIdx.x] = prm.scale[threadIdx.x];
+    s_width[threadIdx.x] = prm.width[threadIdx.x];
+  }
   __syncthreads();
   const int L = prm.n_levels;
   Item it = item_of(nl);
@@ -127,7 +137,7 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
   const uint32_t mask = (1u << prm.log2_T) - 1u;
   uint32_t slot[V];
   float w[V];
-  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, slot, w);
+  lattice<SIMPLEX, D>(xv, s_scale[it.l], prm.skew_F, mask, s_width[it.l], slot, w);
   const int64_t lbase = (int64_t)it.l << prm.log2_T;
   // all bitmap words in flight at once, then the (fire-and-forget) atomics, then the marks
   uint32_t words[V];
@@ -164,7 +174,7 @@ encode_vertices_kernel(const float* __restrict__ x, int64_t P, uint32_t* __restr
   load_point<D>(x, it.p, xv);
   uint32_t slot[V];
   float w[V];
-  lattice<SIMPLEX, D>(xv, prm.scale[it.l], prm.skew_F, (1u << prm.log2_T) - 1u, slot, w);
+  lattice<SIMPLEX, D>(xv, prm.scale[it.l], prm.skew_F, (1u << prm.log2_T) - 1u, prm.width[it.l], slot, w);
   const int64_t o = (it.p * L + it.l) * V;
 #pragma unroll
   for (int k = 0; k < V; ++k) {
@@ -176,6 +186,162 @@ encode_vertices_kernel(const float* __restrict__ x, int64_t P, uint32_t* __restr
 inline unsigned grid_for(int64_t P, int L) { return (unsigned)((P * L + kThreads - 1) / kThreads); }
 
 // ---- dispatch ---------------------------------------------------------------
+// Input gradient: dx[p][i] += sum over levels and features of dout * d out / d x_i.
+// Simplex (Sec. 4.3 weights): inside the point's simplex the output is affine in the
+// fractional parts, and moving f along the axis of rank k shifts weight from vertex k to
+// vertex k+1, so d out / d q_i = H(v_{rank_i + 1}) - H(v_{rank_i}); Eq. 2's skew matrix
+// is symmetric (d/dp_j = g_j + F_n sum_i g_i) and p = x s_l.  Grid (Algorithm 1): the
+// derivative of the n-linear weights along each axis, times N_l.  The levels of one point
+// are consecutive lanes: a segmented shuffle reduction leaves one atomic add per axis per
+// point and warp.
+template <bool SIMPLEX, int D, int F, typename TT>
+__global__ void __launch_bounds__(kThreads)
+encode_dx_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__ tables,
+                 const float* __restrict__ dout, float* __restrict__ dx, const EncParams prm) {
+  constexpr int V = Verts<SIMPLEX, D>::V;
+  __shared__ float s_scale[SXE_MAX_LEVELS];
+  __shared__ uint32_t s_width[SXE_MAX_LEVELS];
+  if (threadIdx.x < SXE_MAX_LEVELS) {
+    s_scale[threadIdx.x] = prm.scale[threadIdx.x];
+    s_width[threadIdx.x] = prm.width[threadIdx.x];
+  }
+  __syncthreads();
+  const int L = prm.n_levels;
+  const Item it = item_of(L);
+  const bool live = it.p < P;
+  float g[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) g[i] = 0.f;
+  if (live) {
+    float xv[D];
+    load_point<D>(x, it.p, xv);
+    float dl[F];
+    const float* pd = dout + (it.p * L + it.l) * F;
+#pragma unroll
+    for (int f = 0; f < F; ++f) dl[f] = __ldg(pd + f);
+    const uint32_t mask = (1u << prm.log2_T) - 1u;
+    const float s = s_scale[it.l];
+    uint32_t slot[V];
+    float w[V];
+    const TT* tab = tables + ((int64_t)it.l << prm.log2_T) * F;
+    if constexpr (SIMPLEX) {
+      int rank[D];
+      simplex_lattice<D>(xv, s, prm.skew_F, mask, s_width[it.l], slot, w, rank);
+      float proj[V];                                  // dout . H(v_k)
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        float h[F];
+        load_entry<TT, F>(tab + (int64_t)slot[k] * F, h);
+        float a = 0.f;
+#pragma unroll
+        for (int f = 0; f < F; ++f) a = fmaf(dl[f], h[f], a);
+        proj[k] = a;
+      }
+      float gq[D], sum = 0.f;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        float v = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) v = (rank[i] == k) ? proj[k + 1] - proj[k] : v;
+        gq[i] = v;
+        sum += v;
+      }
+      const float t = prm.skew_F * sum;
+#pragma unroll
+      for (int i = 0; i < D; ++i) g[i] = s * (gq[i] + t);
+    } else {
+      float fr[D];
+      grid_lattice<D>(xv, s, mask, s_width[it.l], slot, w, fr);
+      float proj[V];
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        float h[F];
+        load_entry<TT, F>(tab + (int64_t)slot[k] * F, h);
+        float a = 0.f;
+#pragma unroll
+        for (int f = 0; f < F; ++f) a = fmaf(dl[f], h[f], a);
+        proj[k] = a;
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float a = 0.f;
+#pragma unroll
+        for (int b = 0; b < V; ++b) {
+          float wt = 1.f;
+#pragma unroll
+          for (int i = 0; i < D; ++i) {
+            const bool bi = (b >> (D - 1 - i)) & 1;
+            if (i == j) wt = bi ? wt : -wt;
+            else wt *= bi ? fr[i] : 1.f - fr[i];
+          }
+          a = fmaf(wt, proj[b], a);
+        }
+        g[j] = s * a;
+      }
+    }
+  }
+  // segmented reduction over the lanes that hold levels of the same point
+  const int lane = threadIdx.x & 31;
+  const uint32_t key = live ? (uint32_t)it.p : 0xffffffffu;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t ko = __shfl_down_sync(0xffffffffu, key, o);
+    const bool take = lane + o < 32 && ko == key;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float v = __shfl_down_sync(0xffffffffu, g[i], o);
+      if (take) g[i] += v;
+    }
+  }
+  const uint32_t kprev = __shfl_up_sync(0xffffffffu, key, 1);
+  if (live && (lane == 0 || kprev != key)) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) atomicAdd(dx + it.p * D + i, g[i]);
+  }
+}
+
+template <bool SIMPLEX, int D, int F>
+sxe_status dx_tt(const sxe_encoder* e, const float* x, int64_t P, const void* tab, const float* dout, float* dx,
+                 cudaStream_t s) {
+  const unsigned g = grid_for(P, e->prm.n_levels);
+  switch (e->desc.table_dtype) {
+    case SXE_F32: encode_dx_kernel<SIMPLEX, D, F, float><<<g, kThreads, 0, s>>>(x, P, (const float*)tab, dout, dx, e->prm); break;
+    case SXE_F16: encode_dx_kernel<SIMPLEX, D, F, __half><<<g, kThreads, 0, s>>>(x, P, (const __half*)tab, dout, dx, e->prm); break;
+    default: encode_dx_kernel<SIMPLEX, D, F, __nv_bfloat16><<<g, kThreads, 0, s>>>(x, P, (const __nv_bfloat16*)tab, dout, dx, e->prm); break;
+  }
+  return check_launch("encode_bwd_input");
+}
+
+template <bool SIMPLEX, int D>
+sxe_status dx_f(const sxe_encoder* e, const float* x, int64_t P, const void* t, const float* d, float* dx, cudaStream_t s) {
+  switch (e->desc.n_features) {
+    case 1: return dx_tt<SIMPLEX, D, 1>(e, x, P, t, d, dx, s);
+    case 2: return dx_tt<SIMPLEX, D, 2>(e, x, P, t, d, dx, s);
+    case 4: return dx_tt<SIMPLEX, D, 4>(e, x, P, t, d, dx, s);
+    default: return dx_tt<SIMPLEX, D, 8>(e, x, P, t, d, dx, s);
+  }
+}
+
+template <bool SIMPLEX>
+sxe_status dx_d(const sxe_encoder* e, const float* x, int64_t P, const void* t, const float* d, float* dx, cudaStream_t s) {
+  switch (e->desc.d) {
+    case 2: return dx_f<SIMPLEX, 2>(e, x, P, t, d, dx, s);
+    case 3: return dx_f<SIMPLEX, 3>(e, x, P, t, d, dx, s);
+    case 4: return dx_f<SIMPLEX, 4>(e, x, P, t, d, dx, s);
+    default: return dx_f<SIMPLEX, 5>(e, x, P, t, d, dx, s);
+  }
+}
+
+}  // namespace
+
+sxe_status launch_encode_bwd_input(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
+                                   const float* dout, float* dx, cudaStream_t s) {
+  return enc->desc.kind == SXE_SIMPLEX ? dx_d<true>(enc, x, P, tables, dout, dx, s)
+                                       : dx_d<false>(enc, x, P, tables, dout, dx, s);
+}
+
+namespace {
+
 template <bool SIMPLEX, int D, int F>
 sxe_status fwd_tt(const sxe_encoder* enc, const float* x, int64_t P, const void* tab, int64_t ts, void* out,
                   cudaStream_t s) {

@@ -26,6 +26,7 @@ struct EncParams {
   int32_t out_dtype;
   float skew_F;                    // F_n of Eq. 2 rounded to binary32 (simplex only)
   float scale[SXE_MAX_LEVELS];     // per-level input multiplier (binary32)
+  uint32_t width[SXE_MAX_LEVELS];  // box width B of a directly indexed level, 0 = hashed
 };
 
 }  // namespace sxe
@@ -52,6 +53,16 @@ sxe_status launch_encode_plain(const sxe_encoder* enc, bool backward, const floa
                                float* b, cudaStream_t s);
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,
                                   float* weights, cudaStream_t s);
+sxe_status launch_encode_bwd_input(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
+                                   const float* dout, float* dx, cudaStream_t s);
+sxe_status launch_vr_samples(const float* o, const float* d, const float* tn, const float* tf, int64_t R, int S,
+                             float* x, float* delta, cudaStream_t s);
+sxe_status launch_vr_field(const float* dens, const float* dirs, int64_t R, int S, int dtype, float* sigma,
+                           void* cin, cudaStream_t s);
+sxe_status launch_probe(int kind, float* buf, int64_t n_slots, int slot_floats, int64_t n_ops, uint64_t seed,
+                        float* sink, cudaStream_t s);
+sxe_status launch_vr_composite(const float* sigma, const float* logits, const float* delta, int64_t R, int S,
+                               float* color, float* trans, float* weights, cudaStream_t s);
 
 int mlp_grid_blocks(const sxe_mlp_desc* d, int64_t P);
 sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out,
@@ -188,11 +199,13 @@ __device__ __forceinline__ void store_lowp(void* base, int64_t e, int ldt, const
 //   larger, or equal with j < i: the stable decreasing order of the paper's sort.
 //   Remark 2: vertex k = c + sum of e_i over axes with rank_i < k.
 //   Sec. 4.3: w_0 = 1 - s_0, w_k = s_{k-1} - s_k, w_d = s_{d-1} on the sorted s.
-//   Sec. 5 (a): slot = XOR_i (uint32(v_i) * prime_i) mod T.
+//   Sec. 5 (a): slot = XOR_i (uint32(v_i) * prime_i) mod T; on a directly indexed level
+//   (width B > 0) slot = (sum_i uint32(v_i) * B^i) mod T instead.
 // ---------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
-                                                uint32_t (&slot)[D + 1], float (&w)[D + 1]) {
+                                                uint32_t width, uint32_t (&slot)[D + 1], float (&w)[D + 1],
+                                                int (&rank)[D]) {
   float p[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) p[i] = __fmul_rn(x[i], s);
@@ -202,16 +215,18 @@ __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, fl
   const float t = __fmul_rn(skewF, sigma);
   float f[D];
   uint32_t h0[D], h1[D];
+  uint32_t pw = 1u;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     const float q = __fadd_rn(p[i], t);
     const float fl = floorf(q);
     f[i] = __fsub_rn(q, fl);
     const uint32_t c = (uint32_t)__float2int_rz(fl);
-    h0[i] = c * hash_prime(i);
-    h1[i] = (c + 1u) * hash_prime(i);
+    const uint32_t mult = width ? pw : hash_prime(i);
+    pw *= width;
+    h0[i] = c * mult;
+    h1[i] = (c + 1u) * mult;
   }
-  int rank[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     int r = 0;
@@ -236,27 +251,39 @@ __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, fl
   for (int k = 0; k <= D; ++k) {
     uint32_t h = 0;
 #pragma unroll
-    for (int i = 0; i < D; ++i) h ^= (rank[i] < k) ? h1[i] : h0[i];
+    for (int i = 0; i < D; ++i) {
+      const uint32_t v = (rank[i] < k) ? h1[i] : h0[i];
+      h = width ? h + v : h ^ v;
+    }
     slot[k] = h & mask;
   }
+}
+
+template <int D>
+__device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
+                                                uint32_t width, uint32_t (&slot)[D + 1], float (&w)[D + 1]) {
+  int rank[D];
+  simplex_lattice<D>(x, s, skewF, mask, width, slot, w, rank);
 }
 
 // 2^D grid corners of one point at one level (Algorithm 1's multilinear weights):
 // p_i = x_i * N (binary32), c = floor(p), f = p - c; corner b (axis 0 = most
 // significant bit) has weight prod_i (b_i ? f_i : 1 - f_i), multiplied in axis order.
 template <int D>
-__device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint32_t mask,
-                                             uint32_t (&slot)[1 << D], float (&w)[1 << D]) {
-  float f[D];
+__device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint32_t mask, uint32_t width,
+                                             uint32_t (&slot)[1 << D], float (&w)[1 << D], float (&f)[D]) {
   uint32_t h0[D], h1[D];
+  uint32_t pw = 1u;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     const float p = __fmul_rn(x[i], N);
     const float fl = floorf(p);
     f[i] = __fsub_rn(p, fl);
     const uint32_t c = (uint32_t)__float2int_rz(fl);
-    h0[i] = c * hash_prime(i);
-    h1[i] = (c + 1u) * hash_prime(i);
+    const uint32_t mult = width ? pw : hash_prime(i);
+    pw *= width;
+    h0[i] = c * mult;
+    h1[i] = (c + 1u) * mult;
   }
 #pragma unroll
   for (int b = 0; b < (1 << D); ++b) {
@@ -266,11 +293,19 @@ __device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint3
     for (int i = 0; i < D; ++i) {
       const bool bi = (b >> (D - 1 - i)) & 1;
       wt = __fmul_rn(wt, bi ? f[i] : __fsub_rn(1.f, f[i]));
-      h ^= bi ? h1[i] : h0[i];
+      const uint32_t v = bi ? h1[i] : h0[i];
+      h = width ? h + v : h ^ v;
     }
     w[b] = wt;
     slot[b] = h & mask;
   }
+}
+
+template <int D>
+__device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint32_t mask, uint32_t width,
+                                             uint32_t (&slot)[1 << D], float (&w)[1 << D]) {
+  float f[D];
+  grid_lattice<D>(x, N, mask, width, slot, w, f);
 }
 
 }  // namespace sxe

@@ -1,0 +1,119 @@
+"""Volumetric rendering with the simplex (or grid) encoding, Sec. 6.2 (Eq. 5).
+
+A ``Renderer`` renders a batch of rays through the library's kernels only:
+
+1. ``sxe_vr_samples``   -- S midpoint samples per ray in [t_near, t_far];
+2. ``sxe_encode_fwd``   -- the multiresolution encoding of every sample (Sec. 5 a-d);
+3. ``sxe_mlp_fwd``      -- density network, encoding -> 64 -> 16;
+4. ``sxe_vr_field``     -- sigma = exp(min(v_0, 15)) and the colour input [v, SH(d)];
+5. ``sxe_mlp_fwd``      -- colour network, 32 -> 64 -> 64 -> 3;
+6. ``sxe_vr_composite`` -- sigmoid colours composited front to back (Eq. 5).
+
+All buffers are allocated once for the largest ray batch and reused; a render is six
+asynchronous launches on one stream.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+from .api import Encoder, Mlp, _need, _ptr, _stream, torch_dtype
+
+_VR_DTYPES = {"f16": L.SXE_F16, "bf16": L.SXE_BF16}
+
+
+class Renderer:
+    """Renders rays of a field = (encoder, density network, colour network)."""
+
+    def __init__(self, encoder: Encoder, max_rays: int, n_samples: int, *, dtype: str = "f16", device="cuda"):
+        if encoder.d != 3:
+            raise ValueError("volumetric rendering needs a 3-D encoder")
+        if encoder.out_dtype != dtype:
+            raise ValueError("encoder output dtype %s != network dtype %s" % (encoder.out_dtype, dtype))
+        self.enc, self.S, self.max_rays, self.dtype = encoder, n_samples, max_rays, dtype
+        self.density = Mlp(encoder.n_out, 16, n_hidden=1, dtype=dtype)
+        self.color = Mlp(32, 3, n_hidden=2, dtype=dtype)
+        dev = torch.device(device)
+        P = max_rays * n_samples
+        self.x = torch.empty((P, 3), dtype=torch.float32, device=dev)
+        self.delta = torch.empty((max_rays,), dtype=torch.float32, device=dev)
+        self.enc_out = torch.empty((P, encoder.n_out), dtype=torch_dtype(dtype), device=dev)
+        self.dens_out = torch.empty((P, 16), dtype=torch.float32, device=dev)
+        self.sigma = torch.empty((P,), dtype=torch.float32, device=dev)
+        self.color_in = torch.empty((P, 32), dtype=torch_dtype(dtype), device=dev)
+        self.logits = torch.empty((P, 3), dtype=torch.float32, device=dev)
+
+    def init_weights(self, seed: int):
+        """He-uniform weights of both networks in the network dtype (device tensors)."""
+        dev = self.x.device
+        Wd = torch.from_numpy(self.density.init_weights(seed)).to(dev).to(torch_dtype(self.dtype))
+        Wc = torch.from_numpy(self.color.init_weights(seed + 1)).to(dev).to(torch_dtype(self.dtype))
+        return Wd, Wc
+
+    def render(self, origins, dirs, t_near, t_far, tables, W_density, W_color, color=None, transmittance=None,
+               weights=None, stream=None):
+        """Colours [R, 3] (and optionally the remaining transmittance [R] and sample weights [R*S])."""
+        R = origins.shape[0]
+        if R > self.max_rays:
+            raise ValueError("batch of %d rays > max_rays %d" % (R, self.max_rays))
+        S = self.S
+        P = R * S
+        for t, name, shape in ((origins, "origins", (R, 3)), (dirs, "dirs", (R, 3)), (t_near, "t_near", (R,)),
+                               (t_far, "t_far", (R,))):
+            _need(t, torch.float32, name, shape)
+        if color is None:
+            color = torch.empty((R, 3), dtype=torch.float32, device=origins.device)
+        _need(color, torch.float32, "color", (R, 3))
+        if transmittance is not None:
+            _need(transmittance, torch.float32, "transmittance", (R,))
+        if weights is not None:
+            _need(weights, torch.float32, "weights", (P,))
+        st = _stream(stream)
+        lib = L.lib()
+        x = self.x[:P]
+        L.check(lib.sxe_vr_samples(_ptr(origins), _ptr(dirs), _ptr(t_near), _ptr(t_far), R, S, _ptr(x),
+                                   _ptr(self.delta), st), "sxe_vr_samples")
+        self.enc.encode_fwd(x, tables, self.enc_out[:P], stream=stream)
+        self.density.mlp_fwd(W_density, self.enc_out[:P], out=self.dens_out[:P], stream=stream)
+        L.check(lib.sxe_vr_field(_ptr(self.dens_out), _ptr(dirs), R, S, _VR_DTYPES[self.dtype], _ptr(self.sigma),
+                                 _ptr(self.color_in), st), "sxe_vr_field")
+        self.color.mlp_fwd(W_color, self.color_in[:P], out=self.logits[:P], stream=stream)
+        L.check(lib.sxe_vr_composite(_ptr(self.sigma), _ptr(self.logits), _ptr(self.delta), R, S, _ptr(color),
+                                     _ptr(transmittance), _ptr(weights), st), "sxe_vr_composite")
+        return color
+
+    @property
+    def n_launches(self) -> int:
+        return 6
+
+
+def vr_samples(origins, dirs, t_near, t_far, n_samples: int, stream=None):
+    """``sxe_vr_samples`` alone: (x [R*S, 3], delta [R])."""
+    R = origins.shape[0]
+    x = torch.empty((R * n_samples, 3), dtype=torch.float32, device=origins.device)
+    delta = torch.empty((R,), dtype=torch.float32, device=origins.device)
+    L.check(L.lib().sxe_vr_samples(_ptr(origins), _ptr(dirs), _ptr(t_near), _ptr(t_far), R, n_samples, _ptr(x),
+                                   _ptr(delta), _stream(stream)), "sxe_vr_samples")
+    return x, delta
+
+
+def vr_field(density_out, dirs, n_samples: int, dtype: str = "f16", stream=None):
+    """``sxe_vr_field`` alone: (sigma [P], color_in [P, 32])."""
+    P = density_out.shape[0]
+    _need(density_out, torch.float32, "density_out", (P, 16))
+    sigma = torch.empty((P,), dtype=torch.float32, device=density_out.device)
+    cin = torch.empty((P, 32), dtype=torch_dtype(dtype), device=density_out.device)
+    L.check(L.lib().sxe_vr_field(_ptr(density_out), _ptr(dirs), dirs.shape[0], n_samples, _VR_DTYPES[dtype],
+                                 _ptr(sigma), _ptr(cin), _stream(stream)), "sxe_vr_field")
+    return sigma, cin
+
+
+def vr_composite(sigma, logits, delta, n_samples: int, with_weights: bool = False, stream=None):
+    """``sxe_vr_composite`` alone: (color [R, 3], transmittance [R], weights [P] or None)."""
+    R = delta.shape[0]
+    color = torch.empty((R, 3), dtype=torch.float32, device=sigma.device)
+    trans = torch.empty((R,), dtype=torch.float32, device=sigma.device)
+    w = torch.empty((R * n_samples,), dtype=torch.float32, device=sigma.device) if with_weights else None
+    L.check(L.lib().sxe_vr_composite(_ptr(sigma), _ptr(logits), _ptr(delta), R, n_samples, _ptr(color), _ptr(trans),
+                                     _ptr(w), _stream(stream)), "sxe_vr_composite")
+    return color, trans, w

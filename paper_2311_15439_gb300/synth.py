@@ -16,6 +16,9 @@ Workload recipes (shapes and distributions of the paper's tasks, Sec. 6):
   bf16 (bf16 is returned as the binary32 values it represents plus its raw
   uint16 bits).
 * ``normal_grads``     -- upstream gradients N(0, 1).
+* ``camera_rays``      -- rays from a sphere of radius 1.2 around the unit cube's centre
+  towards random targets inside the cube, with the entry and exit distances of the
+  cube [0,1]^3 (the volumetric workload of Sec. 6.2).
 * ``ProceduralImage``  -- an RGB image defined analytically as a seeded sum of
   sinusoids plus bilinear value noise on a coarse lattice; it stands in for the
   gigapixel photograph of Sec. 6.1, which is not available here.
@@ -145,6 +148,26 @@ def sdf_points(P: int, seed: int, n_shapes: int = 32, band: float = 0.01) -> np.
     pts.append(np.clip(sur, 0.0, np.nextafter(1.0, 0.0)))
     out = np.concatenate(pts).astype(np.float32)
     return out[g.permutation(P)]
+
+
+def camera_rays(R: int, seed: int):
+    """(origins [R,3], unit directions [R,3], t_near [R], t_far [R]) float32: origins on the
+    sphere of radius 1.2 about (0.5, 0.5, 0.5), each aimed at a uniform point of [0.25, 0.75]^3;
+    [t_near, t_far] is the ray's segment inside [0,1]^3 (slab test in FP64)."""
+    g = rng(seed)
+    u = g.standard_normal((R, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    o = 0.5 + 1.2 * u
+    target = g.uniform(0.25, 0.75, size=(R, 3))
+    d = target - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    with np.errstate(divide="ignore"):
+        inv = 1.0 / d
+    t0 = (0.0 - o) * inv
+    t1 = (1.0 - o) * inv
+    tn = np.maximum(np.minimum(t0, t1).max(axis=1), 0.0)
+    tf = np.maximum(t0, t1).min(axis=1)
+    return (o.astype(np.float32), d.astype(np.float32), tn.astype(np.float32), tf.astype(np.float32))
 
 
 class ProceduralImage:

@@ -52,7 +52,7 @@ def _create(L, **kw):
     (dict(d=7), -2), (dict(d=0), -1), (dict(n_levels=0), -1), (dict(n_levels=33), -1),
     (dict(n_features=3), -1), (dict(log2_T=3), -1), (dict(log2_T=27), -1), (dict(base_res=0.5), -1),
     (dict(growth=0.9), -1), (dict(kind=5), -1), (dict(res_mode=2), -1), (dict(table_dtype=9), -1),
-    (dict(kind=1, res_mode=1), -1), (dict(base_res=float("nan")), -1),
+    (dict(kind=1, res_mode=1), -1), (dict(base_res=float("nan")), -1), (dict(index_mode=2), -1),
 ])
 def test_encoder_create_rejects_bad_descriptions(L, bad, status):
     st, h = _create(L, **bad)
@@ -109,6 +109,16 @@ def test_level_constants_match_oracle(L, kind, cfg):
         else:
             want = lattice.grid_level_scales_fp32(nl, base, growth)
         assert np.array_equal(s.view(np.uint32), want.view(np.uint32))
+        for index_mode in (L.SXE_INDEX_HASH, L.SXE_INDEX_DENSE_COARSE):
+            for log2_T in (12, 19, 22):
+                st, h = _create(L, d=d, n_levels=nl, base_res=base, growth=growth, log2_T=log2_T,
+                                kind=L.SXE_SIMPLEX if kind == "simplex" else L.SXE_GRID, res_mode=res_mode,
+                                index_mode=index_mode)
+                assert st == 0
+                w = np.zeros(nl, np.int32)
+                assert L.lib().sxe_encoder_level_index(h, w.ctypes.data) == 0
+                L.lib().sxe_encoder_destroy(h)
+                assert w.tolist() == lattice.level_box_widths(kind, d, want, log2_T, index_mode)
 
 
 def test_product_path_refuses_to_run_without_library(tmp_path):
@@ -121,3 +131,15 @@ def test_product_path_refuses_to_run_without_library(tmp_path):
             _lib.lib(str(tmp_path / "missing.so"))
     finally:
         _lib._lib = saved
+
+
+def test_render_entries_validate_before_launch(L):
+    """Argument errors of the rendering entries are caught on the host (no GPU needed)."""
+    lib = L.lib()
+    assert lib.sxe_vr_samples(16, 16, 16, 16, 4, 0, 16, 16, None) == L.SXE_EINVAL          # S = 0
+    assert lib.sxe_vr_samples(16, 16, 16, 16, -1, 4, 16, 16, None) == L.SXE_EINVAL         # R < 0
+    assert lib.sxe_vr_field(16, 16, 4, 8, L.SXE_F32, 16, 16, None) == L.SXE_EINVAL        # f32 colour input
+    assert lib.sxe_vr_field(8, 16, 4, 8, L.SXE_F16, 16, 16, None) == L.SXE_EINVAL         # misaligned rows
+    assert lib.sxe_vr_composite(None, 16, 16, 4, 8, 16, None, None, None) == L.SXE_EINVAL
+    assert lib.sxe_vr_composite(16, 16, 16, 0, 8, 16, None, None, None) == L.SXE_OK       # no rays: nothing
+    assert lib.sxe_encode_bwd_input(None, 16, 4, 16, 16, 16, None) == L.SXE_EINVAL         # NULL encoder

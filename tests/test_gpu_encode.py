@@ -229,3 +229,116 @@ def test_full_size_sdf_workload(cuda_lib):
                                       levels=levels, with_denominator=True)
     for l in levels:
         assert rel_err(grad[l].cpu().numpy(), gref[l], gden[l]) <= 1e-5
+
+
+DX_CASES = [c for c in CASES if c[8] <= 1 << 14]
+
+
+@pytest.mark.parametrize("kind", ["simplex", "grid"])
+@pytest.mark.parametrize("case", DX_CASES, ids=_ids)
+def test_input_gradient_matches_oracle(cuda_lib, case, kind):
+    """dL/dx through the C ABI against the oracle's chain rule, every point and axis, within
+    1e-5 of the sum of the magnitudes of the terms (binary32 products and sums)."""
+    enc, vals, t, x = _setup(cuda_lib, case, kind, seed=20)
+    d, L, F = case[:3]
+    if kind == "grid" and d > 4:
+        pytest.skip("2^5 corners: covered at smaller sizes")
+    base, growth = case[4], case[5]
+    dout = synth.normal_grads(len(x), L * F, 21)
+    dx = enc.encode_bwd_input(torch.from_numpy(x).cuda(), t, torch.from_numpy(dout).cuda()).cpu().numpy()
+    f = O.simplex_encode_dx if kind == "simplex" else O.grid_encode_dx
+    ref, den = f(x, vals, dout, base_res=base, growth=growth, with_denominator=True)
+    assert np.all(np.abs(dx - ref) <= 1e-5 * den + 1e-30)
+
+
+def test_input_gradient_accumulates_and_handles_empty(cuda_lib):
+    from paper_2311_15439_gb300.api import Encoder
+    enc = Encoder(3, 6, 2, 12, 8.0, 2.0, table_dtype="f32")
+    vals, _ = synth.uniform_tables(6, 1 << 12, 2, 30)
+    t = torch.from_numpy(vals).cuda()
+    x = torch.from_numpy(synth.uniform_points(1000, 3, 31)).cuda()
+    dout = torch.from_numpy(synth.normal_grads(1000, 12, 32)).cuda()
+    once = enc.encode_bwd_input(x, t, dout)
+    twice = enc.encode_bwd_input(x, t, dout, dx=once.clone())
+    torch.testing.assert_close(twice, 2 * once, rtol=1e-6, atol=0)
+    empty = enc.encode_bwd_input(x[:0], t, dout[:0])
+    assert empty.shape == (0, 3)
+
+
+def test_input_gradient_full_size_sdf(cuda_lib):
+    """SDF-style configuration at full size (d = 3, L = 16, T = 2^19 bf16, 2^20 points, one
+    launch as the training path runs it): a 4096-point sample against the oracle."""
+    from paper_2311_15439_gb300.api import Encoder
+    enc = Encoder(3, 16, 2, 19, 16.0, 1.38, table_dtype="bf16")
+    vals, bits = synth.uniform_tables(16, 1 << 19, 2, 80, dtype="bf16", scale=1e-2)
+    t = torch.from_numpy(bits.astype(np.int16)).cuda().view(torch.bfloat16)
+    x = synth.sdf_points(1 << 20, 81)
+    dout = synth.normal_grads(len(x), 32, 82)
+    dx = enc.encode_bwd_input(torch.from_numpy(x).cuda(), t, torch.from_numpy(dout).cuda()).cpu().numpy()
+    idx = synth.rng(83).choice(len(x), 4096, replace=False)
+    ref, den = O.simplex_encode_dx(x[idx], vals, dout[idx], base_res=16.0, growth=1.38, with_denominator=True)
+    assert np.all(np.abs(dx[idx] - ref) <= 1e-5 * den + 1e-30)
+
+
+DENSE_CASES = [
+    (2, 8, 2, 16, 16.0, 2.0, "f16", "f16", 5000),      # levels 0-3 direct (130^2 <= 2^16 < 258^2)
+    (3, 6, 2, 16, 8.0, 1.5, "f32", "f32", 3000),
+    (4, 4, 2, 18, 4.0, 1.5, "bf16", "bf16", 2000),
+    (5, 3, 1, 20, 3.0, 1.5, "f32", "f32", 1500),
+]
+
+
+@pytest.mark.parametrize("kind", ["simplex", "grid"])
+@pytest.mark.parametrize("case", DENSE_CASES, ids=_ids)
+def test_dense_coarse_levels_match_oracle(cuda_lib, case, kind):
+    """Direct indexing of the levels that fit: box widths equal the oracle's, slots bit for
+    bit, forward, table gradient and input gradient within the usual tolerances."""
+    from paper_2311_15439_gb300.api import Encoder
+    from oracle.lattice import INDEX_DENSE_COARSE, level_box_widths
+    d, L, F, log2_T, base, growth, tdt, odt, P = case
+    enc = Encoder(d, L, F, log2_T, base, growth, kind=kind, table_dtype=tdt, out_dtype=odt, index_mode="dense_coarse")
+    vals, store = synth.uniform_tables(L, 1 << log2_T, F, 90, dtype=tdt, scale=1e-2)
+    t = torch.from_numpy(store.astype(np.int16) if tdt == "bf16" else store).cuda()
+    if tdt == "bf16":
+        t = t.view(torch.bfloat16)
+    x = _points(d, P, 91)
+    xd = torch.from_numpy(x).cuda()
+    if kind == "simplex":
+        scales = lattice.simplex_level_scales_fp32(d, L, base, growth)
+    else:
+        scales = lattice.grid_level_scales_fp32(L, base, growth)
+    widths = level_box_widths(kind, d, scales, log2_T, INDEX_DENSE_COARSE)
+    assert list(enc.level_index()) == widths and any(widths)
+    slots = enc.encode_vertices(xd)[0].cpu().numpy()
+    for l in range(L):
+        if kind == "simplex":
+            s_ref = O.simplex_level_vertices(x, scales[l], log2_T, widths[l])[0]
+        else:
+            s_ref = O.grid_level_vertices(x, scales[l], log2_T, widths[l])[0]
+        assert np.array_equal(slots[:, l, :].astype(np.int64), s_ref), "level %d" % l
+    kw = dict(base_res=base, growth=growth, index_mode=INDEX_DENSE_COARSE)
+    out = enc.encode_fwd(xd, t).float().cpu().numpy()
+    if kind == "simplex":
+        ref, den = O.simplex_encode(x, vals, with_denominator=True, **kw)
+    else:
+        ref = O.grid_encode(x, vals, **kw)
+        den = O.grid_encode(x, np.abs(vals), **kw)
+    assert worst_ratio(out, ref, den, ENC_TOL[odt], ENC_ATOL[odt]) <= 1.0
+    dout = synth.normal_grads(len(x), L * F, 92)
+    dd = torch.from_numpy(dout).cuda()
+    grad = torch.zeros((L, 1 << log2_T, F), dtype=torch.float32, device="cuda")
+    enc.encode_bwd(xd, dd, grad)
+    g = grad.cpu().numpy()
+    bkw = dict(n_levels=L, log2_T=log2_T, n_features=F, **kw)
+    if kind == "simplex":
+        gref, gden = O.simplex_encode_bwd(x, dout, with_denominator=True, **bkw)
+    else:
+        gref = O.grid_encode_bwd(x, dout, **bkw)
+        gden = O.grid_encode_bwd(x, np.abs(dout), **bkw)
+    for l in range(L):
+        assert rel_err(g[l], gref[l], gden[l]) <= 1e-5, "level %d" % l
+    if not (kind == "grid" and d == 5):
+        dx = enc.encode_bwd_input(xd, t, dd).cpu().numpy()
+        f = O.simplex_encode_dx if kind == "simplex" else O.grid_encode_dx
+        xref, xden = f(x, vals, dout, with_denominator=True, **kw)
+        assert np.all(np.abs(dx - xref) <= 1e-5 * xden + 1e-30)

@@ -1,0 +1,131 @@
+"""GPU parity of the volumetric rendering kernels (Sec. 6.2, Eq. 5) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import render as OR
+from paper_2311_15439_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def _rays(R, seed):
+    return [torch.from_numpy(a).cuda() for a in synth.camera_rays(R, seed)]
+
+
+@pytest.mark.parametrize("S", [1, 3, 32, 33, 257])
+def test_samples_bit_exact(cuda_lib, S):
+    from paper_2311_15439_gb300.render import vr_samples
+    o, d, tn, tf = synth.camera_rays(500, 1)
+    x, delta = vr_samples(*[torch.from_numpy(a).cuda() for a in (o, d, tn, tf)], S)
+    xr, dr = OR.ray_samples_fp32(o, d, tn, tf, S)
+    assert np.array_equal(x.cpu().numpy().view(np.uint32), xr.view(np.uint32))
+    assert np.array_equal(delta.cpu().numpy().view(np.uint32), dr.view(np.uint32))
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_field_head_matches_oracle(cuda_lib, dtype):
+    from paper_2311_15439_gb300.render import vr_field
+    R, S = 300, 7
+    g = synth.rng(2)
+    dens = (4.0 * g.standard_normal((R * S, 16))).astype(np.float32)
+    dens[::11, 0] = g.uniform(15.0, 40.0, size=dens[::11, 0].shape)          # clamped logits
+    _, d, _, _ = synth.camera_rays(R, 3)
+    sigma, cin = vr_field(torch.from_numpy(dens).cuda(), torch.from_numpy(d).cuda(), S, dtype)
+    sigma = sigma.cpu().numpy()
+    want = OR.density_from_logit(dens[:, 0])
+    assert np.all(np.abs(sigma - want) <= 8 * U32 * want)
+    c = cin.float().cpu().numpy()
+    if dtype == "f16":
+        lowp = dens.astype(np.float16).astype(np.float32)
+        ulp = 2.0 ** -11
+    else:
+        lowp = synth.bf16_bits_to_fp32(synth.fp32_to_bf16_bits(dens))
+        ulp = 2.0 ** -8
+    assert np.array_equal(c[:, :16], lowp)                                   # rounded once, to nearest even
+    sh = np.repeat(OR.sh_basis(d.astype(np.float64)), S, axis=0)
+    assert np.all(np.abs(c[:, 16:] - sh) <= ulp * np.abs(sh) + 1e-6)          # binary32 polynomial, one rounding
+
+
+@pytest.mark.parametrize("S", [1, 5, 32, 33, 100, 1024])
+def test_composite_matches_oracle(cuda_lib, S):
+    from paper_2311_15439_gb300.render import vr_composite
+    R = 257
+    g = synth.rng(10 + S)
+    scale = g.choice([0.0, 0.1, 3.0, 50.0, 1e4], size=(R, 1))
+    sigma = (g.exponential(1.0, size=(R, S)) * scale).astype(np.float32)
+    logits = (3.0 * g.standard_normal((R * S, 3))).astype(np.float32)
+    delta = g.uniform(1e-3, 2.0 / S, size=R).astype(np.float32)
+    color, trans, w = vr_composite(torch.from_numpy(sigma.reshape(-1)).cuda(), torch.from_numpy(logits).cuda(),
+                                   torch.from_numpy(delta).cuda(), S, with_weights=True)
+    rgb = OR.sigmoid(logits).reshape(R, S, 3)
+    C, T, W = OR.composite(sigma, rgb, delta)
+    # binary32 error: the scan of sigma*delta (at most 5 + S/32 additions deep), exp/expm1, products
+    tau = np.concatenate([np.zeros((R, 1)), np.cumsum(sigma.astype(np.float64) * delta[:, None], axis=1)[:, :-1]], 1)
+    depth = 5 + (S + 31) // 32
+    werr = W * ((depth + 2) * tau + 12) * U32 + 1e-30
+    assert np.all(np.abs(w.cpu().numpy().reshape(R, S) - W) <= werr)
+    cerr = (werr[:, :, None] * rgb).sum(axis=1) + W.sum(axis=1, keepdims=True) * (depth + 8) * U32 + 1e-7
+    assert np.all(np.abs(color.cpu().numpy() - C) <= cerr)
+    tot = tau[:, -1] + sigma[:, -1].astype(np.float64) * delta
+    assert np.all(np.abs(trans.cpu().numpy() - T) <= T * ((depth + 2) * tot + 4) * U32 + 1e-30)
+
+
+def _renderer(kind, R, S, L=8, log2_T=14, seed=0):
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.render import Renderer
+    enc = Encoder(3, L, 2, log2_T, 16.0, 1.5, kind=kind, table_dtype="f16")
+    rr = Renderer(enc, R, S, dtype="f16")
+    vals, store = synth.uniform_tables(L, 1 << log2_T, 2, seed + 1, dtype="f16", scale=1.0)
+    Wd, Wc = rr.init_weights(seed + 2)
+    return enc, rr, vals, torch.from_numpy(store).cuda(), Wd, Wc
+
+
+def _oracle_render(rays, n, S, vals, Wd, Wc, rr, kind):
+    o, d, tn, tf = [a[:n] for a in rays]
+    Wd_ = [w.astype(np.float64) for w in rr.density.split(Wd.float().cpu().numpy())]
+    Wc_ = [w.astype(np.float64) for w in rr.color.split(Wc.float().cpu().numpy())]
+    return OR.render(o, d, tn, tf, S, vals, Wd_, Wc_, kind=kind, base_res=16.0, growth=1.5)
+
+
+@pytest.mark.parametrize("kind", ["simplex", "grid"])
+def test_render_end_to_end(cuda_lib, kind):
+    """Six launches against the FP64 pipeline (fp16 encoding and networks on the GPU): colours
+    within 0.03, and the weights plus the remaining transmittance sum to 1."""
+    R, S = 96, 24
+    enc, rr, vals, t, Wd, Wc = _renderer(kind, R, S)
+    rays = synth.camera_rays(R, 20)
+    trans = torch.empty((R,), device="cuda")
+    w = torch.empty((R * S,), device="cuda")
+    C = rr.render(*[torch.from_numpy(a).cuda() for a in rays], t, Wd, Wc, transmittance=trans, weights=w)
+    Cref, Tref, _ = _oracle_render(rays, R, S, vals, Wd, Wc, rr, kind)
+    err = np.abs(C.cpu().numpy() - Cref)
+    assert err.max() <= 0.03 and np.median(err) <= 3e-3
+    np.testing.assert_allclose(w.view(R, S).sum(1).cpu().numpy() + trans.cpu().numpy(), 1.0, atol=2e-5)
+
+
+def test_render_full_size(cuda_lib):
+    """2^16 rays x 1024 samples (2^26 encoded points, T = 2^19 fp16, L = 16), one render as the
+    benchmark times it: 8 sampled rays against the oracle, invariants on every ray."""
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.render import Renderer
+    R, S, L = 1 << 16, 1024, 16
+    enc = Encoder(3, L, 2, 19, 16.0, 1.38, table_dtype="f16")
+    rr = Renderer(enc, R, S, dtype="f16")
+    vals, store = synth.uniform_tables(L, 1 << 19, 2, 30, dtype="f16", scale=1.0)
+    t = torch.from_numpy(store).cuda()
+    Wd, Wc = rr.init_weights(31)
+    rays = synth.camera_rays(R, 32)
+    trans = torch.empty((R,), device="cuda")
+    C = rr.render(*[torch.from_numpy(a).cuda() for a in rays], t, Wd, Wc, transmittance=trans).cpu().numpy()
+    T = trans.cpu().numpy()
+    assert np.isfinite(C).all() and C.min() >= 0 and np.all(C <= 1 - T[:, None] + 1e-5)
+    assert T.min() >= 0 and T.max() <= 1
+    idx = synth.rng(33).choice(R, 8, replace=False)
+    sub = [a[idx] for a in rays]
+    Wd_ = [w.astype(np.float64) for w in rr.density.split(Wd.float().cpu().numpy())]
+    Wc_ = [w.astype(np.float64) for w in rr.color.split(Wc.float().cpu().numpy())]
+    Cref, _, _ = OR.render(*sub, S, vals, Wd_, Wc_, kind="simplex", base_res=16.0, growth=1.38)
+    assert np.abs(C[idx] - Cref).max() <= 0.03

@@ -158,6 +158,45 @@ def test_autograd_encoding_matches_oracle_and_fd():
         assert abs(fd - g[l, s, f]) <= 1e-4 * max(1.0, den[l][s, f])
 
 
+@pytest.mark.parametrize("kind", ["simplex", "grid"])
+def test_autograd_input_gradient(kind):
+    """x.grad through the autograd Function equals the oracle's input gradient and the
+    central difference of the CUDA forward (points whose cells stay the same at x +- h)."""
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.autograd import encode
+    enc = Encoder(3, 6, 2, 12, 8.0, 1.5, kind=kind, table_dtype="f32")
+    vals = synth.uniform_tables(6, 1 << 12, 2, 40, scale=1.0)[0]
+    H = torch.from_numpy(vals).cuda()
+    x = np.clip(synth.uniform_points(1500, 3, 41), 0.01, 0.99).astype(np.float32)
+    D = synth.normal_grads(1500, 12, 42)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    Dt = torch.from_numpy(D).cuda()
+    (encode(xt, H, enc) * Dt).sum().backward()
+    g = xt.grad.cpu().numpy()
+    f = OE.simplex_encode_dx if kind == "simplex" else OE.grid_encode_dx
+    ref, den = f(x, vals, D, base_res=8.0, growth=1.5, with_denominator=True)
+    assert np.all(np.abs(g - ref) <= 1e-5 * den + 1e-30)
+    h = 2.0 ** -12
+    slots0 = enc.encode_vertices(torch.from_numpy(x).cuda())[0].sort(dim=-1).values
+    n_checked = 0
+    for j in range(3):
+        xp, xm = x.copy(), x.copy()
+        xp[:, j] += h
+        xm[:, j] -= h
+        same = torch.ones(len(x), dtype=torch.bool, device="cuda")
+        outs = []
+        for xx in (xp, xm):
+            xd = torch.from_numpy(xx).cuda()
+            s1 = enc.encode_vertices(xd)[0].sort(dim=-1).values
+            same &= (s1 == slots0).flatten(1).all(dim=1)
+            outs.append((enc.encode_fwd(xd, H).double() * Dt.double()).sum(dim=1))
+        fd = ((outs[0] - outs[1]) / (2 * h)).cpu().numpy()
+        ok = same.cpu().numpy()
+        assert np.all(np.abs(fd - g[:, j])[ok] <= 2e-3 * den[ok, j] + 1e-12)
+        n_checked += ok.sum()
+    assert n_checked > 1000
+
+
 def test_autograd_mlp_matches_oracle():
     from paper_2311_15439_gb300.api import Mlp
     from paper_2311_15439_gb300.autograd import mlp_apply

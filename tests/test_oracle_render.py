@@ -37,6 +37,14 @@ def test_composite_piecewise_constant_media():
     np.testing.assert_allclose(C, (1.0 - T)[:, None] * c[None, :], rtol=1e-12, atol=1e-15)
 
 
+def test_composite_keeps_tiny_transmittance():
+    """A nearly opaque segment: T = exp(-sigma delta) to full relative precision, not 1 - (1 - e^-x)."""
+    sigma = np.array([[80.0], [700.0], [1e-20]])
+    C, T, w = render.composite(sigma, np.ones((3, 1, 3)), np.ones(3))
+    np.testing.assert_allclose(T, np.exp(-sigma[:, 0]), rtol=1e-15)
+    np.testing.assert_allclose(w[:, 0], -np.expm1(-sigma[:, 0]), rtol=1e-15)
+
+
 def test_composite_opaque_and_empty():
     S = 16
     rgb = synth.rng(3).random((1, S, 3))
