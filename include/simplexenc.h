@@ -134,10 +134,18 @@ sxe_status sxe_encode_fwd(const sxe_encoder* enc, const float* x, int64_t n_poin
  *                for entry e = l*T + slot); every entry that receives a term gets
  *                its bit set.  NULL disables marking.
  * Accumulation order is unspecified (atomic adds), so results agree with the
- * exact sum to within floating-point reassociation. */
+ * exact sum to within floating-point reassociation.  Levels whose lattice box is
+ * small are summed per thread block in shared memory first and added once per
+ * block (see sxe_encode_bwd_kernel_count); one or two kernels on `stream`. */
 sxe_status sxe_encode_bwd(const sxe_encoder* enc, const float* x, int64_t n_points,
                           const float* dout, float* grad, int64_t grad_stride,
                           uint32_t* touched, void* stream);
+
+/* Number of kernels sxe_encode_bwd launches for n_points (1 or 2; 0 for none): levels
+ * whose lattice box is small are first summed per thread block in shared memory and
+ * added to the table once per block (many contributions per vertex would otherwise
+ * serialise on the same addresses); the other levels take the direct path. */
+int32_t sxe_encode_bwd_kernel_count(const sxe_encoder* enc, int64_t n_points);
 
 /* Gradient with respect to the points (the chain rule through Sec. 4.3's weights, Eq. 2's
  * skew and the level scale; the paper does not state it):

@@ -128,6 +128,10 @@ class Encoder:
                 "sxe_encode_bwd")
         return grad
 
+    def bwd_kernel_count(self, n_points: int) -> int:
+        """Kernels one ``encode_bwd`` call launches for this many points (1 or 2)."""
+        return int(L.lib().sxe_encode_bwd_kernel_count(self._h, n_points))
+
     def encode_bwd_input(self, x: torch.Tensor, tables: torch.Tensor, dout: torch.Tensor,
                          dx: torch.Tensor | None = None, stream=None):
         """dx += d(out)/dx^T dout (``sxe_encode_bwd_input``); returns dx [P, d] float32."""

@@ -85,11 +85,11 @@ sxe_status sxe_encoder_create(const sxe_encoding_desc* d, sxe_encoder** out) {
     // Directly indexed level: the vertices of [0,1]^n take B = floor(top) + 2 values per axis,
     // top = s_l sqrt(n+1) (simplex, q_i <= s_l (1 + n F_n)) or N_l (grid), with a 2^-20
     // margin for binary32 rounding; used when B^n fits the table.
-    if (d->index_mode == SXE_INDEX_DENSE_COARSE) {
-      const double top = (double)e->prm.scale[l] * (d->kind == SXE_SIMPLEX ? std::sqrt(n + 1.0) : 1.0);
-      const double B = std::floor(top * (1.0 + std::ldexp(1.0, -20))) + 2.0;
-      if (std::pow(B, n) <= std::ldexp(1.0, d->log2_T)) e->prm.width[l] = (uint32_t)B;
-    }
+    const double top = (double)e->prm.scale[l] * (d->kind == SXE_SIMPLEX ? std::sqrt(n + 1.0) : 1.0);
+    const double B = std::floor(top * (1.0 + std::ldexp(1.0, -20))) + 2.0;
+    e->box_width[l] = B < 4.0e9 ? (uint32_t)B : 0u;
+    if (d->index_mode == SXE_INDEX_DENSE_COARSE && std::pow(B, n) <= std::ldexp(1.0, d->log2_T))
+      e->prm.width[l] = (uint32_t)B;
   }
   e->prm.n_levels = d->n_levels;
   e->prm.log2_T = d->log2_T;
@@ -157,6 +157,11 @@ sxe_status sxe_encode_bwd(const sxe_encoder* e, const float* x, int64_t P, const
   if (!aligned(dout, F == 2 ? 8 : 4)) return set_error(SXE_EINVAL, "encode_bwd: dout misaligned");
   if (touched && !aligned(touched, 4)) return set_error(SXE_EINVAL, "encode_bwd: touched misaligned");
   return launch_encode_bwd(e, x, P, dout, grad, grad_stride, touched, (cudaStream_t)stream);
+}
+
+int32_t sxe_encode_bwd_kernel_count(const sxe_encoder* e, int64_t P) {
+  if (!e || P <= 0) return 0;
+  return encode_bwd_launches(e, P);
 }
 
 sxe_status sxe_encode_bwd_input(const sxe_encoder* e, const float* x, int64_t P, const void* tables,

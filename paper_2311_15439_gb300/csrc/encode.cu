@@ -5,6 +5,8 @@
 // threads write consecutive F-feature groups of the [P][L*F] output (coalesced) and
 // read consecutive groups of dout.  Every item issues its V = d+1 (simplex) or 2^d
 // (grid) independent gathers before it consumes any of them.
+#include <algorithm>
+
 #include "sxe_internal.cuh"
 
 namespace sxe {
@@ -109,7 +111,7 @@ template <bool SIMPLEX, int D, int F>
 __global__ void __launch_bounds__(kThreads)
 encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restrict__ dout,
                   float* __restrict__ grad, int64_t stride, uint32_t* __restrict__ touched,
-                  const EncParams prm, int l0, int nl, bool dout_level_major) {
+                  const EncParams prm, int l0, int nl) {
   constexpr int V = Verts<SIMPLEX, D>::V;
   __shared__ float s_scale[SXE_MAX_LEVELS];
   __shared__ uint32_t s_width[SXE_MAX_LEVELS];
@@ -124,7 +126,7 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
   it.l += l0;
   // issue the gradient and point loads first, the lattice arithmetic overlaps them
   float g[F];
-  const float* pd = dout + (dout_level_major ? (int64_t)it.l * P + it.p : it.p * L + it.l) * F;
+  const float* pd = dout + (it.p * L + it.l) * F;
   if constexpr (F == 2) {
     const float2 a = __ldg(reinterpret_cast<const float2*>(pd));
     g[0] = a.x; g[1] = a.y;
@@ -186,6 +188,121 @@ encode_vertices_kernel(const float* __restrict__ x, int64_t P, uint32_t* __restr
 inline unsigned grid_for(int64_t P, int L) { return (unsigned)((P * L + kThreads - 1) / kThreads); }
 
 // ---- dispatch ---------------------------------------------------------------
+// Coarse levels, privately per CTA.  The lattice box of a coarse level has few vertices
+// (B^d, B coordinates per axis) that receive many contributions each, and same-address
+// reductions serialise in L2.  CTA k of level c sums the contributions of its chunk of the
+// points in shared memory, indexed by the vertex's box coordinate sum_i v_i B^i, marks the
+// vertices it touched in a shared bitmap, then adds each touched vertex to its table slot
+// once.  Vertices outside the box (points outside [0,1]^d) take the global path directly.
+constexpr int kMaxCoarse = 4;
+constexpr int kCoarseSmem = 48 * 1024;
+
+struct CoarsePlan {
+  int n;                                    // coarse levels 0..n-1
+  int start[kMaxCoarse + 1];                // CTAs of level c: [start[c], start[c+1])
+  uint32_t box[kMaxCoarse];                 // box width B of level c
+  int smem;                                 // dynamic shared memory bytes
+};
+
+template <bool SIMPLEX, int D, int F>
+__global__ void __launch_bounds__(kThreads)
+encode_bwd_coarse_kernel(const float* __restrict__ x, int64_t P, const float* __restrict__ dout,
+                         float* __restrict__ grad, int64_t stride, uint32_t* __restrict__ touched,
+                         const EncParams prm, const CoarsePlan plan) {
+  constexpr int V = Verts<SIMPLEX, D>::V;
+  extern __shared__ float s_acc[];
+  int c = 0;
+  while (c + 1 < plan.n && (int)blockIdx.x >= plan.start[c + 1]) ++c;
+  const uint32_t B = c == 0 ? plan.box[0] : c == 1 ? plan.box[1] : c == 2 ? plan.box[2] : plan.box[3];
+  uint32_t cells = 1;
+#pragma unroll
+  for (int i = 0; i < D; ++i) cells *= B;
+  uint32_t* s_flag = reinterpret_cast<uint32_t*>(s_acc + cells * F);
+  for (uint32_t i = threadIdx.x; i < cells * F; i += kThreads) s_acc[i] = 0.f;
+  for (uint32_t i = threadIdx.x; i < (cells + 31) / 32; i += kThreads) s_flag[i] = 0u;
+  __syncthreads();
+  const int L = prm.n_levels;
+  const int K = plan.start[c + 1] - plan.start[c];
+  const int k = (int)blockIdx.x - plan.start[c];
+  const int64_t p0 = P * k / K, p1 = P * (k + 1) / K;
+  const uint32_t mask = (1u << prm.log2_T) - 1u;
+  const uint32_t width = prm.width[c];
+  const float s = prm.scale[c];
+  const int64_t lbase = (int64_t)c << prm.log2_T;
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
+    float g[F];
+    const float* pd = dout + (p * L + c) * F;
+#pragma unroll
+    for (int f = 0; f < F; ++f) g[f] = __ldg(pd + f);
+    float xv[D];
+    load_point<D>(x, p, xv);
+    uint32_t box[V];
+    float w[V];
+    int cell[D];
+    bool inside = true;
+    if constexpr (SIMPLEX) {
+      int rank[D];
+      simplex_lattice<D>(xv, s, prm.skew_F, 0xffffffffu, B, box, w, rank, cell);
+#pragma unroll
+      for (int i = 0; i < D; ++i) inside &= cell[i] >= 0 && cell[i] <= (int)B - 2;
+      if (!inside) {
+#pragma unroll
+        for (int kk = 0; kk < V; ++kk) {
+          uint32_t v[D];
+#pragma unroll
+          for (int i = 0; i < D; ++i) v[i] = (uint32_t)cell[i] + (rank[i] < kk ? 1u : 0u);
+          box[kk] = vertex_slot<D>(v, width, mask);
+        }
+      }
+    } else {
+      float fr[D];
+      grid_lattice<D>(xv, s, 0xffffffffu, B, box, w, fr, cell);
+#pragma unroll
+      for (int i = 0; i < D; ++i) inside &= cell[i] >= 0 && cell[i] <= (int)B - 2;
+      if (!inside) {
+#pragma unroll
+        for (int b = 0; b < V; ++b) {
+          uint32_t v[D];
+#pragma unroll
+          for (int i = 0; i < D; ++i) v[i] = (uint32_t)cell[i] + ((b >> (D - 1 - i)) & 1);
+          box[b] = vertex_slot<D>(v, width, mask);
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < V; ++kk) {
+      if (inside) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) atomicAdd(s_acc + box[kk] * F + f, w[kk] * g[f]);
+        atomicOr(s_flag + (box[kk] >> 5), 1u << (box[kk] & 31));
+      } else {
+        float cc[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) cc[f] = w[kk] * g[f];
+        const int64_t e = lbase + box[kk];
+        atomic_add_entry<F>(grad + e * stride, cc);
+        if (touched) atomicOr(touched + (e >> 5), 1u << (uint32_t)(e & 31));
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < cells; b += kThreads) {
+    if (!((s_flag[b >> 5] >> (b & 31)) & 1u)) continue;
+    uint32_t v[D], r = b;
+#pragma unroll
+    for (int i = 0; i < D; ++i) { v[i] = r % B; r /= B; }
+    const int64_t e = lbase + vertex_slot<D>(v, width, mask);
+    float cc[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) cc[f] = s_acc[b * F + f];
+    atomic_add_entry<F>(grad + e * stride, cc);
+    if (touched) {
+      const uint32_t bit = 1u << (uint32_t)(e & 31);
+      if (!(__ldcg(touched + (e >> 5)) & bit)) atomicOr(touched + (e >> 5), bit);
+    }
+  }
+}
+
 // Input gradient: dx[p][i] += sum over levels and features of dout * d out / d x_i.
 // Simplex (Sec. 4.3 weights): inside the point's simplex the output is affine in the
 // fractional parts, and moving f along the axis of rank k shifts weight from vertex k to
@@ -374,32 +491,71 @@ sxe_status fwd_d(const sxe_encoder* e, const float* x, int64_t P, const void* t,
   }
 }
 
+// Coarse levels for the privatised backward: a prefix of levels whose box fits the shared
+// memory budget and receives at least 8 contributions per vertex.  A level gets one CTA per
+// 8192 contributions, fewer if a CTA would then see under 4 contributions per vertex, and
+// at most 2 per SM: the flush then costs at most a quarter of the contributions, and each
+// table entry receives at most K flushed sums instead of thousands of single terms.
+CoarsePlan coarse_plan(const sxe_encoder* e, int64_t P) {
+  CoarsePlan plan{};
+  const int d = e->desc.d, F = e->desc.n_features;
+  const int64_t V = e->desc.kind == SXE_SIMPLEX ? d + 1 : (1 << d);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  plan.start[0] = 0;
+  for (int c = 0; c < kMaxCoarse && c < e->prm.n_levels; ++c) {
+    const uint32_t B = e->box_width[c];
+    if (B == 0) break;
+    int64_t cells = 1;
+    for (int i = 0; i < d; ++i) cells *= B;
+    const int64_t bytes = cells * F * 4 + (cells + 31) / 32 * 4;
+    if (bytes > kCoarseSmem || P * V < 8 * cells) break;
+    const int64_t K = std::max<int64_t>(1, std::min<int64_t>(std::min(P * V / 8192, P * V / (4 * cells)), 2 * sms));
+    plan.box[c] = B;
+    plan.start[c + 1] = plan.start[c] + (int)K;
+    plan.smem = std::max(plan.smem, (int)bytes);
+    plan.n = c + 1;
+  }
+  return plan;
+}
+
 template <bool SIMPLEX, int D, int F>
 sxe_status bwd_f(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                 uint32_t* touched, int l0, int nl, cudaStream_t s, bool lm) {
-  encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, nl), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm, l0, nl, lm);
+                 uint32_t* touched, cudaStream_t s) {
+  const CoarsePlan plan = coarse_plan(e, P);
+  if (plan.n > 0) {
+    encode_bwd_coarse_kernel<SIMPLEX, D, F><<<plan.start[plan.n], kThreads, plan.smem, s>>>(
+        x, P, dout, g, stride, touched, e->prm, plan);
+    sxe_status st = check_launch("encode_bwd_coarse");
+    if (st != SXE_OK) return st;
+  }
+  const int nl = e->prm.n_levels - plan.n;
+  if (nl == 0) return SXE_OK;
+  encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, nl), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm,
+                                                                       plan.n, nl);
   return check_launch("encode_bwd");
 }
 
 template <bool SIMPLEX, int D>
 sxe_status bwd_fd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                  uint32_t* t, int l0, int nl, cudaStream_t s, bool lm) {
+                  uint32_t* t, cudaStream_t s) {
   switch (e->desc.n_features) {
-    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
-    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
-    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
-    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
+    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, s);
+    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, s);
+    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, s);
+    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, s);
   }
 }
 
 template <bool SIMPLEX>
 sxe_status bwd_d(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                 uint32_t* t, int l0, int nl, cudaStream_t s, bool lm) {
+                 uint32_t* t, cudaStream_t s) {
   switch (e->desc.d) {
-    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
-    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
-    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
-    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, l0, nl, s, lm);
+    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, s);
+    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, s);
+    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, s);
+    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, s);
   }
 }
 
@@ -425,10 +581,14 @@ sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, 
 }
 
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout, float* grad,
-                             int64_t stride, uint32_t* touched, cudaStream_t s, int l0, int nl, bool dout_lm) {
-  if (nl < 0) nl = enc->prm.n_levels - l0;
-  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, l0, nl, s, dout_lm)
-                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, l0, nl, s, dout_lm);
+                             int64_t stride, uint32_t* touched, cudaStream_t s) {
+  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, s)
+                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, s);
+}
+
+int encode_bwd_launches(const sxe_encoder* enc, int64_t P) {
+  const CoarsePlan plan = coarse_plan(enc, P);
+  return (plan.n > 0 ? 1 : 0) + (plan.n < enc->prm.n_levels ? 1 : 0);
 }
 
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,

@@ -34,6 +34,7 @@ struct EncParams {
 struct sxe_encoder {
   sxe_encoding_desc desc;
   int32_t level_res[SXE_MAX_LEVELS];
+  uint32_t box_width[SXE_MAX_LEVELS];   // lattice coordinates per axis of [0,1]^d at each level
   sxe::EncParams prm;
 };
 
@@ -47,8 +48,8 @@ sxe_status check_launch(const char* what);
 sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
                              void* out, cudaStream_t s, int64_t table_stride = 0);
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
-                             float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s,
-                             int level_begin = 0, int n_levels = -1, bool dout_level_major = false);
+                             float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s);
+int encode_bwd_launches(const sxe_encoder* enc, int64_t P);
 sxe_status launch_encode_plain(const sxe_encoder* enc, bool backward, const float* x, int64_t P, const float* a,
                                float* b, cudaStream_t s);
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,
@@ -205,7 +206,7 @@ __device__ __forceinline__ void store_lowp(void* base, int64_t e, int ldt, const
 template <int D>
 __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
                                                 uint32_t width, uint32_t (&slot)[D + 1], float (&w)[D + 1],
-                                                int (&rank)[D]) {
+                                                int (&rank)[D], int (&cell)[D]) {
   float p[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) p[i] = __fmul_rn(x[i], s);
@@ -221,7 +222,8 @@ __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, fl
     const float q = __fadd_rn(p[i], t);
     const float fl = floorf(q);
     f[i] = __fsub_rn(q, fl);
-    const uint32_t c = (uint32_t)__float2int_rz(fl);
+    cell[i] = __float2int_rz(fl);
+    const uint32_t c = (uint32_t)cell[i];
     const uint32_t mult = width ? pw : hash_prime(i);
     pw *= width;
     h0[i] = c * mult;
@@ -261,6 +263,14 @@ __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, fl
 
 template <int D>
 __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
+                                                uint32_t width, uint32_t (&slot)[D + 1], float (&w)[D + 1],
+                                                int (&rank)[D]) {
+  int cell[D];
+  simplex_lattice<D>(x, s, skewF, mask, width, slot, w, rank, cell);
+}
+
+template <int D>
+__device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
                                                 uint32_t width, uint32_t (&slot)[D + 1], float (&w)[D + 1]) {
   int rank[D];
   simplex_lattice<D>(x, s, skewF, mask, width, slot, w, rank);
@@ -271,7 +281,8 @@ __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, fl
 // significant bit) has weight prod_i (b_i ? f_i : 1 - f_i), multiplied in axis order.
 template <int D>
 __device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint32_t mask, uint32_t width,
-                                             uint32_t (&slot)[1 << D], float (&w)[1 << D], float (&f)[D]) {
+                                             uint32_t (&slot)[1 << D], float (&w)[1 << D], float (&f)[D],
+                                             int (&cell)[D]) {
   uint32_t h0[D], h1[D];
   uint32_t pw = 1u;
 #pragma unroll
@@ -279,7 +290,8 @@ __device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint3
     const float p = __fmul_rn(x[i], N);
     const float fl = floorf(p);
     f[i] = __fsub_rn(p, fl);
-    const uint32_t c = (uint32_t)__float2int_rz(fl);
+    cell[i] = __float2int_rz(fl);
+    const uint32_t c = (uint32_t)cell[i];
     const uint32_t mult = width ? pw : hash_prime(i);
     pw *= width;
     h0[i] = c * mult;
@@ -303,9 +315,28 @@ __device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint3
 
 template <int D>
 __device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint32_t mask, uint32_t width,
+                                             uint32_t (&slot)[1 << D], float (&w)[1 << D], float (&f)[D]) {
+  int cell[D];
+  grid_lattice<D>(x, N, mask, width, slot, w, f, cell);
+}
+
+template <int D>
+__device__ __forceinline__ void grid_lattice(const float (&x)[D], float N, uint32_t mask, uint32_t width,
                                              uint32_t (&slot)[1 << D], float (&w)[1 << D]) {
   float f[D];
   grid_lattice<D>(x, N, mask, width, slot, w, f);
+}
+
+// Table slot of lattice vertex v under a level's rule (hash, or direct index for width > 0).
+template <int D>
+__device__ __forceinline__ uint32_t vertex_slot(const uint32_t (&v)[D], uint32_t width, uint32_t mask) {
+  uint32_t h = 0, pw = 1u;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    h = width ? h + v[i] * pw : h ^ (v[i] * hash_prime(i));
+    pw *= width;
+  }
+  return h & mask;
 }
 
 }  // namespace sxe

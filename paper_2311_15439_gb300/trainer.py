@@ -66,7 +66,9 @@ class Trainer:
 
     @property
     def n_launches_per_step(self) -> int:
-        return 6   # encode_fwd, mlp train, its partial reduction, encode_bwd, table Adam, network Adam
+        # encode_fwd, network training + its partial reduction, encode_bwd (coarse levels in shared
+        # memory, then the rest), table Adam, network Adam
+        return 5 + self.enc.bwd_kernel_count(self.P)
 
     def step(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
         """One optimisation step on batch (x [P, d] float32, target [P, n_out] float32); asynchronous."""

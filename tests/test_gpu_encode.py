@@ -342,3 +342,48 @@ def test_dense_coarse_levels_match_oracle(cuda_lib, case, kind):
         f = O.simplex_encode_dx if kind == "simplex" else O.grid_encode_dx
         xref, xden = f(x, vals, dout, with_denominator=True, **kw)
         assert np.all(np.abs(dx - xref) <= 1e-5 * xden + 1e-30)
+
+
+@pytest.mark.parametrize("kind,d,index_mode", [("simplex", 2, "hash"), ("simplex", 3, "hash"), ("grid", 2, "hash"),
+                                               ("simplex", 2, "dense_coarse"), ("grid", 3, "dense_coarse")])
+def test_coarse_levels_summed_per_block(cuda_lib, kind, d, index_mode):
+    """Backward with the coarse levels summed per thread block in shared memory (two kernels):
+    gradients in interleaved records equal the oracle's, points outside the box (x in
+    [-0.3, 1.3]) included, and the bitmap marks exactly the entries that received a term."""
+    from paper_2311_15439_gb300.api import Encoder
+    from oracle.lattice import INDEX_DENSE_COARSE, INDEX_HASH
+    L, F, log2_T, base, growth = 6, 2, 14, 8.0, 1.6
+    T = 1 << log2_T
+    enc = Encoder(d, L, F, log2_T, base, growth, kind=kind, table_dtype="f32", index_mode=index_mode)
+    P = 40000
+    assert enc.bwd_kernel_count(P) == 2
+    g = synth.rng(95 + d)
+    x = g.uniform(-0.3, 1.3, size=(P, d)).astype(np.float32)
+    x[: P // 2] = synth.uniform_points(P // 2, d, 96)
+    xd = torch.from_numpy(x).cuda()
+    dout = synth.normal_grads(P, L * F, 97)
+    state = torch.zeros((L * T, 4 * F), device="cuda")
+    bm = torch.zeros(((L * T + 31) // 32,), dtype=torch.int32, device="cuda")
+    enc.encode_bwd(xd, torch.from_numpy(dout).cuda(), state, grad_stride=4 * F, grad_offset=3 * F, touched=bm)
+    grad = state[:, 3 * F:].reshape(L, T, F).cpu().numpy()
+    assert torch.all(state[:, :3 * F] == 0)
+    mode = INDEX_DENSE_COARSE if index_mode == "dense_coarse" else INDEX_HASH
+    kw = dict(n_levels=L, log2_T=log2_T, n_features=F, base_res=base, growth=growth, index_mode=mode)
+    if kind == "simplex":
+        ref, den = O.simplex_encode_bwd(x, dout, with_denominator=True, **kw)
+        scales = lattice.simplex_level_scales_fp32(d, L, base, growth)
+    else:
+        ref = O.grid_encode_bwd(x, dout, **kw)
+        den = O.grid_encode_bwd(x, np.abs(dout), **kw)
+        scales = lattice.grid_level_scales_fp32(L, base, growth)
+    widths = lattice.level_box_widths(kind, d, scales, log2_T, mode)
+    want = np.zeros(L * T, dtype=bool)
+    for l in range(L):
+        assert rel_err(grad[l], ref[l], den[l]) <= 1e-5, "level %d" % l
+        if kind == "simplex":
+            sl = O.simplex_level_vertices(x, scales[l], log2_T, widths[l])[0]
+        else:
+            sl = O.grid_level_vertices(x, scales[l], log2_T, widths[l])[0]
+        want[l * T + np.unique(sl)] = True
+    bits = np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little").astype(bool)[: L * T]
+    assert np.array_equal(bits, want)
