@@ -128,7 +128,7 @@ def _stage_work(n_touched, F=2, L=16, d=2, width=64, n_in=32):
     fwd = BATCH * (4 * d + L * V * 2 * F + L * F * 2)              # x, fp16 gathers, fp16 encoding
     bwd = BATCH * (4 * d + 4 * L * F + L * V * 2 * 4 * F)           # x, dL/d(enc), fp32 RMW per vertex
     adam = n_touched * (2 * 16 * F + 2 * F) + L * (1 << 22) // 8    # record r+w, fp16 copy; bitmap scan
-    flops = 2 * (n_in * width + width * width + width * 16)        # forward MACs (output padded to 16)
+    flops = 2 * (n_in * width + width * width + width * N_OUT)     # forward multiply-adds per point
     flops = 3 * flops * BATCH                                      # forward + delta + weight-gradient GEMMs
     return {"encode_fwd": ("hbm", fwd), "encode_bwd": ("hbm", bwd), "adam_tables": ("hbm", adam),
             "mlp_train_l2": ("tensor", flops)}
@@ -360,6 +360,7 @@ def random_access_peaks(dev, state_bytes, table, n_ops=1 << 24, reps=5):
     st = torch.cuda.current_stream(dev).cuda_stream
     tab = table.view(torch.float32).reshape(-1)
     cases = {"red_f2_miss": (0, buf, n_rec, 8), "red_f2_l2": (0, buf, 1 << 18, 8),
+             "rmw_32B_random_order": (2, buf, n_rec, 8),
              "gather_4B_table": (1, tab, 1 << int(math.log2(tab.numel())), 1)}
     out = {}
     for name, (kind, b, slots, sf) in cases.items():

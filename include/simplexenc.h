@@ -224,7 +224,9 @@ sxe_status sxe_vr_composite(const float* sigma, const float* rgb_logits, const f
  *   kind 0: a float2 atomic add of (1, 1) into the slot's last two floats
  *           (the shape of the table backward's reductions into state records);
  *   kind 1: a 4-byte load of the slot's first float (the shape of the forward gathers);
- *           sink [1] is written only if the loaded sum is -1.
+ *           sink [1] is written only if the loaded sum is -1;
+ *   kind 2: a read and write back of the whole 32-byte slot (slot_floats = 8, buf 16-byte
+ *           aligned; the shape of the table optimiser), four slots in flight per thread.
  * Timed by the caller to give the peak rate of that pattern for a given footprint. */
 sxe_status sxe_probe_random_access(int32_t kind, float* buf, int64_t n_slots, int32_t slot_floats,
                                    int64_t n_ops, uint64_t seed, float* sink, void* stream);
@@ -353,6 +355,7 @@ sxe_status sxe_step(const sxe_adam_desc* desc, int64_t t, int64_t n, float* para
 sxe_status sxe_step_touched(const sxe_adam_desc* desc, int64_t t, int64_t n_entries,
                             int32_t n_features, float* state, uint32_t* touched,
                             void* table_lowp, int32_t lowp_dtype, void* stream);
+
 
 /* Which kernel runs the network's training pass (sxe_mlp_bwd, sxe_mlp_train_l2*),
  * process-wide: SXE_MLP_KERNEL_MMA_SYNC (warp-level mma.sync for every product) or

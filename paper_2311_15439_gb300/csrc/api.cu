@@ -219,12 +219,14 @@ sxe_status sxe_vr_composite(const float* sigma, const float* rgb_logits, const f
 
 sxe_status sxe_probe_random_access(int32_t kind, float* buf, int64_t n_slots, int32_t slot_floats, int64_t n_ops,
                                    uint64_t seed, float* sink, void* stream) {
-  if (kind != 0 && kind != 1) return set_error(SXE_EINVAL, "probe_random_access: kind must be 0 or 1");
+  if (kind < 0 || kind > 2) return set_error(SXE_EINVAL, "probe_random_access: kind must be 0, 1 or 2");
+  if (kind == 2 && slot_floats != 8) return set_error(SXE_EINVAL, "probe_random_access: kind 2 needs slot_floats = 8");
   if (n_slots < 1 || (n_slots & (n_slots - 1)) != 0 || n_slots > ((int64_t)1 << 34))
     return set_error(SXE_EINVAL, "probe_random_access: n_slots must be a power of two");
   if (slot_floats < 2 || slot_floats > 64 || (slot_floats & 1) || n_ops < 0)
     return set_error(SXE_EINVAL, "probe_random_access: slot_floats must be even in 2..64");
-  if (!buf || !sink || !aligned(buf, 8)) return set_error(SXE_EINVAL, "probe_random_access: NULL or misaligned buffer");
+  if (!buf || !sink || !aligned(buf, kind == 2 ? 16 : 8))
+    return set_error(SXE_EINVAL, "probe_random_access: NULL or misaligned buffer");
   if (n_ops == 0) return SXE_OK;
   return launch_probe(kind, buf, n_slots, slot_floats, n_ops, seed, sink, (cudaStream_t)stream);
 }

@@ -7,47 +7,12 @@
 // (grid) independent gathers before it consumes any of them.
 #include <algorithm>
 
-#include "sxe_internal.cuh"
+#include "encode_common.cuh"
 
 namespace sxe {
 namespace {
 
-constexpr int kThreads = 256;
-
-template <bool SIMPLEX, int D> struct Verts { static constexpr int V = SIMPLEX ? D + 1 : (1 << D); };
-
-template <bool SIMPLEX, int D>
-__device__ __forceinline__ void lattice(const float (&x)[D], float s, float skewF, uint32_t mask, uint32_t width,
-                                        uint32_t (&slot)[Verts<SIMPLEX, D>::V], float (&w)[Verts<SIMPLEX, D>::V]) {
-  if constexpr (SIMPLEX) simplex_lattice<D>(x, s, skewF, mask, width, slot, w);
-  else grid_lattice<D>(x, s, mask, width, slot, w);
-}
-
-// Decode work item i = blockIdx.x * kThreads + threadIdx.x into (point, level) = (i / L, i % L)
-// with 32-bit divisions only: blockIdx.x = qb L + rb gives i = qb kThreads L + j with
-// j = rb kThreads + threadIdx.x < L kThreads, so i / L = qb kThreads + j / L.
-struct Item { int64_t p; int l; };
-__device__ __forceinline__ Item item_of(int L) {
-  const uint32_t uL = (uint32_t)L;
-  const uint32_t qb = blockIdx.x / uL;
-  const uint32_t j = (blockIdx.x - qb * uL) * kThreads + threadIdx.x;
-  const uint32_t q = j / uL;
-  return Item{(int64_t)qb * kThreads + q, (int)(j - q * uL)};
-}
-
-template <int D>
-__device__ __forceinline__ void load_point(const float* __restrict__ x, int64_t p, float (&v)[D]) {
-  if constexpr (D == 2) {
-    const float2 a = __ldg(reinterpret_cast<const float2*>(x) + p);
-    v[0] = a.x; v[1] = a.y;
-  } else if constexpr (D == 4) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(x) + p);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  } else {
-#pragma unroll
-    for (int i = 0; i < D; ++i) v[i] = __ldg(x + p * D + i);
-  }
-}
+using namespace encode_detail;
 
 template <bool SIMPLEX, int D, int F, typename TT>
 __global__ void __launch_bounds__(kThreads)
@@ -185,7 +150,6 @@ encode_vertices_kernel(const float* __restrict__ x, int64_t P, uint32_t* __restr
   }
 }
 
-inline unsigned grid_for(int64_t P, int L) { return (unsigned)((P * L + kThreads - 1) / kThreads); }
 
 // ---- dispatch ---------------------------------------------------------------
 // Coarse levels, privately per CTA.  The lattice box of a coarse level has few vertices
