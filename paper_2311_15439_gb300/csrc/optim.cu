@@ -31,43 +31,54 @@ __global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p,
   }
 }
 
-// A warp reads 32 consecutive bitmap words at once (one per lane, coalesced) and visits
-// only the nonzero ones, the 32 lanes taking a word's 32 entries.  Up to NB nonzero words are
-// handled together: all their marked records are loaded before any is updated, so a warp
-// keeps NB record loads in flight instead of one.  Each lane clears the word it loaded.
+// A warp takes 32 consecutive bitmap words (1024 entries).  The set bits of the 32 words are
+// listed in shared memory in address order (a warp prefix sum of the words' popcounts gives
+// each word's place in the list); then the lanes take the listed entries in turn, NB records per
+// lane loaded before any is updated, so a warp keeps up to 32 NB record loads in flight however
+// sparse the words are.  Each lane clears the word it loaded.
 template <int F>
 __global__ void __launch_bounds__(256)
 adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state, uint32_t* __restrict__ touched,
                     void* __restrict__ lowp, int ldt) {
   constexpr int NB = F <= 2 ? 4 : (F == 4 ? 2 : 1);
-  const int lane = threadIdx.x & 31;
+  __shared__ uint16_t list[8][1024];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t n_words = (n_entries + 31) >> 5;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  uint16_t* my = list[wib];
   for (int64_t w0 = warp0 << 5; w0 < n_words; w0 += n_warps << 5) {
     const int64_t wi = w0 + lane;
     const uint32_t mine = wi < n_words ? touched[wi] : 0u;
-    uint32_t todo = __ballot_sync(0xffffffffu, mine != 0u);
-    while (todo) {
+    const int cnt = __popc(mine);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    int at = incl - cnt;
+    for (uint32_t bits = mine; bits; bits &= bits - 1u) my[at++] = (uint16_t)(lane * 32 + __ffs(bits) - 1);
+    __syncwarp();
+    const int64_t ebase = w0 << 5;
+    for (int i0 = 0; i0 < total; i0 += 32 * NB) {
       int64_t e[NB];
       bool on[NB];
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int src = todo ? __ffs(todo) - 1 : 0;
-        const uint32_t bits = __shfl_sync(0xffffffffu, mine, src);
-        on[b] = todo != 0u && ((bits >> lane) & 1u);
-        todo &= todo ? todo - 1u : 0u;
-        e[b] = ((w0 + src) << 5) + lane;
-        on[b] = on[b] && e[b] < n_entries;
-      }
       union Rec { float4 v[F]; float f[4 * F]; } r[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b)
+      for (int b = 0; b < NB; ++b) {
+        const int i = i0 + b * 32 + lane;
+        on[b] = i < total;
+        e[b] = on[b] ? ebase + my[i] : 0;
+        on[b] = on[b] && e[b] < n_entries;
         if (on[b]) {
           const float4* rec = reinterpret_cast<const float4*>(state + e[b] * (4 * F));
 #pragma unroll
           for (int j = 0; j < F; ++j) r[b].v[j] = rec[j];
         }
+      }
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         if (on[b]) {
@@ -86,6 +97,7 @@ adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state, u
           store_lowp<F>(lowp, e[b], ldt, p);
         }
     }
+    __syncwarp();
     if (mine) touched[wi] = 0u;
   }
 }
