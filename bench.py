@@ -36,6 +36,26 @@ WORKLOAD = "image_fit_2d_L16_F2_T2^22_fp16_mlp64x2_P2^18"
 METRIC = "simplex encode fwd+bwd training-step throughput"
 N_POOL = 8   # distinct resident batches cycled through the timed steps
 
+# DRAM traffic of one step's launch of a stage (dram__bytes_read.sum + dram__bytes_write.sum of its
+# kernels in one ncu capture of this workload), with the SHA-1 of the kernel sources it was taken
+# on: the figure is reported only while those sources are unchanged.
+TRAFFIC = {
+    "encode_bwd": (35.81e6 + 758.56e6, "65de9e393f40360e92e785382ac0535627982d7a",
+                   ("encode.cu", "encode_common.cuh", "sxe_internal.cuh")),
+}
+
+
+def _traffic(stage):
+    import hashlib
+    if stage not in TRAFFIC:
+        return None
+    nbytes, sha, files = TRAFFIC[stage]
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2311_15439_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return nbytes if h.hexdigest() == sha else None
+
 
 def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
@@ -273,7 +293,7 @@ def run_gpu(args):
             "e2e": {"value": BATCH * e2e_steps * world / (ms_e2e / 1e3), "unit": "points/s",
                     "h2d_bytes_per_step": BATCH * (2 + N_OUT) * 4, "d2h_bytes_per_step": 4},
             "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "frac": achieved / peak, "traffic": _traffic(dom), "peak_source": peak_src,
                          "work_per_step": amount, "touched_entries_per_step": n_touched},
             "per_kernel_ms": per_kernel,
             "gpu_launches": args.steps * tr.n_launches_per_step,
