@@ -261,6 +261,18 @@ int64_t sxe_mlp_n_params(const sxe_mlp_desc* desc);
 sxe_status sxe_mlp_fwd(const sxe_mlp_desc* desc, const void* weights, const void* in,
                        int64_t n_points, float* out, void* act, void* stream);
 
+/* The field between the encoding and the compositing in one kernel: the density network
+ * (dd: n_in -> 64 -> 16, weights Wd), sigma = exp(min(v_0, 15)) and the colour network's
+ * input [v_0..v_15, SH(d)] (as sxe_vr_field, kept in shared memory), then the colour network
+ * (dc: 32 -> ... -> n_out, weights Wc, same dtype).  enc [n_rays*S][n_in] of the network
+ * dtype (16-byte aligned rows), dirs [n_rays][3]; writes sigma [n_rays*S] and
+ * logits [n_rays*S][dc.n_out] binary32.  Same results as sxe_mlp_fwd, sxe_vr_field and
+ * sxe_mlp_fwd in sequence, bit for bit.  Volumetric rendering, Sec. 6.2. */
+sxe_status sxe_vr_field_mlp(const sxe_mlp_desc* density, const void* Wd,
+                            const sxe_mlp_desc* color, const void* Wc, const void* enc,
+                            const float* dirs, int64_t n_rays, int32_t n_samples, float* sigma,
+                            float* logits, void* stream);
+
 /* Size in bytes of the workspace sxe_mlp_bwd needs for n_points (host). */
 int64_t sxe_mlp_bwd_workspace_bytes(const sxe_mlp_desc* desc, int64_t n_points);
 

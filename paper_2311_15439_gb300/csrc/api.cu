@@ -276,6 +276,24 @@ static sxe_status check_mlp(const char* fn, const sxe_mlp_desc* d) {
   return SXE_OK;
 }
 
+sxe_status sxe_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
+                            const void* enc, const float* dirs, int64_t R, int32_t S, float* sigma, float* logits,
+                            void* stream) {
+  sxe_status st = check_rays("vr_field_mlp", R, S);
+  if (st != SXE_OK) return st;
+  if (!dd || !dc) return set_error(SXE_EINVAL, "vr_field_mlp: NULL network description");
+  if ((st = check_mlp("vr_field_mlp", dd)) != SXE_OK || (st = check_mlp("vr_field_mlp", dc)) != SXE_OK) return st;
+  if (dd->n_hidden != 1 || dd->n_out != 16 || dc->n_in != 32 || dc->dtype != dd->dtype)
+    return set_error(SXE_EUNSUPPORTED, "vr_field_mlp: needs a density network n_in -> 64 -> 16 and a colour "
+                     "network 32 -> ... of the same dtype");
+  if (R == 0) return SXE_OK;
+  if (!Wd || !Wc || !enc || !dirs || !sigma || !logits) return set_error(SXE_EINVAL, "vr_field_mlp: NULL buffer");
+  if (!aligned(enc, 16) || !aligned(Wd, 4) || !aligned(Wc, 4) || !aligned(dirs, 4) || !aligned(sigma, 4) ||
+      !aligned(logits, 4))
+    return set_error(SXE_EINVAL, "vr_field_mlp: misaligned buffer (encoding rows need 16 bytes)");
+  return launch_vr_field_mlp(dd, Wd, dc, Wc, enc, dirs, R, S, sigma, logits, (cudaStream_t)stream);
+}
+
 int64_t sxe_mlp_n_params(const sxe_mlp_desc* d) {
   if (!d) return 0;
   return (int64_t)d->width * d->n_in + (int64_t)(d->n_hidden - 1) * d->width * d->width + (int64_t)d->n_out * d->width;

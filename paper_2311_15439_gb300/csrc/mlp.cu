@@ -251,6 +251,71 @@ mlp_fwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
   }
 }
 
+// Volumetric field of a tile of samples in one pass (Sec. 6.2): the density network, then
+// sigma = exp(min(v_0, 15)) and the colour network's input row [v_0..v_15, SH(d)] written to
+// shared memory by the warp that owns the rows, then the colour network.  The arithmetic is
+// that of sxe_mlp_fwd, sxe_vr_field and sxe_mlp_fwd in sequence; nothing but sigma and the
+// colour logits leaves the chip.
+template <typename T, int N_IN, int NHC>
+__global__ void __launch_bounds__(kThreads)
+vr_field_mlp_kernel(const T* __restrict__ Wd, const T* __restrict__ Wc, const T* __restrict__ enc,
+                    const float* __restrict__ dirs, int64_t P, int S, int n_out_c, float* __restrict__ sigma,
+                    float* __restrict__ logits) {
+  using SD = Smem<N_IN, 1>;
+  using SC = Smem<32, NHC>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smd = reinterpret_cast<T*>(smem_raw);
+  T* smc = smd + SD::FWD_END;
+  load_weights<T, N_IN, 1>(Wd, 16, smd);
+  load_weights<T, 32, NHC>(Wc, n_out_c, smc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = warp * 16;
+  const int64_t n_tiles = (P + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kTile;
+    __syncthreads();
+    load_inputs<T, N_IN, 1>(enc, row0, P, smd);
+    __syncthreads();
+    float y[2][4];
+    uint32_t hfr[1][4][4];
+    forward_rows<T, N_IN, 1>(smd, r0, g, t, false, y, hfr);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int rl = r0 + g + 8 * half;
+      const int64_t row = row0 + rl;
+      if (t == 0 && row < P) sigma[row] = vr_density(y[0][2 * half]);
+      T* xr = smc + SC::X + rl * SC::SX;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) sts32(xr + nt * 8 + 2 * t, pack2<T>(y[nt][2 * half], y[nt][2 * half + 1]));
+      const int64_t ray = (row < P ? row : P - 1) / S;
+      float h[16];
+      sh16(__ldg(dirs + ray * 3), __ldg(dirs + ray * 3 + 1), __ldg(dirs + ray * 3 + 2), h);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (t == q) {
+          sts32(xr + 16 + 4 * q, pack2<T>(h[4 * q], h[4 * q + 1]));
+          sts32(xr + 18 + 4 * q, pack2<T>(h[4 * q + 2], h[4 * q + 3]));
+        }
+    }
+    __syncwarp();
+    float y2[2][4];
+    uint32_t hfr2[NHC][4][4];
+    forward_rows<T, 32, NHC>(smc, r0, g, t, false, y2, hfr2);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int64_t row = row0 + r0 + g + half * 8;
+      if (row >= P) continue;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int o = nt * 8 + 2 * t + j;
+          if (o < n_out_c) logits[row * n_out_c + o] = y2[nt][half * 2 + j];
+        }
+    }
+  }
+}
+
 // MODE 0: dy = dout * loss_scale.  MODE 1: dy = loss_scale * 2 (y - target) / (P n_out),
 // and the squared residuals are summed into *sq_sum.
 // Two CTAs per SM where the shared-memory plan allows it (then at most 128 registers).
@@ -536,11 +601,53 @@ sxe_status fwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, int6
   using S = Smem<N_IN, NH>;
   const size_t bytes = (size_t)S::FWD_END * sizeof(T);   // weights + input tile
   auto k = mlp_fwd_kernel<T, N_IN, NH>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static int per_sm = 0;                        // resident CTAs per SM (registers, shared memory)
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, bytes) != cudaSuccess || per_sm < 1)
+      per_sm = 2;
+  }
   const int64_t n_tiles = (P + kTile - 1) / kTile;
-  const int grid = (int)std::min<int64_t>(n_tiles, 2 * num_sms());
+  const int grid = (int)std::min<int64_t>(n_tiles, (int64_t)per_sm * num_sms());
   k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, out, (T*)act);
   return check_launch("mlp_fwd");
+}
+
+template <typename T, int N_IN, int NHC>
+sxe_status field_launch(const void* Wd, const void* Wc, const void* enc, const float* dirs, int64_t P, int S,
+                        int n_out_c, float* sigma, float* logits, cudaStream_t s) {
+  const size_t bytes = (size_t)(Smem<N_IN, 1>::FWD_END + Smem<32, NHC>::FWD_END) * sizeof(T);
+  auto k = vr_field_mlp_kernel<T, N_IN, NHC>;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, bytes) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+  }
+  const int64_t n_tiles = (P + kTile - 1) / kTile;
+  const int grid = (int)std::min<int64_t>(n_tiles, (int64_t)per_sm * num_sms());
+  k<<<grid, kThreads, bytes, s>>>((const T*)Wd, (const T*)Wc, (const T*)enc, dirs, P, S, n_out_c, sigma, logits);
+  return check_launch("vr_field_mlp");
+}
+
+template <typename T, int N_IN>
+sxe_status field_nh(int nhc, const void* Wd, const void* Wc, const void* enc, const float* dirs, int64_t P, int S,
+                    int n_out_c, float* sigma, float* logits, cudaStream_t s) {
+  switch (nhc) {
+    case 1: return field_launch<T, N_IN, 1>(Wd, Wc, enc, dirs, P, S, n_out_c, sigma, logits, s);
+    case 2: return field_launch<T, N_IN, 2>(Wd, Wc, enc, dirs, P, S, n_out_c, sigma, logits, s);
+    default: return field_launch<T, N_IN, 3>(Wd, Wc, enc, dirs, P, S, n_out_c, sigma, logits, s);
+  }
+}
+
+template <typename T>
+sxe_status field_in(int n_in, int nhc, const void* Wd, const void* Wc, const void* enc, const float* dirs, int64_t P,
+                    int S, int n_out_c, float* sigma, float* logits, cudaStream_t s) {
+  switch (n_in) {
+    case 16: return field_nh<T, 16>(nhc, Wd, Wc, enc, dirs, P, S, n_out_c, sigma, logits, s);
+    case 32: return field_nh<T, 32>(nhc, Wd, Wc, enc, dirs, P, S, n_out_c, sigma, logits, s);
+    default: return field_nh<T, 64>(nhc, Wd, Wc, enc, dirs, P, S, n_out_c, sigma, logits, s);
+  }
 }
 
 template <typename T, int N_IN, int NH>
@@ -632,6 +739,15 @@ sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, 
                           cudaStream_t s) {
   return d->dtype == SXE_F16 ? fwd_in<__half>(d, W, in, P, out, act, s)
                              : fwd_in<__nv_bfloat16>(d, W, in, P, out, act, s);
+}
+
+sxe_status launch_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
+                               const void* enc, const float* dirs, int64_t R, int S, float* sigma, float* logits,
+                               cudaStream_t s) {
+  const int64_t P = R * S;
+  return dd->dtype == SXE_F16
+             ? field_in<__half>(dd->n_in, dc->n_hidden, Wd, Wc, enc, dirs, P, S, dc->n_out, sigma, logits, s)
+             : field_in<__nv_bfloat16>(dd->n_in, dc->n_hidden, Wd, Wc, enc, dirs, P, S, dc->n_out, sigma, logits, s);
 }
 
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,

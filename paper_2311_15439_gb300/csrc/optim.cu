@@ -37,7 +37,7 @@ __global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p,
 // lane loaded before any is updated, so a warp keeps up to 32 NB record loads in flight however
 // sparse the words are.  Each lane clears the word it loaded.
 template <int F>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state, uint32_t* __restrict__ touched,
                     void* __restrict__ lowp, int ldt) {
   constexpr int NB = F <= 2 ? 4 : (F == 4 ? 2 : 1);

@@ -29,28 +29,6 @@ vr_samples_kernel(const float* __restrict__ o, const float* __restrict__ d, cons
   if (k == 0) delta[r] = dl;
 }
 
-// Real spherical harmonics of degree 0..3 (l-major, m = -l..l) of a unit vector: the
-// orthonormal real basis built from the complex harmonics with the Condon-Shortley phase.
-__device__ __forceinline__ void sh16(float x, float y, float z, float (&h)[16]) {
-  const float xx = x * x, yy = y * y, zz = z * z;
-  h[0] = 0.28209479177387814f;                       // 1/(2 sqrt(pi))
-  h[1] = 0.4886025119029199f * y;                    // sqrt(3/(4 pi))
-  h[2] = 0.4886025119029199f * z;
-  h[3] = 0.4886025119029199f * x;
-  h[4] = 1.0925484305920792f * x * y;                // sqrt(15/pi)/2
-  h[5] = 1.0925484305920792f * y * z;
-  h[6] = 0.31539156525252005f * (3.f * zz - 1.f);    // sqrt(5/pi)/4
-  h[7] = 1.0925484305920792f * x * z;
-  h[8] = 0.5462742152960396f * (xx - yy);            // sqrt(15/pi)/4
-  h[9] = 0.5900435899266435f * y * (3.f * xx - yy);  // sqrt(35/(2 pi))/4
-  h[10] = 2.890611442640554f * x * y * z;            // sqrt(105/pi)/2
-  h[11] = 0.4570457994644658f * y * (5.f * zz - 1.f);  // sqrt(21/(2 pi))/4
-  h[12] = 0.3731763325901154f * z * (5.f * zz - 3.f);  // sqrt(7/pi)/4
-  h[13] = 0.4570457994644658f * x * (5.f * zz - 1.f);
-  h[14] = 1.445305721320277f * z * (xx - yy);        // sqrt(105/pi)/4
-  h[15] = 0.5900435899266435f * x * (xx - 3.f * yy);
-}
-
 // Field head: sigma = exp(min(v_0, 15)) from the density network's 16 outputs v, and the
 // colour network's input row [v_0..v_15, SH(d)] in the network dtype.
 template <typename T>
@@ -66,7 +44,7 @@ vr_field_kernel(const float* __restrict__ dens, const float* __restrict__ dirs, 
     const float4 a = __ldg(src + j);
     v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
   }
-  sigma[p] = expf(fminf(v[0], 15.f));
+  sigma[p] = vr_density(v[0]);
   const int64_t r = p / S;
   float h[16];
   sh16(__ldg(dirs + r * 3), __ldg(dirs + r * 3 + 1), __ldg(dirs + r * 3 + 2), h);

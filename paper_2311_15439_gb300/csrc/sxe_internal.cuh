@@ -62,6 +62,9 @@ sxe_status launch_vr_field(const float* dens, const float* dirs, int64_t R, int 
                            void* cin, cudaStream_t s);
 sxe_status launch_probe(int kind, float* buf, int64_t n_slots, int slot_floats, int64_t n_ops, uint64_t seed,
                         float* sink, cudaStream_t s);
+sxe_status launch_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
+                               const void* enc, const float* dirs, int64_t R, int S, float* sigma, float* logits,
+                               cudaStream_t s);
 sxe_status launch_vr_composite(const float* sigma, const float* logits, const float* delta, int64_t R, int S,
                                float* color, float* trans, float* weights, cudaStream_t s);
 
@@ -338,5 +341,31 @@ __device__ __forceinline__ uint32_t vertex_slot(const uint32_t (&v)[D], uint32_t
   }
   return h & mask;
 }
+
+// Real spherical harmonics of degree 0..3 (l-major, m = -l..l) of a unit vector: the
+// orthonormal real basis built from the complex harmonics with the Condon-Shortley phase.
+__device__ __forceinline__ void sh16(float x, float y, float z, float (&h)[16]) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  h[0] = 0.28209479177387814f;                       // 1/(2 sqrt(pi))
+  h[1] = 0.4886025119029199f * y;                    // sqrt(3/(4 pi))
+  h[2] = 0.4886025119029199f * z;
+  h[3] = 0.4886025119029199f * x;
+  h[4] = 1.0925484305920792f * x * y;                // sqrt(15/pi)/2
+  h[5] = 1.0925484305920792f * y * z;
+  h[6] = 0.31539156525252005f * (3.f * zz - 1.f);    // sqrt(5/pi)/4
+  h[7] = 1.0925484305920792f * x * z;
+  h[8] = 0.5462742152960396f * (xx - yy);            // sqrt(15/pi)/4
+  h[9] = 0.5900435899266435f * y * (3.f * xx - yy);  // sqrt(35/(2 pi))/4
+  h[10] = 2.890611442640554f * x * y * z;            // sqrt(105/pi)/2
+  h[11] = 0.4570457994644658f * y * (5.f * zz - 1.f);  // sqrt(21/(2 pi))/4
+  h[12] = 0.3731763325901154f * z * (5.f * zz - 3.f);  // sqrt(7/pi)/4
+  h[13] = 0.4570457994644658f * x * (5.f * zz - 1.f);
+  h[14] = 1.445305721320277f * z * (xx - yy);        // sqrt(105/pi)/4
+  h[15] = 0.5900435899266435f * x * (xx - 3.f * yy);
+}
+
+// Density of the volumetric field from the density network's first output (Instant-NGP's
+// exponential activation, argument clamped at 15).
+__device__ __forceinline__ float vr_density(float v0) { return expf(fminf(v0, 15.f)); }
 
 }  // namespace sxe

@@ -4,15 +4,18 @@ A ``Renderer`` renders a batch of rays through the library's kernels only:
 
 1. ``sxe_vr_samples``   -- S midpoint samples per ray in [t_near, t_far];
 2. ``sxe_encode_fwd``   -- the multiresolution encoding of every sample (Sec. 5 a-d);
-3. ``sxe_mlp_fwd``      -- density network, encoding -> 64 -> 16;
-4. ``sxe_vr_field``     -- sigma = exp(min(v_0, 15)) and the colour input [v, SH(d)];
-5. ``sxe_mlp_fwd``      -- colour network, 32 -> 64 -> 64 -> 3;
-6. ``sxe_vr_composite`` -- sigmoid colours composited front to back (Eq. 5).
+3. ``sxe_vr_field_mlp`` -- density network (encoding -> 64 -> 16), sigma = exp(min(v_0, 15)),
+                           colour input [v, SH(d)] and colour network (32 -> 64 -> 64 -> 3) in
+                           one kernel;
+4. ``sxe_vr_composite`` -- sigmoid colours composited front to back (Eq. 5).
 
-All buffers are allocated once for the largest ray batch and reused; a render is six
-asynchronous launches on one stream.
+With ``fused=False`` step 3 is three launches (``sxe_mlp_fwd``, ``sxe_vr_field``,
+``sxe_mlp_fwd``) with the same results.  All buffers are allocated once for the largest ray
+batch and reused; every launch is asynchronous on one stream.
 """
 from __future__ import annotations
+
+import ctypes
 
 import torch
 
@@ -25,12 +28,13 @@ _VR_DTYPES = {"f16": L.SXE_F16, "bf16": L.SXE_BF16}
 class Renderer:
     """Renders rays of a field = (encoder, density network, colour network)."""
 
-    def __init__(self, encoder: Encoder, max_rays: int, n_samples: int, *, dtype: str = "f16", device="cuda"):
+    def __init__(self, encoder: Encoder, max_rays: int, n_samples: int, *, dtype: str = "f16", device="cuda",
+                 fused: bool = True):
         if encoder.d != 3:
             raise ValueError("volumetric rendering needs a 3-D encoder")
         if encoder.out_dtype != dtype:
             raise ValueError("encoder output dtype %s != network dtype %s" % (encoder.out_dtype, dtype))
-        self.enc, self.S, self.max_rays, self.dtype = encoder, n_samples, max_rays, dtype
+        self.enc, self.S, self.max_rays, self.dtype, self.fused = encoder, n_samples, max_rays, dtype, fused
         self.density = Mlp(encoder.n_out, 16, n_hidden=1, dtype=dtype)
         self.color = Mlp(32, 3, n_hidden=2, dtype=dtype)
         dev = torch.device(device)
@@ -74,17 +78,24 @@ class Renderer:
         L.check(lib.sxe_vr_samples(_ptr(origins), _ptr(dirs), _ptr(t_near), _ptr(t_far), R, S, _ptr(x),
                                    _ptr(self.delta), st), "sxe_vr_samples")
         self.enc.encode_fwd(x, tables, self.enc_out[:P], stream=stream)
-        self.density.mlp_fwd(W_density, self.enc_out[:P], out=self.dens_out[:P], stream=stream)
-        L.check(lib.sxe_vr_field(_ptr(self.dens_out), _ptr(dirs), R, S, _VR_DTYPES[self.dtype], _ptr(self.sigma),
-                                 _ptr(self.color_in), st), "sxe_vr_field")
-        self.color.mlp_fwd(W_color, self.color_in[:P], out=self.logits[:P], stream=stream)
+        if self.fused:
+            for W, m, nm in ((W_density, self.density, "W_density"), (W_color, self.color, "W_color")):
+                _need(W, torch_dtype(self.dtype), nm, (m.n_params,))
+            L.check(lib.sxe_vr_field_mlp(ctypes.byref(self.density.desc), _ptr(W_density), ctypes.byref(self.color.desc),
+                                         _ptr(W_color), _ptr(self.enc_out), _ptr(dirs), R, S, _ptr(self.sigma),
+                                         _ptr(self.logits), st), "sxe_vr_field_mlp")
+        else:
+            self.density.mlp_fwd(W_density, self.enc_out[:P], out=self.dens_out[:P], stream=stream)
+            L.check(lib.sxe_vr_field(_ptr(self.dens_out), _ptr(dirs), R, S, _VR_DTYPES[self.dtype],
+                                     _ptr(self.sigma), _ptr(self.color_in), st), "sxe_vr_field")
+            self.color.mlp_fwd(W_color, self.color_in[:P], out=self.logits[:P], stream=stream)
         L.check(lib.sxe_vr_composite(_ptr(self.sigma), _ptr(self.logits), _ptr(self.delta), R, S, _ptr(color),
                                      _ptr(transmittance), _ptr(weights), st), "sxe_vr_composite")
         return color
 
     @property
     def n_launches(self) -> int:
-        return 6
+        return 4 if self.fused else 6
 
 
 def vr_samples(origins, dirs, t_near, t_far, n_samples: int, stream=None):
@@ -117,3 +128,38 @@ def vr_composite(sigma, logits, delta, n_samples: int, with_weights: bool = Fals
     L.check(L.lib().sxe_vr_composite(_ptr(sigma), _ptr(logits), _ptr(delta), R, n_samples, _ptr(color), _ptr(trans),
                                      _ptr(w), _stream(stream)), "sxe_vr_composite")
     return color, trans, w
+
+
+def _main(argv=None):
+    """Render seeded camera rays through a random field and print the time per render:
+    ``python -m paper_2311_15439_gb300.render --rays 65536 --samples 64 --kind simplex``."""
+    import argparse
+    from . import synth
+    ap = argparse.ArgumentParser(description=_main.__doc__)
+    ap.add_argument("--rays", type=int, default=1 << 16)
+    ap.add_argument("--samples", type=int, default=64)
+    ap.add_argument("--kind", default="simplex", choices=["simplex", "grid"])
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--repeat", type=int, default=5)
+    ap.add_argument("--unfused", action="store_true", help="the field as three launches")
+    a = ap.parse_args(argv)
+    enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=a.kind, table_dtype="f16")
+    rr = Renderer(enc, a.rays, a.samples, dtype="f16", fused=not a.unfused)
+    _, store = synth.uniform_tables(16, 1 << 19, 2, 61, dtype="f16", scale=1.0)
+    tab = torch.from_numpy(store).cuda()
+    Wd, Wc = rr.init_weights(62)
+    rays = [torch.from_numpy(v).cuda() for v in synth.camera_rays(a.rays, 60)]
+    for _ in range(a.warmup):
+        rr.render(*rays, tab, Wd, Wc)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(a.repeat):
+        rr.render(*rays, tab, Wd, Wc)
+    e.record()
+    torch.cuda.synchronize()
+    print("render %s: %d rays x %d samples: %.3f ms" % (a.kind, a.rays, a.samples, s.elapsed_time(e) / a.repeat))
+
+
+if __name__ == "__main__":
+    _main()

@@ -129,3 +129,28 @@ def test_render_full_size(cuda_lib):
     Wc_ = [w.astype(np.float64) for w in rr.color.split(Wc.float().cpu().numpy())]
     Cref, _, _ = OR.render(*sub, S, vals, Wd_, Wc_, kind="simplex", base_res=16.0, growth=1.38)
     assert np.abs(C[idx] - Cref).max() <= 0.03
+
+
+@pytest.mark.parametrize("kind,dtype,L", [("simplex", "f16", 16), ("grid", "bf16", 8), ("simplex", "f16", 32)])
+def test_fused_field_equals_three_launches(cuda_lib, kind, dtype, L):
+    """The one-kernel field (density network, field head, colour network) gives the same sigma,
+    colour logits and colours, bit for bit, as the three separate launches; ragged last tile."""
+    from paper_2311_15439_gb300.api import Encoder, torch_dtype
+    from paper_2311_15439_gb300.render import Renderer
+    R, S = 333, 7
+    F = 2 if L <= 16 else 1
+    enc = Encoder(3, L, F, 14, 16.0, 1.4, kind=kind, table_dtype=dtype)
+    _, store = synth.uniform_tables(L, 1 << 14, F, 40, dtype=dtype, scale=1.0)
+    t = torch.from_numpy(store.astype(np.int16) if dtype == "bf16" else store).cuda()
+    if dtype == "bf16":
+        t = t.view(torch.bfloat16)
+    rays = [torch.from_numpy(a).cuda() for a in synth.camera_rays(R, 41)]
+    out = []
+    for fused in (False, True):
+        rr = Renderer(enc, R, S, dtype=dtype, fused=fused)
+        Wd, Wc = rr.init_weights(42)
+        tr = torch.empty((R,), device="cuda")
+        C = rr.render(*rays, t, Wd, Wc, transmittance=tr)
+        out.append((C.clone(), tr.clone(), rr.sigma[:R * S].clone(), rr.logits[:R * S].clone()))
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
