@@ -160,7 +160,7 @@ __device__ __forceinline__ void issue_gemm(uint32_t tmem, const unsigned char* A
 
 // MODE 0: dy = dout * loss_scale.  MODE 1: L2 loss against target.
 template <typename T, int N_IN, int NH, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 mlp_train_tc_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
                     const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
                     float* __restrict__ din, int din_group, float* __restrict__ ws, int64_t n_params) {
