@@ -23,6 +23,11 @@ __device__ __forceinline__ void lattice(const float (&x)[D], float s, float skew
 // j = rb kThreads + threadIdx.x < L kThreads, so i / L = qb kThreads + j / L.
 struct Item { int64_t p; int l; };
 __device__ __forceinline__ Item item_of(int L) {
+  if ((L & (L - 1)) == 0) {                          // L a power of two: shifts
+    const int sh = __ffs(L) - 1;
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    return Item{i >> sh, (int)(i & (L - 1))};
+  }
   const uint32_t uL = (uint32_t)L;
   const uint32_t qb = blockIdx.x / uL;
   const uint32_t j = (blockIdx.x - qb * uL) * kThreads + threadIdx.x;

@@ -195,16 +195,47 @@ __device__ __forceinline__ void store_lowp(void* base, int64_t e, int ldt, const
   }
 }
 
+// Compare-exchange of a descending sort of (f, axis) with ties broken by the lower axis first,
+// carrying each axis's hash step along.
+__device__ __forceinline__ void sort_cx(float& fa, int& ia, uint32_t& da, float& fb, int& ib, uint32_t& db) {
+  const bool sw = (fb > fa) || (fb == fa && ib < ia);
+  const float f = sw ? fb : fa;
+  const int i = sw ? ib : ia;
+  const uint32_t d = sw ? db : da;
+  fb = sw ? fa : fb; ib = sw ? ia : ib; db = sw ? da : db;
+  fa = f; ia = i; da = d;
+}
+
+// Sorting networks (1, 3, 5 and 9 comparators for 2, 3, 4 and 5 keys).
+template <int D>
+__device__ __forceinline__ void sort_desc(float (&f)[D], int (&ix)[D], uint32_t (&dl)[D]) {
+#define SXE_CX(a, b) sort_cx(f[a], ix[a], dl[a], f[b], ix[b], dl[b])
+  if constexpr (D == 2) {
+    SXE_CX(0, 1);
+  } else if constexpr (D == 3) {
+    SXE_CX(0, 1); SXE_CX(1, 2); SXE_CX(0, 1);
+  } else if constexpr (D == 4) {
+    SXE_CX(0, 1); SXE_CX(2, 3); SXE_CX(0, 2); SXE_CX(1, 3); SXE_CX(1, 2);
+  } else {
+    static_assert(D == 5, "d = 2..5");
+    SXE_CX(0, 1); SXE_CX(3, 4); SXE_CX(2, 4); SXE_CX(2, 3); SXE_CX(0, 3);
+    SXE_CX(0, 2); SXE_CX(1, 4); SXE_CX(1, 3); SXE_CX(1, 2);
+  }
+#undef SXE_CX
+}
+
 // ---------------------------------------------------------------------------
 // Simplex lattice of one point at one level.
 //   Sec. 5.1 + Eq. 2: p_i = x_i * s, sigma = sum_i p_i (left to right), t = F * sigma,
 //   q_i = p_i + t; each operation rounded once (no contraction).
-//   Sec. 4.2: c = floor(q), f = q - c (exact).  rank_i = number of axes j whose f_j is
-//   larger, or equal with j < i: the stable decreasing order of the paper's sort.
-//   Remark 2: vertex k = c + sum of e_i over axes with rank_i < k.
+//   Sec. 4.2: c = floor(q), f = q - c (exact); the fractional parts are sorted in decreasing
+//   order, ties lower axis first (a sorting network carrying the axis and its hash step).
+//   Remark 2: vertex k = c + the unit vectors of the first k sorted axes; its slot is the base
+//   vertex's hash updated by the hash steps of those axes.
 //   Sec. 4.3: w_0 = 1 - s_0, w_k = s_{k-1} - s_k, w_d = s_{d-1} on the sorted s.
 //   Sec. 5 (a): slot = XOR_i (uint32(v_i) * prime_i) mod T; on a directly indexed level
-//   (width B > 0) slot = (sum_i uint32(v_i) * B^i) mod T instead.
+//   (width B > 0) slot = (sum_i uint32(v_i) * B^i) mod T instead.  rank_i is the position of
+//   axis i in the sorted order.
 // ---------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, float skewF, uint32_t mask,
@@ -218,8 +249,9 @@ __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, fl
   for (int i = 1; i < D; ++i) sigma = __fadd_rn(sigma, p[i]);
   const float t = __fmul_rn(skewF, sigma);
   float f[D];
-  uint32_t h0[D], h1[D];
-  uint32_t pw = 1u;
+  int ix[D];
+  uint32_t dl[D];
+  uint32_t h = 0, pw = 1u;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     const float q = __fadd_rn(p[i], t);
@@ -229,38 +261,28 @@ __device__ __forceinline__ void simplex_lattice(const float (&x)[D], float s, fl
     const uint32_t c = (uint32_t)cell[i];
     const uint32_t mult = width ? pw : hash_prime(i);
     pw *= width;
-    h0[i] = c * mult;
-    h1[i] = (c + 1u) * mult;
+    const uint32_t h0 = c * mult;
+    h = width ? h + h0 : h ^ h0;
+    dl[i] = width ? mult : (h0 ^ (h0 + mult));          // hash step of moving +1 along axis i
+    ix[i] = i;
   }
+  sort_desc<D>(f, ix, dl);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     int r = 0;
 #pragma unroll
-    for (int j = 0; j < D; ++j)
-      if (j != i) r += (f[j] > f[i]) || (j < i && f[j] == f[i]);
+    for (int k = 0; k < D; ++k) r = ix[k] == i ? k : r;
     rank[i] = r;
   }
-  float srt[D];
+  w[0] = __fsub_rn(1.f, f[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) w[k] = __fsub_rn(f[k - 1], f[k]);
+  w[D] = f[D - 1];
+  slot[0] = h & mask;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    float v = 0.f;
-#pragma unroll
-    for (int i = 0; i < D; ++i) v = (rank[i] == k) ? f[i] : v;
-    srt[k] = v;
-  }
-  w[0] = __fsub_rn(1.f, srt[0]);
-#pragma unroll
-  for (int k = 1; k < D; ++k) w[k] = __fsub_rn(srt[k - 1], srt[k]);
-  w[D] = srt[D - 1];
-#pragma unroll
-  for (int k = 0; k <= D; ++k) {
-    uint32_t h = 0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const uint32_t v = (rank[i] < k) ? h1[i] : h0[i];
-      h = width ? h + v : h ^ v;
-    }
-    slot[k] = h & mask;
+    h = width ? h + dl[k] : h ^ dl[k];
+    slot[k + 1] = h & mask;
   }
 }
 
