@@ -61,6 +61,22 @@ def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's); world 1: x."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_rank_step: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job points/s: every rank's points over the slowest rank's time (weak scaling)."""
+    return points_per_rank_step * steps * world / (ms / 1e3)
+
+
 def _tensor_peak():
     """Dense fp16 tensor peak for a kernel timed inside a long step: the measured sustained
     bf16 figure (fp16 and bf16 run at the same dense rate)."""
@@ -232,10 +248,7 @@ def run_gpu(args):
     ms = start.elapsed_time(stop)
     per_kernel = {n: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)]))
                   for i, n in enumerate(names)}
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world, dev)
     loss = tr.loss()
     n_touched = count_touched(tr, xd[0])
 
@@ -258,10 +271,7 @@ def run_gpu(args):
     e2.record(stream)
     torch.cuda.synchronize(dev)
     ms_e2e = s2.elapsed_time(e2)
-    if world > 1:
-        tt = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_e2e = float(tt.item())
+    ms_e2e = max_over_ranks(ms_e2e, world, dev)
 
     # ---- comparators on the same GPU (encode forward + backward only, equal L, F, T)
     comparators = encode_sweep(dev) if (rank == 0 and not args.no_sweep) else None
@@ -270,7 +280,7 @@ def run_gpu(args):
     volume = volume_sweep(dev) if (rank == 0 and not args.no_volume) else None
 
     if rank == 0:
-        value = BATCH * args.steps * world / (ms / 1e3)
+        value = job_throughput(BATCH, args.steps, world, ms)
         work = _stage_work(n_touched)
         dom = max(work, key=lambda n: per_kernel[n])
         bound, amount = work[dom]
@@ -290,7 +300,7 @@ def run_gpu(args):
                        "points_per_step_per_gpu": BATCH, "parallelism": "replicas (one per GPU)",
                        "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state records, no flush",
                        "batches": "%d resident distinct batches cycled" % N_POOL},
-            "e2e": {"value": BATCH * e2e_steps * world / (ms_e2e / 1e3), "unit": "points/s",
+            "e2e": {"value": job_throughput(BATCH, e2e_steps, world, ms_e2e), "unit": "points/s",
                     "h2d_bytes_per_step": BATCH * (2 + N_OUT) * 4, "d2h_bytes_per_step": 4},
             "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                          "frac": achieved / peak, "traffic": _traffic(dom), "peak_source": peak_src,
