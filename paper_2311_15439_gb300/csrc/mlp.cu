@@ -72,6 +72,20 @@ __device__ __forceinline__ void ldsm_x2_trans(uint32_t& r0, uint32_t& r1, const 
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+
+// B fragments (k16 x n8) of n-tiles nt and nt+1 of a row-major [n][k] shared array (row stride
+// ld halves, rows 16-byte aligned) with one ldmatrix: r = {b0, b1} of nt, then of nt+1.
+template <typename T>
+__device__ __forceinline__ void bfrag_pair(const T* W, int ld, int nt, int kk, int lane, uint32_t (&r)[4]) {
+  const int m = lane >> 3;
+  ldsm_x4(r, W + ((nt + (m >> 1)) * 8 + (lane & 7)) * ld + kk * 16 + (m & 1) * 8);
+}
+
 // B fragment (k16 x n8) of a row-major [n][k] shared array with row stride `ld` (halves).
 template <typename T>
 __device__ __forceinline__ void bfrag(const T* W, int ld, int nt, int kk, int g, int t, uint32_t& b0, uint32_t& b1) {
@@ -145,35 +159,30 @@ __device__ __forceinline__ void forward_rows(T* sm, int r0, int g, int t, bool k
                                              uint32_t (&hfr)[NH][4][4]) {
   using S = Smem<N_IN, NH>;
   uint32_t afr[4][4];
-  // input fragments
+  const int lane = g * 4 + t;
+  // input fragments (one ldmatrix per 16 x 16 block)
 #pragma unroll
   for (int kk = 0; kk < N_IN / 16; ++kk) {
-    const T* base = sm + S::X + (r0 + g) * S::SX + kk * 16 + 2 * t;
-    afr[kk][0] = lds32(base);
-    afr[kk][1] = lds32(base + 8 * S::SX);
-    afr[kk][2] = lds32(base + 8);
-    afr[kk][3] = lds32(base + 8 * S::SX + 8);
+    const int m = lane >> 3;
+    ldsm_x4(afr[kk], sm + S::X + (r0 + (m & 1) * 8 + (lane & 7)) * S::SX + kk * 16 + (m >> 1) * 8);
   }
 #pragma unroll
   for (int h = 0; h < NH; ++h) {
     float acc[8][4];
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-      if (h == 0) {
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    const T* Wl = h == 0 ? sm + S::W0 : sm + S::WH + (h - 1) * kWidth * kSW;
+    const int ld = h == 0 ? S::SX : kSW;
+    const int nk = h == 0 ? N_IN / 16 : 4;
 #pragma unroll
-        for (int kk = 0; kk < N_IN / 16; ++kk) {
-          uint32_t b0, b1;
-          bfrag<T>(sm + S::W0, S::SX, nt, kk, g, t, b0, b1);
-          mma16816<T>(acc[nt], afr[kk], b0, b1);
-        }
-      } else {
+    for (int np = 0; np < 4; ++np) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          uint32_t b0, b1;
-          bfrag<T>(sm + S::WH + (h - 1) * kWidth * kSW, kSW, nt, kk, g, t, b0, b1);
-          mma16816<T>(acc[nt], afr[kk], b0, b1);
-        }
+      for (int kk = 0; kk < 4; ++kk) {
+        if (kk >= nk) break;
+        uint32_t b[4];
+        bfrag_pair<T>(Wl, ld, 2 * np, kk, lane, b);
+        mma16816<T>(acc[2 * np], afr[kk], b[0], b[1]);
+        mma16816<T>(acc[2 * np + 1], afr[kk], b[2], b[3]);
       }
     }
     // ReLU, round to the operand type; the rounded values are both the next layer's
@@ -196,14 +205,13 @@ __device__ __forceinline__ void forward_rows(T* sm, int r0, int g, int t, bool k
     }
   }
 #pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    y[nt][0] = y[nt][1] = y[nt][2] = y[nt][3] = 0.f;
+  for (int nt = 0; nt < 2; ++nt) y[nt][0] = y[nt][1] = y[nt][2] = y[nt][3] = 0.f;
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      uint32_t b0, b1;
-      bfrag<T>(sm + S::WO, kSW, nt, kk, g, t, b0, b1);
-      mma16816<T>(y[nt], afr[kk], b0, b1);
-    }
+  for (int kk = 0; kk < 4; ++kk) {
+    uint32_t b[4];
+    bfrag_pair<T>(sm + S::WO, kSW, 0, kk, lane, b);
+    mma16816<T>(y[0], afr[kk], b[0], b[1]);
+    mma16816<T>(y[1], afr[kk], b[2], b[3]);
   }
 }
 
