@@ -229,6 +229,7 @@ def run_gpu(args):
             x, t = xd[k % N_POOL], td[k % N_POOL]
             e = ev[k]
             tr.t += 1
+            tr.adam_tables.advance(tr.t_dev, tr.corrections)
             e[0].record(stream)
             tr.enc.encode_fwd(x, tr.tables, tr.enc_out)
             e[1].record(stream)
@@ -237,9 +238,9 @@ def run_gpu(args):
             e[2].record(stream)
             tr.enc.encode_bwd(x, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
             e[3].record(stream)
-            tr.adam_tables.step_touched(tr.t, tr.state, tr.touched, tr.tables, F)
+            tr.adam_tables.step_touched_dev(tr.corrections, tr.state, tr.touched, tr.tables, F)
             e[4].record(stream)
-            tr.adam_mlp.step(tr.t, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
+            tr.adam_mlp.step_dev(tr.corrections, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
             e[5].record(stream)
         stop.record(stream)
         torch.cuda.synchronize(dev)
@@ -252,11 +253,15 @@ def run_gpu(args):
     loss = tr.loss()
     n_touched = count_touched(tr, xd[0])
 
-    # ---- end to end through the public API: pinned host batch -> device, step, loss -> host
+    # ---- end to end through the public API: pinned host batch -> device, the step (recorded once
+    # into a CUDA graph, replayed), loss -> host
     hx = [torch.from_numpy(x).pin_memory() for x in xs]
     ht = [torch.from_numpy(t).pin_memory() for t in ts]
     bx = torch.empty_like(xd[0])
     bt = torch.empty_like(td[0])
+    bx.copy_(hx[0])
+    bt.copy_(ht[0])
+    tr.capture(bx, bt)
     e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -266,7 +271,7 @@ def run_gpu(args):
     for k in range(e2e_steps):
         bx.copy_(hx[k % N_POOL], non_blocking=True)
         bt.copy_(ht[k % N_POOL], non_blocking=True)
-        tr.step(bx, bt)
+        tr.replay()
         tr.loss()                                   # device -> host read of the step's loss
     e2.record(stream)
     torch.cuda.synchronize(dev)

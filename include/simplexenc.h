@@ -368,6 +368,20 @@ sxe_status sxe_step_touched(const sxe_adam_desc* desc, int64_t t, int64_t n_entr
                             int32_t n_features, float* state, uint32_t* touched,
                             void* table_lowp, int32_t lowp_dtype, void* stream);
 
+/* Step counter on the device, for training loops captured into a CUDA graph (where a host-side
+ * t would be frozen at capture): sxe_adam_advance increments t (int64, device) and writes the
+ * bias corrections of the new t, corrections[0] = 1/(1-beta1^t) and corrections[1] =
+ * 1/(1-beta2^t) (binary32, device; FP64 then rounded once, as the host form does); one thread,
+ * on `stream`.  sxe_step_dev and sxe_step_touched_dev are sxe_step and sxe_step_touched with
+ * the corrections read from that device array when the kernel runs. */
+sxe_status sxe_adam_advance(const sxe_adam_desc* desc, int64_t* t, float* corrections, void* stream);
+sxe_status sxe_step_dev(const sxe_adam_desc* desc, const float* corrections, int64_t n, float* param,
+                        float* m, float* v, float* grad, void* param_lowp, int32_t lowp_dtype,
+                        void* stream);
+sxe_status sxe_step_touched_dev(const sxe_adam_desc* desc, const float* corrections, int64_t n_entries,
+                                int32_t F, float* state, uint32_t* touched, void* table_lowp,
+                                int32_t lowp_dtype, void* stream);
+
 
 /* Which kernel runs the network's training pass (sxe_mlp_bwd, sxe_mlp_train_l2*),
  * process-wide: SXE_MLP_KERNEL_MMA_SYNC (warp-level mma.sync for every product) or

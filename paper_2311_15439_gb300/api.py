@@ -318,6 +318,45 @@ class Adam:
         L.check(L.lib().sxe_step(ctypes.byref(self.desc), int(t), n, _ptr(param), _ptr(m), _ptr(v), _ptr(grad),
                                  _ptr(lowp), ldt, _stream(stream)), "sxe_step")
 
+    def advance(self, t_dev: torch.Tensor, corrections: torch.Tensor, stream=None):
+        """Device step counter: t_dev += 1 (int64 [1]) and corrections = bias corrections (float32 [2])."""
+        _need(t_dev, torch.int64, "t", (1,))
+        _need(corrections, torch.float32, "corrections", (2,))
+        L.check(L.lib().sxe_adam_advance(ctypes.byref(self.desc), _ptr(t_dev), _ptr(corrections), _stream(stream)),
+                "sxe_adam_advance")
+
+    def step_dev(self, corrections, param, m, v, grad, lowp=None, stream=None):
+        """``step`` with the bias corrections read from device memory (``advance``)."""
+        n = param.numel()
+        _need(corrections, torch.float32, "corrections", (2,))
+        for x, nm in ((param, "param"), (m, "m"), (v, "v"), (grad, "grad")):
+            _need(x, torch.float32, nm)
+            if x.numel() != n:
+                raise ValueError("%s has %d elements, expected %d" % (nm, x.numel(), n))
+        ldt = L.SXE_F32
+        if lowp is not None:
+            ldt = {torch.float32: L.SXE_F32, torch.float16: L.SXE_F16, torch.bfloat16: L.SXE_BF16}[lowp.dtype]
+            if not lowp.is_cuda or not lowp.is_contiguous() or lowp.numel() != n:
+                raise ValueError("lowp must be a contiguous CUDA tensor with %d elements" % n)
+        L.check(L.lib().sxe_step_dev(ctypes.byref(self.desc), _ptr(corrections), n, _ptr(param), _ptr(m), _ptr(v),
+                                     _ptr(grad), _ptr(lowp), ldt, _stream(stream)), "sxe_step_dev")
+
+    def step_touched_dev(self, corrections, state, touched, table_lowp, n_features: int, stream=None):
+        """``step_touched`` with the bias corrections read from device memory (``advance``)."""
+        F = n_features
+        _need(corrections, torch.float32, "corrections", (2,))
+        _need(state, torch.float32, "state")
+        _need(touched, torch.int32, "touched")
+        n_entries = table_lowp.numel() // F
+        if state.numel() != 4 * F * n_entries or touched.numel() * 32 < n_entries:
+            raise ValueError("state / touched sizes do not match the table")
+        ldt = {torch.float32: L.SXE_F32, torch.float16: L.SXE_F16, torch.bfloat16: L.SXE_BF16}[table_lowp.dtype]
+        if not table_lowp.is_cuda or not table_lowp.is_contiguous():
+            raise ValueError("table_lowp must be a contiguous CUDA tensor")
+        L.check(L.lib().sxe_step_touched_dev(ctypes.byref(self.desc), _ptr(corrections), n_entries, F, _ptr(state),
+                                             _ptr(touched), _ptr(table_lowp), ldt, _stream(stream)),
+                "sxe_step_touched_dev")
+
     def step_touched(self, t: int, state, touched, table_lowp, n_features: int, stream=None):
         F = n_features
         _need(state, torch.float32, "state")

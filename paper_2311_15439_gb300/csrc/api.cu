@@ -425,4 +425,40 @@ sxe_status sxe_step_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries
   return launch_adam_touched(a, t, n_entries, F, state, touched, lowp, lowp_dtype, (cudaStream_t)stream);
 }
 
+sxe_status sxe_adam_advance(const sxe_adam_desc* a, int64_t* t, float* corrections, void* stream) {
+  sxe_status st = check_adam("adam_advance", a, 1);
+  if (st != SXE_OK) return st;
+  if (!t || !corrections || !aligned(t, 8) || !aligned(corrections, 4))
+    return set_error(SXE_EINVAL, "adam_advance: NULL or misaligned step counter or corrections");
+  return launch_adam_advance(a, t, corrections, (cudaStream_t)stream);
+}
+
+sxe_status sxe_step_dev(const sxe_adam_desc* a, const float* corrections, int64_t n, float* p, float* m, float* v,
+                        float* g, void* lowp, int32_t lowp_dtype, void* stream) {
+  if (!corrections || !aligned(corrections, 4)) return set_error(SXE_EINVAL, "step_dev: NULL or misaligned corrections");
+  sxe_status st = check_adam("step_dev", a, 1);
+  if (st != SXE_OK) return st;
+  if (n < 0) return set_error(SXE_EINVAL, "step_dev: n < 0");
+  if (n == 0) return SXE_OK;
+  if (!p || !m || !v || !g) return set_error(SXE_EINVAL, "step_dev: NULL buffer");
+  if (lowp && !valid_dtype(lowp_dtype)) return set_error(SXE_EINVAL, "step_dev: bad lowp dtype");
+  return launch_adam_dense(a, 1, n, p, m, v, g, lowp, lowp_dtype, (cudaStream_t)stream, corrections);
+}
+
+sxe_status sxe_step_touched_dev(const sxe_adam_desc* a, const float* corrections, int64_t n_entries, int32_t F,
+                                float* state, uint32_t* touched, void* lowp, int32_t lowp_dtype, void* stream) {
+  if (!corrections || !aligned(corrections, 4))
+    return set_error(SXE_EINVAL, "step_touched_dev: NULL or misaligned corrections");
+  sxe_status st = check_adam("step_touched_dev", a, 1);
+  if (st != SXE_OK) return st;
+  if (n_entries < 0) return set_error(SXE_EINVAL, "step_touched_dev: n_entries < 0");
+  if (!(F == 1 || F == 2 || F == 4 || F == 8)) return set_error(SXE_EINVAL, "step_touched_dev: F=%d", F);
+  if (n_entries == 0) return SXE_OK;
+  if (!state || !touched || !lowp) return set_error(SXE_EINVAL, "step_touched_dev: NULL state, touched or table");
+  if (!valid_dtype(lowp_dtype)) return set_error(SXE_EINVAL, "step_touched_dev: bad lowp dtype");
+  if (!aligned(state, 16) || !aligned(touched, 4) || !aligned(lowp, F == 2 ? 2 * dtype_size(lowp_dtype) : 1))
+    return set_error(SXE_EINVAL, "step_touched_dev: misaligned buffer");
+  return launch_adam_touched(a, 1, n_entries, F, state, touched, lowp, lowp_dtype, (cudaStream_t)stream, corrections);
+}
+
 }  // extern "C"

@@ -16,8 +16,9 @@
 namespace sxe {
 namespace {
 
-__global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p, float* __restrict__ m,
+__global__ void adam_dense_kernel(AdamConst kin, int64_t n, float* __restrict__ p, float* __restrict__ m,
                                   float* __restrict__ v, float* __restrict__ g, void* __restrict__ lowp, int ldt) {
+  const AdamConst k = adam_resolve(kin);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
     float pi = p[i];
@@ -38,8 +39,9 @@ __global__ void adam_dense_kernel(AdamConst k, int64_t n, float* __restrict__ p,
 // sparse the words are.  Each lane clears the word it loaded.
 template <int F>
 __global__ void __launch_bounds__(256, 4)
-adam_touched_kernel(AdamConst k, int64_t n_entries, float* __restrict__ state, uint32_t* __restrict__ touched,
+adam_touched_kernel(AdamConst kin, int64_t n_entries, float* __restrict__ state, uint32_t* __restrict__ touched,
                     void* __restrict__ lowp, int ldt) {
+  const AdamConst k = adam_resolve(kin);
   constexpr int NB = F <= 2 ? 4 : (F == 4 ? 2 : 1);
   __shared__ uint16_t list[8][1024];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -122,6 +124,14 @@ __global__ void loss_l2_kernel(const float* __restrict__ y, const float* __restr
   }
 }
 
+// One thread: the step count t += 1 and the bias corrections of the new t, in FP64 rounded once.
+__global__ void adam_advance_kernel(int64_t* __restrict__ t, float* __restrict__ c, float b1, float b2) {
+  const int64_t tn = *t + 1;
+  *t = tn;
+  c[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)tn)));
+  c[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)tn)));
+}
+
 unsigned blocks_for(int64_t n, int threads, unsigned cap) {
   const int64_t b = (n + threads - 1) / threads;
   return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
@@ -130,14 +140,17 @@ unsigned blocks_for(int64_t n, int threads, unsigned cap) {
 }  // namespace
 
 sxe_status launch_adam_dense(const sxe_adam_desc* a, int64_t t, int64_t n, float* p, float* m, float* v, float* g,
-                             void* lowp, int32_t ldt, cudaStream_t s) {
-  adam_dense_kernel<<<blocks_for(n, 256, 1u << 16), 256, 0, s>>>(make_adam_const(a, t), n, p, m, v, g, lowp, ldt);
+                             void* lowp, int32_t ldt, cudaStream_t s, const float* corrections) {
+  AdamConst k = make_adam_const(a, corrections ? 1 : t);
+  k.cdev = corrections;
+  adam_dense_kernel<<<blocks_for(n, 256, 1u << 16), 256, 0, s>>>(k, n, p, m, v, g, lowp, ldt);
   return check_launch("adam_dense");
 }
 
 sxe_status launch_adam_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries, int32_t F, float* state,
-                               uint32_t* touched, void* lowp, int32_t ldt, cudaStream_t s) {
-  const AdamConst k = make_adam_const(a, t);
+                               uint32_t* touched, void* lowp, int32_t ldt, cudaStream_t s, const float* corrections) {
+  AdamConst k = make_adam_const(a, corrections ? 1 : t);
+  k.cdev = corrections;
   // one warp per 32 bitmap words, at most 16 blocks of 8 warps per SM
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -158,6 +171,11 @@ sxe_status launch_loss_l2(const float* y, const float* target, int64_t P, int32_
   const int64_t n = P * n_out;
   loss_l2_kernel<<<blocks_for(n, 256, 4096), 256, 0, s>>>(y, target, n, (float)(2.0 / (double)n), dy, sq_sum);
   return check_launch("loss_l2");
+}
+
+sxe_status launch_adam_advance(const sxe_adam_desc* a, int64_t* t, float* corrections, cudaStream_t s) {
+  adam_advance_kernel<<<1, 1, 0, s>>>(t, corrections, a->beta1, a->beta2);
+  return check_launch("adam_advance");
 }
 
 }  // namespace sxe

@@ -50,6 +50,7 @@ sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, 
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
                              float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s);
 int encode_bwd_launches(const sxe_encoder* enc, int64_t P);
+sxe_status launch_adam_advance(const sxe_adam_desc* a, int64_t* t, float* corrections, cudaStream_t s);
 sxe_status launch_encode_plain(const sxe_encoder* enc, bool backward, const float* x, int64_t P, const float* a,
                                float* b, cudaStream_t s);
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,
@@ -84,10 +85,12 @@ extern int g_mlp_kernel;
 sxe_status launch_loss_l2(const float* y, const float* target, int64_t P, int32_t n_out, float* dy,
                           float* sq_sum, cudaStream_t s);
 sxe_status launch_adam_dense(const sxe_adam_desc* a, int64_t t, int64_t n, float* p, float* m, float* v,
-                             float* g, void* lowp, int32_t lowp_dtype, cudaStream_t s);
+                             float* g, void* lowp, int32_t lowp_dtype, cudaStream_t s,
+                             const float* corrections = nullptr);
 sxe_status launch_adam_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entries, int32_t F,
                                float* state, uint32_t* touched, void* lowp, int32_t lowp_dtype,
-                               cudaStream_t s);
+                               cudaStream_t s,
+                               const float* corrections = nullptr);
 
 // ---------------------------------------------------------------------------
 // device helpers
@@ -162,7 +165,19 @@ __device__ __forceinline__ void atomic_add_entry(float* p, const float (&v)[F]) 
 struct AdamConst {
   float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
   int skip;
+  const float* cdev;              // if set: c1, c2 are read from device memory (cdev[0], cdev[1])
 };
+
+// The constants a kernel uses: the bias corrections from device memory where the step count
+// lives on the device (captured training loops), else the host-computed ones.
+__device__ __forceinline__ AdamConst adam_resolve(const AdamConst& k) {
+  AdamConst r = k;
+  if (k.cdev) {
+    r.c1 = __ldg(k.cdev);
+    r.c2 = __ldg(k.cdev + 1);
+  }
+  return r;
+}
 
 inline AdamConst make_adam_const(const sxe_adam_desc* a, int64_t t) {
   AdamConst k;
@@ -170,6 +185,7 @@ inline AdamConst make_adam_const(const sxe_adam_desc* a, int64_t t) {
   k.c1 = (float)(1.0 / (1.0 - pow((double)a->beta1, (double)t)));
   k.c2 = (float)(1.0 / (1.0 - pow((double)a->beta2, (double)t)));
   k.skip = a->skip_zero_grad;
+  k.cdev = nullptr;
   return k;
 }
 

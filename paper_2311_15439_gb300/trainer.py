@@ -13,6 +13,11 @@ kernels:
                            refreshing the low-precision tables;
 5. ``sxe_step``         -- Adam on the network weights, refreshing their low-precision copy.
 
+The step count lives on the device (``sxe_adam_advance`` increments it and writes the bias
+corrections that both Adam launches read), so a step has no host-side value that changes from
+one step to the next: ``capture`` records it once into a CUDA graph and ``replay`` reruns it
+with a single launch.
+
 Table state layout in HBM: one binary32 record {param[F], m[F], v[F], grad[F]} per entry
 (32 bytes for F = 2: one DRAM sector), entries ordered [level][slot]; a separate dense
 [L][T][F] low-precision copy is what the forward pass gathers from; a bitmap of L*T bits
@@ -63,24 +68,48 @@ class Trainer:
         self.adam_tables = Adam(lr, betas[0], betas[1], eps, skip_zero_grad=True)
         self.adam_mlp = Adam(lr, betas[0], betas[1], eps, skip_zero_grad=False)
         self.t = 0
+        self.t_dev = torch.zeros((1,), dtype=torch.int64, device=self.device)
+        self.corrections = torch.zeros((2,), dtype=torch.float32, device=self.device)
+        self.graph = None
 
     @property
     def n_launches_per_step(self) -> int:
         # encode_fwd, network training + its partial reduction, encode_bwd (coarse levels in shared
         # memory, then the rest), table Adam, network Adam
-        return 5 + self.enc.bwd_kernel_count(self.P)
+        return 6 + self.enc.bwd_kernel_count(self.P)   # + the device step counter
 
     def step(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
         """One optimisation step on batch (x [P, d] float32, target [P, n_out] float32); asynchronous."""
         F = self.enc.n_features
         self.t += 1
+        self.adam_tables.advance(self.t_dev, self.corrections, stream=stream)
         self.enc.encode_fwd(x, self.tables, self.enc_out, stream=stream)
         self.mlp.mlp_train_l2(self.W_lowp, self.enc_out, target, self.dW, self.sq_sum, din=self.d_enc,
                               loss_scale=self.loss_scale, workspace=self.ws, stream=stream)
         self.enc.encode_bwd(x, self.d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F, touched=self.touched,
                             stream=stream)
-        self.adam_tables.step_touched(self.t, self.state, self.touched, self.tables, F, stream=stream)
-        self.adam_mlp.step(self.t, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=stream)
+        self.adam_tables.step_touched_dev(self.corrections, self.state, self.touched, self.tables, F, stream=stream)
+        self.adam_mlp.step_dev(self.corrections, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=stream)
+
+    def capture(self, x: torch.Tensor, target: torch.Tensor, warmup: int = 2) -> None:
+        """Record one step on the fixed input buffers x and target into a CUDA graph (after
+        ``warmup`` ordinary steps on them, which train like any other step)."""
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                self.step(x, target)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step(x, target)
+        self.t -= 1                      # recording did not run the step
+        self._graph_io = (x, target)
+
+    def replay(self) -> None:
+        """One step on the current contents of the buffers given to ``capture``."""
+        self.t += 1
+        self.graph.replay()
 
     def loss(self) -> float:
         """Mean squared error of the last step (synchronises)."""

@@ -260,3 +260,30 @@ def test_sdf_training_reduces_loss():
         if it in (0, 79):
             losses.append(tr.loss())
     assert np.isfinite(losses).all() and losses[1] < 0.5 * losses[0]
+
+
+def test_graph_replay_equals_eager_steps():
+    """A step recorded into a CUDA graph and replayed on new batch contents (the step count and
+    the Adam bias corrections advance on the device) gives the eager steps' parameters."""
+    P = 4096
+    a, b = _make(P, seed=11), _make(P, seed=11)
+    img = synth.ProceduralImage(3, size=1024, n_waves=4)
+    batches = []
+    for i in range(5):
+        x = synth.uniform_points(P, 2, 40 + i)
+        batches.append((torch.from_numpy(x).cuda(), torch.from_numpy(img.sample(x)).cuda()))
+    bx, bt = torch.empty_like(batches[0][0]), torch.empty_like(batches[0][1])
+    bx.copy_(batches[0][0]); bt.copy_(batches[0][1])
+    b.capture(bx, bt, warmup=2)                      # two eager steps on batch 0
+    a.step(*batches[0]); a.step(*batches[0])
+    for x, t in batches[1:]:
+        a.step(x, t)
+        bx.copy_(x); bt.copy_(t)
+        b.replay()
+    torch.cuda.synchronize()
+    assert a.t == b.t == 6 and int(b.t_dev.item()) == 6
+    # equal up to the order of the binary32 atomics of the table backward (which then feeds the
+    # next steps' encodings and network gradients)
+    torch.testing.assert_close(a.W, b.W, rtol=1e-3, atol=1e-5)
+    torch.testing.assert_close(a.state, b.state, rtol=1e-3, atol=1e-6)
+    assert a.loss() == pytest.approx(b.loss(), rel=1e-3)
