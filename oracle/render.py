@@ -22,7 +22,9 @@ taken here (NeRF's quadrature and Instant-NGP's field layout, the systems Sec. 6
 
 Parity pins (tests): the compositing equals the closed form of Eq. 5 for piecewise-constant
 media; the harmonics equal scipy's complex harmonics through the real-basis relation and are
-orthonormal on the sphere; every sample lies on its ray inside [t_near, t_far].
+orthonormal on the sphere; every sample lies on its ray inside [t_near, t_far].  The gradients
+(``composite_bwd``, ``render_l2_grads``) equal central differences of the forward functions and,
+for a homogeneous medium, the derivative of its closed form.
 """
 from __future__ import annotations
 
@@ -97,12 +99,66 @@ def composite(sigma, rgb, delta):
     return C, T, w
 
 
+def composite_bwd(sigma, rgb, delta, dC):
+    """Gradients of sum(dC * C) of ``composite`` with respect to sigma [R, S] and rgb [R, S, 3].
+
+    From Eq. 5's quadrature: sigma_k enters alpha_k (d alpha_k / d sigma_k = delta (1 - alpha_k)) and
+    every later transmittance (d T_i / d sigma_k = -delta T_i for i > k), so
+    dC/dsigma_k = delta (T_{k+1} c_k - sum_{i>k} w_i c_i) and dC/dc_k = w_k.  Written out per sample
+    with the suffix sums accumulated from the far end of the ray."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    rgb = np.asarray(rgb, dtype=np.float64)
+    delta = np.asarray(delta, dtype=np.float64)
+    dC = np.asarray(dC, dtype=np.float64)
+    R, S = sigma.shape
+    _, T, w = composite(sigma, rgb, delta)
+    Tk = np.ones((R, S + 1))                                  # T_0 .. T_S
+    for i in range(S):
+        Tk[:, i + 1] = Tk[:, i] * np.exp(-sigma[:, i] * delta)
+    dsigma = np.zeros((R, S))
+    suffix = np.zeros((R, 3))                                 # sum_{i>k} w_i c_i
+    for k in range(S - 1, -1, -1):
+        dsigma[:, k] = delta * np.einsum("rc,rc->r", dC, Tk[:, k + 1, None] * rgb[:, k] - suffix)
+        suffix += w[:, k, None] * rgb[:, k]
+    drgb = w[:, :, None] * dC[:, None, :]
+    return dsigma, drgb
+
+
 def density_from_logit(v):
     return np.exp(np.minimum(np.asarray(v, dtype=np.float64), DENSITY_LOGIT_MAX))
 
 
 def sigmoid(v):
     return 1.0 / (1.0 + np.exp(-np.asarray(v, dtype=np.float64)))
+
+
+def render_l2_grads(o, d, t_near, t_far, S, tables, W_density, W_color, target, *, kind, base_res, growth,
+                    index_mode=0):
+    """Loss mean((C - target)^2) over rays and channels of ``render`` and its gradients with respect to
+    the tables ({level: [T, F]}) and both networks' weights, by the chain rule through Eq. 5, the
+    sigmoid, the colour network, the field head (sigma = exp(min(v_0, 15)): d sigma / d v_0 = sigma
+    below the clamp, 0 above; the harmonics take no gradient), the density network and the encoding."""
+    C, _, it = render(o, d, t_near, t_far, S, tables, W_density, W_color, kind=kind, base_res=base_res,
+                      growth=growth, index_mode=index_mode)
+    R = C.shape[0]
+    target = np.asarray(target, dtype=np.float64)
+    loss = float(np.mean((C - target) ** 2))
+    dC = 2.0 * (C - target) / C.size
+    rgb = sigmoid(it["logits"])
+    dsigma, drgb = composite_bwd(it["sigma"].reshape(R, S), rgb.reshape(R, S, 3), it["delta"], dC)
+    dlogits = drgb.reshape(-1, 3) * rgb * (1.0 - rgb)
+    _, acts_c = mlp.mlp_forward(W_color, it["color_in"])
+    dWc, dcin = mlp.mlp_backward(W_color, acts_c, dlogits)
+    dv = dcin[:, :16].copy()
+    h0 = it["density_out"][:, 0]
+    dv[:, 0] += dsigma.reshape(-1) * np.where(h0 < DENSITY_LOGIT_MAX, it["sigma"], 0.0)
+    _, acts_d = mlp.mlp_forward(W_density, it["enc"])
+    dWd, denc = mlp.mlp_backward(W_density, acts_d, dv)
+    L, T, F = np.asarray(tables).shape
+    bwd = encoding.simplex_encode_bwd if kind == "simplex" else encoding.grid_encode_bwd
+    gt = bwd(it["x"], denc, n_levels=L, log2_T=int(T).bit_length() - 1, n_features=F, base_res=base_res,
+             growth=growth, index_mode=index_mode)
+    return loss, gt, dWd, dWc, dict(it, C=C, dC=dC, dsigma=dsigma, dlogits=dlogits, dv=dv, denc=denc)
 
 
 def render(o, d, t_near, t_far, S, tables, W_density, W_color, *, kind, base_res, growth, index_mode=0):

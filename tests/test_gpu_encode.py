@@ -24,6 +24,8 @@ CASES = [
     (2, 4, 1, 12, 8.0, 2.0, "f32", "f32", 4999),
     (3, 5, 4, 12, 8.0, 2.0, "f32", "bf16", 3001),
     (4, 3, 8, 10, 4.0, 1.5, "f32", "f32", 777),
+    (2, 32, 1, 12, 4.0, 1.2, "f32", "f32", 2000),        # the most levels (32), a power of two
+    (3, 20, 2, 13, 8.0, 1.15, "f16", "f16", 1500),       # levels not a power of two
 ]
 
 

@@ -109,3 +109,89 @@ def test_samples_lie_on_their_rays_in_order():
     proj = np.einsum("rsk,rk->rs", x - o[:, None, :], d.astype(np.float64))
     assert np.all(np.diff(proj, axis=1) > 0)
     assert np.all(proj > tn[:, None] - 1e-5) and np.all(proj < tf[:, None] + 1e-5)
+
+
+def test_composite_bwd_matches_central_differences():
+    g = synth.rng(20)
+    R, S = 4, 9
+    sigma = g.exponential(2.0, (R, S))
+    rgb = g.random((R, S, 3))
+    delta = g.uniform(0.05, 0.3, R)
+    dC = g.standard_normal((R, 3))
+    ds, dr = render.composite_bwd(sigma, rgb, delta, dC)
+    h = 1e-6
+    for r in range(R):
+        for k in range(S):
+            sp, sm = sigma.copy(), sigma.copy()
+            sp[r, k] += h
+            sm[r, k] -= h
+            fd = ((render.composite(sp, rgb, delta)[0] - render.composite(sm, rgb, delta)[0]) * dC).sum() / (2 * h)
+            assert abs(fd - ds[r, k]) <= 1e-8 * (1 + abs(fd))
+            for c in range(3):
+                rp, rm = rgb.copy(), rgb.copy()
+                rp[r, k, c] += h
+                rm[r, k, c] -= h
+                fd = ((render.composite(sigma, rp, delta)[0] - render.composite(sigma, rm, delta)[0]) * dC).sum() / (2 * h)
+                assert abs(fd - dr[r, k, c]) <= 1e-8 * (1 + abs(fd))
+
+
+def test_composite_bwd_homogeneous_closed_form():
+    """Raising the density of every sample of a homogeneous segment of length l: d/d sigma of
+    c (1 - exp(-sigma l)) = c l exp(-sigma l), the sum of the per-sample derivatives."""
+    R, S = 3, 40
+    sig = np.array([0.5, 3.0, 10.0])
+    length = np.array([0.7, 0.2, 1.3])
+    c = synth.rng(21).random((R, 3))
+    sigma = np.repeat(sig[:, None], S, axis=1)
+    ds, _ = render.composite_bwd(sigma, np.repeat(c[:, None, :], S, axis=1), length / S, np.ones((R, 3)))
+    want = c.sum(axis=1) * length * np.exp(-sig * length)
+    np.testing.assert_allclose(ds.sum(axis=1), want, rtol=1e-10)
+
+
+def test_render_l2_grads_match_central_differences():
+    """The chain rule of the render loss against central differences of the whole oracle render
+    (a few table entries and weights of each network, where two step sizes agree)."""
+    from oracle import mlp as OM
+    g = synth.rng(22)
+    R, S, L, log2_T = 6, 8, 3, 8
+    o, d, tn, tf = synth.camera_rays(R, 23)
+    tables = g.uniform(-1, 1, (L, 1 << log2_T, 2))
+    Wd = [g.standard_normal((64, 6)) * 0.4, g.standard_normal((16, 64)) * 0.2]
+    Wc = [g.standard_normal((64, 32)) * 0.3, g.standard_normal((64, 64)) * 0.2, g.standard_normal((3, 64)) * 0.2]
+    target = g.random((R, 3))
+    kw = dict(kind="simplex", base_res=4.0, growth=1.5)
+    loss, gt, dWd, dWc, _ = render.render_l2_grads(o, d, tn, tf, S, tables, Wd, Wc, target, **kw)
+
+    def L_of(tab=tables, wd=Wd, wc=Wc):
+        C, _, _ = render.render(o, d, tn, tf, S, tab, wd, wc, **kw)
+        return np.mean((C - target) ** 2)
+
+    checked = 0
+    for l in range(L):
+        nz = np.nonzero(np.abs(gt[l]).sum(axis=1))[0][:3]
+        for s in nz:
+            fds = []
+            for h in (1e-4, 1e-5):
+                tp, tm = tables.copy(), tables.copy()
+                tp[l, s, 0] += h
+                tm[l, s, 0] -= h
+                fds.append((L_of(tab=tp) - L_of(tab=tm)) / (2 * h))
+            if abs(fds[0] - fds[1]) <= 1e-6 * (abs(fds[1]) + 1e-9):
+                assert abs(fds[1] - gt[l][s, 0]) <= 1e-5 * (abs(fds[1]) + 1e-9)
+                checked += 1
+    for W, dW, name in ((Wd, dWd, "d"), (Wc, dWc, "c")):
+        for li in range(len(W)):
+            i, j = g.integers(W[li].shape[0]), g.integers(W[li].shape[1])
+            fds = []
+            for h in (1e-4, 1e-5):
+                Wp = [w.copy() for w in W]
+                Wm = [w.copy() for w in W]
+                Wp[li][i, j] += h
+                Wm[li][i, j] -= h
+                args_p = dict(wd=Wp) if name == "d" else dict(wc=Wp)
+                args_m = dict(wd=Wm) if name == "d" else dict(wc=Wm)
+                fds.append((L_of(**args_p) - L_of(**args_m)) / (2 * h))
+            if abs(fds[0] - fds[1]) <= 1e-6 * (abs(fds[1]) + 1e-9):
+                assert abs(fds[1] - dW[li][i, j]) <= 1e-5 * (abs(fds[1]) + 1e-9)
+                checked += 1
+    assert checked >= 8
