@@ -231,6 +231,26 @@ sxe_status sxe_vr_composite(const float* sigma, const float* rgb_logits, const f
 sxe_status sxe_probe_random_access(int32_t kind, float* buf, int64_t n_slots, int32_t slot_floats,
                                    int64_t n_ops, uint64_t seed, float* sink, void* stream);
 
+/* Backward of sxe_vr_composite for upstream colour gradients dcolor [n_rays][3]: with
+ * w_k = T_k alpha_k and P_k = sum_{i<=k} w_i c_i,
+ *   dsigma[k] = delta sum_c dcolor_c (T_{k+1} c_k,c - (color_c - P_k,c)),
+ *   dlogits[k][c] = dcolor_c w_k c_k,c (1 - c_k,c),
+ * (the derivative of Eq. 5's quadrature; the paper does not state it).  color [n_rays][3] is the
+ * forward pass's output; sigma, rgb_logits, delta as in sxe_vr_composite.  Writes dsigma
+ * [n_rays*S] and dlogits [n_rays*S][3] binary32.  One warp per ray. */
+sxe_status sxe_vr_composite_bwd(const float* sigma, const float* rgb_logits, const float* delta,
+                                const float* color, const float* dcolor, int64_t n_rays,
+                                int32_t n_samples, float* dsigma, float* dlogits, void* stream);
+
+/* Backward of sxe_vr_field: the gradient of the density network's 16 outputs,
+ *   dv[p][j] = dcolor_in[p][j] (j < 16) + (j == 0 and v_0 < 15 ? dsigma[p] sigma[p] : 0)
+ * from the colour network's input gradient dcolor_in [n_rays*S][32] (binary32, 16-byte aligned),
+ * dsigma, sigma [n_rays*S] and the forward density outputs density_out [n_rays*S][16]; the
+ * harmonics take no gradient.  dv [n_rays*S][16] binary32 (16-byte aligned), overwritten. */
+sxe_status sxe_vr_field_bwd(const float* dcolor_in, const float* dsigma, const float* sigma,
+                            const float* density_out, int64_t n_rays, int32_t n_samples, float* dv,
+                            void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Tiny fully connected network (Sec. 5 d-e; about 7k weights, Sec. 6.1).     */
 /* ------------------------------------------------------------------------ */

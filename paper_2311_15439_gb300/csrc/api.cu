@@ -206,6 +206,31 @@ sxe_status sxe_vr_field(const float* density_out, const float* dirs, int64_t R, 
   return launch_vr_field(density_out, dirs, R, S, dtype, sigma, color_in, (cudaStream_t)stream);
 }
 
+sxe_status sxe_vr_composite_bwd(const float* sigma, const float* rgb_logits, const float* delta, const float* color,
+                                const float* dcolor, int64_t R, int32_t S, float* dsigma, float* dlogits,
+                                void* stream) {
+  sxe_status st = check_rays("vr_composite_bwd", R, S);
+  if (st != SXE_OK || R == 0) return st;
+  if (!sigma || !rgb_logits || !delta || !color || !dcolor || !dsigma || !dlogits)
+    return set_error(SXE_EINVAL, "vr_composite_bwd: NULL buffer");
+  if (!aligned(sigma, 4) || !aligned(rgb_logits, 4) || !aligned(delta, 4) || !aligned(color, 4) ||
+      !aligned(dcolor, 4) || !aligned(dsigma, 4) || !aligned(dlogits, 4))
+    return set_error(SXE_EINVAL, "vr_composite_bwd: misaligned buffer");
+  return launch_vr_composite_bwd(sigma, rgb_logits, delta, color, dcolor, R, S, dsigma, dlogits,
+                                 (cudaStream_t)stream);
+}
+
+sxe_status sxe_vr_field_bwd(const float* dcolor_in, const float* dsigma, const float* sigma, const float* density_out,
+                            int64_t R, int32_t S, float* dv, void* stream) {
+  sxe_status st = check_rays("vr_field_bwd", R, S);
+  if (st != SXE_OK || R == 0) return st;
+  if (!dcolor_in || !dsigma || !sigma || !density_out || !dv) return set_error(SXE_EINVAL, "vr_field_bwd: NULL buffer");
+  if (!aligned(dcolor_in, 16) || !aligned(dv, 16) || !aligned(dsigma, 4) || !aligned(sigma, 4) ||
+      !aligned(density_out, 4))
+    return set_error(SXE_EINVAL, "vr_field_bwd: dcolor_in and dv must be 16-byte aligned");
+  return launch_vr_field_bwd(dcolor_in, dsigma, sigma, density_out, R * S, dv, (cudaStream_t)stream);
+}
+
 sxe_status sxe_vr_composite(const float* sigma, const float* rgb_logits, const float* delta, int64_t R, int32_t S,
                             float* color, float* transmittance, float* weights, void* stream) {
   sxe_status st = check_rays("vr_composite", R, S);

@@ -113,6 +113,95 @@ vr_composite_kernel(const float* __restrict__ sigma, const float* __restrict__ l
   }
 }
 
+// Backward of the compositing for upstream colour gradients dC [R][3], one warp per ray.
+// With w_k = T_k alpha_k and P_k = sum_{i<=k} w_i c_i (the colour accumulated up to sample k):
+//   dL/dsigma_k = delta sum_c dC_c (T_{k+1} c_k,c - (C_c - P_k,c)),
+//   dL/dlogit_k,c = dC_c w_k c_k,c (1 - c_k,c)  (1 - c taken as the sigmoid of -logit),
+// where T_{k+1} = T_k (1 - alpha_k) and C is the forward pass's colour.  The same prefix scans
+// as the forward pass, plus one of w c per channel.
+__global__ void __launch_bounds__(kThreads)
+vr_composite_bwd_kernel(const float* __restrict__ sigma, const float* __restrict__ logits,
+                        const float* __restrict__ delta, const float* __restrict__ color,
+                        const float* __restrict__ dcolor, int64_t R, int S, float* __restrict__ dsigma,
+                        float* __restrict__ dlogits) {
+  const int64_t r = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  if (r >= R) return;                                   // whole warps leave together
+  const int lane = threadIdx.x & 31;
+  const float dl = __ldg(delta + r);
+  float Cc[3], dC[3], pc[3] = {0.f, 0.f, 0.f};          // colour, its gradient, P_{k-1} carried
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Cc[c] = __ldg(color + r * 3 + c);
+    dC[c] = __ldg(dcolor + r * 3 + c);
+  }
+  float carry = 0.f;
+  for (int base = 0; base < S; base += 32) {
+    const int k = base + lane;
+    const int64_t i = r * S + k;
+    float s = 0.f, col[3] = {0.f, 0.f, 0.f}, ncol[3] = {0.f, 0.f, 0.f};
+    if (k < S) {
+      s = __ldg(sigma + i) * dl;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float x = __ldg(logits + i * 3 + c);
+        col[c] = 1.f / (1.f + expf(-x));
+        ncol[c] = 1.f / (1.f + expf(x));                // 1 - c without cancellation near c = 1
+      }
+    }
+    float incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.f;
+    const float w = expf(-(carry + excl)) * -expm1f(-s);
+    const float t_next = expf(-(carry + incl));         // T_{k+1}
+    float wc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      wc[c] = w * col[c];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_up_sync(0xffffffffu, wc[c], o);
+        if (lane >= o) wc[c] += t;
+      }
+    }
+    if (k < S) {
+      float g = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float Pk = pc[c] + wc[c];                 // P_k, inclusive
+        g = fmaf(dC[c], t_next * col[c] - (Cc[c] - Pk), g);
+        dlogits[i * 3 + c] = dC[c] * w * col[c] * ncol[c];
+      }
+      dsigma[i] = dl * g;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pc[c] += __shfl_sync(0xffffffffu, wc[c], 31);
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+// Gradient of the density network's 16 outputs: the colour network's input gradient of the
+// first 16 columns, plus dL/dsigma * sigma on output 0 below the clamp (sigma = exp(min(v_0, 15))).
+__global__ void __launch_bounds__(kThreads)
+vr_field_bwd_kernel(const float* __restrict__ dcin, const float* __restrict__ dsigma,
+                    const float* __restrict__ sigma, const float* __restrict__ dens, int64_t P,
+                    float* __restrict__ dv) {
+  const int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= P) return;
+  const float4* src = reinterpret_cast<const float4*>(dcin + p * 32);
+  float4* dst = reinterpret_cast<float4*>(dv + p * 16);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float4 a = __ldg(src + j);
+    if (j == 0 && __ldg(dens + p * 16) < 15.f) a.x = fmaf(__ldg(dsigma + p), __ldg(sigma + p), a.x);
+    dst[j] = a;
+  }
+}
+
 unsigned blocks(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 }  // namespace
@@ -138,6 +227,20 @@ sxe_status launch_vr_composite(const float* sigma, const float* logits, const fl
                                float* color, float* trans, float* weights, cudaStream_t s) {
   vr_composite_kernel<<<blocks(R, kThreads / 32), kThreads, 0, s>>>(sigma, logits, delta, R, S, color, trans, weights);
   return check_launch("vr_composite");
+}
+
+sxe_status launch_vr_composite_bwd(const float* sigma, const float* logits, const float* delta, const float* color,
+                                   const float* dcolor, int64_t R, int S, float* dsigma, float* dlogits,
+                                   cudaStream_t s) {
+  vr_composite_bwd_kernel<<<blocks(R, kThreads / 32), kThreads, 0, s>>>(sigma, logits, delta, color, dcolor, R, S,
+                                                                         dsigma, dlogits);
+  return check_launch("vr_composite_bwd");
+}
+
+sxe_status launch_vr_field_bwd(const float* dcin, const float* dsigma, const float* sigma, const float* dens,
+                               int64_t P, float* dv, cudaStream_t s) {
+  vr_field_bwd_kernel<<<blocks(P, kThreads), kThreads, 0, s>>>(dcin, dsigma, sigma, dens, P, dv);
+  return check_launch("vr_field_bwd");
 }
 
 }  // namespace sxe

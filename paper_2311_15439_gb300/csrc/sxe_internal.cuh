@@ -66,6 +66,11 @@ sxe_status launch_probe(int kind, float* buf, int64_t n_slots, int slot_floats, 
 sxe_status launch_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
                                const void* enc, const float* dirs, int64_t R, int S, float* sigma, float* logits,
                                cudaStream_t s);
+sxe_status launch_vr_composite_bwd(const float* sigma, const float* logits, const float* delta, const float* color,
+                                   const float* dcolor, int64_t R, int S, float* dsigma, float* dlogits,
+                                   cudaStream_t s);
+sxe_status launch_vr_field_bwd(const float* dcin, const float* dsigma, const float* sigma, const float* dens,
+                               int64_t P, float* dv, cudaStream_t s);
 sxe_status launch_vr_composite(const float* sigma, const float* logits, const float* delta, int64_t R, int S,
                                float* color, float* trans, float* weights, cudaStream_t s);
 

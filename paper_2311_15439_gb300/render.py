@@ -98,6 +98,92 @@ class Renderer:
         return 4 if self.fused else 6
 
 
+class VolumeTrainer:
+    """Trains a field (hash tables + density and colour networks) from ray colours (Sec. 6.2): one
+    ``step(rays, target)`` renders the rays, takes the mean squared colour error, back-propagates
+    it through the compositing (``sxe_vr_composite_bwd``), the colour network, the field head
+    (``sxe_vr_field_bwd``), the density network and the encoding, and takes Adam steps on the table
+    entries that received a gradient and on both networks.  Every step runs in the library's
+    kernels; the step count lives on the device."""
+
+    def __init__(self, encoder: Encoder, max_rays: int, n_samples: int, *, dtype: str = "f16", seed: int = 0,
+                 device="cuda", table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15):
+        from . import synth
+        from .api import Adam
+        from .trainer import default_loss_scale
+        self.enc, self.R, self.S = encoder, max_rays, n_samples
+        self.rr = Renderer(encoder, max_rays, n_samples, dtype=dtype, device=device, fused=False)
+        dev = self.rr.x.device
+        F, n_entries = encoder.n_features, encoder.n_levels * encoder.T
+        vals = synth.uniform_tables(encoder.n_levels, encoder.T, F, seed, dtype="f32", scale=table_init)[0]
+        init = torch.from_numpy(vals.reshape(n_entries, F)).to(dev)
+        self.state = torch.zeros((n_entries, 4 * F), dtype=torch.float32, device=dev)
+        self.state[:, :F] = init
+        self.tables = init.to(torch_dtype(encoder.table_dtype)).reshape(encoder.table_shape()).contiguous()
+        self.touched = torch.zeros(((n_entries + 31) // 32,), dtype=torch.int32, device=dev)
+        self.nets = []
+        for k, m in enumerate((self.rr.density, self.rr.color)):
+            W = torch.from_numpy(m.init_weights(seed + 1 + k)).to(dev)
+            self.nets.append(dict(mlp=m, W=W, W_lowp=W.to(torch_dtype(dtype)), m=torch.zeros_like(W),
+                                  v=torch.zeros_like(W), dW=torch.zeros_like(W), ws=m.workspace(max_rays * n_samples, dev)))
+        P = max_rays * n_samples
+        self.color = torch.empty((max_rays, 3), dtype=torch.float32, device=dev)
+        self.dcolor = torch.empty_like(self.color)
+        self.sq_sum = torch.zeros((1,), dtype=torch.float32, device=dev)
+        self.dsigma = torch.empty((P,), dtype=torch.float32, device=dev)
+        self.dlogits = torch.empty((P, 3), dtype=torch.float32, device=dev)
+        self.dcin = torch.empty((P, 32), dtype=torch.float32, device=dev)
+        self.dv = torch.empty((P, 16), dtype=torch.float32, device=dev)
+        self.denc = torch.empty((P, encoder.n_out), dtype=torch.float32, device=dev)
+        self.loss_scale = default_loss_scale(max_rays, 3)
+        self.adam_tables = Adam(lr, betas[0], betas[1], eps, skip_zero_grad=True)
+        self.adam_nets = Adam(lr, betas[0], betas[1], eps, skip_zero_grad=False)
+        self.t = 0
+        self.t_dev = torch.zeros((1,), dtype=torch.int64, device=dev)
+        self.corrections = torch.zeros((2,), dtype=torch.float32, device=dev)
+        self._n_rays = 0
+
+    def gradients(self, origins, dirs, t_near, t_far, target, stream=None) -> None:
+        """Forward render, loss and every gradient (table gradients in the state records' gradient
+        fields, touched entries marked; network gradients in nets[k]['dW'])."""
+        from .api import loss_l2
+        R, S, F = origins.shape[0], self.S, self.enc.n_features
+        P = R * S
+        rr, st = self.rr, _stream(stream)
+        dens, col = self.nets
+        rr.render(origins, dirs, t_near, t_far, self.tables, dens["W_lowp"], col["W_lowp"], color=self.color[:R],
+                  stream=stream)
+        self.sq_sum.zero_()
+        _need(target, torch.float32, "target", (R, 3))
+        loss_l2(self.color[:R], target, self.dcolor[:R], self.sq_sum, stream=stream)
+        L.check(L.lib().sxe_vr_composite_bwd(_ptr(rr.sigma), _ptr(rr.logits), _ptr(rr.delta), _ptr(self.color),
+                                             _ptr(self.dcolor), R, S, _ptr(self.dsigma), _ptr(self.dlogits), st),
+                "sxe_vr_composite_bwd")
+        col["mlp"].mlp_bwd(col["W_lowp"], rr.color_in[:P], self.dlogits[:P], col["dW"], din=self.dcin[:P],
+                           loss_scale=self.loss_scale, workspace=col["ws"], stream=stream)
+        L.check(L.lib().sxe_vr_field_bwd(_ptr(self.dcin), _ptr(self.dsigma), _ptr(rr.sigma), _ptr(rr.dens_out), R, S,
+                                         _ptr(self.dv), st), "sxe_vr_field_bwd")
+        dens["mlp"].mlp_bwd(dens["W_lowp"], rr.enc_out[:P], self.dv[:P], dens["dW"], din=self.denc[:P],
+                            loss_scale=self.loss_scale, workspace=dens["ws"], stream=stream)
+        self.enc.encode_bwd(rr.x[:P], self.denc[:P], self.state, grad_stride=4 * F, grad_offset=3 * F,
+                            touched=self.touched, stream=stream)
+        self._n_rays = R
+
+    def step(self, origins, dirs, t_near, t_far, target, stream=None) -> None:
+        """One optimisation step on a batch of rays and their target colours [R, 3]."""
+        self.t += 1
+        self.adam_tables.advance(self.t_dev, self.corrections, stream=stream)
+        self.gradients(origins, dirs, t_near, t_far, target, stream=stream)
+        self.adam_tables.step_touched_dev(self.corrections, self.state, self.touched, self.tables,
+                                          self.enc.n_features, stream=stream)
+        for n in self.nets:
+            self.adam_nets.step_dev(self.corrections, n["W"], n["m"], n["v"], n["dW"], lowp=n["W_lowp"], stream=stream)
+
+    def loss(self) -> float:
+        """Mean squared colour error of the last step (synchronises)."""
+        return float(self.sq_sum.item()) / (self._n_rays * 3)
+
+
 def vr_samples(origins, dirs, t_near, t_far, n_samples: int, stream=None):
     """``sxe_vr_samples`` alone: (x [R*S, 3], delta [R])."""
     R = origins.shape[0]

@@ -19,6 +19,9 @@ Workload recipes (shapes and distributions of the paper's tasks, Sec. 6):
 * ``camera_rays``      -- rays from a sphere of radius 1.2 around the unit cube's centre
   towards random targets inside the cube, with the entry and exit distances of the
   cube [0,1]^3 (the volumetric workload of Sec. 6.2).
+* ``BlobScene``        -- a volumetric scene: density a seeded sum of Gaussian blobs inside
+  the unit cube, colour a smooth function of position (the training target of Sec. 6.2's
+  setting: ray colours rendered from it).
 * ``ProceduralImage``  -- an RGB image defined analytically as a seeded sum of
   sinusoids plus bilinear value noise on a coarse lattice; it stands in for the
   gigapixel photograph of Sec. 6.1, which is not available here.
@@ -168,6 +171,27 @@ def camera_rays(R: int, seed: int):
     tn = np.maximum(np.minimum(t0, t1).max(axis=1), 0.0)
     tf = np.maximum(t0, t1).min(axis=1)
     return (o.astype(np.float32), d.astype(np.float32), tn.astype(np.float32), tf.astype(np.float32))
+
+
+class BlobScene:
+    """Density sigma(x) = sum_k a_k exp(-|x - m_k|^2 / (2 s_k^2)) over seeded blobs (centres in
+    [0.3, 0.7]^3, widths 0.03..0.1, peaks 20..80) and colour c(x) = 0.5 + 0.5 sin(omega x + phi)
+    per channel; ``field(x)`` returns (sigma [P], rgb [P, 3]) in FP64."""
+
+    def __init__(self, seed: int, n_blobs: int = 12):
+        g = rng(seed)
+        self.m = g.uniform(0.3, 0.7, size=(n_blobs, 3))
+        self.s = g.uniform(0.03, 0.1, size=n_blobs)
+        self.a = g.uniform(20.0, 80.0, size=n_blobs)
+        self.omega = g.uniform(2.0, 8.0, size=(3, 3))
+        self.phi = g.uniform(0.0, 2 * np.pi, size=3)
+
+    def field(self, x: np.ndarray):
+        x = np.asarray(x, dtype=np.float64)
+        d2 = ((x[:, None, :] - self.m[None, :, :]) ** 2).sum(axis=2)
+        sigma = (self.a[None, :] * np.exp(-d2 / (2.0 * self.s[None, :] ** 2))).sum(axis=1)
+        rgb = 0.5 + 0.5 * np.sin(x @ self.omega.T + self.phi[None, :])
+        return sigma, rgb
 
 
 class ProceduralImage:
