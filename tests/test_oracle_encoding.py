@@ -238,6 +238,7 @@ def test_adam_matches_library_and_skips_zero_grads():
         zero = gr == 0
         assert np.array_equal(th_new[zero], th[zero]) and np.array_equal(m_new[zero], m[zero])
         th, m, v = th_new, m_new, v_new
+    th_skip = th
     # without skipping, every entry follows torch.optim.Adam exactly
     p = torch.tensor(theta.copy(), requires_grad=True)
     opt = torch.optim.Adam([p], lr=hp["lr"], betas=(hp["beta1"], hp["beta2"]), eps=hp["eps"])
@@ -247,6 +248,10 @@ def test_adam_matches_library_and_skips_zero_grads():
         opt.step()
         th, m, v = adam.adam_step(th, gr, m, v, t, skip_zero_grad=False, **hp)
     np.testing.assert_allclose(th, p.detach().numpy(), rtol=1e-12, atol=1e-12)
+    # with skipping, entries that had a gradient at every step took every step: the same values
+    always = np.all([gr != 0 for gr in grads], axis=0)
+    assert always.sum() > 100
+    np.testing.assert_allclose(th_skip[always], p.detach().numpy()[always], rtol=1e-12, atol=1e-12)
 
 
 # --------------------------------------------------------------------------
@@ -381,6 +386,10 @@ def test_dense_levels_are_exactly_those_that_fit():
     assert w == [N + 2 if (N + 2) ** 2 <= (1 << log2_T) else 0 for N in Ns]
     assert w[:4] == [18, 34, 66, 130] and w[4:] == [0] * 4          # 258^2 > 2^16
     assert lattice.level_box_widths("simplex", n, scales, log2_T, lattice.INDEX_HASH) == [0] * L
+    # at the boundary: a grid level of resolution 254 needs a box of 256 = 2^8 coordinates, whose
+    # 2^16 vertices exactly fill a table of 2^16 entries (stored directly); resolution 255 does not fit
+    dense = lattice.INDEX_DENSE_COARSE
+    assert lattice.level_box_widths("grid", 2, [np.float32(254), np.float32(255)], 16, dense) == [256, 0]
 
 
 @pytest.mark.parametrize("kind,n", [("simplex", 2), ("simplex", 3), ("grid", 2), ("grid", 3)])

@@ -84,6 +84,14 @@ def test_theoretical_memory_usage_figure():
         assert 100.0 / geometry.parallelepiped_volume(n) == pytest.approx(float(pct), abs=6e-5)
 
 
+def test_equal_memory_factor_keeps_touched_volume():
+    """Sec. 5.2: scaling every level by m = (n+1)^((n-1)/(2n)) makes the touched simplex lattice of
+    the unit cube, (m N)^n / V vertices with V the parallelepiped volume, as large as the grid's N^n:
+    m^n equals V = |det(unskew(S_n I))| computed from the skew matrices."""
+    for n in range(2, 8):
+        assert lattice.equal_memory_factor(n) ** n == pytest.approx(geometry.parallelepiped_volume(n), rel=1e-12)
+
+
 @pytest.mark.parametrize("n", range(2, 8))
 def test_weights_reconstruct_point(n):
     """Theorem 1 / Sec. 4.3: weights are >= 0, sum to 1 and reproduce the skewed point."""
@@ -212,6 +220,15 @@ def test_hash_special_cases():
             assert np.array_equal(lattice.hash_slot(v, T), a % (1 << T))
             v[:, 0] = -1
             assert np.all(lattice.hash_slot(v, T) == (1 << T) - 1)
+        # the published multipliers: a unit vertex e_i lands in slot pi_i mod T; the axes combine by
+        # XOR, so (1, 1) lands in pi_2 XOR 1 = pi_2 - 1 (pi_2 odd) and (2, 3) in (3 pi_2 mod 2^32) XOR 2
+        # = 3668339987 XOR 2 = 3668339985 (its two low bits are 11); all mod T = 2^19 here
+        e = np.eye(n, dtype=np.int64)
+        assert lattice.hash_slot(e, 19).tolist() == [p % (1 << 19) for p in (1, 2654435761, 805459861,
+                                                                             1013904263, 2773480771)[:n]]
+        pair = np.zeros((2, n), dtype=np.int64)
+        pair[0, :2], pair[1, :2] = (1, 1), (2, 3)
+        assert lattice.hash_slot(pair, 19).tolist() == [489904, 421137]
         big = synth.rng(n).integers(-2**31, 2**31 - 1, size=(1000, n))
         s = lattice.hash_slot(big, 19)
         assert s.min() >= 0 and s.max() < (1 << 19)
