@@ -141,11 +141,26 @@ sxe_status sxe_encode_bwd(const sxe_encoder* enc, const float* x, int64_t n_poin
                           const float* dout, float* grad, int64_t grad_stride,
                           uint32_t* touched, void* stream);
 
+/* sxe_encode_bwd restricted to the levels [level_begin, level_end) (0 <= level_begin <=
+ * level_end <= L; an empty range does nothing): only the terms of those levels are added and
+ * only their entries are marked in `touched`.  Entries of different levels never share a
+ * gradient address or a bitmap word when T >= 32, so a caller can run the optimiser on the
+ * entries of one range (see sxe_step_touched on a sub-range of the state) while the backward
+ * of another range runs on a second stream.  Same arguments and errors as sxe_encode_bwd,
+ * plus SXE_EINVAL for a range outside [0, L]. */
+sxe_status sxe_encode_bwd_levels(const sxe_encoder* enc, const float* x, int64_t n_points,
+                                 const float* dout, float* grad, int64_t grad_stride,
+                                 uint32_t* touched, int32_t level_begin, int32_t level_end,
+                                 void* stream);
+
 /* Number of kernels sxe_encode_bwd launches for n_points (1 or 2; 0 for none): levels
  * whose lattice box is small are first summed per thread block in shared memory and
  * added to the table once per block (many contributions per vertex would otherwise
  * serialise on the same addresses); the other levels take the direct path. */
 int32_t sxe_encode_bwd_kernel_count(const sxe_encoder* enc, int64_t n_points);
+/* The same for sxe_encode_bwd_levels on [level_begin, level_end) (0 for an empty or invalid range). */
+int32_t sxe_encode_bwd_levels_kernel_count(const sxe_encoder* enc, int64_t n_points, int32_t level_begin,
+                                           int32_t level_end);
 
 /* Gradient with respect to the points (the chain rule through Sec. 4.3's weights, Eq. 2's
  * skew and the level scale; the paper does not state it):

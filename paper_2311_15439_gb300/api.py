@@ -109,9 +109,11 @@ class Encoder:
         return out
 
     def encode_bwd(self, x: torch.Tensor, dout: torch.Tensor, grad: torch.Tensor, grad_stride: int | None = None,
-                   touched: torch.Tensor | None = None, grad_offset: int = 0, stream=None):
+                   touched: torch.Tensor | None = None, grad_offset: int = 0, levels: tuple[int, int] | None = None,
+                   stream=None):
         """grad += d(out)/d(tables)^T dout.  ``grad`` is a float32 tensor; entry (l, slot) starts at
-        float ``grad_offset + (l*T + slot) * grad_stride`` (default stride F: a dense [L, T, F] array)."""
+        float ``grad_offset + (l*T + slot) * grad_stride`` (default stride F: a dense [L, T, F] array).
+        ``levels = (begin, end)`` restricts the terms to those levels (``sxe_encode_bwd_levels``)."""
         P = x.shape[0]
         _need(x, torch.float32, "x", (P, self.d))
         _need(dout, torch.float32, "dout", (P, self.n_out))
@@ -124,13 +126,20 @@ class Encoder:
             if touched.numel() * 32 < self.n_levels * self.T:
                 raise ValueError("touched bitmap too small")
         gp = grad.data_ptr() + 4 * grad_offset
-        L.check(L.lib().sxe_encode_bwd(self._h, _ptr(x), P, _ptr(dout), gp, stride, _ptr(touched), _stream(stream)),
-                "sxe_encode_bwd")
+        if levels is None:
+            L.check(L.lib().sxe_encode_bwd(self._h, _ptr(x), P, _ptr(dout), gp, stride, _ptr(touched),
+                                           _stream(stream)), "sxe_encode_bwd")
+        else:
+            L.check(L.lib().sxe_encode_bwd_levels(self._h, _ptr(x), P, _ptr(dout), gp, stride, _ptr(touched),
+                                                  int(levels[0]), int(levels[1]), _stream(stream)),
+                    "sxe_encode_bwd_levels")
         return grad
 
-    def bwd_kernel_count(self, n_points: int) -> int:
-        """Kernels one ``encode_bwd`` call launches for this many points (1 or 2)."""
-        return int(L.lib().sxe_encode_bwd_kernel_count(self._h, n_points))
+    def bwd_kernel_count(self, n_points: int, levels: tuple[int, int] | None = None) -> int:
+        """Kernels one ``encode_bwd`` call launches for this many points (0, 1 or 2)."""
+        if levels is None:
+            return int(L.lib().sxe_encode_bwd_kernel_count(self._h, n_points))
+        return int(L.lib().sxe_encode_bwd_levels_kernel_count(self._h, n_points, int(levels[0]), int(levels[1])))
 
     def encode_bwd_input(self, x: torch.Tensor, tables: torch.Tensor, dout: torch.Tensor,
                          dx: torch.Tensor | None = None, stream=None):

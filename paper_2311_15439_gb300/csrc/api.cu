@@ -144,6 +144,13 @@ sxe_status sxe_encode_fwd(const sxe_encoder* e, const float* x, int64_t P, const
 
 sxe_status sxe_encode_bwd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* grad,
                           int64_t grad_stride, uint32_t* touched, void* stream) {
+  if (!e) return set_error(SXE_EINVAL, "encode_bwd: NULL encoder");
+  return sxe_encode_bwd_levels(e, x, P, dout, grad, grad_stride, touched, 0, e->desc.n_levels, stream);
+}
+
+sxe_status sxe_encode_bwd_levels(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* grad,
+                                 int64_t grad_stride, uint32_t* touched, int32_t level_begin, int32_t level_end,
+                                 void* stream) {
   sxe_status st = check_points("encode_bwd", e, x, P);
   if (st != SXE_OK) return st;
   if (P == 0) return SXE_OK;
@@ -156,12 +163,21 @@ sxe_status sxe_encode_bwd(const sxe_encoder* e, const float* x, int64_t P, const
     return set_error(SXE_EINVAL, "encode_bwd: gradient entries must be %zu-byte aligned", ga);
   if (!aligned(dout, F == 2 ? 8 : 4)) return set_error(SXE_EINVAL, "encode_bwd: dout misaligned");
   if (touched && !aligned(touched, 4)) return set_error(SXE_EINVAL, "encode_bwd: touched misaligned");
-  return launch_encode_bwd(e, x, P, dout, grad, grad_stride, touched, (cudaStream_t)stream);
+  if (level_begin < 0 || level_end > e->desc.n_levels || level_begin > level_end)
+    return set_error(SXE_EINVAL, "encode_bwd: level range [%d, %d) outside [0, %d)", level_begin, level_end,
+                     e->desc.n_levels);
+  if (level_begin == level_end) return SXE_OK;
+  return launch_encode_bwd(e, x, P, dout, grad, grad_stride, touched, (cudaStream_t)stream, level_begin, level_end);
 }
 
 int32_t sxe_encode_bwd_kernel_count(const sxe_encoder* e, int64_t P) {
   if (!e || P <= 0) return 0;
   return encode_bwd_launches(e, P);
+}
+
+int32_t sxe_encode_bwd_levels_kernel_count(const sxe_encoder* e, int64_t P, int32_t level_begin, int32_t level_end) {
+  if (!e || P <= 0 || level_begin < 0 || level_end > e->desc.n_levels || level_begin >= level_end) return 0;
+  return encode_bwd_launches(e, P, level_begin, level_end);
 }
 
 sxe_status sxe_encode_bwd_input(const sxe_encoder* e, const float* x, int64_t P, const void* tables,

@@ -162,7 +162,8 @@ constexpr int kMaxCoarse = 4;
 constexpr int kCoarseSmem = 48 * 1024;
 
 struct CoarsePlan {
-  int n;                                    // coarse levels 0..n-1
+  int first;                                // level of plan entry 0
+  int n;                                    // coarse levels first..first+n-1
   int start[kMaxCoarse + 1];                // CTAs of level c: [start[c], start[c+1])
   uint32_t box[kMaxCoarse];                 // box width B of level c
   int smem;                                 // dynamic shared memory bytes
@@ -175,9 +176,10 @@ encode_bwd_coarse_kernel(const float* __restrict__ x, int64_t P, const float* __
                          const EncParams prm, const CoarsePlan plan) {
   constexpr int V = Verts<SIMPLEX, D>::V;
   extern __shared__ float s_acc[];
-  int c = 0;
+  int c = 0;                                            // plan entry; its level is plan.first + c
   while (c + 1 < plan.n && (int)blockIdx.x >= plan.start[c + 1]) ++c;
   const uint32_t B = c == 0 ? plan.box[0] : c == 1 ? plan.box[1] : c == 2 ? plan.box[2] : plan.box[3];
+  const int lev = plan.first + c;
   uint32_t cells = 1;
 #pragma unroll
   for (int i = 0; i < D; ++i) cells *= B;
@@ -190,12 +192,12 @@ encode_bwd_coarse_kernel(const float* __restrict__ x, int64_t P, const float* __
   const int k = (int)blockIdx.x - plan.start[c];
   const int64_t p0 = P * k / K, p1 = P * (k + 1) / K;
   const uint32_t mask = (1u << prm.log2_T) - 1u;
-  const uint32_t width = prm.width[c];
-  const float s = prm.scale[c];
-  const int64_t lbase = (int64_t)c << prm.log2_T;
+  const uint32_t width = prm.width[lev];
+  const float s = prm.scale[lev];
+  const int64_t lbase = (int64_t)lev << prm.log2_T;
   for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) {
     float g[F];
-    const float* pd = dout + (p * L + c) * F;
+    const float* pd = dout + (p * L + lev) * F;
 #pragma unroll
     for (int f = 0; f < F; ++f) g[f] = __ldg(pd + f);
     float xv[D];
@@ -484,42 +486,58 @@ CoarsePlan coarse_plan(const sxe_encoder* e, int64_t P) {
   return plan;
 }
 
+// The part of the plan inside levels [lb, le): its coarse levels, renumbered from lb.
+CoarsePlan slice_plan(const CoarsePlan& full, int lb, int le) {
+  CoarsePlan plan{};
+  plan.first = lb;
+  const int c1 = std::min(full.n, le);
+  for (int c = lb; c < c1; ++c) {
+    plan.box[c - lb] = full.box[c];
+    plan.start[c - lb + 1] = full.start[c + 1] - full.start[lb];
+    plan.n = c - lb + 1;
+  }
+  plan.smem = plan.n > 0 ? full.smem : 0;
+  return plan;
+}
+
 template <bool SIMPLEX, int D, int F>
 sxe_status bwd_f(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                 uint32_t* touched, cudaStream_t s) {
-  const CoarsePlan plan = coarse_plan(e, P);
+                 uint32_t* touched, cudaStream_t s, int lb, int le) {
+  const CoarsePlan full = coarse_plan(e, P);
+  const CoarsePlan plan = slice_plan(full, lb, le);
   if (plan.n > 0) {
     encode_bwd_coarse_kernel<SIMPLEX, D, F><<<plan.start[plan.n], kThreads, plan.smem, s>>>(
         x, P, dout, g, stride, touched, e->prm, plan);
     sxe_status st = check_launch("encode_bwd_coarse");
     if (st != SXE_OK) return st;
   }
-  const int nl = e->prm.n_levels - plan.n;
-  if (nl == 0) return SXE_OK;
+  const int l0 = std::max(lb, full.n);
+  const int nl = le - l0;
+  if (nl <= 0) return SXE_OK;
   encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, nl), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm,
-                                                                       plan.n, nl);
+                                                                       l0, nl);
   return check_launch("encode_bwd");
 }
 
 template <bool SIMPLEX, int D>
 sxe_status bwd_fd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                  uint32_t* t, cudaStream_t s) {
+                  uint32_t* t, cudaStream_t s, int lb, int le) {
   switch (e->desc.n_features) {
-    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, s);
-    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, s);
-    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, s);
-    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, s);
+    case 1: return bwd_f<SIMPLEX, D, 1>(e, x, P, dout, g, stride, t, s, lb, le);
+    case 2: return bwd_f<SIMPLEX, D, 2>(e, x, P, dout, g, stride, t, s, lb, le);
+    case 4: return bwd_f<SIMPLEX, D, 4>(e, x, P, dout, g, stride, t, s, lb, le);
+    default: return bwd_f<SIMPLEX, D, 8>(e, x, P, dout, g, stride, t, s, lb, le);
   }
 }
 
 template <bool SIMPLEX>
 sxe_status bwd_d(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* g, int64_t stride,
-                 uint32_t* t, cudaStream_t s) {
+                 uint32_t* t, cudaStream_t s, int lb, int le) {
   switch (e->desc.d) {
-    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, s);
-    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, s);
-    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, s);
-    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, s);
+    case 2: return bwd_fd<SIMPLEX, 2>(e, x, P, dout, g, stride, t, s, lb, le);
+    case 3: return bwd_fd<SIMPLEX, 3>(e, x, P, dout, g, stride, t, s, lb, le);
+    case 4: return bwd_fd<SIMPLEX, 4>(e, x, P, dout, g, stride, t, s, lb, le);
+    default: return bwd_fd<SIMPLEX, 5>(e, x, P, dout, g, stride, t, s, lb, le);
   }
 }
 
@@ -545,14 +563,18 @@ sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, 
 }
 
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout, float* grad,
-                             int64_t stride, uint32_t* touched, cudaStream_t s) {
-  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, s)
-                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, s);
+                             int64_t stride, uint32_t* touched, cudaStream_t s, int level_begin, int level_end) {
+  if (level_end < 0) level_end = enc->prm.n_levels;
+  return enc->desc.kind == SXE_SIMPLEX ? bwd_d<true>(enc, x, P, dout, grad, stride, touched, s, level_begin, level_end)
+                                       : bwd_d<false>(enc, x, P, dout, grad, stride, touched, s, level_begin, level_end);
 }
 
-int encode_bwd_launches(const sxe_encoder* enc, int64_t P) {
-  const CoarsePlan plan = coarse_plan(enc, P);
-  return (plan.n > 0 ? 1 : 0) + (plan.n < enc->prm.n_levels ? 1 : 0);
+int encode_bwd_launches(const sxe_encoder* enc, int64_t P, int level_begin, int level_end) {
+  if (level_end < 0) level_end = enc->prm.n_levels;
+  if (P == 0 || level_begin >= level_end) return 0;
+  const CoarsePlan full = coarse_plan(enc, P);
+  const CoarsePlan plan = slice_plan(full, level_begin, level_end);
+  return (plan.n > 0 ? 1 : 0) + (std::max(level_begin, full.n) < level_end ? 1 : 0);
 }
 
 sxe_status launch_encode_vertices(const sxe_encoder* enc, const float* x, int64_t P, uint32_t* slots,

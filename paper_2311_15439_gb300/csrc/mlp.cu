@@ -132,11 +132,13 @@ __device__ void load_weights(const T* __restrict__ W, int n_out, T* sm) {
   }
 }
 
-// B fragment (k16 x n8) of a row-major [k][n] shared array (n contiguous), via ldmatrix.trans.
-__device__ __forceinline__ void bfrag_kn(const void* base, int ld_halves, int kk, int nt, int lane,
-                                         uint32_t& b0, uint32_t& b1) {
+// B fragments of n-tiles nt and nt+1 of a row-major [k][n] shared array with one ldmatrix.trans:
+// r = {b0, b1} of nt, then of nt+1 (lanes 16..31 address the second pair).
+__device__ __forceinline__ void bfrag_kn_pair(const void* base, int ld_halves, int kk, int nt, int lane,
+                                              uint32_t (&r)[4]) {
   const int q = lane >> 3, rr = lane & 7;
-  ldsm_x2_trans(b0, b1, reinterpret_cast<const __half*>(base) + (kk * 16 + (q & 1) * 8 + rr) * ld_halves + nt * 8);
+  ldsm_x4_trans(r, reinterpret_cast<const __half*>(base) + (kk * 16 + (q & 1) * 8 + rr) * ld_halves +
+                       (nt + (q >> 1)) * 8);
 }
 
 // Stage the tile's inputs [128][N_IN] into shared memory (zero rows past P).
@@ -394,18 +396,21 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
     for (int h = NH - 1; h >= 0; --h) {
       float acc[8][4];
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+      for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+      for (int np = 0; np < 8; np += 2) {
         if (h == NH - 1) {          // dY W_out: B[k = o][n = j] = W_out[o][j]
-          uint32_t b0, b1;
-          bfrag_kn(sm + S::WO, kSW, 0, nt, lane, b0, b1);
-          mma16816<T>(acc[nt], afr[0], b0, b1);
+          uint32_t b[4];
+          bfrag_kn_pair(sm + S::WO, kSW, 0, np, lane, b);
+          mma16816<T>(acc[np], afr[0], b[0], b[1]);
+          mma16816<T>(acc[np + 1], afr[0], b[2], b[3]);
         } else {                    // dH_{h+1} W_{h+1}: B[k = j][n = j'] = W_{h+1}[j][j']
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            uint32_t b0, b1;
-            bfrag_kn(sm + S::WH + h * kWidth * kSW, kSW, kk, nt, lane, b0, b1);
-            mma16816<T>(acc[nt], afr[kk], b0, b1);
+            uint32_t b[4];
+            bfrag_kn_pair(sm + S::WH + h * kWidth * kSW, kSW, kk, np, lane, b);
+            mma16816<T>(acc[np], afr[kk], b[0], b[1]);
+            mma16816<T>(acc[np + 1], afr[kk], b[2], b[3]);
           }
         }
       }
@@ -431,16 +436,19 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
     if (din) {
       const float inv_scale = 1.f / loss_scale;
 #pragma unroll
-      for (int nt = 0; nt < N_IN / 8; ++nt) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int np = 0; np < N_IN / 8; np += 2) {
+        float acc2[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {    // dH_0 W_0: B[k = j][n = i] = W_0[j][i]
-          uint32_t b0, b1;
-          bfrag_kn(sm + S::W0, S::SX, kk, nt, lane, b0, b1);
-          mma16816<T>(acc, afr[kk], b0, b1);
+          uint32_t b[4];
+          bfrag_kn_pair(sm + S::W0, S::SX, kk, np, lane, b);
+          mma16816<T>(acc2[0], afr[kk], b[0], b[1]);
+          mma16816<T>(acc2[1], afr[kk], b[2], b[3]);
         }
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+        for (int u = 0; u < 4; ++u) {
+          const int nt = np + (u >> 1), half = u & 1;
+          const float* acc = acc2[u >> 1];
           const int64_t row = row0 + r0 + g + half * 8;
           if (row >= P) continue;
           const int c = nt * 8 + 2 * t;                 // columns c, c + 1
@@ -457,29 +465,58 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
       }
     }
     __syncthreads();
-    // ---- weight gradients of the tile: dW_l += Delta_l^T In_l, K = 128 rows
-#pragma unroll
-    for (int i = 0; i < S::TILES_PER_WARP; ++i) {
-      const int id = warp + i * kWarps;
-      if (id >= S::N_WTILES) break;
-      const T* Dl; int ldd; const T* In; int ldi; int mt, nt;
-      if (id < 8) {                                       // output layer: [16][64]
-        Dl = sm + S::DY; ldd = kSO; In = sm + S::A + (NH - 1) * kTile * kSW; ldi = kSW; mt = 0; nt = id;
-      } else if (id < 8 + (NH - 1) * 32) {                // hidden h: [64][64]
-        const int j = id - 8, h = 1 + j / 32, r = j % 32;
-        Dl = sm + S::D + h * kTile * kSW; ldd = kSW; In = sm + S::A + (h - 1) * kTile * kSW; ldi = kSW;
-        mt = r / 8; nt = r % 8;
-      } else {                                            // first layer: [64][N_IN]
-        const int j = id - 8 - (NH - 1) * 32;
-        Dl = sm + S::D; ldd = kSW; In = sm + S::X; ldi = S::SX; mt = j / (N_IN / 8); nt = j % (N_IN / 8);
-      }
+    // ---- weight gradients of the tile: dW_l += Delta_l^T In_l, K = 128 rows.  Warp w owns the
+    // m16n8 tiles w, w + 8, w + 16, ... of the list [output layer 1x8, hidden h 4x8 each, first
+    // layer 4x(N_IN/8)] (dw[i] = tile w + 8i).  Since N_IN/8 divides 8, all of a warp's tiles of
+    // one hidden or first layer have the same input columns nt: their B fragment is loaded once
+    // per k step and used by every m-tile.
+    {
       const int q = lane >> 3, rr = lane & 7;
+      const int arow = (q >> 1) * 8 + rr, acol = (q & 1) * 8, brow = (q & 1) * 8 + rr;
+      {                                                   // output layer [16][64]: tile 0, nt = warp
+        const T* Dl = sm + S::DY;
+        const T* In = sm + S::A + (NH - 1) * kTile * kSW;
 #pragma unroll
-      for (int ks = 0; ks < kTile / 16; ++ks) {
-        uint32_t a[4], b0, b1;
-        ldsm_x4_trans(a, Dl + (ks * 16 + (q >> 1) * 8 + rr) * ldd + mt * 16 + (q & 1) * 8);
-        ldsm_x2_trans(b0, b1, In + (ks * 16 + (q & 1) * 8 + rr) * ldi + nt * 8);
-        mma16816<T>(dw[i], a, b0, b1);
+        for (int ks = 0; ks < kTile / 16; ++ks) {
+          uint32_t a[4], b0, b1;
+          ldsm_x4_trans(a, Dl + (ks * 16 + arow) * kSO + acol);
+          ldsm_x2_trans(b0, b1, In + (ks * 16 + brow) * kSW + warp * 8);
+          mma16816<T>(dw[0], a, b0, b1);
+        }
+      }
+#pragma unroll
+      for (int h = 1; h < NH; ++h) {                      // hidden h [64][64]: mt = 0..3, nt = warp
+        const T* Dl = sm + S::D + h * kTile * kSW;
+        const T* In = sm + S::A + (h - 1) * kTile * kSW;
+#pragma unroll
+        for (int ks = 0; ks < kTile / 16; ++ks) {
+          uint32_t b0, b1;
+          ldsm_x2_trans(b0, b1, In + (ks * 16 + brow) * kSW + warp * 8);
+#pragma unroll
+          for (int mt = 0; mt < 4; ++mt) {
+            uint32_t a[4];
+            ldsm_x4_trans(a, Dl + (ks * 16 + arow) * kSW + mt * 16 + acol);
+            mma16816<T>(dw[1 + 4 * (h - 1) + mt], a, b0, b1);
+          }
+        }
+      }
+      {                                                   // first layer [64][N_IN]
+        constexpr int n8 = N_IN / 8, FT = N_IN / 16;      // n-tiles, tiles per warp
+        static_assert(8 % n8 == 0 && 1 + 4 * (NH - 1) + FT == S::TILES_PER_WARP, "tile plan");
+        const T* Dl = sm + S::D;
+        const T* In = sm + S::X;
+        const int nt = warp % n8, mt0 = warp / n8;
+#pragma unroll
+        for (int ks = 0; ks < kTile / 16; ++ks) {
+          uint32_t b0, b1;
+          ldsm_x2_trans(b0, b1, In + (ks * 16 + brow) * S::SX + nt * 8);
+#pragma unroll
+          for (int i = 0; i < FT; ++i) {
+            uint32_t a[4];
+            ldsm_x4_trans(a, Dl + (ks * 16 + arow) * kSW + (mt0 + i * (8 / n8)) * 16 + acol);
+            mma16816<T>(dw[1 + 4 * (NH - 1) + i], a, b0, b1);
+          }
+        }
       }
     }
   }

@@ -47,9 +47,11 @@ sxe_status check_launch(const char* what);
 // launchers (defined in encode.cu / mlp.cu / optim.cu); arguments already validated
 sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
                              void* out, cudaStream_t s, int64_t table_stride = 0);
+// level_end < 0 means n_levels; only levels [level_begin, level_end) are accumulated
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
-                             float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s);
-int encode_bwd_launches(const sxe_encoder* enc, int64_t P);
+                             float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s,
+                             int level_begin = 0, int level_end = -1);
+int encode_bwd_launches(const sxe_encoder* enc, int64_t P, int level_begin = 0, int level_end = -1);
 sxe_status launch_adam_advance(const sxe_adam_desc* a, int64_t* t, float* corrections, cudaStream_t s);
 sxe_status launch_encode_plain(const sxe_encoder* enc, bool backward, const float* x, int64_t P, const float* a,
                                float* b, cudaStream_t s);

@@ -33,6 +33,25 @@ from . import synth
 from .api import Adam, Encoder, Mlp, torch_dtype
 
 
+def level_chunks(enc: Encoder, P: int, k: int) -> list[tuple[int, int]]:
+    """Split the levels into at most k contiguous ranges that each hold about the same number of
+    touched table entries, estimated per level as min(T, lattice box of [0,1]^d, vertices * P)."""
+    m = (enc.d + 1.0) ** ((enc.d - 1.0) / (2.0 * enc.d)) if enc.res_mode == "equal_mem" else 1.0
+    est = []
+    for l in range(enc.n_levels):
+        N = math.floor(enc.base_res * enc.growth ** l) * (m if enc.kind == "simplex" else 1.0)
+        est.append(min(float(enc.T), (N + 2.0) ** enc.d, float(enc.n_vertices * P)))
+    k = max(1, min(k, enc.n_levels))
+    total, acc, out, lb = sum(est), 0.0, [], 0
+    for l, e in enumerate(est):
+        acc += e
+        if len(out) < k - 1 and acc >= total * (len(out) + 1) / k and l + 1 < enc.n_levels:
+            out.append((lb, l + 1))
+            lb = l + 1
+    out.append((lb, enc.n_levels))
+    return out
+
+
 def default_loss_scale(P: int, n_out: int) -> float:
     """Power of two near P*n_out/2 so that the scaled L2 gradient 2 r / (P n_out) is O(r)."""
     return float(2.0 ** max(0, math.floor(math.log2(max(1.0, P * n_out / 2.0)))))
@@ -40,7 +59,8 @@ def default_loss_scale(P: int, n_out: int) -> float:
 
 class Trainer:
     def __init__(self, encoder: Encoder, mlp: Mlp, batch: int, *, seed: int = 0, device="cuda",
-                 table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15):
+                 table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15,
+                 table_chunks: int = 1):
         if mlp.n_in != encoder.n_out:
             raise ValueError("network input %d != encoding width %d" % (mlp.n_in, encoder.n_out))
         self.enc, self.mlp, self.P = encoder, mlp, batch
@@ -71,12 +91,28 @@ class Trainer:
         self.t_dev = torch.zeros((1,), dtype=torch.int64, device=self.device)
         self.corrections = torch.zeros((2,), dtype=torch.float32, device=self.device)
         self.graph = None
+        self.set_table_chunks(table_chunks)
+
+    def set_table_chunks(self, k: int) -> None:
+        """Run the table backward and the table Adam in k level ranges: the Adam of range i runs on
+        a second (high-priority) stream while the backward of range i+1 runs on the step's stream.
+        Entries of different levels share no state record or bitmap word (T >= 32), so the ranges
+        are independent; k = 1 is the plain two-pass step."""
+        if k > 1 and self.enc.T < 32:
+            k = 1
+        self.chunks = level_chunks(self.enc, self.P, k)
+        if len(self.chunks) > 1:
+            self._aux = torch.cuda.Stream(device=self.device, priority=-1)
+            self._ready = [torch.cuda.Event() for _ in self.chunks]
+            self._joined = torch.cuda.Event()
 
     @property
     def n_launches_per_step(self) -> int:
-        # encode_fwd, network training + its partial reduction, encode_bwd (coarse levels in shared
-        # memory, then the rest), table Adam, network Adam
-        return 6 + self.enc.bwd_kernel_count(self.P)   # + the device step counter
+        # the device step counter, encode_fwd, network training + its partial reduction, encode_bwd
+        # per level range (coarse levels in shared memory, then the rest), table Adam per range,
+        # network Adam
+        bwd = sum(self.enc.bwd_kernel_count(self.P, levels=c) for c in self.chunks)
+        return 4 + bwd + len(self.chunks)
 
     def step(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
         """One optimisation step on batch (x [P, d] float32, target [P, n_out] float32); asynchronous."""
@@ -86,10 +122,31 @@ class Trainer:
         self.enc.encode_fwd(x, self.tables, self.enc_out, stream=stream)
         self.mlp.mlp_train_l2(self.W_lowp, self.enc_out, target, self.dW, self.sq_sum, din=self.d_enc,
                               loss_scale=self.loss_scale, workspace=self.ws, stream=stream)
-        self.enc.encode_bwd(x, self.d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F, touched=self.touched,
-                            stream=stream)
-        self.adam_tables.step_touched_dev(self.corrections, self.state, self.touched, self.tables, F, stream=stream)
+        if len(self.chunks) == 1:
+            self.enc.encode_bwd(x, self.d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F,
+                                touched=self.touched, stream=stream)
+            self.adam_tables.step_touched_dev(self.corrections, self.state, self.touched, self.tables, F,
+                                              stream=stream)
+        else:
+            self._table_step_overlapped(x, stream)
         self.adam_mlp.step_dev(self.corrections, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=stream)
+        if len(self.chunks) > 1:
+            main = torch.cuda.current_stream(self.device) if stream is None else stream
+            main.wait_event(self._joined)
+
+    def _table_step_overlapped(self, x, stream) -> None:
+        F, T = self.enc.n_features, self.enc.T
+        main = torch.cuda.current_stream(self.device) if stream is None else stream
+        flat = self.tables.view(-1)
+        for i, (lb, le) in enumerate(self.chunks):
+            self.enc.encode_bwd(x, self.d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F,
+                                touched=self.touched, levels=(lb, le), stream=main)
+            self._ready[i].record(main)
+            self._aux.wait_event(self._ready[i])
+            a, b = lb * T, le * T
+            self.adam_tables.step_touched_dev(self.corrections, self.state[a:b], self.touched[a // 32:b // 32],
+                                              flat[a * F:b * F], F, stream=self._aux)
+        self._joined.record(self._aux)
 
     def capture(self, x: torch.Tensor, target: torch.Tensor, warmup: int = 2) -> None:
         """Record one step on the fixed input buffers x and target into a CUDA graph (after

@@ -73,6 +73,13 @@ def test_entry_points_validate_before_launch(L):
         assert lib.sxe_encode_fwd(h, 12, 10, 16, 16, None) == -1            # x misaligned for d = 2
         assert lib.sxe_encode_bwd(h, 16, 10, 16, 16, 3, None, None) == -1    # stride not a multiple of F
         assert lib.sxe_encode_bwd(h, 16, 10, 16, 20, 2, None, None) == -1    # grad entries misaligned
+        # level ranges of the backward: inside [0, L] and not reversed; an empty range does nothing
+        assert lib.sxe_encode_bwd_levels(h, 16, 10, 16, 16, 2, None, 3, 2, None) == -1
+        assert lib.sxe_encode_bwd_levels(h, 16, 10, 16, 16, 2, None, -1, 2, None) == -1
+        assert lib.sxe_encode_bwd_levels(h, 16, 10, 16, 16, 2, None, 0, 99, None) == -1
+        assert lib.sxe_encode_bwd_levels(h, 16, 10, 16, 16, 2, None, 2, 2, None) == 0
+        assert lib.sxe_encode_bwd_levels_kernel_count(h, 10, 2, 2) == 0
+        assert lib.sxe_encode_bwd_levels_kernel_count(h, 10, 0, 99) == 0
         # zero points: nothing to do, no pointer needed
         assert lib.sxe_encode_fwd(h, None, 0, None, None, None) == 0
         assert lib.sxe_encode_bwd(h, None, 0, None, None, 2, None, None) == 0

@@ -346,6 +346,56 @@ def test_dense_coarse_levels_match_oracle(cuda_lib, case, kind):
         assert np.all(np.abs(dx - xref) <= 1e-5 * xden + 1e-30)
 
 
+@pytest.mark.parametrize("kind,index_mode", [("simplex", "hash"), ("grid", "dense_coarse")])
+def test_backward_by_level_ranges(cuda_lib, kind, index_mode):
+    """sxe_encode_bwd_levels: ranges that cut through the shared-memory coarse levels and the
+    rest, run one after the other, give the oracle's gradient and bitmap; a single range adds
+    and marks nothing outside its levels."""
+    from paper_2311_15439_gb300.api import Encoder
+    from oracle.lattice import INDEX_DENSE_COARSE, INDEX_HASH
+    d, L, F, log2_T, base, growth = 2, 6, 2, 14, 8.0, 1.6
+    T = 1 << log2_T
+    enc = Encoder(d, L, F, log2_T, base, growth, kind=kind, table_dtype="f32", index_mode=index_mode)
+    P = 40000
+    assert enc.bwd_kernel_count(P) == 2
+    ranges = [(0, 1), (1, 1), (1, 3), (3, 4), (4, 6)]
+    assert sum(enc.bwd_kernel_count(P, levels=r) for r in ranges) >= 4
+    x = synth.uniform_points(P, d, 98)
+    xd = torch.from_numpy(x).cuda()
+    dout = synth.normal_grads(P, L * F, 99)
+    dd = torch.from_numpy(dout).cuda()
+    state = torch.zeros((L * T, 4 * F), device="cuda")
+    bm = torch.zeros(((L * T + 31) // 32,), dtype=torch.int32, device="cuda")
+    enc.encode_bwd(xd, dd, state, grad_stride=4 * F, grad_offset=3 * F, touched=bm, levels=(1, 3))
+    grad = state[:, 3 * F:].reshape(L, T, F)
+    bits = np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little").astype(bool)[: L * T]
+    outside = np.r_[0:T, 3 * T:L * T]
+    assert torch.all(grad[0] == 0) and torch.all(grad[3:] == 0) and not bits[outside].any()
+    assert bits[T:3 * T].any()
+    state.zero_()
+    bm.zero_()
+    for r in ranges:
+        enc.encode_bwd(xd, dd, state, grad_stride=4 * F, grad_offset=3 * F, touched=bm, levels=r)
+    grad = state[:, 3 * F:].reshape(L, T, F).cpu().numpy()
+    mode = INDEX_DENSE_COARSE if index_mode == "dense_coarse" else INDEX_HASH
+    kw = dict(n_levels=L, log2_T=log2_T, n_features=F, base_res=base, growth=growth, index_mode=mode)
+    if kind == "simplex":
+        ref, den = O.simplex_encode_bwd(x, dout, with_denominator=True, **kw)
+        scales = lattice.simplex_level_scales_fp32(d, L, base, growth)
+    else:
+        ref = O.grid_encode_bwd(x, dout, **kw)
+        den = O.grid_encode_bwd(x, np.abs(dout), **kw)
+        scales = lattice.grid_level_scales_fp32(L, base, growth)
+    widths = lattice.level_box_widths(kind, d, scales, log2_T, mode)
+    want = np.zeros(L * T, dtype=bool)
+    for l in range(L):
+        assert rel_err(grad[l], ref[l], den[l]) <= 1e-5, "level %d" % l
+        vert = O.simplex_level_vertices if kind == "simplex" else O.grid_level_vertices
+        want[l * T + np.unique(vert(x, scales[l], log2_T, widths[l])[0])] = True
+    bits = np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little").astype(bool)[: L * T]
+    assert np.array_equal(bits, want)
+
+
 @pytest.mark.parametrize("kind,d,index_mode", [("simplex", 2, "hash"), ("simplex", 3, "hash"), ("grid", 2, "hash"),
                                                ("simplex", 2, "dense_coarse"), ("grid", 3, "dense_coarse")])
 def test_coarse_levels_summed_per_block(cuda_lib, kind, d, index_mode):
