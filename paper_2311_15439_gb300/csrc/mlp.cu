@@ -559,28 +559,38 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
 
 // dW[j] += (sum_b ws[b][j]) / loss_scale, summed over b in increasing order; the loss
 // partials (after the nb x n weight partials) are summed the same way into *sq_sum.
-// Sums the per-CTA partial weight gradients: one CTA per 32 consecutive parameters, its 8
-// warps take interleaved slices of the partials (coalesced 128-byte rows), and the 8 warp
-// sums are added in a fixed order, so the result does not depend on scheduling.
-constexpr int kReduceCols = 32, kReduceWarps = 8;
+// Sums the per-CTA partial weight gradients: one CTA per 32 consecutive parameters, its 16
+// warps take interleaved slices of the partials (coalesced 128-byte rows, eight in flight per
+// warp), and the 16 warp sums are added in a fixed order, so the result does not depend on
+// scheduling.
+constexpr int kReduceCols = 32, kReduceWarps = 16, kReduceUnroll = 8;
 __global__ void __launch_bounds__(kReduceCols * kReduceWarps)
 reduce_partials_kernel(const float* __restrict__ ws, int nb, int64_t n, float inv_scale,
                        float* __restrict__ dW, float* __restrict__ sq_sum) {
   __shared__ float part[kReduceWarps][kReduceCols];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t j = (int64_t)blockIdx.x * kReduceCols + lane;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  // warp w takes partial rows w, w + 16, ...; kReduceUnroll independent loads in flight, each
+  // into its own accumulator, combined pairwise in a fixed order
+  float acc[kReduceUnroll];
+#pragma unroll
+  for (int u = 0; u < kReduceUnroll; ++u) acc[u] = 0.f;
   if (j < n) {
     int b = w;
-    for (; b + 3 * kReduceWarps < nb; b += 4 * kReduceWarps) {
-      s0 += ws[(int64_t)b * n + j];
-      s1 += ws[(int64_t)(b + kReduceWarps) * n + j];
-      s2 += ws[(int64_t)(b + 2 * kReduceWarps) * n + j];
-      s3 += ws[(int64_t)(b + 3 * kReduceWarps) * n + j];
+    for (; b + (kReduceUnroll - 1) * kReduceWarps < nb; b += kReduceUnroll * kReduceWarps) {
+      float v[kReduceUnroll];
+#pragma unroll
+      for (int u = 0; u < kReduceUnroll; ++u) v[u] = __ldcs(ws + (int64_t)(b + u * kReduceWarps) * n + j);
+#pragma unroll
+      for (int u = 0; u < kReduceUnroll; ++u) acc[u] += v[u];
     }
-    for (; b < nb; b += kReduceWarps) s0 += ws[(int64_t)b * n + j];
+    for (; b < nb; b += kReduceWarps) acc[0] += __ldcs(ws + (int64_t)b * n + j);
   }
-  part[w][lane] = (s0 + s1) + (s2 + s3);
+#pragma unroll
+  for (int width = kReduceUnroll / 2; width > 0; width >>= 1)
+#pragma unroll
+    for (int u = 0; u < width; ++u) acc[u] += acc[u + width];
+  part[w][lane] = acc[0];
   __syncthreads();
   if (w == 0 && j < n) {
     float s = 0.f;

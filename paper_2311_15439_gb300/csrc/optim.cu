@@ -124,12 +124,21 @@ __global__ void loss_l2_kernel(const float* __restrict__ y, const float* __restr
   }
 }
 
-// One thread: the step count t += 1 and the bias corrections of the new t, in FP64 rounded once.
+// Two threads: the step count t += 1 and the bias corrections 1 / (1 - beta_i^t) of the new t,
+// thread i for beta_i, in FP64 rounded once to binary32.  beta^t by binary exponentiation (about
+// 2 log2 t dependent FP64 products, each rounded once, so within a few ulps of FP64 of the exact
+// power, far below the binary32 rounding that follows): FP64 latency is long on this part, and a
+// general pow() is a much longer dependent chain on the critical path of every step.
 __global__ void adam_advance_kernel(int64_t* __restrict__ t, float* __restrict__ c, float b1, float b2) {
   const int64_t tn = *t + 1;
-  *t = tn;
-  c[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)tn)));
-  c[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)tn)));
+  double p = 1.0, x = threadIdx.x == 0 ? (double)b1 : (double)b2;
+  for (int64_t e = tn; e > 0; e >>= 1) {
+    if (e & 1) p *= x;
+    x *= x;
+  }
+  c[threadIdx.x] = (float)(1.0 / (1.0 - p));
+  __syncthreads();                                      // both threads have read the old t
+  if (threadIdx.x == 0) *t = tn;
 }
 
 unsigned blocks_for(int64_t n, int threads, unsigned cap) {
@@ -174,7 +183,7 @@ sxe_status launch_loss_l2(const float* y, const float* target, int64_t P, int32_
 }
 
 sxe_status launch_adam_advance(const sxe_adam_desc* a, int64_t* t, float* corrections, cudaStream_t s) {
-  adam_advance_kernel<<<1, 1, 0, s>>>(t, corrections, a->beta1, a->beta2);
+  adam_advance_kernel<<<1, 2, 0, s>>>(t, corrections, a->beta1, a->beta2);
   return check_launch("adam_advance");
 }
 

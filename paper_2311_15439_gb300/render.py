@@ -218,7 +218,9 @@ def vr_composite(sigma, logits, delta, n_samples: int, with_weights: bool = Fals
 
 def _main(argv=None):
     """Render seeded camera rays through a random field and print the time per render:
-    ``python -m paper_2311_15439_gb300.render --rays 65536 --samples 64 --kind simplex``."""
+    ``python -m paper_2311_15439_gb300.render --rays 65536 --samples 64 --kind simplex``;
+    with ``--train``, the time per training step (``VolumeTrainer.step``) towards seeded uniform
+    target colours."""
     import argparse
     from . import synth
     ap = argparse.ArgumentParser(description=_main.__doc__)
@@ -228,8 +230,25 @@ def _main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--repeat", type=int, default=5)
     ap.add_argument("--unfused", action="store_true", help="the field as three launches")
+    ap.add_argument("--train", action="store_true", help="time training steps instead of renders")
     a = ap.parse_args(argv)
     enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=a.kind, table_dtype="f16")
+    if a.train:
+        vt = VolumeTrainer(enc, a.rays, a.samples, seed=63)
+        rays = [torch.from_numpy(v).cuda() for v in synth.camera_rays(a.rays, 60)]
+        target = torch.from_numpy(synth.rng(64).random((a.rays, 3)).astype("float32")).cuda()
+        for _ in range(a.warmup):
+            vt.step(*rays, target)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        for _ in range(a.repeat):
+            vt.step(*rays, target)
+        e.record()
+        torch.cuda.synchronize()
+        print("train %s: %d rays x %d samples: %.3f ms per step, loss %.4g" %
+              (a.kind, a.rays, a.samples, s.elapsed_time(e) / a.repeat, vt.loss()))
+        return
     rr = Renderer(enc, a.rays, a.samples, dtype="f16", fused=not a.unfused)
     _, store = synth.uniform_tables(16, 1 << 19, 2, 61, dtype="f16", scale=1.0)
     tab = torch.from_numpy(store).cuda()

@@ -333,3 +333,21 @@ def test_overlapped_table_step_equals_plain_step(k):
     _close_up_to_atomics(a.W, b.W, steps=5, atol=1e-5)
     _close_up_to_atomics(a.state, b.state, steps=5)
     _close_up_to_atomics(a.tables.float(), b.tables.float(), steps=5)
+
+
+def test_device_step_counter_and_bias_corrections():
+    """sxe_adam_advance: t counts up on the device and the corrections are 1 / (1 - beta^t) in FP64
+    rounded once to binary32 (at most one binary32 ulp from the exactly rounded value)."""
+    from paper_2311_15439_gb300.api import Adam
+    a = Adam(1e-2, 0.9, 0.99, 1e-15, skip_zero_grad=True)
+    t = torch.zeros((1,), dtype=torch.int64, device="cuda")
+    c = torch.zeros((2,), dtype=torch.float32, device="cuda")
+    b1, b2 = np.float64(np.float32(0.9)), np.float64(np.float32(0.99))    # the descriptor's binary32 betas
+    checks = {1, 2, 3, 7, 64, 1000, 4097}
+    for k in range(1, 4098):
+        a.advance(t, c)
+        if k in checks:
+            got = c.cpu().numpy()
+            want32 = np.array([1.0 / (1.0 - b1 ** k), 1.0 / (1.0 - b2 ** k)]).astype(np.float32)
+            assert int(t.item()) == k
+            assert np.all(np.abs(got.astype(np.float64) - want32) <= np.spacing(want32)), (k, got, want32)
