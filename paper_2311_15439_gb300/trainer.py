@@ -176,3 +176,66 @@ class Trainer:
         """binary32 master table parameters as [L, T, F]."""
         F = self.enc.n_features
         return self.state[:, :F].reshape(self.enc.table_shape())
+
+
+class HostFeed:
+    """Trains from batches in pinned host memory with the copies off the critical path.
+
+    Two input-buffer pairs live on the device, each with its own recording of the training step
+    (a CUDA graph).  ``step(x_host, target_host)`` copies the batch into the free pair on a copy
+    stream, replays that pair's graph on the current stream once the copy has landed, and sends the
+    step's loss back to pinned host memory; it then returns the loss of the step before, so the
+    host stays one step ahead of the device and the copy of batch k+1 runs while step k computes.
+    Every step still moves its whole batch host -> device and its loss device -> host."""
+
+    def __init__(self, trainer: Trainer, first_batch, warmup: int = 2):
+        tr = self.tr = trainer
+        x0, t0 = first_batch
+        dev = tr.device
+        self.bx = [torch.empty(x0.shape, dtype=x0.dtype, device=dev) for _ in range(2)]
+        self.bt = [torch.empty(t0.shape, dtype=t0.dtype, device=dev) for _ in range(2)]
+        for i in range(2):
+            self.bx[i].copy_(x0)
+            self.bt[i].copy_(t0)
+        tr.capture(self.bx[0], self.bt[0], warmup=warmup)
+        g0 = tr.graph
+        tr.capture(self.bx[1], self.bt[1], warmup=0)
+        self.graphs = [g0, tr.graph]
+        self.copy = torch.cuda.Stream(device=dev)
+        self.copy.wait_stream(torch.cuda.current_stream(dev))
+        self._ready = [torch.cuda.Event() for _ in range(2)]
+        self._free = [torch.cuda.Event() for _ in range(2)]
+        self._done = [torch.cuda.Event() for _ in range(2)]
+        self._loss = torch.zeros((2,), dtype=torch.float32).pin_memory()
+        self._scale = 1.0 / (tr.P * tr.mlp.n_out)
+        self.k = 0
+
+    def step(self, x_host: torch.Tensor, target_host: torch.Tensor):
+        """Queue one step on a pinned host batch; returns the previous step's loss (None at first)."""
+        i = self.k % 2
+        main = torch.cuda.current_stream(self.tr.device)
+        if self.k >= 2:
+            self.copy.wait_event(self._free[i])          # step k-2, which read this pair, is done
+        with torch.cuda.stream(self.copy):
+            self.bx[i].copy_(x_host, non_blocking=True)
+            self.bt[i].copy_(target_host, non_blocking=True)
+            self._ready[i].record(self.copy)
+        main.wait_event(self._ready[i])
+        self.tr.t += 1
+        self.graphs[i].replay()
+        self._free[i].record(main)
+        self._loss[i:i + 1].copy_(self.tr.sq_sum, non_blocking=True)
+        self._done[i].record(main)
+        prev = None
+        if self.k >= 1:
+            j = 1 - i
+            self._done[j].synchronize()
+            prev = float(self._loss[j]) * self._scale
+        self.k += 1
+        return prev
+
+    def finish(self) -> float:
+        """Waits for the last queued step and returns its loss."""
+        j = (self.k - 1) % 2
+        self._done[j].synchronize()
+        return float(self._loss[j]) * self._scale

@@ -351,3 +351,32 @@ def test_device_step_counter_and_bias_corrections():
             want32 = np.array([1.0 / (1.0 - b1 ** k), 1.0 / (1.0 - b2 ** k)]).astype(np.float32)
             assert int(t.item()) == k
             assert np.all(np.abs(got.astype(np.float64) - want32) <= np.spacing(want32)), (k, got, want32)
+
+
+def test_host_feed_equals_eager_steps():
+    """HostFeed (pinned host batches, double-buffered copies on a copy stream, a recorded step per
+    buffer pair, the loss returned one step late) trains like eager steps on device copies of the
+    same batches and reports each step's loss."""
+    from paper_2311_15439_gb300.trainer import HostFeed
+    P = 4096
+    a, b = _make(P, seed=13), _make(P, seed=13)
+    img = synth.ProceduralImage(5, size=1024, n_waves=4)
+    batches = []
+    for i in range(7):
+        x = synth.uniform_points(P, 2, 80 + i)
+        batches.append((torch.from_numpy(x).pin_memory(), torch.from_numpy(img.sample(x)).pin_memory()))
+    feed = HostFeed(b, batches[0], warmup=2)            # two eager steps on batch 0, then two recordings
+    for _ in range(2):
+        a.step(batches[0][0].cuda(), batches[0][1].cuda())
+    want = []
+    for x, t in batches[1:]:
+        a.step(x.cuda(), t.cuda())
+        want.append(a.loss())
+    got = [feed.step(x, t) for x, t in batches[1:]]
+    last = feed.finish()
+    assert got[0] is None
+    got = got[1:] + [last]
+    assert a.t == b.t == 8
+    assert got == pytest.approx(want, rel=1e-3)
+    _close_up_to_atomics(a.W, b.W, steps=8, atol=1e-5)
+    _close_up_to_atomics(a.state, b.state, steps=8)
