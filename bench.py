@@ -205,7 +205,7 @@ def run_gpu(args):
                "sxe_mlp_set_kernel")
     enc = Encoder(**CFG, kind=args.kind, table_dtype="f16")
     mlp = Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16")
-    tr = Trainer(enc, mlp, BATCH, seed=rank, device=dev)
+    tr = Trainer(enc, mlp, BATCH, seed=rank, device=dev, table_layout="records")
     xs, ts = make_batches(N_POOL, seed0=1000 + 100 * rank)
     xd = [torch.from_numpy(x).to(dev) for x in xs]
     td = [torch.from_numpy(t).to(dev) for t in ts]
@@ -480,7 +480,7 @@ def volume_train(dev, rays, S=64, steps=10, warmup=3):
         b.record()
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / steps
-        out[kind] = {"ms_per_step": ms, "samples_per_s": R * S / (ms / 1e3)}
+        out[kind] = {"ms_per_step": ms, "samples_per_s": R * S / (ms / 1e3), "table_layout": vt.tab.layout}
         del vt
         torch.cuda.empty_cache()
     out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]

@@ -106,6 +106,17 @@ sxe_status sxe_encoder_level_params(const sxe_encoder* enc, float* level_scale, 
  * (0 for a hashed level; all 0 under SXE_INDEX_HASH). */
 sxe_status sxe_encoder_level_index(const sxe_encoder* enc, int32_t* box_width);
 
+/* Backward strategy for the levels that are not summed in shared memory (sxe_encode_bwd,
+ * sxe_encode_bwd_levels).  on = 0 (default): one thread per (point, level), every term added
+ * to its table entry with its own reduction.  on = 1: a warp takes 32 consecutive points of one
+ * level, finds the lanes whose vertices share a table entry (Sec. 5 step (e) adds all of them
+ * into the same H_l[slot]) and adds each group's sum with one reduction; this pays when
+ * consecutive points are spatially coherent (the samples along a ray, Sec. 6.2), where
+ * neighbours share vertices.  The sums are the same up to floating-point reassociation.
+ * SXE_EINVAL for a NULL encoder or on not 0 or 1.  Not thread-safe with concurrent calls on the
+ * same encoder. */
+sxe_status sxe_encoder_set_bwd_aggregation(sxe_encoder* enc, int32_t on);
+
 /* Forward encoding, Sec. 5 steps (a)-(d): for every point and level, scale and skew
  * (Eq. 2) the point, find its simplex by sorting the fractional parts (Sec. 4.2),
  * weight its n+1 vertices barycentrically (Sec. 4.3), hash each vertex into that

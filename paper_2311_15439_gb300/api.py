@@ -135,6 +135,12 @@ class Encoder:
                     "sxe_encode_bwd_levels")
         return grad
 
+    def set_bwd_aggregation(self, on: bool) -> None:
+        """Warp-level sums of the backward terms that land in the same table entry
+        (``sxe_encoder_set_bwd_aggregation``): for batches whose consecutive points are spatially
+        coherent, such as the samples along rays."""
+        L.check(L.lib().sxe_encoder_set_bwd_aggregation(self._h, 1 if on else 0), "sxe_encoder_set_bwd_aggregation")
+
     def bwd_kernel_count(self, n_points: int, levels: tuple[int, int] | None = None) -> int:
         """Kernels one ``encode_bwd`` call launches for this many points (0, 1 or 2)."""
         if levels is None:

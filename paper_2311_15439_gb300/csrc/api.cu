@@ -105,6 +105,13 @@ sxe_status sxe_encoder_level_index(const sxe_encoder* e, int32_t* width) {
   return SXE_OK;
 }
 
+sxe_status sxe_encoder_set_bwd_aggregation(sxe_encoder* e, int32_t on) {
+  if (!e) return set_error(SXE_EINVAL, "encoder_set_bwd_aggregation: NULL encoder");
+  if (on != 0 && on != 1) return set_error(SXE_EINVAL, "encoder_set_bwd_aggregation: on=%d is not 0 or 1", on);
+  e->bwd_aggregate = on;
+  return SXE_OK;
+}
+
 sxe_status sxe_encoder_destroy(sxe_encoder* e) {
   delete e;
   return SXE_OK;

@@ -129,6 +129,79 @@ encode_bwd_kernel(const float* __restrict__ x, int64_t P, const float* __restric
   }
 }
 
+// Backward with warp-level sums of colliding terms, for batches whose consecutive points are
+// spatially coherent (the samples of a ray).  Block b takes the 32 points [32 b, 32 b + 32) and
+// warp w the levels l0 + w, l0 + w + 8, ... of them, lane i point 32 b + i, so the 32 lanes of a
+// warp add into the same level's table.  For every vertex k the lanes whose entries coincide are
+// found with match.any; a lane alone adds its term directly, a group sums its terms in the warp's
+// shared scratch and its lowest lane adds the sum with one reduction.  dout rows are read through
+// L1 (the 8 warps of a block read the 16 levels of the same 32 rows).
+constexpr int kAggPoints = 32;
+
+template <bool SIMPLEX, int D, int F>
+__global__ void __launch_bounds__(kThreads)
+encode_bwd_agg_kernel(const float* __restrict__ x, int64_t P, const float* __restrict__ dout,
+                      float* __restrict__ grad, int64_t stride, uint32_t* __restrict__ touched,
+                      const EncParams prm, int l0, int nl) {
+  constexpr int V = Verts<SIMPLEX, D>::V;
+  constexpr int kWarps = kThreads / 32;
+  __shared__ float s_scr[kWarps][32][F];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int f = 0; f < F; ++f) s_scr[warp][lane][f] = 0.f;
+  __syncwarp();
+  const int L = prm.n_levels;
+  const int64_t p = (int64_t)blockIdx.x * kAggPoints + lane;
+  const bool live = p < P;
+  float xv[D];
+  if (live) load_point<D>(x, p, xv);
+  else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) xv[i] = 0.f;
+  }
+  const uint32_t mask = (1u << prm.log2_T) - 1u;
+  for (int l = l0 + warp; l < l0 + nl; l += kWarps) {
+    float g[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) g[f] = live ? __ldg(dout + (p * L + l) * F + f) : 0.f;
+    uint32_t slot[V];
+    float w[V];
+    lattice<SIMPLEX, D>(xv, prm.scale[l], prm.skew_F, mask, prm.width[l], slot, w);
+    const int64_t lbase = (int64_t)l << prm.log2_T;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const uint32_t key = live ? slot[k] : 0xffffffffu;        // slots are < T <= 2^26
+      const uint32_t peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      float c[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) c[f] = w[k] * g[f];
+      const bool alone = __popc(peers) == 1;
+      if (live && !alone) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) atomicAdd(&s_scr[warp][leader][f], c[f]);
+      }
+      __syncwarp();
+      if (live && (alone || lane == leader)) {
+        if (!alone) {
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            c[f] = s_scr[warp][lane][f];
+            s_scr[warp][lane][f] = 0.f;
+          }
+        }
+        const int64_t e = lbase + slot[k];
+        atomic_add_entry<F>(grad + e * stride, c);
+        if (touched) {
+          const uint32_t bit = 1u << (uint32_t)(e & 31);
+          if (!(__ldcg(touched + (e >> 5)) & bit)) atomicOr(touched + (e >> 5), bit);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 template <bool SIMPLEX, int D>
 __global__ void __launch_bounds__(kThreads)
 encode_vertices_kernel(const float* __restrict__ x, int64_t P, uint32_t* __restrict__ slots,
@@ -514,6 +587,11 @@ sxe_status bwd_f(const sxe_encoder* e, const float* x, int64_t P, const float* d
   const int l0 = std::max(lb, full.n);
   const int nl = le - l0;
   if (nl <= 0) return SXE_OK;
+  if (e->bwd_aggregate) {
+    const unsigned nb = (unsigned)((P + kAggPoints - 1) / kAggPoints);
+    encode_bwd_agg_kernel<SIMPLEX, D, F><<<nb, kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm, l0, nl);
+    return check_launch("encode_bwd_agg");
+  }
   encode_bwd_kernel<SIMPLEX, D, F><<<grid_for(P, nl), kThreads, 0, s>>>(x, P, dout, g, stride, touched, e->prm,
                                                                        l0, nl);
   return check_launch("encode_bwd");

@@ -36,6 +36,7 @@ struct sxe_encoder {
   int32_t level_res[SXE_MAX_LEVELS];
   uint32_t box_width[SXE_MAX_LEVELS];   // lattice coordinates per axis of [0,1]^d at each level
   sxe::EncParams prm;
+  int32_t bwd_aggregate = 0;            // backward: warp-level sum of colliding terms (coherent batches)
 };
 
 namespace sxe {

@@ -107,20 +107,19 @@ class VolumeTrainer:
     kernels; the step count lives on the device."""
 
     def __init__(self, encoder: Encoder, max_rays: int, n_samples: int, *, dtype: str = "f16", seed: int = 0,
-                 device="cuda", table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15):
+                 device="cuda", table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15,
+                 table_layout: str = "auto"):
         from . import synth
         from .api import Adam
-        from .trainer import default_loss_scale
+        from .trainer import TableState, choose_table_layout, default_loss_scale
         self.enc, self.R, self.S = encoder, max_rays, n_samples
         self.rr = Renderer(encoder, max_rays, n_samples, dtype=dtype, device=device, fused=False)
         dev = self.rr.x.device
         F, n_entries = encoder.n_features, encoder.n_levels * encoder.T
         vals = synth.uniform_tables(encoder.n_levels, encoder.T, F, seed, dtype="f32", scale=table_init)[0]
         init = torch.from_numpy(vals.reshape(n_entries, F)).to(dev)
-        self.state = torch.zeros((n_entries, 4 * F), dtype=torch.float32, device=dev)
-        self.state[:, :F] = init
-        self.tables = init.to(torch_dtype(encoder.table_dtype)).reshape(encoder.table_shape()).contiguous()
-        self.touched = torch.zeros(((n_entries + 31) // 32,), dtype=torch.int32, device=dev)
+        self.tab = TableState(encoder, init, choose_table_layout(encoder, dev, table_layout), dev)
+        self.tables = self.tab.tables
         self.nets = []
         for k, m in enumerate((self.rr.density, self.rr.color)):
             W = torch.from_numpy(m.init_weights(seed + 1 + k)).to(dev)
@@ -165,8 +164,7 @@ class VolumeTrainer:
                                          _ptr(self.dv), st), "sxe_vr_field_bwd")
         dens["mlp"].mlp_bwd(dens["W_lowp"], rr.enc_out[:P], self.dv[:P], dens["dW"], din=self.denc[:P],
                             loss_scale=self.loss_scale, workspace=dens["ws"], stream=stream)
-        self.enc.encode_bwd(rr.x[:P], self.denc[:P], self.state, grad_stride=4 * F, grad_offset=3 * F,
-                            touched=self.touched, stream=stream)
+        self.tab.backward(rr.x[:P], self.denc[:P], stream=stream)
         self._n_rays = R
 
     def step(self, origins, dirs, t_near, t_far, target, stream=None) -> None:
@@ -174,14 +172,17 @@ class VolumeTrainer:
         self.t += 1
         self.adam_tables.advance(self.t_dev, self.corrections, stream=stream)
         self.gradients(origins, dirs, t_near, t_far, target, stream=stream)
-        self.adam_tables.step_touched_dev(self.corrections, self.state, self.touched, self.tables,
-                                          self.enc.n_features, stream=stream)
+        self.tab.adam(self.adam_tables, self.corrections, stream=stream)
         for n in self.nets:
             self.adam_nets.step_dev(self.corrections, n["W"], n["m"], n["v"], n["dW"], lowp=n["W_lowp"], stream=stream)
 
     def loss(self) -> float:
         """Mean squared colour error of the last step (synchronises)."""
         return float(self.sq_sum.item()) / (self._n_rays * 3)
+
+    def table_grads(self) -> torch.Tensor:
+        """Table gradient of the last ``gradients`` call, [L, T, F] (before the Adam step)."""
+        return self.tab.grads()
 
 
 def vr_samples(origins, dirs, t_near, t_far, n_samples: int, stream=None):

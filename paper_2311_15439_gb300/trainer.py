@@ -18,10 +18,13 @@ corrections that both Adam launches read), so a step has no host-side value that
 one step to the next: ``capture`` records it once into a CUDA graph and ``replay`` reruns it
 with a single launch.
 
-Table state layout in HBM: one binary32 record {param[F], m[F], v[F], grad[F]} per entry
-(32 bytes for F = 2: one DRAM sector), entries ordered [level][slot]; a separate dense
-[L][T][F] low-precision copy is what the forward pass gathers from; a bitmap of L*T bits
-marks the entries that received a gradient in the current step.
+Table state layout in HBM (``choose_table_layout``), for tables far larger than L2 of which a
+step touches a small part: one binary32 record {param[F], m[F], v[F], grad[F]} per entry (32
+bytes for F = 2: one DRAM sector), entries ordered [level][slot], and a bitmap of L*T bits that
+marks the entries that received a gradient in the current step; for tables whose gradient array
+fits in L2: separate dense binary32 arrays (the backward's reductions then stay in L2) and a dense
+Adam that skips zero gradients.  Either way a separate dense [L][T][F] low-precision copy is what
+the forward pass gathers from.
 """
 from __future__ import annotations
 
@@ -52,6 +55,75 @@ def level_chunks(enc: Encoder, P: int, k: int) -> list[tuple[int, int]]:
     return out
 
 
+DENSE_L2_FRACTION = 0.6
+
+
+def choose_table_layout(encoder: Encoder, device, layout: str = "auto") -> str:
+    """"records": one binary32 record {param, m, v, grad} per entry, a bitmap of the entries a step
+    touched and an optimiser sweep over those only -- for tables far larger than L2 of which a
+    step touches a small part.  "dense": separate binary32 arrays, the gradient a dense [L][T][F]
+    array that the backward's reductions keep in L2, and a dense Adam that skips zero gradients
+    (the same update) -- for tables whose gradient array fits in L2.  "auto" picks "dense" when
+    the gradient array is at most DENSE_L2_FRACTION of the device's L2."""
+    if layout in ("records", "dense"):
+        return layout
+    if layout != "auto":
+        raise ValueError("table layout must be 'auto', 'records' or 'dense'")
+    l2 = getattr(torch.cuda.get_device_properties(torch.device(device)), "L2_cache_size", 0) or (96 << 20)
+    grad_bytes = 4 * encoder.n_levels * encoder.T * encoder.n_features
+    return "dense" if grad_bytes <= DENSE_L2_FRACTION * l2 else "records"
+
+
+class TableState:
+    """Master table parameters, Adam moments and gradients in one of the two layouts of
+    ``choose_table_layout``, with the low-precision copy the forward pass gathers from."""
+
+    def __init__(self, encoder: Encoder, init: torch.Tensor, layout: str, device):
+        F = encoder.n_features
+        n_entries = encoder.n_levels * encoder.T
+        self.enc, self.layout = encoder, layout
+        self.tables = init.to(torch_dtype(encoder.table_dtype)).reshape(encoder.table_shape()).contiguous()
+        if layout == "records":
+            self.state = torch.zeros((n_entries, 4 * F), dtype=torch.float32, device=device)
+            self.state[:, :F] = init
+            self.touched = torch.zeros(((n_entries + 31) // 32,), dtype=torch.int32, device=device)
+        else:
+            self.state = self.touched = None
+            self.param = init.reshape(-1).clone()
+            self.m = torch.zeros_like(self.param)
+            self.v = torch.zeros_like(self.param)
+            self.grad = torch.zeros_like(self.param)
+
+    def backward(self, x, d_enc, stream=None, levels=None) -> None:
+        """Table gradients of one step (into the records' gradient fields or the dense array)."""
+        F = self.enc.n_features
+        if self.layout == "records":
+            self.enc.encode_bwd(x, d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F, touched=self.touched,
+                                levels=levels, stream=stream)
+        else:
+            self.enc.encode_bwd(x, d_enc, self.grad, levels=levels, stream=stream)
+
+    def adam(self, adam: Adam, corrections, stream=None) -> None:
+        """Adam on every entry with a nonzero gradient; refreshes the low-precision tables."""
+        if self.layout == "records":
+            adam.step_touched_dev(corrections, self.state, self.touched, self.tables, self.enc.n_features,
+                                  stream=stream)
+        else:
+            adam.step_dev(corrections, self.param, self.m, self.v, self.grad, lowp=self.tables.view(-1),
+                          stream=stream)
+
+    def params(self) -> torch.Tensor:
+        F = self.enc.n_features
+        p = self.state[:, :F] if self.layout == "records" else self.param
+        return p.reshape(self.enc.table_shape())
+
+    def grads(self) -> torch.Tensor:
+        """The gradient accumulated since the last Adam step, [L, T, F]."""
+        F = self.enc.n_features
+        g = self.state[:, 3 * F:] if self.layout == "records" else self.grad
+        return g.reshape(self.enc.table_shape())
+
+
 def default_loss_scale(P: int, n_out: int) -> float:
     """Power of two near P*n_out/2 so that the scaled L2 gradient 2 r / (P n_out) is O(r)."""
     return float(2.0 ** max(0, math.floor(math.log2(max(1.0, P * n_out / 2.0)))))
@@ -60,7 +132,7 @@ def default_loss_scale(P: int, n_out: int) -> float:
 class Trainer:
     def __init__(self, encoder: Encoder, mlp: Mlp, batch: int, *, seed: int = 0, device="cuda",
                  table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15,
-                 table_chunks: int = 1):
+                 table_chunks: int = 1, table_layout: str = "auto"):
         if mlp.n_in != encoder.n_out:
             raise ValueError("network input %d != encoding width %d" % (mlp.n_in, encoder.n_out))
         self.enc, self.mlp, self.P = encoder, mlp, batch
@@ -70,10 +142,8 @@ class Trainer:
         # seeded host values U(-table_init, table_init), so any checker can regenerate them
         vals = synth.uniform_tables(encoder.n_levels, encoder.T, F, seed, dtype="f32", scale=table_init)[0]
         init = torch.from_numpy(vals.reshape(n_entries, F)).to(self.device)
-        self.state = torch.zeros((n_entries, 4 * F), dtype=torch.float32, device=self.device)
-        self.state[:, :F] = init
-        self.tables = init.to(torch_dtype(encoder.table_dtype)).reshape(encoder.table_shape()).contiguous()
-        self.touched = torch.zeros(((n_entries + 31) // 32,), dtype=torch.int32, device=self.device)
+        self.tab = TableState(encoder, init, choose_table_layout(encoder, self.device, table_layout), self.device)
+        self.tables, self.state, self.touched = self.tab.tables, self.tab.state, self.tab.touched
         W0 = torch.from_numpy(mlp.init_weights(seed + 1)).to(self.device)
         self.W = W0.clone()
         self.W_lowp = W0.to(torch_dtype(mlp.dtype))
@@ -98,7 +168,7 @@ class Trainer:
         a second (high-priority) stream while the backward of range i+1 runs on the step's stream.
         Entries of different levels share no state record or bitmap word (T >= 32), so the ranges
         are independent; k = 1 is the plain two-pass step."""
-        if k > 1 and self.enc.T < 32:
+        if k > 1 and (self.enc.T < 32 or self.tab.layout != "records"):
             k = 1
         self.chunks = level_chunks(self.enc, self.P, k)
         if len(self.chunks) > 1:
@@ -116,17 +186,14 @@ class Trainer:
 
     def step(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
         """One optimisation step on batch (x [P, d] float32, target [P, n_out] float32); asynchronous."""
-        F = self.enc.n_features
         self.t += 1
         self.adam_tables.advance(self.t_dev, self.corrections, stream=stream)
         self.enc.encode_fwd(x, self.tables, self.enc_out, stream=stream)
         self.mlp.mlp_train_l2(self.W_lowp, self.enc_out, target, self.dW, self.sq_sum, din=self.d_enc,
                               loss_scale=self.loss_scale, workspace=self.ws, stream=stream)
         if len(self.chunks) == 1:
-            self.enc.encode_bwd(x, self.d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F,
-                                touched=self.touched, stream=stream)
-            self.adam_tables.step_touched_dev(self.corrections, self.state, self.touched, self.tables, F,
-                                              stream=stream)
+            self.tab.backward(x, self.d_enc, stream=stream)
+            self.tab.adam(self.adam_tables, self.corrections, stream=stream)
         else:
             self._table_step_overlapped(x, stream)
         self.adam_mlp.step_dev(self.corrections, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=stream)
@@ -174,8 +241,11 @@ class Trainer:
 
     def table_params(self) -> torch.Tensor:
         """binary32 master table parameters as [L, T, F]."""
-        F = self.enc.n_features
-        return self.state[:, :F].reshape(self.enc.table_shape())
+        return self.tab.params()
+
+    def table_grads(self) -> torch.Tensor:
+        """Table gradient accumulated since the last Adam step, [L, T, F]."""
+        return self.tab.grads()
 
 
 class HostFeed:

@@ -80,6 +80,11 @@ def test_entry_points_validate_before_launch(L):
         assert lib.sxe_encode_bwd_levels(h, 16, 10, 16, 16, 2, None, 2, 2, None) == 0
         assert lib.sxe_encode_bwd_levels_kernel_count(h, 10, 2, 2) == 0
         assert lib.sxe_encode_bwd_levels_kernel_count(h, 10, 0, 99) == 0
+        # backward strategy switch: 0 or 1 only
+        assert lib.sxe_encoder_set_bwd_aggregation(None, 1) == -1
+        assert lib.sxe_encoder_set_bwd_aggregation(h, 2) == -1
+        assert lib.sxe_encoder_set_bwd_aggregation(h, 1) == 0
+        assert lib.sxe_encoder_set_bwd_aggregation(h, 0) == 0
         # zero points: nothing to do, no pointer needed
         assert lib.sxe_encode_fwd(h, None, 0, None, None, None) == 0
         assert lib.sxe_encode_bwd(h, None, 0, None, None, 2, None, None) == 0

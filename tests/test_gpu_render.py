@@ -220,15 +220,18 @@ def test_field_bwd_matches_oracle(cuda_lib):
     assert np.all(np.abs(got - want) <= 2 * U32 * (np.abs(want) + np.abs(dsig.astype(np.float64) * sig)[:, None]))
 
 
-def test_volume_gradients_match_oracle(cuda_lib):
+@pytest.mark.parametrize("layout", ["records", "dense"])
+def test_volume_gradients_match_oracle(cuda_lib, layout):
     """Every gradient of one volumetric training step (tables, density and colour networks)
     against the FP64 chain rule on the same fp16 weights and tables: relative L2 error within
-    5 %, direction within 0.99 cosine (fp16 networks, ReLU decisions near zero can flip)."""
+    5 %, direction within 0.99 cosine (fp16 networks, ReLU decisions near zero can flip); both
+    table layouts."""
     from paper_2311_15439_gb300.api import Encoder
     from paper_2311_15439_gb300.render import VolumeTrainer
     R, S, L, log2_T = 128, 16, 8, 12
     enc = Encoder(3, L, 2, log2_T, 8.0, 1.5, table_dtype="f16")
-    vt = VolumeTrainer(enc, R, S, seed=3, table_init=0.5)
+    vt = VolumeTrainer(enc, R, S, seed=3, table_init=0.5, table_layout=layout)
+    assert vt.tab.layout == layout
     rays = synth.camera_rays(R, 44)
     target = synth.rng(45).random((R, 3)).astype(np.float32)
     vt.gradients(*[torch.from_numpy(a).cuda() for a in rays], torch.from_numpy(target).cuda())
@@ -245,7 +248,7 @@ def test_volume_gradients_match_oracle(cuda_lib):
         cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
         return rel <= 0.05 and cos >= 0.99
 
-    g_tab = vt.state[:, 6:].cpu().numpy().reshape(L, 1 << log2_T, 2)
+    g_tab = vt.table_grads().cpu().numpy()
     assert close(g_tab, np.stack([gt[l] for l in range(L)]))
     assert close(vt.nets[0]["dW"].cpu().numpy(), np.concatenate([w.ravel() for w in dWd]))
     assert close(vt.nets[1]["dW"].cpu().numpy(), np.concatenate([w.ravel() for w in dWc]))

@@ -15,23 +15,26 @@ pytestmark = pytest.mark.gpu
 CFG = dict(d=2, n_levels=8, n_features=2, log2_T=12, base_res=16.0, growth=1.5)
 
 
-def _make(P=4096, seed=0, table_dtype="f16"):
+def _make(P=4096, seed=0, table_dtype="f16", layout="auto"):
     from paper_2311_15439_gb300.api import Encoder, Mlp
     from paper_2311_15439_gb300.trainer import Trainer
     enc = Encoder(**CFG, table_dtype=table_dtype)
     mlp = Mlp(16, 3, n_hidden=2, dtype="f16")
-    return Trainer(enc, mlp, P, seed=seed)
+    return Trainer(enc, mlp, P, seed=seed, table_layout=layout)
 
 
-def test_one_step_matches_oracle():
+@pytest.mark.parametrize("layout", ["records", "dense"])
+def test_one_step_matches_oracle(layout):
     """Gradients of one step against the oracle pipeline: encode (FP64, rounded to the fp16
     encoding the network consumes), network + L2 loss and backward (FP64), scatter-add of
     dL/d(encoding) into the tables (FP64); then the Adam step of every table entry whose
-    gradient sign is unambiguous, and of every network weight likewise."""
+    gradient sign is unambiguous, and of every network weight likewise; for both table layouts
+    (interleaved records + touched bitmap, dense arrays)."""
     from paper_2311_15439_gb300.build import build
     build()
     P = 4096
-    tr = _make(P)
+    tr = _make(P, layout=layout)
+    assert tr.tab.layout == layout
     x = synth.uniform_points(P, 2, 5)
     tgt = synth.ProceduralImage(6, size=4096, n_waves=16).sample(x)
     F, L, T = 2, 8, 1 << 12
@@ -46,8 +49,8 @@ def test_one_step_matches_oracle():
     tr.enc.encode_fwd(xd, tr.tables, tr.enc_out)
     tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, td, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
                         workspace=tr.ws)
-    tr.enc.encode_bwd(xd, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
-    g_tab = tr.state[:, 3 * F:].cpu().numpy().copy()
+    tr.tab.backward(xd, tr.d_enc)
+    g_tab = tr.table_grads().reshape(L * T, F).cpu().numpy().copy()
     g_W = tr.dW.cpu().numpy().copy()
     loss_gpu = tr.loss()
 
@@ -81,7 +84,8 @@ def test_one_step_matches_oracle():
 
     # optimiser: Adam at t = 1 moves each parameter by -lr * g / (|g| + eps); compare where the
     # sign of the gradient is unambiguous (|g_ref| well above the tolerance)
-    tr.adam_tables.step_touched(1, tr.state, tr.touched, tr.tables, F)
+    tr.adam_tables.advance(tr.t_dev, tr.corrections)                 # t = 1 on the device
+    tr.tab.adam(tr.adam_tables, tr.corrections)
     tr.adam_mlp.step(1, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
     hp = dict(lr=float(np.float32(1e-2)), beta1=float(np.float32(0.9)), beta2=float(np.float32(0.99)),
               eps=float(np.float32(1e-15)))
@@ -89,7 +93,7 @@ def test_one_step_matches_oracle():
     den_all = np.concatenate([den_bound[l] for l in range(L)])
     p_ref, _, _ = OA.adam_step(p_tab0, g_all, np.zeros_like(g_all), np.zeros_like(g_all), 1, skip_zero_grad=True, **hp)
     clear = ((np.abs(g_all) > 4 * tol * den_all) | (den_all == 0)) & ~shaky
-    p_gpu = tr.state[:, :F].cpu().numpy()
+    p_gpu = tr.table_params().reshape(L * T, F).cpu().numpy()
     np.testing.assert_allclose(p_gpu[clear], p_ref[clear], rtol=0, atol=2e-6)
     assert (clear & (den_all > 0)).sum() > 200           # the comparison covers many updated entries
     gW_ref = np.concatenate([a.ravel() for a in dW_ref])
@@ -296,7 +300,7 @@ def test_graph_replay_equals_eager_steps():
     # equal up to the order of the binary32 atomics of the table backward (which then feeds the
     # next steps' encodings and network gradients)
     _close_up_to_atomics(a.W, b.W, steps=6, atol=1e-5)
-    _close_up_to_atomics(a.state, b.state, steps=6)
+    _close_up_to_atomics(a.table_params(), b.table_params(), steps=6)
     assert a.loss() == pytest.approx(b.loss(), rel=1e-3)
 
 
@@ -306,7 +310,7 @@ def test_overlapped_table_step_equals_plain_step(k):
     the backward of the next runs, gives the plain two-pass step's parameters (equal up to the
     order of the binary32 atomics), eagerly and replayed from a CUDA graph."""
     P = 4096
-    a, b = _make(P, seed=12), _make(P, seed=12)
+    a, b = _make(P, seed=12, layout="records"), _make(P, seed=12, layout="records")
     b.set_table_chunks(k)
     assert len(b.chunks) == k and b.chunks[0][0] == 0 and b.chunks[-1][1] == CFG["n_levels"]
     assert all(c[1] == n[0] for c, n in zip(b.chunks, b.chunks[1:]))
@@ -379,4 +383,24 @@ def test_host_feed_equals_eager_steps():
     assert a.t == b.t == 8
     assert got == pytest.approx(want, rel=1e-3)
     _close_up_to_atomics(a.W, b.W, steps=8, atol=1e-5)
-    _close_up_to_atomics(a.state, b.state, steps=8)
+    _close_up_to_atomics(a.table_params(), b.table_params(), steps=8)
+
+
+def test_table_layouts_train_alike():
+    """The interleaved-record layout (touched bitmap, sweep over the touched records) and the dense
+    layout (dense gradient array, dense Adam skipping zero gradients) take the same steps."""
+    P = 4096
+    a, b = _make(P, seed=14, layout="records"), _make(P, seed=14, layout="dense")
+    img = synth.ProceduralImage(6, size=1024, n_waves=4)
+    for i in range(4):
+        x = synth.uniform_points(P, 2, 90 + i)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(img.sample(x)).cuda()
+        a.step(xd, td)
+        b.step(xd, td)
+        if i == 0:
+            assert a.loss() == b.loss()                  # same first forward pass
+    torch.cuda.synchronize()
+    _close_up_to_atomics(a.W, b.W, steps=4, atol=1e-5)
+    _close_up_to_atomics(a.table_params(), b.table_params(), steps=4)
+    _close_up_to_atomics(a.tables.float(), b.tables.float(), steps=4)
+    assert int(a.touched.abs().sum().item()) == 0 and float(b.tab.grad.abs().max()) == 0.0
