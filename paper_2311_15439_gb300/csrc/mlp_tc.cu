@@ -99,9 +99,8 @@ __device__ __forceinline__ T* cm(unsigned char* base, int n, int k, int K) {
 
 // Write W (global [fan_out][fan_in]) as B operand [fan_out][fan_in] and its transpose
 // [fan_in][fan_out], rows of the output layer past n_out zero.
-template <typename T, int N_IN, int NH>
+template <typename T, int N_IN, int NH, typename S = TcSmem<N_IN, NH>>
 __device__ void load_weights_cm(const T* __restrict__ W, int n_out, unsigned char* sm) {
-  using S = TcSmem<N_IN, NH>;
   const T zero = from_f32<T>(0.f);
   for (int i = threadIdx.x; i < kW * N_IN; i += blockDim.x) {
     const int o = i / N_IN, c = i % N_IN;
@@ -398,6 +397,319 @@ mlp_train_tc_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P
   }
 }
 
+// ---- two tiles in flight per CTA ----------------------------------------------------------
+// The kernel above runs each tile's products strictly in sequence (issue, wait, epilogue, next
+// product), so the tensor cores idle during the epilogues and the mma.sync weight gradients.
+// This one runs two tiles per CTA at once: warps 0-3 (group 0) and warps 4-7 (group 1) each
+// own a tile, its shared-memory buffers, 64 TMEM columns, an mbarrier and a named barrier, and
+// step through the same sequence independently, so that one group's products run on the tensor
+// cores while the other group is in an epilogue or in its weight gradients.  Thread q*32 + lane
+// of a group (warp 4g + q) holds row 32 q + lane of its tile, which is TMEM lane 32 q + lane.
+// The weights are staged once and shared.  Each group writes its own row of weight-gradient
+// partials (rows 2 b and 2 b + 1 of CTA b), summed in a fixed order afterwards.
+template <int N_IN, int NH>
+struct Tc2Smem {
+  static constexpr int X = 0;                                 // per group: [128][N_IN]
+  static constexpr int H = X + kM * N_IN * 2;                 // NH x [128][64]
+  static constexpr int DH = H + NH * kM * kW * 2;             // NH x [128][64]
+  static constexpr int DY = DH + NH * kM * kW * 2;            // [128][16]
+  static constexpr int GROUP = DY + kM * 16 * 2;              // bytes of one group's buffers
+  static constexpr int W0 = 2 * GROUP;                        // shared weights, as TcSmem
+  static constexpr int WH = W0 + kW * N_IN * 2;
+  static constexpr int WO = WH + (NH - 1) * kW * kW * 2;
+  static constexpr int WOT = WO + 16 * kW * 2;
+  static constexpr int WHT = WOT + kW * 16 * 2;
+  static constexpr int W0T = WHT + (NH - 1) * kW * kW * 2;
+  static constexpr int END = W0T + N_IN * kW * 2;
+  // weight-gradient m16n8 tiles per warp of a group: output layer 2 (nt = q, q + 4), hidden
+  // layer 8 each (nt = q, q + 4; mt = 0..3), first layer N_IN / 8 (see first_tile)
+  static constexpr int N8 = N_IN / 8;
+  static constexpr int T_OUT = 2, T_HID = 8, T_FIRST = N8;
+  static constexpr int TILES = T_OUT + (NH - 1) * T_HID + T_FIRST;
+  static constexpr int FIRST_NT = N8 >= 4 ? N8 / 4 : 1;      // n-tiles of the first layer per warp
+  static constexpr int FIRST_MT = N8 >= 4 ? 4 : 2;            // m-tiles per n-tile
+};
+
+__device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// true on every thread of the 128-thread group if `p` holds on any of them (a barrier too)
+__device__ __forceinline__ bool group_any(int id, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, %2, 128, q;\n selp.u32 %0, 1, 0, o;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(id)
+      : "memory");
+  return r != 0;
+}
+
+// (mt, nt) of weight-gradient tile `i` of warp q of a group, and where its values go in the
+// [fan_out][fan_in] parameter block: base offset, fan_in, rows kept
+template <int N_IN, int NH>
+__device__ __forceinline__ void tc2_tile(int i, int q, int n_out, int& mt, int& nt, int& base, int& fan_in,
+                                         int& rows) {
+  using S = Tc2Smem<N_IN, NH>;
+  const int off_h = kW * N_IN, off_o = off_h + (NH - 1) * kW * kW;
+  if (i < S::T_OUT) {
+    mt = 0; nt = q + 4 * i; base = off_o; fan_in = kW; rows = n_out;
+  } else if (i < S::T_OUT + (NH - 1) * S::T_HID) {
+    const int j = i - S::T_OUT, h = j / S::T_HID, r = j % S::T_HID;
+    mt = r % 4; nt = q + 4 * (r / 4); base = off_h + h * kW * kW; fan_in = kW; rows = kW;
+  } else {
+    const int r = i - S::T_OUT - (NH - 1) * S::T_HID;
+    const int j = r / S::FIRST_MT, k = r % S::FIRST_MT;
+    nt = S::N8 >= 4 ? q + 4 * j : q % 2;
+    mt = S::N8 >= 4 ? k : q / 2 + 2 * k;
+    base = 0; fan_in = N_IN; rows = kW;
+  }
+}
+
+template <typename T, int N_IN, int NH, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
+                     const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
+                     float* __restrict__ din, int din_group, float* __restrict__ ws, int64_t n_params) {
+  using S = Tc2Smem<N_IN, NH>;
+  constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ float sq_part[8];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp >> 2, q = warp & 3, bar_id = 1 + g;
+  const bool issuer = (tid & 127) == 0;
+  const int r = q * 32 + lane;                          // this thread's tile row / TMEM lane
+  const int64_t n_tiles = (P + kM - 1) / kM;
+  const float inv_count = 2.f / (float)((double)P * n_out);
+  const float inv_scale = 1.f / loss_scale;
+  unsigned char* gs = sm + g * S::GROUP;                // this group's buffers
+
+  load_weights_cm<T, N_IN, NH, S>(W, n_out, sm);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * kTmemCols);
+  tc::fence_smem_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base + (uint32_t)(g * kTmemCols);
+  const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  float dw[S::TILES][4];
+#pragma unroll
+  for (int i = 0; i < S::TILES; ++i) dw[i][0] = dw[i][1] = dw[i][2] = dw[i][3] = 0.f;
+  float sq = 0.f;
+
+  auto issue = [&](const unsigned char* A, const unsigned char* B, int K, int N) {
+    tc::fence_smem_async();
+    tc::fence_before_sync();
+    group_sync(bar_id);
+    if (issuer) {
+      tc::fence_after_sync();
+      issue_gemm(tmem, A, B, K, tc::idesc_f16(kM, N, BF16));
+      tc::commit(&mbar[g]);
+    }
+  };
+  auto wait = [&]() -> bool {
+    const bool ok = tc::mbar_wait(&mbar[g], phase, kWaitPolls);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    return !group_any(bar_id, !ok);
+  };
+
+  for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < n_tiles; tile += 2 * (int64_t)gridDim.x) {
+    const int64_t row0 = tile * kM;
+    for (int i = r; i < kM * (N_IN / 8); i += 128) {
+      const int rr = i / (N_IN / 8), c = (i % (N_IN / 8)) * 8;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (row0 + rr < P) v = __ldg(reinterpret_cast<const uint4*>(in + (row0 + rr) * N_IN + c));
+      *reinterpret_cast<uint4*>(gs + S::X + tc::cm_offset(rr, c, N_IN)) = v;
+    }
+    // ---- forward
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      if (h == 0) issue(gs + S::X, sm + S::W0, N_IN, kW);
+      else issue(gs + S::H + (h - 1) * kM * kW * 2, sm + S::WH + (h - 1) * kW * kW * 2, kW, kW);
+      if (!wait()) { failed = true; break; }
+#pragma unroll
+      for (int c0 = 0; c0 < kW; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+        store16<T>(gs + S::H + h * kM * kW * 2, r, c0, kW, v);
+      }
+    }
+    if (failed) break;
+    issue(gs + S::H + (NH - 1) * kM * kW * 2, sm + S::WO, kW, 16);
+    if (!wait()) { failed = true; break; }
+    // ---- output delta
+    {
+      float v[16];
+      tc::tmem_ld16(lane_addr, v);
+      const int64_t row = row0 + r;
+#pragma unroll
+      for (int o = 0; o < 16; ++o) {
+        float dyo = 0.f;
+        if (row < P && o < n_out) {
+          if (MODE == 0) {
+            dyo = dout[row * n_out + o] * loss_scale;
+          } else {
+            const float res = v[o] - target[row * n_out + o];
+            sq = fmaf(res, res, sq);
+            dyo = res * inv_count * loss_scale;
+          }
+        }
+        v[o] = dyo;
+      }
+      store16<T>(gs + S::DY, r, 0, 16, v);
+    }
+    // ---- hidden deltas, top layer down
+#pragma unroll
+    for (int h = NH - 1; h >= 0; --h) {
+      if (h == NH - 1) issue(gs + S::DY, sm + S::WOT, 16, kW);
+      else issue(gs + S::DH + (h + 1) * kM * kW * 2, sm + S::WHT + h * kW * kW * 2, kW, kW);
+      if (!wait()) { failed = true; break; }
+#pragma unroll
+      for (int c0 = 0; c0 < kW; c0 += 16) {
+        float v[16], a[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+        load16<T>(gs + S::H + h * kM * kW * 2, r, c0, kW, a);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = a[j] > 0.f ? v[j] : 0.f;
+        store16<T>(gs + S::DH + h * kM * kW * 2, r, c0, kW, v);
+      }
+    }
+    if (failed) break;
+    // ---- dX = dH_0 W_0 on the tensor cores; the weight gradients on mma.sync meanwhile
+    issue(gs + S::DH, sm + S::W0T, kW, N_IN);
+    {
+      const int gq = lane >> 2, t4 = lane & 3, lo = lane >> 3, rr = lane & 7;
+      (void)gq; (void)t4;
+      const int arow = (lo >> 1) * 8 + rr, acol = (lo & 1) * 8, brow = (lo & 1) * 8 + rr;
+      {                                                 // output layer: tiles 0, 1 (nt = q, q + 4)
+        const uint32_t dl = tc::smem_u32(gs + S::DY), il = tc::smem_u32(gs + S::H + (NH - 1) * kM * kW * 2);
+#pragma unroll
+        for (int ks = 0; ks < kM / 16; ++ks) {
+          uint32_t a[4];
+          ldsm_x4_trans(a, dl + tc::cm_offset(ks * 16 + arow, acol, 16));
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            uint32_t b0, b1;
+            ldsm_x2_trans(b0, b1, il + tc::cm_offset(ks * 16 + brow, (q + 4 * j) * 8, kW));
+            mma16816<T>(dw[j], a, b0, b1);
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 1; h < NH; ++h) {                   // hidden h: nt = q, q + 4; mt = 0..3
+        const uint32_t dl = tc::smem_u32(gs + S::DH + h * kM * kW * 2);
+        const uint32_t il = tc::smem_u32(gs + S::H + (h - 1) * kM * kW * 2);
+#pragma unroll
+        for (int ks = 0; ks < kM / 16; ++ks) {
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            uint32_t b0, b1;
+            ldsm_x2_trans(b0, b1, il + tc::cm_offset(ks * 16 + brow, (q + 4 * j) * 8, kW));
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+              uint32_t a[4];
+              ldsm_x4_trans(a, dl + tc::cm_offset(ks * 16 + arow, mt * 16 + acol, kW));
+              mma16816<T>(dw[S::T_OUT + (h - 1) * S::T_HID + j * 4 + mt], a, b0, b1);
+            }
+          }
+        }
+      }
+      {                                                 // first layer
+        const uint32_t dl = tc::smem_u32(gs + S::DH), il = tc::smem_u32(gs + S::X);
+        constexpr int base = S::T_OUT + (NH - 1) * S::T_HID;
+#pragma unroll
+        for (int ks = 0; ks < kM / 16; ++ks) {
+#pragma unroll
+          for (int j = 0; j < S::FIRST_NT; ++j) {
+            const int nt = S::N8 >= 4 ? q + 4 * j : q % 2;
+            uint32_t b0, b1;
+            ldsm_x2_trans(b0, b1, il + tc::cm_offset(ks * 16 + brow, nt * 8, N_IN));
+#pragma unroll
+            for (int k = 0; k < S::FIRST_MT; ++k) {
+              const int mt = S::N8 >= 4 ? k : q / 2 + 2 * k;
+              uint32_t a[4];
+              ldsm_x4_trans(a, dl + tc::cm_offset(ks * 16 + arow, mt * 16 + acol, kW));
+              mma16816<T>(dw[base + j * S::FIRST_MT + k], a, b0, b1);
+            }
+          }
+        }
+      }
+    }
+    if (!wait()) { failed = true; break; }
+    // ---- input gradient
+    {
+      const int64_t row = row0 + r;
+#pragma unroll
+      for (int c0 = 0; c0 < N_IN; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+        if (din && row < P) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const int col = c0 + j;
+            const float2 val = make_float2(v[j] * inv_scale, v[j + 1] * inv_scale);
+            if (din_group == 0) {
+              *reinterpret_cast<float2*>(din + row * N_IN + col) = val;
+            } else if (din_group == 1) {
+              din[(int64_t)col * P + row] = val.x;
+              din[(int64_t)(col + 1) * P + row] = val.y;
+            } else {
+              *reinterpret_cast<float2*>(din + ((int64_t)(col / din_group) * P + row) * din_group + col % din_group) =
+                  val;
+            }
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    group_sync(bar_id);                                 // the tile's buffers are free again
+  }
+
+  // ---- per-group partials (both groups reach this point; a failed group left its loop whole)
+  if (failed && (tid & 127) == 0) atomicExch(&g_tc_error, 1);
+  float* wsb = ws + (2 * (int64_t)blockIdx.x + g) * n_params;
+  {
+    const int gq = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int i = 0; i < S::TILES; ++i) {
+      int mt, nt, base, fan_in, rows;
+      tc2_tile<N_IN, NH>(i, q, n_out, mt, nt, base, fan_in, rows);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = mt * 16 + gq + (e >> 1) * 8, n = nt * 8 + 2 * t4 + (e & 1);
+        if (m < rows) wsb[base + m * fan_in + n] = dw[i][e];
+      }
+    }
+  }
+  if (MODE == 1) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) sq_part[warp] = sq;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (MODE == 1 && (tid & 127) == 0) {
+    float s = 0.f;
+    for (int w = 4 * g; w < 4 * g + 4; ++w) s += sq_part[w];
+    ws[(int64_t)2 * gridDim.x * n_params + 2 * blockIdx.x + g] = s;
+  }
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem_base, 2 * kTmemCols);
+  }
+}
+
 }  // namespace
 }  // namespace sxe
 
@@ -418,6 +730,34 @@ int tc_ctas_per_sm() {
   return cached;
 }
 
+// Two-tile kernel: one CTA per SM, two partial rows per CTA (the workspace holds `grid` rows).
+constexpr int kMaxDynSmem = 227 * 1024;
+
+template <typename T, int N_IN, int NH>
+sxe_status tc2_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                      float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, int sms,
+                      cudaStream_t s) {
+  constexpr int bytes = Tc2Smem<N_IN, NH>::END;
+  const int64_t n_params = sxe_mlp_n_params(d);
+  const int64_t n_tiles = (P + kM - 1) / kM;
+  const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)sms, (int64_t)(grid / 2), (n_tiles + 1) / 2}));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(mlp_train_tc2_kernel<T, N_IN, NH, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(mlp_train_tc2_kernel<T, N_IN, NH, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr = true;
+  }
+  if (target)
+    mlp_train_tc2_kernel<T, N_IN, NH, 1><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
+                                                                    target, ls, din, dg, ws, n_params);
+  else
+    mlp_train_tc2_kernel<T, N_IN, NH, 0><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
+                                                                    target, ls, din, dg, ws, n_params);
+  sxe_status st = check_launch("mlp_train_tc2");
+  if (st != SXE_OK) return st;
+  return launch_mlp_reduce(ws, 2 * g2, n_params, 1.f / ls, dW, target ? sq : nullptr, s);
+}
+
 template <typename T, int N_IN, int NH>
 sxe_status tc_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
                      float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
@@ -426,6 +766,9 @@ sxe_status tc_launch(const sxe_mlp_desc* d, const void* W, const void* in, const
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if constexpr (Tc2Smem<N_IN, NH>::END <= kMaxDynSmem) {
+    if (grid >= 2) return tc2_launch<T, N_IN, NH>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, sms, s);
+  }
   if (target) {
     grid = std::min(grid, sms * tc_ctas_per_sm<T, N_IN, NH, 1>());
     mlp_train_tc_kernel<T, N_IN, NH, 1><<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
