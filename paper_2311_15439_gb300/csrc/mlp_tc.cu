@@ -464,7 +464,12 @@ __device__ __forceinline__ void tc2_tile(int i, int q, int n_out, int& mt, int& 
   }
 }
 
-template <typename T, int N_IN, int NH, int MODE>
+// TCW: the weight gradients on tcgen05 as well.  dW_out^T = H_last^T dY (64 x 16), dW_h = dH_h^T
+// H_{h-1} (64 x 64) and dW_0 = dH_0^T X (64 x N_IN) are M = 64 products over the tile's 128
+// points, whose operands are the tile's activation, delta and input buffers read as MN-major
+// operands; they accumulate in TMEM (256 columns per group) over the whole persistent loop and
+// are read out once at the end.  Without TCW they run on mma.sync into registers.
+template <typename T, int N_IN, int NH, int MODE, bool TCW>
 __global__ void __launch_bounds__(kThreads, 1)
 mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
                      const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
@@ -490,20 +495,36 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * kTmemCols);
+  constexpr uint32_t kGroupCols = TCW ? 256u : kTmemCols;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * kGroupCols);
   tc::fence_smem_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = tmem_base + (uint32_t)(g * kTmemCols);
+  const uint32_t tmem = tmem_base + (uint32_t)g * kGroupCols;
   const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+  // TCW accumulators: dW_out^T at column 64, dW_h at 80 + 64 (h - 1), dW_0 after them
+  const uint32_t c_out = tmem + 64u, c_first = tmem + 80u + 64u * (NH - 1);
+  static_assert(!TCW || 80 + 64 * (NH - 1) + N_IN <= 256, "TMEM columns of one group");
   uint32_t phase = 0;
-  bool failed = false;
+  bool failed = false, any_tile = false;
 
-  float dw[S::TILES][4];
+  float dw[TCW ? 1 : S::TILES][4];
 #pragma unroll
-  for (int i = 0; i < S::TILES; ++i) dw[i][0] = dw[i][1] = dw[i][2] = dw[i][3] = 0.f;
+  for (int i = 0; i < (TCW ? 1 : S::TILES); ++i) dw[i][0] = dw[i][1] = dw[i][2] = dw[i][3] = 0.f;
   float sq = 0.f;
+
+  // M = 64 weight-gradient product over the tile's 128 points (8 MMAs of K = 16): A' and B' are
+  // MN-major views of [points][features] tiles whose 8-point core-matrix rows are kA / kB bytes
+  // apart per 8 points; the 8-feature blocks are 128 bytes apart
+  auto wgrad = [&](uint32_t d, const unsigned char* A, uint32_t kA, const unsigned char* B, uint32_t kB, int N,
+                   bool first) {
+    const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B), id = tc::idesc_f16_mn(64, N, BF16);
+#pragma unroll
+    for (int ks = 0; ks < kM / 16; ++ks)
+      tc::mma_f16(d, tc::smem_desc(a0 + ks * 2 * kA, kA, 128u), tc::smem_desc(b0 + ks * 2 * kB, kB, 128u), id,
+                  !(first && ks == 0));
+  };
 
   auto issue = [&](const unsigned char* A, const unsigned char* B, int K, int N) {
     tc::fence_smem_async();
@@ -522,13 +543,35 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
     return !group_any(bar_id, !ok);
   };
 
+  // the tile's inputs are loaded into registers one tile ahead (item i = r + 128 j of the
+  // tile's 128 x N_IN / 8 sixteen-byte pieces), so their latency hides behind a whole tile
+  constexpr int kPieces = N_IN / 8;                     // per thread: 128 rows x N_IN / 8 / 128
+  uint4 pf[kPieces];
+  auto prefetch = [&](int64_t t) {
+#pragma unroll
+    for (int j = 0; j < kPieces; ++j) {
+      const int i = r + 128 * j, rr = i / (N_IN / 8), c = (i % (N_IN / 8)) * 8;
+      const int64_t row = t * kM + rr;
+      pf[j] = (t < n_tiles && row < P) ? __ldg(reinterpret_cast<const uint4*>(in + row * N_IN + c))
+                                       : make_uint4(0, 0, 0, 0);
+    }
+  };
+  prefetch(2 * (int64_t)blockIdx.x + g);
   for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < n_tiles; tile += 2 * (int64_t)gridDim.x) {
     const int64_t row0 = tile * kM;
-    for (int i = r; i < kM * (N_IN / 8); i += 128) {
-      const int rr = i / (N_IN / 8), c = (i % (N_IN / 8)) * 8;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (row0 + rr < P) v = __ldg(reinterpret_cast<const uint4*>(in + (row0 + rr) * N_IN + c));
-      *reinterpret_cast<uint4*>(gs + S::X + tc::cm_offset(rr, c, N_IN)) = v;
+#pragma unroll
+    for (int j = 0; j < kPieces; ++j) {
+      const int i = r + 128 * j, rr = i / (N_IN / 8), c = (i % (N_IN / 8)) * 8;
+      *reinterpret_cast<uint4*>(gs + S::X + tc::cm_offset(rr, c, N_IN)) = pf[j];
+    }
+    prefetch(tile + 2 * (int64_t)gridDim.x);
+    // this row's targets (L2 loss) or upstream gradients, needed after the forward products
+    float yin[16];
+    {
+      const int64_t row = row0 + r;
+      const float* src = MODE == 0 ? dout : target;
+#pragma unroll
+      for (int o = 0; o < 16; ++o) yin[o] = (row < P && o < n_out) ? __ldg(src + row * n_out + o) : 0.f;
     }
     // ---- forward
 #pragma unroll
@@ -537,12 +580,16 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
       else issue(gs + S::H + (h - 1) * kM * kW * 2, sm + S::WH + (h - 1) * kW * kW * 2, kW, kW);
       if (!wait()) { failed = true; break; }
 #pragma unroll
-      for (int c0 = 0; c0 < kW; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+      for (int c0 = 0; c0 < kW; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-        store16<T>(gs + S::H + h * kM * kW * 2, r, c0, kW, v);
+        for (int half = 0; half < 2; ++half) {
+          float u[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) u[j] = fmaxf(v[16 * half + j], 0.f);
+          store16<T>(gs + S::H + h * kM * kW * 2, r, c0 + 16 * half, kW, u);
+        }
       }
     }
     if (failed) break;
@@ -558,9 +605,9 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
         float dyo = 0.f;
         if (row < P && o < n_out) {
           if (MODE == 0) {
-            dyo = dout[row * n_out + o] * loss_scale;
+            dyo = yin[o] * loss_scale;
           } else {
-            const float res = v[o] - target[row * n_out + o];
+            const float res = v[o] - yin[o];
             sq = fmaf(res, res, sq);
             dyo = res * inv_count * loss_scale;
           }
@@ -576,17 +623,40 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
       else issue(gs + S::DH + (h + 1) * kM * kW * 2, sm + S::WHT + h * kW * kW * 2, kW, kW);
       if (!wait()) { failed = true; break; }
 #pragma unroll
-      for (int c0 = 0; c0 < kW; c0 += 16) {
-        float v[16], a[16];
-        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
-        load16<T>(gs + S::H + h * kM * kW * 2, r, c0, kW, a);
+      for (int c0 = 0; c0 < kW; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = a[j] > 0.f ? v[j] : 0.f;
-        store16<T>(gs + S::DH + h * kM * kW * 2, r, c0, kW, v);
+        for (int half = 0; half < 2; ++half) {
+          float a[16], u[16];
+          load16<T>(gs + S::H + h * kM * kW * 2, r, c0 + 16 * half, kW, a);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) u[j] = a[j] > 0.f ? v[16 * half + j] : 0.f;
+          store16<T>(gs + S::DH + h * kM * kW * 2, r, c0 + 16 * half, kW, u);
+        }
       }
     }
     if (failed) break;
-    // ---- dX = dH_0 W_0 on the tensor cores; the weight gradients on mma.sync meanwhile
+    // ---- dX = dH_0 W_0 on the tensor cores; the weight gradients on tcgen05 with it (TCW) or on
+    // mma.sync meanwhile
+    if constexpr (TCW) {
+      tc::fence_smem_async();
+      tc::fence_before_sync();
+      group_sync(bar_id);
+      if (issuer) {
+        tc::fence_after_sync();
+        constexpr uint32_t kH = (kW / 8) * 128, kDY = (16 / 8) * 128, kX = (N_IN / 8) * 128;
+        wgrad(c_out, gs + S::H + (NH - 1) * kM * kW * 2, kH, gs + S::DY, kDY, 16, !any_tile);
+#pragma unroll
+        for (int h = 1; h < NH; ++h)
+          wgrad(tmem + 80u + 64u * (h - 1), gs + S::DH + h * kM * kW * 2, kH, gs + S::H + (h - 1) * kM * kW * 2, kH,
+                kW, !any_tile);
+        wgrad(c_first, gs + S::DH, kH, gs + S::X, kX, N_IN, !any_tile);
+        issue_gemm(tmem, gs + S::DH, sm + S::W0T, kW, tc::idesc_f16(kM, N_IN, BF16));
+        tc::commit(&mbar[g]);
+      }
+      any_tile = true;
+    } else {
     issue(gs + S::DH, sm + S::W0T, kW, N_IN);
     {
       const int gq = lane >> 2, t4 = lane & 3, lo = lane >> 3, rr = lane & 7;
@@ -646,6 +716,7 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
         }
       }
     }
+    }
     if (!wait()) { failed = true; break; }
     // ---- input gradient
     {
@@ -679,7 +750,33 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
   // ---- per-group partials (both groups reach this point; a failed group left its loop whole)
   if (failed && (tid & 127) == 0) atomicExch(&g_tc_error, 1);
   float* wsb = ws + (2 * (int64_t)blockIdx.x + g) * n_params;
-  {
+  if constexpr (TCW) {
+    // row m = 16 q + lane of every M = 64 accumulator sits in lane 32 q + lane (lanes 0-15 of the
+    // warp); a group without a tile never wrote its accumulators and writes zeros
+    const int off_h = kW * N_IN, off_o = off_h + (NH - 1) * kW * kW;
+    const int m = 16 * q + lane;
+    const uint32_t la = (uint32_t)(q * 32) << 16;
+    float v[16];
+    tc::tmem_ld16(c_out + la, v);
+    if (lane < 16)
+      for (int o = 0; o < n_out; ++o) wsb[off_o + o * kW + m] = any_tile ? v[o] : 0.f;
+#pragma unroll
+    for (int h = 1; h < NH; ++h)
+#pragma unroll
+      for (int c0 = 0; c0 < kW; c0 += 16) {
+        tc::tmem_ld16(tmem + 80u + 64u * (h - 1) + la + (uint32_t)c0, v);
+        if (lane < 16)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) wsb[off_h + (h - 1) * kW * kW + m * kW + c0 + j] = any_tile ? v[j] : 0.f;
+      }
+#pragma unroll
+    for (int c0 = 0; c0 < N_IN; c0 += 16) {
+      tc::tmem_ld16(c_first + la + (uint32_t)c0, v);
+      if (lane < 16)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) wsb[m * N_IN + c0 + j] = any_tile ? v[j] : 0.f;
+    }
+  } else {
     const int gq = lane >> 2, t4 = lane & 3;
 #pragma unroll
     for (int i = 0; i < S::TILES; ++i) {
@@ -688,7 +785,7 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int m = mt * 16 + gq + (e >> 1) * 8, n = nt * 8 + 2 * t4 + (e & 1);
-        if (m < rows) wsb[base + m * fan_in + n] = dw[i][e];
+        if (m < rows) wsb[base + m * fan_in + n] = dw[TCW ? 0 : i][e];
       }
     }
   }
@@ -706,7 +803,7 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
   }
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem_base, 2 * kTmemCols);
+    tc::tmem_dealloc(tmem_base, 2 * kGroupCols);
   }
 }
 
@@ -737,22 +834,25 @@ template <typename T, int N_IN, int NH>
 sxe_status tc2_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
                       float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, int sms,
                       cudaStream_t s) {
-  constexpr int bytes = Tc2Smem<N_IN, NH>::END;
+  // at least 116 KB, so that one CTA (holding all 512 TMEM columns) runs per SM
+  constexpr int bytes = Tc2Smem<N_IN, NH>::END > 116 * 1024 ? Tc2Smem<N_IN, NH>::END : 116 * 1024;
   const int64_t n_params = sxe_mlp_n_params(d);
   const int64_t n_tiles = (P + kM - 1) / kM;
   const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)sms, (int64_t)(grid / 2), (n_tiles + 1) / 2}));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(mlp_train_tc2_kernel<T, N_IN, NH, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(mlp_train_tc2_kernel<T, N_IN, NH, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(mlp_train_tc2_kernel<T, N_IN, NH, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes);
+    cudaFuncSetAttribute(mlp_train_tc2_kernel<T, N_IN, NH, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes);
     attr = true;
   }
   if (target)
-    mlp_train_tc2_kernel<T, N_IN, NH, 1><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
-                                                                    target, ls, din, dg, ws, n_params);
+    mlp_train_tc2_kernel<T, N_IN, NH, 1, true><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out,
+                                                                          dout, target, ls, din, dg, ws, n_params);
   else
-    mlp_train_tc2_kernel<T, N_IN, NH, 0><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
-                                                                    target, ls, din, dg, ws, n_params);
+    mlp_train_tc2_kernel<T, N_IN, NH, 0, true><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out,
+                                                                          dout, target, ls, din, dg, ws, n_params);
   sxe_status st = check_launch("mlp_train_tc2");
   if (st != SXE_OK) return st;
   return launch_mlp_reduce(ws, 2 * g2, n_params, 1.f / ls, dW, target ? sq : nullptr, s);

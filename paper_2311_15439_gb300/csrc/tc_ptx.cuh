@@ -38,6 +38,20 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with A and B "MN-major" (transposed): operand element (mn, k) stored with 8 consecutive
+// MN elements in 16 contiguous bytes and the 8 k of a core matrix 16 bytes apart.  For these the
+// descriptor's leading-dimension offset is the distance between core matrices adjacent in K and
+// the stride-dimension offset the distance between core matrices adjacent in MN (measured on
+// sm_103a with exactly representable operands).  A tile stored K-major for M = points ([points]
+// [features], 8-feature core rows) is thus read, unchanged, as the MN-major operand of a product
+// that reduces over the points.
+__host__ __device__ constexpr uint32_t idesc_f16_mn(int M, int N, bool bf16) {
+  return idesc_f16(M, N, bf16) | (1u << 15) | (1u << 16);
+}
+
+// Accumulator rows of an M = 64 product (cta_group::1) sit in TMEM lanes 32 (m / 16) + m % 16:
+// warp w % 4 reads rows 16 (w % 4) .. +15 from its lanes 0-15 (measured on sm_103a).
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(dst_smem)),
                "r"(ncols) : "memory");
@@ -93,6 +107,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane, loaded and waited for in one statement
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 }  // namespace tc
