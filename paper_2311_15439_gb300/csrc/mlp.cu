@@ -107,6 +107,11 @@ struct Smem {
   static constexpr int DY = D + NH * kTile * kSW;               // [128][kSO]    output delta
   static constexpr int FWD_END = A;                             // forward-only kernels stop here
   static constexpr int END = DY + kTile * kSO;
+  // training kernel: an unpadded [128][N_IN] staging buffer that cp.async fills with the next
+  // tile's inputs while the current tile computes, where two CTAs per SM still fit with it
+  static constexpr int XS = END;
+  static constexpr bool PF = (END + kTile * N_IN) * 2 <= 113 * 1024;
+  static constexpr int BWD_END = END + (PF ? kTile * N_IN : 0);
   // weight-gradient tiles: output layer 1x8, hidden 4x8 each, first layer 4x(N_IN/8)
   static constexpr int N_WTILES = 8 + (NH - 1) * 32 + 4 * (N_IN / 8);
   static constexpr int TILES_PER_WARP = (N_WTILES + kWarps - 1) / kWarps;
@@ -330,7 +335,14 @@ vr_field_mlp_kernel(const T* __restrict__ Wd, const T* __restrict__ Wc, const T*
 // and the squared residuals are summed into *sq_sum.
 // Two CTAs per SM where the shared-memory plan allows it (then at most 128 registers).
 template <int N_IN, int NH>
-struct BwdOcc { static constexpr int value = Smem<N_IN, NH>::END * 2 <= 110 * 1024 ? 2 : 1; };
+struct BwdOcc { static constexpr int value = Smem<N_IN, NH>::BWD_END * 2 <= 113 * 1024 ? 2 : 1; };
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <typename T, int N_IN, int NH, int MODE>
 __global__ void __launch_bounds__(kThreads, BwdOcc<N_IN, NH>::value)
@@ -350,11 +362,39 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
 #pragma unroll
   for (int i = 0; i < S::TILES_PER_WARP; ++i) dw[i][0] = dw[i][1] = dw[i][2] = dw[i][3] = 0.f;
   float sq = 0.f;
+  // inputs one tile ahead: each thread cp.asyncs its own 16-byte pieces of the next tile into the
+  // staging buffer and later moves exactly those pieces into the padded tile, so it waits only for
+  // its own copies (rows past P are zero-filled)
+  constexpr int VPR = N_IN * 2 / 16;
+  constexpr int PIECES = kTile * VPR / kThreads;
+  static_assert(!S::PF || (kTile * VPR) % kThreads == 0, "staging pieces per thread");
+  auto stage = [&](int64_t tl) {
+#pragma unroll
+    for (int j = 0; j < PIECES; ++j) {
+      const int i = threadIdx.x + j * kThreads, rr = i / VPR, c = i % VPR;
+      const int64_t row = tl * kTile + rr;
+      const bool valid = tl < n_tiles && row < P;
+      cp_async16(sm + S::XS + rr * N_IN + c * 8, valid ? in + row * N_IN + c * 8 : in, valid);
+    }
+    cp_async_commit();
+  };
+  if constexpr (S::PF) stage(blockIdx.x);
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t row0 = tile * kTile;
     __syncthreads();
-    load_inputs<T, N_IN, NH>(in, row0, P, sm);
+    if constexpr (S::PF) {
+      cp_async_wait_all();
+#pragma unroll
+      for (int j = 0; j < PIECES; ++j) {
+        const int i = threadIdx.x + j * kThreads, rr = i / VPR, c = i % VPR;
+        *reinterpret_cast<uint4*>(sm + S::X + rr * S::SX + c * 8) =
+            *reinterpret_cast<const uint4*>(sm + S::XS + rr * N_IN + c * 8);
+      }
+      stage(tile + gridDim.x);
+    } else {
+      load_inputs<T, N_IN, NH>(in, row0, P, sm);
+    }
     __syncthreads();
     float y[2][4];
     uint32_t hfr[NH][4][4];
@@ -520,6 +560,7 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
       }
     }
   }
+  if constexpr (S::PF) cp_async_wait_all();     // the last staging copies (zero fill) have landed
   // ---- per-CTA partials to the workspace
   float* wsb = ws + (int64_t)blockIdx.x * n_params;
   const int off_h = kWidth * N_IN;
@@ -631,7 +672,7 @@ int bwd_ctas_per_sm() {
   static int cached = 0;
   if (cached == 0) {
     auto k = mlp_bwd_kernel<T, N_IN, NH, MODE>;
-    const int bytes = Smem<N_IN, NH>::END * (int)sizeof(T);
+    const int bytes = Smem<N_IN, NH>::BWD_END * (int)sizeof(T);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, bytes) != cudaSuccess || n < 1) n = 1;
@@ -710,7 +751,7 @@ sxe_status bwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
                       float loss_scale, int64_t P, float* din, float* dW, float* sq_sum, float* ws, int grid,
                       cudaStream_t s, int din_group) {
   using S = Smem<N_IN, NH>;
-  const size_t bytes = (size_t)S::END * sizeof(T);
+  const size_t bytes = (size_t)S::BWD_END * sizeof(T);
   const int64_t n_params = sxe_mlp_n_params(d);
   if (target) {
     auto k = mlp_bwd_kernel<T, N_IN, NH, 1>;
