@@ -171,14 +171,16 @@ def _stage_work(n_touched, F=2, L=16, d=2, width=64, n_in=32):
 
 
 def count_touched(tr, x):
-    """Entries that one batch touches (for the table stage's algorithmic bytes)."""
+    """Entries that one batch touches (for the table stage's algorithmic bytes), and the 32-byte
+    sectors of the fp16 table they lie in (8 entries of F = 2 fp16 values per sector: one byte
+    of the touched bitmap)."""
     import torch
     enc = tr.enc
     dense = torch.zeros(enc.table_shape(), dtype=torch.float32, device=x.device)
     bm = torch.zeros_like(tr.touched)
     enc.encode_bwd(x, torch.ones((x.shape[0], enc.n_out), device=x.device), dense, touched=bm)
-    bits = bm.cpu().numpy().view(np.uint32)
-    return int(np.unpackbits(bits.view(np.uint8)).sum())
+    bytes_ = bm.cpu().numpy().view(np.uint8)
+    return int(np.unpackbits(bytes_).sum()), int(np.count_nonzero(bytes_))
 
 
 def run_gpu(args):
@@ -251,7 +253,7 @@ def run_gpu(args):
                   for i, n in enumerate(names)}
     ms = max_over_ranks(ms, world, dev)
     loss = tr.loss()
-    n_touched = count_touched(tr, xd[0])
+    n_touched, n_sectors = count_touched(tr, xd[0])
 
     # ---- end to end through the public API (HostFeed): every step copies its batch from pinned
     # host memory to the device (copy stream, double-buffered), replays the recorded step and reads
@@ -321,6 +323,16 @@ def run_gpu(args):
             "predicted_ms": pred_bwd * 1e3, "measured_ms": per_kernel["encode_bwd"],
             "frac": pred_bwd * 1e3 / per_kernel["encode_bwd"],
             "model": "first touch of an entry = one random float2 reduction missing L2; later ones hit"}
+        gathers = contrib
+        pred_fwd = n_sectors / peaks_ra["gather_4B_table"] + (gathers - n_sectors) / peaks_ra["gather_4B_l2"]
+        line["gather_roofline"] = {
+            "kernel": "encode_fwd", "gathers": gathers, "table_sectors_touched": n_sectors,
+            "achieved_gathers_per_s": gathers / (per_kernel["encode_fwd"] / 1e3),
+            "achieved_over_random_gather_peak": gathers / (per_kernel["encode_fwd"] / 1e3) / peaks_ra["gather_4B_table"],
+            "predicted_ms": pred_fwd * 1e3, "measured_ms": per_kernel["encode_fwd"],
+            "frac": pred_fwd * 1e3 / per_kernel["encode_fwd"],
+            "model": "first gather from a 32-byte table sector = one random 4-byte gather missing L2 "
+                     "(probe over the fp16 tables); later ones hit (probe over 8 MiB)"}
         if comparators is not None:
             line["comparators"] = comparators
         if volume is not None:
@@ -394,7 +406,8 @@ def random_access_peaks(dev, state_bytes, table, n_ops=1 << 24, reps=5):
     tab = table.view(torch.float32).reshape(-1)
     cases = {"red_f2_miss": (0, buf, n_rec, 8), "red_f2_l2": (0, buf, 1 << 18, 8),
              "rmw_32B_random_order": (2, buf, n_rec, 8),
-             "gather_4B_table": (1, tab, 1 << int(math.log2(tab.numel())), 1)}
+             "gather_4B_table": (1, tab, 1 << int(math.log2(tab.numel())), 1),
+             "gather_4B_l2": (1, buf, 1 << 20, 2)}
     out = {}
     for name, (kind, b, slots, sf) in cases.items():
         if sf < 2:          # 4-byte gathers: slots of 2 floats over the first half of the table words
