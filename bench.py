@@ -281,6 +281,7 @@ def run_gpu(args):
     serving = serve_bench(dev) if (rank == 0 and not args.no_serve) else None
     peaks_ra = random_access_peaks(dev, tr.state.numel() * 4, tr.tables) if rank == 0 else None
     volume = volume_sweep(dev) if (rank == 0 and not args.no_volume) else None
+    sdf = sdf_train(dev) if (rank == 0 and not args.no_sweep) else None
 
     if rank == 0:
         value = job_throughput(BATCH, args.steps, world, ms)
@@ -337,6 +338,8 @@ def run_gpu(args):
             line["comparators"] = comparators
         if volume is not None:
             line["volume"] = volume
+        if sdf is not None:
+            line["sdf_train"] = sdf
         if serving is not None:
             line["serve"] = serving
         if not args.no_cpu:
@@ -495,6 +498,40 @@ def volume_train(dev, rays, S=64, steps=10, warmup=3):
         ms = a.elapsed_time(b) / steps
         out[kind] = {"ms_per_step": ms, "samples_per_s": R * S / (ms / 1e3), "table_layout": vt.tab.layout}
         del vt
+        torch.cuda.empty_cache()
+    out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]
+    return out
+
+
+def sdf_train(dev, P=1 << 20, steps=20, warmup=3, n_batches=4):
+    """SDF-style training step (d = 3, L = 16, F = 2, T = 2^19 bf16 tables, network 32-64-1 bf16,
+    2^20 points: half uniform in the unit cube, half within 0.01 of a seeded union of 32 spheres
+    and tori, target their signed distance), Trainer with the table layout its size selects;
+    simplex and the 8-corner grid, points/s."""
+    import torch
+    from paper_2311_15439_gb300 import synth
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+    scene = synth.SphereTorusScene(5)
+    xs = [synth.sdf_points(P, 300 + i) for i in range(n_batches)]
+    batches = [(torch.from_numpy(x).to(dev), torch.from_numpy(scene.sdf(x)).to(dev)) for x in xs]
+    out = {"points_per_step": P, "config": "d=3 L=16 F=2 T=2^19 bf16, network 32-64-1 bf16"}
+    for kind in ("simplex", "grid"):
+        tr = Trainer(Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, table_dtype="bf16"),
+                     Mlp(32, 1, n_hidden=1, dtype="bf16"), P, seed=6, device=dev)
+        for i in range(warmup):
+            tr.step(*batches[i % n_batches])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record()
+        for i in range(steps):
+            tr.step(*batches[i % n_batches])
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / steps
+        out[kind] = {"ms_per_step": ms, "points_per_s": P / (ms / 1e3), "table_layout": tr.tab.layout,
+                     "loss": tr.loss()}
+        del tr
         torch.cuda.empty_cache()
     out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]
     return out
