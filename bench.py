@@ -299,7 +299,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "kind": args.kind, "mlp_kernel": args.mlp_kernel,
+            "config": {"workload": WORKLOAD, "kind": args.kind, "mlp_kernel": {"auto": "auto (two-tile tcgen05 kernel for this network)", "mma_sync": "mma_sync",
+                                      "tcgen05": "tcgen05"}[args.mlp_kernel],
                        "global_batch": BATCH * world,
                        "points_per_step_per_gpu": BATCH, "parallelism": "replicas (one per GPU)",
                        "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state records, no flush",
