@@ -182,7 +182,7 @@ class Trainer:
         # per level range (coarse levels in shared memory, then the rest), table Adam per range,
         # network Adam
         bwd = sum(self.enc.bwd_kernel_count(self.P, levels=c) for c in self.chunks)
-        return 4 + bwd + len(self.chunks)
+        return 5 + bwd + len(self.chunks)
 
     def step(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
         """One optimisation step on batch (x [P, d] float32, target [P, n_out] float32); asynchronous."""
