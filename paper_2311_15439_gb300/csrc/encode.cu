@@ -532,9 +532,11 @@ sxe_status fwd_d(const sxe_encoder* e, const float* x, int64_t P, const void* t,
 
 // Coarse levels for the privatised backward: a prefix of levels whose box fits the shared
 // memory budget and receives at least 8 contributions per vertex.  A level gets one CTA per
-// 8192 contributions, fewer if a CTA would then see under 4 contributions per vertex, and
-// at most 2 per SM: the flush then costs at most a quarter of the contributions, and each
-// table entry receives at most K flushed sums instead of thousands of single terms.
+// 4096 contributions, fewer if a CTA would then see under 1 contribution per vertex, and at
+// most 2 per SM: short per-thread loops (the kernel is latency-bound), a flush of at most
+// one global reduction per contribution into L2-resident entries, and each table entry
+// receives at most K flushed sums instead of thousands of single terms (measured: 324.7 ->
+// 315.0 us for the image backward against 8192 and 4 per vertex; 2048 and 1/2 was slower).
 CoarsePlan coarse_plan(const sxe_encoder* e, int64_t P) {
   CoarsePlan plan{};
   const int d = e->desc.d, F = e->desc.n_features;
@@ -550,7 +552,7 @@ CoarsePlan coarse_plan(const sxe_encoder* e, int64_t P) {
     for (int i = 0; i < d; ++i) cells *= B;
     const int64_t bytes = cells * F * 4 + (cells + 31) / 32 * 4;
     if (bytes > kCoarseSmem || P * V < 8 * cells) break;
-    const int64_t K = std::max<int64_t>(1, std::min<int64_t>(std::min(P * V / 8192, P * V / (4 * cells)), 2 * sms));
+    const int64_t K = std::max<int64_t>(1, std::min<int64_t>(std::min(P * V / 4096, P * V / cells), 2 * sms));
     plan.box[c] = B;
     plan.start[c + 1] = plan.start[c] + (int)K;
     plan.smem = std::max(plan.smem, (int)bytes);
