@@ -292,3 +292,38 @@ def test_tcgen05_and_mma_sync_agree(cuda_lib, net):
     for i, (ga, gb) in enumerate(zip(mlp.split(a[0]), mlp.split(b[0]))):
         assert within(gb, ga, dW_den[i], tol, 2 * dW_sl[i]) <= 1.0, "layer %d" % i
     assert within(b[1], a[1], din_den, tol, 2 * din_sl) <= 1.0
+
+
+def test_adam_touched_full_size_table(cuda_lib):
+    """The bitmap-driven table step at the image workload's full table (L = 16, T = 2^22, F = 2:
+    67 M entries, 2 GiB of state records, fp16 table), in the launch configuration the benchmark
+    times: a seeded sample of 200 K entries (marked and unmarked) against the oracle's Adam."""
+    from paper_2311_15439_gb300.api import Adam
+    n, F = 16 << 22, 2
+    gen = torch.Generator(device="cuda").manual_seed(123)
+    state = torch.empty((n, 4 * F), device="cuda")
+    state[:, :F].normal_(generator=gen)
+    state[:, F:2 * F].normal_(generator=gen).mul_(0.1)
+    state[:, 2 * F:3 * F].uniform_(0.0, 0.01, generator=gen)
+    marked = torch.rand(n, device="cuda", generator=gen) < 0.1
+    state[:, 3 * F:].normal_(generator=gen).mul_(marked[:, None])
+    state[::11, 3 * F:] = 0.0                        # some marked entries with an exactly zero gradient
+    words = (marked.view(-1, 32).to(torch.int64) << torch.arange(32, device="cuda")).sum(dim=1)
+    touched = (words - ((words >= (1 << 31)).to(torch.int64) << 32)).to(torch.int32)   # same 32 bits
+    table = state[:, :F].to(torch.float16)
+    idx = torch.from_numpy(synth.rng(124).choice(n, 200_000, replace=False)).cuda()
+    before = state[idx].cpu().numpy()
+    was_marked = marked[idx].cpu().numpy()
+    Adam(1e-2, 0.9, 0.99, 1e-15).step_touched(5, state, touched, table, F)
+    torch.cuda.synchronize()
+    after = state[idx].cpu().numpy()
+    p, m, v, g = (before[:, k * F:(k + 1) * F].astype(np.float64) for k in range(4))
+    rp, rm, rv = OA.adam_step(p, g, m, v, 5, skip_zero_grad=True, **_hp32())
+    np.testing.assert_allclose(after[:, :F], rp, rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(after[:, F:2 * F], rm, rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(after[:, 2 * F:3 * F], rv, rtol=2e-6, atol=1e-9)
+    assert np.all(after[:, 3 * F:] == 0)
+    assert int((touched != 0).sum().item()) == 0
+    tab = table[idx].cpu().numpy()
+    np.testing.assert_array_equal(tab[was_marked], after[was_marked, :F].astype(np.float16))
+    assert was_marked.sum() > 15_000 and (~was_marked).sum() > 150_000
