@@ -49,10 +49,10 @@ def test_field_head_matches_oracle(cuda_lib, dtype):
     assert np.all(np.abs(c[:, 16:] - sh) <= ulp * np.abs(sh) + 1e-6)          # binary32 polynomial, one rounding
 
 
-@pytest.mark.parametrize("S", [1, 5, 32, 33, 100, 1024])
-def test_composite_matches_oracle(cuda_lib, S):
+@pytest.mark.parametrize("R,S", [(257, 1), (257, 5), (257, 32), (257, 33), (257, 100), (257, 1024),
+                                 (1 << 16, 64)])                  # the last: the volumetric workload's size
+def test_composite_matches_oracle(cuda_lib, R, S):
     from paper_2311_15439_gb300.render import vr_composite
-    R = 257
     g = synth.rng(10 + S)
     scale = g.choice([0.0, 0.1, 3.0, 50.0, 1e4], size=(R, 1))
     sigma = (g.exponential(1.0, size=(R, S)) * scale).astype(np.float32)
@@ -156,13 +156,12 @@ def test_fused_field_equals_three_launches(cuda_lib, kind, dtype, L):
         assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("S", [1, 33, 100, 1024])
-def test_composite_bwd_matches_oracle(cuda_lib, S):
+@pytest.mark.parametrize("R,S", [(129, 1), (129, 33), (129, 100), (129, 1024), (1 << 16, 64)])
+def test_composite_bwd_matches_oracle(cuda_lib, R, S):
     """dL/dsigma and dL/dlogits of the compositing against the FP64 chain rule, within a bound
     built from the binary32 scans (transmittance and accumulated colour) the kernel runs."""
     from paper_2311_15439_gb300 import _lib as L
     from paper_2311_15439_gb300.render import vr_composite
-    R = 129
     g = synth.rng(30 + S)
     scale = g.choice([0.0, 0.1, 3.0, 50.0], size=(R, 1))
     sigma = (g.exponential(1.0, size=(R, S)) * scale).astype(np.float32)
