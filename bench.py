@@ -282,6 +282,8 @@ def run_gpu(args):
     peaks_ra = random_access_peaks(dev, tr.state.numel() * 4, tr.tables) if rank == 0 else None
     volume = volume_sweep(dev) if (rank == 0 and not args.no_volume) else None
     sdf = sdf_train(dev) if (rank == 0 and not args.no_sweep) else None
+    grid_img = image_grid_step(dev, xd, td, ms / args.steps) if (rank == 0 and not args.no_sweep and
+                                                                  args.kind == "simplex") else None
 
     if rank == 0:
         value = job_throughput(BATCH, args.steps, world, ms)
@@ -341,6 +343,8 @@ def run_gpu(args):
             line["volume"] = volume
         if sdf is not None:
             line["sdf_train"] = sdf
+        if grid_img is not None:
+            line["image_grid_step"] = grid_img
         if serving is not None:
             line["serve"] = serving
         if not args.no_cpu:
@@ -502,6 +506,32 @@ def volume_train(dev, rays, S=64, steps=10, warmup=3):
         torch.cuda.empty_cache()
     out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]
     return out
+
+
+def image_grid_step(dev, xd, td, simplex_ms, steps=100, warmup=5):
+    """The headline training step with the 2^d grid encoder instead of the simplex one (same
+    L, F, T, tables, network, batches): the comparison of Sec. 6.1's image-fitting run time."""
+    import torch
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+    enc = Encoder(**CFG, kind="grid", table_dtype="f16")
+    tr = Trainer(enc, Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16"), BATCH, seed=0,
+                 device=dev, table_layout="records")
+    for i in range(warmup):
+        tr.step(xd[i % len(xd)], td[i % len(td)])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record()
+    for i in range(steps):
+        tr.step(xd[i % len(xd)], td[i % len(td)])
+    b.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    del tr
+    torch.cuda.empty_cache()
+    return {"grid_ms_per_step": ms, "grid_points_per_s": BATCH / (ms / 1e3), "simplex_ms_per_step": simplex_ms,
+            "grid_over_simplex": ms / simplex_ms, "steps": steps,
+            "note": "grid: 4 corners per level against the simplex's 3 vertices, same tables and network"}
 
 
 def sdf_train(dev, P=1 << 20, steps=20, warmup=3, n_batches=4):
