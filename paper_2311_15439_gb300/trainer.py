@@ -7,10 +7,12 @@ kernels:
                            tables (Sec. 5 a-d);
 2. ``sxe_mlp_train_l2`` -- network forward, L2 loss, network backward, dL/d(encoding)
                            (Sec. 5 d-e);
-3. ``sxe_encode_bwd``   -- scatter-add of dL/d(encoding) into the gradient field of the
-                           interleaved table state, marking touched entries (Sec. 5 e);
-4. ``sxe_step_touched`` -- Adam on the marked table entries (zero-gradient skip rule),
-                           refreshing the low-precision tables;
+3. ``sxe_encode_bwd``   -- scatter-add of dL/d(encoding) into the table gradients (Sec. 5 e):
+                           the gradient field of the interleaved records, marking touched
+                           entries, or the dense gradient array (see the layouts below);
+4. ``sxe_step_touched`` -- Adam on the marked table entries, or ``sxe_step`` over the dense
+                           arrays (both with the zero-gradient skip rule), refreshing the
+                           low-precision tables;
 5. ``sxe_step``         -- Adam on the network weights, refreshing their low-precision copy.
 
 The step count lives on the device (``sxe_adam_advance`` increments it and writes the bias
