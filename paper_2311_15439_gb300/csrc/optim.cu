@@ -32,6 +32,40 @@ __global__ void adam_dense_kernel(AdamConst kin, int64_t n, float* __restrict__ 
   }
 }
 
+// The same over 4 consecutive parameters per thread with 16-byte accesses (n a multiple of 4,
+// every array 16-byte aligned and the low-precision copy 8-byte aligned).  Every element is
+// written back: a skipped element keeps its values and its gradient is already zero, so the
+// result equals the scalar kernel's.
+__global__ void adam_dense4_kernel(AdamConst kin, int64_t n4, float4* __restrict__ p, float4* __restrict__ m,
+                                   float4* __restrict__ v, float4* __restrict__ g, void* __restrict__ lowp,
+                                   int ldt) {
+  const AdamConst k = adam_resolve(kin);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 gi = g[i];
+    float4 pi = p[i], mi = m[i], vi = v[i];
+    const float ga[4] = {gi.x, gi.y, gi.z, gi.w};
+    float pa[4] = {pi.x, pi.y, pi.z, pi.w}, ma[4] = {mi.x, mi.y, mi.z, mi.w}, va[4] = {vi.x, vi.y, vi.z, vi.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (!(k.skip && ga[j] == 0.f)) adam_one(k, ga[j], pa[j], ma[j], va[j]);
+    p[i] = make_float4(pa[0], pa[1], pa[2], pa[3]);
+    m[i] = make_float4(ma[0], ma[1], ma[2], ma[3]);
+    v[i] = make_float4(va[0], va[1], va[2], va[3]);
+    g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lowp) {
+      if (ldt == SXE_F32) {
+        reinterpret_cast<float4*>(lowp)[i] = make_float4(pa[0], pa[1], pa[2], pa[3]);
+      } else if (ldt == SXE_F16) {
+        __half2 lo = __floats2half2_rn(pa[0], pa[1]), hi = __floats2half2_rn(pa[2], pa[3]);
+        reinterpret_cast<uint2*>(lowp)[i] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+      } else {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(pa[0], pa[1]), hi = __floats2bfloat162_rn(pa[2], pa[3]);
+        reinterpret_cast<uint2*>(lowp)[i] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+      }
+    }
+  }
+}
+
 // A warp takes 32 consecutive bitmap words (1024 entries).  The set bits of the 32 words are
 // listed in shared memory in address order (a warp prefix sum of the words' popcounts gives
 // each word's place in the list); then the lanes take the listed entries in turn, NB records per
@@ -152,7 +186,15 @@ sxe_status launch_adam_dense(const sxe_adam_desc* a, int64_t t, int64_t n, float
                              void* lowp, int32_t ldt, cudaStream_t s, const float* corrections) {
   AdamConst k = make_adam_const(a, corrections ? 1 : t);
   k.cdev = corrections;
-  adam_dense_kernel<<<blocks_for(n, 256, 1u << 16), 256, 0, s>>>(k, n, p, m, v, g, lowp, ldt);
+  auto al = [](const void* q, uintptr_t b) { return ((uintptr_t)q % b) == 0; };
+  const bool vec = n % 4 == 0 && al(p, 16) && al(m, 16) && al(v, 16) && al(g, 16) &&
+                   (!lowp || al(lowp, ldt == SXE_F32 ? 16 : 8));
+  if (vec)
+    adam_dense4_kernel<<<blocks_for(n / 4, 256, 1u << 16), 256, 0, s>>>(
+        k, n / 4, reinterpret_cast<float4*>(p), reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v),
+        reinterpret_cast<float4*>(g), lowp, ldt);
+  else
+    adam_dense_kernel<<<blocks_for(n, 256, 1u << 16), 256, 0, s>>>(k, n, p, m, v, g, lowp, ldt);
   return check_launch("adam_dense");
 }
 

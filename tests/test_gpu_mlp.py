@@ -214,22 +214,23 @@ def _hp32():
                 eps=float(np.float32(1e-15)))
 
 
+@pytest.mark.parametrize("n,low_dt", [(10007, torch.float16), (10008, torch.float16), (10008, torch.bfloat16),
+                                      (10008, torch.float32)])      # n % 4 == 0: the 16-byte-access kernel
 @pytest.mark.parametrize("skip", [False, True])
-def test_adam_dense(cuda_lib, skip):
+def test_adam_dense(cuda_lib, skip, n, low_dt):
     from paper_2311_15439_gb300.api import Adam
     g = synth.rng(4)
-    n = 10007
     p = g.standard_normal(n).astype(np.float32)
     m = (g.standard_normal(n) * 0.1).astype(np.float32)
     v = (g.random(n) * 0.01).astype(np.float32)
     gr = (g.standard_normal(n) * (g.random(n) < 0.8)).astype(np.float32)
     dev = [torch.from_numpy(a.copy()).cuda() for a in (p, m, v, gr)]
-    low = torch.empty(n, dtype=torch.float16, device="cuda")
+    low = torch.empty(n, dtype=low_dt, device="cuda")
     Adam(1e-2, 0.9, 0.99, 1e-15, skip_zero_grad=skip).step(3, *dev, lowp=low)
     rp, rm, rv = OA.adam_step(p, gr, m, v, 3, skip_zero_grad=skip, **_hp32())
     for got, want in zip(dev[:3], (rp, rm, rv)):
         np.testing.assert_allclose(got.cpu().numpy(), want, rtol=2e-6, atol=1e-7)
-    assert torch.equal(low, dev[0].half())
+    assert torch.equal(low, dev[0].to(low_dt))
     if skip:
         assert torch.all(dev[3] == 0)
 
