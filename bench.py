@@ -284,6 +284,7 @@ def run_gpu(args):
     sdf = sdf_train(dev) if (rank == 0 and not args.no_sweep) else None
     grid_img = image_grid_step(dev, xd, td, ms / args.steps) if (rank == 0 and not args.no_sweep and
                                                                   args.kind == "simplex") else None
+    per_cfg = per_config_encode(dev) if (rank == 0 and not args.no_sweep) else None
 
     if rank == 0:
         value = job_throughput(BATCH, args.steps, world, ms)
@@ -345,6 +346,8 @@ def run_gpu(args):
             line["sdf_train"] = sdf
         if grid_img is not None:
             line["image_grid_step"] = grid_img
+        if per_cfg is not None:
+            line["per_config_encode"] = per_cfg
         if serving is not None:
             line["serve"] = serving
         if not args.no_cpu:
@@ -505,6 +508,112 @@ def volume_train(dev, rays, S=64, steps=10, warmup=3):
         del vt
         torch.cuda.empty_cache()
     out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]
+    return out
+
+
+# Encode forward + backward of each configuration of the benchmark plan (the plain binary32 case,
+# the image, SDF-style and volumetric workloads; the serving load is `serve`), simplex and grid.
+PER_CONFIG = [
+    ("plain_fp32_2d_L8_T2^14_P2^16", dict(d=2, n_levels=8, n_features=2, log2_T=14, base_res=16.0, growth=1.5),
+     "f32", 1 << 16, "uniform"),
+    ("image_2d_L16_T2^22_fp16_P2^18", dict(CFG), "f16", 1 << 18, "uniform"),
+    ("sdf_3d_L16_T2^19_bf16_P2^20", dict(d=3, n_levels=16, n_features=2, log2_T=19, base_res=16.0, growth=1.38),
+     "bf16", 1 << 20, "sdf"),
+    ("volume_3d_L16_T2^19_fp16_2^16rays_x1024", dict(d=3, n_levels=16, n_features=2, log2_T=19, base_res=16.0,
+                                                      growth=1.38), "f16", 1 << 26, "rays"),
+]
+
+
+def per_config_encode(dev):
+    """Per configuration: encode forward and backward points/s (each recorded once into a CUDA graph
+    and replayed), simplex and grid on the same tables, and the forward's achieved random gathers/s
+    over the probe's random 4-byte gather rate on that configuration's own tables (the fraction of
+    the gather roofline; above 1 where tables or reuse sit in L2)."""
+    import torch
+    from paper_2311_15439_gb300 import _lib as L
+    from paper_2311_15439_gb300 import synth
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.render import vr_samples
+    lib = L.lib()
+    st = torch.cuda.current_stream(dev).cuda_stream
+    sink = torch.zeros((1,), dtype=torch.float32, device=dev)
+    dts = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+    gen = torch.Generator(device=dev).manual_seed(77)
+    out = {}
+    for name, ea, tdt, P, pts in PER_CONFIG:
+        if pts == "uniform":
+            x = torch.from_numpy(synth.uniform_points(P, ea["d"], 78)).to(dev)
+        elif pts == "sdf":
+            x = torch.from_numpy(synth.sdf_points(P, 79)).to(dev)
+        else:
+            rays = [torch.from_numpy(a).to(dev) for a in synth.camera_rays(1 << 16, 60)]
+            x = vr_samples(*rays, P >> 16)[0]
+        n_out = ea["n_levels"] * ea["n_features"]
+        dout = torch.randn((P, n_out), device=dev, generator=gen)
+        reps = 1000 if P <= (1 << 16) else (3 if P >= (1 << 26) else 50)
+        row = {"points": P, "table_dtype": tdt, "replays": reps}
+        for kind in ("simplex", "grid"):
+            enc = Encoder(**ea, kind=kind, table_dtype=tdt, out_dtype=tdt)
+            tab = (torch.rand(enc.table_shape(), device=dev, generator=gen) * 2 - 1).to(dts[tdt])
+            grad = torch.zeros(enc.table_shape(), dtype=torch.float32, device=dev)
+            o = torch.empty((P, n_out), dtype=dts[tdt], device=dev)
+            times = {}
+            for stage, fn in (("fwd", lambda: enc.encode_fwd(x, tab, o)), ("bwd", lambda: enc.encode_bwd(x, dout, grad))):
+                fn()
+                torch.cuda.synchronize(dev)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    fn()
+                g.replay()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                a.record()
+                for _ in range(reps):
+                    g.replay()
+                b.record()
+                torch.cuda.synchronize(dev)
+                times[stage] = a.elapsed_time(b) / reps / 1e3
+                del g
+            gathers = P * ea["n_levels"] * enc.n_vertices
+            words = tab.view(torch.float32).reshape(-1) if tab.element_size() == 4 else tab.view(torch.float32)
+            slots = 1 << int(math.log2(words.numel() // 2))
+            n_ops = 1 << 24
+            lib.sxe_probe_random_access(1, words.data_ptr(), slots, 2, n_ops, 1, sink.data_ptr(), st)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for r in range(3):
+                lib.sxe_probe_random_access(1, words.data_ptr(), slots, 2, n_ops, 2 + r, sink.data_ptr(), st)
+            b.record()
+            torch.cuda.synchronize(dev)
+            peak = 3 * n_ops / (a.elapsed_time(b) / 1e3)
+            row[kind] = {"fwd_bwd_points_per_s": P / (times["fwd"] + times["bwd"]),
+                         "fwd_ms": times["fwd"] * 1e3, "bwd_ms": times["bwd"] * 1e3,
+                         "fwd_gathers_per_s": gathers / times["fwd"], "random_gather_peak_per_s": peak,
+                         "gather_roofline_frac": gathers / times["fwd"] / peak}
+            if kind == "simplex" and tdt == "f32":
+                times_p = {}
+                for stage, fn in (("fwd", lambda: enc.encode_plain_fwd(x, tab, o)),
+                                  ("bwd", lambda: enc.encode_plain_bwd(x, dout, grad))):
+                    fn()
+                    torch.cuda.synchronize(dev)
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g):
+                        fn()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize(dev)
+                    a.record()
+                    for _ in range(reps):
+                        g.replay()
+                    b.record()
+                    torch.cuda.synchronize(dev)
+                    times_p[stage] = a.elapsed_time(b) / reps / 1e3
+                    del g
+                row["simplex_plain_f32"] = {"fwd_bwd_points_per_s": P / (times_p["fwd"] + times_p["bwd"])}
+            del enc, tab, grad, o
+        row["grid_over_simplex"] = row["simplex"]["fwd_bwd_points_per_s"] / row["grid"]["fwd_bwd_points_per_s"]
+        out[name] = row
+        del x, dout
+        torch.cuda.empty_cache()
     return out
 
 
