@@ -172,6 +172,12 @@ int32_t sxe_encode_bwd_kernel_count(const sxe_encoder* enc, int64_t n_points);
 /* The same for sxe_encode_bwd_levels on [level_begin, level_end) (0 for an empty or invalid range). */
 int32_t sxe_encode_bwd_levels_kernel_count(const sxe_encoder* enc, int64_t n_points, int32_t level_begin,
                                            int32_t level_end);
+/* Number of leading levels (0 <= n <= L) that sxe_encode_bwd sums per thread block in shared
+ * memory for n_points points; they run as their own kernel, so a caller may run the levels
+ * [0, n) and [n, L) through sxe_encode_bwd_levels on two streams at once (they share no
+ * gradient address, nor a bitmap word when T >= 32).  Returns 0 for a NULL encoder or
+ * n_points <= 0. */
+int32_t sxe_encode_bwd_coarse_levels(const sxe_encoder* enc, int64_t n_points);
 
 /* Gradient with respect to the points (the chain rule through Sec. 4.3's weights, Eq. 2's
  * skew and the level scale; the paper does not state it):

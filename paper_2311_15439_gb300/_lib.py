@@ -24,7 +24,8 @@ EXPORTS = (
     "sxe_encoder_create", "sxe_encoder_destroy", "sxe_encoder_level_params", "sxe_encoder_level_index",
     "sxe_encoder_set_bwd_aggregation",
     "sxe_encode_fwd", "sxe_encode_bwd", "sxe_encode_bwd_levels", "sxe_encode_bwd_kernel_count",
-    "sxe_encode_bwd_levels_kernel_count", "sxe_encode_bwd_input", "sxe_encode_vertices",
+    "sxe_encode_bwd_levels_kernel_count", "sxe_encode_bwd_coarse_levels", "sxe_encode_bwd_input",
+    "sxe_encode_vertices",
     "sxe_encode_plain_fwd", "sxe_encode_plain_bwd", "sxe_vr_samples", "sxe_vr_field", "sxe_vr_field_mlp", "sxe_vr_composite",
     "sxe_vr_composite_bwd", "sxe_vr_field_bwd",
     "sxe_probe_random_access", "sxe_adam_advance", "sxe_step_dev", "sxe_step_touched_dev",
@@ -72,6 +73,7 @@ def _declare(L):
         "sxe_encode_bwd_kernel_count": (i32, [vp, i64]),
         "sxe_encode_bwd_levels": (i32, [vp, vp, i64, vp, vp, i64, vp, i32, i32, vp]),
         "sxe_encode_bwd_levels_kernel_count": (i32, [vp, i64, i32, i32]),
+        "sxe_encode_bwd_coarse_levels": (i32, [vp, i64]),
         "sxe_encode_vertices": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_encode_plain_fwd": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_vr_samples": (i32, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),

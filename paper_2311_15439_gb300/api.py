@@ -147,6 +147,11 @@ class Encoder:
             return int(L.lib().sxe_encode_bwd_kernel_count(self._h, n_points))
         return int(L.lib().sxe_encode_bwd_levels_kernel_count(self._h, n_points, int(levels[0]), int(levels[1])))
 
+    def bwd_coarse_levels(self, n_points: int) -> int:
+        """Leading levels whose backward is summed per block in shared memory for this many points
+        (their own kernel; ``encode_bwd(levels=(0, n))`` and ``levels=(n, L)`` may run on two streams)."""
+        return int(L.lib().sxe_encode_bwd_coarse_levels(self._h, n_points))
+
     def encode_bwd_input(self, x: torch.Tensor, tables: torch.Tensor, dout: torch.Tensor,
                          dx: torch.Tensor | None = None, stream=None):
         """dx += d(out)/dx^T dout (``sxe_encode_bwd_input``); returns dx [P, d] float32."""

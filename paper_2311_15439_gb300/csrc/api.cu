@@ -187,6 +187,11 @@ int32_t sxe_encode_bwd_levels_kernel_count(const sxe_encoder* e, int64_t P, int3
   return encode_bwd_launches(e, P, level_begin, level_end);
 }
 
+int32_t sxe_encode_bwd_coarse_levels(const sxe_encoder* e, int64_t P) {
+  if (!e || P <= 0) return 0;
+  return encode_bwd_coarse_levels(e, P);
+}
+
 sxe_status sxe_encode_bwd_input(const sxe_encoder* e, const float* x, int64_t P, const void* tables,
                                 const float* dout, float* dx, void* stream) {
   sxe_status st = check_points("encode_bwd_input", e, x, P);

@@ -649,6 +649,8 @@ sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, 
                                        : bwd_d<false>(enc, x, P, dout, grad, stride, touched, s, level_begin, level_end);
 }
 
+int encode_bwd_coarse_levels(const sxe_encoder* enc, int64_t P) { return coarse_plan(enc, P).n; }
+
 int encode_bwd_launches(const sxe_encoder* enc, int64_t P, int level_begin, int level_end) {
   if (level_end < 0) level_end = enc->prm.n_levels;
   if (P == 0 || level_begin >= level_end) return 0;

@@ -779,7 +779,9 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
     float v[16];
     tc::tmem_ld16(c_out + la, v);
     if (lane < 16)
-      for (int o = 0; o < n_out; ++o) wsb[off_o + o * kW + m] = any_tile ? v[o] : 0.f;
+#pragma unroll
+      for (int o = 0; o < 16; ++o)
+        if (o < n_out) wsb[off_o + o * kW + m] = any_tile ? v[o] : 0.f;
 #pragma unroll
     for (int h = 1; h < NH; ++h)
 #pragma unroll

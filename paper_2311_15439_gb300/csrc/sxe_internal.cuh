@@ -53,6 +53,7 @@ sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, 
                              float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s,
                              int level_begin = 0, int level_end = -1);
 int encode_bwd_launches(const sxe_encoder* enc, int64_t P, int level_begin = 0, int level_end = -1);
+int encode_bwd_coarse_levels(const sxe_encoder* enc, int64_t P);
 sxe_status launch_adam_advance(const sxe_adam_desc* a, int64_t* t, float* corrections, cudaStream_t s);
 sxe_status launch_encode_plain(const sxe_encoder* enc, bool backward, const float* x, int64_t P, const float* a,
                                float* b, cudaStream_t s);

@@ -108,7 +108,7 @@ class VolumeTrainer:
 
     def __init__(self, encoder: Encoder, max_rays: int, n_samples: int, *, dtype: str = "f16", seed: int = 0,
                  device="cuda", table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15,
-                 table_layout: str = "auto"):
+                 table_layout: str = "auto", split_coarse="auto"):
         from . import synth
         from .api import Adam
         from .trainer import TableState, choose_table_layout, default_loss_scale
@@ -118,7 +118,8 @@ class VolumeTrainer:
         F, n_entries = encoder.n_features, encoder.n_levels * encoder.T
         vals = synth.uniform_tables(encoder.n_levels, encoder.T, F, seed, dtype="f32", scale=table_init)[0]
         init = torch.from_numpy(vals.reshape(n_entries, F)).to(dev)
-        self.tab = TableState(encoder, init, choose_table_layout(encoder, dev, table_layout), dev)
+        self.tab = TableState(encoder, init, choose_table_layout(encoder, dev, table_layout), dev,
+                              split_coarse=split_coarse)
         self.tables = self.tab.tables
         self.nets = []
         for k, m in enumerate((self.rr.density, self.rr.color)):

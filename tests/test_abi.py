@@ -80,6 +80,8 @@ def test_entry_points_validate_before_launch(L):
         assert lib.sxe_encode_bwd_levels(h, 16, 10, 16, 16, 2, None, 2, 2, None) == 0
         assert lib.sxe_encode_bwd_levels_kernel_count(h, 10, 2, 2) == 0
         assert lib.sxe_encode_bwd_levels_kernel_count(h, 10, 0, 99) == 0
+        assert lib.sxe_encode_bwd_coarse_levels(None, 10) == 0
+        assert lib.sxe_encode_bwd_coarse_levels(h, 0) == 0
         # backward strategy switch: 0 or 1 only
         assert lib.sxe_encoder_set_bwd_aggregation(None, 1) == -1
         assert lib.sxe_encoder_set_bwd_aggregation(h, 2) == -1

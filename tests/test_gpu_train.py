@@ -339,6 +339,45 @@ def test_overlapped_table_step_equals_plain_step(k):
     _close_up_to_atomics(a.tables.float(), b.tables.float(), steps=5)
 
 
+@pytest.mark.parametrize("layout", ["records", "dense"])
+def test_coarse_levels_on_a_second_stream_equal_plain_step(layout):
+    """The backward of the levels summed in shared memory on a second stream, concurrently with
+    the other levels, gives the one-stream step's parameters (equal up to the order of the
+    binary32 atomics), eagerly and replayed from a CUDA graph."""
+    P = 4096
+    a, b = _make(P, seed=13, layout=layout), _make(P, seed=13, layout=layout)
+    a.tab.set_split_coarse(False)
+    b.tab.set_split_coarse(True)
+    assert a.tab.split_coarse is False and b.tab.split_coarse is True
+    lc = b.enc.bwd_coarse_levels(P)
+    assert 0 < lc < CFG["n_levels"]
+    assert b.enc.bwd_kernel_count(P, levels=(0, lc)) == 1 and b.enc.bwd_kernel_count(P, levels=(lc, 8)) == 1
+    img = synth.ProceduralImage(5, size=1024, n_waves=4)
+    batches = []
+    for i in range(5):
+        x = synth.uniform_points(P, 2, 70 + i)
+        batches.append((torch.from_numpy(x).cuda(), torch.from_numpy(img.sample(x)).cuda()))
+    for x, t in batches[:3]:
+        a.step(x, t)
+        b.step(x, t)
+    torch.cuda.synchronize()
+    _close_up_to_atomics(a.table_params(), b.table_params(), steps=3)
+    bx, bt = torch.empty_like(batches[0][0]), torch.empty_like(batches[0][1])
+    bx.copy_(batches[3][0]); bt.copy_(batches[3][1])
+    b.capture(bx, bt, warmup=1)                                    # one eager step on batch 3
+    a.step(*batches[3])
+    a.step(*batches[4])
+    bx.copy_(batches[4][0]); bt.copy_(batches[4][1])
+    b.replay()
+    torch.cuda.synchronize()
+    assert a.t == b.t == 5
+    _close_up_to_atomics(a.W, b.W, steps=5, atol=1e-5)
+    _close_up_to_atomics(a.table_params(), b.table_params(), steps=5)
+    _close_up_to_atomics(a.tables.float(), b.tables.float(), steps=5)
+    if layout == "records":
+        assert int(b.touched.abs().sum().item()) == 0
+
+
 def test_device_step_counter_and_bias_corrections():
     """sxe_adam_advance: t counts up on the device and the corrections are 1 / (1 - beta^t) in FP64
     rounded once to binary32 (at most one binary32 ulp from the exactly rounded value)."""
