@@ -504,7 +504,8 @@ def volume_train(dev, rays, S=64, steps=10, warmup=3):
         b.record()
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / steps
-        out[kind] = {"ms_per_step": ms, "samples_per_s": R * S / (ms / 1e3), "table_layout": vt.tab.layout}
+        out[kind] = {"ms_per_step": ms, "samples_per_s": R * S / (ms / 1e3), "table_layout": vt.tab.layout,
+                     "coarse_levels_on_second_stream": vt.tab.split_coarse}
         del vt
         torch.cuda.empty_cache()
     out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]
@@ -670,7 +671,7 @@ def sdf_train(dev, P=1 << 20, steps=20, warmup=3, n_batches=4):
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / steps
         out[kind] = {"ms_per_step": ms, "points_per_s": P / (ms / 1e3), "table_layout": tr.tab.layout,
-                     "loss": tr.loss()}
+                     "coarse_levels_on_second_stream": tr.tab.split_coarse, "loss": tr.loss()}
         del tr
         torch.cuda.empty_cache()
     out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]

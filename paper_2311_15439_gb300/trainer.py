@@ -343,3 +343,51 @@ class HostFeed:
         j = (self.k - 1) % 2
         self._done[j].synchronize()
         return float(self._loss[j]) * self._scale
+
+
+def _main(argv=None):
+    """Train on seeded synthetic batches and print the time per step:
+    ``python -m paper_2311_15439_gb300.trainer --workload sdf`` (d = 3, L = 16, F = 2, T = 2^19
+    bf16, network 32-64-1, 2^20 points per step: half uniform, half near a seeded union of spheres
+    and tori, target their signed distance) or ``--workload image`` (d = 2, L = 16, F = 2,
+    T = 2^22 fp16, network 32-64-64-3, 2^18 points of a procedural image per step)."""
+    import argparse
+    ap = argparse.ArgumentParser(description=_main.__doc__)
+    ap.add_argument("--workload", default="sdf", choices=["sdf", "image"])
+    ap.add_argument("--kind", default="simplex", choices=["simplex", "grid"])
+    ap.add_argument("--points", type=int, default=0, help="points per step (default: the workload's)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--repeat", type=int, default=10)
+    ap.add_argument("--split-coarse", default="auto", choices=["auto", "on", "off"])
+    a = ap.parse_args(argv)
+    split = {"auto": "auto", "on": True, "off": False}[a.split_coarse]
+    dev = torch.device("cuda")
+    if a.workload == "sdf":
+        P = a.points or 1 << 20
+        scene = synth.SphereTorusScene(5)
+        xs = [synth.sdf_points(P, 300 + i) for i in range(4)]
+        batches = [(torch.from_numpy(x).to(dev), torch.from_numpy(scene.sdf(x)).to(dev)) for x in xs]
+        tr = Trainer(Encoder(3, 16, 2, 19, 16.0, 1.38, kind=a.kind, table_dtype="bf16"),
+                     Mlp(32, 1, n_hidden=1, dtype="bf16"), P, seed=6, device=dev, split_coarse=split)
+    else:
+        P = a.points or 1 << 18
+        img = synth.ProceduralImage(1, size=16384, n_waves=64)
+        xs = [synth.uniform_points(P, 2, 400 + i) for i in range(4)]
+        batches = [(torch.from_numpy(x).to(dev), torch.from_numpy(img.sample(x)).to(dev)) for x in xs]
+        tr = Trainer(Encoder(2, 16, 2, 22, 16.0, 2.0, kind=a.kind, table_dtype="f16"),
+                     Mlp(32, 3, n_hidden=2, dtype="f16"), P, seed=3, device=dev, split_coarse=split)
+    for i in range(a.warmup):
+        tr.step(*batches[i % 4])
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for i in range(a.repeat):
+        tr.step(*batches[i % 4])
+    e.record()
+    torch.cuda.synchronize()
+    print("train %s %s: %d points, %s layout, coarse levels on a second stream: %s: %.3f ms per step, loss %.4g" %
+          (a.workload, a.kind, P, tr.tab.layout, tr.tab.split_coarse, s.elapsed_time(e) / a.repeat, tr.loss()))
+
+
+if __name__ == "__main__":
+    _main()
