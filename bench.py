@@ -675,7 +675,51 @@ def sdf_train(dev, P=1 << 20, steps=20, warmup=3, n_batches=4):
         del tr
         torch.cuda.empty_cache()
     out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]
+    out["table_backward_roofline"] = dense_bwd_roofline(dev, xs[0])
     return out
+
+
+def dense_bwd_roofline(dev, x_host, reps=20):
+    """The SDF-style table backward of the levels that take the direct path, against the probe's
+    rate of random float2 reductions over a footprint the size of the dense gradient array (which
+    stays in L2): contributions / that rate over the CUDA-event time of the kernel."""
+    import torch
+    from paper_2311_15439_gb300 import _lib as L
+    from paper_2311_15439_gb300 import synth
+    from paper_2311_15439_gb300.api import Encoder
+    enc = Encoder(3, 16, 2, 19, 16.0, 1.38, table_dtype="bf16")
+    P = x_host.shape[0]
+    x = torch.from_numpy(x_host).to(dev)
+    dout = torch.from_numpy(synth.normal_grads(P, enc.n_out, 301)).to(dev)
+    grad = torch.zeros((enc.n_levels * enc.T, enc.n_features), dtype=torch.float32, device=dev)
+    lc = enc.bwd_coarse_levels(P)
+    st = torch.cuda.current_stream(dev).cuda_stream
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn(1)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        s.record()
+        for r in range(n):
+            fn(2 + r)
+        e.record()
+        torch.cuda.synchronize(dev)
+        return s.elapsed_time(e) / n / 1e3
+
+    sec = timed(lambda r: enc.encode_bwd(x, dout, grad, levels=(lc, enc.n_levels)), reps)
+    n_ops, slots = 1 << 24, grad.numel() // 2
+    sink = torch.zeros((1,), dtype=torch.float32, device=dev)
+    lib = L.lib()
+    probe = timed(lambda r: L.check(lib.sxe_probe_random_access(0, grad.data_ptr(), slots, 2, n_ops, r,
+                                                                sink.data_ptr(), st), "sxe_probe_random_access"), 5)
+    contributions = P * (enc.n_levels - lc) * enc.n_vertices
+    peak = n_ops / probe
+    return {"kernel": "encode_bwd (levels %d-%d, dense binary32 gradient, %d MiB)" % (lc, enc.n_levels - 1,
+                                                                                    grad.numel() * 4 >> 20),
+            "contributions": contributions, "measured_ms": sec * 1e3, "achieved_ops_per_s": contributions / sec,
+            "peak_ops_per_s": peak, "peak": "probe: random float2 reductions over the gradient array's footprint",
+            "frac": contributions / sec / peak}
 
 
 def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5):
