@@ -12,7 +12,7 @@ import textwrap
 
 import pytest
 
-from oracle import adam, encoding, lattice, mlp, render
+from oracle import adam, encoding, geometry, lattice, mlp, render
 
 import test_oracle_encoding as TE
 import test_oracle_lattice as TL
@@ -55,6 +55,18 @@ CASES = {
                                         "w[:, 0] = 1.0 - s[:, n - 1]", [P(TL.test_weights_reconstruct_point, 3)]),
     "weight difference sign": (lattice, "barycentric_weights", "s[:, k - 1] - s[:, k]", "s[:, k] - s[:, k - 1]",
                                [P(TL.test_weights_reconstruct_point, 3)]),
+    # geometry used by the pins (Remark 2, Theorem 1's proof, Sec. 5.1-5.2, Kuhn hat functions)
+    "Kuhn vertex steps along the unpermuted axis": (geometry, "kuhn_simplex", "V[i + 1, axis] = 1", "V[i + 1, i] = 1",
+                                                    [P(TL.test_subdivision_matches_brute_force, 3)]),
+    "barycentric solve without the partition of unity": (geometry, "barycentric_solve", "np.concatenate([[1.0],",
+                                                         "np.concatenate([[0.0],",
+                                                         [P(TL.test_subdivision_matches_brute_force, 3)]),
+    "cell volume without the scale adjustment": (geometry, "parallelepiped_volume", "S = math.sqrt(n + 1.0)",
+                                                 "S = 1.0", [TL.test_theoretical_memory_usage_figure]),
+    "hat function adds the one-sided extents": (geometry, "vertex_hat_weight", "1.0 - (hi - lo)", "1.0 - (hi + lo)",
+                                                [P(TL.test_weights_equal_hat_functions, 3)]),
+    "touched count at the unadjusted scale": (geometry, "touched_vertex_count", "s = N / math.sqrt(n + 1.0)",
+                                              "s = N / math.sqrt(n)", [TL.test_memory_usage_figure_exact]),
     # Sec. 5 (a) hash and the direct coarse indexing
     "hash axes added": (lattice, "hash_slot", "h ^= (vi", "h += (vi", [TL.test_hash_special_cases]),
     "hash multiplier of the next axis": (lattice, "hash_slot", "HASH_PRIMES[i]", "HASH_PRIMES[(i + 1) % n]",
