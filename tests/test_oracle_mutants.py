@@ -81,6 +81,13 @@ CASES = {
     "weights reversed in the interpolation": (encoding, "simplex_encode", '"pk,pkf->pf", w, H)',
                                               '"pk,pkf->pf", w[:, ::-1], H)',
                                               [P(TE.test_simplex_reproduces_affine_fields, 3)]),
+    "lookup in level 0's table": (encoding, "simplex_encode", "np.asarray(tables[l], dtype=np.float64)[slots]",
+                                  "np.asarray(tables[0], dtype=np.float64)[slots]",
+                                  [P(TE.test_simplex_reproduces_affine_fields, 3)]),
+    "level scale of the next level": (encoding, "simplex_encode", "simplex_level_vertices(x32, scales[l],",
+                                      "simplex_level_vertices(x32, scales[min(l + 1, L - 1)],",
+                                      [P(TE.test_simplex_reproduces_affine_fields, 3),
+                                       P(TE.test_backward_is_adjoint_of_forward, "simplex", 3)]),
     "backward scatters reversed weights": (encoding, "simplex_encode_bwd", "w[:, :, None] * dout",
                                            "w[:, ::-1, None] * dout",
                                            [P(TE.test_backward_is_adjoint_of_forward, "simplex", 3)]),
