@@ -98,6 +98,13 @@ CASES = {
                                       "np.stack([lo, hi], axis=1)", [P(TE.test_grid_weights_are_products, 3)]),
     "grid lerp swapped": (encoding, "grid_encode", "v0 * (1.0 - t) + v1 * t", "v0 * t + v1 * (1.0 - t)",
                           [P(TE.test_grid_reproduces_multilinear_fields, 3)]),
+    "grid lookup in level 0's table": (encoding, "grid_encode", "np.asarray(tables[l], dtype=np.float64)",
+                                       "np.asarray(tables[0], dtype=np.float64)",
+                                       [P(TE.test_grid_reproduces_multilinear_fields, 3)]),
+    "grid cell at level 0's resolution": (encoding, "grid_encode", "grid_level_cell(x32, res[l])",
+                                          "grid_level_cell(x32, res[0])",
+                                          [P(TE.test_grid_reproduces_multilinear_fields, 3),
+                                           P(TE.test_backward_is_adjoint_of_forward, "grid", 3)]),
     "grid backward reversed corners": (encoding, "grid_encode_bwd", "w[:, :, None] * dout",
                                        "w[:, ::-1, None] * dout",
                                        [P(TE.test_backward_is_adjoint_of_forward, "grid", 3)]),
