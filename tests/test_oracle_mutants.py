@@ -133,6 +133,9 @@ CASES = {
                                  [TE.test_mlp_finite_differences]),
     "loss gradient over rows only": (mlp, "l2_loss", "2.0 * r / r.size", "2.0 * r / len(r)",
                                      [TE.test_l2_loss_closed_form]),
+    "loss residual sign flipped in the square": (mlp, "l2_loss", "float(np.mean(r * r))", "float(np.mean(r * np.abs(r)))",
+                                                  [TE.test_l2_loss_closed_form]),
+    "loss as a sum": (mlp, "l2_loss", "float(np.mean(r * r))", "float(np.sum(r * r))", [TE.test_l2_loss_closed_form]),
     "adam second-moment correction with beta1": (adam, "adam_step", "(1.0 - beta2 ** t)", "(1.0 - beta1 ** t)",
                                                  [TE.test_adam_matches_library_and_skips_zero_grads]),
     "adam epsilon inside the root": (adam, "adam_step", "np.sqrt(v_hat) + eps", "np.sqrt(v_hat + eps)",
