@@ -138,6 +138,13 @@ CASES = {
     "loss as a sum": (mlp, "l2_loss", "float(np.mean(r * r))", "float(np.sum(r * r))", [TE.test_l2_loss_closed_form]),
     "adam second-moment correction with beta1": (adam, "adam_step", "(1.0 - beta2 ** t)", "(1.0 - beta1 ** t)",
                                                  [TE.test_adam_matches_library_and_skips_zero_grads]),
+    "adam first-moment correction with beta2": (adam, "adam_step", "m_new / (1.0 - beta1 ** t)",
+                                                "m_new / (1.0 - beta2 ** t)",
+                                                [TE.test_adam_matches_library_and_skips_zero_grads]),
+    "adam second moment of the raw gradient": (adam, "adam_step", "(1.0 - beta2) * g * g", "(1.0 - beta2) * np.abs(g)",
+                                               [TE.test_adam_matches_library_and_skips_zero_grads]),
+    "adam first moment without the decay": (adam, "adam_step", "m_new = beta1 * m +", "m_new = m +",
+                                            [TE.test_adam_matches_library_and_skips_zero_grads]),
     "adam epsilon inside the root": (adam, "adam_step", "np.sqrt(v_hat) + eps", "np.sqrt(v_hat + eps)",
                                      [TE.test_adam_matches_library_and_skips_zero_grads]),
     "adam skips negative gradients": (adam, "adam_step", "(g != 0.0)", "(g > 0.0)",
