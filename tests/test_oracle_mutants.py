@@ -161,6 +161,14 @@ CASES = {
                               [TR.test_sh_equals_scipy_real_basis]),
     "harmonic l=2 m=0 constant sign": (render, "sh_basis", "(3.0 * z * z - 1.0)", "(3.0 * z * z + 1.0)",
                                        [TR.test_sh_equals_scipy_real_basis, TR.test_sh_orthonormal_on_the_sphere]),
+    "harmonic l=2 xy term on yz": (render, "sh_basis", "out[:, 4] = c2 * x * y", "out[:, 4] = c2 * y * z",
+                                   [TR.test_sh_equals_scipy_real_basis, TR.test_sh_orthonormal_on_the_sphere]),
+    "harmonic l=3 m=-1 constant sign": (render, "sh_basis", "out[:, 11] = c3 * y * (5.0 * z * z - 1.0)",
+                                        "out[:, 11] = c3 * y * (5.0 * z * z + 1.0)",
+                                        [TR.test_sh_equals_scipy_real_basis, TR.test_sh_orthonormal_on_the_sphere]),
+    "harmonic l=3 xyz normalisation": (render, "sh_basis", "out[:, 10] = b3 * x * y * z",
+                                       "out[:, 10] = c3 * x * y * z",
+                                       [TR.test_sh_equals_scipy_real_basis, TR.test_sh_orthonormal_on_the_sphere]),
     "compositing gradient with T_k": (render, "composite_bwd", "Tk[:, k + 1, None] * rgb[:, k]",
                                       "Tk[:, k, None] * rgb[:, k]",
                                       [TR.test_composite_bwd_matches_central_differences,
