@@ -152,6 +152,12 @@ CASES = {
     # volumetric rendering (Sec. 6.2, Eq. 5)
     "weights without transmittance": (render, "composite", "w[:, i] = T * alpha", "w[:, i] = alpha",
                                       [TR.test_composite_equals_eq5_for_homogeneous_media]),
+    "opacity as the transmittance factor": (render, "composite", "alpha = -np.expm1(-sigma[:, i] * delta)",
+                                            "alpha = np.exp(-sigma[:, i] * delta)",
+                                            [TR.test_composite_equals_eq5_for_homogeneous_media]),
+    "opacity without delta": (render, "composite", "alpha = -np.expm1(-sigma[:, i] * delta)",
+                              "alpha = -np.expm1(-sigma[:, i])",
+                              [TR.test_composite_equals_eq5_for_homogeneous_media]),
     "transmittance without delta": (render, "composite", "T = T * np.exp(-sigma[:, i] * delta)",
                                     "T = T * np.exp(-sigma[:, i])",
                                     [TR.test_composite_equals_eq5_for_homogeneous_media]),
