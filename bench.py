@@ -57,6 +57,39 @@ def _traffic(stage):
     return nbytes if h.hexdigest() == sha else None
 
 
+_PROBE = None
+
+
+def probe_lib():
+    """The bench-only random-access probe (``bench_probe.cu`` beside this file), compiled for
+    sm_103a into ``_build/libsxeprobe.so`` on first use and loaded with ctypes."""
+    global _PROBE
+    if _PROBE is None:
+        import ctypes
+        from paper_2311_15439_gb300 import build as B
+        src = os.path.join(ROOT, "bench_probe.cu")
+        so = os.path.join(ROOT, "_build", "libsxeprobe.so")
+        os.makedirs(os.path.dirname(so), exist_ok=True)
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            subprocess.run([B.nvcc(), *B.ARCH, "-O3", "-lineinfo", "-shared", "-Xcompiler", "-fPIC", src,
+                            "-o", so + ".tmp"], check=True)
+            os.replace(so + ".tmp", so)
+        lib = ctypes.CDLL(so)
+        fn = lib.sxe_probe_random_access
+        fn.restype = ctypes.c_int
+        fn.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                       ctypes.c_void_p, ctypes.c_void_p]
+        _PROBE = fn
+    return _PROBE
+
+
+def probe(kind, buf_ptr, n_slots, slot_floats, n_ops, seed, sink_ptr, stream):
+    """One launch of the random-access probe; raises on an argument or launch error."""
+    rc = probe_lib()(kind, buf_ptr, n_slots, slot_floats, n_ops, seed, sink_ptr, stream)
+    if rc != 0:
+        raise RuntimeError("sxe_probe_random_access failed with status %d" % rc)
+
+
 def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -158,7 +191,7 @@ def make_batches(n, seed0=1000):
 
 
 def _stage_work(n_touched, F=2, L=16, d=2, width=64, n_in=32):
-    """Algorithmic work of each timed kernel of one step (stated in the design notes):
+    """Algorithmic work of each timed kernel of one step:
     bytes for the memory-bound kernels, FLOPs for the network."""
     V = d + 1
     fwd = BATCH * (4 * d + L * V * 2 * F + L * F * 2)              # x, fp16 gathers, fp16 encoding
@@ -423,12 +456,11 @@ def random_access_peaks(dev, state_bytes, table, n_ops=1 << 24, reps=5):
     for name, (kind, b, slots, sf) in cases.items():
         if sf < 2:          # 4-byte gathers: slots of 2 floats over the first half of the table words
             slots, sf = slots // 2, 2
-        lib.sxe_probe_random_access(kind, b.data_ptr(), slots, sf, n_ops, 1, sink.data_ptr(), st)
+        probe(kind, b.data_ptr(), slots, sf, n_ops, 1, sink.data_ptr(), st)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
         for r in range(reps):
-            L.check(lib.sxe_probe_random_access(kind, b.data_ptr(), slots, sf, n_ops, 2 + r, sink.data_ptr(), st),
-                    "sxe_probe_random_access")
+            probe(kind, b.data_ptr(), slots, sf, n_ops, 2 + r, sink.data_ptr(), st)
         e.record()
         torch.cuda.synchronize(dev)
         out[name] = n_ops * reps / (s.elapsed_time(e) / 1e3)
@@ -579,11 +611,11 @@ def per_config_encode(dev):
             words = tab.view(torch.float32).reshape(-1) if tab.element_size() == 4 else tab.view(torch.float32)
             slots = 1 << int(math.log2(words.numel() // 2))
             n_ops = 1 << 24
-            lib.sxe_probe_random_access(1, words.data_ptr(), slots, 2, n_ops, 1, sink.data_ptr(), st)
+            probe(1, words.data_ptr(), slots, 2, n_ops, 1, sink.data_ptr(), st)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             for r in range(3):
-                lib.sxe_probe_random_access(1, words.data_ptr(), slots, 2, n_ops, 2 + r, sink.data_ptr(), st)
+                probe(1, words.data_ptr(), slots, 2, n_ops, 2 + r, sink.data_ptr(), st)
             b.record()
             torch.cuda.synchronize(dev)
             peak = 3 * n_ops / (a.elapsed_time(b) / 1e3)
@@ -711,10 +743,9 @@ def dense_bwd_roofline(dev, x_host, reps=20):
     n_ops, slots = 1 << 24, grad.numel() // 2
     sink = torch.zeros((1,), dtype=torch.float32, device=dev)
     lib = L.lib()
-    probe = timed(lambda r: L.check(lib.sxe_probe_random_access(0, grad.data_ptr(), slots, 2, n_ops, r,
-                                                                sink.data_ptr(), st), "sxe_probe_random_access"), 5)
+    probe_s = timed(lambda r: probe(0, grad.data_ptr(), slots, 2, n_ops, r, sink.data_ptr(), st), 5)
     contributions = P * (enc.n_levels - lc) * enc.n_vertices
-    peak = n_ops / probe
+    peak = n_ops / probe_s
     return {"kernel": "encode_bwd (levels %d-%d, dense binary32 gradient, %d MiB)" % (lc, enc.n_levels - 1,
                                                                                     grad.numel() * 4 >> 20),
             "contributions": contributions, "measured_ms": sec * 1e3, "achieved_ops_per_s": contributions / sec,

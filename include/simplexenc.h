@@ -250,19 +250,6 @@ sxe_status sxe_vr_composite(const float* sigma, const float* rgb_logits, const f
                             int64_t n_rays, int32_t n_samples, float* color,
                             float* transmittance, float* weights, void* stream);
 
-/* Measurement aid (no counterpart in the paper): n_ops scattered accesses to random slots
- * of buf [n_slots][slot_floats] binary32 (n_slots a power of two, slot_floats even, 2..64),
- * slot = mix64(seed ^ i) mod n_slots with a counter-based 64-bit mixer:
- *   kind 0: a float2 atomic add of (1, 1) into the slot's last two floats
- *           (the shape of the table backward's reductions into state records);
- *   kind 1: a 4-byte load of the slot's first float (the shape of the forward gathers);
- *           sink [1] is written only if the loaded sum is -1;
- *   kind 2: a read and write back of the whole 32-byte slot (slot_floats = 8, buf 16-byte
- *           aligned; the shape of the table optimiser), four slots in flight per thread.
- * Timed by the caller to give the peak rate of that pattern for a given footprint. */
-sxe_status sxe_probe_random_access(int32_t kind, float* buf, int64_t n_slots, int32_t slot_floats,
-                                   int64_t n_ops, uint64_t seed, float* sink, void* stream);
-
 /* Backward of sxe_vr_composite for upstream colour gradients dcolor [n_rays][3]: with
  * w_k = T_k alpha_k and P_k = sum_{i<=k} w_i c_i,
  *   dsigma[k] = delta sum_c dcolor_c (T_{k+1} c_k,c - (color_c - P_k,c)),
@@ -423,8 +410,9 @@ sxe_status sxe_step_touched(const sxe_adam_desc* desc, int64_t t, int64_t n_entr
 /* Step counter on the device, for training loops captured into a CUDA graph (where a host-side
  * t would be frozen at capture): sxe_adam_advance increments t (int64, device) and writes the
  * bias corrections of the new t, corrections[0] = 1/(1-beta1^t) and corrections[1] =
- * 1/(1-beta2^t) (binary32, device; FP64 then rounded once, as the host form does); one thread,
- * on `stream`.  sxe_step_dev and sxe_step_touched_dev are sxe_step and sxe_step_touched with
+ * 1/(1-beta2^t) (binary32, device), formed in double-word binary32 arithmetic (about 48
+ * significant bits; no FP64 instruction runs on the device) and rounded once, within one binary32
+ * ulp of the exactly rounded value; one thread per beta, on `stream`.  sxe_step_dev and sxe_step_touched_dev are sxe_step and sxe_step_touched with
  * the corrections read from that device array when the kernel runs. */
 sxe_status sxe_adam_advance(const sxe_adam_desc* desc, int64_t* t, float* corrections, void* stream);
 sxe_status sxe_step_dev(const sxe_adam_desc* desc, const float* corrections, int64_t n, float* param,

@@ -12,7 +12,7 @@ Restates, in the paper's order and notation:
   sorted fractional parts s (Sec. 4.3, from the proof of Theorem 1);
 * the vertex hash of Sec. 5 (a) (each vertex's integer coordinates are hashed).
 
-Readings where the paper is silent (each also listed in the design notes):
+Readings where the paper is silent:
 
 * Level resolution N_l = floor(base * growth^l), the Instant-NGP rule the
   backbone of Sec. 5 uses; no +0.5 offset; the point is used as given.

@@ -28,7 +28,7 @@ EXPORTS = (
     "sxe_encode_vertices",
     "sxe_encode_plain_fwd", "sxe_encode_plain_bwd", "sxe_vr_samples", "sxe_vr_field", "sxe_vr_field_mlp", "sxe_vr_composite",
     "sxe_vr_composite_bwd", "sxe_vr_field_bwd",
-    "sxe_probe_random_access", "sxe_adam_advance", "sxe_step_dev", "sxe_step_touched_dev",
+    "sxe_adam_advance", "sxe_step_dev", "sxe_step_touched_dev",
     "sxe_mlp_n_params", "sxe_mlp_fwd", "sxe_mlp_bwd_workspace_bytes", "sxe_mlp_bwd", "sxe_mlp_train_l2",
     "sxe_loss_l2", "sxe_step", "sxe_step_touched", "sxe_last_error", "sxe_version",
     "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped",
@@ -77,7 +77,6 @@ def _declare(L):
         "sxe_encode_vertices": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_encode_plain_fwd": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_vr_samples": (i32, [vp, vp, vp, vp, i64, i32, vp, vp, vp]),
-        "sxe_probe_random_access": (i32, [i32, vp, i64, i32, i64, ctypes.c_uint64, vp, vp]),
         "sxe_adam_advance": (i32, [A, vp, vp, vp]),
         "sxe_step_dev": (i32, [A, vp, i64, vp, vp, vp, vp, vp, i32, vp]),
         "sxe_step_touched_dev": (i32, [A, vp, i64, i32, vp, vp, vp, i32, vp]),

@@ -21,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsimplexenc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I", os.path.join(ROOT, "include")]
+         "-Xptxas", "--warn-on-double-precision-use", "-I", os.path.join(ROOT, "include")]
 
 
 def nvcc() -> str:
@@ -46,6 +46,11 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
         sys.stderr.write(res.stdout + res.stderr)
     if res.returncode != 0:
         raise RuntimeError("nvcc failed on %s" % src)
+    if "double" in (res.stdout + res.stderr).lower():
+        # no device code of the library computes in FP64: ptxas reports any FP64 instruction
+        os.remove(obj)
+        sys.stderr.write(res.stdout + res.stderr)
+        raise RuntimeError("FP64 instruction in the device code of %s" % src)
     return obj
 
 

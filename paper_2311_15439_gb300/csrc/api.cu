@@ -6,7 +6,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "sxe_internal.cuh"
 
@@ -25,6 +28,56 @@ sxe_status set_error(sxe_status st, const char* fmt, ...) {
 sxe_status check_launch(const char* what) {
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(SXE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return SXE_OK;
+}
+
+// Launch set-up cached per device: a kernel's dynamic shared-memory limit and its occupancy
+// belong to the device that is current when they are set or queried, so a second device in the
+// same process gets its own set-up instead of inheriting (or missing) the first one's.
+static std::mutex g_setup_mu;
+static std::map<int, int> g_sms;
+static std::map<std::tuple<int, const void*, int, int>, int> g_ctas;
+
+static int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  return dev;
+}
+
+int device_sm_count() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  auto it = g_sms.find(dev);
+  if (it != g_sms.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+  g_sms[dev] = n;
+  return n;
+}
+
+int kernel_ctas_per_sm(const void* kernel, int threads, int smem_bytes) {
+  const int dev = current_device();
+  const auto key = std::make_tuple(dev, kernel, threads, smem_bytes);
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  auto it = g_ctas.find(key);
+  if (it != g_ctas.end()) return it->second;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, (size_t)smem_bytes) != cudaSuccess || n < 1)
+    n = 1;
+  cudaGetLastError();   // a refused attribute shows up at launch, not here
+  g_ctas[key] = n;
+  return n;
+}
+
+sxe_status check_mlp(const char* fn, const sxe_mlp_desc* d) {
+  if (!d) return set_error(SXE_EINVAL, "%s: NULL desc", fn);
+  if (d->width != 64) return set_error(SXE_EUNSUPPORTED, "%s: width=%d (only 64 is built)", fn, d->width);
+  if (!(d->n_in == 16 || d->n_in == 32 || d->n_in == 64))
+    return set_error(SXE_EUNSUPPORTED, "%s: n_in=%d not in {16,32,64}", fn, d->n_in);
+  if (d->n_hidden < 1 || d->n_hidden > 3) return set_error(SXE_EUNSUPPORTED, "%s: n_hidden=%d not in 1..3", fn, d->n_hidden);
+  if (d->n_out < 1 || d->n_out > 16) return set_error(SXE_EINVAL, "%s: n_out=%d not in 1..16", fn, d->n_out);
+  if (d->dtype != SXE_F16 && d->dtype != SXE_BF16) return set_error(SXE_EINVAL, "%s: dtype must be F16 or BF16", fn);
   return SXE_OK;
 }
 
@@ -128,7 +181,10 @@ sxe_status sxe_encoder_level_params(const sxe_encoder* e, float* scale, int32_t*
 
 static sxe_status check_points(const char* fn, const sxe_encoder* e, const float* x, int64_t P) {
   if (!e) return set_error(SXE_EINVAL, "%s: NULL encoder", fn);
-  if (P < 0 || P > ((int64_t)1 << 40) / e->desc.n_levels) return set_error(SXE_EINVAL, "%s: n_points=%lld out of range", fn, (long long)P);
+  // the encoding kernels run one thread per (point, level): P * L <= 2^38 keeps their grids of
+  // P * L / 256 blocks far inside the 2^31 - 1 limit of gridDim.x
+  if (P < 0 || P > ((int64_t)1 << 38) / e->desc.n_levels)
+    return set_error(SXE_EINVAL, "%s: n_points=%lld out of range (n_points * n_levels <= 2^38)", fn, (long long)P);
   if (P > 0 && !x) return set_error(SXE_EINVAL, "%s: NULL x", fn);
   const size_t xa = e->desc.d == 2 ? 8 : e->desc.d == 4 ? 16 : 4;
   if (!aligned(x, xa)) return set_error(SXE_EINVAL, "%s: x must be %zu-byte aligned for d=%d", fn, xa, e->desc.d);
@@ -270,20 +326,6 @@ sxe_status sxe_vr_composite(const float* sigma, const float* rgb_logits, const f
   return launch_vr_composite(sigma, rgb_logits, delta, R, S, color, transmittance, weights, (cudaStream_t)stream);
 }
 
-sxe_status sxe_probe_random_access(int32_t kind, float* buf, int64_t n_slots, int32_t slot_floats, int64_t n_ops,
-                                   uint64_t seed, float* sink, void* stream) {
-  if (kind < 0 || kind > 2) return set_error(SXE_EINVAL, "probe_random_access: kind must be 0, 1 or 2");
-  if (kind == 2 && slot_floats != 8) return set_error(SXE_EINVAL, "probe_random_access: kind 2 needs slot_floats = 8");
-  if (n_slots < 1 || (n_slots & (n_slots - 1)) != 0 || n_slots > ((int64_t)1 << 34))
-    return set_error(SXE_EINVAL, "probe_random_access: n_slots must be a power of two");
-  if (slot_floats < 2 || slot_floats > 64 || (slot_floats & 1) || n_ops < 0)
-    return set_error(SXE_EINVAL, "probe_random_access: slot_floats must be even in 2..64");
-  if (!buf || !sink || !aligned(buf, kind == 2 ? 16 : 8))
-    return set_error(SXE_EINVAL, "probe_random_access: NULL or misaligned buffer");
-  if (n_ops == 0) return SXE_OK;
-  return launch_probe(kind, buf, n_slots, slot_floats, n_ops, seed, sink, (cudaStream_t)stream);
-}
-
 sxe_status sxe_encode_vertices(const sxe_encoder* e, const float* x, int64_t P, uint32_t* slots, float* weights,
                                void* stream) {
   sxe_status st = check_points("encode_vertices", e, x, P);
@@ -318,17 +360,6 @@ sxe_status sxe_encode_plain_bwd(const sxe_encoder* e, const float* x, int64_t P,
 }
 
 // ---------------------------------------------------------------------------
-static sxe_status check_mlp(const char* fn, const sxe_mlp_desc* d) {
-  if (!d) return set_error(SXE_EINVAL, "%s: NULL desc", fn);
-  if (d->width != 64) return set_error(SXE_EUNSUPPORTED, "%s: width=%d (only 64 is built)", fn, d->width);
-  if (!(d->n_in == 16 || d->n_in == 32 || d->n_in == 64))
-    return set_error(SXE_EUNSUPPORTED, "%s: n_in=%d not in {16,32,64}", fn, d->n_in);
-  if (d->n_hidden < 1 || d->n_hidden > 3) return set_error(SXE_EUNSUPPORTED, "%s: n_hidden=%d not in 1..3", fn, d->n_hidden);
-  if (d->n_out < 1 || d->n_out > 16) return set_error(SXE_EINVAL, "%s: n_out=%d not in 1..16", fn, d->n_out);
-  if (d->dtype != SXE_F16 && d->dtype != SXE_BF16) return set_error(SXE_EINVAL, "%s: dtype must be F16 or BF16", fn);
-  return SXE_OK;
-}
-
 sxe_status sxe_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
                             const void* enc, const float* dirs, int64_t R, int32_t S, float* sigma, float* logits,
                             void* stream) {

@@ -541,9 +541,7 @@ CoarsePlan coarse_plan(const sxe_encoder* e, int64_t P) {
   CoarsePlan plan{};
   const int d = e->desc.d, F = e->desc.n_features;
   const int64_t V = e->desc.kind == SXE_SIMPLEX ? d + 1 : (1 << d);
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = device_sm_count();
   plan.start[0] = 0;
   for (int c = 0; c < kMaxCoarse && c < e->prm.n_levels; ++c) {
     const uint32_t B = e->box_width[c];

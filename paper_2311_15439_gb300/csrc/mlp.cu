@@ -347,7 +347,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename T, int N_IN, int NH, int MODE>
 __global__ void __launch_bounds__(kThreads, BwdOcc<N_IN, NH>::value)
 mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
-               const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
+               const float* __restrict__ dout, const float* __restrict__ target, float loss_scale, float inv_count,
                float* __restrict__ din, float* __restrict__ ws, int64_t n_params, float* __restrict__ sq_sum,
                int din_group) {
   using S = Smem<N_IN, NH>;
@@ -357,7 +357,6 @@ mlp_bwd_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int r0 = warp * 16;
   const int64_t n_tiles = (P + kTile - 1) / kTile;
-  const float inv_count = 2.f / (float)((double)P * n_out);
   float dw[S::TILES_PER_WARP][4];
 #pragma unroll
   for (int i = 0; i < S::TILES_PER_WARP; ++i) dw[i][0] = dw[i][1] = dw[i][2] = dw[i][3] = 0.f;
@@ -663,33 +662,16 @@ int g_mlp_kernel = SXE_MLP_KERNEL_AUTO;
 
 namespace {
 
-int g_num_sms = 0;
 int num_sms();
 
 // CTAs of the backward kernel that fit on one SM (shared memory and registers), cached.
 template <typename T, int N_IN, int NH, int MODE>
 int bwd_ctas_per_sm() {
-  static int cached = 0;
-  if (cached == 0) {
-    auto k = mlp_bwd_kernel<T, N_IN, NH, MODE>;
-    const int bytes = Smem<N_IN, NH>::BWD_END * (int)sizeof(T);
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, bytes) != cudaSuccess || n < 1) n = 1;
-    cached = n;
-  }
-  return cached;
+  return kernel_ctas_per_sm((const void*)mlp_bwd_kernel<T, N_IN, NH, MODE>, kThreads,
+                            Smem<N_IN, NH>::BWD_END * (int)sizeof(T));
 }
 
-int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    g_num_sms = n > 0 ? n : 148;
-  }
-  return g_num_sms;
-}
+int num_sms() { return device_sm_count(); }
 
 template <typename T, int N_IN, int NH>
 sxe_status fwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,
@@ -697,12 +679,7 @@ sxe_status fwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, int6
   using S = Smem<N_IN, NH>;
   const size_t bytes = (size_t)S::FWD_END * sizeof(T);   // weights + input tile
   auto k = mlp_fwd_kernel<T, N_IN, NH>;
-  static int per_sm = 0;                        // resident CTAs per SM (registers, shared memory)
-  if (per_sm == 0) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, bytes) != cudaSuccess || per_sm < 1)
-      per_sm = 2;
-  }
+  const int per_sm = kernel_ctas_per_sm((const void*)k, kThreads, (int)bytes);   // registers, shared memory
   const int64_t n_tiles = (P + kTile - 1) / kTile;
   const int grid = (int)std::min<int64_t>(n_tiles, (int64_t)per_sm * num_sms());
   k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, out, (T*)act);
@@ -714,12 +691,7 @@ sxe_status field_launch(const void* Wd, const void* Wc, const void* enc, const f
                         int n_out_c, float* sigma, float* logits, cudaStream_t s) {
   const size_t bytes = (size_t)(Smem<N_IN, 1>::FWD_END + Smem<32, NHC>::FWD_END) * sizeof(T);
   auto k = vr_field_mlp_kernel<T, N_IN, NHC>;
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, bytes) != cudaSuccess || per_sm < 1)
-      per_sm = 1;
-  }
+  const int per_sm = kernel_ctas_per_sm((const void*)k, kThreads, (int)bytes);
   const int64_t n_tiles = (P + kTile - 1) / kTile;
   const int grid = (int)std::min<int64_t>(n_tiles, (int64_t)per_sm * num_sms());
   k<<<grid, kThreads, bytes, s>>>((const T*)Wd, (const T*)Wc, (const T*)enc, dirs, P, S, n_out_c, sigma, logits);
@@ -755,14 +727,14 @@ sxe_status bwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
   const int64_t n_params = sxe_mlp_n_params(d);
   if (target) {
     auto k = mlp_bwd_kernel<T, N_IN, NH, 1>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale, din, ws,
-                                    n_params, sq_sum, din_group);
+    kernel_ctas_per_sm((const void*)k, kThreads, (int)bytes);
+    k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale,
+                                    l2_inv_count(P, d->n_out), din, ws, n_params, sq_sum, din_group);
   } else {
     auto k = mlp_bwd_kernel<T, N_IN, NH, 0>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale, din, ws,
-                                    n_params, sq_sum, din_group);
+    kernel_ctas_per_sm((const void*)k, kThreads, (int)bytes);
+    k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale,
+                                    l2_inv_count(P, d->n_out), din, ws, n_params, sq_sum, din_group);
   }
   sxe_status st = check_launch("mlp_bwd");
   if (st != SXE_OK) return st;

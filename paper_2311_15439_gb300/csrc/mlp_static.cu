@@ -63,10 +63,8 @@ using namespace sxe;
 extern "C" sxe_status sxe_mlp_train_l2_static(const sxe_mlp_desc* d, const void* W, const void* in,
                                               const float* target, float loss_scale, int64_t P, float* din,
                                               float* dW, float* sq_sum, void* stream) {
-  if (!d) return set_error(SXE_EINVAL, "mlp_train_l2_static: NULL desc");
-  if (d->width != 64 || !(d->n_in == 16 || d->n_in == 32 || d->n_in == 64) || d->n_hidden < 1 ||
-      d->n_hidden > 3 || d->n_out < 1 || d->n_out > 16 || (d->dtype != SXE_F16 && d->dtype != SXE_BF16))
-    return set_error(SXE_EUNSUPPORTED, "mlp_train_l2_static: network shape or dtype not built");
+  sxe_status st = check_mlp("mlp_train_l2_static", d);
+  if (st != SXE_OK) return st;
   if (P < 0) return set_error(SXE_EINVAL, "mlp_train_l2_static: n_points < 0");
   if (!(loss_scale > 0.f) || !isfinite(loss_scale)) return set_error(SXE_EINVAL, "mlp_train_l2_static: loss_scale must be > 0");
   if (P > 0 && (!target || !sq_sum || !W || !in || !dW))
@@ -79,7 +77,7 @@ extern "C" sxe_status sxe_mlp_train_l2_static(const sxe_mlp_desc* d, const void*
                      (long long)per_cta, SXE_MLP_STATIC_SCRATCH_FLOATS);
   if (P == 0) return SXE_OK;
   float* ws = nullptr;
-  sxe_status st = scratch_for_current_device(&ws);
+  st = scratch_for_current_device(&ws);
   if (st != SXE_OK) return st;
   // the persistent grid is cut down to what the static scratch holds (results do not
   // depend on the grid beyond the summation order of the weight-gradient partials)

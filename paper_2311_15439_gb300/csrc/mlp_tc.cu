@@ -161,7 +161,7 @@ __device__ __forceinline__ void issue_gemm(uint32_t tmem, const unsigned char* A
 template <typename T, int N_IN, int NH, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
 mlp_train_tc_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
-                    const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
+                    const float* __restrict__ dout, const float* __restrict__ target, float loss_scale, float inv_count,
                     float* __restrict__ din, int din_group, float* __restrict__ ws, int64_t n_params) {
   using S = TcSmem<N_IN, NH>;
   constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
@@ -174,7 +174,6 @@ mlp_train_tc_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P
   const int quad = warp & 3, half = warp >> 2;
   const int r = quad * 32 + lane;                       // this thread's tile row / TMEM lane
   const int64_t n_tiles = (P + kM - 1) / kM;
-  const float inv_count = 2.f / (float)((double)P * n_out);
   const float inv_scale = 1.f / loss_scale;
 
   load_weights_cm<T, N_IN, NH>(W, n_out, sm);
@@ -472,7 +471,7 @@ __device__ __forceinline__ void tc2_tile(int i, int q, int n_out, int& mt, int& 
 template <typename T, int N_IN, int NH, int MODE, bool TCW>
 __global__ void __launch_bounds__(kThreads, 1)
 mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
-                     const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
+                     const float* __restrict__ dout, const float* __restrict__ target, float loss_scale, float inv_count,
                      float* __restrict__ din, int din_group, float* __restrict__ ws, int64_t n_params) {
   using S = Tc2Smem<N_IN, NH>;
   constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
@@ -486,7 +485,6 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
   const bool issuer = (tid & 127) == 0;
   const int r = q * 32 + lane;                          // this thread's tile row / TMEM lane
   const int64_t n_tiles = (P + kM - 1) / kM;
-  const float inv_count = 2.f / (float)((double)P * n_out);
   const float inv_scale = 1.f / loss_scale;
   unsigned char* gs = sm + g * S::GROUP;                // this group's buffers
 
@@ -837,16 +835,7 @@ namespace {
 
 template <typename T, int N_IN, int NH, int MODE>
 int tc_ctas_per_sm() {
-  static int cached = 0;
-  if (cached == 0) {
-    auto k = mlp_train_tc_kernel<T, N_IN, NH, MODE>;
-    const int bytes = TcSmem<N_IN, NH>::END;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, bytes) != cudaSuccess || n < 1) n = 1;
-    cached = n;
-  }
-  return cached;
+  return kernel_ctas_per_sm((const void*)mlp_train_tc_kernel<T, N_IN, NH, MODE>, kThreads, TcSmem<N_IN, NH>::END);
 }
 
 // Two-tile kernel: one CTA per SM, two partial rows per CTA (the workspace holds `grid` rows).
@@ -861,20 +850,16 @@ sxe_status tc2_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
   const int64_t n_params = sxe_mlp_n_params(d);
   const int64_t n_tiles = (P + kM - 1) / kM;
   const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)sms, (int64_t)(grid / 2), (n_tiles + 1) / 2}));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(mlp_train_tc2_kernel<T, N_IN, NH, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         bytes);
-    cudaFuncSetAttribute(mlp_train_tc2_kernel<T, N_IN, NH, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         bytes);
-    attr = true;
-  }
+  kernel_ctas_per_sm((const void*)mlp_train_tc2_kernel<T, N_IN, NH, 0, true>, kThreads, bytes);
+  kernel_ctas_per_sm((const void*)mlp_train_tc2_kernel<T, N_IN, NH, 1, true>, kThreads, bytes);
   if (target)
     mlp_train_tc2_kernel<T, N_IN, NH, 1, true><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out,
-                                                                          dout, target, ls, din, dg, ws, n_params);
+                                                                          dout, target, ls, l2_inv_count(P, d->n_out),
+                                                                          din, dg, ws, n_params);
   else
     mlp_train_tc2_kernel<T, N_IN, NH, 0, true><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out,
-                                                                          dout, target, ls, din, dg, ws, n_params);
+                                                                          dout, target, ls, l2_inv_count(P, d->n_out),
+                                                                          din, dg, ws, n_params);
   sxe_status st = check_launch("mlp_train_tc2");
   if (st != SXE_OK) return st;
   return launch_mlp_reduce(ws, 2 * g2, n_params, 1.f / ls, dW, target ? sq : nullptr, s);
@@ -885,20 +870,18 @@ sxe_status tc_launch(const sxe_mlp_desc* d, const void* W, const void* in, const
                      float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
   const int bytes = TcSmem<N_IN, NH>::END;
   const int64_t n_params = sxe_mlp_n_params(d);
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = device_sm_count();
   if constexpr (Tc2Smem<N_IN, NH>::END <= kMaxDynSmem) {
     if (grid >= 2) return tc2_launch<T, N_IN, NH>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, sms, s);
   }
   if (target) {
     grid = std::min(grid, sms * tc_ctas_per_sm<T, N_IN, NH, 1>());
     mlp_train_tc_kernel<T, N_IN, NH, 1><<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
-                                                                     target, ls, din, dg, ws, n_params);
+                                                                     target, ls, l2_inv_count(P, d->n_out), din, dg, ws, n_params);
   } else {
     grid = std::min(grid, sms * tc_ctas_per_sm<T, N_IN, NH, 0>());
     mlp_train_tc_kernel<T, N_IN, NH, 0><<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
-                                                                     target, ls, din, dg, ws, n_params);
+                                                                     target, ls, l2_inv_count(P, d->n_out), din, dg, ws, n_params);
   }
   sxe_status st = check_launch("mlp_train_tc");
   if (st != SXE_OK) return st;

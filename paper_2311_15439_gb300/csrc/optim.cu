@@ -158,19 +158,52 @@ __global__ void loss_l2_kernel(const float* __restrict__ y, const float* __restr
   }
 }
 
+// Double-word binary32 arithmetic (Dekker 1971; the bounds of Joldes, Muller and Popescu, "Tight and
+// rigorous error bounds for basic building blocks of double-word arithmetic", 2017): a value is the
+// unevaluated sum hi + lo of two binary32 numbers with |lo| <= ulp(hi) / 2, about 48 significant
+// bits.  The product uses the exact error of a binary32 product, fmaf(a, b, -a*b); every other
+// operation is an explicitly rounded intrinsic so that no contraction changes the error terms.
+struct Dw {
+  float hi, lo;
+};
+
+__device__ __forceinline__ Dw dw_mul(Dw a, Dw b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);                  // a.hi * b.hi = p + e exactly
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));  // cross terms (a.lo * b.lo is below u^2)
+  const float s = __fadd_rn(p, e);                      // Fast2Sum renormalisation, |p| >= |e|
+  return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+// 1 / (1 - b) for a double-word b in [0, 1), rounded to binary32: 1 - b by Fast2Sum (|1| >= |b.hi|),
+// then one Newton correction of the correctly rounded reciprocal of the leading part, whose
+// residual 1 - d.hi * r is exact in one fma.
+__device__ __forceinline__ float dw_recip_one_minus(Dw b) {
+  const float s = __fadd_rn(1.f, -b.hi);
+  const float z = __fsub_rn(s, 1.f);
+  const float err = __fsub_rn(-b.hi, z);                // 1 - b.hi = s + err exactly
+  const float lo = __fsub_rn(err, b.lo);
+  const float dh = __fadd_rn(s, lo), dl = __fsub_rn(lo, __fsub_rn(dh, s));
+  const float r = __frcp_rn(dh);
+  const float res = __fmaf_rn(-dl, r, __fmaf_rn(-dh, r, 1.f));   // 1 - (dh + dl) r
+  return __fmaf_rn(r, res, r);
+}
+
 // Two threads: the step count t += 1 and the bias corrections 1 / (1 - beta_i^t) of the new t,
-// thread i for beta_i, in FP64 rounded once to binary32.  beta^t by binary exponentiation (about
-// 2 log2 t dependent FP64 products, each rounded once, so within a few ulps of FP64 of the exact
-// power, far below the binary32 rounding that follows): FP64 latency is long on this part, and a
-// general pow() is a much longer dependent chain on the critical path of every step.
+// thread i for beta_i.  beta^t by binary exponentiation in double-word binary32 arithmetic (about
+// 2 log2 t products, each with a relative error of a few 2^-48), then 1 / (1 - beta^t) as above:
+// the amplification 1 / (1 - beta) <= 100 of the subtraction for beta <= 0.99 keeps the result
+// far inside half a binary32 ulp of the exact value before its last rounding.  No FP64 on the
+// device.  Near underflow the low parts lose their meaning, but beta^t is then below 2^-100 and
+// 1 - beta^t rounds to 1 either way.
 __global__ void adam_advance_kernel(int64_t* __restrict__ t, float* __restrict__ c, float b1, float b2) {
   const int64_t tn = *t + 1;
-  double p = 1.0, x = threadIdx.x == 0 ? (double)b1 : (double)b2;
+  Dw p = {1.f, 0.f}, x = {threadIdx.x == 0 ? b1 : b2, 0.f};
   for (int64_t e = tn; e > 0; e >>= 1) {
-    if (e & 1) p *= x;
-    x *= x;
+    if (e & 1) p = dw_mul(p, x);
+    x = dw_mul(x, x);
   }
-  c[threadIdx.x] = (float)(1.0 / (1.0 - p));
+  c[threadIdx.x] = dw_recip_one_minus(p);
   __syncthreads();                                      // both threads have read the old t
   if (threadIdx.x == 0) *t = tn;
 }
@@ -203,9 +236,7 @@ sxe_status launch_adam_touched(const sxe_adam_desc* a, int64_t t, int64_t n_entr
   AdamConst k = make_adam_const(a, corrections ? 1 : t);
   k.cdev = corrections;
   // one warp per 32 bitmap words, at most 16 blocks of 8 warps per SM
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = device_sm_count();
   const int64_t chunks = (((n_entries + 31) >> 5) + 31) >> 5;
   const unsigned nb = blocks_for(chunks * 32, 256, (unsigned)(16 * sms));
   switch (F) {

@@ -45,6 +45,17 @@ namespace sxe {
 sxe_status set_error(sxe_status st, const char* fmt, ...);
 sxe_status check_launch(const char* what);
 
+// Launch set-up of the current device, cached per device (defined in api.cu): its SM count, and
+// for a kernel the resident CTAs per SM at `threads` threads and `smem_bytes` of dynamic shared
+// memory, after raising the kernel's dynamic shared-memory limit to `smem_bytes` on that device.
+int device_sm_count();
+int kernel_ctas_per_sm(const void* kernel, int threads, int smem_bytes);
+// 2 / (P n_out), the factor of the L2 loss's gradient dy = 2 (y - t) / (P n_out), rounded on the
+// host so that no kernel needs FP64 to form it exactly (P n_out exceeds 2^24).
+inline float l2_inv_count(int64_t P, int n_out) { return 2.f / (float)((double)P * n_out); }
+// Shape and dtype check of a network description, shared by every network entry point.
+sxe_status check_mlp(const char* fn, const sxe_mlp_desc* d);
+
 // launchers (defined in encode.cu / mlp.cu / optim.cu); arguments already validated
 sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
                              void* out, cudaStream_t s, int64_t table_stride = 0);
@@ -65,8 +76,6 @@ sxe_status launch_vr_samples(const float* o, const float* d, const float* tn, co
                              float* x, float* delta, cudaStream_t s);
 sxe_status launch_vr_field(const float* dens, const float* dirs, int64_t R, int S, int dtype, float* sigma,
                            void* cin, cudaStream_t s);
-sxe_status launch_probe(int kind, float* buf, int64_t n_slots, int slot_floats, int64_t n_ops, uint64_t seed,
-                        float* sink, cudaStream_t s);
 sxe_status launch_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
                                const void* enc, const float* dirs, int64_t R, int S, float* sigma, float* logits,
                                cudaStream_t s);

@@ -35,6 +35,16 @@ def test_library_exports_every_declared_symbol(L):
     assert b"sm_103a" in lib.sxe_version()
 
 
+def test_library_exports_nothing_undeclared(L):
+    """The product library's dynamic symbols are exactly the header's entry points (the
+    bench-only random-access probe lives in its own library, beside the benchmark)."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = sorted({ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("sxe_")})
+    assert exported == _declared_functions()
+    assert "sxe_probe_random_access" not in exported
+
+
 def _desc(L, **kw):
     base = dict(d=2, n_levels=8, n_features=2, log2_T=14, base_res=16.0, growth=1.5, kind=L.SXE_SIMPLEX,
                 res_mode=L.SXE_RES_RAW, table_dtype=L.SXE_F32, out_dtype=L.SXE_F32)

@@ -378,21 +378,48 @@ def test_coarse_levels_on_a_second_stream_equal_plain_step(layout):
         assert int(b.touched.abs().sum().item()) == 0
 
 
+def _bias_corrections(b1, b2, k):
+    """1 / (1 - beta^k) for the descriptor's binary32 betas, exactly rounded to binary32 (FP64 on
+    the host; beta^k through exact rationals where FP64 could lose the last bit)."""
+    from fractions import Fraction
+    out = []
+    for b in (b1, b2):
+        bb = Fraction(float(np.float32(b)))
+        pk = bb ** k if k <= 4096 else Fraction(float(np.float64(np.float32(b))) ** k)
+        out.append(np.float32(float(1 / (1 - pk))))
+    return np.array(out, dtype=np.float32)
+
+
 def test_device_step_counter_and_bias_corrections():
-    """sxe_adam_advance: t counts up on the device and the corrections are 1 / (1 - beta^t) in FP64
-    rounded once to binary32 (at most one binary32 ulp from the exactly rounded value)."""
+    """sxe_adam_advance: t counts up on the device and the corrections are 1 / (1 - beta^t), formed
+    in double-word binary32 arithmetic (no FP64 on the device) and rounded once: at most one
+    binary32 ulp from the exactly rounded value, for every t up to 4097 checked, and for t far out
+    (10^6, 2^31) where beta^t has underflowed."""
     from paper_2311_15439_gb300.api import Adam
     a = Adam(1e-2, 0.9, 0.99, 1e-15, skip_zero_grad=True)
     t = torch.zeros((1,), dtype=torch.int64, device="cuda")
     c = torch.zeros((2,), dtype=torch.float32, device="cuda")
-    b1, b2 = np.float64(np.float32(0.9)), np.float64(np.float32(0.99))    # the descriptor's binary32 betas
-    checks = {1, 2, 3, 7, 64, 1000, 4097}
+    checks = {1, 2, 3, 4, 5, 7, 10, 16, 33, 64, 100, 229, 459, 1000, 2048, 4097}
     for k in range(1, 4098):
         a.advance(t, c)
         if k in checks:
             got = c.cpu().numpy()
-            want32 = np.array([1.0 / (1.0 - b1 ** k), 1.0 / (1.0 - b2 ** k)]).astype(np.float32)
+            want32 = _bias_corrections(0.9, 0.99, k)
             assert int(t.item()) == k
+            assert np.all(np.abs(got.astype(np.float64) - want32) <= np.spacing(want32)), (k, got, want32)
+    for k in (10 ** 6, 1 << 31):
+        t.fill_(k - 1)
+        a.advance(t, c)
+        assert int(t.item()) == k
+        assert np.array_equal(c.cpu().numpy(), np.ones(2, dtype=np.float32)), (k, c.cpu().numpy())
+    # other betas, including the 0.999 of Kingma & Ba (amplification 1 / (1 - beta) = 1000)
+    a2 = Adam(1e-3, 0.5, 0.999, 1e-8)
+    t.zero_()
+    for k in range(1, 3001):
+        a2.advance(t, c)
+        if k in checks or k % 500 == 0:
+            got = c.cpu().numpy()
+            want32 = _bias_corrections(0.5, 0.999, k)
             assert np.all(np.abs(got.astype(np.float64) - want32) <= np.spacing(want32)), (k, got, want32)
 
 
