@@ -13,6 +13,37 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300, sm_103a)")
 
 
+#: worst achieved error per result over the session: name -> (error, tolerance, what it is relative to)
+_ERRORS = {}
+
+
+def record_error(result, err, tol, relative_to):
+    """Keep the worst error of ``result`` against the FP64 oracle seen in this session; the
+    summary at the end lists every result with its tolerance (and a JSON copy goes to the file
+    named by the environment variable SXE_PARITY_REPORT, if set)."""
+    err = float(err)
+    prev = _ERRORS.get(result)
+    if prev is None or err > prev[0]:
+        _ERRORS[result] = (err, float(tol), relative_to)
+    return err
+
+
+def pytest_terminal_summary(terminalreporter):
+    if not _ERRORS:
+        return
+    import json
+    tr = terminalreporter
+    tr.write_sep("-", "worst achieved error against the FP64 oracle, per result")
+    for name in sorted(_ERRORS):
+        err, tol, rel = _ERRORS[name]
+        tr.write_line("%-66s %10.3g  tol %8.3g  (%.3f of tol)  vs %s" % (name, err, tol, err / tol if tol else 0.0, rel))
+    path = os.environ.get("SXE_PARITY_REPORT")
+    if path:
+        with open(path, "w") as fh:
+            json.dump({k: {"error": v[0], "tolerance": v[1], "relative_to": v[2]} for k, v in sorted(_ERRORS.items())},
+                      fh, indent=1)
+
+
 def read_golden(name):
     rows = []
     with open(os.path.join(GOLDEN, name)) as fh:

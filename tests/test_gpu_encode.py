@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import torch
 
-from conftest import ENC_ATOL, ENC_TOL, rel_err, worst_ratio
+from conftest import ENC_ATOL, ENC_TOL, record_error, rel_err, worst_ratio
 from oracle import encoding as O
 from oracle import render as OR
 from oracle import lattice
@@ -84,7 +84,10 @@ def test_forward_matches_oracle(cuda_lib, case, kind):
     else:
         ref = O.grid_encode(x, vals, base_res=base, growth=growth)
         den = O.grid_encode(x, np.abs(vals), base_res=base, growth=growth)   # weights are >= 0
-    assert worst_ratio(out, ref, den, ENC_TOL[case[7]], ENC_ATOL[case[7]]) <= 1.0
+    tol = ENC_TOL[case[7]]
+    r = worst_ratio(out, ref, den, tol, ENC_ATOL[case[7]])
+    record_error("encode_fwd %s output, %s tables (%s)" % (case[7], case[6], kind), r * tol, tol, "sum_k |w_k H_k| (+ fp16 subnormal spacing)")
+    assert r <= 1.0
 
 
 @pytest.mark.parametrize("kind", ["simplex", "grid"])
@@ -105,28 +108,34 @@ def test_backward_matches_oracle(cuda_lib, case, kind):
         ref = O.grid_encode_bwd(x, dout, **kw)
         den = O.grid_encode_bwd(x, np.abs(dout), **kw)
     for l in range(L):
-        assert rel_err(g[l], ref[l], den[l]) <= 1e-5, "level %d" % l
+        e = record_error("encode_bwd table gradient (%s)" % kind, rel_err(g[l], ref[l], den[l]), 1e-5, "sum_k |w_k dout| per entry")
+        assert e <= 1e-5, "level %d" % l
         assert np.all(g[l][den[l] == 0] == 0)
 
 
 def test_full_size_image_workload(cuda_lib):
     """2^18 points, L = 16, T = 2^22 fp16 tables, the launch the benchmark times: every output
-    against the oracle, and the gradients of three levels (coarse, middle, finest)."""
+    and every table-gradient entry of all 16 levels against the oracle."""
     case = (2, 16, 2, 22, 16.0, 2.0, "f16", "f16", 1 << 18)
     enc, vals, t, x = _setup(cuda_lib, case, "simplex", seed=11)
     x = x[: 1 << 18]
     xd = torch.from_numpy(x).cuda()
     out = enc.encode_fwd(xd, t).float().cpu().numpy()
     ref, den = O.simplex_encode(x, vals, base_res=16.0, growth=2.0, with_denominator=True)
-    assert worst_ratio(out, ref, den, ENC_TOL["f16"], ENC_ATOL["f16"]) <= 1.0
+    r = worst_ratio(out, ref, den, ENC_TOL["f16"], ENC_ATOL["f16"])
+    record_error("encode_fwd f16 output, image workload at full size", r * ENC_TOL["f16"], ENC_TOL["f16"], "sum_k |w_k H_k| (+ fp16 subnormal spacing)")
+    assert r <= 1.0
     dout = synth.normal_grads(len(x), 32, 12)
     grad = torch.zeros((16, 1 << 22, 2), dtype=torch.float32, device="cuda")
     enc.encode_bwd(xd, torch.from_numpy(dout).cuda(), grad)
-    levels = [0, 7, 15]
-    ref, den = O.simplex_encode_bwd(x, dout, n_levels=16, log2_T=22, n_features=2, base_res=16.0, growth=2.0,
-                                    levels=levels, with_denominator=True)
-    for l in levels:
-        assert rel_err(grad[l].cpu().numpy(), ref[l], den[l]) <= 1e-5
+    for l in range(16):                                  # every level, one at a time (1 GiB of FP64 each)
+        ref, den = O.simplex_encode_bwd(x, dout, n_levels=16, log2_T=22, n_features=2, base_res=16.0, growth=2.0,
+                                        levels=[l], with_denominator=True)
+        g = grad[l].cpu().numpy()
+        e = record_error("encode_bwd table gradient, image workload at full size", rel_err(g, ref[l], den[l]), 1e-5,
+                         "sum_k |w_k dout| per entry")
+        assert e <= 1e-5, "level %d" % l
+        assert np.all(g[den[l] == 0] == 0), "level %d" % l
 
 
 def test_strided_gradient_and_touched_bitmap(cuda_lib):
@@ -200,7 +209,7 @@ def test_plain_path_matches_oracle(cuda_lib, d):
     xd = torch.from_numpy(x).cuda()
     out = enc.encode_plain_fwd(xd, torch.from_numpy(vals).cuda()).cpu().numpy()
     ref, den = O.simplex_encode(x, vals, base_res=16.0, growth=1.5, with_denominator=True)
-    assert rel_err(out, ref, den) <= 1e-5
+    assert record_error("encode_plain_fwd f32 output", rel_err(out, ref, den), 1e-5, "sum_k |w_k H_k| (+ fp16 subnormal spacing)") <= 1e-5
     dout = synth.normal_grads(len(x), L * 2, 40 + d)
     grad = torch.zeros((L, 1 << log2_T, 2), device="cuda")
     enc.encode_plain_bwd(xd, torch.from_numpy(dout).cuda(), grad)
@@ -208,7 +217,7 @@ def test_plain_path_matches_oracle(cuda_lib, d):
                                       growth=1.5, with_denominator=True)
     g = grad.cpu().numpy()
     for l in range(L):
-        assert rel_err(g[l], gref[l], gden[l]) <= 1e-5
+        assert record_error("encode_plain_bwd table gradient", rel_err(g[l], gref[l], gden[l]), 1e-5, "sum_k |w_k dout| per entry") <= 1e-5
 
 
 def test_full_size_sdf_workload(cuda_lib):
@@ -223,7 +232,9 @@ def test_full_size_sdf_workload(cuda_lib):
     xd = torch.from_numpy(x).cuda()
     out = enc.encode_fwd(xd, t).float().cpu().numpy()
     ref, den = O.simplex_encode(x, vals, base_res=16.0, growth=1.38, with_denominator=True)
-    assert worst_ratio(out, ref, den, ENC_TOL["bf16"], ENC_ATOL["bf16"]) <= 1.0
+    r = worst_ratio(out, ref, den, ENC_TOL["bf16"], ENC_ATOL["bf16"])
+    record_error("encode_fwd bf16 output, SDF workload at full size", r * ENC_TOL["bf16"], ENC_TOL["bf16"], "sum_k |w_k H_k| (+ fp16 subnormal spacing)")
+    assert r <= 1.0
     dout = synth.normal_grads(len(x), 32, 72)
     grad = torch.zeros((16, 1 << 19, 2), dtype=torch.float32, device="cuda")
     enc.encode_bwd(xd, torch.from_numpy(dout).cuda(), grad)
@@ -231,7 +242,8 @@ def test_full_size_sdf_workload(cuda_lib):
     gref, gden = O.simplex_encode_bwd(x, dout, n_levels=16, log2_T=19, n_features=2, base_res=16.0, growth=1.38,
                                       levels=levels, with_denominator=True)
     for l in levels:
-        assert rel_err(grad[l].cpu().numpy(), gref[l], gden[l]) <= 1e-5
+        e = rel_err(grad[l].cpu().numpy(), gref[l], gden[l])
+        assert record_error("encode_bwd table gradient, SDF workload at full size", e, 1e-5, "sum_k |w_k dout| per entry") <= 1e-5
 
 
 DX_CASES = [c for c in CASES if c[8] <= 1 << 14]
@@ -244,13 +256,15 @@ def test_input_gradient_matches_oracle(cuda_lib, case, kind):
     1e-5 of the sum of the magnitudes of the terms (binary32 products and sums)."""
     enc, vals, t, x = _setup(cuda_lib, case, kind, seed=20)
     d, L, F = case[:3]
-    if kind == "grid" and d > 4:
-        pytest.skip("2^5 corners: covered at smaller sizes")
+    if kind == "grid" and d > 4:                # 2^5 corners: 400 uniform points and every edge point
+        x = np.concatenate([x[:400], x[case[8]:]])
     base, growth = case[4], case[5]
     dout = synth.normal_grads(len(x), L * F, 21)
     dx = enc.encode_bwd_input(torch.from_numpy(x).cuda(), t, torch.from_numpy(dout).cuda()).cpu().numpy()
     f = O.simplex_encode_dx if kind == "simplex" else O.grid_encode_dx
     ref, den = f(x, vals, dout, base_res=base, growth=growth, with_denominator=True)
+    e = float(np.max(np.abs(dx - ref) / (den + 1e-30)))
+    record_error("encode_bwd_input dL/dx (%s)" % kind, e, 1e-5, "sum of |terms| of each dL/dx_i")
     assert np.all(np.abs(dx - ref) <= 1e-5 * den + 1e-30)
 
 
@@ -488,3 +502,98 @@ def test_coarse_levels_summed_per_block(cuda_lib, kind, d, index_mode):
         want[l * T + np.unique(sl)] = True
     bits = np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little").astype(bool)[: L * T]
     assert np.array_equal(bits, want)
+
+
+# Sec. 5.2's equal-memory setting: every simplex level scaled by (n+1)^((n-1)/(2n)), so that the
+# touched simplex lattice is as large as the grid's at the same N_l (the comparison setting).
+EQ_CASES = [
+    (2, 16, 2, 19, 16.0, 1.38, "f16", "f16", 4000),
+    (3, 16, 2, 19, 16.0, 1.38, "bf16", "bf16", 4000),
+    (4, 16, 2, 19, 16.0, 1.38, "f16", "f32", 3000),
+    (5, 16, 2, 19, 16.0, 1.38, "f16", "f16", 3000),
+    (2, 16, 2, 22, 16.0, 2.0, "f16", "f16", 1 << 14),      # image-style tables, finest N = 524288
+    (3, 6, 4, 12, 8.0, 2.0, "f32", "f32", 2001),
+]
+
+
+def _eq_setup(case, seed=40):
+    from paper_2311_15439_gb300.api import Encoder
+    d, L, F, log2_T, base, growth, tdt, odt, P = case
+    enc = Encoder(d, L, F, log2_T, base, growth, res_mode="equal_mem", table_dtype=tdt, out_dtype=odt)
+    vals, store = synth.uniform_tables(L, 1 << log2_T, F, seed, dtype=tdt, scale=1e-4)
+    t = torch.from_numpy(store.astype(np.int16) if tdt == "bf16" else store).cuda()
+    if tdt == "bf16":
+        t = t.view(torch.bfloat16)
+    return enc, vals, t, _points(d, P, seed + 1)
+
+
+@pytest.mark.parametrize("case", EQ_CASES, ids=_ids)
+def test_equal_mem_vertices_forward_backward(cuda_lib, case):
+    """res_mode = equal_mem: the binary32 level multipliers equal the oracle's, slots are bit-exact,
+    weights within 2^-23, encodings and table gradients within the stated tolerances."""
+    d, L, F, log2_T, base, growth, tdt, odt, P = case
+    enc, vals, t, x = _eq_setup(case)
+    eq = lattice.RES_EQUAL_MEM
+    scales = lattice.simplex_level_scales_fp32(d, L, base, growth, eq)
+    assert np.array_equal(enc.level_params()[0], scales)
+    assert np.all(scales > lattice.simplex_level_scales_fp32(d, L, base, growth))
+    xd = torch.from_numpy(x).cuda()
+    slots, w = enc.encode_vertices(xd)
+    slots, w = slots.cpu().numpy(), w.cpu().numpy()
+    for l in range(L):
+        s_ref, w_ref, _ = O.simplex_level_vertices(x, scales[l], log2_T)
+        assert np.array_equal(slots[:, l, :].astype(np.int64), s_ref), "level %d" % l
+        assert np.max(np.abs(w[:, l, :] - w_ref)) <= 2.0 ** -23
+    out = enc.encode_fwd(xd, t).float().cpu().numpy()
+    ref, den = O.simplex_encode(x, vals, base_res=base, growth=growth, res_mode=eq, with_denominator=True)
+    r = worst_ratio(out, ref, den, ENC_TOL[odt], ENC_ATOL[odt])
+    record_error("encode_fwd %s output, %s tables (simplex, equal_mem)" % (odt, tdt), r * ENC_TOL[odt], ENC_TOL[odt],
+                 "sum_k |w_k H_k| (+ fp16 subnormal spacing)")
+    assert r <= 1.0
+    dout = synth.normal_grads(len(x), L * F, 42)
+    grad = torch.zeros((L, 1 << log2_T, F), dtype=torch.float32, device="cuda")
+    enc.encode_bwd(xd, torch.from_numpy(dout).cuda(), grad)
+    gref, gden = O.simplex_encode_bwd(x, dout, n_levels=L, log2_T=log2_T, n_features=F, base_res=base,
+                                      growth=growth, res_mode=eq, with_denominator=True)
+    g = grad.cpu().numpy()
+    for l in range(L):
+        e = record_error("encode_bwd table gradient (simplex, equal_mem)", rel_err(g[l], gref[l], gden[l]), 1e-5,
+                         "sum_k |w_k dout| per entry")
+        assert e <= 1e-5, "level %d" % l
+        assert np.all(g[l][gden[l] == 0] == 0)
+    if log2_T <= 19:
+        dx = enc.encode_bwd_input(xd, t, torch.from_numpy(dout).cuda()).cpu().numpy()
+        dref, dden = O.simplex_encode_dx(x, vals, dout, base_res=base, growth=growth, res_mode=eq,
+                                         with_denominator=True)
+        record_error("encode_bwd_input dL/dx (simplex, equal_mem)", np.max(np.abs(dx - dref) / (dden + 1e-30)), 1e-5,
+                     "sum of |terms| of each dL/dx_i")
+        assert np.all(np.abs(dx - dref) <= 1e-5 * dden + 1e-30)
+
+
+def test_equal_mem_full_size_sdf_workload(cuda_lib):
+    """The SDF-style configuration at full size (d = 3, L = 16, T = 2^19 bf16, 2^20 points, half near
+    a union of spheres and tori) in the equal-memory setting: every output, and every table-gradient
+    entry of all 16 levels, against the oracle."""
+    from paper_2311_15439_gb300.api import Encoder
+    eq = lattice.RES_EQUAL_MEM
+    enc = Encoder(3, 16, 2, 19, 16.0, 1.38, res_mode="equal_mem", table_dtype="bf16", out_dtype="bf16")
+    vals, bits = synth.uniform_tables(16, 1 << 19, 2, 73, dtype="bf16", scale=1e-4)
+    t = torch.from_numpy(bits.astype(np.int16)).cuda().view(torch.bfloat16)
+    x = synth.sdf_points(1 << 20, 74)
+    xd = torch.from_numpy(x).cuda()
+    out = enc.encode_fwd(xd, t).float().cpu().numpy()
+    ref, den = O.simplex_encode(x, vals, base_res=16.0, growth=1.38, res_mode=eq, with_denominator=True)
+    r = worst_ratio(out, ref, den, ENC_TOL["bf16"], ENC_ATOL["bf16"])
+    record_error("encode_fwd bf16 output, SDF workload at full size (equal_mem)", r * ENC_TOL["bf16"],
+                 ENC_TOL["bf16"], "sum_k |w_k H_k| (+ fp16 subnormal spacing)")
+    assert r <= 1.0
+    dout = synth.normal_grads(len(x), 32, 75)
+    grad = torch.zeros((16, 1 << 19, 2), dtype=torch.float32, device="cuda")
+    enc.encode_bwd(xd, torch.from_numpy(dout).cuda(), grad)
+    g = grad.cpu().numpy()
+    for l in range(16):
+        gref, gden = O.simplex_encode_bwd(x, dout, n_levels=16, log2_T=19, n_features=2, base_res=16.0,
+                                          growth=1.38, res_mode=eq, levels=[l], with_denominator=True)
+        e = rel_err(g[l], gref[l], gden[l])
+        record_error("encode_bwd table gradient, SDF workload at full size (equal_mem)", e, 1e-5, "sum_k |w_k dout| per entry")
+        assert e <= 1e-5, "level %d" % l

@@ -3,6 +3,8 @@ import numpy as np
 import pytest
 import torch
 
+from conftest import record_error
+
 from oracle import render as OR
 from paper_2311_15439_gb300 import synth
 
@@ -68,6 +70,8 @@ def test_composite_matches_oracle(cuda_lib, R, S):
     werr = W * ((depth + 2) * tau + 12) * U32 + 1e-30
     assert np.all(np.abs(w.cpu().numpy().reshape(R, S) - W) <= werr)
     cerr = (werr[:, :, None] * rgb).sum(axis=1) + W.sum(axis=1, keepdims=True) * (depth + 8) * U32 + 1e-7
+    record_error("vr_composite colour (Eq. 5 quadrature)", np.max(np.abs(color.cpu().numpy() - C) / cerr), 1.0,
+                 "binary32 bound of the transmittance scan")
     assert np.all(np.abs(color.cpu().numpy() - C) <= cerr)
     tot = tau[:, -1] + sigma[:, -1].astype(np.float64) * delta
     assert np.all(np.abs(trans.cpu().numpy() - T) <= T * ((depth + 2) * tot + 4) * U32 + 1e-30)
@@ -189,11 +193,15 @@ def test_composite_bwd_matches_oracle(cuda_lib, R, S):
     sum_err = 4 * (depth + 12) * (C[:, None, :] + P)
     bound = (delta[:, None] * (np.abs(dC)[:, None, :] * (t_err + sum_err)).sum(axis=2)) * U32 + 1e-30
     got = dsig.cpu().numpy().reshape(R, S)
+    record_error("vr_composite_bwd dL/dsigma", np.max(np.abs(got - ds_ref) / bound), 1.0,
+                 "binary32 bound of the two scans")
     bad = np.argwhere(np.abs(got - ds_ref) > bound)
     assert len(bad) == 0, [(tuple(i), float(got[tuple(i)]), float(ds_ref[tuple(i)]), float(bound[tuple(i)]),
                             float(sigma[tuple(i)]), float(delta[i[0]])) for i in bad[:5]]
     lbound = np.abs(dl_ref) * ((depth + 2) * np.repeat(tau.reshape(-1), 3).reshape(-1, 3) + 16) * U32 + 1e-30
     gl = dlog.cpu().numpy()
+    record_error("vr_composite_bwd dL/dlogits", np.max(np.abs(gl - dl_ref) / lbound), 1.0,
+                 "binary32 bound of the scan and sigmoid")
     badl = np.argwhere(np.abs(gl - dl_ref) > lbound)
     assert len(badl) == 0, [(tuple(i), float(gl[tuple(i)]), float(dl_ref[tuple(i)]), float(lbound[tuple(i)]))
                             for i in badl[:5]]

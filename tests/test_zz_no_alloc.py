@@ -51,10 +51,11 @@ def test_static_scratch_matches_workspace_entry(cuda_lib):
 @pytest.mark.parametrize("kernel", ["mma_sync", "tcgen05"])
 def test_static_scratch_cuts_the_grid(cuda_lib, kernel):
     """A network large enough that the fixed array holds fewer per-CTA partial rows than the
-    persistent grid the workspace entry point launches (64 -> 64 -> 64 -> 64 -> 16: 13312 weights,
-    room for 157 rows): the static entry point then runs on the smaller grid, and its gradients
-    still match the workspace entry point's (same products; only the summation order of the
-    partials differs), on two calls in a row, under both network kernels."""
+    persistent grid the workspace entry point launches (the first of the candidates below for which
+    that holds on this GPU; 2^21 / (weights + 1) rows fit): the static entry point then runs on the
+    smaller grid, and its gradients still match the workspace entry point's (same products; only
+    the summation order of the partials differs), on two calls in a row, under both network
+    kernels."""
     import ctypes
     from paper_2311_15439_gb300 import _lib as L
     from paper_2311_15439_gb300.api import Mlp
@@ -63,12 +64,17 @@ def test_static_scratch_cuts_the_grid(cuda_lib, kernel):
     prev = L.lib().sxe_mlp_get_kernel()
     assert L.lib().sxe_mlp_set_kernel(code) == 0
     try:
-        P, n_in, n_out = 1 << 18, 64, 16
-        mlp = Mlp(n_in, n_out, n_hidden=3, dtype="f16")
-        assert mlp.n_params == 13312
-        capacity = (1 << 21) // (mlp.n_params + 1)
-        grid = mlp.workspace_bytes(P) // (4 * (mlp.n_params + 1))
-        assert capacity == 157 and capacity < grid, (capacity, grid)
+        P = 1 << 18
+        chosen = None
+        for n_in, nh, n_out in ((32, 3, 16), (16, 3, 16), (32, 2, 16), (64, 2, 16), (64, 3, 16)):
+            mlp = Mlp(n_in, n_out, n_hidden=nh, dtype="f16")
+            capacity = (1 << 21) // (mlp.n_params + 1)
+            grid = mlp.workspace_bytes(P) // (4 * (mlp.n_params + 1))
+            if capacity < grid:
+                chosen = (n_in, nh, n_out)
+                break
+        assert chosen is not None, "no candidate network has a grid above the array's capacity"
+        n_in, nh, n_out = chosen
         W_t, W = _round(mlp.init_weights(11), "f16")
         x_t, x = _round(synth.rng(12).uniform(-1, 1, size=(P, n_in)), "f16")
         Wd, xd = W_t.cuda(), x_t.cuda()
@@ -79,7 +85,7 @@ def test_static_scratch_cuts_the_grid(cuda_lib, kernel):
         ref_sq = torch.zeros((1,), device="cuda")
         mlp.mlp_train_l2(Wd, xd, tgt, ref_dW, ref_sq, din=ref_din, loss_scale=ls)
         u = 2.0 ** -11
-        tol = (2 * 3 + 2) * u
+        tol = (2 * nh + 2) * u
         Ws = mlp.split(W)
         yden = _dens(Ws, x, np.zeros((P, n_out)))[0]
         _, dW_den, _ = _dens(Ws, x, 2.0 * (yden + 1.0) / (P * n_out))
@@ -91,7 +97,8 @@ def test_static_scratch_cuts_the_grid(cuda_lib, kernel):
             torch.cuda.synchronize()
             got, ref = mlp.split(dW.cpu().numpy()), mlp.split(ref_dW.cpu().numpy())
             for i in range(len(Ws)):
-                assert within(got[i], ref[i], dW_den[i], tol) <= 1.0, "%s call %d layer %d" % (kernel, call, i)
+                assert within(got[i], ref[i], dW_den[i], tol) <= 1.0, "%s %s call %d layer %d" % (kernel, chosen,
+                                                                                                 call, i)
             assert torch.equal(din, ref_din)
             assert abs(sq.item() - ref_sq.item()) <= 1e-5 * ref_sq.item()
         flag = ctypes.c_int32(0)
