@@ -482,3 +482,52 @@ def test_table_layouts_train_alike():
     _close_up_to_atomics(a.table_params(), b.table_params(), steps=4)
     _close_up_to_atomics(a.tables.float(), b.tables.float(), steps=4)
     assert int(a.touched.abs().sum().item()) == 0 and float(b.tab.grad.abs().max()) == 0.0
+
+
+def test_data_parallel_shards_average_to_the_union_step():
+    """The data-parallel step on the library's kernels, two ranks emulated one after the other on
+    one GPU (no collective: their gradient buffers are averaged in place of the all-reduce): the
+    average equals the gradients and loss of one step on the union of the two batches, and Adam on
+    it moves the parameters like the union step."""
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.data_parallel import DataParallelTrainer, shard
+    from paper_2311_15439_gb300.trainer import Trainer
+    cfg = dict(d=3, n_levels=8, n_features=2, log2_T=15, base_res=16.0, growth=1.5)
+    P = 1 << 14
+    dp = DataParallelTrainer(Encoder(**cfg, table_dtype="f16"), Mlp(16, 1, n_hidden=1, dtype="f16"), P, seed=3)
+    un = Trainer(Encoder(**cfg, table_dtype="f16"), Mlp(16, 1, n_hidden=1, dtype="f16"), 2 * P, seed=3,
+                 table_layout="dense")
+    scene = synth.SphereTorusScene(5)
+    x = scene.sample(2 * P, 77)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(scene.sdf(x)).cuda()
+    un.t += 1
+    un.adam_tables.advance(un.t_dev, un.corrections)
+    un.enc.encode_fwd(xd, un.tables, un.enc_out)
+    un.mlp.mlp_train_l2(un.W_lowp, un.enc_out, td, un.dW, un.sq_sum, din=un.d_enc, loss_scale=un.loss_scale,
+                        workspace=un.ws)
+    un.tab.backward(xd, un.d_enc)
+    g_un, dW_un, loss_un = un.table_grads().cpu().numpy().copy(), un.dW.cpu().numpy().copy(), un.loss()
+    dp.tr.t += 1
+    dp.tr.adam_tables.advance(dp.tr.t_dev, dp.tr.corrections)
+    flats = []
+    for r in range(2):
+        s = shard(2 * P, r, 2)
+        dp.flat.zero_()
+        dp.local_grads(xd[s].contiguous(), td[s].contiguous())
+        flats.append(dp.flat.clone())
+    dp.flat.copy_((flats[0] + flats[1]) * 0.5)          # what the all-reduce (mean over 2 ranks) gives
+    g_dp, dW_dp = dp.tr.table_grads().cpu().numpy(), dp.tr.dW.cpu().numpy()
+    assert abs(dp.loss() - loss_un) <= 1e-5 * loss_un
+    gmax = np.abs(g_un).max()
+    assert gmax > 0 and np.abs(g_dp - g_un).max() <= 1e-5 * gmax
+    assert np.array_equal(g_dp == 0, g_un == 0)
+    assert np.abs(dW_dp - dW_un).max() <= 1e-5 * np.abs(dW_un).max()
+    dp.apply()
+    un.tab.adam(un.adam_tables, un.corrections)
+    un.adam_mlp.step_dev(un.corrections, un.W, un.mW, un.vW, un.dW, lowp=un.W_lowp)
+    clear = np.abs(g_un) > 1e-3 * gmax                 # entries whose step direction is unambiguous
+    assert clear.sum() > 1000
+    p_dp, p_un = dp.tr.table_params().cpu().numpy(), un.table_params().cpu().numpy()
+    np.testing.assert_allclose(p_dp[clear], p_un[clear], rtol=0, atol=1e-6)
+    assert np.array_equal(p_dp[g_un == 0], p_un[g_un == 0])
+    assert torch.all(dp.flat[:-1] == 0)                 # Adam left the gradient parts zero
