@@ -33,7 +33,10 @@ CFG = dict(d=2, n_levels=16, n_features=2, log2_T=22, base_res=16.0, growth=2.0)
 BATCH = 1 << 18
 N_OUT = 3
 WORKLOAD = "image_fit_2d_L16_F2_T2^22_fp16_mlp64x2_P2^18"
-METRIC = "simplex encode fwd+bwd training-step throughput"
+# The headline metric as the benchmark plan names it; the value is points/s of one whole training
+# step of the image workload, which contains the encoding's forward and backward (see the line's
+# config.step), and the grid, plain binary32 and serving figures are the line's extra records.
+METRIC = "simplex encode fwd+bwd points/s vs 2^d grid & plain FP32 path; serve p50/p99 ms"
 N_POOL = 8   # distinct resident batches cycled through the timed steps
 
 # DRAM traffic of one step's launch of a stage (dram__bytes_read.sum + dram__bytes_write.sum of its
@@ -41,7 +44,7 @@ N_POOL = 8   # distinct resident batches cycled through the timed steps
 # on: the figure is reported only while those sources are unchanged.
 TRAFFIC = {
     "encode_bwd": (35.82e6 + 755.55e6, "6db9b692110c81022350715653cfadf71ada9d02",
-                   ("encode.cu", "encode_common.cuh", "sxe_internal.cuh")),
+                   ("encode.cu", "encode_common.cuh", "lattice.cuh")),
 }
 
 
@@ -236,7 +239,8 @@ def run_gpu(args):
 
     from paper_2311_15439_gb300 import _lib
     _lib.check(_lib.lib().sxe_mlp_set_kernel({"auto": _lib.SXE_MLP_KERNEL_AUTO, "mma_sync": _lib.SXE_MLP_KERNEL_MMA_SYNC,
-                                              "tcgen05": _lib.SXE_MLP_KERNEL_TCGEN05}[args.mlp_kernel]),
+                                              "tcgen05": _lib.SXE_MLP_KERNEL_TCGEN05,
+                                              "tcgen05_pipelined": _lib.SXE_MLP_KERNEL_TCGEN05_PIPELINED}[args.mlp_kernel]),
                "sxe_mlp_set_kernel")
     enc = Encoder(**CFG, kind=args.kind, table_dtype="f16")
     mlp = Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16")
@@ -315,9 +319,11 @@ def run_gpu(args):
     peaks_ra = random_access_peaks(dev, tr.state.numel() * 4, tr.tables) if rank == 0 else None
     volume = volume_sweep(dev) if (rank == 0 and not args.no_volume) else None
     sdf = sdf_train(dev) if (rank == 0 and not args.no_sweep) else None
-    grid_img = image_grid_step(dev, xd, td, ms / args.steps) if (rank == 0 and not args.no_sweep and
-                                                                  args.kind == "simplex") else None
+    grid_img = image_step_variants(dev, xd, td, ms / args.steps) if (rank == 0 and not args.no_sweep and
+                                                                      args.kind == "simplex") else None
     per_cfg = per_config_encode(dev) if (rank == 0 and not args.no_sweep) else None
+    quality = (fit_quality(dev, args.quality_steps, max(1, args.quality_steps * 2 // 5))
+               if (rank == 0 and args.quality_steps > 0) else None)
 
     if rank == 0:
         value = job_throughput(BATCH, args.steps, world, ms)
@@ -335,8 +341,11 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "kind": args.kind, "mlp_kernel": {"auto": "auto (two-tile tcgen05 kernel for this network)", "mma_sync": "mma_sync",
-                                      "tcgen05": "tcgen05"}[args.mlp_kernel],
+            "config": {"workload": WORKLOAD, "kind": args.kind, "res_mode": "raw",
+                       "step": "encode forward, network forward + L2 loss + backward, encode backward into the "
+                               "table state, Adam on the touched table entries and on the network",
+                       "mlp_kernel": {"auto": "auto (two-tile tcgen05 kernel for this network)", "mma_sync": "mma_sync",
+                                      "tcgen05": "tcgen05", "tcgen05_pipelined": "tcgen05_pipelined"}[args.mlp_kernel],
                        "global_batch": BATCH * world,
                        "points_per_step_per_gpu": BATCH, "parallelism": "replicas (one per GPU)",
                        "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state records, no flush",
@@ -366,19 +375,20 @@ def run_gpu(args):
         line["gather_roofline"] = {
             "kernel": "encode_fwd", "gathers": gathers, "table_sectors_touched": n_sectors,
             "achieved_gathers_per_s": gathers / (per_kernel["encode_fwd"] / 1e3),
-            "achieved_over_random_gather_peak": gathers / (per_kernel["encode_fwd"] / 1e3) / peaks_ra["gather_4B_table"],
             "predicted_ms": pred_fwd * 1e3, "measured_ms": per_kernel["encode_fwd"],
             "frac": pred_fwd * 1e3 / per_kernel["encode_fwd"],
             "model": "first gather from a 32-byte table sector = one random 4-byte gather missing L2 "
                      "(probe over the fp16 tables); later ones hit (probe over 8 MiB)"}
         if comparators is not None:
             line["comparators"] = comparators
+        if quality is not None:
+            line["fit_quality"] = quality
         if volume is not None:
             line["volume"] = volume
         if sdf is not None:
             line["sdf_train"] = sdf
         if grid_img is not None:
-            line["image_grid_step"] = grid_img
+            line["image_step_variants"] = grid_img
         if per_cfg is not None:
             line["per_config_encode"] = per_cfg
         if serving is not None:
@@ -390,59 +400,80 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# The encoders every comparison runs on the same tables and points: the simplex encoding at the level
+# scale of Sec. 5.1 ("raw"), the simplex encoding in Sec. 5.2's equal-memory setting (each level's
+# resolution multiplied by (d+1)^((d-1)/(2d)), so that it touches as many lattice vertices as the
+# grid), and the 2^d multilinear grid (Algorithm 1).
+VARIANTS = (("simplex", "raw"), ("simplex", "equal_mem"), ("grid", "raw"))
+
+
+def vname(kind, mode):
+    return "grid" if kind == "grid" else "simplex_" + mode
+
+
+def _ratios(row, key):
+    """grid / simplex time ratios of one record, per res_mode of the simplex side."""
+    return {"grid_over_simplex_" + m: row[vname("simplex", m)][key] / row["grid"][key]
+            for m in ("raw", "equal_mem") if vname("simplex", m) in row}
+
+
 def encode_sweep(dev, reps=20):
-    """Encode forward+backward points/s of the simplex encoder vs the 2^d grid at d = 2..5
-    (L = 16, F = 2, T = 2^19, fp16 tables, 2^20 points), and the binary32 path."""
+    """Encode forward+backward points/s at d = 2..5 (L = 16, F = 2, T = 2^19, fp16 tables, 2^20
+    uniform points): the simplex encoder in both res_modes, the 2^d grid, and the binary32 paths
+    (the optimised kernels on fp32 tables, and the plain one-thread-per-point path)."""
     import torch
     from paper_2311_15439_gb300 import synth
     from paper_2311_15439_gb300.api import Encoder
     P = 1 << 20
     out = {}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        s.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize(dev)
+        return P * reps / (s.elapsed_time(e) / 1e3)
+
     for d in (2, 3, 4, 5):
         x = torch.from_numpy(synth.uniform_points(P, d, 50 + d)).to(dev)
         dout = torch.randn((P, 32), device=dev)
         row = {}
-        for kind, tdt in (("simplex", "f16"), ("grid", "f16"), ("simplex", "f32")):
-            enc = Encoder(d, 16, 2, 19, 16.0, 1.38, kind=kind, table_dtype=tdt, out_dtype=tdt)
+        for (kind, mode), tdt in [(v, "f16") for v in VARIANTS] + [(("simplex", "raw"), "f32")]:
+            enc = Encoder(d, 16, 2, 19, 16.0, 1.38, kind=kind, res_mode=mode, table_dtype=tdt, out_dtype=tdt)
             tab = torch.zeros(enc.table_shape(), dtype=torch.float16 if tdt == "f16" else torch.float32, device=dev)
             grad = torch.zeros(enc.table_shape(), dtype=torch.float32, device=dev)
             o = torch.empty((P, 32), dtype=tab.dtype, device=dev)
-            for _ in range(3):
+
+            def fb():
                 enc.encode_fwd(x, tab, o)
                 enc.encode_bwd(x, dout, grad)
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize(dev)
-            s.record()
-            for _ in range(reps):
-                enc.encode_fwd(x, tab, o)
-                enc.encode_bwd(x, dout, grad)
-            e.record()
-            torch.cuda.synchronize(dev)
-            row["%s_%s" % (kind, tdt)] = P * reps / (s.elapsed_time(e) / 1e3)
-            if kind == "simplex" and tdt == "f32":       # the plain binary32 path on the same tables
-                for _ in range(2):
+            name = vname(kind, mode) + ("" if tdt == "f16" else "_f32")
+            row[name] = {"fwd_bwd_points_per_s": timed(fb), "res_mode": mode, "table_dtype": tdt}
+            if tdt == "f32":                                # the plain binary32 path on the same tables
+                def pl():
                     enc.encode_plain_fwd(x, tab, o)
                     enc.encode_plain_bwd(x, dout, grad)
-                torch.cuda.synchronize(dev)
-                s.record()
-                for _ in range(reps):
-                    enc.encode_plain_fwd(x, tab, o)
-                    enc.encode_plain_bwd(x, dout, grad)
-                e.record()
-                torch.cuda.synchronize(dev)
-                row["simplex_plain_f32"] = P * reps / (s.elapsed_time(e) / 1e3)
+                row["simplex_plain_f32"] = {"fwd_bwd_points_per_s": timed(pl), "res_mode": mode,
+                                            "table_dtype": "f32"}
+        for m in ("raw", "equal_mem"):
+            row["grid_over_simplex_time_" + m] = (row[vname("simplex", m)]["fwd_bwd_points_per_s"]
+                                                  / row["grid"]["fwd_bwd_points_per_s"])
         out["d%d" % d] = row
-    return {"encode_fwd_bwd_points_per_s": out, "config": "L=16 F=2 T=2^19 base 16 growth 1.38, 2^20 points"}
+    return {"encode_fwd_bwd": out, "points": P,
+            "config": "L=16 F=2 T=2^19 base 16 growth 1.38, 2^20 uniform points, fp16 tables unless _f32"}
 
 
 def random_access_peaks(dev, state_bytes, table, n_ops=1 << 24, reps=5):
     """Peak rates of the scattered patterns that bound the table kernels, measured on this GPU
-    with the library's probe: float2 reductions into random 32-byte records of a footprint the
+    with the bench-only probe: float2 reductions into random 32-byte records of a footprint the
     size of the table state (L2 misses) and of 8 MiB (L2 hits), and 4-byte gathers from the
     fp16 tables.  Returns ops/s."""
     import torch
-    from paper_2311_15439_gb300 import _lib as L
-    lib = L.lib()
     n_rec = 1 << int(math.log2(state_bytes // 32))
     buf = torch.zeros((n_rec, 8), dtype=torch.float32, device=dev)
     sink = torch.zeros((1,), dtype=torch.float32, device=dev)
@@ -479,8 +510,8 @@ def volume_sweep(dev, n_rays=1 << 16, samples=(1, 4, 16, 64, 256, 1024), reps=3)
     from paper_2311_15439_gb300.render import Renderer
     rays = [torch.from_numpy(a).to(dev) for a in synth.camera_rays(n_rays, 60)]
     res = {}
-    for kind in ("simplex", "grid"):
-        enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, table_dtype="f16")
+    for kind, mode in VARIANTS:
+        enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, res_mode=mode, table_dtype="f16")
         vals, store = synth.uniform_tables(16, 1 << 19, 2, 61, dtype="f16", scale=1.0)
         tab = torch.from_numpy(store).to(dev)
         for S in samples:
@@ -500,13 +531,16 @@ def volume_sweep(dev, n_rays=1 << 16, samples=(1, 4, 16, 64, 256, 1024), reps=3)
                 enc.encode_fwd(x, tab, rr.enc_out[: n_rays * S])
             ev[3].record()
             torch.cuda.synchronize(dev)
-            res.setdefault(str(S), {})[kind] = {"render_ms": ev[0].elapsed_time(ev[1]) / reps,
-                                                "encode_ms": ev[2].elapsed_time(ev[3]) / reps}
+            res.setdefault(str(S), {})[vname(kind, mode)] = {"res_mode": mode,
+                                                             "render_ms": ev[0].elapsed_time(ev[1]) / reps,
+                                                             "encode_ms": ev[2].elapsed_time(ev[3]) / reps}
             del rr
             torch.cuda.empty_cache()
     for S, r in res.items():
-        r["grid_over_simplex_render"] = r["grid"]["render_ms"] / r["simplex"]["render_ms"]
-        r["grid_over_simplex_encode"] = r["grid"]["encode_ms"] / r["simplex"]["encode_ms"]
+        for m in ("raw", "equal_mem"):
+            v = vname("simplex", m)
+            r["grid_over_simplex_render_" + m] = r["grid"]["render_ms"] / r[v]["render_ms"]
+            r["grid_over_simplex_encode_" + m] = r["grid"]["encode_ms"] / r[v]["encode_ms"]
     return {"rays": n_rays, "config": "d=3 L=16 F=2 T=2^19 fp16 growth 1.38; nets 32-64-16 and 32-64-64-3",
             "by_samples_per_ray": res, "train": volume_train(dev, rays)}
 
@@ -523,8 +557,8 @@ def volume_train(dev, rays, S=64, steps=10, warmup=3):
     R = rays[0].shape[0]
     target = torch.from_numpy(synth.rng(64).random((R, 3)).astype(np.float32)).to(dev)
     out = {"rays": R, "samples_per_ray": S, "targets": "seeded uniform colours"}
-    for kind in ("simplex", "grid"):
-        enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, table_dtype="f16")
+    for kind, mode in VARIANTS:
+        enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, res_mode=mode, table_dtype="f16")
         vt = VolumeTrainer(enc, R, S, seed=63, device=dev)
         for _ in range(warmup):
             vt.step(*rays, target)
@@ -536,16 +570,17 @@ def volume_train(dev, rays, S=64, steps=10, warmup=3):
         b.record()
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / steps
-        out[kind] = {"ms_per_step": ms, "samples_per_s": R * S / (ms / 1e3), "table_layout": vt.tab.layout,
-                     "coarse_levels_on_second_stream": vt.tab.split_coarse}
+        out[vname(kind, mode)] = {"res_mode": mode, "ms_per_step": ms, "samples_per_s": R * S / (ms / 1e3),
+                                  "table_layout": vt.tab.layout, "coarse_levels_on_second_stream": vt.tab.split_coarse}
         del vt
         torch.cuda.empty_cache()
-    out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]
+    for m in ("raw", "equal_mem"):
+        out["grid_over_simplex_time_" + m] = out["grid"]["ms_per_step"] / out[vname("simplex", m)]["ms_per_step"]
     return out
 
 
 # Encode forward + backward of each configuration of the benchmark plan (the plain binary32 case,
-# the image, SDF-style and volumetric workloads; the serving load is `serve`), simplex and grid.
+# the image, SDF-style and volumetric workloads; the serving load is `serve`).
 PER_CONFIG = [
     ("plain_fp32_2d_L8_T2^14_P2^16", dict(d=2, n_levels=8, n_features=2, log2_T=14, base_res=16.0, growth=1.5),
      "f32", 1 << 16, "uniform"),
@@ -556,124 +591,459 @@ PER_CONFIG = [
                                                       growth=1.38), "f16", 1 << 26, "rays"),
 ]
 
+# ncu counters of the encoding kernels per configuration, encoder and stage, from one capture of
+# ``bench.py --profile-encode`` (the volumetric configuration at 2^16 rays x 64 samples there):
+# L2 sector throughput and DRAM throughput as a percentage of their peaks, L2 hit rate, DRAM bytes
+# per point.  Reported only while the kernel sources hash to ENCODE_NCU_SHA.
+ENCODE_NCU_SHA = '6db701334defea99e67fdb327a63812a5a022b63'
+ENCODE_NCU = {
+ "plain_fp32_2d_L8_T2^14_P2^16/simplex_raw/fwd": {
+  "l2_throughput_pct": 22.1,
+  "l2_sectors_pct": 9.5,
+  "dram_throughput_pct": 1.4,
+  "l2_hit_pct": 66.3,
+  "dram_bytes_per_point": 13.9,
+  "points_captured": 65536
+ },
+ "plain_fp32_2d_L8_T2^14_P2^16/simplex_raw/bwd": {
+  "l2_throughput_pct": 16.5,
+  "l2_sectors_pct": 7.9,
+  "dram_throughput_pct": 4.9,
+  "l2_hit_pct": 47.1,
+  "dram_bytes_per_point": 150.1,
+  "points_captured": 65536
+ },
+ "plain_fp32_2d_L8_T2^14_P2^16/simplex_equal_mem/fwd": {
+  "l2_throughput_pct": 24.8,
+  "l2_sectors_pct": 10.4,
+  "dram_throughput_pct": 1.5,
+  "l2_hit_pct": 69.1,
+  "dram_bytes_per_point": 15.3,
+  "points_captured": 65536
+ },
+ "plain_fp32_2d_L8_T2^14_P2^16/simplex_equal_mem/bwd": {
+  "l2_throughput_pct": 16.1,
+  "l2_sectors_pct": 7.7,
+  "dram_throughput_pct": 4.7,
+  "l2_hit_pct": 47.0,
+  "dram_bytes_per_point": 151.3,
+  "points_captured": 65536
+ },
+ "plain_fp32_2d_L8_T2^14_P2^16/grid/fwd": {
+  "l2_throughput_pct": 25.2,
+  "l2_sectors_pct": 10.4,
+  "dram_throughput_pct": 1.4,
+  "l2_hit_pct": 70.9,
+  "dram_bytes_per_point": 14.9,
+  "points_captured": 65536
+ },
+ "plain_fp32_2d_L8_T2^14_P2^16/grid/bwd": {
+  "l2_throughput_pct": 20.6,
+  "l2_sectors_pct": 9.2,
+  "dram_throughput_pct": 4.8,
+  "l2_hit_pct": 48.5,
+  "dram_bytes_per_point": 151.0,
+  "points_captured": 65536
+ },
+ "image_2d_L16_T2^22_fp16_P2^18/simplex_raw/fwd": {
+  "l2_throughput_pct": 50.0,
+  "l2_sectors_pct": 36.7,
+  "dram_throughput_pct": 70.2,
+  "l2_hit_pct": 28.6,
+  "dram_bytes_per_point": 1225.1,
+  "points_captured": 262144
+ },
+ "image_2d_L16_T2^22_fp16_P2^18/simplex_raw/bwd": {
+  "l2_throughput_pct": 23.5,
+  "l2_sectors_pct": 11.9,
+  "dram_throughput_pct": 33.1,
+  "l2_hit_pct": 29.6,
+  "dram_bytes_per_point": 1968.6,
+  "points_captured": 262144
+ },
+ "image_2d_L16_T2^22_fp16_P2^18/simplex_equal_mem/fwd": {
+  "l2_throughput_pct": 49.7,
+  "l2_sectors_pct": 36.8,
+  "dram_throughput_pct": 71.9,
+  "l2_hit_pct": 27.4,
+  "dram_bytes_per_point": 1318.6,
+  "points_captured": 262144
+ },
+ "image_2d_L16_T2^22_fp16_P2^18/simplex_equal_mem/bwd": {
+  "l2_throughput_pct": 24.5,
+  "l2_sectors_pct": 12.0,
+  "dram_throughput_pct": 34.4,
+  "l2_hit_pct": 28.9,
+  "dram_bytes_per_point": 2062.2,
+  "points_captured": 262144
+ },
+ "image_2d_L16_T2^22_fp16_P2^18/grid/fwd": {
+  "l2_throughput_pct": 51.5,
+  "l2_sectors_pct": 37.2,
+  "dram_throughput_pct": 71.2,
+  "l2_hit_pct": 29.0,
+  "dram_bytes_per_point": 1351.0,
+  "points_captured": 262144
+ },
+ "image_2d_L16_T2^22_fp16_P2^18/grid/bwd": {
+  "l2_throughput_pct": 26.4,
+  "l2_sectors_pct": 12.6,
+  "dram_throughput_pct": 32.0,
+  "l2_hit_pct": 33.7,
+  "dram_bytes_per_point": 2197.4,
+  "points_captured": 262144
+ },
+ "sdf_3d_L16_T2^19_bf16_P2^20/simplex_raw/fwd": {
+  "l2_throughput_pct": 70.7,
+  "l2_sectors_pct": 25.6,
+  "dram_throughput_pct": 4.0,
+  "l2_hit_pct": 90.0,
+  "dram_bytes_per_point": 54.6,
+  "points_captured": 1048576
+ },
+ "sdf_3d_L16_T2^19_bf16_P2^20/simplex_raw/bwd": {
+  "l2_throughput_pct": 70.6,
+  "l2_sectors_pct": 25.6,
+  "dram_throughput_pct": 11.5,
+  "l2_hit_pct": 55.1,
+  "dram_bytes_per_point": 329.7,
+  "points_captured": 1048576
+ },
+ "sdf_3d_L16_T2^19_bf16_P2^20/simplex_equal_mem/fwd": {
+  "l2_throughput_pct": 71.7,
+  "l2_sectors_pct": 25.9,
+  "dram_throughput_pct": 4.2,
+  "l2_hit_pct": 90.3,
+  "dram_bytes_per_point": 60.6,
+  "points_captured": 1048576
+ },
+ "sdf_3d_L16_T2^19_bf16_P2^20/simplex_equal_mem/bwd": {
+  "l2_throughput_pct": 76.8,
+  "l2_sectors_pct": 27.0,
+  "dram_throughput_pct": 7.2,
+  "l2_hit_pct": 61.4,
+  "dram_bytes_per_point": 193.9,
+  "points_captured": 1048576
+ },
+ "sdf_3d_L16_T2^19_bf16_P2^20/grid/fwd": {
+  "l2_throughput_pct": 75.7,
+  "l2_sectors_pct": 26.3,
+  "dram_throughput_pct": 2.3,
+  "l2_hit_pct": 94.7,
+  "dram_bytes_per_point": 59.4,
+  "points_captured": 1048576
+ },
+ "sdf_3d_L16_T2^19_bf16_P2^20/grid/bwd": {
+  "l2_throughput_pct": 74.1,
+  "l2_sectors_pct": 25.9,
+  "dram_throughput_pct": 6.3,
+  "l2_hit_pct": 59.4,
+  "dram_bytes_per_point": 335.5,
+  "points_captured": 1048576
+ },
+ "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_raw/fwd": {
+  "l2_throughput_pct": 68.1,
+  "l2_sectors_pct": 24.5,
+  "dram_throughput_pct": 6.3,
+  "l2_hit_pct": 89.9,
+  "dram_bytes_per_point": 70.7,
+  "points_captured": 4194304
+ },
+ "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_raw/bwd": {
+  "l2_throughput_pct": 63.9,
+  "l2_sectors_pct": 23.1,
+  "dram_throughput_pct": 9.4,
+  "l2_hit_pct": 54.4,
+  "dram_bytes_per_point": 293.0,
+  "points_captured": 4194304
+ },
+ "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_equal_mem/fwd": {
+  "l2_throughput_pct": 70.3,
+  "l2_sectors_pct": 25.2,
+  "dram_throughput_pct": 6.0,
+  "l2_hit_pct": 90.8,
+  "dram_bytes_per_point": 72.0,
+  "points_captured": 4194304
+ },
+ "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_equal_mem/bwd": {
+  "l2_throughput_pct": 77.8,
+  "l2_sectors_pct": 27.3,
+  "dram_throughput_pct": 5.9,
+  "l2_hit_pct": 62.1,
+  "dram_bytes_per_point": 153.7,
+  "points_captured": 4194304
+ },
+ "volume_3d_L16_T2^19_fp16_2^16rays_x1024/grid/fwd": {
+  "l2_throughput_pct": 76.4,
+  "l2_sectors_pct": 26.5,
+  "dram_throughput_pct": 3.4,
+  "l2_hit_pct": 95.0,
+  "dram_bytes_per_point": 71.7,
+  "points_captured": 4194304
+ },
+ "volume_3d_L16_T2^19_fp16_2^16rays_x1024/grid/bwd": {
+  "l2_throughput_pct": 76.0,
+  "l2_sectors_pct": 26.5,
+  "dram_throughput_pct": 5.9,
+  "l2_hit_pct": 58.1,
+  "dram_bytes_per_point": 297.8,
+  "points_captured": 4194304
+ }
+}
+
+
+def _sources_sha(files=("encode.cu", "encode_common.cuh", "lattice.cuh")):
+    import hashlib
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2311_15439_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _config_points(dev, ea, P, pts):
+    import torch
+    from paper_2311_15439_gb300 import synth
+    from paper_2311_15439_gb300.render import vr_samples
+    if pts == "uniform":
+        return torch.from_numpy(synth.uniform_points(P, ea["d"], 78)).to(dev)
+    if pts == "sdf":
+        return torch.from_numpy(synth.sdf_points(P, 79)).to(dev)
+    rays = [torch.from_numpy(a).to(dev) for a in synth.camera_rays(1 << 16, 60)]
+    return vr_samples(*rays, P >> 16)[0]
+
+
+def encode_bytes_per_point(ea, kind, tdt, odt):
+    """Algorithmic bytes per point of the forward (point, one table entry per vertex and level, the
+    encoding) and of the backward (point, dL/d(encoding) in binary32, one binary32 read-modify-write
+    of each vertex's F gradients)."""
+    d, L, F = ea["d"], ea["n_levels"], ea["n_features"]
+    V = d + 1 if kind == "simplex" else 1 << d
+    es = {"f32": 4, "f16": 2, "bf16": 2}
+    return (4 * d + L * V * F * es[tdt] + L * F * es[odt], 4 * d + 4 * L * F + 2 * L * V * F * 4)
+
 
 def per_config_encode(dev):
     """Per configuration: encode forward and backward points/s (each recorded once into a CUDA graph
-    and replayed), simplex and grid on the same tables, and the forward's achieved random gathers/s
-    over the probe's random 4-byte gather rate on that configuration's own tables (the fraction of
-    the gather roofline; above 1 where tables or reuse sit in L2)."""
+    and replayed), for the simplex encoder in both res_modes and the 2^d grid on the same tables
+    and points; each stage's algorithmic bytes over its time against the measured HBM copy peak,
+    and the ncu L2 / DRAM throughput of the same kernels where the committed capture matches."""
     import torch
-    from paper_2311_15439_gb300 import _lib as L
-    from paper_2311_15439_gb300 import synth
     from paper_2311_15439_gb300.api import Encoder
-    from paper_2311_15439_gb300.render import vr_samples
-    lib = L.lib()
-    st = torch.cuda.current_stream(dev).cuda_stream
-    sink = torch.zeros((1,), dtype=torch.float32, device=dev)
     dts = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+    hbm, _ = _peaks()
+    ncu_ok = ENCODE_NCU_SHA is not None and _sources_sha() == ENCODE_NCU_SHA
     gen = torch.Generator(device=dev).manual_seed(77)
     out = {}
+
+    def graph_time(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record()
+        for _ in range(reps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize(dev)
+        del g
+        return a.elapsed_time(b) / reps / 1e3
+
     for name, ea, tdt, P, pts in PER_CONFIG:
-        if pts == "uniform":
-            x = torch.from_numpy(synth.uniform_points(P, ea["d"], 78)).to(dev)
-        elif pts == "sdf":
-            x = torch.from_numpy(synth.sdf_points(P, 79)).to(dev)
-        else:
-            rays = [torch.from_numpy(a).to(dev) for a in synth.camera_rays(1 << 16, 60)]
-            x = vr_samples(*rays, P >> 16)[0]
+        x = _config_points(dev, ea, P, pts)
         n_out = ea["n_levels"] * ea["n_features"]
         dout = torch.randn((P, n_out), device=dev, generator=gen)
         reps = 1000 if P <= (1 << 16) else (3 if P >= (1 << 26) else 50)
         row = {"points": P, "table_dtype": tdt, "replays": reps}
-        for kind in ("simplex", "grid"):
-            enc = Encoder(**ea, kind=kind, table_dtype=tdt, out_dtype=tdt)
-            tab = (torch.rand(enc.table_shape(), device=dev, generator=gen) * 2 - 1).to(dts[tdt])
+        tab = None
+        for kind, mode in VARIANTS:
+            enc = Encoder(**ea, kind=kind, res_mode=mode, table_dtype=tdt, out_dtype=tdt)
+            if tab is None:                        # the same tables for every encoder
+                tab = (torch.rand(enc.table_shape(), device=dev, generator=gen) * 2 - 1).to(dts[tdt])
             grad = torch.zeros(enc.table_shape(), dtype=torch.float32, device=dev)
             o = torch.empty((P, n_out), dtype=dts[tdt], device=dev)
-            times = {}
-            for stage, fn in (("fwd", lambda: enc.encode_fwd(x, tab, o)), ("bwd", lambda: enc.encode_bwd(x, dout, grad))):
-                fn()
-                torch.cuda.synchronize(dev)
-                g = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(g):
-                    fn()
-                g.replay()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize(dev)
-                a.record()
-                for _ in range(reps):
-                    g.replay()
-                b.record()
-                torch.cuda.synchronize(dev)
-                times[stage] = a.elapsed_time(b) / reps / 1e3
-                del g
-            gathers = P * ea["n_levels"] * enc.n_vertices
-            words = tab.view(torch.float32).reshape(-1) if tab.element_size() == 4 else tab.view(torch.float32)
-            slots = 1 << int(math.log2(words.numel() // 2))
-            n_ops = 1 << 24
-            probe(1, words.data_ptr(), slots, 2, n_ops, 1, sink.data_ptr(), st)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            for r in range(3):
-                probe(1, words.data_ptr(), slots, 2, n_ops, 2 + r, sink.data_ptr(), st)
-            b.record()
-            torch.cuda.synchronize(dev)
-            peak = 3 * n_ops / (a.elapsed_time(b) / 1e3)
-            row[kind] = {"fwd_bwd_points_per_s": P / (times["fwd"] + times["bwd"]),
-                         "fwd_ms": times["fwd"] * 1e3, "bwd_ms": times["bwd"] * 1e3,
-                         "fwd_gathers_per_s": gathers / times["fwd"], "random_gather_peak_per_s": peak,
-                         "gather_roofline_frac": gathers / times["fwd"] / peak}
-            if kind == "simplex" and tdt == "f32":
-                times_p = {}
-                for stage, fn in (("fwd", lambda: enc.encode_plain_fwd(x, tab, o)),
-                                  ("bwd", lambda: enc.encode_plain_bwd(x, dout, grad))):
-                    fn()
-                    torch.cuda.synchronize(dev)
-                    g = torch.cuda.CUDAGraph()
-                    with torch.cuda.graph(g):
-                        fn()
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    torch.cuda.synchronize(dev)
-                    a.record()
-                    for _ in range(reps):
-                        g.replay()
-                    b.record()
-                    torch.cuda.synchronize(dev)
-                    times_p[stage] = a.elapsed_time(b) / reps / 1e3
-                    del g
-                row["simplex_plain_f32"] = {"fwd_bwd_points_per_s": P / (times_p["fwd"] + times_p["bwd"])}
-            del enc, tab, grad, o
-        row["grid_over_simplex"] = row["simplex"]["fwd_bwd_points_per_s"] / row["grid"]["fwd_bwd_points_per_s"]
+            tf = graph_time(lambda: enc.encode_fwd(x, tab, o), reps)
+            tb = graph_time(lambda: enc.encode_bwd(x, dout, grad), reps)
+            bf, bb = encode_bytes_per_point(ea, kind, tdt, tdt)
+            rec = {"res_mode": mode, "fwd_bwd_points_per_s": P / (tf + tb), "fwd_ms": tf * 1e3, "bwd_ms": tb * 1e3,
+                   "fwd_bytes_per_point": bf, "bwd_bytes_per_point": bb,
+                   "fwd_hbm_frac": P * bf / tf / 1e9 / hbm, "bwd_hbm_frac": P * bb / tb / 1e9 / hbm}
+            v = vname(kind, mode)
+            if ncu_ok:
+                for stage in ("fwd", "bwd"):
+                    c = ENCODE_NCU.get("%s/%s/%s" % (name, v, stage))
+                    if c:
+                        rec["%s_ncu" % stage] = c
+            row[v] = rec
+            if kind == "simplex" and mode == "raw" and tdt == "f32":
+                tpf = graph_time(lambda: enc.encode_plain_fwd(x, tab, o), reps)
+                tpb = graph_time(lambda: enc.encode_plain_bwd(x, dout, grad), reps)
+                row["simplex_plain_f32"] = {"res_mode": "raw", "fwd_bwd_points_per_s": P / (tpf + tpb),
+                                            "fwd_ms": tpf * 1e3, "bwd_ms": tpb * 1e3}
+            del enc, grad, o
+        for m in ("raw", "equal_mem"):
+            row["grid_over_simplex_time_" + m] = (row[vname("simplex", m)]["fwd_bwd_points_per_s"]
+                                                  / row["grid"]["fwd_bwd_points_per_s"])
         out[name] = row
-        del x, dout
+        del x, dout, tab
         torch.cuda.empty_cache()
+    out["ceiling"] = ("fwd/bwd_hbm_frac: algorithmic bytes / time / measured HBM copy peak (%.1f GB/s); "
+                      "*_ncu: ncu L2 sector and DRAM throughput as %% of peak, L2 hit rate, DRAM bytes per point "
+                      "(%s)" % (hbm, "capture matches these sources" if ncu_ok else "no capture of these sources"))
     return out
 
 
-def image_grid_step(dev, xd, td, simplex_ms, steps=100, warmup=5):
-    """The headline training step with the 2^d grid encoder instead of the simplex one (same
-    L, F, T, tables, network, batches): the comparison of Sec. 6.1's image-fitting run time."""
+def profile_encode(dev):
+    """One forward and one backward launch of every configuration and encoder of
+    ``per_config_encode`` (the volumetric configuration at 2^16 rays x 64 samples, so that the
+    capture holds a few GB), for an ncu capture of the encoding kernels; prints each launch's key."""
+    import torch
+    from paper_2311_15439_gb300.api import Encoder
+    dts = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+    gen = torch.Generator(device=dev).manual_seed(77)
+    for name, ea, tdt, P, pts in PER_CONFIG:
+        P = min(P, 1 << 22)
+        x = _config_points(dev, ea, P, pts)
+        n_out = ea["n_levels"] * ea["n_features"]
+        dout = torch.randn((P, n_out), device=dev, generator=gen)
+        tab = None
+        for kind, mode in VARIANTS:
+            enc = Encoder(**ea, kind=kind, res_mode=mode, table_dtype=tdt, out_dtype=tdt)
+            if tab is None:
+                tab = (torch.rand(enc.table_shape(), device=dev, generator=gen) * 2 - 1).to(dts[tdt])
+            grad = torch.zeros(enc.table_shape(), dtype=torch.float32, device=dev)
+            o = torch.empty((P, n_out), dtype=dts[tdt], device=dev)
+            enc.encode_fwd(x, tab, o)
+            nb = enc.bwd_kernel_count(P)
+            enc.encode_bwd(x, dout, grad)
+            torch.cuda.synchronize(dev)
+            print("launch %s/%s fwd 1, bwd %s points %d" % (name, vname(kind, mode), nb, P), flush=True)
+        del x, dout, tab
+        torch.cuda.empty_cache()
+
+
+def image_step_variants(dev, xd, td, simplex_ms, steps=100, warmup=5):
+    """The headline training step with the simplex encoder in the equal-memory setting and with the
+    2^d grid encoder instead (same L, F, T, table layout, network and batches): the comparison of
+    Sec. 6.1's image-fitting run time, per res_mode of the simplex side."""
     import torch
     from paper_2311_15439_gb300.api import Encoder, Mlp
     from paper_2311_15439_gb300.trainer import Trainer
-    enc = Encoder(**CFG, kind="grid", table_dtype="f16")
-    tr = Trainer(enc, Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16"), BATCH, seed=0,
-                 device=dev, table_layout="records")
-    for i in range(warmup):
-        tr.step(xd[i % len(xd)], td[i % len(td)])
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    a.record()
-    for i in range(steps):
-        tr.step(xd[i % len(xd)], td[i % len(td)])
-    b.record()
-    torch.cuda.synchronize(dev)
-    ms = a.elapsed_time(b) / steps
-    del tr
-    torch.cuda.empty_cache()
-    return {"grid_ms_per_step": ms, "grid_points_per_s": BATCH / (ms / 1e3), "simplex_ms_per_step": simplex_ms,
-            "grid_over_simplex": ms / simplex_ms, "steps": steps,
-            "note": "grid: 4 corners per level against the simplex's 3 vertices, same tables and network"}
+    out = {"simplex_raw": {"res_mode": "raw", "ms_per_step": simplex_ms, "points_per_s": BATCH / (simplex_ms / 1e3),
+                           "note": "the headline step"}}
+    for kind, mode in VARIANTS[1:]:
+        enc = Encoder(**CFG, kind=kind, res_mode=mode, table_dtype="f16")
+        tr = Trainer(enc, Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16"), BATCH, seed=0,
+                     device=dev, table_layout="records")
+        for i in range(warmup):
+            tr.step(xd[i % len(xd)], td[i % len(td)])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record()
+        for i in range(steps):
+            tr.step(xd[i % len(xd)], td[i % len(td)])
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / steps
+        out[vname(kind, mode)] = {"res_mode": mode, "ms_per_step": ms, "points_per_s": BATCH / (ms / 1e3),
+                                  "steps": steps}
+        del tr
+        torch.cuda.empty_cache()
+    for m in ("raw", "equal_mem"):
+        out["grid_over_simplex_time_" + m] = out["grid"]["ms_per_step"] / out[vname("simplex", m)]["ms_per_step"]
+    return out
+
+
+def _train_fixed_steps(dev, tr, steps, make_batch, chunk=100):
+    """``steps`` eager training steps on batches made on the device ``chunk`` at a time outside the
+    timed part; returns the summed CUDA-event time of the steps (s)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    total = 0.0
+    for c0 in range(0, steps, chunk):
+        batches = [make_batch() for _ in range(min(chunk, steps - c0))]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for x, t in batches:
+            tr.step(x, t)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        total += a.elapsed_time(b) / 1e3
+        del batches
+    return total
+
+
+def _predict(tr, x):
+    """The trained field at points x (device float32 [P, d]): encoding, then the network forward."""
+    enc = tr.enc.encode_fwd(x, tr.tables)
+    return tr.mlp.mlp_fwd(tr.W_lowp, enc)
+
+
+def fit_quality(dev, image_steps=5000, sdf_steps=2000):
+    """Quality at equal table size (Sec. 6.1): the image workload (L=16, F=2, T=2^22 fp16, network
+    32-64-64-3, 2^18 points per step, Adam) trained for ``image_steps`` steps with each encoder, and
+    the PSNR of its prediction (clipped to [0, 1]) over 2^18 held-out pixel centres against the FP64
+    image; the SDF-style workload (d=3, T=2^19 bf16, network 32-64-1, 2^20 points per step) trained
+    for ``sdf_steps`` steps, and its mean squared SDF error on 2^18 held-out points of the same
+    distribution (half uniform, half within 0.01 of the surface).  Training batches are drawn on
+    the device by torch from seeded generators; the step time excludes drawing them."""
+    import torch
+    from paper_2311_15439_gb300 import synth
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+    out = {}
+    img = synth.ProceduralImage(seed=7, size=16384, n_waves=64)
+    x_eval = synth.uniform_points(1 << 18, 2, 4242)
+    t_eval = img.sample(x_eval).astype(np.float64)
+    xe = torch.from_numpy(x_eval).to(dev)
+    res = {"steps": image_steps, "points_per_step": BATCH, "eval_pixels": 1 << 18,
+           "config": "d=2 L=16 F=2 T=2^22 fp16 base 16 growth 2.0, network 32-64-64-3 fp16"}
+    for kind, mode in VARIANTS:
+        enc = Encoder(**CFG, kind=kind, res_mode=mode, table_dtype="f16")
+        tr = Trainer(enc, Mlp(32, N_OUT, n_hidden=2, dtype="f16"), BATCH, seed=0, device=dev, table_layout="records")
+        gen = torch.Generator(device=dev).manual_seed(2024)
+
+        def batch():
+            x = torch.rand((BATCH, 2), generator=gen, device=dev)
+            return x, img.sample_torch(x)
+        sec = _train_fixed_steps(dev, tr, image_steps, batch)
+        y = np.clip(_predict(tr, xe).cpu().numpy().astype(np.float64), 0.0, 1.0)
+        mse = float(np.mean((y - t_eval) ** 2))
+        res[vname(kind, mode)] = {"res_mode": mode, "psnr_db": 10.0 * math.log10(1.0 / mse), "train_s": sec,
+                                  "final_batch_loss": tr.loss()}
+        del tr
+        torch.cuda.empty_cache()
+    out["image"] = res
+    scene = synth.SphereTorusScene(5)
+    xs_eval = scene.sample(1 << 18, 4343)
+    s_eval = scene.sdf(xs_eval).astype(np.float64)
+    xse = torch.from_numpy(xs_eval).to(dev)
+    P = 1 << 20
+    res = {"steps": sdf_steps, "points_per_step": P, "eval_points": 1 << 18,
+           "config": "d=3 L=16 F=2 T=2^19 bf16 base 16 growth 1.38, network 32-64-1 bf16"}
+    for kind, mode in VARIANTS:
+        enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, res_mode=mode, table_dtype="bf16")
+        tr = Trainer(enc, Mlp(32, 1, n_hidden=1, dtype="bf16"), P, seed=6, device=dev)
+        gen = torch.Generator(device=dev).manual_seed(2025)
+
+        def batch():
+            x = scene.sample_torch(P, gen)
+            return x, scene.sdf_torch(x)
+        sec = _train_fixed_steps(dev, tr, sdf_steps, batch)
+        err = _predict(tr, xse).cpu().numpy().astype(np.float64) - s_eval
+        near = np.abs(s_eval[:, 0]) < 0.01
+        res[vname(kind, mode)] = {"res_mode": mode, "eval_mse": float(np.mean(err ** 2)),
+                                  "eval_mae_near_surface": float(np.mean(np.abs(err[near]))), "train_s": sec,
+                                  "final_batch_loss": tr.loss()}
+        del tr
+        torch.cuda.empty_cache()
+    out["sdf"] = res
+    return out
 
 
 def sdf_train(dev, P=1 << 20, steps=20, warmup=3, n_batches=4):
@@ -689,8 +1059,8 @@ def sdf_train(dev, P=1 << 20, steps=20, warmup=3, n_batches=4):
     xs = [synth.sdf_points(P, 300 + i) for i in range(n_batches)]
     batches = [(torch.from_numpy(x).to(dev), torch.from_numpy(scene.sdf(x)).to(dev)) for x in xs]
     out = {"points_per_step": P, "config": "d=3 L=16 F=2 T=2^19 bf16, network 32-64-1 bf16"}
-    for kind in ("simplex", "grid"):
-        tr = Trainer(Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, table_dtype="bf16"),
+    for kind, mode in VARIANTS:
+        tr = Trainer(Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, res_mode=mode, table_dtype="bf16"),
                      Mlp(32, 1, n_hidden=1, dtype="bf16"), P, seed=6, device=dev)
         for i in range(warmup):
             tr.step(*batches[i % n_batches])
@@ -702,11 +1072,13 @@ def sdf_train(dev, P=1 << 20, steps=20, warmup=3, n_batches=4):
         b.record()
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / steps
-        out[kind] = {"ms_per_step": ms, "points_per_s": P / (ms / 1e3), "table_layout": tr.tab.layout,
-                     "coarse_levels_on_second_stream": tr.tab.split_coarse, "loss": tr.loss()}
+        out[vname(kind, mode)] = {"res_mode": mode, "ms_per_step": ms, "points_per_s": P / (ms / 1e3),
+                                  "table_layout": tr.tab.layout, "coarse_levels_on_second_stream": tr.tab.split_coarse,
+                                  "loss": tr.loss()}
         del tr
         torch.cuda.empty_cache()
-    out["grid_over_simplex"] = out["grid"]["ms_per_step"] / out["simplex"]["ms_per_step"]
+    for m in ("raw", "equal_mem"):
+        out["grid_over_simplex_time_" + m] = out["grid"]["ms_per_step"] / out[vname("simplex", m)]["ms_per_step"]
     out["table_backward_roofline"] = dense_bwd_roofline(dev, xs[0])
     return out
 
@@ -716,7 +1088,6 @@ def dense_bwd_roofline(dev, x_host, reps=20):
     rate of random float2 reductions over a footprint the size of the dense gradient array (which
     stays in L2): contributions / that rate over the CUDA-event time of the kernel."""
     import torch
-    from paper_2311_15439_gb300 import _lib as L
     from paper_2311_15439_gb300 import synth
     from paper_2311_15439_gb300.api import Encoder
     enc = Encoder(3, 16, 2, 19, 16.0, 1.38, table_dtype="bf16")
@@ -742,7 +1113,6 @@ def dense_bwd_roofline(dev, x_host, reps=20):
     sec = timed(lambda r: enc.encode_bwd(x, dout, grad, levels=(lc, enc.n_levels)), reps)
     n_ops, slots = 1 << 24, grad.numel() // 2
     sink = torch.zeros((1,), dtype=torch.float32, device=dev)
-    lib = L.lib()
     probe_s = timed(lambda r: probe(0, grad.data_ptr(), slots, 2, n_ops, r, sink.data_ptr(), st), 5)
     contributions = P * (enc.n_levels - lc) * enc.n_vertices
     peak = n_ops / probe_s
@@ -753,29 +1123,56 @@ def dense_bwd_roofline(dev, x_host, reps=20):
             "frac": contributions / sec / peak}
 
 
-def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5):
-    """Poisson-arriving field queries of 4K..4M points (log-uniform), d uniform in 2..5, served
-    by the continuous-batching loop; simplex fields vs 2^d grid fields (L=16, F=2, T=2^19, fp16)."""
+def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5, repeats=3, sweep=(250.0, 500.0, 1000.0, 2000.0)):
+    """Field queries of 4K..4M points (log-uniform), d uniform in 2..5, served by the continuous-
+    batching loop (L=16, F=2, T=2^19, fp16): per encoder (simplex in both res_modes, 2^d grid)
+    p50/p99 latency of ``repeats`` seeded Poisson runs at ``rate_hz`` (each run's figures and their
+    median), p50/p99 at a rising offered rate, and the capacity: points/s of a closed-loop run in
+    which every request of a stream is queued at once, so that the GPU never waits for arrivals."""
     import torch
     from paper_2311_15439_gb300 import synth
     from paper_2311_15439_gb300.serve import FieldServer, make_field, poisson_load, run_load
     sys.setswitchinterval(2e-4)          # let the scheduler thread take the GIL promptly
-    arrivals, ds, sizes = poisson_load(rate_hz, n_requests, (2, 3, 4, 5), 4096, 4 << 20, seed)
-    pools = {d: torch.from_numpy(synth.uniform_points(4 << 20, d, 900 + d)).pin_memory() for d in (2, 3, 4, 5)}
-    out = {"load": "%d Poisson requests at %.0f/s, sizes log-uniform 4K..4M points, d in {2,3,4,5}" % (n_requests, rate_hz)}
-    for kind in ("simplex", "grid"):
-        fields = {d: make_field(d, kind=kind, seed=d, device=dev) for d in (2, 3, 4, 5)}
+    dims = (2, 3, 4, 5)
+    pools = {d: torch.from_numpy(synth.uniform_points(4 << 20, d, 900 + d)).pin_memory() for d in dims}
+    out = {"load": "%d Poisson requests at %.0f/s per run, %d runs, sizes log-uniform 4K..4M points, d in {2,3,4,5}"
+                   % (n_requests, rate_hz, repeats)}
+
+    def one_run(srv, rate, n, s):
+        arrivals, ds, sizes = poisson_load(rate, n, dims, 4096, 4 << 20, s)
+        if rate == float("inf"):
+            arrivals = np.zeros_like(arrivals)
+        reqs, wall = run_load(srv, arrivals, ds, sizes, pools, s)
+        lat = np.array([r.latency for r in reqs]) * 1e3
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "offered_points_per_s": float(sizes.sum() / arrivals[-1]) if arrivals[-1] > 0 else None,
+                "served_points_per_s": float(sizes.sum() / wall),
+                "errors": sum(r.error is not None for r in reqs)}
+
+    for kind, mode in VARIANTS:
+        fields = {d: make_field(d, kind=kind, res_mode=mode, seed=d, device=dev) for d in dims}
         srv = FieldServer(fields, mem_budget_bytes=4 << 30, n_slots=4, max_batch_points=4 << 20, device=dev).start()
-        # warm-up: one request per d (allocator, pinned buffers, kernel load)
-        for d in (2, 3, 4, 5):
+        for d in dims:                   # warm-up: one request per d (allocator, pinned buffers, kernel load)
             if not srv.submit(d, pools[d][:65536]).wait(120.0):
                 raise TimeoutError("serving warm-up request did not complete")
-        reqs, wall = run_load(srv, arrivals, ds, sizes, pools, seed)
+        runs = [one_run(srv, rate_hz, n_requests, seed + r) for r in range(repeats)]
+        rising = {str(int(rt)): one_run(srv, rt, n_requests // 2, seed + 100 + k) for k, rt in enumerate(sweep)}
+        closed = one_run(srv, float("inf"), n_requests, seed + 200)
         srv.stop()
-        lat = np.array([r.latency for r in reqs]) * 1e3
-        out[kind] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "points_per_s": float(sizes.sum() / wall), "batches": srv.n_batches,
-                     "errors": sum(r.error is not None for r in reqs)}
+        out[vname(kind, mode)] = {
+            "res_mode": mode,
+            "p50_ms": float(np.median([r["p50_ms"] for r in runs])),
+            "p99_ms": float(np.median([r["p99_ms"] for r in runs])),
+            "p50_ms_runs": [r["p50_ms"] for r in runs], "p99_ms_runs": [r["p99_ms"] for r in runs],
+            "offered_points_per_s": float(np.median([r["offered_points_per_s"] for r in runs])),
+            "capacity_points_per_s": closed["served_points_per_s"],
+            "by_offered_rate_hz": rising, "batches": srv.n_batches,
+            "errors": sum(r["errors"] for r in runs) + closed["errors"]}
+        del srv, fields
+        torch.cuda.empty_cache()
+    for m in ("raw", "equal_mem"):
+        out["simplex_over_grid_capacity_" + m] = (out[vname("simplex", m)]["capacity_points_per_s"]
+                                                   / out["grid"]["capacity_points_per_s"])
     return out
 
 
@@ -803,27 +1200,148 @@ def oracle_step(x, tgt, H, W, state, t):
     return loss
 
 
-def time_oracle(sample_points, steps, seconds_cap):
+# The same oracle step spread over host cores: a pool of worker processes (spawn) attached to the
+# table, moment and gradient arrays in shared memory.  Phase 1 splits the points: each worker
+# encodes its chunk, runs the network forward, the L2 loss and the backward (its loss gradient
+# rescaled from its chunk's mean to the batch's); phase 2 splits the levels: each worker
+# scatters dL/d(encoding) of all points into its levels of the gradient; phase 3 splits the table
+# parameters: each worker runs Adam on its range.  Every phase calls the oracle's own functions.
+_W = {}
+
+
+def _shm_array(name, shape):
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=name)
+    return shm, np.ndarray(shape, dtype=np.float64, buffer=shm.buf)
+
+
+def _worker_init(names, shape):
+    for key, name in names.items():
+        _W[key] = _shm_array(name, shape)
+
+
+def _w_points(x, tgt, W, P_total):
+    from oracle import encoding, mlp
+    H = _W["H"][1]
+    e = encoding.simplex_encode(x, H, base_res=CFG["base_res"], growth=CFG["growth"])
+    y, acts = mlp.mlp_forward(W, e)
+    loss, dy = mlp.l2_loss(y, tgt)
+    dy = dy * (x.shape[0] / P_total)                      # the batch mean's gradient
+    dW, de = mlp.mlp_backward(W, acts, dy)
+    return loss * x.shape[0], dW, de
+
+
+def _w_levels(x, de, levels):
+    from oracle import encoding
+    H, g = _W["H"][1], _W["g"][1]
+    L, T, F = H.shape
+    grads = encoding.simplex_encode_bwd(x, de, n_levels=L, log2_T=int(T).bit_length() - 1, n_features=F,
+                                        base_res=CFG["base_res"], growth=CFG["growth"], levels=levels)
+    for l, gl in grads.items():
+        g[l] = gl
+
+
+def _w_adam(lo, hi, t):
+    from oracle import adam
+    H, m, v, g = (_W[k][1].reshape(-1) for k in ("H", "m", "v", "g"))
+    H[lo:hi], m[lo:hi], v[lo:hi] = adam.adam_step(H[lo:hi], g[lo:hi], m[lo:hi], v[lo:hi], t, skip_zero_grad=True,
+                                                  lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15)
+
+
+class ParallelOracle:
+    """The oracle's training step (encode, network + L2 loss, backward, scatter, Adam over every
+    table parameter and the network) on ``n`` worker processes; the arrays of the full workload
+    (L = 16, T = 2^22, F = 2, FP64) live in shared memory."""
+
+    def __init__(self, n):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        from paper_2311_15439_gb300 import synth
+        L, T, F = CFG["n_levels"], 1 << CFG["log2_T"], CFG["n_features"]
+        self.shape, self.n = (L, T, F), n
+        self.shm, self.arr = {}, {}
+        for key in ("H", "m", "v", "g"):
+            shm = shared_memory.SharedMemory(create=True, size=L * T * F * 8)
+            self.shm[key] = shm
+            self.arr[key] = np.ndarray(self.shape, dtype=np.float64, buffer=shm.buf)
+            self.arr[key][:] = 0.0
+        self.arr["H"][:] = synth.uniform_tables(L, T, F, 0, dtype="f32", scale=1e-4)[0]
+        g = np.random.Generator(np.random.PCG64(1))
+        self.W = [g.uniform(-math.sqrt(6 / fi), math.sqrt(6 / fi), size=(fo, fi)) for fo, fi in
+                  [(64, 32), (64, 64), (3, 64)]]
+        self.mW = [np.zeros_like(w) for w in self.W]
+        self.vW = [np.zeros_like(w) for w in self.W]
+        self.pool = mp.get_context("spawn").Pool(n, initializer=_worker_init,
+                                                 initargs=({k: v.name for k, v in self.shm.items()}, self.shape))
+
+    def step(self, x, tgt, t):
+        from oracle import adam
+        P, n = x.shape[0], self.n
+        cuts = np.linspace(0, P, n + 1).astype(int)
+        parts = self.pool.starmap(_w_points, [(x[a:b], tgt[a:b], self.W, P) for a, b in zip(cuts[:-1], cuts[1:])
+                                              if b > a])
+        loss = sum(p[0] for p in parts) / P
+        dW = [sum(p[1][i] for p in parts) for i in range(len(self.W))]
+        de = np.concatenate([p[2] for p in parts])
+        L = self.shape[0]
+        self.pool.starmap(_w_levels, [(x, de, list(range(k, L, n))) for k in range(min(n, L))])
+        N = int(np.prod(self.shape))
+        cuts = np.linspace(0, N, n + 1).astype(np.int64)
+        self.pool.starmap(_w_adam, [(int(a), int(b), t) for a, b in zip(cuts[:-1], cuts[1:])])
+        for i in range(len(self.W)):
+            self.W[i], self.mW[i], self.vW[i] = adam.adam_step(self.W[i], dW[i], self.mW[i], self.vW[i], t,
+                                                               skip_zero_grad=False, lr=1e-2, beta1=0.9, beta2=0.99,
+                                                               eps=1e-15)
+        return loss
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for shm in self.shm.values():
+            shm.close()
+            shm.unlink()
+
+
+def host_cores():
+    """Host cores this process may run on (the count ``nproc`` prints)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(sample_points, steps, seconds_cap, cores=1):
+    """Points/s of the oracle's training step on ``sample_points``-point batches of the image
+    workload (full tables), on one core (the plain oracle step) or ``cores`` worker processes."""
     from paper_2311_15439_gb300 import synth
-    L, T, F = CFG["n_levels"], 1 << CFG["log2_T"], CFG["n_features"]
-    H = synth.uniform_tables(L, T, F, 0, dtype="f32", scale=1e-4)[0].astype(np.float64)
-    g = np.random.Generator(np.random.PCG64(1))
-    dims = [(64, 32), (64, 64), (3, 64)]
-    W = [g.uniform(-math.sqrt(6 / fi), math.sqrt(6 / fi), size=(fo, fi)) for fo, fi in dims]
-    state = {"m": np.zeros_like(H), "v": np.zeros_like(H), "mW": [np.zeros_like(w) for w in W],
-             "vW": [np.zeros_like(w) for w in W]}
     img = synth.ProceduralImage(seed=7, size=16384, n_waves=64)
+    par = ParallelOracle(cores) if cores > 1 else None
+    if par is None:
+        L, T, F = CFG["n_levels"], 1 << CFG["log2_T"], CFG["n_features"]
+        H = synth.uniform_tables(L, T, F, 0, dtype="f32", scale=1e-4)[0].astype(np.float64)
+        g = np.random.Generator(np.random.PCG64(1))
+        dims = [(64, 32), (64, 64), (3, 64)]
+        W = [g.uniform(-math.sqrt(6 / fi), math.sqrt(6 / fi), size=(fo, fi)) for fo, fi in dims]
+        state = {"m": np.zeros_like(H), "v": np.zeros_like(H), "mW": [np.zeros_like(w) for w in W],
+                 "vW": [np.zeros_like(w) for w in W]}
     done, t0 = 0, time.perf_counter()
     times = []
-    for k in range(steps):
-        x = synth.uniform_points(sample_points, 2, 5000 + k)
-        tgt = img.sample(x)
-        s = time.perf_counter()
-        oracle_step(x, tgt, H, W, state, k + 1)
-        times.append(time.perf_counter() - s)
-        done += 1
-        if time.perf_counter() - t0 > seconds_cap:
-            break
+    try:
+        for k in range(steps):
+            x = synth.uniform_points(sample_points, 2, 5000 + k)
+            tgt = img.sample(x)
+            s = time.perf_counter()
+            if par is None:
+                oracle_step(x, tgt, H, W, state, k + 1)
+            else:
+                par.step(x, tgt, k + 1)
+            times.append(time.perf_counter() - s)
+            done += 1
+            if time.perf_counter() - t0 > seconds_cap:
+                break
+    finally:
+        if par is not None:
+            par.close()
     return sample_points * done / sum(times), done, times
 
 
@@ -831,26 +1349,36 @@ def cpu_baseline_subprocess(seconds):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--cpu-seconds", str(seconds)]
     try:
-        res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+        res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
         return json.loads(res.stdout.strip().splitlines()[-1])
     except Exception as exc:  # report, do not fail the GPU line
         return {"value": None, "error": repr(exc)[:200]}
 
 
 def cpu_baseline_only(seconds):
+    """The oracle's training step on all host cores (the reported value) and on one core, each
+    for about ``seconds`` of wall time."""
     sample = 1 << 13
-    v, done, _ = time_oracle(sample, 1000, seconds)
-    print(json.dumps({"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
-                      "sample": "%d oracle steps of %d points each on the full workload tables "
-                               "(L=16, T=2^22, F=2; Adam over all 134M table parameters)" % (done, sample)}))
+    n = host_cores()
+    v1, d1, _ = time_oracle(sample, 1000, seconds / 2, cores=1)
+    vn, dn, _ = time_oracle(sample, 1000, seconds / 2, cores=n) if n > 1 else (v1, d1, None)
+    what = ("oracle steps of %d points each on the full workload tables (L=16, T=2^22, F=2; Adam over all "
+            "134M table parameters)" % sample)
+    print(json.dumps({"value": vn, "unit": "points/s", "cores": n, "kind": "oracle",
+                      "sample": "%d %s, %d worker processes (points, levels and parameter ranges split)"
+                                % (dn, what, n),
+                      "single_core": {"value": v1, "cores": 1, "sample": "%d %s" % (d1, what)}}))
 
 
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
         return
-    sample = 1 << 12
-    _, done, times = time_oracle(sample, args.warmup + args.steps, 1e9)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")                     # one thread per worker process
+    sample = 1 << 13
+    n = host_cores()
+    _, done, times = time_oracle(sample, args.warmup + args.steps, 1e9, cores=n)
     t = times[args.warmup:]
     value = sample * len(t) / sum(t)
     print(json.dumps({
@@ -858,8 +1386,9 @@ def run_reference(args):
         "steps": len(t), "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points_per_step": sample},
-        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d-point steps of the full workload (tables L=16, T=2^22)" % sample},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": n, "kind": "oracle",
+                         "sample": "%d-point steps of the full workload (tables L=16, T=2^22), %d worker processes"
+                                   % (sample, n)},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -875,14 +1404,23 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-volume", action="store_true")
-    ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05"],
+    ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05", "tcgen05_pipelined"],
                     help="kernel of the network training pass")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--quality-steps", type=int, default=5000,
+                    help="training steps of the image quality runs (the SDF runs take 2/5 of it); 0 skips them")
+    ap.add_argument("--profile-encode", action="store_true",
+                    help="one launch of each encoding kernel per configuration and encoder (for an ncu capture)")
     ap.add_argument("--cpu-baseline-only", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.cpu_baseline_only:
+    if args.profile_encode:
+        import torch
+        from paper_2311_15439_gb300 import build as B
+        B.build()
+        profile_encode(torch.device("cuda", 0))
+    elif args.cpu_baseline_only:
         cpu_baseline_only(args.cpu_seconds)
     elif args.impl == "reference":
         run_reference(args)

@@ -238,11 +238,12 @@ class FieldServer:
 
 
 def make_field(d: int, *, n_levels=16, n_features=2, log2_T=19, base_res=16.0, growth=1.38, kind="simplex",
-               n_out=1, seed=0, device="cuda", table_dtype="f16") -> Field:
+               res_mode="raw", n_out=1, seed=0, device="cuda", table_dtype="f16") -> Field:
     """A field with seeded tables U(-1e-1, 1e-1) and He-uniform weights (a stand-in for a trained one:
     the serving cost does not depend on the values)."""
     from . import synth
-    enc = Encoder(d, n_levels, n_features, log2_T, base_res, growth, kind=kind, table_dtype=table_dtype)
+    enc = Encoder(d, n_levels, n_features, log2_T, base_res, growth, kind=kind, res_mode=res_mode,
+                  table_dtype=table_dtype)
     vals = synth.uniform_tables(n_levels, 1 << log2_T, n_features, seed, dtype="f32", scale=1e-1)[0]
     dt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[table_dtype]
     tables = torch.from_numpy(vals).to(device=device, dtype=dt)

@@ -122,6 +122,69 @@ class SphereTorusScene:
             best = np.minimum(best, dist)
         return best.astype(np.float32)[:, None]
 
+    def sdf_torch(self, x):
+        """``sdf`` evaluated with torch on x's device in binary32 (float32 tensor [P, 3] -> [P, 1])."""
+        import torch
+        best = torch.full((x.shape[0],), float("inf"), dtype=torch.float32, device=x.device)
+        for kind, c, r in zip(self.kinds, self.centres, self.radii):
+            p = x - torch.as_tensor(c, dtype=torch.float32, device=x.device)
+            if kind == 0:
+                dist = torch.linalg.norm(p, dim=1) - float(r)
+            else:
+                q = torch.stack([torch.hypot(p[:, 0], p[:, 1]) - float(r), p[:, 2]], dim=1)
+                dist = torch.linalg.norm(q, dim=1) - float(r) / 3.0
+            best = torch.minimum(best, dist)
+        return best[:, None]
+
+    def sample_torch(self, P: int, gen, band: float = 0.01):
+        """P training points on ``gen``'s device: half uniform in [0,1)^3, half within ``band`` of
+        this scene's surface (a random shape, a random point on it, a random normal offset), the
+        recipe of ``sdf_points`` applied to this scene; float32 [P, 3]."""
+        import torch
+        dev = gen.device
+        n_uni = P // 2
+        n_sur = P - n_uni
+        uni = torch.rand((n_uni, 3), generator=gen, device=dev)
+        which = torch.randint(0, len(self.kinds), (n_sur,), generator=gen, device=dev)
+        kinds = torch.as_tensor(self.kinds, device=dev)[which]
+        c = torch.as_tensor(self.centres, dtype=torch.float32, device=dev)[which]
+        r = torch.as_tensor(self.radii, dtype=torch.float32, device=dev)[which]
+        off = (torch.rand((n_sur,), generator=gen, device=dev) * 2 - 1) * band
+        u = torch.randn((n_sur, 3), generator=gen, device=dev)
+        u = u / torch.linalg.norm(u, dim=1, keepdim=True)
+        angle = torch.rand((n_sur,), generator=gen, device=dev) * (2 * np.pi)
+        tube = torch.rand((n_sur,), generator=gen, device=dev) * (2 * np.pi)
+        sph = c + (r + off)[:, None] * u
+        rm = r / 3.0 + off
+        tor = torch.stack([c[:, 0] + (r + rm * torch.cos(tube)) * torch.cos(angle),
+                           c[:, 1] + (r + rm * torch.cos(tube)) * torch.sin(angle),
+                           c[:, 2] + rm * torch.sin(tube)], dim=1)
+        sur = torch.where((kinds == 0)[:, None], sph, tor).clamp_(0.0, float(np.nextafter(np.float32(1), 0)))
+        pts = torch.cat([uni, sur])
+        return pts[torch.randperm(P, generator=gen, device=dev)]
+
+    def sample(self, P: int, seed: int, band: float = 0.01) -> np.ndarray:
+        """Host (numpy) form of ``sample_torch``'s recipe: half uniform in [0,1)^3, half within
+        ``band`` of this scene's surface; float32 [P, 3]."""
+        g = rng(seed)
+        n_uni = P // 2
+        n_sur = P - n_uni
+        uni = g.random((n_uni, 3))
+        which = g.integers(0, len(self.kinds), size=n_sur)
+        c, r = self.centres[which], self.radii[which]
+        off = g.uniform(-band, band, size=n_sur)
+        u = g.standard_normal((n_sur, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        angle = g.uniform(0.0, 2 * np.pi, size=n_sur)
+        tube = g.uniform(0.0, 2 * np.pi, size=n_sur)
+        sph = c + (r + off)[:, None] * u
+        rm = r / 3.0 + off
+        tor = np.stack([c[:, 0] + (r + rm * np.cos(tube)) * np.cos(angle),
+                        c[:, 1] + (r + rm * np.cos(tube)) * np.sin(angle),
+                        c[:, 2] + rm * np.sin(tube)], axis=1)
+        sur = np.clip(np.where((self.kinds[which] == 0)[:, None], sph, tor), 0.0, np.nextafter(1.0, 0.0))
+        return np.concatenate([uni, sur]).astype(np.float32)
+
 
 def sdf_points(P: int, seed: int, n_shapes: int = 32, band: float = 0.01) -> np.ndarray:
     """Half uniform in [0,1)^3, half within ``band`` of a seeded union of spheres and tori."""
@@ -228,3 +291,25 @@ class ProceduralImage:
                   + (1 - fx) * fy * nz[ix, iy + 1] + fx * fy * nz[ix + 1, iy + 1])
             out[:, ch] = 0.5 + 0.35 * s + 0.3 * (vn - 0.5)
         return np.clip(out, 0.0, 1.0).astype(np.float32)
+
+    def sample_torch(self, x):
+        """``sample`` evaluated with torch on x's device in binary32 (for generating many training
+        batches on the GPU; within about 1e-5 of the FP64 ``sample``).  x: float32 tensor [P, 2]."""
+        import torch
+        dev = x.device
+        px = (torch.floor(x * self.size) + 0.5) / self.size
+        gx, gy = px[:, 0] * 64.0, px[:, 1] * 64.0
+        ix = torch.clamp(gx.to(torch.int64), max=63)
+        iy = torch.clamp(gy.to(torch.int64), max=63)
+        fx, fy = gx - ix.to(gx.dtype), gy - iy.to(gy.dtype)
+        out = torch.empty((x.shape[0], 3), dtype=torch.float32, device=dev)
+        for ch in range(3):
+            k = torch.as_tensor(self.dirs[ch] * np.abs(self.freq[ch]), dtype=torch.float32, device=dev)
+            ph = torch.as_tensor(self.phase[ch], dtype=torch.float32, device=dev)
+            amp = torch.as_tensor(self.amp[ch], dtype=torch.float32, device=dev)
+            s = torch.sin(px @ k.T + ph) @ amp
+            nz = torch.as_tensor(self.noise[ch], dtype=torch.float32, device=dev)
+            vn = ((1 - fx) * (1 - fy) * nz[ix, iy] + fx * (1 - fy) * nz[ix + 1, iy]
+                  + (1 - fx) * fy * nz[ix, iy + 1] + fx * fy * nz[ix + 1, iy + 1])
+            out[:, ch] = 0.5 + 0.35 * s + 0.3 * (vn - 0.5)
+        return out.clamp_(0.0, 1.0)
