@@ -40,10 +40,10 @@ METRIC = "simplex encode fwd+bwd points/s vs 2^d grid & plain FP32 path; serve p
 N_POOL = 8   # distinct resident batches cycled through the timed steps
 
 # DRAM traffic of one step's launch of a stage (dram__bytes_read.sum + dram__bytes_write.sum of its
-# kernels in one ncu capture of this workload), with the SHA-1 of the kernel sources it was taken
-# on: the figure is reported only while those sources are unchanged.
+# kernels in one ncu capture of this workload, profiles/train_step_image2d_L16_T2^22_P2^18_dram_traffic.md),
+# with the SHA-1 of the kernel sources it was taken on: reported only while those sources are unchanged.
 TRAFFIC = {
-    "encode_bwd": (35.82e6 + 755.55e6, "6db9b692110c81022350715653cfadf71ada9d02",
+    "encode_bwd": (35.8e6 + 755.5e6, "6db701334defea99e67fdb327a63812a5a022b63",
                    ("encode.cu", "encode_common.cuh", "lattice.cuh")),
 }
 
@@ -897,6 +897,28 @@ def per_config_encode(dev):
     return out
 
 
+def profile_mlp(dev, kernel):
+    """Three launches of the image workload's network training pass (32 -> 64 -> 64 -> 3 fp16, L2
+    loss, 2^18 points) on ``kernel``, for a one-kernel ncu capture (about 60 MB on the device)."""
+    import torch
+    from paper_2311_15439_gb300 import _lib, synth
+    from paper_2311_15439_gb300.api import Mlp
+    from paper_2311_15439_gb300.trainer import default_loss_scale
+    _lib.check(_lib.lib().sxe_mlp_set_kernel(kernel), "sxe_mlp_set_kernel")
+    mlp = Mlp(32, N_OUT, n_hidden=2, dtype="f16")
+    W = torch.from_numpy(mlp.init_weights(1)).to(dev).half()
+    x = torch.from_numpy(synth.rng(2).uniform(-1, 1, size=(BATCH, 32)).astype(np.float32)).to(dev).half()
+    t = torch.from_numpy(synth.rng(3).random((BATCH, N_OUT)).astype(np.float32)).to(dev)
+    dW = torch.zeros((mlp.n_params,), device=dev)
+    din = torch.empty((BATCH, 32), device=dev)
+    sq = torch.zeros((1,), device=dev)
+    ws = mlp.workspace(BATCH, dev)
+    for _ in range(3):
+        mlp.mlp_train_l2(W, x, t, dW, sq, din=din, loss_scale=default_loss_scale(BATCH, N_OUT), workspace=ws)
+    torch.cuda.synchronize(dev)
+    print("network training pass x3 done, kernel %d" % kernel)
+
+
 def profile_encode(dev):
     """One forward and one backward launch of every configuration and encoder of
     ``per_config_encode`` (the volumetric configuration at 2^16 rays x 64 samples, so that the
@@ -1409,13 +1431,23 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--quality-steps", type=int, default=5000,
                     help="training steps of the image quality runs (the SDF runs take 2/5 of it); 0 skips them")
+    ap.add_argument("--profile-mlp", action="store_true",
+                    help="three launches of the network training pass on --mlp-kernel (for an ncu capture)")
     ap.add_argument("--profile-encode", action="store_true",
                     help="one launch of each encoding kernel per configuration and encoder (for an ncu capture)")
     ap.add_argument("--cpu-baseline-only", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.profile_encode:
+    if args.profile_mlp:
+        import torch
+        from paper_2311_15439_gb300 import _lib
+        from paper_2311_15439_gb300 import build as B
+        B.build()
+        profile_mlp(torch.device("cuda", 0), {"auto": _lib.SXE_MLP_KERNEL_AUTO, "mma_sync": _lib.SXE_MLP_KERNEL_MMA_SYNC,
+                                              "tcgen05": _lib.SXE_MLP_KERNEL_TCGEN05,
+                                              "tcgen05_pipelined": _lib.SXE_MLP_KERNEL_TCGEN05_PIPELINED}[args.mlp_kernel])
+    elif args.profile_encode:
         import torch
         from paper_2311_15439_gb300 import build as B
         B.build()

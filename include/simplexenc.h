@@ -429,11 +429,15 @@ sxe_status sxe_step_touched_dev(const sxe_adam_desc* desc, const float* correcti
  * fits, two 128-point tiles in flight per SM and the weight gradients on tcgen05 too, else one
  * tile per CTA with the weight gradients on mma.sync).  SXE_MLP_KERNEL_AUTO (the default)
  * takes the two-tile tcgen05 kernel where it applies and mma.sync elsewhere.  All compute the
- * same products in the same precision (fp16/bf16 operands, binary32 accumulation).  Not
- * thread-safe: set it before launching work. */
+ * same products in the same precision (fp16/bf16 operands, binary32 accumulation).
+ * SXE_MLP_KERNEL_TCGEN05_PIPELINED: tcgen05 with one warp issuing every product of the CTA for up
+ * to four 128-point tiles in flight (each tile's epilogues run in its own warpgroup), the weight
+ * gradients of all tiles accumulating in one set of TMEM accumulators.  Not thread-safe: set it
+ * before launching work. */
 #define SXE_MLP_KERNEL_AUTO 0
 #define SXE_MLP_KERNEL_MMA_SYNC 1
 #define SXE_MLP_KERNEL_TCGEN05 2
+#define SXE_MLP_KERNEL_TCGEN05_PIPELINED 3
 sxe_status sxe_mlp_set_kernel(int32_t kernel);
 int32_t sxe_mlp_get_kernel(void);
 

@@ -823,6 +823,8 @@ sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, 
                           float* ws, int grid, cudaStream_t s, int din_group) {
   // automatic choice: the two-tile tcgen05 kernel where it applies (measured faster than mma.sync:
   // 65.6 against 67.6 us per 2^18-point pass), mma.sync elsewhere
+  if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_PIPELINED)
+    return launch_mlp_bwd_ws(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);
   if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05 || (g_mlp_kernel == SXE_MLP_KERNEL_AUTO && mlp_tc2_applies(d, grid)))
     return launch_mlp_bwd_tc(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);
   return d->dtype == SXE_F16

@@ -827,6 +827,427 @@ mlp_train_tc2_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
   }
 }
 
+// ---- warp-specialised: one MMA-issuing warp feeding up to four tiles -------------------------
+// The two kernels above issue each tile's products from the tile's own threads, so a tile's
+// chain of products (2 NH + 2 of them, each waiting for the epilogue before it) leaves the tensor
+// cores idle unless another tile happens to be ready.  Here one thread of a dedicated warp issues
+// every product of the CTA: it polls the tiles' "operands ready" barriers in turn and issues the
+// next product of whichever tile is ready, so up to SLOTS tiles (one per epilogue warpgroup) keep
+// the tensor cores fed.  Because a single thread issues every product, the weight-gradient
+// products of all tiles accumulate into one set of TMEM accumulators (products from one thread
+// execute in order), which is what leaves TMEM room for four tiles.  Shared memory per tile is the
+// input tile, one buffer per hidden layer and the output delta: each hidden layer's activations
+// are overwritten in place by its delta once the products that read them have completed.
+//
+// Stages of one tile (one product each, weight-gradient products riding along on the backward):
+//   0            acc = X W_0^T                               -> H_0 = relu(acc)
+//   h < NH       acc = H_{h-1} W_h^T                         -> H_h = relu(acc)
+//   NH           acc = H_{NH-1} W_out^T                      -> dY (loss) in registers, DY tile
+//   NH+1         dW_out^T += H_{NH-1}^T DY; acc = DY W_out   -> dH_{NH-1} = acc * [H_{NH-1} > 0], in place
+//   NH+1+j       dW_h += dH_h^T H_{h-1};    acc = dH_h W_h   -> dH_{h-1} = acc * [H_{h-1} > 0], in place
+//   2 NH + 1     dW_0 += dH_0^T X;          acc = dH_0 W_0   -> dX (the input gradient)
+// Barriers per tile slot: ready (one epilogue thread arrives, after a named barrier of the slot's
+// 128 threads, once the stage's operands are in shared memory and the previous accumulator has been
+// read) and full (the MMA thread's commit);
+// every wait is bounded and a shared abort word lets all warps unwind together.
+template <int N_IN, int NH>
+struct WsSmem {
+  static constexpr int X = 0;                                 // per slot: [128][N_IN]
+  static constexpr int H = X + kM * N_IN * 2;                 // NH x [128][64], activations then deltas
+  static constexpr int DY = H + NH * kM * kW * 2;             // [128][16]
+  static constexpr int SLOT = DY + kM * 16 * 2;
+  static constexpr int WBYTES = 2 * (kW * N_IN * 2) + 2 * ((NH - 1) * kW * kW * 2) + 2 * (16 * kW * 2);
+  static constexpr int FIT = (227 * 1024 - WBYTES) / SLOT;
+  static constexpr int SLOTS = FIT >= 4 ? 4 : FIT;
+  static constexpr int W0 = SLOTS * SLOT;                     // weights, as TcSmem
+  static constexpr int WH = W0 + kW * N_IN * 2;
+  static constexpr int WO = WH + (NH - 1) * kW * kW * 2;
+  static constexpr int WOT = WO + 16 * kW * 2;
+  static constexpr int WHT = WOT + kW * 16 * 2;
+  static constexpr int W0T = WHT + (NH - 1) * kW * kW * 2;
+  static constexpr int END = W0T + N_IN * kW * 2;
+  static constexpr int THREADS = SLOTS * 128 + 32;
+  static constexpr int STAGES = 2 * NH + 2;
+  // TMEM: one 64-column accumulator per slot, then dW_out^T (16), dW_1..dW_{NH-1} (64 each), dW_0
+  static constexpr int C_OUT = SLOTS * 64;
+  static constexpr int C_HID = C_OUT + 16;
+  static constexpr int C_FIRST = C_HID + 64 * (NH - 1);
+  static constexpr int COLS = C_FIRST + N_IN;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(mbar)) : "memory");
+}
+
+// non-blocking probe: has the phase with this parity completed?
+__device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(tc::smem_u32(mbar)), "r"(parity) : "memory");
+  return done != 0;
+}
+
+// bounded wait (try_wait lets the hardware suspend the thread until the phase completes or a short
+// time limit passes, instead of spinning on shared memory) that also gives up once another thread
+// has raised the CTA's abort word, checked every 64 polls
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* mbar, uint32_t parity, volatile int* abort_word) {
+  for (uint32_t it = 0; it < kWaitPolls; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(tc::smem_u32(mbar)), "r"(parity) : "memory");
+    if (done) return true;
+    if ((it & 63u) == 63u && *abort_word) return false;
+  }
+  *abort_word = 1;
+  return false;
+}
+
+template <typename T, int N_IN, int NH, int MODE>
+__global__ void __launch_bounds__(WsSmem<N_IN, NH>::THREADS, 1)
+mlp_train_ws_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
+                    const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
+                    float inv_count, float* __restrict__ din, int din_group, float* __restrict__ ws,
+                    int64_t n_params) {
+  using S = WsSmem<N_IN, NH>;
+  constexpr int SL = S::SLOTS;
+  constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
+  static_assert(SL >= 1 && S::END <= 227 * 1024 && S::COLS <= 512, "shared memory / TMEM plan");
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t ready[SL], full[SL], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_word;
+  __shared__ int n_done_tiles;
+  __shared__ float sq_part[SL * 4];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t n_tiles = (P + kM - 1) / kM;
+  const int64_t stride = (int64_t)gridDim.x * SL;
+  const float inv_scale = 1.f / loss_scale;
+
+  load_weights_cm<T, N_IN, NH, S>(W, n_out, sm);
+  if (tid == 0) {
+    for (int s = 0; s < SL; ++s) {
+      tc::mbar_init(&ready[s], 1);
+      tc::mbar_init(&full[s], 1);
+    }
+    tc::mbar_init(&done, 1);
+    abort_word = 0;
+    n_done_tiles = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  tc::fence_smem_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  volatile int* abort_p = &abort_word;
+  float sq = 0.f;
+
+  if (warp == 4 * SL) {
+    // ---------------- the MMA-issuing warp (one thread)
+    if (lane == 0) {
+      int st[SL], rnd[SL];
+      int64_t tile[SL];
+      uint32_t rph[SL];
+      int active = 0;
+      for (int s = 0; s < SL; ++s) {
+        tile[s] = (int64_t)blockIdx.x * SL + s;
+        st[s] = 0;
+        rnd[s] = 0;
+        rph[s] = 0;
+        active += tile[s] < n_tiles;
+      }
+      // The weight-gradient stages (NH + 1 .. 2 NH + 1) of this CTA's tiles are issued in tile order
+      // (ordinal rnd * SL + slot), one turn counter per stage, so that every TMEM accumulator sums
+      // its tiles in the same order on every run: the partials, and dweights, are deterministic.
+      // A tile only ever waits for lower ordinals, so the turns cannot deadlock.
+      int turn[NH + 1];
+      for (int j = 0; j <= NH; ++j) turn[j] = 0;
+      bool first_out = true, first_0 = true;
+      uint32_t first_h = (1u << NH) - 1u;
+      constexpr uint32_t kH = (kW / 8) * 128, kDY = (16 / 8) * 128, kX = (N_IN / 8) * 128;
+      auto wgrad = [&](uint32_t d, const unsigned char* A, uint32_t kA, const unsigned char* B, uint32_t kB, int N,
+                       bool first) {
+        const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B), id = tc::idesc_f16_mn(64, N, BF16);
+#pragma unroll
+        for (int ks = 0; ks < kM / 16; ++ks)
+          tc::mma_f16(d, tc::smem_desc(a0 + ks * 2 * kA, kA, 128u), tc::smem_desc(b0 + ks * 2 * kB, kB, 128u), id,
+                      !(first && ks == 0));
+      };
+      uint32_t idle = 0;
+      while (active > 0) {
+        bool progressed = false;
+        for (int s = 0; s < SL; ++s) {
+          if (tile[s] >= n_tiles) continue;
+          const int ord = rnd[s] * SL + s;
+          if (st[s] > NH && turn[st[s] - NH - 1] != ord) continue;
+          if (!mbar_test(&ready[s], rph[s])) continue;
+          rph[s] ^= 1u;
+          if (st[s] > NH) turn[st[s] - NH - 1] = ord + 1;
+          tc::fence_after_sync();
+          unsigned char* b = sm + s * S::SLOT;
+          const uint32_t acc = tmem + 64u * (uint32_t)s;
+          const int k = st[s];
+          if (k == 0) {
+            issue_gemm(acc, b + S::X, sm + S::W0, N_IN, tc::idesc_f16(kM, kW, BF16));
+          } else if (k < NH) {
+            issue_gemm(acc, b + S::H + (k - 1) * kM * kW * 2, sm + S::WH + (k - 1) * kW * kW * 2, kW,
+                       tc::idesc_f16(kM, kW, BF16));
+          } else if (k == NH) {
+            issue_gemm(acc, b + S::H + (NH - 1) * kM * kW * 2, sm + S::WO, kW, tc::idesc_f16(kM, 16, BF16));
+          } else if (k == NH + 1) {
+            wgrad(tmem + S::C_OUT, b + S::H + (NH - 1) * kM * kW * 2, kH, b + S::DY, kDY, 16, first_out);
+            first_out = false;
+            issue_gemm(acc, b + S::DY, sm + S::WOT, 16, tc::idesc_f16(kM, kW, BF16));
+          } else if (k < 2 * NH + 1) {
+            const int h = 2 * NH + 1 - k;              // delta of layer h known; dW_h, then dH_{h-1}
+            wgrad(tmem + S::C_HID + 64u * (uint32_t)(h - 1), b + S::H + h * kM * kW * 2, kH,
+                  b + S::H + (h - 1) * kM * kW * 2, kH, kW, (first_h >> h) & 1u);
+            first_h &= ~(1u << h);
+            issue_gemm(acc, b + S::H + h * kM * kW * 2, sm + S::WHT + (h - 1) * kW * kW * 2, kW,
+                       tc::idesc_f16(kM, kW, BF16));
+          } else {
+            wgrad(tmem + S::C_FIRST, b + S::H, kH, b + S::X, kX, N_IN, first_0);
+            first_0 = false;
+            issue_gemm(acc, b + S::H, sm + S::W0T, kW, tc::idesc_f16(kM, N_IN, BF16));
+          }
+          tc::commit(&full[s]);
+          if (++st[s] == S::STAGES) {
+            st[s] = 0;
+            ++rnd[s];
+            tile[s] += stride;
+            active -= tile[s] >= n_tiles;
+          }
+          progressed = true;
+        }
+        if (progressed) {
+          idle = 0;
+        } else if (++idle > kWaitPolls || *abort_p) {
+          *abort_p = 1;
+          break;
+        }
+      }
+      tc::commit(&done);                               // arrives once every product has completed
+      if (!tc::mbar_wait(&done, 0, kWaitPolls)) *abort_p = 1;   // TMEM is freed only after this
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue warpgroup `slot`: warp q reads TMEM lanes 32 q .. 32 q + 31
+    const int slot = warp >> 2, q = warp & 3, r = q * 32 + lane;
+    unsigned char* b = sm + slot * S::SLOT;
+    const uint32_t lane_addr = tmem + 64u * (uint32_t)slot + ((uint32_t)(q * 32) << 16);
+    uint32_t fph = 0;
+    bool failed = false;
+    // the warpgroup's writes are made visible to the tensor cores (proxy fence), its TMEM reads are
+    // ordered before the barrier, and one thread arrives once all 128 have passed the named barrier
+    auto operands_ready = [&]() {
+      tc::fence_smem_async();
+      tc::fence_before_sync();
+      group_sync(1 + slot);
+      if (r == 0) mbar_arrive(&ready[slot]);
+    };
+    // every thread of the warpgroup takes the same branch (group_any is a barrier of the 128), so
+    // no thread can be left waiting at the warpgroup's named barrier for one that gave up
+    auto acc_full = [&]() -> bool {
+      const bool ok = mbar_wait_abort(&full[slot], fph, abort_p);
+      fph ^= 1u;
+      tc::fence_after_sync();
+      return !group_any(1 + slot, !ok);
+    };
+    constexpr int kPieces = N_IN / 8;
+    uint4 pf[kPieces];
+    auto prefetch = [&](int64_t t) {
+#pragma unroll
+      for (int j = 0; j < kPieces; ++j) {
+        const int i = r + 128 * j, rr = i / (N_IN / 8), c = (i % (N_IN / 8)) * 8;
+        const int64_t row = t * kM + rr;
+        pf[j] = (t < n_tiles && row < P) ? __ldg(reinterpret_cast<const uint4*>(in + row * N_IN + c))
+                                         : make_uint4(0, 0, 0, 0);
+      }
+    };
+    int tiles_here = 0;
+    prefetch((int64_t)blockIdx.x * SL + slot);
+    for (int64_t tile = (int64_t)blockIdx.x * SL + slot; tile < n_tiles && !failed; tile += stride) {
+      const int64_t row0 = tile * kM;
+#pragma unroll
+      for (int j = 0; j < kPieces; ++j) {
+        const int i = r + 128 * j, rr = i / (N_IN / 8), c = (i % (N_IN / 8)) * 8;
+        *reinterpret_cast<uint4*>(b + S::X + tc::cm_offset(rr, c, N_IN)) = pf[j];
+      }
+      operands_ready();                                // stage 0: the input tile
+      prefetch(tile + stride);
+      float yin[16];
+      {
+        const int64_t row = row0 + r;
+        const float* src = MODE == 0 ? dout : target;
+#pragma unroll
+        for (int o = 0; o < 16; ++o) yin[o] = (row < P && o < n_out) ? __ldg(src + row * n_out + o) : 0.f;
+      }
+      // ---- forward
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        if (!acc_full()) { failed = true; break; }
+#pragma unroll
+        for (int c0 = 0; c0 < kW; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            float u[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) u[j] = fmaxf(v[16 * half + j], 0.f);
+            store16<T>(b + S::H + h * kM * kW * 2, r, c0 + 16 * half, kW, u);
+          }
+        }
+        operands_ready();
+      }
+      if (failed || !acc_full()) { failed = true; break; }
+      // ---- output delta
+      {
+        float v[16];
+        tc::tmem_ld16(lane_addr, v);
+        const int64_t row = row0 + r;
+#pragma unroll
+        for (int o = 0; o < 16; ++o) {
+          float dyo = 0.f;
+          if (row < P && o < n_out) {
+            if (MODE == 0) {
+              dyo = yin[o] * loss_scale;
+            } else {
+              const float res = v[o] - yin[o];
+              sq = fmaf(res, res, sq);
+              dyo = res * inv_count * loss_scale;
+            }
+          }
+          v[o] = dyo;
+        }
+        store16<T>(b + S::DY, r, 0, 16, v);
+      }
+      operands_ready();
+      // ---- hidden deltas, top layer down, each written over its layer's activations
+#pragma unroll
+      for (int h = NH - 1; h >= 0; --h) {
+        if (!acc_full()) { failed = true; break; }
+#pragma unroll
+        for (int c0 = 0; c0 < kW; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            float a[16], u[16];
+            load16<T>(b + S::H + h * kM * kW * 2, r, c0 + 16 * half, kW, a);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) u[j] = a[j] > 0.f ? v[16 * half + j] : 0.f;
+            store16<T>(b + S::H + h * kM * kW * 2, r, c0 + 16 * half, kW, u);
+          }
+        }
+        operands_ready();
+      }
+      if (failed || !acc_full()) { failed = true; break; }
+      // ---- input gradient (the slot's buffers are free: every product of the tile has completed)
+      if (din && din_group == 0 && kM * (N_IN + 4) * 4 <= NH * kM * kW * 2) {
+        constexpr int LD = N_IN + 4;
+        float* stg = reinterpret_cast<float*>(b + S::H);
+#pragma unroll
+        for (int c0 = 0; c0 < N_IN; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(stg + r * LD + c0 + j) =
+                make_float4(v[j] * inv_scale, v[j + 1] * inv_scale, v[j + 2] * inv_scale, v[j + 3] * inv_scale);
+        }
+        group_sync(1 + slot);
+        for (int i = r; i < kM * (N_IN / 4); i += 128) {
+          const int rr = i / (N_IN / 4), c4 = i % (N_IN / 4);
+          if (row0 + rr < P)
+            *reinterpret_cast<float4*>(din + (row0 + rr) * N_IN + c4 * 4) =
+                *reinterpret_cast<const float4*>(stg + rr * LD + c4 * 4);
+        }
+        group_sync(1 + slot);                          // staging read before the next tile's H_0
+      } else {
+        const int64_t row = row0 + r;
+#pragma unroll
+        for (int c0 = 0; c0 < N_IN; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+          if (din && row < P) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+              const int col = c0 + j;
+              const float2 val = make_float2(v[j] * inv_scale, v[j + 1] * inv_scale);
+              if (din_group == 0) {
+                *reinterpret_cast<float2*>(din + row * N_IN + col) = val;
+              } else if (din_group == 1) {
+                din[(int64_t)col * P + row] = val.x;
+                din[(int64_t)(col + 1) * P + row] = val.y;
+              } else {
+                *reinterpret_cast<float2*>(din + ((int64_t)(col / din_group) * P + row) * din_group +
+                                           col % din_group) = val;
+              }
+            }
+          }
+        }
+      }
+      ++tiles_here;
+    }
+    if (failed) *abort_p = 1;
+    if (q == 0 && lane == 0 && tiles_here > 0) atomicAdd(&n_done_tiles, tiles_here);
+    if (MODE == 1) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) sq_part[warp] = sq;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const bool failed_cta = abort_word != 0;
+  if (failed_cta && tid == 0) atomicExch(&g_tc_error, 1);
+  // ---- this CTA's partials: the weight-gradient accumulators (row m of an M = 64 accumulator in
+  // TMEM lane 32 (m / 16) + m % 16, read by warps 0-3 from their lanes 0-15); zeros without a tile
+  float* wsb = ws + (int64_t)blockIdx.x * n_params;
+  const bool any = n_done_tiles > 0 && !failed_cta;
+  if (warp < 4) {
+    const int q = warp, off_h = kW * N_IN, off_o = off_h + (NH - 1) * kW * kW;
+    const int m = 16 * q + lane;
+    const uint32_t la = (uint32_t)(q * 32) << 16;
+    float v[16];
+    tc::tmem_ld16(tmem + S::C_OUT + la, v);
+    if (lane < 16)
+#pragma unroll
+      for (int o = 0; o < 16; ++o)
+        if (o < n_out) wsb[off_o + o * kW + m] = any ? v[o] : 0.f;
+#pragma unroll
+    for (int h = 1; h < NH; ++h)
+#pragma unroll
+      for (int c0 = 0; c0 < kW; c0 += 16) {
+        tc::tmem_ld16(tmem + S::C_HID + 64u * (h - 1) + la + (uint32_t)c0, v);
+        if (lane < 16)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) wsb[off_h + (h - 1) * kW * kW + m * kW + c0 + j] = any ? v[j] : 0.f;
+      }
+#pragma unroll
+    for (int c0 = 0; c0 < N_IN; c0 += 16) {
+      tc::tmem_ld16(tmem + S::C_FIRST + la + (uint32_t)c0, v);
+      if (lane < 16)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) wsb[m * N_IN + c0 + j] = any ? v[j] : 0.f;
+    }
+  }
+  if (MODE == 1 && tid == 0) {
+    float s = 0.f;
+    for (int w = 0; w < 4 * SL; ++w) s += sq_part[w];
+    ws[(int64_t)gridDim.x * n_params + blockIdx.x] = s;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
 }  // namespace
 }  // namespace sxe
 
@@ -863,6 +1284,52 @@ sxe_status tc2_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
   sxe_status st = check_launch("mlp_train_tc2");
   if (st != SXE_OK) return st;
   return launch_mlp_reduce(ws, 2 * g2, n_params, 1.f / ls, dW, target ? sq : nullptr, s);
+}
+
+// Warp-specialised kernel: one CTA per SM (its shared-memory plan takes the SM), SLOTS tiles per
+// CTA in flight; one partial row per CTA (the workspace holds `grid` rows).
+template <typename T, int N_IN, int NH>
+sxe_status ws_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                     float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid,
+                     cudaStream_t s) {
+  using S = WsSmem<N_IN, NH>;
+  const int64_t n_params = sxe_mlp_n_params(d);
+  const int64_t n_tiles = (P + kM - 1) / kM;
+  const int g = (int)std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)device_sm_count(), (int64_t)grid, (n_tiles + S::SLOTS - 1) / S::SLOTS}));
+  const float ic = l2_inv_count(P, d->n_out);
+  if (target) {
+    kernel_ctas_per_sm((const void*)mlp_train_ws_kernel<T, N_IN, NH, 1>, S::THREADS, S::END);
+    mlp_train_ws_kernel<T, N_IN, NH, 1><<<g, S::THREADS, S::END, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
+                                                                      target, ls, ic, din, dg, ws, n_params);
+  } else {
+    kernel_ctas_per_sm((const void*)mlp_train_ws_kernel<T, N_IN, NH, 0>, S::THREADS, S::END);
+    mlp_train_ws_kernel<T, N_IN, NH, 0><<<g, S::THREADS, S::END, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
+                                                                      target, ls, ic, din, dg, ws, n_params);
+  }
+  sxe_status st = check_launch("mlp_train_ws");
+  if (st != SXE_OK) return st;
+  return launch_mlp_reduce(ws, g, n_params, 1.f / ls, dW, target ? sq : nullptr, s);
+}
+
+template <typename T, int N_IN>
+sxe_status ws_nh(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+  switch (d->n_hidden) {
+    case 1: return ws_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    case 2: return ws_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    default: return ws_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+  }
+}
+
+template <typename T>
+sxe_status ws_in(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
+                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+  switch (d->n_in) {
+    case 16: return ws_nh<T, 16>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    case 32: return ws_nh<T, 32>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    default: return ws_nh<T, 64>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+  }
 }
 
 template <typename T, int N_IN, int NH>
@@ -916,6 +1383,14 @@ sxe_status launch_mlp_bwd_tc(const sxe_mlp_desc* d, const void* W, const void* i
   return d->dtype == SXE_F16
              ? tc_in<__half>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s)
              : tc_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s);
+}
+
+sxe_status launch_mlp_bwd_ws(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
+                             const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
+                             float* ws, int grid, cudaStream_t s, int din_group) {
+  return d->dtype == SXE_F16
+             ? ws_in<__half>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s)
+             : ws_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s);
 }
 
 // Whether the two-tile tcgen05 kernel runs this network (its shared-memory plan fits and the

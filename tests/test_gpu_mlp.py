@@ -90,13 +90,14 @@ def within(got, want, den, tol, slack=0.0):
     return float(np.max(err / np.maximum(bound, 1e-300)))
 
 
-@pytest.fixture(params=["mma_sync", "tcgen05"])
+@pytest.fixture(params=["mma_sync", "tcgen05", "tcgen05_pipelined"])
 def mlp_kernel(request, cuda_lib):
     """Run the test with the network's training pass on each kernel; afterwards no bounded
     device wait may have given up."""
     import ctypes
     L = cuda_lib
-    code = {"mma_sync": L.SXE_MLP_KERNEL_MMA_SYNC, "tcgen05": L.SXE_MLP_KERNEL_TCGEN05}[request.param]
+    code = {"mma_sync": L.SXE_MLP_KERNEL_MMA_SYNC, "tcgen05": L.SXE_MLP_KERNEL_TCGEN05,
+            "tcgen05_pipelined": L.SXE_MLP_KERNEL_TCGEN05_PIPELINED}[request.param]
     prev = L.lib().sxe_mlp_get_kernel()
     assert L.lib().sxe_mlp_set_kernel(code) == 0
     try:
@@ -294,7 +295,7 @@ def test_tcgen05_and_mma_sync_agree(cuda_lib, net):
     outs = {}
     prev = L.lib().sxe_mlp_get_kernel()
     try:
-        for k in (L.SXE_MLP_KERNEL_MMA_SYNC, L.SXE_MLP_KERNEL_TCGEN05):
+        for k in (L.SXE_MLP_KERNEL_MMA_SYNC, L.SXE_MLP_KERNEL_TCGEN05, L.SXE_MLP_KERNEL_TCGEN05_PIPELINED):
             assert L.lib().sxe_mlp_set_kernel(k) == 0
             dW = torch.zeros((mlp.n_params,), device="cuda")
             din = torch.empty((x.shape[0], net[0]), device="cuda")
@@ -307,10 +308,12 @@ def test_tcgen05_and_mma_sync_agree(cuda_lib, net):
     _, dW_den, din_den = _dens(Ws, x, dy.cpu().numpy().astype(np.float64))
     dW_sl, din_sl = flip_slack(Ws, x, dy.cpu().numpy().astype(np.float64), U[net[3]])
     tol = (2 * net[1] + 2) * U[net[3]]
-    a, b = outs[L.SXE_MLP_KERNEL_MMA_SYNC], outs[L.SXE_MLP_KERNEL_TCGEN05]
-    for i, (ga, gb) in enumerate(zip(mlp.split(a[0]), mlp.split(b[0]))):
-        assert within(gb, ga, dW_den[i], tol, 2 * dW_sl[i]) <= 1.0, "layer %d" % i
-    assert within(b[1], a[1], din_den, tol, 2 * din_sl) <= 1.0
+    a = outs[L.SXE_MLP_KERNEL_MMA_SYNC]
+    for k in (L.SXE_MLP_KERNEL_TCGEN05, L.SXE_MLP_KERNEL_TCGEN05_PIPELINED):
+        b = outs[k]
+        for i, (ga, gb) in enumerate(zip(mlp.split(a[0]), mlp.split(b[0]))):
+            assert within(gb, ga, dW_den[i], tol, 2 * dW_sl[i]) <= 1.0, "kernel %d layer %d" % (k, i)
+        assert within(b[1], a[1], din_den, tol, 2 * din_sl) <= 1.0
 
 
 def test_adam_touched_full_size_table(cuda_lib):
