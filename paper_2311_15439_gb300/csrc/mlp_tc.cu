@@ -950,6 +950,7 @@ mlp_train_ws_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P
       int64_t tile[SL];
       uint32_t rph[SL];
       int active = 0;
+#pragma unroll
       for (int s = 0; s < SL; ++s) {
         tile[s] = (int64_t)blockIdx.x * SL + s;
         st[s] = 0;
@@ -961,7 +962,10 @@ mlp_train_ws_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P
       // (ordinal rnd * SL + slot), one turn counter per stage, so that every TMEM accumulator sums
       // its tiles in the same order on every run: the partials, and dweights, are deterministic.
       // A tile only ever waits for lower ordinals, so the turns cannot deadlock.
+      // (every per-slot and per-stage array is indexed only inside fully unrolled loops, so the
+      // issuing thread's state stays in registers)
       int turn[NH + 1];
+#pragma unroll
       for (int j = 0; j <= NH; ++j) turn[j] = 0;
       bool first_out = true, first_0 = true;
       uint32_t first_h = (1u << NH) - 1u;
@@ -977,13 +981,21 @@ mlp_train_ws_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P
       uint32_t idle = 0;
       while (active > 0) {
         bool progressed = false;
+#pragma unroll
         for (int s = 0; s < SL; ++s) {
           if (tile[s] >= n_tiles) continue;
           const int ord = rnd[s] * SL + s;
-          if (st[s] > NH && turn[st[s] - NH - 1] != ord) continue;
+          const int j = st[s] - NH - 1;                // weight-gradient stage, or negative
+          int tj = ord;
+#pragma unroll
+          for (int jj = 0; jj <= NH; ++jj)
+            if (jj == j) tj = turn[jj];
+          if (tj != ord) continue;
           if (!mbar_test(&ready[s], rph[s])) continue;
           rph[s] ^= 1u;
-          if (st[s] > NH) turn[st[s] - NH - 1] = ord + 1;
+#pragma unroll
+          for (int jj = 0; jj <= NH; ++jj)
+            if (jj == j) turn[jj] = ord + 1;
           tc::fence_after_sync();
           unsigned char* b = sm + s * S::SLOT;
           const uint32_t acc = tmem + 64u * (uint32_t)s;
@@ -1124,22 +1136,19 @@ mlp_train_ws_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P
         store16<T>(b + S::DY, r, 0, 16, v);
       }
       operands_ready();
-      // ---- hidden deltas, top layer down, each written over its layer's activations
+      // ---- hidden deltas, top layer down, each written over its layer's activations (16 columns
+      // at a time: fewer live registers than 32)
 #pragma unroll
       for (int h = NH - 1; h >= 0; --h) {
         if (!acc_full()) { failed = true; break; }
 #pragma unroll
-        for (int c0 = 0; c0 < kW; c0 += 32) {
-          float v[32];
-          tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
+        for (int c0 = 0; c0 < kW; c0 += 16) {
+          float v[16], a[16];
+          tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
+          load16<T>(b + S::H + h * kM * kW * 2, r, c0, kW, a);
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            float a[16], u[16];
-            load16<T>(b + S::H + h * kM * kW * 2, r, c0 + 16 * half, kW, a);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) u[j] = a[j] > 0.f ? v[16 * half + j] : 0.f;
-            store16<T>(b + S::H + h * kM * kW * 2, r, c0 + 16 * half, kW, u);
-          }
+          for (int jj = 0; jj < 16; ++jj) v[jj] = a[jj] > 0.f ? v[jj] : 0.f;
+          store16<T>(b + S::H + h * kM * kW * 2, r, c0, kW, v);
         }
         operands_ready();
       }
