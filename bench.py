@@ -244,7 +244,7 @@ def run_gpu(args):
                "sxe_mlp_set_kernel")
     enc = Encoder(**CFG, kind=args.kind, table_dtype="f16")
     mlp = Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16")
-    tr = Trainer(enc, mlp, BATCH, seed=rank, device=dev, table_layout="records")
+    tr = Trainer(enc, mlp, BATCH, seed=rank, device=dev, table_layout="records", split_batch=args.split_batch)
     xs, ts = make_batches(N_POOL, seed0=1000 + 100 * rank)
     xd = [torch.from_numpy(x).to(dev) for x in xs]
     td = [torch.from_numpy(t).to(dev) for t in ts]
@@ -254,40 +254,27 @@ def run_gpu(args):
         tr.step(xd[i % N_POOL], td[i % N_POOL])
     torch.cuda.synchronize(dev)
 
-    # ---- device-timed region: K steps, per-stage events on the launching stream
+    # ---- device-timed region: K steps of Trainer.step; the trainer records an event before and
+    # after each stage on the stream that stage's kernels run on (the table backward of a split
+    # step on its second stream), from which each stage's time per step is summed
     names = ["encode_fwd", "mlp_train_l2", "encode_bwd", "adam_tables", "adam_mlp"]
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
-    F = enc.n_features
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tr.stage_events = {}
     with ClockSampler(local) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
         start.record(stream)
         for k in range(args.steps):
-            x, t = xd[k % N_POOL], td[k % N_POOL]
-            e = ev[k]
-            tr.t += 1
-            tr.adam_tables.advance(tr.t_dev, tr.corrections)
-            e[0].record(stream)
-            tr.enc.encode_fwd(x, tr.tables, tr.enc_out)
-            e[1].record(stream)
-            tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, t, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
-                                workspace=tr.ws)
-            e[2].record(stream)
-            tr.enc.encode_bwd(x, tr.d_enc, tr.state, grad_stride=4 * F, grad_offset=3 * F, touched=tr.touched)
-            e[3].record(stream)
-            tr.adam_tables.step_touched_dev(tr.corrections, tr.state, tr.touched, tr.tables, F)
-            e[4].record(stream)
-            tr.adam_mlp.step_dev(tr.corrections, tr.W, tr.mW, tr.vW, tr.dW, lowp=tr.W_lowp)
-            e[5].record(stream)
+            tr.step(xd[k % N_POOL], td[k % N_POOL])
         stop.record(stream)
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
+    ev, tr.stage_events = tr.stage_events, None
+    ev["adam_mlp"] = ev["adam_tables_end"]
+    per_kernel = {n: float(sum(a.elapsed_time(b) for a, b in zip(ev[n], ev[n + "_end"]))) / args.steps for n in names}
     ms = start.elapsed_time(stop)
-    per_kernel = {n: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)]))
-                  for i, n in enumerate(names)}
     ms = max_over_ranks(ms, world, dev)
     loss = tr.loss()
     n_touched, n_sectors = count_touched(tr, xd[0])
@@ -344,6 +331,7 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "kind": args.kind, "res_mode": "raw",
                        "step": "encode forward, network forward + L2 loss + backward, encode backward into the "
                                "table state, Adam on the touched table entries and on the network",
+                       "split_batch": tr.split,
                        "mlp_kernel": {"auto": "auto (two-tile tcgen05 kernel for this network)", "mma_sync": "mma_sync",
                                       "tcgen05": "tcgen05", "tcgen05_pipelined": "tcgen05_pipelined"}[args.mlp_kernel],
                        "global_batch": BATCH * world,
@@ -351,7 +339,7 @@ def run_gpu(args):
                        "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state records, no flush",
                        "batches": "%d resident distinct batches cycled" % N_POOL},
             "e2e": {"value": job_throughput(BATCH, e2e_steps, world, ms_e2e), "unit": "points/s",
-                    "h2d_bytes_per_step": BATCH * (2 + N_OUT) * 4, "d2h_bytes_per_step": 4,
+                    "h2d_bytes_per_step": BATCH * (2 + N_OUT) * 4, "d2h_bytes_per_step": 4 * tr.split,
                     "api": "trainer.HostFeed.step (double-buffered copies on a copy stream, recorded step "
                            "replayed, loss read one step behind)"},
             "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
@@ -1429,6 +1417,8 @@ def main():
     ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05", "tcgen05_pipelined"],
                     help="kernel of the network training pass")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--split-batch", type=int, default=1,
+                    help="parts of the step's batch: each part's table backward beside the next part's network pass")
     ap.add_argument("--quality-steps", type=int, default=5000,
                     help="training steps of the image quality runs (the SDF runs take 2/5 of it); 0 skips them")
     ap.add_argument("--profile-mlp", action="store_true",

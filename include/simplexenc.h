@@ -340,6 +340,18 @@ sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* desc, const void* weights, const
                             float* din, float* dweights, float* sq_sum,
                             void* workspace, int64_t workspace_bytes, void* stream);
 
+/* sxe_mlp_train_l2 on one part of a batch that is processed in several calls (the points of a
+ * step split so that one part's network pass can overlap another part's table backward, or the
+ * shard of one rank in data-parallel training): the upstream gradient is normalised by the whole
+ * batch, dy = 2 (y - target) / (batch_points * n_out), so that the parts' weight gradients,
+ * accumulated into the same dweights (+=), sum to the batch's; *sq_sum is overwritten with this
+ * part's sum of squared residuals.  SXE_EINVAL unless 1 <= n_points <= batch_points (n_points = 0
+ * enqueues nothing).  Other arguments as sxe_mlp_train_l2.  Sec. 6.1's L2 loss over the batch. */
+sxe_status sxe_mlp_train_l2_part(const sxe_mlp_desc* desc, const void* weights, const void* in,
+                                 const float* target, float loss_scale, int64_t n_points,
+                                 int64_t batch_points, float* din, float* dweights, float* sq_sum,
+                                 void* workspace, int64_t workspace_bytes, void* stream);
+
 /* sxe_mlp_train_l2 without a caller-provided workspace, for callers that cannot
  * allocate device memory: code running under another framework's allocator that owns
  * all device memory, real-time or embedded loops where an allocation may block or fail,

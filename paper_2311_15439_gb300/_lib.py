@@ -31,7 +31,7 @@ EXPORTS = (
     "sxe_adam_advance", "sxe_step_dev", "sxe_step_touched_dev",
     "sxe_mlp_n_params", "sxe_mlp_fwd", "sxe_mlp_bwd_workspace_bytes", "sxe_mlp_bwd", "sxe_mlp_train_l2",
     "sxe_loss_l2", "sxe_step", "sxe_step_touched", "sxe_last_error", "sxe_version",
-    "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped",
+    "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped", "sxe_mlp_train_l2_part",
     "sxe_mlp_set_kernel", "sxe_mlp_get_kernel", "sxe_device_error",
 )
 
@@ -96,6 +96,7 @@ def _declare(L):
         "sxe_step_touched": (i32, [A, i64, i64, i32, vp, vp, vp, i32, vp]),
         "sxe_mlp_train_l2_grouped": (i32, [M, vp, vp, vp, f32, i64, vp, i32, vp, vp, vp, i64, vp]),
         "sxe_mlp_train_l2_static": (i32, [M, vp, vp, vp, f32, i64, vp, vp, vp, vp]),
+        "sxe_mlp_train_l2_part": (i32, [M, vp, vp, vp, f32, i64, i64, vp, vp, vp, vp, i64, vp]),
         "sxe_mlp_set_kernel": (i32, [i32]),
         "sxe_mlp_get_kernel": (i32, []),
         "sxe_device_error": (i32, [ctypes.POINTER(i32), i32]),

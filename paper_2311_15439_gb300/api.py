@@ -273,6 +273,26 @@ class Mlp:
                                          _stream(stream)), "sxe_mlp_train_l2")
         return dW
 
+    def mlp_train_l2_part(self, W, x, target, dW, sq_sum, batch_points: int, din=None, loss_scale: float = 1.0,
+                          workspace=None, stream=None):
+        """``sxe_mlp_train_l2_part``: the L2 pass on one part (x, target) of a batch of ``batch_points``
+        points; the gradient is normalised by the whole batch and accumulated into dW."""
+        dt = torch_dtype(self.dtype)
+        P = x.shape[0]
+        _need(W, dt, "weights", (self.n_params,))
+        _need(x, dt, "in", (P, self.n_in))
+        _need(target, torch.float32, "target", (P, self.n_out))
+        _need(dW, torch.float32, "dweights", (self.n_params,))
+        _need(sq_sum, torch.float32, "sq_sum", (1,))
+        if din is not None:
+            _need(din, torch.float32, "din", (P, self.n_in))
+        ws = workspace if workspace is not None else self.workspace(P, x.device)
+        L.check(L.lib().sxe_mlp_train_l2_part(ctypes.byref(self.desc), _ptr(W), _ptr(x), _ptr(target),
+                                              float(loss_scale), P, int(batch_points), _ptr(din), _ptr(dW),
+                                              _ptr(sq_sum), _ptr(ws), ws.numel() * 4, _stream(stream)),
+                "sxe_mlp_train_l2_part")
+        return dW
+
     def mlp_train_l2_grouped(self, W, x, target, dW, sq_sum, din, din_group: int, loss_scale: float = 1.0,
                              workspace=None, stream=None):
         """``sxe_mlp_train_l2_grouped``: din written as [n_in / g, P, g]."""

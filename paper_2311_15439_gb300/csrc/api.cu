@@ -402,7 +402,8 @@ int64_t sxe_mlp_bwd_workspace_bytes(const sxe_mlp_desc* d, int64_t P) {
 
 static sxe_status mlp_bwd_common(const char* fn, const sxe_mlp_desc* d, const void* W, const void* in,
                                  const float* dout, const float* target, float loss_scale, int64_t P, float* din,
-                                 float* dW, float* sq_sum, void* ws, int64_t ws_bytes, void* stream) {
+                                 float* dW, float* sq_sum, void* ws, int64_t ws_bytes, void* stream,
+                                 int64_t loss_count = 0) {
   sxe_status st = check_mlp(fn, d);
   if (st != SXE_OK) return st;
   if (P < 0) return set_error(SXE_EINVAL, "%s: n_points < 0", fn);
@@ -414,7 +415,7 @@ static sxe_status mlp_bwd_common(const char* fn, const sxe_mlp_desc* d, const vo
   const int64_t need = sxe_mlp_bwd_workspace_bytes(d, P);
   if (ws_bytes < need) return set_error(SXE_ENOMEM, "%s: workspace %lld < %lld bytes", fn, (long long)ws_bytes, (long long)need);
   return launch_mlp_bwd(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, (float*)ws, mlp_grid_blocks(d, P),
-                        (cudaStream_t)stream);
+                        (cudaStream_t)stream, 0, loss_count);
 }
 
 sxe_status sxe_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, float loss_scale,
@@ -429,6 +430,17 @@ sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* d, const void* W, const void* in
   if (P > 0 && (!target || !sq_sum)) return set_error(SXE_EINVAL, "mlp_train_l2: NULL target or sq_sum");
   return mlp_bwd_common("mlp_train_l2", d, W, in, nullptr, target, loss_scale, P, din, dW, sq_sum, ws, ws_bytes,
                         stream);
+}
+
+sxe_status sxe_mlp_train_l2_part(const sxe_mlp_desc* d, const void* W, const void* in, const float* target,
+                                 float loss_scale, int64_t P, int64_t batch_points, float* din, float* dW,
+                                 float* sq_sum, void* ws, int64_t ws_bytes, void* stream) {
+  if (P > 0 && (!target || !sq_sum)) return set_error(SXE_EINVAL, "mlp_train_l2_part: NULL target or sq_sum");
+  if (batch_points < P || batch_points < 1)
+    return set_error(SXE_EINVAL, "mlp_train_l2_part: batch_points=%lld must be >= n_points=%lld and >= 1",
+                     (long long)batch_points, (long long)P);
+  return mlp_bwd_common("mlp_train_l2_part", d, W, in, nullptr, target, loss_scale, P, din, dW, sq_sum, ws, ws_bytes,
+                        stream, batch_points);
 }
 
 sxe_status sxe_mlp_train_l2_grouped(const sxe_mlp_desc* d, const void* W, const void* in, const float* target,

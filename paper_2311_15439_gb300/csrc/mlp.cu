@@ -721,7 +721,7 @@ sxe_status field_in(int n_in, int nhc, const void* Wd, const void* Wc, const voi
 template <typename T, int N_IN, int NH>
 sxe_status bwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
                       float loss_scale, int64_t P, float* din, float* dW, float* sq_sum, float* ws, int grid,
-                      cudaStream_t s, int din_group) {
+                      cudaStream_t s, int din_group, int64_t lc) {
   using S = Smem<N_IN, NH>;
   const size_t bytes = (size_t)S::BWD_END * sizeof(T);
   const int64_t n_params = sxe_mlp_n_params(d);
@@ -729,12 +729,12 @@ sxe_status bwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
     auto k = mlp_bwd_kernel<T, N_IN, NH, 1>;
     kernel_ctas_per_sm((const void*)k, kThreads, (int)bytes);
     k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale,
-                                    l2_inv_count(P, d->n_out), din, ws, n_params, sq_sum, din_group);
+                                    l2_inv_count(lc, d->n_out), din, ws, n_params, sq_sum, din_group);
   } else {
     auto k = mlp_bwd_kernel<T, N_IN, NH, 0>;
     kernel_ctas_per_sm((const void*)k, kThreads, (int)bytes);
     k<<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout, target, loss_scale,
-                                    l2_inv_count(P, d->n_out), din, ws, n_params, sq_sum, din_group);
+                                    l2_inv_count(lc, d->n_out), din, ws, n_params, sq_sum, din_group);
   }
   sxe_status st = check_launch("mlp_bwd");
   if (st != SXE_OK) return st;
@@ -759,20 +759,22 @@ sxe_status fwd_in(const sxe_mlp_desc* d, const void* W, const void* in, int64_t 
 }
 template <typename T, int N_IN>
 sxe_status bwd_nh(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int dg) {
+                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int dg,
+                  int64_t lc) {
   switch (d->n_hidden) {
-    case 1: return bwd_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
-    case 2: return bwd_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
-    default: return bwd_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
+    case 1: return bwd_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg, lc);
+    case 2: return bwd_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg, lc);
+    default: return bwd_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg, lc);
   }
 }
 template <typename T>
 sxe_status bwd_in(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int dg) {
+                  float ls, int64_t P, float* din, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int dg,
+                  int64_t lc) {
   switch (d->n_in) {
-    case 16: return bwd_nh<T, 16>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
-    case 32: return bwd_nh<T, 32>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
-    default: return bwd_nh<T, 64>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg);
+    case 16: return bwd_nh<T, 16>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg, lc);
+    case 32: return bwd_nh<T, 32>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg, lc);
+    default: return bwd_nh<T, 64>(d, W, in, dout, target, ls, P, din, dW, sq, ws, grid, s, dg, lc);
   }
 }
 
@@ -820,16 +822,17 @@ sxe_status launch_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe
 
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                           const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
-                          float* ws, int grid, cudaStream_t s, int din_group) {
+                          float* ws, int grid, cudaStream_t s, int din_group, int64_t loss_count) {
+  const int64_t lc = loss_count > 0 ? loss_count : P;   // the L2 gradient's 2 / (count * n_out)
   // automatic choice: the two-tile tcgen05 kernel where it applies (measured faster than mma.sync:
   // 65.6 against 67.6 us per 2^18-point pass), mma.sync elsewhere
   if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_PIPELINED)
-    return launch_mlp_bwd_ws(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);
+    return launch_mlp_bwd_ws(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc);
   if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05 || (g_mlp_kernel == SXE_MLP_KERNEL_AUTO && mlp_tc2_applies(d, grid)))
-    return launch_mlp_bwd_tc(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);
+    return launch_mlp_bwd_tc(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc);
   return d->dtype == SXE_F16
-             ? bwd_in<__half>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group)
-             : bwd_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group);
+             ? bwd_in<__half>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc)
+             : bwd_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc);
 }
 
 }  // namespace sxe

@@ -1274,7 +1274,7 @@ constexpr int kMaxDynSmem = 227 * 1024;
 template <typename T, int N_IN, int NH>
 sxe_status tc2_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
                       float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, int sms,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t lc) {
   // at least 116 KB, so that one CTA (holding all 512 TMEM columns) runs per SM
   constexpr int bytes = Tc2Smem<N_IN, NH>::END > 116 * 1024 ? Tc2Smem<N_IN, NH>::END : 116 * 1024;
   const int64_t n_params = sxe_mlp_n_params(d);
@@ -1284,11 +1284,11 @@ sxe_status tc2_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
   kernel_ctas_per_sm((const void*)mlp_train_tc2_kernel<T, N_IN, NH, 1, true>, kThreads, bytes);
   if (target)
     mlp_train_tc2_kernel<T, N_IN, NH, 1, true><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out,
-                                                                          dout, target, ls, l2_inv_count(P, d->n_out),
+                                                                          dout, target, ls, l2_inv_count(lc, d->n_out),
                                                                           din, dg, ws, n_params);
   else
     mlp_train_tc2_kernel<T, N_IN, NH, 0, true><<<g2, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out,
-                                                                          dout, target, ls, l2_inv_count(P, d->n_out),
+                                                                          dout, target, ls, l2_inv_count(lc, d->n_out),
                                                                           din, dg, ws, n_params);
   sxe_status st = check_launch("mlp_train_tc2");
   if (st != SXE_OK) return st;
@@ -1300,13 +1300,13 @@ sxe_status tc2_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
 template <typename T, int N_IN, int NH>
 sxe_status ws_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
                      float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid,
-                     cudaStream_t s) {
+                     cudaStream_t s, int64_t lc) {
   using S = WsSmem<N_IN, NH>;
   const int64_t n_params = sxe_mlp_n_params(d);
   const int64_t n_tiles = (P + kM - 1) / kM;
   const int g = (int)std::max<int64_t>(
       1, std::min<int64_t>({(int64_t)device_sm_count(), (int64_t)grid, (n_tiles + S::SLOTS - 1) / S::SLOTS}));
-  const float ic = l2_inv_count(P, d->n_out);
+  const float ic = l2_inv_count(lc, d->n_out);
   if (target) {
     kernel_ctas_per_sm((const void*)mlp_train_ws_kernel<T, N_IN, NH, 1>, S::THREADS, S::END);
     mlp_train_ws_kernel<T, N_IN, NH, 1><<<g, S::THREADS, S::END, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
@@ -1323,41 +1323,42 @@ sxe_status ws_launch(const sxe_mlp_desc* d, const void* W, const void* in, const
 
 template <typename T, int N_IN>
 sxe_status ws_nh(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int64_t lc) {
   switch (d->n_hidden) {
-    case 1: return ws_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
-    case 2: return ws_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
-    default: return ws_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    case 1: return ws_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
+    case 2: return ws_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
+    default: return ws_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
   }
 }
 
 template <typename T>
 sxe_status ws_in(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int64_t lc) {
   switch (d->n_in) {
-    case 16: return ws_nh<T, 16>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
-    case 32: return ws_nh<T, 32>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
-    default: return ws_nh<T, 64>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    case 16: return ws_nh<T, 16>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
+    case 32: return ws_nh<T, 32>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
+    default: return ws_nh<T, 64>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
   }
 }
 
 template <typename T, int N_IN, int NH>
 sxe_status tc_launch(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                     float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+                     float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s,
+                     int64_t lc) {
   const int bytes = TcSmem<N_IN, NH>::END;
   const int64_t n_params = sxe_mlp_n_params(d);
   const int sms = device_sm_count();
   if constexpr (Tc2Smem<N_IN, NH>::END <= kMaxDynSmem) {
-    if (grid >= 2) return tc2_launch<T, N_IN, NH>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, sms, s);
+    if (grid >= 2) return tc2_launch<T, N_IN, NH>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, sms, s, lc);
   }
   if (target) {
     grid = std::min(grid, sms * tc_ctas_per_sm<T, N_IN, NH, 1>());
     mlp_train_tc_kernel<T, N_IN, NH, 1><<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
-                                                                     target, ls, l2_inv_count(P, d->n_out), din, dg, ws, n_params);
+                                                                     target, ls, l2_inv_count(lc, d->n_out), din, dg, ws, n_params);
   } else {
     grid = std::min(grid, sms * tc_ctas_per_sm<T, N_IN, NH, 0>());
     mlp_train_tc_kernel<T, N_IN, NH, 0><<<grid, kThreads, bytes, s>>>((const T*)W, (const T*)in, P, d->n_out, dout,
-                                                                     target, ls, l2_inv_count(P, d->n_out), din, dg, ws, n_params);
+                                                                     target, ls, l2_inv_count(lc, d->n_out), din, dg, ws, n_params);
   }
   sxe_status st = check_launch("mlp_train_tc");
   if (st != SXE_OK) return st;
@@ -1366,21 +1367,21 @@ sxe_status tc_launch(const sxe_mlp_desc* d, const void* W, const void* in, const
 
 template <typename T, int N_IN>
 sxe_status tc_nh(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int64_t lc) {
   switch (d->n_hidden) {
-    case 1: return tc_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
-    case 2: return tc_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
-    default: return tc_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    case 1: return tc_launch<T, N_IN, 1>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
+    case 2: return tc_launch<T, N_IN, 2>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
+    default: return tc_launch<T, N_IN, 3>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
   }
 }
 
 template <typename T>
 sxe_status tc_in(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout, const float* target,
-                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s) {
+                 float ls, int64_t P, float* din, int dg, float* dW, float* sq, float* ws, int grid, cudaStream_t s, int64_t lc) {
   switch (d->n_in) {
-    case 16: return tc_nh<T, 16>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
-    case 32: return tc_nh<T, 32>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
-    default: return tc_nh<T, 64>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s);
+    case 16: return tc_nh<T, 16>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
+    case 32: return tc_nh<T, 32>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
+    default: return tc_nh<T, 64>(d, W, in, dout, target, ls, P, din, dg, dW, sq, ws, grid, s, lc);
   }
 }
 
@@ -1388,18 +1389,18 @@ sxe_status tc_in(const sxe_mlp_desc* d, const void* W, const void* in, const flo
 
 sxe_status launch_mlp_bwd_tc(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                              const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
-                             float* ws, int grid, cudaStream_t s, int din_group) {
+                             float* ws, int grid, cudaStream_t s, int din_group, int64_t lc) {
   return d->dtype == SXE_F16
-             ? tc_in<__half>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s)
-             : tc_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s);
+             ? tc_in<__half>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s, lc)
+             : tc_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s, lc);
 }
 
 sxe_status launch_mlp_bwd_ws(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                              const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
-                             float* ws, int grid, cudaStream_t s, int din_group) {
+                             float* ws, int grid, cudaStream_t s, int din_group, int64_t lc) {
   return d->dtype == SXE_F16
-             ? ws_in<__half>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s)
-             : ws_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s);
+             ? ws_in<__half>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s, lc)
+             : ws_in<__nv_bfloat16>(d, W, in, dout, target, loss_scale, P, din, din_group, dW, sq_sum, ws, grid, s, lc);
 }
 
 // Whether the two-tile tcgen05 kernel runs this network (its shared-memory plan fits and the

@@ -74,13 +74,16 @@ sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, 
                           void* act, cudaStream_t s);
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                           const float* target, float loss_scale, int64_t P, float* din, float* dW,
-                          float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group = 0);
+                          float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group = 0,
+                          int64_t loss_count = 0);   // 0: the L2 gradient is normalised by P
 sxe_status launch_mlp_bwd_tc(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                              const float* target, float loss_scale, int64_t P, float* din, float* dW,
-                             float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group);
+                             float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group,
+                             int64_t loss_count);
 sxe_status launch_mlp_bwd_ws(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                              const float* target, float loss_scale, int64_t P, float* din, float* dW,
-                             float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group);
+                             float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group,
+                             int64_t loss_count);
 bool mlp_tc2_applies(const sxe_mlp_desc* d, int grid);
 sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
                              cudaStream_t s);

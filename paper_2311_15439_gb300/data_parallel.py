@@ -78,7 +78,7 @@ class DataParallelTrainer:
         self.flat = torch.zeros((n_tab + n_w + 1,), dtype=torch.float32, device=tr.device)
         tr.tab.grad = self.flat[:n_tab]
         tr.dW = self.flat[n_tab:n_tab + n_w]
-        tr.sq_sum = self.flat[n_tab + n_w:]
+        tr.sq_sum = tr.sq_parts = self.flat[n_tab + n_w:]
         self.group = group
         self.world = dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
         self._step = DataParallelStep(self.flat, self._local, self._apply, group)

@@ -165,7 +165,7 @@ def default_loss_scale(P: int, n_out: int) -> float:
 class Trainer:
     def __init__(self, encoder: Encoder, mlp: Mlp, batch: int, *, seed: int = 0, device="cuda",
                  table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15,
-                 table_chunks: int = 1, table_layout: str = "auto", split_coarse="auto"):
+                 table_chunks: int = 1, table_layout: str = "auto", split_coarse="auto", split_batch: int = 1):
         if mlp.n_in != encoder.n_out:
             raise ValueError("network input %d != encoding width %d" % (mlp.n_in, encoder.n_out))
         self.enc, self.mlp, self.P = encoder, mlp, batch
@@ -186,7 +186,11 @@ class Trainer:
         self.dW = torch.zeros_like(W0)
         self.enc_out = torch.empty((batch, encoder.n_out), dtype=torch_dtype(encoder.out_dtype), device=self.device)
         self.d_enc = torch.empty((batch, encoder.n_out), dtype=torch.float32, device=self.device)
-        self.sq_sum = torch.zeros((1,), dtype=torch.float32, device=self.device)
+        # the batch's sum of squared residuals, one entry per part of a split step (sq_sum: the first)
+        self.split = max(1, int(split_batch))
+        self.sq_parts = torch.zeros((self.split,), dtype=torch.float32, device=self.device)
+        self.sq_sum = self.sq_parts[:1]
+        self.stage_events = None
         self.ws = mlp.workspace(batch, self.device)
         self.loss_scale = default_loss_scale(batch, mlp.n_out)
         self.adam_tables = Adam(lr, betas[0], betas[1], eps, skip_zero_grad=True)
@@ -196,6 +200,12 @@ class Trainer:
         self.corrections = torch.zeros((2,), dtype=torch.float32, device=self.device)
         self.graph = None
         self.set_table_chunks(table_chunks)
+        if self.split > 1:
+            if len(self.chunks) > 1:
+                raise ValueError("split_batch and table_chunks > 1 cannot be combined")
+            self._bwd_stream = torch.cuda.Stream(device=self.device)
+            self._part_ready = [torch.cuda.Event() for _ in range(self.split)]
+            self._bwd_done = torch.cuda.Event()
 
     def set_table_chunks(self, k: int) -> None:
         """Run the table backward and the table Adam in k level ranges: the Adam of range i runs on
@@ -215,25 +225,87 @@ class Trainer:
         # the device step counter, encode_fwd, network training + its partial reduction, encode_bwd
         # per level range (coarse levels in shared memory, then the rest), table Adam per range,
         # network Adam
+        if self.split > 1:
+            bwd = sum(self.enc.bwd_kernel_count(b - a) for a, b in self.parts())
+            return 4 + 2 * self.split + bwd
         bwd = sum(self.enc.bwd_kernel_count(self.P, levels=c) for c in self.chunks)
         return 5 + bwd + len(self.chunks)
 
+    def parts(self):
+        """Row ranges of the parts of a split step (the whole batch when it is not split)."""
+        cut = [i * self.P // self.split for i in range(self.split + 1)]
+        return [(cut[i], cut[i + 1]) for i in range(self.split)]
+
+    def _mark(self, name, stream):
+        """Record a timing event on `stream` when ``stage_events`` (a dict name -> list) is set."""
+        if self.stage_events is not None:
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            self.stage_events.setdefault(name, []).append(ev)
+
     def step(self, x: torch.Tensor, target: torch.Tensor, stream=None) -> None:
         """One optimisation step on batch (x [P, d] float32, target [P, n_out] float32); asynchronous."""
+        if self.split > 1:
+            self._step_split(x, target, stream)
+            return
         self.t += 1
+        main = torch.cuda.current_stream(self.device) if stream is None else stream
         self.adam_tables.advance(self.t_dev, self.corrections, stream=stream)
+        self._mark("encode_fwd", main)
         self.enc.encode_fwd(x, self.tables, self.enc_out, stream=stream)
+        self._mark("encode_fwd_end", main)
+        self._mark("mlp_train_l2", main)
         self.mlp.mlp_train_l2(self.W_lowp, self.enc_out, target, self.dW, self.sq_sum, din=self.d_enc,
                               loss_scale=self.loss_scale, workspace=self.ws, stream=stream)
+        self._mark("mlp_train_l2_end", main)
         if len(self.chunks) == 1:
+            self._mark("encode_bwd", main)
             self.tab.backward(x, self.d_enc, stream=stream)
+            self._mark("encode_bwd_end", main)
+            self._mark("adam_tables", main)
             self.tab.adam(self.adam_tables, self.corrections, stream=stream)
+            self._mark("adam_tables_end", main)
         else:
             self._table_step_overlapped(x, stream)
         self.adam_mlp.step_dev(self.corrections, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=stream)
+        self._mark("adam_mlp_end", main)
         if len(self.chunks) > 1:
             main = torch.cuda.current_stream(self.device) if stream is None else stream
             main.wait_event(self._joined)
+
+    def _step_split(self, x, target, stream) -> None:
+        """The step with the batch in ``split`` parts: the encoding forward of the whole batch, then
+        per part the network pass (``sxe_mlp_train_l2_part``, normalised by the whole batch) on the
+        step's stream and that part's table backward on a second stream, so that a part's backward
+        (random reductions, waiting on memory) runs beside the next part's network pass (tensor
+        cores, waiting on its product chain); then Adam on the tables and the network.  The table
+        gradient is the same sum of the same terms as the unsplit step's (atomic additions in
+        another order); the network gradient sums the parts' partials."""
+        main = torch.cuda.current_stream(self.device) if stream is None else stream
+        side = self._bwd_stream
+        self.t += 1
+        self.adam_tables.advance(self.t_dev, self.corrections, stream=main)
+        self._mark("encode_fwd", main)
+        self.enc.encode_fwd(x, self.tables, self.enc_out, stream=main)
+        self._mark("encode_fwd_end", main)
+        for i, (a, b) in enumerate(self.parts()):
+            self._mark("mlp_train_l2", main)
+            self.mlp.mlp_train_l2_part(self.W_lowp, self.enc_out[a:b], target[a:b], self.dW, self.sq_parts[i:i + 1],
+                                       self.P, din=self.d_enc[a:b], loss_scale=self.loss_scale, workspace=self.ws,
+                                       stream=main)
+            self._mark("mlp_train_l2_end", main)
+            self._part_ready[i].record(main)
+            side.wait_event(self._part_ready[i])
+            self._mark("encode_bwd", side)
+            self.tab.backward(x[a:b], self.d_enc[a:b], stream=side)
+            self._mark("encode_bwd_end", side)
+        self._bwd_done.record(side)
+        main.wait_event(self._bwd_done)
+        self._mark("adam_tables", main)
+        self.tab.adam(self.adam_tables, self.corrections, stream=main)
+        self._mark("adam_tables_end", main)
+        self.adam_mlp.step_dev(self.corrections, self.W, self.mW, self.vW, self.dW, lowp=self.W_lowp, stream=main)
+        self._mark("adam_mlp_end", main)
 
     def _table_step_overlapped(self, x, stream) -> None:
         F, T = self.enc.n_features, self.enc.T
@@ -271,7 +343,7 @@ class Trainer:
 
     def loss(self) -> float:
         """Mean squared error of the last step (synchronises)."""
-        return float(self.sq_sum.item()) / (self.P * self.mlp.n_out)
+        return float(self.sq_parts.sum().item()) / (self.P * self.mlp.n_out)
 
     def table_params(self) -> torch.Tensor:
         """binary32 master table parameters as [L, T, F]."""
@@ -310,7 +382,7 @@ class HostFeed:
         self._ready = [torch.cuda.Event() for _ in range(2)]
         self._free = [torch.cuda.Event() for _ in range(2)]
         self._done = [torch.cuda.Event() for _ in range(2)]
-        self._loss = torch.zeros((2,), dtype=torch.float32).pin_memory()
+        self._loss = torch.zeros((2, tr.split), dtype=torch.float32).pin_memory()   # per pair: the parts' sums
         self._scale = 1.0 / (tr.P * tr.mlp.n_out)
         self.k = 0
 
@@ -328,13 +400,13 @@ class HostFeed:
         self.tr.t += 1
         self.graphs[i].replay()
         self._free[i].record(main)
-        self._loss[i:i + 1].copy_(self.tr.sq_sum, non_blocking=True)
+        self._loss[i].copy_(self.tr.sq_parts, non_blocking=True)
         self._done[i].record(main)
         prev = None
         if self.k >= 1:
             j = 1 - i
             self._done[j].synchronize()
-            prev = float(self._loss[j]) * self._scale
+            prev = float(self._loss[j].sum()) * self._scale
         self.k += 1
         return prev
 
@@ -342,7 +414,7 @@ class HostFeed:
         """Waits for the last queued step and returns its loss."""
         j = (self.k - 1) % 2
         self._done[j].synchronize()
-        return float(self._loss[j]) * self._scale
+        return float(self._loss[j].sum()) * self._scale
 
 
 def _main(argv=None):

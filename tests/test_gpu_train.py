@@ -352,6 +352,50 @@ def test_overlapped_table_step_equals_plain_step(k):
 
 
 @pytest.mark.parametrize("layout", ["records", "dense"])
+def test_split_batch_step_equals_plain_step(layout):
+    """The step in two parts (each part's network pass normalised by the whole batch, each part's
+    table backward on a second stream beside the next part's network pass) trains like the plain
+    step: the same loss, and parameters equal up to the order of the binary32 atomics and of the
+    network gradient's partial sums, eagerly and replayed from a CUDA graph; the end-to-end feed
+    reads both parts' losses."""
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import HostFeed, Trainer
+    P = 4096 + 128
+    mk = lambda split: Trainer(Encoder(**CFG, table_dtype="f16"), Mlp(16, 3, n_hidden=2, dtype="f16"), P, seed=14,
+                               table_layout=layout, split_batch=split)
+    a, b = mk(1), mk(2)
+    assert b.parts() == [(0, P // 2), (P // 2, P)]
+    img = synth.ProceduralImage(4, size=1024, n_waves=4)
+    batches = []
+    for i in range(6):
+        x = synth.uniform_points(P, 2, 90 + i)
+        batches.append((torch.from_numpy(x).cuda(), torch.from_numpy(img.sample(x)).cuda()))
+    for x, t in batches[:3]:
+        a.step(x, t)
+        b.step(x, t)
+        assert abs(a.loss() - b.loss()) <= 1e-5 * a.loss()
+    torch.cuda.synchronize()
+    _close_up_to_atomics(a.W, b.W, steps=3, atol=1e-5)
+    _close_up_to_atomics(a.table_params(), b.table_params(), steps=3)
+    bx, bt = torch.empty_like(batches[0][0]), torch.empty_like(batches[0][1])
+    bx.copy_(batches[3][0]); bt.copy_(batches[3][1])
+    b.capture(bx, bt, warmup=1)
+    a.step(*batches[3])
+    a.step(*batches[4])
+    bx.copy_(batches[4][0]); bt.copy_(batches[4][1])
+    b.replay()
+    torch.cuda.synchronize()
+    assert a.t == b.t == 5
+    assert abs(a.loss() - b.loss()) <= 1e-5 * a.loss()
+    _close_up_to_atomics(a.W, b.W, steps=5, atol=1e-5)
+    _close_up_to_atomics(a.table_params(), b.table_params(), steps=5)
+    feed = HostFeed(b, (batches[5][0].cpu().pin_memory(), batches[5][1].cpu().pin_memory()), warmup=0)
+    assert feed.step(batches[5][0].cpu().pin_memory(), batches[5][1].cpu().pin_memory()) is None
+    last = feed.finish()
+    assert np.isfinite(last) and last > 0
+
+
+@pytest.mark.parametrize("layout", ["records", "dense"])
 def test_coarse_levels_on_a_second_stream_equal_plain_step(layout):
     """The backward of the levels summed in shared memory on a second stream, concurrently with
     the other levels, gives the one-stream step's parameters (equal up to the order of the
