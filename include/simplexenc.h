@@ -345,8 +345,8 @@ sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* desc, const void* weights, const
  * shard of one rank in data-parallel training): the upstream gradient is normalised by the whole
  * batch, dy = 2 (y - target) / (batch_points * n_out), so that the parts' weight gradients,
  * accumulated into the same dweights (+=), sum to the batch's; *sq_sum is overwritten with this
- * part's sum of squared residuals.  SXE_EINVAL unless 1 <= n_points <= batch_points (n_points = 0
- * enqueues nothing).  Other arguments as sxe_mlp_train_l2.  Sec. 6.1's L2 loss over the batch. */
+ * part's sum of squared residuals.  SXE_EINVAL if n_points > batch_points; n_points = 0 enqueues
+ * nothing.  Other arguments as sxe_mlp_train_l2.  Sec. 6.1's L2 loss over the batch. */
 sxe_status sxe_mlp_train_l2_part(const sxe_mlp_desc* desc, const void* weights, const void* in,
                                  const float* target, float loss_scale, int64_t n_points,
                                  int64_t batch_points, float* din, float* dweights, float* sq_sum,

@@ -436,8 +436,8 @@ sxe_status sxe_mlp_train_l2_part(const sxe_mlp_desc* d, const void* W, const voi
                                  float loss_scale, int64_t P, int64_t batch_points, float* din, float* dW,
                                  float* sq_sum, void* ws, int64_t ws_bytes, void* stream) {
   if (P > 0 && (!target || !sq_sum)) return set_error(SXE_EINVAL, "mlp_train_l2_part: NULL target or sq_sum");
-  if (batch_points < P || batch_points < 1)
-    return set_error(SXE_EINVAL, "mlp_train_l2_part: batch_points=%lld must be >= n_points=%lld and >= 1",
+  if (P > 0 && batch_points < P)
+    return set_error(SXE_EINVAL, "mlp_train_l2_part: batch_points=%lld must be >= n_points=%lld",
                      (long long)batch_points, (long long)P);
   return mlp_bwd_common("mlp_train_l2_part", d, W, in, nullptr, target, loss_scale, P, din, dW, sq_sum, ws, ws_bytes,
                         stream, batch_points);
