@@ -23,7 +23,9 @@ backward passes are pinned by adjointness and by exact finite differences
 (both encodings are linear in the tables).  The input gradients
 (``simplex_encode_dx`` / ``grid_encode_dx``) are pinned by the exact gradient of
 affine (simplex) and multilinear (grid) fields and by central differences of the
-forward pass inside one cell.
+forward pass inside one cell.  ``simplex_encode_fp64`` / ``grid_encode_fp64`` evaluate the level
+scaling and skew in FP64 from x (no binary32 step): pinned by the same affine / multilinear
+exactness and by agreement with the binary32-conditioned paths within the quantisation bound.
 """
 from __future__ import annotations
 
@@ -79,6 +81,30 @@ def simplex_encode(x32, tables, *, base_res, growth, res_mode=lattice.RES_RAW, w
         out[:, l * F:(l + 1) * F] = np.einsum("pk,pkf->pf", w, H)      # (c) interpolate, (d) concat
         den[:, l * F:(l + 1) * F] = np.einsum("pk,pkf->pf", np.abs(w), np.abs(H))
     return (out, den) if with_denominator else out
+
+
+def simplex_encode_fp64(x, tables, *, base_res, growth, res_mode=lattice.RES_RAW):
+    """The forward simplex encoding with the level scale and the skew of Eq. 2 evaluated in FP64
+    from x (FP64 multipliers N_l m / sqrt(n+1)), instead of from the binary32 skewed coordinate
+    ``simplex_encode`` conditions on; hashed levels only.  Everything else is ``simplex_encode``'s.
+
+    Its difference from ``simplex_encode`` is the binary32 quantisation of the skewed coordinate
+    (reported beside the parity results, not a parity gate), and it is an exactly piecewise-linear
+    function of x, so that its central differences give the input gradient in FP64.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    P, n = x.shape
+    L, T, F = tables.shape
+    log2_T = int(T).bit_length() - 1
+    scales = lattice.simplex_level_scales_fp64(n, L, base_res, growth, res_mode)
+    out = np.zeros((P, L * F), dtype=np.float64)
+    for l in range(L):
+        q = lattice.skew(x * scales[l])
+        c, order, f = lattice.subdivide(q)
+        slots = lattice.slot_of(lattice.simplex_vertices(c, order), log2_T)
+        w = lattice.barycentric_weights(f, order)
+        out[:, l * F:(l + 1) * F] = np.einsum("pk,pkf->pf", w, np.asarray(tables[l], dtype=np.float64)[slots])
+    return out
 
 
 def simplex_encode_bwd(x32, dout, *, n_levels, log2_T, n_features, base_res, growth,
@@ -210,6 +236,26 @@ def grid_encode(x32, tables, *, base_res, growth, index_mode=lattice.INDEX_HASH)
             v1 = np.take(vals, 1, axis=1 + i)
             vals = v0 * (1.0 - t) + v1 * t
         out[:, l * F:(l + 1) * F] = vals.reshape(P, F)
+    return out
+
+
+def grid_encode_fp64(x, tables, *, base_res, growth):
+    """``grid_encode`` with p = x N_l in FP64 (instead of binary32), hashed levels only: the
+    comparator's FP64 forward, exactly multilinear in x inside a cell (see ``simplex_encode_fp64``)."""
+    x = np.asarray(x, dtype=np.float64)
+    P, n = x.shape
+    L, T, F = tables.shape
+    log2_T = int(T).bit_length() - 1
+    res = lattice.level_resolutions(L, base_res, growth)
+    offs = _corner_offsets(n)
+    out = np.zeros((P, L * F), dtype=np.float64)
+    for l in range(L):
+        p = x * float(res[l])
+        c = np.floor(p)
+        f = p - c
+        corners = c.astype(np.int64)[:, None, :] + offs[None, :, :]
+        vals = np.asarray(tables[l], dtype=np.float64)[lattice.slot_of(corners, log2_T)]
+        out[:, l * F:(l + 1) * F] = np.einsum("pk,pkf->pf", grid_level_corner_weights(f), vals)
     return out
 
 

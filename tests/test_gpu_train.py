@@ -172,6 +172,23 @@ def test_autograd_encoding_matches_oracle_and_fd():
         Hm[l, s, f] -= 0.5
         fd = ((enc.encode_fwd(xd, Hp) * Dt).double().sum() - (enc.encode_fwd(xd, Hm) * Dt).double().sum()).item()
         assert abs(fd - g[l, s, f]) <= 1e-4 * max(1.0, den[l][s, f])
+    # FP64 finite differences of the oracle's forward (exact up to FP64 rounding: the encoding is
+    # linear in the tables): the library's table gradient within 1e-4 of the sum of |w D| per entry
+    n_fd = 0
+    for _ in range(12):
+        l, s, f = int(rng.integers(6)), int(rng.integers(1 << 12)), int(rng.integers(2))
+        if den[l][s, f] == 0:
+            continue
+        Hp, Hm = vals.astype(np.float64), vals.astype(np.float64)
+        Hp[l, s, f] += 0.5
+        Hm[l, s, f] -= 0.5
+        fd64 = (np.sum(OE.simplex_encode(x, Hp, base_res=8.0, growth=1.5) * D)
+                - np.sum(OE.simplex_encode(x, Hm, base_res=8.0, growth=1.5) * D))
+        e = abs(fd64 - g[l, s, f]) / den[l][s, f]
+        record_error("encode_bwd table gradient against FP64 finite differences", e, 1e-4, "sum_k |w_k dout| per entry")
+        assert e <= 1e-4
+        n_fd += 1
+    assert n_fd >= 3
 
 
 @pytest.mark.parametrize("kind", ["simplex", "grid"])
@@ -211,6 +228,31 @@ def test_autograd_input_gradient(kind):
         assert np.all(np.abs(fd - g[:, j])[ok] <= 2e-3 * den[ok, j] + 1e-12)
         n_checked += ok.sum()
     assert n_checked > 1000
+    # FP64 central differences of the oracle's FP64 forward (scale and skew in FP64, exactly
+    # piecewise linear in x) for points whose FP64 cells stay the same at x +- h
+    fwd64 = OE.simplex_encode_fp64 if kind == "simplex" else OE.grid_encode_fp64
+    x64, h64 = x.astype(np.float64), 1e-7
+    from test_oracle_encoding import _fp64_cells, _same_cells
+    cells = _fp64_cells(kind, x64, 3, 6, 8.0, 1.5, 12)
+    same32 = np.ones(len(x), dtype=bool)              # the binary32 coordinate picks the same cell
+    for c32, c64 in zip(_same_cells(kind, x, 3, 6, 8.0, 1.5, 12), cells):
+        same32 &= np.all(c32 == c64, axis=1)
+    n_fd = 0
+    for j in range(3):
+        xp, xm = x64.copy(), x64.copy()
+        xp[:, j] += h64
+        xm[:, j] -= h64
+        ok = same32.copy()
+        for xx in (xp, xm):
+            for c0, c1 in zip(cells, _fp64_cells(kind, xx, 3, 6, 8.0, 1.5, 12)):
+                ok &= np.all(c0 == c1, axis=1)
+        fd64 = ((fwd64(xp, vals, base_res=8.0, growth=1.5) - fwd64(xm, vals, base_res=8.0, growth=1.5)) * D).sum(1) / (2 * h64)
+        e = np.max(np.abs(fd64 - g[:, j])[ok] / (den[ok, j] + 1e-30))
+        record_error("encode_bwd_input dL/dx against FP64 finite differences (%s)" % kind, e, 1e-4,
+                     "sum of |terms| of each dL/dx_i")
+        assert e <= 1e-4
+        n_fd += ok.sum()
+    assert n_fd > 1000
 
 
 def test_autograd_mlp_matches_oracle():

@@ -9,9 +9,10 @@ from oracle import adam, encoding, lattice, mlp
 from paper_2311_15439_gb300 import synth
 
 
-def _collision_free_tables(kind, n, L, base, growth, log2_T, fn):
+def _collision_free_tables(kind, n, L, base, growth, log2_T, fn, fp32_scale=True):
     """Tables whose entry at each vertex of every level's lattice box holds fn(position in
-    the original unit-cube coordinates); asserts no two box vertices share a slot."""
+    the original unit-cube coordinates, through the binary32 level multiplier, or the FP64 one
+    with fp32_scale=False); asserts no two box vertices share a slot."""
     T = 1 << log2_T
     tables = np.zeros((L, T, 1))
     if kind == "simplex":
@@ -26,7 +27,7 @@ def _collision_free_tables(kind, n, L, base, growth, log2_T, fn):
         pos = box.astype(float)
         if kind == "simplex":
             pos = lattice.unskew(pos)
-        tables[l, slots, 0] = fn(pos / float(np.float32(scales[l])))
+        tables[l, slots, 0] = fn(pos / (float(np.float32(scales[l])) if fp32_scale else float(scales[l])))
     return tables
 
 
@@ -425,3 +426,95 @@ def test_dense_levels_reproduce_fields_with_a_small_table(kind, n):
         else:
             xs = (x * np.float32(scales[l])).astype(np.float64) / float(scales[l])
         np.testing.assert_allclose(out[:, l], fn(xs), rtol=0, atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# forward paths with the level scale and skew in FP64
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_fp64_paths_reproduce_affine_and_multilinear_fields(n):
+    """With the scale and skew in FP64 the simplex encoding returns a.x + b at the point itself
+    (not at a binary32 rounding of it), and the grid encoding prod_i (1 + c_i x_i)."""
+    g = synth.rng(240 + n)
+    a, b, cc = g.standard_normal(n), 0.4, g.standard_normal(n)
+    L, growth = 3, 1.5
+    base, log2_T = (4.0, 20) if n < 4 else (3.0, 22)
+    x = np.concatenate([synth.uniform_points(300, n, 241), synth.edge_points(n, 242, per_kind=4)]).astype(np.float64)
+    x[:50] += synth.rng(243).uniform(-1e-9, 1e-9, size=(50, n))       # off the binary32 grid
+    x = np.clip(x, 0.0, 1.0)
+    tab = _collision_free_tables("simplex", n, L, base, growth, log2_T, lambda p: p @ a + b, fp32_scale=False)
+    out = encoding.simplex_encode_fp64(x, tab, base_res=base, growth=growth)
+    for l in range(L):
+        np.testing.assert_allclose(out[:, l], x @ a + b, rtol=0, atol=1e-11)
+    fn = lambda p: np.prod(1.0 + cc * p, axis=-1)
+    tab = _collision_free_tables("grid", n, L, base, growth, log2_T, fn)
+    out = encoding.grid_encode_fp64(x, tab, base_res=base, growth=growth)
+    for l in range(L):
+        np.testing.assert_allclose(out[:, l], fn(x), rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("kind,n", [("simplex", 2), ("simplex", 3), ("simplex", 5), ("grid", 2), ("grid", 4)])
+def test_fp64_paths_agree_with_binary32_conditioned_paths(kind, n):
+    """On binary32 points the FP64 paths differ from the binary32-conditioned ones only by the
+    rounding of the scaled (skewed) coordinate: a few ulps of |q| times the interpolant's slope,
+    bounded by 2 max |H| per unit of q (continuity carries the bound across cell faces)."""
+    L, base, growth, log2_T, F = 4, 8.0, 1.5, 14, 2
+    tables = synth.uniform_tables(L, 1 << log2_T, F, 250 + n, scale=1.0)[0].astype(np.float64)
+    x = np.concatenate([synth.uniform_points(2000, n, 251 + n), synth.edge_points(n, 252, per_kind=8)])
+    if kind == "simplex":
+        a = encoding.simplex_encode(x, tables, base_res=base, growth=growth)
+        b = encoding.simplex_encode_fp64(x, tables, base_res=base, growth=growth)
+        top = np.array(lattice.simplex_level_scales_fp64(n, L, base, growth)) * (1 + n * lattice.skew_factor(n))
+    else:
+        a = encoding.grid_encode(x, tables, base_res=base, growth=growth)
+        b = encoding.grid_encode_fp64(x, tables, base_res=base, growth=growth)
+        top = np.array(lattice.level_resolutions(L, base, growth), dtype=float)
+    for l in range(L):
+        bound = (n + 2) * n * 2.0 ** -24 * top[l] * 2 * np.abs(tables[l]).max()
+        assert np.abs(a[:, l * F:(l + 1) * F] - b[:, l * F:(l + 1) * F]).max() <= bound
+    assert np.abs(a - b).max() > 0                       # the rounding is visible somewhere
+
+
+def _fp64_cells(kind, x, n, L, base, growth, log2_T):
+    """Per level, the sorted slot sets of the cell of each point under the FP64 scale and skew."""
+    out = []
+    if kind == "simplex":
+        for s in lattice.simplex_level_scales_fp64(n, L, base, growth):
+            c, order, _ = lattice.subdivide(lattice.skew(x * s))
+            out.append(np.sort(lattice.slot_of(lattice.simplex_vertices(c, order), log2_T), axis=1))
+    else:
+        offs = np.array(list(itertools.product((0, 1), repeat=n)), dtype=np.int64)
+        for N in lattice.level_resolutions(L, base, growth):
+            c = np.floor(x * float(N)).astype(np.int64)
+            out.append(lattice.slot_of(c[:, None, :] + offs[None], log2_T))
+    return out
+
+
+@pytest.mark.parametrize("kind,n", [("simplex", 2), ("simplex", 3), ("simplex", 4), ("grid", 2), ("grid", 3)])
+def test_fp64_central_differences_equal_the_input_gradient(kind, n):
+    """Central differences of the FP64 forward (h = 1e-7, exact on a linear piece up to FP64
+    rounding) equal the input-gradient formula wherever the point's cells do not change, within
+    1e-6 of the sum of the magnitudes of its terms (the formula uses the binary32 constants)."""
+    L, base, growth, log2_T, F = 3, 4.0, 1.5, 12, 2
+    tables = synth.uniform_tables(L, 1 << log2_T, F, 260 + n, scale=1.0)[0].astype(np.float64)
+    x = np.clip(synth.uniform_points(400, n, 261 + n), 0.01, 0.99).astype(np.float32)
+    dout = synth.normal_grads(len(x), L * F, 262).astype(np.float64)
+    fwd = encoding.simplex_encode_fp64 if kind == "simplex" else encoding.grid_encode_fp64
+    dxf = encoding.simplex_encode_dx if kind == "simplex" else encoding.grid_encode_dx
+    dx, den = dxf(x, tables, dout, base_res=base, growth=growth, with_denominator=True)
+    x64, h = x.astype(np.float64), 1e-7
+    cells = _fp64_cells(kind, x64, n, L, base, growth, log2_T)
+    checked = 0
+    for j in range(n):
+        xp, xm = x64.copy(), x64.copy()
+        xp[:, j] += h
+        xm[:, j] -= h
+        ok = np.ones(len(x), dtype=bool)
+        for xx in (xp, xm):
+            for c0, c1 in zip(cells, _fp64_cells(kind, xx, n, L, base, growth, log2_T)):
+                ok &= np.all(c0 == c1, axis=1)
+        fd = ((fwd(xp, tables, base_res=base, growth=growth) - fwd(xm, tables, base_res=base, growth=growth))
+              * dout).sum(axis=1) / (2.0 * h)
+        assert np.all(np.abs(fd - dx[:, j])[ok] <= 1e-6 * den[ok, j] + 1e-12)
+        checked += ok.sum()
+    assert checked > 300 * n

@@ -105,6 +105,19 @@ CASES = {
                                           "grid_level_cell(x32, res[0])",
                                           [P(TE.test_grid_reproduces_multilinear_fields, 3),
                                            P(TE.test_backward_is_adjoint_of_forward, "grid", 3)]),
+    # the FP64 forward paths (scale and skew in FP64)
+    "FP64 path without the skew": (encoding, "simplex_encode_fp64", "q = lattice.skew(x * scales[l])",
+                                   "q = x * scales[l]",
+                                   [P(TE.test_fp64_paths_reproduce_affine_and_multilinear_fields, 2),
+                                    P(TE.test_fp64_paths_agree_with_binary32_conditioned_paths, "simplex", 2)]),
+    "FP64 path at the next level's scale": (encoding, "simplex_encode_fp64", "x * scales[l]",
+                                            "x * scales[min(l + 1, L - 1)]",
+                                            [P(TE.test_fp64_paths_reproduce_affine_and_multilinear_fields, 3),
+                                             P(TE.test_fp64_paths_agree_with_binary32_conditioned_paths, "simplex", 3)]),
+    "FP64 grid weights of the floor's complement": (encoding, "grid_encode_fp64", "f = p - c", "f = 1.0 - (p - c)",
+                                                    [P(TE.test_fp64_paths_reproduce_affine_and_multilinear_fields, 2),
+                                                     P(TE.test_fp64_central_differences_equal_the_input_gradient,
+                                                       "grid", 2)]),
     "grid backward reversed corners": (encoding, "grid_encode_bwd", "w[:, :, None] * dout",
                                        "w[:, ::-1, None] * dout",
                                        [P(TE.test_backward_is_adjoint_of_forward, "grid", 3)]),
