@@ -131,6 +131,15 @@ sxe_status sxe_encoder_set_bwd_aggregation(sxe_encoder* enc, int32_t on);
 sxe_status sxe_encode_fwd(const sxe_encoder* enc, const float* x, int64_t n_points,
                           const void* tables, void* out, void* stream);
 
+/* sxe_encode_fwd that also sets, in the bitmap `touched` (L*T bits, the layout of
+ * sxe_encode_bwd's), the bit of every table entry it reads: for the same points these are exactly
+ * the entries whose gradient the backward pass adds to (Sec. 5 step (e) scatters into the entries
+ * step (b) looked up), so a training step can mark them here and call the backward with touched =
+ * NULL.  Bits are only set, never cleared.  Same arguments and errors as sxe_encode_fwd, plus
+ * SXE_EINVAL for a NULL touched when n_points > 0. */
+sxe_status sxe_encode_fwd_marked(const sxe_encoder* enc, const float* x, int64_t n_points,
+                                 const void* tables, void* out, uint32_t* touched, void* stream);
+
 /* Backward encoding, Sec. 5 step (e): for every point, level, vertex k and feature f,
  *   grad[(l*T + slot_k) * grad_stride + f] += w_k * dout[p][l*F + f]
  * with the same vertices and weights as the forward pass (recomputed).

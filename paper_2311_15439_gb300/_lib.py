@@ -23,7 +23,7 @@ SXE_MLP_KERNEL_AUTO, SXE_MLP_KERNEL_MMA_SYNC, SXE_MLP_KERNEL_TCGEN05, SXE_MLP_KE
 EXPORTS = (
     "sxe_encoder_create", "sxe_encoder_destroy", "sxe_encoder_level_params", "sxe_encoder_level_index",
     "sxe_encoder_set_bwd_aggregation",
-    "sxe_encode_fwd", "sxe_encode_bwd", "sxe_encode_bwd_levels", "sxe_encode_bwd_kernel_count",
+    "sxe_encode_fwd", "sxe_encode_fwd_marked", "sxe_encode_bwd", "sxe_encode_bwd_levels", "sxe_encode_bwd_kernel_count",
     "sxe_encode_bwd_levels_kernel_count", "sxe_encode_bwd_coarse_levels", "sxe_encode_bwd_input",
     "sxe_encode_vertices",
     "sxe_encode_plain_fwd", "sxe_encode_plain_bwd", "sxe_vr_samples", "sxe_vr_field", "sxe_vr_field_mlp", "sxe_vr_composite",
@@ -68,6 +68,7 @@ def _declare(L):
         "sxe_encoder_level_index": (i32, [vp, vp]),
         "sxe_encoder_set_bwd_aggregation": (i32, [vp, i32]),
         "sxe_encode_fwd": (i32, [vp, vp, i64, vp, vp, vp]),
+        "sxe_encode_fwd_marked": (i32, [vp, vp, i64, vp, vp, vp, vp]),
         "sxe_encode_bwd": (i32, [vp, vp, i64, vp, vp, i64, vp, vp]),
         "sxe_encode_bwd_input": (i32, [vp, vp, i64, vp, vp, vp, vp]),
         "sxe_encode_bwd_kernel_count": (i32, [vp, i64]),

@@ -97,15 +97,22 @@ class Encoder:
         L.check(L.lib().sxe_encoder_level_index(self._h, w.ctypes.data), "sxe_encoder_level_index")
         return w
 
-    def encode_fwd(self, x: torch.Tensor, tables: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    def encode_fwd(self, x: torch.Tensor, tables: torch.Tensor, out: torch.Tensor | None = None, stream=None,
+                   touched: torch.Tensor | None = None):
+        """``sxe_encode_fwd``; with ``touched`` (int32 bitmap of L*T bits) ``sxe_encode_fwd_marked``."""
         P = x.shape[0]
         _need(x, torch.float32, "x", (P, self.d))
         _need(tables, torch_dtype(self.table_dtype), "tables", self.table_shape())
         if out is None:
             out = torch.empty((P, self.n_out), dtype=torch_dtype(self.out_dtype), device=x.device)
         _need(out, torch_dtype(self.out_dtype), "out", (P, self.n_out))
-        L.check(L.lib().sxe_encode_fwd(self._h, _ptr(x), P, _ptr(tables), _ptr(out), _stream(stream)),
-                "sxe_encode_fwd")
+        if touched is None:
+            L.check(L.lib().sxe_encode_fwd(self._h, _ptr(x), P, _ptr(tables), _ptr(out), _stream(stream)),
+                    "sxe_encode_fwd")
+        else:
+            _need(touched, torch.int32, "touched", ((self.n_levels * self.T + 31) // 32,))
+            L.check(L.lib().sxe_encode_fwd_marked(self._h, _ptr(x), P, _ptr(tables), _ptr(out), _ptr(touched),
+                                                  _stream(stream)), "sxe_encode_fwd_marked")
         return out
 
     def encode_bwd(self, x: torch.Tensor, dout: torch.Tensor, grad: torch.Tensor, grad_stride: int | None = None,

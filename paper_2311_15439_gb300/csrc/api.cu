@@ -191,18 +191,30 @@ static sxe_status check_points(const char* fn, const sxe_encoder* e, const float
   return SXE_OK;
 }
 
-sxe_status sxe_encode_fwd(const sxe_encoder* e, const float* x, int64_t P, const void* tables, void* out,
-                          void* stream) {
-  sxe_status st = check_points("encode_fwd", e, x, P);
+static sxe_status encode_fwd_common(const char* fn, const sxe_encoder* e, const float* x, int64_t P,
+                                    const void* tables, void* out, uint32_t* touched, void* stream) {
+  sxe_status st = check_points(fn, e, x, P);
   if (st != SXE_OK) return st;
   if (P == 0) return SXE_OK;
-  if (!tables || !out) return set_error(SXE_EINVAL, "encode_fwd: NULL tables or out");
+  if (!tables || !out) return set_error(SXE_EINVAL, "%s: NULL tables or out", fn);
   const int F = e->desc.n_features;
   const size_t ta = std::min<size_t>(16, F * dtype_size(e->desc.table_dtype));
-  if (!aligned(tables, ta)) return set_error(SXE_EINVAL, "encode_fwd: tables must be %zu-byte aligned", ta);
+  if (!aligned(tables, ta)) return set_error(SXE_EINVAL, "%s: tables must be %zu-byte aligned", fn, ta);
   const size_t oa = F == 2 ? 2 * dtype_size(e->desc.out_dtype) : dtype_size(e->desc.out_dtype);
-  if (!aligned(out, oa)) return set_error(SXE_EINVAL, "encode_fwd: out must be %zu-byte aligned", oa);
-  return launch_encode_fwd(e, x, P, tables, out, (cudaStream_t)stream);
+  if (!aligned(out, oa)) return set_error(SXE_EINVAL, "%s: out must be %zu-byte aligned", fn, oa);
+  return launch_encode_fwd(e, x, P, tables, out, (cudaStream_t)stream, 0, touched);
+}
+
+sxe_status sxe_encode_fwd(const sxe_encoder* e, const float* x, int64_t P, const void* tables, void* out,
+                          void* stream) {
+  return encode_fwd_common("encode_fwd", e, x, P, tables, out, nullptr, stream);
+}
+
+sxe_status sxe_encode_fwd_marked(const sxe_encoder* e, const float* x, int64_t P, const void* tables, void* out,
+                                 uint32_t* touched, void* stream) {
+  if (P > 0 && !touched) return set_error(SXE_EINVAL, "encode_fwd_marked: NULL touched");
+  if (touched && !aligned(touched, 4)) return set_error(SXE_EINVAL, "encode_fwd_marked: touched misaligned");
+  return encode_fwd_common("encode_fwd_marked", e, x, P, tables, out, touched, stream);
 }
 
 sxe_status sxe_encode_bwd(const sxe_encoder* e, const float* x, int64_t P, const float* dout, float* grad,

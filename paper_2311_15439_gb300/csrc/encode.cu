@@ -17,7 +17,7 @@ using namespace encode_detail;
 template <bool SIMPLEX, int D, int F, typename TT>
 __global__ void __launch_bounds__(kThreads)
 encode_fwd_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__ tables, int64_t tstride,
-                  void* __restrict__ out, const EncParams prm) {
+                  void* __restrict__ out, const EncParams prm, uint32_t* __restrict__ touched) {
   constexpr int V = Verts<SIMPLEX, D>::V;
   __shared__ float s_scale[SXE_MAX_LEVELS];
   __shared__ uint32_t s_width[SXE_MAX_LEVELS];
@@ -39,6 +39,20 @@ encode_fwd_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__
   float val[V][F];
 #pragma unroll
   for (int k = 0; k < V; ++k) load_entry<TT, F>(tab + (int64_t)slot[k] * tstride, val[k]);
+  if (touched) {
+    // mark every entry read (the entries the backward of the same points adds to), while the
+    // gathers are in flight: all bitmap words first, then the missing bits
+    const int64_t lbase = (int64_t)it.l << prm.log2_T;
+    uint32_t words[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) words[k] = __ldcg(touched + ((lbase + slot[k]) >> 5));
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int64_t e = lbase + slot[k];
+      const uint32_t bit = 1u << (uint32_t)(e & 31);
+      if (!(words[k] & bit)) atomicOr(touched + (e >> 5), bit);
+    }
+  }
   float acc[F];
 #pragma unroll
   for (int f = 0; f < F; ++f) acc[f] = 0.f;
@@ -500,33 +514,35 @@ namespace {
 
 template <bool SIMPLEX, int D, int F>
 sxe_status fwd_tt(const sxe_encoder* enc, const float* x, int64_t P, const void* tab, int64_t ts, void* out,
-                  cudaStream_t s) {
+                  uint32_t* touched, cudaStream_t s) {
   const unsigned g = grid_for(P, enc->prm.n_levels);
   switch (enc->desc.table_dtype) {
-    case SXE_F32: encode_fwd_kernel<SIMPLEX, D, F, float><<<g, kThreads, 0, s>>>(x, P, (const float*)tab, ts, out, enc->prm); break;
-    case SXE_F16: encode_fwd_kernel<SIMPLEX, D, F, __half><<<g, kThreads, 0, s>>>(x, P, (const __half*)tab, ts, out, enc->prm); break;
-    default: encode_fwd_kernel<SIMPLEX, D, F, __nv_bfloat16><<<g, kThreads, 0, s>>>(x, P, (const __nv_bfloat16*)tab, ts, out, enc->prm); break;
+    case SXE_F32: encode_fwd_kernel<SIMPLEX, D, F, float><<<g, kThreads, 0, s>>>(x, P, (const float*)tab, ts, out, enc->prm, touched); break;
+    case SXE_F16: encode_fwd_kernel<SIMPLEX, D, F, __half><<<g, kThreads, 0, s>>>(x, P, (const __half*)tab, ts, out, enc->prm, touched); break;
+    default: encode_fwd_kernel<SIMPLEX, D, F, __nv_bfloat16><<<g, kThreads, 0, s>>>(x, P, (const __nv_bfloat16*)tab, ts, out, enc->prm, touched); break;
   }
   return check_launch("encode_fwd");
 }
 
 template <bool SIMPLEX, int D>
-sxe_status fwd_f(const sxe_encoder* e, const float* x, int64_t P, const void* t, int64_t ts, void* o, cudaStream_t s) {
+sxe_status fwd_f(const sxe_encoder* e, const float* x, int64_t P, const void* t, int64_t ts, void* o, uint32_t* tm,
+                 cudaStream_t s) {
   switch (e->desc.n_features) {
-    case 1: return fwd_tt<SIMPLEX, D, 1>(e, x, P, t, ts, o, s);
-    case 2: return fwd_tt<SIMPLEX, D, 2>(e, x, P, t, ts, o, s);
-    case 4: return fwd_tt<SIMPLEX, D, 4>(e, x, P, t, ts, o, s);
-    default: return fwd_tt<SIMPLEX, D, 8>(e, x, P, t, ts, o, s);
+    case 1: return fwd_tt<SIMPLEX, D, 1>(e, x, P, t, ts, o, tm, s);
+    case 2: return fwd_tt<SIMPLEX, D, 2>(e, x, P, t, ts, o, tm, s);
+    case 4: return fwd_tt<SIMPLEX, D, 4>(e, x, P, t, ts, o, tm, s);
+    default: return fwd_tt<SIMPLEX, D, 8>(e, x, P, t, ts, o, tm, s);
   }
 }
 
 template <bool SIMPLEX>
-sxe_status fwd_d(const sxe_encoder* e, const float* x, int64_t P, const void* t, int64_t ts, void* o, cudaStream_t s) {
+sxe_status fwd_d(const sxe_encoder* e, const float* x, int64_t P, const void* t, int64_t ts, void* o, uint32_t* tm,
+                 cudaStream_t s) {
   switch (e->desc.d) {
-    case 2: return fwd_f<SIMPLEX, 2>(e, x, P, t, ts, o, s);
-    case 3: return fwd_f<SIMPLEX, 3>(e, x, P, t, ts, o, s);
-    case 4: return fwd_f<SIMPLEX, 4>(e, x, P, t, ts, o, s);
-    default: return fwd_f<SIMPLEX, 5>(e, x, P, t, ts, o, s);
+    case 2: return fwd_f<SIMPLEX, 2>(e, x, P, t, ts, o, tm, s);
+    case 3: return fwd_f<SIMPLEX, 3>(e, x, P, t, ts, o, tm, s);
+    case 4: return fwd_f<SIMPLEX, 4>(e, x, P, t, ts, o, tm, s);
+    default: return fwd_f<SIMPLEX, 5>(e, x, P, t, ts, o, tm, s);
   }
 }
 
@@ -634,10 +650,10 @@ sxe_status verts_d(const sxe_encoder* e, const float* x, int64_t P, uint32_t* sl
 }  // namespace
 
 sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables, void* out,
-                             cudaStream_t s, int64_t table_stride) {
+                             cudaStream_t s, int64_t table_stride, uint32_t* touched) {
   if (table_stride <= 0) table_stride = enc->desc.n_features;
-  return enc->desc.kind == SXE_SIMPLEX ? fwd_d<true>(enc, x, P, tables, table_stride, out, s)
-                                       : fwd_d<false>(enc, x, P, tables, table_stride, out, s);
+  return enc->desc.kind == SXE_SIMPLEX ? fwd_d<true>(enc, x, P, tables, table_stride, out, touched, s)
+                                       : fwd_d<false>(enc, x, P, tables, table_stride, out, touched, s);
 }
 
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout, float* grad,

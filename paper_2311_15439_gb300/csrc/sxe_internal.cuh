@@ -40,7 +40,7 @@ sxe_status check_mlp(const char* fn, const sxe_mlp_desc* d);
 
 // launchers (defined in encode.cu / mlp.cu / optim.cu); arguments already validated
 sxe_status launch_encode_fwd(const sxe_encoder* enc, const float* x, int64_t P, const void* tables,
-                             void* out, cudaStream_t s, int64_t table_stride = 0);
+                             void* out, cudaStream_t s, int64_t table_stride = 0, uint32_t* touched = nullptr);
 // level_end < 0 means n_levels; only levels [level_begin, level_end) are accumulated
 sxe_status launch_encode_bwd(const sxe_encoder* enc, const float* x, int64_t P, const float* dout,
                              float* grad, int64_t grad_stride, uint32_t* touched, cudaStream_t s,

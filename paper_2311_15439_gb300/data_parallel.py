@@ -93,7 +93,7 @@ class DataParallelTrainer:
         """This rank's part of a step: encoding, network + L2 loss + backward, encoding backward,
         into ``flat`` (the squared-residual sum overwritten, the gradients accumulated)."""
         tr = self.tr
-        tr.enc.encode_fwd(x, tr.tables, tr.enc_out)
+        tr.tab.forward(x, tr.enc_out)
         tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, target, tr.dW, tr.sq_sum, din=tr.d_enc,
                             loss_scale=tr.loss_scale, workspace=tr.ws)
         tr.tab.backward(x, tr.d_enc)

@@ -4,7 +4,9 @@ One ``step(x, target)`` runs, on the caller's stream and entirely in libsimplexe
 kernels:
 
 1. ``sxe_encode_fwd``   -- multiresolution encoding of the batch from the low-precision
-                           tables (Sec. 5 a-d);
+                           tables (Sec. 5 a-d); optionally (``mark_touched_in_forward``, records
+                           layout) ``sxe_encode_fwd_marked``, which also marks the touched entries
+                           that the backward then leaves unmarked;
 2. ``sxe_mlp_train_l2`` -- network forward, L2 loss, network backward, dL/d(encoding)
                            (Sec. 5 d-e);
 3. ``sxe_encode_bwd``   -- scatter-add of dL/d(encoding) into the table gradients (Sec. 5 e):
@@ -85,6 +87,10 @@ class TableState:
         n_entries = encoder.n_levels * encoder.T
         self.enc, self.layout, self.device = encoder, layout, torch.device(device)
         self.split_coarse, self._side = False, None
+        # records layout: mark the touched entries in the forward pass (``forward``) instead of the
+        # backward; the owner turns it on when its step runs this state's forward and backward on
+        # the same points
+        self.mark_in_forward = False
         self.set_split_coarse(layout == "dense" if split_coarse == "auto" else split_coarse)
         self.tables = init.to(torch_dtype(encoder.table_dtype)).reshape(encoder.table_shape()).contiguous()
         if layout == "records":
@@ -112,6 +118,14 @@ class TableState:
             self._side = torch.cuda.Stream(device=self.device, priority=-1)
             self._fork, self._join = torch.cuda.Event(), torch.cuda.Event()
 
+    def forward(self, x, out, stream=None) -> None:
+        """The encoding of x from the low-precision tables into out; with the records layout and
+        ``mark_in_forward`` it also sets the touched bits of every entry it reads
+        (``sxe_encode_fwd_marked``), exactly the entries the backward of the same points adds to,
+        so that the backward's reductions run without the bitmap's reads and ORs."""
+        mark = self.touched if (self.layout == "records" and self.mark_in_forward) else None
+        self.enc.encode_fwd(x, self.tables, out, stream=stream, touched=mark)
+
     def backward(self, x, d_enc, stream=None, levels=None) -> None:
         """Table gradients of one step (into the records' gradient fields or the dense array)."""
         if levels is None and self.split_coarse and self.enc.T >= 32:
@@ -131,8 +145,8 @@ class TableState:
     def _backward(self, x, d_enc, stream, levels) -> None:
         F = self.enc.n_features
         if self.layout == "records":
-            self.enc.encode_bwd(x, d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F, touched=self.touched,
-                                levels=levels, stream=stream)
+            self.enc.encode_bwd(x, d_enc, self.state, grad_stride=4 * F, grad_offset=3 * F,
+                                touched=None if self.mark_in_forward else self.touched, levels=levels, stream=stream)
         else:
             self.enc.encode_bwd(x, d_enc, self.grad, levels=levels, stream=stream)
 
@@ -165,7 +179,8 @@ def default_loss_scale(P: int, n_out: int) -> float:
 class Trainer:
     def __init__(self, encoder: Encoder, mlp: Mlp, batch: int, *, seed: int = 0, device="cuda",
                  table_init: float = 1e-4, lr: float = 1e-2, betas=(0.9, 0.99), eps: float = 1e-15,
-                 table_chunks: int = 1, table_layout: str = "auto", split_coarse="auto", split_batch: int = 1):
+                 table_chunks: int = 1, table_layout: str = "auto", split_coarse="auto", split_batch: int = 1,
+                 mark_touched_in_forward: bool = False):
         if mlp.n_in != encoder.n_out:
             raise ValueError("network input %d != encoding width %d" % (mlp.n_in, encoder.n_out))
         self.enc, self.mlp, self.P = encoder, mlp, batch
@@ -199,6 +214,7 @@ class Trainer:
         self.t_dev = torch.zeros((1,), dtype=torch.int64, device=self.device)
         self.corrections = torch.zeros((2,), dtype=torch.float32, device=self.device)
         self.graph = None
+        self.mark_touched_in_forward = bool(mark_touched_in_forward)
         self.set_table_chunks(table_chunks)
         if self.split > 1:
             if len(self.chunks) > 1:
@@ -215,6 +231,8 @@ class Trainer:
         if k > 1 and (self.enc.T < 32 or self.tab.layout != "records"):
             k = 1
         self.chunks = level_chunks(self.enc, self.P, k)
+        # the level-range step marks entries in its backward (per range); the plain step in the forward
+        self.tab.mark_in_forward = len(self.chunks) == 1 and self.mark_touched_in_forward
         if len(self.chunks) > 1:
             self._aux = torch.cuda.Stream(device=self.device, priority=-1)
             self._ready = [torch.cuda.Event() for _ in self.chunks]
@@ -252,7 +270,7 @@ class Trainer:
         main = torch.cuda.current_stream(self.device) if stream is None else stream
         self.adam_tables.advance(self.t_dev, self.corrections, stream=stream)
         self._mark("encode_fwd", main)
-        self.enc.encode_fwd(x, self.tables, self.enc_out, stream=stream)
+        self.tab.forward(x, self.enc_out, stream=stream)
         self._mark("encode_fwd_end", main)
         self._mark("mlp_train_l2", main)
         self.mlp.mlp_train_l2(self.W_lowp, self.enc_out, target, self.dW, self.sq_sum, din=self.d_enc,
@@ -286,7 +304,7 @@ class Trainer:
         self.t += 1
         self.adam_tables.advance(self.t_dev, self.corrections, stream=main)
         self._mark("encode_fwd", main)
-        self.enc.encode_fwd(x, self.tables, self.enc_out, stream=main)
+        self.tab.forward(x, self.enc_out, stream=main)
         self._mark("encode_fwd_end", main)
         for i, (a, b) in enumerate(self.parts()):
             self._mark("mlp_train_l2", main)

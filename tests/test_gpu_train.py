@@ -51,7 +51,7 @@ def test_one_step_matches_oracle(layout):
 
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda()
     # run the first three stages of the step and stop before the optimiser
-    tr.enc.encode_fwd(xd, tr.tables, tr.enc_out)
+    tr.tab.forward(xd, tr.enc_out)
     tr.mlp.mlp_train_l2(tr.W_lowp, tr.enc_out, td, tr.dW, tr.sq_sum, din=tr.d_enc, loss_scale=tr.loss_scale,
                         workspace=tr.ws)
     tr.tab.backward(xd, tr.d_enc)
@@ -113,6 +113,73 @@ def test_one_step_matches_oracle(layout):
                                                                         W_ref[clearW])), 1e-5, "absolute")
     np.testing.assert_allclose(tr.W.cpu().numpy()[clearW], W_ref[clearW], rtol=0, atol=1e-5)
     assert np.abs(g_W - gW_ref).max() <= tol * np.abs(gW_ref).max() * 4
+
+
+@pytest.mark.parametrize("kind,d", [("simplex", 2), ("simplex", 3), ("grid", 2), ("grid", 3)])
+def test_forward_marks_the_entries_the_backward_marks(kind, d):
+    """``sxe_encode_fwd_marked`` sets exactly the touched bits that the backward of the same points
+    sets (every vertex slot of every level), and its encoding equals the unmarked forward's bit
+    for bit; marking into a bitmap that already holds bits only adds the missing ones."""
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.build import build
+    build()
+    cfg = dict(CFG, d=d, n_levels=6, log2_T=13)
+    enc = Encoder(kind=kind, **cfg, table_dtype="f16")
+    L, T, F = 6, 1 << 13, 2
+    P = 3000 + 17                                            # several blocks and a ragged tail
+    tables = torch.from_numpy(synth.uniform_tables(L, T, F, 3, dtype="f32", scale=1e-1)[0]).half().cuda()
+    x = torch.from_numpy(synth.uniform_points(P, d, 41)).cuda()
+    words = (L * T + 31) // 32
+    t_fwd = torch.zeros((words,), dtype=torch.int32, device="cuda")
+    t_bwd = torch.zeros_like(t_fwd)
+    out_plain = enc.encode_fwd(x, tables)
+    out_marked = enc.encode_fwd(x, tables, touched=t_fwd)
+    assert torch.equal(out_plain, out_marked)
+    state = torch.zeros((L * T, 4 * F), dtype=torch.float32, device="cuda")
+    dout = torch.ones((P, L * F), dtype=torch.float32, device="cuda")
+    enc.encode_bwd(x, dout, state, grad_stride=4 * F, grad_offset=3 * F, touched=t_bwd)
+    torch.cuda.synchronize()
+    assert torch.equal(t_fwd, t_bwd)
+    n_set = int(sum(bin(w & 0xFFFFFFFF).count("1") for w in t_fwd.cpu().tolist()))
+    assert 0 < n_set < L * T
+    # a second pass over other points adds their bits to those already set
+    x2 = torch.from_numpy(synth.uniform_points(500, d, 42)).cuda()
+    enc.encode_fwd(x2, tables, touched=t_fwd)
+    enc.encode_bwd(x2, dout[:500], state, grad_stride=4 * F, grad_offset=3 * F, touched=t_bwd)
+    torch.cuda.synchronize()
+    assert torch.equal(t_fwd, t_bwd)
+    # an empty batch marks nothing
+    before = t_fwd.clone()
+    enc.encode_fwd(x[:0], tables, touched=t_fwd)
+    torch.cuda.synchronize()
+    assert torch.equal(before, t_fwd)
+
+
+def test_marking_in_forward_trains_like_marking_in_backward():
+    """The records-layout step with the touched entries marked in the forward trains like the step
+    that marks them in the backward (parameters equal up to the order of the binary32 atomics);
+    Adam clears every bit either way."""
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+    P = 4096
+    mk = lambda mark: Trainer(Encoder(**CFG, table_dtype="f16"), Mlp(16, 3, n_hidden=2, dtype="f16"), P, seed=21,
+                              table_layout="records", mark_touched_in_forward=mark)
+    a, b = mk(True), mk(False)
+    assert a.tab.mark_in_forward and not b.tab.mark_in_forward
+    img = synth.ProceduralImage(4, size=1024, n_waves=4)
+    for i in range(4):
+        x = synth.uniform_points(P, 2, 120 + i)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(img.sample(x)).cuda()
+        a.step(xd, td)
+        b.step(xd, td)
+    torch.cuda.synchronize()
+    assert int(a.touched.abs().sum().item()) == 0 and int(b.touched.abs().sum().item()) == 0
+    _close_up_to_atomics(a.W, b.W, steps=4, atol=1e-5)
+    _close_up_to_atomics(a.state, b.state, steps=4)
+    a.set_table_chunks(3)                                    # level ranges mark in their backward
+    assert not a.tab.mark_in_forward
+    a.set_table_chunks(1)
+    assert a.tab.mark_in_forward
 
 
 def test_training_reduces_loss():
@@ -588,7 +655,7 @@ def test_data_parallel_shards_average_to_the_union_step():
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(scene.sdf(x)).cuda()
     un.t += 1
     un.adam_tables.advance(un.t_dev, un.corrections)
-    un.enc.encode_fwd(xd, un.tables, un.enc_out)
+    un.tab.forward(xd, un.enc_out)
     un.mlp.mlp_train_l2(un.W_lowp, un.enc_out, td, un.dW, un.sq_sum, din=un.d_enc, loss_scale=un.loss_scale,
                         workspace=un.ws)
     un.tab.backward(xd, un.d_enc)
