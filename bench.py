@@ -240,7 +240,8 @@ def run_gpu(args):
     from paper_2311_15439_gb300 import _lib
     _lib.check(_lib.lib().sxe_mlp_set_kernel({"auto": _lib.SXE_MLP_KERNEL_AUTO, "mma_sync": _lib.SXE_MLP_KERNEL_MMA_SYNC,
                                               "tcgen05": _lib.SXE_MLP_KERNEL_TCGEN05,
-                                              "tcgen05_pipelined": _lib.SXE_MLP_KERNEL_TCGEN05_PIPELINED}[args.mlp_kernel]),
+                                              "tcgen05_pipelined": _lib.SXE_MLP_KERNEL_TCGEN05_PIPELINED,
+                                              "tcgen05_3tile": _lib.SXE_MLP_KERNEL_TCGEN05_3TILE}[args.mlp_kernel]),
                "sxe_mlp_set_kernel")
     enc = Encoder(**CFG, kind=args.kind, table_dtype="f16")
     mlp = Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16")
@@ -332,8 +333,9 @@ def run_gpu(args):
                        "step": "encode forward, network forward + L2 loss + backward, encode backward into the "
                                "table state, Adam on the touched table entries and on the network",
                        "split_batch": tr.split,
-                       "mlp_kernel": {"auto": "auto (two-tile tcgen05 kernel for this network)", "mma_sync": "mma_sync",
-                                      "tcgen05": "tcgen05", "tcgen05_pipelined": "tcgen05_pipelined"}[args.mlp_kernel],
+                       "mlp_kernel": {"auto": "auto (three-tile tcgen05 kernel for this network)", "mma_sync": "mma_sync",
+                                      "tcgen05": "tcgen05", "tcgen05_pipelined": "tcgen05_pipelined",
+                                      "tcgen05_3tile": "tcgen05_3tile"}[args.mlp_kernel],
                        "global_batch": BATCH * world,
                        "points_per_step_per_gpu": BATCH, "parallelism": "replicas (one per GPU)",
                        "l2": "working set > L2: 256 MiB fp16 tables + 2 GiB fp32 table state records, no flush",
@@ -1414,7 +1416,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-volume", action="store_true")
-    ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05", "tcgen05_pipelined"],
+    ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05", "tcgen05_pipelined", "tcgen05_3tile"],
                     help="kernel of the network training pass")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--split-batch", type=int, default=1,
@@ -1436,7 +1438,8 @@ def main():
         B.build()
         profile_mlp(torch.device("cuda", 0), {"auto": _lib.SXE_MLP_KERNEL_AUTO, "mma_sync": _lib.SXE_MLP_KERNEL_MMA_SYNC,
                                               "tcgen05": _lib.SXE_MLP_KERNEL_TCGEN05,
-                                              "tcgen05_pipelined": _lib.SXE_MLP_KERNEL_TCGEN05_PIPELINED}[args.mlp_kernel])
+                                              "tcgen05_pipelined": _lib.SXE_MLP_KERNEL_TCGEN05_PIPELINED,
+                                              "tcgen05_3tile": _lib.SXE_MLP_KERNEL_TCGEN05_3TILE}[args.mlp_kernel])
     elif args.profile_encode:
         import torch
         from paper_2311_15439_gb300 import build as B

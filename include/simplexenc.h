@@ -449,16 +449,22 @@ sxe_status sxe_step_touched_dev(const sxe_adam_desc* desc, const float* correcti
  * SXE_MLP_KERNEL_TCGEN05 (tcgen05.mma with TMEM accumulators; where its shared-memory plan
  * fits, two 128-point tiles in flight per SM and the weight gradients on tcgen05 too, else one
  * tile per CTA with the weight gradients on mma.sync).  SXE_MLP_KERNEL_AUTO (the default)
- * takes the two-tile tcgen05 kernel where it applies and mma.sync elsewhere.  All compute the
- * same products in the same precision (fp16/bf16 operands, binary32 accumulation).
+ * takes SXE_MLP_KERNEL_TCGEN05_3TILE for n_out <= 8, else the two-tile tcgen05 kernel where it
+ * applies, else mma.sync.  All compute the same products in the same precision (fp16/bf16
+ * operands, binary32 accumulation).
  * SXE_MLP_KERNEL_TCGEN05_PIPELINED: tcgen05 with one warp issuing every product of the CTA for up
  * to four 128-point tiles in flight (each tile's epilogues run in its own warpgroup), the weight
- * gradients of all tiles accumulating in one set of TMEM accumulators.  Not thread-safe: set it
- * before launching work. */
+ * gradients of all tiles accumulating in one set of TMEM accumulators.
+ * SXE_MLP_KERNEL_TCGEN05_3TILE: for networks with n_out <= 8 (others fall back to
+ * SXE_MLP_KERNEL_TCGEN05), up to three 128-point tiles in flight per SM, each issuing its own
+ * tcgen05 products, with the output layer, the loss and the output layer's backward on warp-level
+ * mma.sync inside the last hidden layer's epilogue (2 NH tensor-core round trips per tile instead
+ * of 2 NH + 2).  Not thread-safe: set it before launching work. */
 #define SXE_MLP_KERNEL_AUTO 0
 #define SXE_MLP_KERNEL_MMA_SYNC 1
 #define SXE_MLP_KERNEL_TCGEN05 2
 #define SXE_MLP_KERNEL_TCGEN05_PIPELINED 3
+#define SXE_MLP_KERNEL_TCGEN05_3TILE 4
 sxe_status sxe_mlp_set_kernel(int32_t kernel);
 int32_t sxe_mlp_get_kernel(void);
 

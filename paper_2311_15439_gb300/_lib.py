@@ -18,6 +18,7 @@ SXE_RES_RAW, SXE_RES_EQUAL_MEM = 0, 1
 SXE_INDEX_HASH, SXE_INDEX_DENSE_COARSE = 0, 1
 SXE_MAX_LEVELS = 32
 SXE_MLP_KERNEL_AUTO, SXE_MLP_KERNEL_MMA_SYNC, SXE_MLP_KERNEL_TCGEN05, SXE_MLP_KERNEL_TCGEN05_PIPELINED = 0, 1, 2, 3
+SXE_MLP_KERNEL_TCGEN05_3TILE = 4
 
 #: every function the header declares (checked by the export test)
 EXPORTS = (

@@ -478,7 +478,7 @@ sxe_status sxe_mlp_train_l2_grouped(const sxe_mlp_desc* d, const void* W, const 
 
 sxe_status sxe_mlp_set_kernel(int32_t k) {
   if (k != SXE_MLP_KERNEL_AUTO && k != SXE_MLP_KERNEL_MMA_SYNC && k != SXE_MLP_KERNEL_TCGEN05 &&
-      k != SXE_MLP_KERNEL_TCGEN05_PIPELINED)
+      k != SXE_MLP_KERNEL_TCGEN05_PIPELINED && k != SXE_MLP_KERNEL_TCGEN05_3TILE)
     return set_error(SXE_EINVAL, "mlp_set_kernel: unknown kernel %d", k);
   g_mlp_kernel = k;
   return SXE_OK;

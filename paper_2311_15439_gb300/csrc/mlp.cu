@@ -824,10 +824,17 @@ sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, 
                           const float* target, float loss_scale, int64_t P, float* din, float* dW, float* sq_sum,
                           float* ws, int grid, cudaStream_t s, int din_group, int64_t loss_count) {
   const int64_t lc = loss_count > 0 ? loss_count : P;   // the L2 gradient's 2 / (count * n_out)
-  // automatic choice: the two-tile tcgen05 kernel where it applies (measured faster than mma.sync:
-  // 65.6 against 67.6 us per 2^18-point pass), mma.sync elsewhere
+  // automatic choice: for a narrow output layer (n_out <= 8) the three-tile tcgen05 kernel (image
+  // network, 2^18 points: 43.8 us per pass, against 62.4 us for the two-tile kernel and 62.5 us
+  // for mma.sync), else the two-tile tcgen05 kernel where its plan fits, else mma.sync
+  if (g_mlp_kernel == SXE_MLP_KERNEL_AUTO && mlp_tc3_applies(d))
+    return launch_mlp_bwd_tc3(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc);
   if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_PIPELINED)
     return launch_mlp_bwd_ws(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc);
+  if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_3TILE && mlp_tc3_applies(d))
+    return launch_mlp_bwd_tc3(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc);
+  if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_3TILE)
+    return launch_mlp_bwd_tc(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc);
   if (g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05 || (g_mlp_kernel == SXE_MLP_KERNEL_AUTO && mlp_tc2_applies(d, grid)))
     return launch_mlp_bwd_tc(d, W, in, dout, target, loss_scale, P, din, dW, sq_sum, ws, grid, s, din_group, lc);
   return d->dtype == SXE_F16

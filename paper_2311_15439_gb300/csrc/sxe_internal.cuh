@@ -84,7 +84,13 @@ sxe_status launch_mlp_bwd_ws(const sxe_mlp_desc* d, const void* W, const void* i
                              const float* target, float loss_scale, int64_t P, float* din, float* dW,
                              float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group,
                              int64_t loss_count);
+sxe_status launch_mlp_bwd_tc3(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
+                              const float* target, float loss_scale, int64_t P, float* din, float* dW,
+                              float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group,
+                              int64_t loss_count);
 bool mlp_tc2_applies(const sxe_mlp_desc* d, int grid);
+bool mlp_tc3_applies(const sxe_mlp_desc* d);
+int* tc_error_word();   // device address of the tcgen05 kernels' error word (current device)
 sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
                              cudaStream_t s);
 sxe_status read_tc_error(int32_t* flag, bool clear);

@@ -92,6 +92,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   return false;
 }
 
+// The same wait with the polling thread suspended between polls (up to `hint_ns` per poll, woken
+// when the phase completes), so that waiting warps take few issue and shared-memory slots; it gives
+// up once the global timer shows more than `limit_ns` since the first timed poll (or after
+// max_iter polls, whichever comes first) and returns false.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* mbar, uint32_t parity, uint32_t hint_ns, uint64_t limit_ns,
+                                                uint32_t max_iter) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0; it < max_iter; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity), "r"(hint_ns) : "memory");
+    if (done) return true;
+    if ((it & 15) == 15) {
+      const uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+    }
+  }
+  return false;
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // make generic-proxy shared-memory writes visible to the tensor cores (async proxy)
@@ -107,6 +133,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 64 consecutive fp32 columns of this thread's TMEM lane: two loads in flight, one wait
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+#define SXE_LD32(OFF, B)                                                                                         \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15," \
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                       \
+               : "=r"(B[0]), "=r"(B[1]), "=r"(B[2]), "=r"(B[3]), "=r"(B[4]), "=r"(B[5]), "=r"(B[6]), "=r"(B[7]), \
+                 "=r"(B[8]), "=r"(B[9]), "=r"(B[10]), "=r"(B[11]), "=r"(B[12]), "=r"(B[13]), "=r"(B[14]),       \
+                 "=r"(B[15]), "=r"(B[16]), "=r"(B[17]), "=r"(B[18]), "=r"(B[19]), "=r"(B[20]), "=r"(B[21]),     \
+                 "=r"(B[22]), "=r"(B[23]), "=r"(B[24]), "=r"(B[25]), "=r"(B[26]), "=r"(B[27]), "=r"(B[28]),     \
+                 "=r"(B[29]), "=r"(B[30]), "=r"(B[31])                                                           \
+               : "r"(taddr + (OFF)))
+  SXE_LD32(0u, r);
+  SXE_LD32(32u, (r + 32));
+#undef SXE_LD32
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // 32 consecutive fp32 columns of this thread's TMEM lane, loaded and waited for in one statement

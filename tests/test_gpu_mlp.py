@@ -90,14 +90,15 @@ def within(got, want, den, tol, slack=0.0):
     return float(np.max(err / np.maximum(bound, 1e-300)))
 
 
-@pytest.fixture(params=["mma_sync", "tcgen05", "tcgen05_pipelined"])
+@pytest.fixture(params=["mma_sync", "tcgen05", "tcgen05_pipelined", "tcgen05_3tile"])
 def mlp_kernel(request, cuda_lib):
     """Run the test with the network's training pass on each kernel; afterwards no bounded
     device wait may have given up."""
     import ctypes
     L = cuda_lib
     code = {"mma_sync": L.SXE_MLP_KERNEL_MMA_SYNC, "tcgen05": L.SXE_MLP_KERNEL_TCGEN05,
-            "tcgen05_pipelined": L.SXE_MLP_KERNEL_TCGEN05_PIPELINED}[request.param]
+            "tcgen05_pipelined": L.SXE_MLP_KERNEL_TCGEN05_PIPELINED,
+            "tcgen05_3tile": L.SXE_MLP_KERNEL_TCGEN05_3TILE}[request.param]
     prev = L.lib().sxe_mlp_get_kernel()
     assert L.lib().sxe_mlp_set_kernel(code) == 0
     try:
@@ -112,7 +113,7 @@ def mlp_kernel(request, cuda_lib):
 
 # (n_in, n_hidden, n_out, dtype, P)
 NETS = [(32, 2, 3, "f16", 4099), (32, 2, 3, "bf16", 2000), (32, 1, 1, "bf16", 3333), (16, 3, 16, "f16", 1000),
-        (64, 1, 5, "f16", 257), (32, 2, 3, "f16", 1 << 16)]
+        (64, 1, 5, "f16", 257), (32, 2, 3, "f16", 1 << 16), (16, 2, 3, "f16", 3001), (64, 3, 8, "bf16", 1500)]
 # the image workload's network at its full batch, in the launch configuration the benchmark times
 FULL = (32, 2, 3, "f16", 1 << 18)
 
@@ -178,7 +179,8 @@ def test_backward_accumulates_and_is_deterministic(cuda_lib, mlp_kernel):
     torch.testing.assert_close(a, 2 * b, rtol=1e-6, atol=0)
 
 
-@pytest.mark.parametrize("net", [NETS[0], NETS[2], NETS[5], FULL], ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
+@pytest.mark.parametrize("net", [NETS[0], NETS[2], NETS[5], NETS[6], NETS[7], FULL],
+                         ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
 def test_train_l2(cuda_lib, net, mlp_kernel):
     """Fused forward + L2 loss + backward equals the oracle's loss and gradients, with the
     gradient scaled by a power of two before the fp16 rounding and unscaled after."""
@@ -284,7 +286,8 @@ def test_adam_touched(cuda_lib, F, dt):
     assert torch.equal(table[torch.from_numpy(marked).cuda()], state[:, :F][torch.from_numpy(marked).cuda()].to(tdt))
 
 
-@pytest.mark.parametrize("net", [NETS[0], NETS[1], NETS[3], NETS[4]], ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
+@pytest.mark.parametrize("net", [NETS[0], NETS[1], NETS[3], NETS[4], NETS[6], NETS[7]],
+                         ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
 def test_tcgen05_and_mma_sync_agree(cuda_lib, net):
     """The two kernels compute the same products in the same precision: their gradients
     differ only by binary32 accumulation order (and the rare ReLU decision at a rounding tie)."""
@@ -295,7 +298,8 @@ def test_tcgen05_and_mma_sync_agree(cuda_lib, net):
     outs = {}
     prev = L.lib().sxe_mlp_get_kernel()
     try:
-        for k in (L.SXE_MLP_KERNEL_MMA_SYNC, L.SXE_MLP_KERNEL_TCGEN05, L.SXE_MLP_KERNEL_TCGEN05_PIPELINED):
+        for k in (L.SXE_MLP_KERNEL_MMA_SYNC, L.SXE_MLP_KERNEL_TCGEN05, L.SXE_MLP_KERNEL_TCGEN05_PIPELINED,
+                  L.SXE_MLP_KERNEL_TCGEN05_3TILE):
             assert L.lib().sxe_mlp_set_kernel(k) == 0
             dW = torch.zeros((mlp.n_params,), device="cuda")
             din = torch.empty((x.shape[0], net[0]), device="cuda")
@@ -309,7 +313,7 @@ def test_tcgen05_and_mma_sync_agree(cuda_lib, net):
     dW_sl, din_sl = flip_slack(Ws, x, dy.cpu().numpy().astype(np.float64), U[net[3]])
     tol = (2 * net[1] + 2) * U[net[3]]
     a = outs[L.SXE_MLP_KERNEL_MMA_SYNC]
-    for k in (L.SXE_MLP_KERNEL_TCGEN05, L.SXE_MLP_KERNEL_TCGEN05_PIPELINED):
+    for k in (L.SXE_MLP_KERNEL_TCGEN05, L.SXE_MLP_KERNEL_TCGEN05_PIPELINED, L.SXE_MLP_KERNEL_TCGEN05_3TILE):
         b = outs[k]
         for i, (ga, gb) in enumerate(zip(mlp.split(a[0]), mlp.split(b[0]))):
             assert within(gb, ga, dW_den[i], tol, 2 * dW_sl[i]) <= 1.0, "kernel %d layer %d" % (k, i)
