@@ -113,7 +113,8 @@ def mlp_kernel(request, cuda_lib):
 
 # (n_in, n_hidden, n_out, dtype, P)
 NETS = [(32, 2, 3, "f16", 4099), (32, 2, 3, "bf16", 2000), (32, 1, 1, "bf16", 3333), (16, 3, 16, "f16", 1000),
-        (64, 1, 5, "f16", 257), (32, 2, 3, "f16", 1 << 16), (16, 2, 3, "f16", 3001), (64, 3, 8, "bf16", 1500)]
+        (64, 1, 5, "f16", 257), (32, 2, 3, "f16", 1 << 16), (16, 2, 3, "f16", 3001), (64, 3, 8, "bf16", 1500),
+        (32, 1, 16, "bf16", 2500)]
 # the image workload's network at its full batch, in the launch configuration the benchmark times
 FULL = (32, 2, 3, "f16", 1 << 18)
 
@@ -179,7 +180,7 @@ def test_backward_accumulates_and_is_deterministic(cuda_lib, mlp_kernel):
     torch.testing.assert_close(a, 2 * b, rtol=1e-6, atol=0)
 
 
-@pytest.mark.parametrize("net", [NETS[0], NETS[2], NETS[5], NETS[6], NETS[7], FULL],
+@pytest.mark.parametrize("net", [NETS[0], NETS[2], NETS[5], NETS[6], NETS[7], NETS[8], FULL],
                          ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
 def test_train_l2(cuda_lib, net, mlp_kernel):
     """Fused forward + L2 loss + backward equals the oracle's loss and gradients, with the
@@ -286,7 +287,7 @@ def test_adam_touched(cuda_lib, F, dt):
     assert torch.equal(table[torch.from_numpy(marked).cuda()], state[:, :F][torch.from_numpy(marked).cuda()].to(tdt))
 
 
-@pytest.mark.parametrize("net", [NETS[0], NETS[1], NETS[3], NETS[4], NETS[6], NETS[7]],
+@pytest.mark.parametrize("net", [NETS[0], NETS[1], NETS[3], NETS[4], NETS[6], NETS[7], NETS[8]],
                          ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
 def test_tcgen05_and_mma_sync_agree(cuda_lib, net):
     """The two kernels compute the same products in the same precision: their gradients

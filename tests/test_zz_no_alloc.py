@@ -48,7 +48,7 @@ def test_static_scratch_matches_workspace_entry(cuda_lib):
         assert abs(sq.item() - ref_sq.item()) <= 1e-5 * ref_sq.item()
 
 
-@pytest.mark.parametrize("kernel", ["mma_sync", "tcgen05", "tcgen05_pipelined"])
+@pytest.mark.parametrize("kernel", ["mma_sync", "tcgen05", "tcgen05_pipelined", "tcgen05_3tile"])
 def test_static_scratch_cuts_the_grid(cuda_lib, kernel):
     """A network large enough that the fixed array holds fewer per-CTA partial rows than the
     persistent grid the workspace entry point launches (the first of the candidates below for which
@@ -61,7 +61,7 @@ def test_static_scratch_cuts_the_grid(cuda_lib, kernel):
     from paper_2311_15439_gb300.api import Mlp
     from test_gpu_mlp import _dens, _round, within
     code = {"mma_sync": L.SXE_MLP_KERNEL_MMA_SYNC, "tcgen05": L.SXE_MLP_KERNEL_TCGEN05,
-            "tcgen05_pipelined": L.SXE_MLP_KERNEL_TCGEN05_PIPELINED}[kernel]
+            "tcgen05_pipelined": L.SXE_MLP_KERNEL_TCGEN05_PIPELINED, "tcgen05_3tile": L.SXE_MLP_KERNEL_TCGEN05_3TILE}[kernel]
     prev = L.lib().sxe_mlp_get_kernel()
     assert L.lib().sxe_mlp_set_kernel(code) == 0
     try:
