@@ -608,6 +608,9 @@ __global__ void __launch_bounds__(kReduceCols * kReduceWarps)
 reduce_partials_kernel(const float* __restrict__ ws, int nb, int64_t n, float inv_scale,
                        float* __restrict__ dW, float* __restrict__ sq_sum) {
   __shared__ float part[kReduceWarps][kReduceCols];
+  // launched as a programmatic dependent of the training pass: wait until that grid has completed
+  // and its writes are visible (a no-op for an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t j = (int64_t)blockIdx.x * kReduceCols + lane;
   // warp w takes partial rows w, w + 16, ...; kReduceUnroll independent loads in flight, each
@@ -651,10 +654,23 @@ int reduce_blocks(int64_t n_params) { return (int)((n_params + kReduceCols - 1) 
 
 }  // namespace
 
+// Launched with programmatic stream serialisation: the reduction grid may be scheduled while the
+// training pass before it on the stream is still running (its launch latency hidden behind that
+// pass); the kernel's first instruction waits for the pass to complete.
 sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
                              cudaStream_t s) {
-  reduce_partials_kernel<<<reduce_blocks(n_params), kReduceCols * kReduceWarps, 0, s>>>(ws, nb, n_params, inv_scale,
-                                                                                     dW, sq_sum);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)reduce_blocks(n_params));
+  cfg.blockDim = dim3(kReduceCols * kReduceWarps);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, reduce_partials_kernel, ws, nb, n_params, inv_scale, dW, sq_sum);
+  if (e != cudaSuccess) return set_error(SXE_ECUDA, "mlp_bwd_reduce: %s", cudaGetErrorString(e));
   return check_launch("mlp_bwd_reduce");
 }
 

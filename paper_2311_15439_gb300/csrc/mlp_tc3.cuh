@@ -147,11 +147,20 @@ __device__ void load_weights_tc3(const T* __restrict__ W, int n_out, unsigned ch
     }
   }
   const T* Wo = W + kW * N_IN + (NH - 1) * kW * kW;
-  for (int i = threadIdx.x; i < 16 * kW; i += S::THREADS) {
-    const int o = i / kW, c = i % kW;
-    const T v = o < n_out ? Wo[o * kW + c] : from_f32<T>(0.f);
-    *cm<T>(sm + S::WO, o, c, kW) = v;
-    *cm<T>(sm + S::WOT, c, o, 16) = v;
+  constexpr int NO = (16 * kW + S::THREADS - 1) / S::THREADS;
+  T wo[NO];
+#pragma unroll
+  for (int j = 0; j < NO; ++j) {
+    const int i = threadIdx.x + j * S::THREADS, o = i / kW;
+    wo[j] = (i < 16 * kW && o < n_out) ? Wo[i] : from_f32<T>(0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < NO; ++j) {
+    const int i = threadIdx.x + j * S::THREADS, o = i / kW, c = i % kW;
+    if (i < 16 * kW) {
+      *cm<T>(sm + S::WO, o, c, kW) = wo[j];
+      *cm<T>(sm + S::WOT, c, o, 16) = wo[j];
+    }
   }
 }
 
@@ -179,6 +188,22 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
   const float inv_scale = 1.f / loss_scale;
   unsigned char* gs = sm + g * S::GROUP;                // this group's buffers
 
+  // the tile's inputs are loaded into registers one tile ahead, each thread its own row
+  constexpr int kPieces = N_IN / 8;
+  uint4 pf[kPieces];
+  auto prefetch = [&](int64_t t) {
+#pragma unroll
+    for (int j = 0; j < kPieces; ++j) {                 // row r, columns 8 j .. 8 j + 7
+      const int64_t row = t * kM + r;
+      pf[j] = (t < n_tiles && row < P) ? __ldg(reinterpret_cast<const uint4*>(in + row * N_IN + 8 * j))
+                                       : make_uint4(0, 0, 0, 0);
+    }
+  };
+  const int64_t stride = (int64_t)G * gridDim.x;
+  // tiles: CTA b takes b, b + grid, b + 2 grid, ... (so that the CTAs' counts differ by at most one)
+  // and its group g every G-th of them, from b + g grid on
+  const int64_t first = (int64_t)blockIdx.x + (int64_t)g * gridDim.x;
+  prefetch(first);                                      // the first tile's loads overlap the set-up
   load_weights_tc3<T, N_IN, NH, S>(W, n_out, sm);
   // NT = 1 (n_out <= 8): the output layer's weights as mma.sync B fragments in registers, by for
   // Y = H W_out^T (n = output gq, k = hidden) and bd for dH = dY W_out (k = output, n = hidden).
@@ -288,20 +313,7 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
     }
   };
 
-  // the tile's inputs are loaded into registers one tile ahead, each thread its own row
-  constexpr int kPieces = N_IN / 8;
-  uint4 pf[kPieces];
-  auto prefetch = [&](int64_t t) {
-#pragma unroll
-    for (int j = 0; j < kPieces; ++j) {                 // row r, columns 8 j .. 8 j + 7
-      const int64_t row = t * kM + r;
-      pf[j] = (t < n_tiles && row < P) ? __ldg(reinterpret_cast<const uint4*>(in + row * N_IN + 8 * j))
-                                       : make_uint4(0, 0, 0, 0);
-    }
-  };
-  const int64_t stride = (int64_t)G * gridDim.x;
-  prefetch((int64_t)G * blockIdx.x + g);
-  for (int64_t tile = (int64_t)G * blockIdx.x + g; tile < n_tiles; tile += stride) {
+  for (int64_t tile = first; tile < n_tiles; tile += stride) {
     const int64_t row0 = tile * kM;
     if (!wait_w()) { failed = true; break; }
 #pragma unroll
@@ -520,6 +532,8 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
 
   // ---- partials: each group's accumulators into its own shared row, then their sum in group
   // order as this CTA's row (every group reaches this point; a failed group left its loop whole)
+  // the reduction of the CTAs' partial rows may be scheduled from here on (it waits for this grid)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (!failed && !wait_w()) failed = true;
   if (failed && (tid & 127) == 0 && err) atomicExch(err, 1);
   tc::fence_before_sync();
