@@ -43,7 +43,7 @@ N_POOL = 8   # distinct resident batches cycled through the timed steps
 # kernels in one ncu capture of this workload, profiles/train_step_image2d_L16_T2^22_P2^18_dram_traffic.md),
 # with the SHA-1 of the kernel sources it was taken on: reported only while those sources are unchanged.
 TRAFFIC = {
-    "encode_bwd": (35.8e6 + 755.5e6, "6db701334defea99e67fdb327a63812a5a022b63",
+    "encode_bwd": (35.8e6 + 755.5e6, "ce99299f167c65a5c0953733d60d2fe2ffe4879f",
                    ("encode.cu", "encode_common.cuh", "lattice.cuh")),
 }
 
@@ -585,29 +585,29 @@ PER_CONFIG = [
 # ``bench.py --profile-encode`` (the volumetric configuration at 2^16 rays x 64 samples there):
 # L2 sector throughput and DRAM throughput as a percentage of their peaks, L2 hit rate, DRAM bytes
 # per point.  Reported only while the kernel sources hash to ENCODE_NCU_SHA.
-ENCODE_NCU_SHA = '6db701334defea99e67fdb327a63812a5a022b63'
+ENCODE_NCU_SHA = 'ce99299f167c65a5c0953733d60d2fe2ffe4879f'
 ENCODE_NCU = {
  "plain_fp32_2d_L8_T2^14_P2^16/simplex_raw/fwd": {
-  "l2_throughput_pct": 22.1,
-  "l2_sectors_pct": 9.5,
-  "dram_throughput_pct": 1.4,
-  "l2_hit_pct": 66.3,
+  "l2_throughput_pct": 21.2,
+  "l2_sectors_pct": 9.1,
+  "dram_throughput_pct": 1.3,
+  "l2_hit_pct": 66.4,
   "dram_bytes_per_point": 13.9,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/simplex_raw/bwd": {
-  "l2_throughput_pct": 16.5,
+  "l2_throughput_pct": 16.6,
   "l2_sectors_pct": 7.9,
   "dram_throughput_pct": 4.9,
   "l2_hit_pct": 47.1,
-  "dram_bytes_per_point": 150.1,
+  "dram_bytes_per_point": 150.0,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/simplex_equal_mem/fwd": {
-  "l2_throughput_pct": 24.8,
-  "l2_sectors_pct": 10.4,
+  "l2_throughput_pct": 24.4,
+  "l2_sectors_pct": 10.3,
   "dram_throughput_pct": 1.5,
-  "l2_hit_pct": 69.1,
+  "l2_hit_pct": 69.0,
   "dram_bytes_per_point": 15.3,
   "points_captured": 65536
  },
@@ -615,112 +615,112 @@ ENCODE_NCU = {
   "l2_throughput_pct": 16.1,
   "l2_sectors_pct": 7.7,
   "dram_throughput_pct": 4.7,
-  "l2_hit_pct": 47.0,
-  "dram_bytes_per_point": 151.3,
+  "l2_hit_pct": 47.2,
+  "dram_bytes_per_point": 151.4,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/grid/fwd": {
-  "l2_throughput_pct": 25.2,
-  "l2_sectors_pct": 10.4,
-  "dram_throughput_pct": 1.4,
-  "l2_hit_pct": 70.9,
+  "l2_throughput_pct": 24.2,
+  "l2_sectors_pct": 10.0,
+  "dram_throughput_pct": 1.3,
+  "l2_hit_pct": 71.0,
   "dram_bytes_per_point": 14.9,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/grid/bwd": {
-  "l2_throughput_pct": 20.6,
-  "l2_sectors_pct": 9.2,
-  "dram_throughput_pct": 4.8,
-  "l2_hit_pct": 48.5,
+  "l2_throughput_pct": 20.4,
+  "l2_sectors_pct": 9.1,
+  "dram_throughput_pct": 4.7,
+  "l2_hit_pct": 48.8,
   "dram_bytes_per_point": 151.0,
   "points_captured": 65536
  },
  "image_2d_L16_T2^22_fp16_P2^18/simplex_raw/fwd": {
-  "l2_throughput_pct": 50.0,
-  "l2_sectors_pct": 36.7,
-  "dram_throughput_pct": 70.2,
+  "l2_throughput_pct": 50.4,
+  "l2_sectors_pct": 37.0,
+  "dram_throughput_pct": 70.6,
   "l2_hit_pct": 28.6,
-  "dram_bytes_per_point": 1225.1,
+  "dram_bytes_per_point": 1224.7,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/simplex_raw/bwd": {
-  "l2_throughput_pct": 23.5,
+  "l2_throughput_pct": 23.6,
   "l2_sectors_pct": 11.9,
-  "dram_throughput_pct": 33.1,
+  "dram_throughput_pct": 33.2,
   "l2_hit_pct": 29.6,
-  "dram_bytes_per_point": 1968.6,
+  "dram_bytes_per_point": 1967.3,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/simplex_equal_mem/fwd": {
-  "l2_throughput_pct": 49.7,
-  "l2_sectors_pct": 36.8,
-  "dram_throughput_pct": 71.9,
-  "l2_hit_pct": 27.4,
-  "dram_bytes_per_point": 1318.6,
+  "l2_throughput_pct": 50.0,
+  "l2_sectors_pct": 37.0,
+  "dram_throughput_pct": 72.2,
+  "l2_hit_pct": 27.5,
+  "dram_bytes_per_point": 1318.8,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/simplex_equal_mem/bwd": {
-  "l2_throughput_pct": 24.5,
-  "l2_sectors_pct": 12.0,
-  "dram_throughput_pct": 34.4,
-  "l2_hit_pct": 28.9,
-  "dram_bytes_per_point": 2062.2,
+  "l2_throughput_pct": 24.4,
+  "l2_sectors_pct": 11.9,
+  "dram_throughput_pct": 34.2,
+  "l2_hit_pct": 29.0,
+  "dram_bytes_per_point": 2063.8,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/grid/fwd": {
-  "l2_throughput_pct": 51.5,
-  "l2_sectors_pct": 37.2,
-  "dram_throughput_pct": 71.2,
-  "l2_hit_pct": 29.0,
-  "dram_bytes_per_point": 1351.0,
+  "l2_throughput_pct": 49.4,
+  "l2_sectors_pct": 35.8,
+  "dram_throughput_pct": 68.7,
+  "l2_hit_pct": 28.8,
+  "dram_bytes_per_point": 1351.2,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/grid/bwd": {
   "l2_throughput_pct": 26.4,
   "l2_sectors_pct": 12.6,
-  "dram_throughput_pct": 32.0,
+  "dram_throughput_pct": 31.8,
   "l2_hit_pct": 33.7,
-  "dram_bytes_per_point": 2197.4,
+  "dram_bytes_per_point": 2196.5,
   "points_captured": 262144
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/simplex_raw/fwd": {
-  "l2_throughput_pct": 70.7,
-  "l2_sectors_pct": 25.6,
-  "dram_throughput_pct": 4.0,
+  "l2_throughput_pct": 63.0,
+  "l2_sectors_pct": 22.8,
+  "dram_throughput_pct": 3.5,
   "l2_hit_pct": 90.0,
   "dram_bytes_per_point": 54.6,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/simplex_raw/bwd": {
-  "l2_throughput_pct": 70.6,
-  "l2_sectors_pct": 25.6,
+  "l2_throughput_pct": 70.8,
+  "l2_sectors_pct": 25.7,
   "dram_throughput_pct": 11.5,
-  "l2_hit_pct": 55.1,
-  "dram_bytes_per_point": 329.7,
+  "l2_hit_pct": 55.2,
+  "dram_bytes_per_point": 329.8,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/simplex_equal_mem/fwd": {
-  "l2_throughput_pct": 71.7,
-  "l2_sectors_pct": 25.9,
-  "dram_throughput_pct": 4.2,
+  "l2_throughput_pct": 64.6,
+  "l2_sectors_pct": 23.3,
+  "dram_throughput_pct": 3.8,
   "l2_hit_pct": 90.3,
-  "dram_bytes_per_point": 60.6,
+  "dram_bytes_per_point": 60.7,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/simplex_equal_mem/bwd": {
-  "l2_throughput_pct": 76.8,
-  "l2_sectors_pct": 27.0,
+  "l2_throughput_pct": 77.0,
+  "l2_sectors_pct": 27.1,
   "dram_throughput_pct": 7.2,
   "l2_hit_pct": 61.4,
-  "dram_bytes_per_point": 193.9,
+  "dram_bytes_per_point": 193.7,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/grid/fwd": {
-  "l2_throughput_pct": 75.7,
-  "l2_sectors_pct": 26.3,
-  "dram_throughput_pct": 2.3,
-  "l2_hit_pct": 94.7,
-  "dram_bytes_per_point": 59.4,
+  "l2_throughput_pct": 67.7,
+  "l2_sectors_pct": 23.6,
+  "dram_throughput_pct": 2.2,
+  "l2_hit_pct": 94.4,
+  "dram_bytes_per_point": 59.2,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/grid/bwd": {
@@ -728,31 +728,31 @@ ENCODE_NCU = {
   "l2_sectors_pct": 25.9,
   "dram_throughput_pct": 6.3,
   "l2_hit_pct": 59.4,
-  "dram_bytes_per_point": 335.5,
+  "dram_bytes_per_point": 335.6,
   "points_captured": 1048576
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_raw/fwd": {
-  "l2_throughput_pct": 68.1,
-  "l2_sectors_pct": 24.5,
-  "dram_throughput_pct": 6.3,
+  "l2_throughput_pct": 58.9,
+  "l2_sectors_pct": 21.2,
+  "dram_throughput_pct": 5.5,
   "l2_hit_pct": 89.9,
-  "dram_bytes_per_point": 70.7,
+  "dram_bytes_per_point": 70.6,
   "points_captured": 4194304
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_raw/bwd": {
   "l2_throughput_pct": 63.9,
   "l2_sectors_pct": 23.1,
   "dram_throughput_pct": 9.4,
-  "l2_hit_pct": 54.4,
+  "l2_hit_pct": 54.5,
   "dram_bytes_per_point": 293.0,
   "points_captured": 4194304
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_equal_mem/fwd": {
-  "l2_throughput_pct": 70.3,
-  "l2_sectors_pct": 25.2,
-  "dram_throughput_pct": 6.0,
+  "l2_throughput_pct": 61.4,
+  "l2_sectors_pct": 22.0,
+  "dram_throughput_pct": 5.2,
   "l2_hit_pct": 90.8,
-  "dram_bytes_per_point": 72.0,
+  "dram_bytes_per_point": 71.9,
   "points_captured": 4194304
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_equal_mem/bwd": {
@@ -760,14 +760,14 @@ ENCODE_NCU = {
   "l2_sectors_pct": 27.3,
   "dram_throughput_pct": 5.9,
   "l2_hit_pct": 62.1,
-  "dram_bytes_per_point": 153.7,
+  "dram_bytes_per_point": 153.8,
   "points_captured": 4194304
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/grid/fwd": {
-  "l2_throughput_pct": 76.4,
-  "l2_sectors_pct": 26.5,
+  "l2_throughput_pct": 60.0,
+  "l2_sectors_pct": 21.0,
   "dram_throughput_pct": 3.4,
-  "l2_hit_pct": 95.0,
+  "l2_hit_pct": 93.7,
   "dram_bytes_per_point": 71.7,
   "points_captured": 4194304
  },
@@ -996,14 +996,17 @@ def _predict(tr, x):
     return tr.mlp.mlp_fwd(tr.W_lowp, enc)
 
 
-def fit_quality(dev, image_steps=5000, sdf_steps=2000):
+def fit_quality(dev, image_steps=5000, sdf_steps=2000, repeats=5):
     """Quality at equal table size (Sec. 6.1): the image workload (L=16, F=2, T=2^22 fp16, network
     32-64-64-3, 2^18 points per step, Adam) trained for ``image_steps`` steps with each encoder, and
     the PSNR of its prediction (clipped to [0, 1]) over 2^18 held-out pixel centres against the FP64
     image; the SDF-style workload (d=3, T=2^19 bf16, network 32-64-1, 2^20 points per step) trained
     for ``sdf_steps`` steps, and its mean squared SDF error on 2^18 held-out points of the same
     distribution (half uniform, half within 0.01 of the surface).  Training batches are drawn on
-    the device by torch from seeded generators; the step time excludes drawing them."""
+    the device by torch from seeded generators; the step time excludes drawing them.  Each fit runs
+    ``repeats`` times with different batch seeds (the same initial tables and network): the table
+    gradients are summed by atomics in no fixed order, so runs diverge, and the final error of one
+    run spreads by several dB; the record gives the median and the range."""
     import torch
     from paper_2311_15439_gb300 import synth
     from paper_2311_15439_gb300.api import Encoder, Mlp
@@ -1016,20 +1019,27 @@ def fit_quality(dev, image_steps=5000, sdf_steps=2000):
     res = {"steps": image_steps, "points_per_step": BATCH, "eval_pixels": 1 << 18,
            "config": "d=2 L=16 F=2 T=2^22 fp16 base 16 growth 2.0, network 32-64-64-3 fp16"}
     for kind, mode in VARIANTS:
-        enc = Encoder(**CFG, kind=kind, res_mode=mode, table_dtype="f16")
-        tr = Trainer(enc, Mlp(32, N_OUT, n_hidden=2, dtype="f16"), BATCH, seed=0, device=dev, table_layout="records")
-        gen = torch.Generator(device=dev).manual_seed(2024)
+        runs = []
+        for rep in range(repeats):
+            enc = Encoder(**CFG, kind=kind, res_mode=mode, table_dtype="f16")
+            tr = Trainer(enc, Mlp(32, N_OUT, n_hidden=2, dtype="f16"), BATCH, seed=0, device=dev,
+                         table_layout="records")
+            gen = torch.Generator(device=dev).manual_seed(2024 + rep)
 
-        def batch():
-            x = torch.rand((BATCH, 2), generator=gen, device=dev)
-            return x, img.sample_torch(x)
-        sec = _train_fixed_steps(dev, tr, image_steps, batch)
-        y = np.clip(_predict(tr, xe).cpu().numpy().astype(np.float64), 0.0, 1.0)
-        mse = float(np.mean((y - t_eval) ** 2))
-        res[vname(kind, mode)] = {"res_mode": mode, "psnr_db": 10.0 * math.log10(1.0 / mse), "train_s": sec,
-                                  "final_batch_loss": tr.loss()}
-        del tr
-        torch.cuda.empty_cache()
+            def batch():
+                x = torch.rand((BATCH, 2), generator=gen, device=dev)
+                return x, img.sample_torch(x)
+            sec = _train_fixed_steps(dev, tr, image_steps, batch)
+            y = np.clip(_predict(tr, xe).cpu().numpy().astype(np.float64), 0.0, 1.0)
+            mse = float(np.mean((y - t_eval) ** 2))
+            runs.append((10.0 * math.log10(1.0 / mse), sec, tr.loss()))
+            del tr
+            torch.cuda.empty_cache()
+        psnr = [r[0] for r in runs]
+        res[vname(kind, mode)] = {"res_mode": mode, "psnr_db": float(np.median(psnr)),
+                                  "psnr_db_min": min(psnr), "psnr_db_max": max(psnr), "runs": repeats,
+                                  "train_s": float(np.median([r[1] for r in runs])),
+                                  "final_batch_loss": float(np.median([r[2] for r in runs]))}
     out["image"] = res
     scene = synth.SphereTorusScene(5)
     xs_eval = scene.sample(1 << 18, 4343)
@@ -1039,21 +1049,27 @@ def fit_quality(dev, image_steps=5000, sdf_steps=2000):
     res = {"steps": sdf_steps, "points_per_step": P, "eval_points": 1 << 18,
            "config": "d=3 L=16 F=2 T=2^19 bf16 base 16 growth 1.38, network 32-64-1 bf16"}
     for kind, mode in VARIANTS:
-        enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, res_mode=mode, table_dtype="bf16")
-        tr = Trainer(enc, Mlp(32, 1, n_hidden=1, dtype="bf16"), P, seed=6, device=dev)
-        gen = torch.Generator(device=dev).manual_seed(2025)
+        runs = []
+        for rep in range(repeats):
+            enc = Encoder(3, 16, 2, 19, 16.0, 1.38, kind=kind, res_mode=mode, table_dtype="bf16")
+            tr = Trainer(enc, Mlp(32, 1, n_hidden=1, dtype="bf16"), P, seed=6, device=dev)
+            gen = torch.Generator(device=dev).manual_seed(2025 + rep)
 
-        def batch():
-            x = scene.sample_torch(P, gen)
-            return x, scene.sdf_torch(x)
-        sec = _train_fixed_steps(dev, tr, sdf_steps, batch)
-        err = _predict(tr, xse).cpu().numpy().astype(np.float64) - s_eval
-        near = np.abs(s_eval[:, 0]) < 0.01
-        res[vname(kind, mode)] = {"res_mode": mode, "eval_mse": float(np.mean(err ** 2)),
-                                  "eval_mae_near_surface": float(np.mean(np.abs(err[near]))), "train_s": sec,
-                                  "final_batch_loss": tr.loss()}
-        del tr
-        torch.cuda.empty_cache()
+            def batch():
+                x = scene.sample_torch(P, gen)
+                return x, scene.sdf_torch(x)
+            sec = _train_fixed_steps(dev, tr, sdf_steps, batch)
+            err = _predict(tr, xse).cpu().numpy().astype(np.float64) - s_eval
+            near = np.abs(s_eval[:, 0]) < 0.01
+            runs.append((float(np.mean(err ** 2)), float(np.mean(np.abs(err[near]))), sec, tr.loss()))
+            del tr
+            torch.cuda.empty_cache()
+        mse = [r[0] for r in runs]
+        res[vname(kind, mode)] = {"res_mode": mode, "eval_mse": float(np.median(mse)), "eval_mse_min": min(mse),
+                                  "eval_mse_max": max(mse), "runs": repeats,
+                                  "eval_mae_near_surface": float(np.median([r[1] for r in runs])),
+                                  "train_s": float(np.median([r[2] for r in runs])),
+                                  "final_batch_loss": float(np.median([r[3] for r in runs]))}
     out["sdf"] = res
     return out
 
