@@ -473,6 +473,14 @@ int32_t sxe_mlp_get_kernel(void);
  * valid).  Synchronous; clears the word when `clear` is nonzero. */
 sxe_status sxe_device_error(int32_t* flag, int32_t clear);
 
+/* Diagnostic of the bounded waits: runs, on `stream`, one mbarrier wait of the kind every
+ * tcgen05 kernel of the library uses (suspended polls, given up after `limit_ns` nanoseconds of
+ * global time).  With expect_timeout != 0 nothing ever arrives on the barrier, so the wait gives up
+ * and raises the device error word (read it with sxe_device_error); with expect_timeout == 0 the
+ * barrier's phase completes first and the word is left as it is.  Either way the kernel returns
+ * and the context stays usable.  limit_ns must lie in (0, 2e9]: SXE_EINVAL otherwise. */
+sxe_status sxe_selftest_wait(int32_t expect_timeout, int64_t limit_ns, void* stream);
+
 /* Thread-local message describing the last failing call on this thread ("" if none). */
 const char* sxe_last_error(void);
 

@@ -33,7 +33,7 @@ EXPORTS = (
     "sxe_mlp_n_params", "sxe_mlp_fwd", "sxe_mlp_bwd_workspace_bytes", "sxe_mlp_bwd", "sxe_mlp_train_l2",
     "sxe_loss_l2", "sxe_step", "sxe_step_touched", "sxe_last_error", "sxe_version",
     "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped", "sxe_mlp_train_l2_part",
-    "sxe_mlp_set_kernel", "sxe_mlp_get_kernel", "sxe_device_error",
+    "sxe_mlp_set_kernel", "sxe_mlp_get_kernel", "sxe_device_error", "sxe_selftest_wait",
 )
 
 
@@ -102,6 +102,7 @@ def _declare(L):
         "sxe_mlp_set_kernel": (i32, [i32]),
         "sxe_mlp_get_kernel": (i32, []),
         "sxe_device_error": (i32, [ctypes.POINTER(i32), i32]),
+        "sxe_selftest_wait": (i32, [i32, i64, vp]),
         "sxe_last_error": (ctypes.c_char_p, []),
         "sxe_version": (ctypes.c_char_p, []),
     }

@@ -486,6 +486,12 @@ sxe_status sxe_mlp_set_kernel(int32_t k) {
 
 int32_t sxe_mlp_get_kernel(void) { return g_mlp_kernel; }
 
+sxe_status sxe_selftest_wait(int32_t expect_timeout, int64_t limit_ns, void* stream) {
+  if (!(limit_ns > 0 && limit_ns <= 2000000000ll))
+    return set_error(SXE_EINVAL, "selftest_wait: limit_ns=%lld outside (0, 2e9]", (long long)limit_ns);
+  return launch_selftest_wait(expect_timeout != 0, limit_ns, (cudaStream_t)stream);
+}
+
 sxe_status sxe_device_error(int32_t* flag, int32_t clear) {
   if (!flag) return set_error(SXE_EINVAL, "device_error: NULL flag");
   return read_tc_error(flag, clear != 0);

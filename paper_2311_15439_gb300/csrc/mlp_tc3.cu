@@ -27,6 +27,28 @@ int* tc3_error_word() {
   return g_err_ptr[dev];
 }
 
+namespace {
+
+// One bounded wait on a fresh mbarrier: with `timeout` set nobody arrives, so the wait runs out
+__global__ void selftest_wait_kernel(int timeout, uint64_t limit_ns, int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar, 1);
+    if (!timeout) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(&mbar)) : "memory");
+    const bool ok = tc::mbar_wait_sleep(&mbar, 0, 20000u, limit_ns, 1u << 20);
+    if (!ok && err) atomicExch(err, 1);
+  }
+}
+
+}  // namespace
+
+sxe_status launch_selftest_wait(int timeout, int64_t limit_ns, cudaStream_t s) {
+  int* err = tc3_error_word();
+  if (!err) return set_error(SXE_ECUDA, "selftest_wait: no device error word");
+  selftest_wait_kernel<<<1, 32, 0, s>>>(timeout, (uint64_t)limit_ns, err);
+  return check_launch("selftest_wait");
+}
+
 bool mlp_tc3_applies(const sxe_mlp_desc* d) { return d->n_out <= 16; }
 
 sxe_status launch_mlp_bwd_tc3(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,

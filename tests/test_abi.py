@@ -70,6 +70,13 @@ def test_encoder_create_rejects_bad_descriptions(L, bad, status):
     assert L.lib().sxe_last_error()
 
 
+def test_selftest_wait_checks_its_limit_on_the_host(L):
+    lib = L.lib()
+    assert lib.sxe_selftest_wait(1, 0, None) == -1
+    assert lib.sxe_selftest_wait(1, -5, None) == -1
+    assert lib.sxe_selftest_wait(0, 3_000_000_000, None) == -1
+
+
 def test_entry_points_validate_before_launch(L):
     lib = L.lib()
     st, h = _create(L)

@@ -354,3 +354,35 @@ def test_adam_touched_full_size_table(cuda_lib):
     tab = table[idx].cpu().numpy()
     np.testing.assert_array_equal(tab[was_marked], after[was_marked, :F].astype(np.float16))
     assert was_marked.sum() > 15_000 and (~was_marked).sum() > 150_000
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(cuda_lib):
+    """The bounded mbarrier wait every tcgen05 kernel uses, on a barrier nothing arrives at: it
+    gives up after its limit (50 ms here) and raises the device error word instead of hanging; the
+    word clears, a wait whose phase completes leaves it clear, and the network's training pass
+    still runs and matches its own earlier result afterwards."""
+    import ctypes
+    import time
+    L = cuda_lib
+    lib = L.lib()
+    mlp, Wd, Ws, xd, x = _setup(NETS[0], seed=41)
+    dy = torch.from_numpy(synth.normal_grads(x.shape[0], NETS[0][2], 42)).cuda()
+    before = torch.zeros((mlp.n_params,), device="cuda")
+    mlp.mlp_bwd(Wd, xd, dy, before)
+    torch.cuda.synchronize()
+    flag = ctypes.c_int32(0)
+    assert lib.sxe_device_error(ctypes.byref(flag), 1) == 0 and flag.value == 0
+    t0 = time.perf_counter()
+    assert lib.sxe_selftest_wait(1, 50_000_000, None) == 0
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 >= 0.045                      # it waited out its limit
+    assert lib.sxe_device_error(ctypes.byref(flag), 1) == 0 and flag.value == 1
+    assert lib.sxe_device_error(ctypes.byref(flag), 0) == 0 and flag.value == 0   # cleared
+    assert lib.sxe_selftest_wait(0, 50_000_000, None) == 0
+    torch.cuda.synchronize()
+    assert lib.sxe_device_error(ctypes.byref(flag), 1) == 0 and flag.value == 0
+    after = torch.zeros((mlp.n_params,), device="cuda")
+    mlp.mlp_bwd(Wd, xd, dy, after)
+    torch.cuda.synchronize()
+    assert torch.equal(before, after)
+    assert lib.sxe_device_error(ctypes.byref(flag), 1) == 0 and flag.value == 0
