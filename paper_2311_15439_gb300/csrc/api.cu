@@ -37,6 +37,7 @@ sxe_status check_launch(const char* what) {
 static std::mutex g_setup_mu;
 static std::map<int, int> g_sms;
 static std::map<std::tuple<int, const void*, int, int>, int> g_ctas;
+static std::map<std::pair<int, const void*>, int> g_smem_limit;   // dynamic shared-memory limit set per kernel
 
 static int current_device() {
   int dev = 0;
@@ -61,7 +62,13 @@ int kernel_ctas_per_sm(const void* kernel, int threads, int smem_bytes) {
   std::lock_guard<std::mutex> lock(g_setup_mu);
   auto it = g_ctas.find(key);
   if (it != g_ctas.end()) return it->second;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  // the kernel's dynamic shared-memory limit only ever grows, so that a launch set up earlier
+  // with a larger size keeps working after a smaller one is set up
+  int& limit = g_smem_limit[std::make_pair(dev, kernel)];
+  if (smem_bytes > limit) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    limit = smem_bytes;
+  }
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, (size_t)smem_bytes) != cudaSuccess || n < 1)
     n = 1;
