@@ -1159,7 +1159,7 @@ def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5, repeats=3, sweep=(2
     which every request of a stream is queued at once, so that the GPU never waits for arrivals."""
     import torch
     from paper_2311_15439_gb300 import synth
-    from paper_2311_15439_gb300.serve import FieldServer, make_field, poisson_load, run_load
+    from paper_2311_15439_gb300.serve import FieldServer, NativeFieldServer, make_field, poisson_load, run_load
     sys.setswitchinterval(2e-4)          # let the scheduler thread take the GIL promptly
     dims = (2, 3, 4, 5)
     pools = {d: torch.from_numpy(synth.uniform_points(4 << 20, d, 900 + d)).pin_memory() for d in dims}
@@ -1179,7 +1179,8 @@ def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5, repeats=3, sweep=(2
 
     for kind, mode in VARIANTS:
         fields = {d: make_field(d, kind=kind, res_mode=mode, seed=d, device=dev) for d in dims}
-        srv = FieldServer(fields, mem_budget_bytes=4 << 30, n_slots=4, max_batch_points=4 << 20, device=dev).start()
+        srv = NativeFieldServer(fields, mem_budget_bytes=4 << 30, n_slots=4, max_batch_points=4 << 20,
+                                device=dev).start()
         for d in dims:                   # warm-up: one request per d (allocator, pinned buffers, kernel load)
             if not srv.submit(d, pools[d][:65536]).wait(120.0):
                 raise TimeoutError("serving warm-up request did not complete")
@@ -1201,6 +1202,18 @@ def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5, repeats=3, sweep=(2
     for m in ("raw", "equal_mem"):
         out["simplex_over_grid_capacity_" + m] = (out[vname("simplex", m)]["capacity_points_per_s"]
                                                    / out["grid"]["capacity_points_per_s"])
+    # the same load through the Python scheduler (simplex, raw), for comparison with the library's
+    fields = {d: make_field(d, seed=d, device=dev) for d in dims}
+    srv = FieldServer(fields, mem_budget_bytes=4 << 30, n_slots=4, max_batch_points=4 << 20, device=dev).start()
+    for d in dims:
+        if not srv.submit(d, pools[d][:65536]).wait(120.0):
+            raise TimeoutError("serving warm-up request did not complete")
+    runs = [one_run(srv, rate_hz, n_requests, seed + r) for r in range(repeats)]
+    srv.stop()
+    out["python_scheduler_simplex_raw"] = {"p50_ms": float(np.median([r["p50_ms"] for r in runs])),
+                                           "p99_ms": float(np.median([r["p99_ms"] for r in runs]))}
+    out["scheduler"] = ("library (sxe_server_*: C++ scheduler thread, 4 stream slots, batches of <= 2^20 points on "
+                        "high-priority streams, host-callback completion); python_scheduler_* is serve.FieldServer")
     return out
 
 

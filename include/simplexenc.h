@@ -473,6 +473,63 @@ int32_t sxe_mlp_get_kernel(void);
  * valid).  Synchronous; clears the word when `clear` is nonzero. */
 sxe_status sxe_device_error(int32_t* flag, int32_t clear);
 
+/* ---- Serving: a native continuous-batching query loop for trained fields --------------
+ *
+ * A server answers queries "value of the field of dimension d at these points" (the forward
+ * encoding, Sec. 5 a-d, then the network's forward pass) for up to one field per dimension
+ * d = 2..5.  One scheduler thread owns the GPU work:
+ *   - continuous batching: queued requests of the same d are merged in arrival order, up to
+ *     max_batch_points, into one batch whenever a stream slot is free;
+ *   - admission by memory: a batch runs only if its device buffers (points, encoding, values)
+ *     fit in the caller's arena next to the batches in flight, else it waits for completions;
+ *   - overlap: each batch runs on its own stream slot (host-to-device copies of its requests'
+ *     points, the two kernels, device-to-host copies of the values), and a host callback on that
+ *     stream completes its requests;
+ *   - priority: a slot has a high- and a normal-priority stream; small batches take the first,
+ *     so the GPU's block scheduler serves them ahead of the blocks of large ones.
+ * A point's value depends only on that point, so a merged request's values equal those it gets
+ * alone.  The library allocates no device memory: the arena is the caller's. */
+typedef struct sxe_server sxe_server;
+typedef struct {
+  void* arena;                /* device buffer the batches' buffers are carved from (caller-owned) */
+  int64_t arena_bytes;        /* its size: the admission budget */
+  int32_t n_slots;            /* batches in flight at most (one CUDA stream each), 1..16 */
+  int64_t max_batch_points;   /* largest merged batch (and largest request), >= 1 */
+  int64_t priority_points;    /* batches of at most this many points run on high-priority streams,
+                                 so that small queries overtake large ones at block boundaries
+                                 (0: every batch at normal priority) */
+} sxe_server_desc;
+
+/* Creates a stopped server on the current device (streams created here). */
+sxe_status sxe_server_create(const sxe_server_desc* desc, sxe_server** out);
+/* Registers the field of dimension enc's d: its encoder, low-precision tables [L][T][F] (device),
+ * network and weights (device).  The encoder's output type must be the network's dtype and its
+ * L*F outputs the network's inputs.  Before sxe_server_start only; the handles and buffers must
+ * outlive the server. */
+sxe_status sxe_server_add_field(sxe_server* srv, const sxe_encoder* enc, const void* tables,
+                                const sxe_mlp_desc* mlp, const void* weights);
+sxe_status sxe_server_start(sxe_server* srv);
+/* Queues a request: n_points points x_host [n][d] binary32 and their values y_host [n][n_out]
+ * binary32, both host memory (pinned for asynchronous copies) that must stay valid until the
+ * request completes.  *request_id receives its id.  SXE_EINVAL (and no request) for a stopped
+ * server, an unknown d, n_points < 1 or above max_batch_points, a request whose buffers could
+ * never fit in the arena, or NULL buffers.  Thread-safe. */
+sxe_status sxe_server_submit(sxe_server* srv, int32_t d, const float* x_host, int64_t n_points,
+                             float* y_host, int64_t* request_id);
+/* Waits up to timeout_us microseconds (0: just polls) for a request.  *state: 0 still pending,
+ * 1 done (y_host holds its values), 2 failed (sxe_last_error says why).  For states 1 and 2,
+ * *latency_s (optional) receives submit-to-completion time in seconds and the id is retired.
+ * Thread-safe; releases no GIL of its own (callers from Python should not hold one). */
+sxe_status sxe_server_wait(sxe_server* srv, int64_t request_id, int64_t timeout_us, int32_t* state,
+                           double* latency_s);
+/* Stops the scheduler: with drain != 0 after every queued request has run, else queued
+ * requests fail; batches in flight always complete. */
+sxe_status sxe_server_stop(sxe_server* srv, int32_t drain);
+/* Batches launched so far and the largest arena footprint in flight. */
+sxe_status sxe_server_stats(const sxe_server* srv, int64_t* n_batches, int64_t* peak_bytes);
+/* Stops (draining) if running, waits for its streams and releases the server. */
+sxe_status sxe_server_destroy(sxe_server* srv);
+
 /* Diagnostic of the bounded waits: runs, on `stream`, one mbarrier wait of the kind every
  * tcgen05 kernel of the library uses (suspended polls, given up after `limit_ns` nanoseconds of
  * global time).  With expect_timeout != 0 nothing ever arrives on the barrier, so the wait gives up

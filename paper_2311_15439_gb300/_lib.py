@@ -34,6 +34,8 @@ EXPORTS = (
     "sxe_loss_l2", "sxe_step", "sxe_step_touched", "sxe_last_error", "sxe_version",
     "sxe_mlp_train_l2_static", "sxe_mlp_train_l2_grouped", "sxe_mlp_train_l2_part",
     "sxe_mlp_set_kernel", "sxe_mlp_get_kernel", "sxe_device_error", "sxe_selftest_wait",
+    "sxe_server_create", "sxe_server_add_field", "sxe_server_start", "sxe_server_submit", "sxe_server_wait",
+    "sxe_server_stop", "sxe_server_stats", "sxe_server_destroy",
 )
 
 
@@ -52,6 +54,11 @@ class MlpDesc(ctypes.Structure):
 class AdamDesc(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("skip_zero_grad", ctypes.c_int32)]
+
+
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_int64), ("n_slots", ctypes.c_int32),
+                ("max_batch_points", ctypes.c_int64), ("priority_points", ctypes.c_int64)]
 
 
 _lib = None
@@ -103,6 +110,14 @@ def _declare(L):
         "sxe_mlp_get_kernel": (i32, []),
         "sxe_device_error": (i32, [ctypes.POINTER(i32), i32]),
         "sxe_selftest_wait": (i32, [i32, i64, vp]),
+        "sxe_server_create": (i32, [ctypes.POINTER(ServerDesc), ctypes.POINTER(vp)]),
+        "sxe_server_add_field": (i32, [vp, vp, vp, M, vp]),
+        "sxe_server_start": (i32, [vp]),
+        "sxe_server_submit": (i32, [vp, i32, vp, i64, vp, ctypes.POINTER(i64)]),
+        "sxe_server_wait": (i32, [vp, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]),
+        "sxe_server_stop": (i32, [vp, i32]),
+        "sxe_server_stats": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "sxe_server_destroy": (i32, [vp]),
         "sxe_last_error": (ctypes.c_char_p, []),
         "sxe_version": (ctypes.c_char_p, []),
     }

@@ -1,5 +1,10 @@
 """Continuous-batching query server for trained fields (encoding + network resident on the GPU).
 
+Two implementations of the same loop: ``NativeFieldServer`` runs it in the library
+(``sxe_server_*``: a C++ scheduler thread, stream slots with high- and normal-priority streams,
+completion by host callbacks; the production path) and ``FieldServer`` below in Python (the
+readable form, kept as a reference and for comparison).
+
 Requests carry a dimension d and a block of points in pinned host memory; the answer is
 the field value at each point (``sxe_encode_fwd`` then ``sxe_mlp_fwd``).  One scheduler
 thread owns the GPU work:
@@ -235,6 +240,119 @@ class FieldServer:
             if not progressed:
                 self.wake.wait(timeout=5e-5)
                 self.wake.clear()
+
+
+class NativeRequest:
+    """A request of ``NativeFieldServer``: same interface as ``Request`` (wait, latency, y, error)."""
+
+    def __init__(self, server, d: int, x: torch.Tensor, y: torch.Tensor, rid: int | None, error: str | None = None):
+        self.server, self.d, self.x, self.y, self.rid = server, d, x, y, rid
+        self.error = error
+        self._latency = 0.0 if error is not None else None
+
+    @property
+    def n_points(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def latency(self) -> float:
+        return self._latency
+
+    def wait(self, timeout: float | None = None) -> bool:
+        """True once the request has completed (or failed); its latency is measured in the
+        library, from submission to the completion callback."""
+        if self._latency is not None:
+            return True
+        import ctypes
+        from . import _lib as L
+        state, lat = ctypes.c_int32(0), ctypes.c_double(0.0)
+        t_us = -1 if timeout is None else int(timeout * 1e6)
+        while True:
+            step = 1_000_000 if t_us < 0 else max(0, min(t_us, 1_000_000))
+            L.check(L.lib().sxe_server_wait(self.server._h, self.rid, step, ctypes.byref(state), ctypes.byref(lat)),
+                    "sxe_server_wait")
+            if state.value != 0:
+                self._latency = lat.value
+                if state.value == 2:
+                    self.error = L.lib().sxe_last_error().decode(errors="replace")
+                return True
+            if t_us >= 0:
+                t_us -= step
+                if t_us <= 0:
+                    return False
+
+
+class NativeFieldServer:
+    """The same serving loop as ``FieldServer`` run by the library (``sxe_server_*``): a native
+    scheduler thread, the batches' buffers carved from one device arena of ``mem_budget_bytes``
+    (allocated here by torch), a stream per slot and a host callback completing each batch;
+    batches of at most ``priority_points`` points run on high-priority streams.
+    ``submit`` answers a request the library refuses (unknown d, malformed, oversize) with a
+    request that carries the error, as ``FieldServer`` does."""
+
+    def __init__(self, fields: dict[int, Field], *, mem_budget_bytes: int = 2 << 30, n_slots: int = 4,
+                 max_batch_points: int = 1 << 22, priority_points: int = 1 << 20, device="cuda"):
+        import ctypes
+        from . import _lib as L
+        self.fields = fields
+        self.device = torch.device(device)
+        self._L = L.lib()                   # kept for __del__, which may run at interpreter exit
+        self.arena = torch.empty((int(mem_budget_bytes),), dtype=torch.uint8, device=self.device)
+        desc = L.ServerDesc(self.arena.data_ptr(), int(mem_budget_bytes), int(n_slots), int(max_batch_points),
+                            int(priority_points))
+        h = ctypes.c_void_p()
+        L.check(L.lib().sxe_server_create(ctypes.byref(desc), ctypes.byref(h)), "sxe_server_create")
+        self._h = h
+        for d, f in fields.items():
+            L.check(L.lib().sxe_server_add_field(h, f.encoder._h, f.tables.data_ptr(), ctypes.byref(f.mlp.desc),
+                                                 f.weights.data_ptr()), "sxe_server_add_field")
+
+    def start(self):
+        from . import _lib as L
+        L.check(L.lib().sxe_server_start(self._h), "sxe_server_start")
+        return self
+
+    def submit(self, d: int, x_host: torch.Tensor, y_host: torch.Tensor | None = None) -> NativeRequest:
+        import ctypes
+        from . import _lib as L
+        f = self.fields.get(d)
+        if (f is None or x_host.dim() != 2 or x_host.shape[1] != d or x_host.dtype != torch.float32
+                or not x_host.is_contiguous() or x_host.shape[0] == 0):
+            return NativeRequest(self, d, x_host, None, None, error="no field of dimension %d, or malformed / empty "
+                                                                     "points" % d)
+        if y_host is None or tuple(y_host.shape) != (x_host.shape[0], f.mlp.n_out):
+            y_host = torch.empty((x_host.shape[0], f.mlp.n_out), dtype=torch.float32, pin_memory=True)
+        rid = ctypes.c_int64(-1)
+        st = L.lib().sxe_server_submit(self._h, int(d), x_host.data_ptr(), int(x_host.shape[0]), y_host.data_ptr(),
+                                       ctypes.byref(rid))
+        if st != L.SXE_OK:
+            return NativeRequest(self, d, x_host, y_host, None, error=L.lib().sxe_last_error().decode(errors="replace"))
+        return NativeRequest(self, d, x_host, y_host, rid.value)
+
+    def stop(self, drain: bool = True):
+        from . import _lib as L
+        L.check(L.lib().sxe_server_stop(self._h, 1 if drain else 0), "sxe_server_stop")
+
+    def _stats(self):
+        import ctypes
+        from . import _lib as L
+        nb, peak = ctypes.c_int64(0), ctypes.c_int64(0)
+        L.check(L.lib().sxe_server_stats(self._h, ctypes.byref(nb), ctypes.byref(peak)), "sxe_server_stats")
+        return nb.value, peak.value
+
+    @property
+    def n_batches(self) -> int:
+        return self._stats()[0]
+
+    @property
+    def peak_used(self) -> int:
+        return self._stats()[1]
+
+    def __del__(self):
+        h, lib = getattr(self, "_h", None), getattr(self, "_L", None)
+        if h is not None and h.value and lib is not None:
+            lib.sxe_server_destroy(h)
+            self._h = None
 
 
 def make_field(d: int, *, n_levels=16, n_features=2, log2_T=19, base_res=16.0, growth=1.38, kind="simplex",

@@ -70,6 +70,26 @@ def test_encoder_create_rejects_bad_descriptions(L, bad, status):
     assert L.lib().sxe_last_error()
 
 
+def test_server_entry_points_validate_on_the_host(L):
+    import ctypes
+    lib = L.lib()
+    h = ctypes.c_void_p()
+    assert lib.sxe_server_create(None, ctypes.byref(h)) == -1
+    for arena, nbytes, slots, maxb, prio in ((None, 1 << 20, 2, 100, 0), (4096 + 16, 1 << 20, 2, 100, 0),
+                                             (4096, 0, 2, 100, 0), (4096, 1 << 20, 0, 100, 0),
+                                             (4096, 1 << 20, 17, 100, 0), (4096, 1 << 20, 2, 0, 0),
+                                             (4096, 1 << 20, 2, 100, -1)):
+        desc = L.ServerDesc(arena, nbytes, slots, maxb, prio)
+        assert lib.sxe_server_create(ctypes.byref(desc), ctypes.byref(h)) == -1
+    rid, st = ctypes.c_int64(0), ctypes.c_int32(0)
+    assert lib.sxe_server_add_field(None, None, None, None, None) == -1
+    assert lib.sxe_server_start(None) == -1
+    assert lib.sxe_server_submit(None, 2, None, 1, None, ctypes.byref(rid)) == -1
+    assert lib.sxe_server_wait(None, 0, 0, ctypes.byref(st), None) == -1
+    assert lib.sxe_server_stop(None, 1) == -1
+    assert lib.sxe_server_destroy(None) == 0
+
+
 def test_selftest_wait_checks_its_limit_on_the_host(L):
     lib = L.lib()
     assert lib.sxe_selftest_wait(1, 0, None) == -1

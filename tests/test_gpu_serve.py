@@ -16,15 +16,21 @@ def _fields(log2_T=14):
     return {d: make_field(d, log2_T=log2_T, seed=10 + d) for d in (2, 3, 4, 5)}
 
 
+@pytest.fixture(params=["python", "native"])
+def server_cls(request):
+    """The scheduler in Python (``FieldServer``) and in the library (``NativeFieldServer``)."""
+    from paper_2311_15439_gb300.serve import FieldServer, NativeFieldServer
+    return {"python": FieldServer, "native": NativeFieldServer}[request.param]
+
+
 def _alone(f, x):
     enc = f.encoder.encode_fwd(x.cuda(), f.tables)
     return f.mlp.mlp_fwd(f.weights, enc).cpu()
 
 
-def test_alone_equals_mixed(cuda_lib):
+def test_alone_equals_mixed(cuda_lib, server_cls):
     """Each request's values are bitwise the same when merged with others (continuous batching
     over 4 stream slots) as when computed alone."""
-    from paper_2311_15439_gb300.serve import FieldServer
     fields = _fields()
     g = synth.rng(1)
     reqs_in = []
@@ -32,7 +38,7 @@ def test_alone_equals_mixed(cuda_lib):
         d = int(g.choice([2, 3, 4, 5]))
         P = int(np.exp(g.uniform(np.log(100), np.log(70000))))
         reqs_in.append((d, torch.from_numpy(synth.uniform_points(P, d, 100 + i)).pin_memory()))
-    srv = FieldServer(fields, mem_budget_bytes=64 << 20, n_slots=4, max_batch_points=1 << 18).start()
+    srv = server_cls(fields, mem_budget_bytes=64 << 20, n_slots=4, max_batch_points=1 << 18).start()
     reqs = [srv.submit(d, x) for d, x in reqs_in]
     for r in reqs:
         assert r.wait(60)
@@ -43,13 +49,12 @@ def test_alone_equals_mixed(cuda_lib):
         assert torch.equal(r.y, _alone(fields[d], x))
 
 
-def test_memory_admission_and_rejections(cuda_lib):
+def test_memory_admission_and_rejections(cuda_lib, server_cls):
     """With a budget that fits about one request, requests wait instead of overcommitting;
     malformed, unknown-dimension and oversize requests fail without disturbing the rest."""
-    from paper_2311_15439_gb300.serve import FieldServer
     fields = _fields()
     budget = 40000 * fields[2].bytes_per_point() + 1024
-    srv = FieldServer(fields, mem_budget_bytes=budget, n_slots=3, max_batch_points=1 << 16).start()
+    srv = server_cls(fields, mem_budget_bytes=budget, n_slots=3, max_batch_points=1 << 16).start()
     good = [(2, torch.from_numpy(synth.uniform_points(30000, 2, i)).pin_memory()) for i in range(6)]
     bad = [(7, torch.zeros((10, 7)).pin_memory()),                      # no field of that dimension
            (3, torch.zeros((10, 2)).pin_memory()),                      # wrong width
@@ -71,14 +76,13 @@ def test_memory_admission_and_rejections(cuda_lib):
 
 
 @pytest.mark.parametrize("d", [2, 5])
-def test_served_values_match_oracle(cuda_lib, d):
+def test_served_values_match_oracle(cuda_lib, d, server_cls):
     """Served values equal the FP64 oracle's encoding + network on the same fp16 tables and
     weights (encoding rounded to fp16 as the network reads it), within the network bound."""
-    from paper_2311_15439_gb300.serve import FieldServer
     from test_gpu_mlp import _dens
     f = _fields()[d]
     x = synth.uniform_points(5000, d, 3)
-    srv = FieldServer({d: f}).start()
+    srv = server_cls({d: f}, mem_budget_bytes=64 << 20).start()
     r = srv.submit(d, torch.from_numpy(x).pin_memory())
     assert r.wait(60)
     srv.stop()
@@ -93,3 +97,26 @@ def test_served_values_match_oracle(cuda_lib, d):
     # rounding itself, so the forward bound needs no slack
     err = np.abs(r.y.numpy().astype(np.float64) - y)
     assert np.all(err <= tol * yden)
+
+
+def test_native_server_stops_without_draining_and_reports_failures(cuda_lib):
+    """Stopping the native server without draining fails what is still queued (each request
+    completes, with an error) while batches already launched finish with their values (200
+    one-batch requests, one slot: the stop lands long before the queue drains); a server refuses
+    submissions once stopped."""
+    from paper_2311_15439_gb300.serve import NativeFieldServer
+    fields = _fields()
+    srv = NativeFieldServer(fields, mem_budget_bytes=8 << 20, n_slots=1, max_batch_points=1 << 16).start()
+    xs = [torch.from_numpy(synth.uniform_points(1 << 16, 3, 500 + i)).pin_memory() for i in range(200)]
+    reqs = [srv.submit(3, x) for x in xs]        # one request per batch, one batch in flight
+    assert reqs[0].wait(60)
+    srv.stop(drain=False)
+    for r in reqs:
+        assert r.wait(60)
+    done = [r for r in reqs if r.error is None]
+    failed = [r for r in reqs if r.error is not None]
+    assert done[0] is reqs[0] and all(torch.equal(r.y, _alone(fields[3], r.x)) for r in done)
+    assert failed and all("stopped" in r.error for r in failed)
+    assert all(r.rid > q.rid for r in failed for q in done)     # the queue's tail failed, in order
+    late = srv.submit(3, xs[0])
+    assert late.wait(1) and late.error is not None
