@@ -23,6 +23,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int64_t kAlign = 256;
 constexpr int kMaxSlots = 16;
+constexpr size_t kCopyPiece = (size_t)4 << 20;   // bytes per copy command
 
 int64_t align_up(int64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 int64_t dtype_bytes(int32_t dt) { return dt == SXE_F32 ? 4 : 2; }
@@ -145,17 +146,30 @@ std::string launch_batch(sxe_server* s, const SrvField& f, SrvBatch* b, int64_t 
   float* y = reinterpret_cast<float*>(base + align_up(P * d * 4) + align_up(P * n_enc * dtype_bytes(f.enc->desc.out_dtype)));
   int64_t o = 0;
   for (SrvRequest* r : b->reqs) {
-    const cudaError_t e = cudaMemcpyAsync(x + o * d, r->x, (size_t)(r->n * d) * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return std::string("points copy: ") + cudaGetErrorString(e);
+    // in pieces of at most kCopyPiece bytes (the values too, below), so that a small batch's
+    // copies on another stream are served between the pieces of a large one's
+    const size_t total = (size_t)(r->n * d) * sizeof(float);
+    for (size_t at = 0; at < total; at += kCopyPiece) {
+      const size_t len = std::min(kCopyPiece, total - at);
+      const cudaError_t e = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(x + o * d) + at,
+                                            reinterpret_cast<const unsigned char*>(r->x) + at, len,
+                                            cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return std::string("points copy: ") + cudaGetErrorString(e);
+    }
     o += r->n;
   }
   if (sxe::launch_encode_fwd(f.enc, x, P, f.tables, enc, st) != SXE_OK) return sxe_last_error();
   if (sxe::launch_mlp_fwd(&f.mlp, f.weights, enc, P, y, nullptr, st) != SXE_OK) return sxe_last_error();
   o = 0;
   for (SrvRequest* r : b->reqs) {
-    const cudaError_t e = cudaMemcpyAsync(r->y, y + o * n_out, (size_t)(r->n * n_out) * sizeof(float),
-                                          cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return std::string("values copy: ") + cudaGetErrorString(e);
+    const size_t total = (size_t)(r->n * n_out) * sizeof(float);
+    for (size_t at = 0; at < total; at += kCopyPiece) {
+      const size_t len = std::min(kCopyPiece, total - at);
+      const cudaError_t e = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(r->y) + at,
+                                            reinterpret_cast<const unsigned char*>(y + o * n_out) + at, len,
+                                            cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return std::string("values copy: ") + cudaGetErrorString(e);
+    }
     o += r->n;
   }
   const cudaError_t e = cudaLaunchHostFunc(st, batch_done, b);
