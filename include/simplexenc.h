@@ -485,8 +485,9 @@ sxe_status sxe_device_error(int32_t* flag, int32_t clear);
  *   - overlap: each batch runs on its own stream slot (host-to-device copies of its requests'
  *     points, the two kernels, device-to-host copies of the values), and a host callback on that
  *     stream completes its requests;
- *   - priority: a slot has a high- and a normal-priority stream; small batches take the first,
- *     so the GPU's block scheduler serves them ahead of the blocks of large ones.
+ *   - priority: requests of at most priority_points points are batched only with each other,
+ *     up to that size, and run on the slot's high-priority stream, so the GPU's block scheduler
+ *     serves them ahead of the blocks of large batches; copies go in pieces of at most 4 MB.
  * A point's value depends only on that point, so a merged request's values equal those it gets
  * alone.  The library allocates no device memory: the arena is the caller's. */
 typedef struct sxe_server sxe_server;
@@ -495,9 +496,9 @@ typedef struct {
   int64_t arena_bytes;        /* its size: the admission budget */
   int32_t n_slots;            /* batches in flight at most (one CUDA stream each), 1..16 */
   int64_t max_batch_points;   /* largest merged batch (and largest request), >= 1 */
-  int64_t priority_points;    /* batches of at most this many points run on high-priority streams,
-                                 so that small queries overtake large ones at block boundaries
-                                 (0: every batch at normal priority) */
+  int64_t priority_points;    /* requests of at most this many points form their own batches,
+                                 run on high-priority streams, so that small queries overtake
+                                 large ones (0: one class, every batch at normal priority) */
 } sxe_server_desc;
 
 /* Creates a stopped server on the current device (streams created here). */

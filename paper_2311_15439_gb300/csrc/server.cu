@@ -184,14 +184,18 @@ void serve_loop(sxe_server* s) {
   for (;;) {
     s->cv_sched.wait(lk, [&] { return leaving() || (!s->queue.empty() && !s->free_slots.empty()); });
     if (leaving()) break;
-    // the head request and the later queued requests of its d, in arrival order, up to the
-    // batch limit; shrunk from the back until the batch fits in the arena beside those in flight
+    // the head request and the later queued requests of its d and its size class, in arrival
+    // order, up to the class's batch limit (small requests, of at most priority_points points,
+    // form high-priority batches of at most that size and are not merged into large batches);
+    // shrunk from the back until the batch fits in the arena beside those in flight
     SrvRequest* head = s->queue.front();
     const SrvField& f = s->fields[head->d];
+    const bool small = head->n <= s->desc.priority_points;
+    const int64_t limit = small ? s->desc.priority_points : s->desc.max_batch_points;
     std::vector<SrvRequest*> group;
     int64_t P = 0;
     for (SrvRequest* r : s->queue)
-      if (r->d == head->d && P + r->n <= s->desc.max_batch_points) {
+      if (r->d == head->d && (r->n <= s->desc.priority_points) == small && P + r->n <= limit) {
         group.push_back(r);
         P += r->n;
       }
