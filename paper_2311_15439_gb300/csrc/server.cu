@@ -191,7 +191,7 @@ void serve_loop(sxe_server* s) {
     SrvRequest* head = s->queue.front();
     const SrvField& f = s->fields[head->d];
     const bool small = head->n <= s->desc.priority_points;
-    const int64_t limit = small ? s->desc.priority_points : s->desc.max_batch_points;
+    const int64_t limit = small ? std::min(s->desc.priority_points, s->desc.max_batch_points) : s->desc.max_batch_points;
     std::vector<SrvRequest*> group;
     int64_t P = 0;
     for (SrvRequest* r : s->queue)
