@@ -455,11 +455,13 @@ sxe_status sxe_step_touched_dev(const sxe_adam_desc* desc, const float* correcti
  * SXE_MLP_KERNEL_TCGEN05_PIPELINED: tcgen05 with one warp issuing every product of the CTA for up
  * to four 128-point tiles in flight (each tile's epilogues run in its own warpgroup), the weight
  * gradients of all tiles accumulating in one set of TMEM accumulators.
- * SXE_MLP_KERNEL_TCGEN05_3TILE: for networks with n_out <= 8 (others fall back to
+ * SXE_MLP_KERNEL_TCGEN05_3TILE: for networks with n_out <= 16 (others fall back to
  * SXE_MLP_KERNEL_TCGEN05), up to three 128-point tiles in flight per SM, each issuing its own
  * tcgen05 products, with the output layer, the loss and the output layer's backward on warp-level
  * mma.sync inside the last hidden layer's epilogue (2 NH tensor-core round trips per tile instead
- * of 2 NH + 2).  Not thread-safe: set it before launching work. */
+ * of 2 NH + 2).  The setting also picks sxe_mlp_fwd's kernel: the three-tile kernel's forward-only
+ * form under SXE_MLP_KERNEL_AUTO and SXE_MLP_KERNEL_TCGEN05_3TILE (n_out <= 16), mma.sync
+ * otherwise.  Not thread-safe: set it before launching work. */
 #define SXE_MLP_KERNEL_AUTO 0
 #define SXE_MLP_KERNEL_MMA_SYNC 1
 #define SXE_MLP_KERNEL_TCGEN05 2

@@ -823,6 +823,9 @@ int mlp_grid_blocks(const sxe_mlp_desc* d, int64_t P) {
 
 sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,
                           cudaStream_t s) {
+  // the three-tile tcgen05 kernel's forward-only form for n_out <= 16 (automatic choice), else mma.sync
+  if ((g_mlp_kernel == SXE_MLP_KERNEL_AUTO || g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_3TILE) && mlp_tc3_applies(d))
+    return launch_mlp_fwd_tc3(d, W, in, P, out, act, s);
   return d->dtype == SXE_F16 ? fwd_in<__half>(d, W, in, P, out, act, s)
                              : fwd_in<__nv_bfloat16>(d, W, in, P, out, act, s);
 }

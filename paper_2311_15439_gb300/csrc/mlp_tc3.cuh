@@ -42,6 +42,8 @@ int* tc3_error_word();   // device address of the tensor-core error word (curren
 sxe_status launch_mlp_bwd_tc3_wide(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                                    const float* target, float loss_scale, int64_t P, float* din, float* dW,
                                    float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group, int64_t lc);
+sxe_status launch_mlp_fwd_tc3(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out,
+                              void* act, cudaStream_t s);   // n_out <= 16 (mlp_tc3_fwd.cu)
 
 namespace {
 
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(Tc3<N_IN, NH>::THREADS, 1)
 mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t P, int n_out,
                      const float* __restrict__ dout, const float* __restrict__ target, float loss_scale,
                      float inv_count, float* __restrict__ din, int din_group, float* __restrict__ ws,
-                     int64_t n_params, int* __restrict__ err) {
+                     int64_t n_params, int* __restrict__ err, float* __restrict__ yout, T* __restrict__ act) {
   using S = Tc3<N_IN, NH>;
   constexpr int G = S::G;
   constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
@@ -323,7 +325,12 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
     // 32 q + 16 mt + gq (+ 8), outputs 2 t4 (+ 1)
     const int rows = (int)(P - row0 < kM ? P - row0 : kM);   // rows of this tile inside the batch
     float yin[2][NT][4];                                // [m-tile][output tile][fragment element]
-    {
+    if constexpr (MODE == 2) {
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) yin[mt][nt][0] = yin[mt][nt][1] = yin[mt][nt][2] = yin[mt][nt][3] = 0.f;
+    } else {
       const float* src = (MODE == 0 ? dout : target) + row0 * n_out;
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt)
@@ -355,6 +362,8 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
           u.z = pack2_relu<T>(v[8 * k + 4], v[8 * k + 5]);
           u.w = pack2_relu<T>(v[8 * k + 6], v[8 * k + 7]);
           *reinterpret_cast<uint4*>(Hh + tc::cm_offset(r, 8 * k, kW)) = u;
+          if constexpr (MODE == 2)                      // the forward's hidden activations, if asked
+            if (act && r < rows) *reinterpret_cast<uint4*>(act + ((int64_t)h * P + row0 + r) * kW + 8 * k) = u;
         }
       }
       if (h < NH - 1) continue;
@@ -379,6 +388,16 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
             mma16816<T>(y[0], ha[ks], b[0], b[1]);
             mma16816<T>(y[NT - 1], ha[ks], b[2], b[3]);
           }
+        }
+        if constexpr (MODE == 2) {                      // forward only: the outputs, then the next m-tile
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int rl = 32 * q + 16 * mt + gq + 8 * (e >> 1), o = 8 * nt + 2 * t4 + (e & 1);
+              if (rl < rows && o < n_out) yout[(row0 + rl) * n_out + o] = y[nt][e];
+            }
+          continue;
         }
         float dy[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
@@ -421,6 +440,7 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
       }
     }
     if (failed) break;
+    if constexpr (MODE == 2) continue;                  // forward only
     // ---- backward through the hidden layers: dH_{h-1} = (dH_h W_h) * [H_{h-1} > 0].  The chain
     // product is committed alone and dW_h += dH_h^T H_{h-1} is issued after it (the next commit
     // covers it), so the epilogue does not wait for the weight gradient; dH_{h-1} goes into H_h's
@@ -539,6 +559,10 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  if constexpr (MODE == 2) {                            // no weight gradients
+    if (warp == 0) tc::tmem_dealloc(tmem_base, 512);
+    return;
+  }
   // this group's partial in shared memory, rows padded (dW_h rows of 68 floats, dW_0 rows of
   // N_IN + 4) so that the accumulator rows of eight lanes land in eight different bank groups
   float* part = reinterpret_cast<float*>(sm) + g * S::PSTRIDE;
@@ -626,15 +650,48 @@ sxe_status tc3_launch(const sxe_mlp_desc* d, const void* W, const void* in, cons
   if (target) {
     kernel_ctas_per_sm((const void*)mlp_train_tc3_kernel<T, N_IN, NH, 1, NT>, S::THREADS, S::SMEM);
     mlp_train_tc3_kernel<T, N_IN, NH, 1, NT><<<g3, S::THREADS, S::SMEM, s>>>(
-        (const T*)W, (const T*)in, P, d->n_out, dout, target, ls, ic, din, dg, ws, n_params, err);
+        (const T*)W, (const T*)in, P, d->n_out, dout, target, ls, ic, din, dg, ws, n_params, err, nullptr,
+        nullptr);
   } else {
     kernel_ctas_per_sm((const void*)mlp_train_tc3_kernel<T, N_IN, NH, 0, NT>, S::THREADS, S::SMEM);
     mlp_train_tc3_kernel<T, N_IN, NH, 0, NT><<<g3, S::THREADS, S::SMEM, s>>>(
-        (const T*)W, (const T*)in, P, d->n_out, dout, target, ls, ic, din, dg, ws, n_params, err);
+        (const T*)W, (const T*)in, P, d->n_out, dout, target, ls, ic, din, dg, ws, n_params, err, nullptr,
+        nullptr);
   }
   sxe_status st = check_launch("mlp_train_tc3");
   if (st != SXE_OK) return st;
   return launch_mlp_reduce(ws, g3, n_params, 1.f / ls, dW, target ? sq : nullptr, s);
+}
+
+// Forward only (MODE 2): the network's outputs out [P][n_out] binary32 and, if act is given, the
+// hidden activations act [NH][P][64]; the same grid and plan as the training pass.
+template <typename T, int N_IN, int NH, int NT>
+sxe_status tc3_fwd_launch(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,
+                          cudaStream_t s) {
+  using S = Tc3<N_IN, NH>;
+  const int64_t n_tiles = (P + kM - 1) / kM;
+  const int g3 = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)device_sm_count(), (n_tiles + S::G - 1) / S::G));
+  kernel_ctas_per_sm((const void*)mlp_train_tc3_kernel<T, N_IN, NH, 2, NT>, S::THREADS, S::SMEM);
+  mlp_train_tc3_kernel<T, N_IN, NH, 2, NT><<<g3, S::THREADS, S::SMEM, s>>>(
+      (const T*)W, (const T*)in, P, d->n_out, nullptr, nullptr, 1.f, 0.f, nullptr, 0, nullptr, 0, tc3_error_word(),
+      out, (T*)act);
+  return check_launch("mlp_fwd_tc3");
+}
+
+template <typename T, int NT>
+sxe_status tc3_fwd_in(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,
+                      cudaStream_t s) {
+  switch (d->n_in * 4 + d->n_hidden) {
+    case 16 * 4 + 1: return tc3_fwd_launch<T, 16, 1, NT>(d, W, in, P, out, act, s);
+    case 16 * 4 + 2: return tc3_fwd_launch<T, 16, 2, NT>(d, W, in, P, out, act, s);
+    case 16 * 4 + 3: return tc3_fwd_launch<T, 16, 3, NT>(d, W, in, P, out, act, s);
+    case 32 * 4 + 1: return tc3_fwd_launch<T, 32, 1, NT>(d, W, in, P, out, act, s);
+    case 32 * 4 + 2: return tc3_fwd_launch<T, 32, 2, NT>(d, W, in, P, out, act, s);
+    case 32 * 4 + 3: return tc3_fwd_launch<T, 32, 3, NT>(d, W, in, P, out, act, s);
+    case 64 * 4 + 1: return tc3_fwd_launch<T, 64, 1, NT>(d, W, in, P, out, act, s);
+    case 64 * 4 + 2: return tc3_fwd_launch<T, 64, 2, NT>(d, W, in, P, out, act, s);
+    default: return tc3_fwd_launch<T, 64, 3, NT>(d, W, in, P, out, act, s);
+  }
 }
 
 template <typename T, int N_IN, int NT>

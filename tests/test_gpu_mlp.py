@@ -129,7 +129,10 @@ def _setup(net, seed=0):
 
 
 @pytest.mark.parametrize("net", NETS, ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
-def test_forward(cuda_lib, net):
+def test_forward(cuda_lib, net, mlp_kernel):
+    """The forward pass and its hidden activations against the oracle (mma.sync under the
+    mma_sync / tcgen05 / pipelined settings, the three-tile tcgen05 kernel's forward form under
+    tcgen05_3tile)."""
     mlp, Wd, Ws, xd, x = _setup(net)
     nh, dt = net[1], net[3]
     act = torch.empty((nh, x.shape[0], 64), dtype=Wd.dtype, device="cuda")
@@ -137,7 +140,8 @@ def test_forward(cuda_lib, net):
     ref, acts = OM.mlp_forward(Ws, x)
     yden, _, _ = _dens(Ws, x, np.zeros_like(ref))
     tol = (2 * nh + 2) * U[dt]
-    assert record_error("mlp_fwd output, %s network" % dt, rel_err(y, ref, yden), tol, "magnitude bound |W|...|x| (+ fp16-ambiguous ReLU slack)") <= tol
+    assert record_error("mlp_fwd output, %s network (%s)" % (dt, mlp_kernel), rel_err(y, ref, yden), tol,
+                        "magnitude bound |W|...|x| (+ fp16-ambiguous ReLU slack)") <= tol
     h = [np.abs(x)]
     for W in Ws[:-1]:
         h.append(h[-1] @ np.abs(W).T)
@@ -386,3 +390,32 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(cuda_lib):
     torch.cuda.synchronize()
     assert torch.equal(before, after)
     assert lib.sxe_device_error(ctypes.byref(flag), 1) == 0 and flag.value == 0
+
+
+@pytest.mark.parametrize("net", [NETS[0], NETS[3], NETS[5], NETS[8]], ids=lambda n: "in%d_h%d_out%d_%s_P%d" % n)
+def test_forward_kernels_agree(cuda_lib, net):
+    """The three-tile tcgen05 forward and the mma.sync forward compute the same products in the
+    same precision: outputs and hidden activations within the accumulation-order bound of their
+    depth against the magnitude bound |W|...|x|."""
+    L = cuda_lib
+    mlp, Wd, Ws, xd, x = _setup(net, seed=77)
+    nh = net[1]
+    outs = {}
+    prev = L.lib().sxe_mlp_get_kernel()
+    try:
+        for k in (L.SXE_MLP_KERNEL_MMA_SYNC, L.SXE_MLP_KERNEL_TCGEN05_3TILE):
+            assert L.lib().sxe_mlp_set_kernel(k) == 0
+            act = torch.empty((nh, x.shape[0], 64), dtype=Wd.dtype, device="cuda")
+            y = mlp.mlp_fwd(Wd, xd, act=act)
+            outs[k] = (y.cpu().numpy(), act.float().cpu().numpy())
+    finally:
+        L.lib().sxe_mlp_set_kernel(prev)
+    (ya, aa), (yb, ab) = outs[L.SXE_MLP_KERNEL_MMA_SYNC], outs[L.SXE_MLP_KERNEL_TCGEN05_3TILE]
+    yden, _, _ = _dens(Ws, x, np.zeros_like(ya, dtype=np.float64))
+    u = U[net[3]]
+    assert np.all(np.abs(yb - ya) <= (2 * nh + 2) * u * yden + 1e-30)
+    h = [np.abs(x)]
+    for W in Ws[:-1]:
+        h.append(h[-1] @ np.abs(W).T)
+    for i in range(nh):                              # hidden layer i: within the bound of its depth
+        assert np.all(np.abs(ab[i] - aa[i]) <= (2 * i + 4) * u * h[i + 1] + 2.0 ** -24), "layer %d" % i

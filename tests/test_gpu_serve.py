@@ -120,3 +120,43 @@ def test_native_server_stops_without_draining_and_reports_failures(cuda_lib):
     assert all(r.rid > q.rid for r in failed for q in done)     # the queue's tail failed, in order
     late = srv.submit(3, xs[0])
     assert late.wait(1) and late.error is not None
+
+
+def test_native_server_takes_requests_from_several_threads(cuda_lib):
+    """Four client threads submit and wait concurrently (submit and wait are thread-safe in the
+    library); every answer equals the request computed alone, and sizes above the batch limit are
+    refused with an error request."""
+    import threading
+    from paper_2311_15439_gb300.serve import NativeFieldServer
+    fields = _fields()
+    srv = NativeFieldServer(fields, mem_budget_bytes=64 << 20, n_slots=4, max_batch_points=1 << 17,
+                            priority_points=1 << 12).start()
+    results, errors = {}, []
+
+    def client(k):
+        try:
+            g = synth.rng(200 + k)
+            mine = []
+            for i in range(30):
+                d = int(g.choice([2, 3, 4, 5]))
+                P = int(np.exp(g.uniform(np.log(50), np.log(1 << 17))))
+                x = torch.from_numpy(synth.uniform_points(P, d, 1000 * k + i)).pin_memory()
+                mine.append((d, x, srv.submit(d, x)))
+            for d, x, r in mine:
+                assert r.wait(60) and r.error is None
+                results[(k, r.rid)] = (d, x, r.y)
+        except Exception as exc:         # surfaced in the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(120)
+    big = srv.submit(2, torch.zeros((1 << 17) + 1, 2).pin_memory())
+    srv.stop()
+    assert not errors, errors[0]
+    assert len(results) == 120
+    for d, x, y in results.values():
+        assert torch.equal(y, _alone(fields[d], x))
+    assert big.wait(1) and big.error is not None
