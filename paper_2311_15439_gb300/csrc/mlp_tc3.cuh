@@ -507,15 +507,12 @@ mlp_train_tc3_kernel(const T* __restrict__ W, const T* __restrict__ in, int64_t 
       // row): the rows of eight lanes land in different bank groups (two-way for N_IN = 16)
       constexpr int SWZ = (N_IN / 4 < 8 ? N_IN / 4 : 8) - 1;
       float* st = reinterpret_cast<float*>(gs + S::H);
+      float v[N_IN];
+      tc::tmem_ld_cols<N_IN>(lane_addr, v);
 #pragma unroll
-      for (int c0 = 0; c0 < N_IN; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(lane_addr + (uint32_t)c0, v);
-#pragma unroll
-        for (int j = 0; j < 16; j += 4)
-          *reinterpret_cast<float4*>(st + (r * (N_IN / 4) + (((c0 + j) >> 2) ^ (r & SWZ))) * 4) =
-              make_float4(v[j] * inv_scale, v[j + 1] * inv_scale, v[j + 2] * inv_scale, v[j + 3] * inv_scale);
-      }
+      for (int j = 0; j < N_IN; j += 4)
+        *reinterpret_cast<float4*>(st + (r * (N_IN / 4) + ((j >> 2) ^ (r & SWZ))) * 4) =
+            make_float4(v[j] * inv_scale, v[j + 1] * inv_scale, v[j + 2] * inv_scale, v[j + 3] * inv_scale);
       group_sync(bar_id);
 #pragma unroll
       for (int j = 0; j < N_IN / 4; ++j) {
