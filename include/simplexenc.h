@@ -461,7 +461,8 @@ sxe_status sxe_step_touched_dev(const sxe_adam_desc* desc, const float* correcti
  * mma.sync inside the last hidden layer's epilogue (2 NH tensor-core round trips per tile instead
  * of 2 NH + 2).  The setting also picks sxe_mlp_fwd's kernel: the three-tile kernel's forward-only
  * form under SXE_MLP_KERNEL_AUTO and SXE_MLP_KERNEL_TCGEN05_3TILE (n_out <= 16), mma.sync
- * otherwise.  Not thread-safe: set it before launching work. */
+ * otherwise, and sxe_vr_field_mlp's: its tcgen05 form under the same two settings (colour
+ * n_out <= 8), mma.sync otherwise.  Not thread-safe: set it before launching work. */
 #define SXE_MLP_KERNEL_AUTO 0
 #define SXE_MLP_KERNEL_MMA_SYNC 1
 #define SXE_MLP_KERNEL_TCGEN05 2

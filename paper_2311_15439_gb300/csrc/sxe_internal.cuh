@@ -93,6 +93,9 @@ bool mlp_tc3_applies(const sxe_mlp_desc* d);
 sxe_status launch_selftest_wait(int timeout, int64_t limit_ns, cudaStream_t s);
 sxe_status launch_mlp_fwd_tc3(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out,
                               void* act, cudaStream_t s);
+sxe_status launch_vr_field_tc3(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
+                               const void* enc, const float* dirs, int64_t R, int S, float* sigma, float* logits,
+                               cudaStream_t s);   // colour n_out <= 8 (render_tc3.cu)
 int* tc_error_word();   // device address of the tcgen05 kernels' error word (current device)
 sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
                              cudaStream_t s);
