@@ -117,7 +117,7 @@ void finish(sxe_server* s, SrvBatch* b, int state, const std::string& err) {
   --s->inflight;
 }
 
-// Host callback at the end of a batch's stream work (a driver thread; no CUDA calls here).
+// Host callback at the end of a batch's stream work (run on a CUDA runtime thread; no CUDA calls here).
 // Everything happens under the lock, so that once it is released the server may be destroyed.
 void CUDART_CB batch_done(void* p) {
   SrvBatch* b = static_cast<SrvBatch*>(p);
