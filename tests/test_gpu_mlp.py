@@ -419,3 +419,33 @@ def test_forward_kernels_agree(cuda_lib, net):
         h.append(h[-1] @ np.abs(W).T)
     for i in range(nh):                              # hidden layer i: within the bound of its depth
         assert np.all(np.abs(ab[i] - aa[i]) <= (2 * i + 4) * u * h[i + 1] + 2.0 ** -24), "layer %d" % i
+
+
+@pytest.mark.parametrize("P", [1, 127, 129, 383])
+def test_tiny_batches(cuda_lib, P, mlp_kernel):
+    """Batches of one point, just under and over one 128-point tile, and a few tiles with a ragged
+    tail: the training pass and the forward match the oracle under every kernel setting (groups
+    and CTAs without a tile contribute nothing)."""
+    from paper_2311_15439_gb300.trainer import default_loss_scale
+    net = (32, 2, 3, "f16", P)
+    mlp, Wd, Ws, xd, x = _setup(net, seed=61)
+    tgt = synth.rng(62).random((P, 3)).astype(np.float32)
+    dW = torch.zeros((mlp.n_params,), device="cuda")
+    din = torch.empty((P, 32), device="cuda")
+    sq = torch.zeros((1,), device="cuda")
+    mlp.mlp_train_l2(Wd, xd, torch.from_numpy(tgt).cuda(), dW, sq, din=din, loss_scale=default_loss_scale(P, 3))
+    y, acts = OM.mlp_forward(Ws, x)
+    loss, dy = OM.l2_loss(y, tgt)
+    dW_ref, din_ref = OM.mlp_backward(Ws, acts, dy)
+    tol = 6 * U["f16"]
+    yden = _dens(Ws, x, dy)[0]
+    dy_bound = 2.0 * (yden + np.abs(tgt)) / dy.size
+    _, dW_den, din_den = _dens(Ws, x, dy_bound)
+    dW_sl, din_sl = flip_slack(Ws, x, dy_bound, U["f16"])
+    got = mlp.split(dW.cpu().numpy())
+    for i in range(len(Ws)):
+        assert within(got[i], dW_ref[i], dW_den[i], tol, dW_sl[i]) <= 1.0, "layer %d" % i
+    assert within(din.cpu().numpy(), din_ref, din_den, tol, din_sl) <= 1.0
+    assert abs(sq.item() / (P * 3) - loss) <= 3 * tol * np.mean((yden + np.abs(tgt)) ** 2)
+    yf = mlp.mlp_fwd(Wd, xd).cpu().numpy()
+    assert rel_err(yf, y, yden) <= tol
