@@ -219,6 +219,16 @@ def count_touched(tr, x):
     return int(np.unpackbits(bytes_).sum()), int(np.count_nonzero(bytes_))
 
 
+def _graph_events_supported() -> bool:
+    """Whether timing events can be recorded as nodes of a CUDA graph (``external`` events)."""
+    import torch
+    try:
+        torch.cuda.Event(enable_timing=True, external=True)
+    except TypeError:
+        return False
+    return True
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -255,26 +265,82 @@ def run_gpu(args):
         tr.step(xd[i % N_POOL], td[i % N_POOL])
     torch.cuda.synchronize(dev)
 
-    # ---- device-timed region: K steps of Trainer.step; the trainer records an event before and
-    # after each stage on the stream that stage's kernels run on (the table backward of a split
-    # step on its second stream), from which each stage's time per step is summed
+    # ---- device-timed region: K steps, each a replay of a recording of Trainer.step (a CUDA graph,
+    # as a training loop runs it) on one of the resident batches, every recording a distinct graph.
+    # Timing events recorded while a step is recorded are nodes of its graph, on the stream that the
+    # stage's kernels run on (the table backward of a split step on its second stream).  Each event
+    # node costs about 2.5 us of the step, so the timed recordings carry events around the dominant
+    # kernel's stage only; a shorter pass before it, on recordings with events around every stage,
+    # gives the time of each stage and picks that kernel.
     names = ["encode_fwd", "mlp_train_l2", "encode_bwd", "adam_tables", "adam_mlp"]
+    graphs = _graph_events_supported()
+
+    def record(n, only):
+        recs = []
+        tr.stage_only = only
+        for k in range(n):
+            tr.stage_events = {}
+            tr.capture(xd[k % N_POOL], td[k % N_POOL], warmup=0)
+            recs.append((tr.graph, tr.stage_events))
+        tr.stage_events, tr.stage_only = None, None
+        for g, _ in recs:                       # first launches (graph upload) outside any timed span
+            tr.t += 1
+            g.replay()
+        torch.cuda.synchronize(dev)
+        return recs
+
+    def stage_ms(evs, stages, n):
+        evs = dict(evs)
+        if "adam_mlp" in stages:
+            evs["adam_mlp"] = evs["adam_tables_end"]
+        return {m: float(sum(a.elapsed_time(b) for a, b in zip(evs[m], evs[m + "_end"]))) / n for m in stages}
+
+    n_pre = max(8, args.steps // 4)
+    if graphs:
+        pre = record(n_pre, None)
+        for g, _ in pre:
+            tr.t += 1
+            g.replay()
+        torch.cuda.synchronize(dev)
+        per_kernel = stage_ms({m: [e for _, r in pre for e in r[m]] for m in pre[0][1]}, names, n_pre)
+        del pre
+    else:                                       # no timing events inside graphs: eager steps
+        tr.stage_events = {}
+        for k in range(n_pre):
+            tr.step(xd[k % N_POOL], td[k % N_POOL])
+        torch.cuda.synchronize(dev)
+        per_kernel = stage_ms(tr.stage_events, names, n_pre)
+        tr.stage_events = None
+    work = _stage_work(1)
+    dom = max(work, key=lambda m: per_kernel[m])
+    only = {dom, "adam_tables"} if dom == "adam_mlp" else {dom}
+    recordings = record(args.steps, only) if graphs else []
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tr.stage_events = {}
+    if not graphs:
+        tr.stage_events, tr.stage_only = {}, only
     with ClockSampler(local) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
         start.record(stream)
-        for k in range(args.steps):
-            tr.step(xd[k % N_POOL], td[k % N_POOL])
+        if recordings:
+            for g, _ in recordings:
+                tr.t += 1
+                g.replay()
+        else:
+            for k in range(args.steps):
+                tr.step(xd[k % N_POOL], td[k % N_POOL])
         stop.record(stream)
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
-    ev, tr.stage_events = tr.stage_events, None
-    ev["adam_mlp"] = ev["adam_tables_end"]
-    per_kernel = {n: float(sum(a.elapsed_time(b) for a, b in zip(ev[n], ev[n + "_end"]))) / args.steps for n in names}
+    if recordings:
+        ev = {m: [e for _, r in recordings for e in r[m]] for m in recordings[0][1]}
+    else:
+        ev, tr.stage_events, tr.stage_only = tr.stage_events, None, None
+    dom_ms = stage_ms(ev, [dom], args.steps)[dom]
+    step_form = "replays of recorded steps (CUDA graphs)" if recordings else "eager steps"
+    del recordings, ev
     ms = start.elapsed_time(stop)
     ms = max_over_ranks(ms, world, dev)
     loss = tr.loss()
@@ -307,8 +373,8 @@ def run_gpu(args):
     peaks_ra = random_access_peaks(dev, tr.state.numel() * 4, tr.tables) if rank == 0 else None
     volume = volume_sweep(dev) if (rank == 0 and not args.no_volume) else None
     sdf = sdf_train(dev) if (rank == 0 and not args.no_sweep) else None
-    grid_img = image_step_variants(dev, xd, td, ms / args.steps) if (rank == 0 and not args.no_sweep and
-                                                                      args.kind == "simplex") else None
+    grid_img = image_step_variants(dev, xd, td) if (rank == 0 and not args.no_sweep and
+                                                     args.kind == "simplex") else None
     per_cfg = per_config_encode(dev) if (rank == 0 and not args.no_sweep) else None
     quality = (fit_quality(dev, args.quality_steps, max(1, args.quality_steps * 2 // 5))
                if (rank == 0 and args.quality_steps > 0) else None)
@@ -316,14 +382,13 @@ def run_gpu(args):
     if rank == 0:
         value = job_throughput(BATCH, args.steps, world, ms)
         work = _stage_work(n_touched)
-        dom = max(work, key=lambda n: per_kernel[n])
         bound, amount = work[dom]
         hbm_peak, peak_src = _peaks()
         if bound == "hbm":
-            achieved = amount / (per_kernel[dom] / 1e3) / 1e9
+            achieved = amount / (dom_ms / 1e3) / 1e9
             peak, unit = hbm_peak, "GB/s"
         else:
-            achieved = amount / (per_kernel[dom] / 1e3) / 1e12
+            achieved = amount / (dom_ms / 1e3) / 1e12
             peak, unit = _tensor_peak(), "TFLOP/s"
         line = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
@@ -332,7 +397,7 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "kind": args.kind, "res_mode": "raw",
                        "step": "encode forward, network forward + L2 loss + backward, encode backward into the "
                                "table state, Adam on the touched table entries and on the network",
-                       "split_batch": tr.split,
+                       "split_batch": tr.split, "timed_steps": step_form,
                        "mlp_kernel": {"auto": "auto (three-tile tcgen05 kernel for this network)", "mma_sync": "mma_sync",
                                       "tcgen05": "tcgen05", "tcgen05_pipelined": "tcgen05_pipelined",
                                       "tcgen05_3tile": "tcgen05_3tile"}[args.mlp_kernel],
@@ -346,8 +411,10 @@ def run_gpu(args):
                            "replayed, loss read one step behind)"},
             "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                          "frac": achieved / peak, "traffic": _traffic(dom), "peak_source": peak_src,
-                         "work_per_step": amount, "touched_entries_per_step": n_touched},
+                         "work_per_step": amount, "touched_entries_per_step": n_touched,
+                         "kernel_ms": dom_ms, "kernel_ms_source": "events around the kernel in each timed step"},
             "per_kernel_ms": per_kernel,
+            "per_kernel_ms_source": "%d steps before the timed region, events around every stage" % n_pre,
             "gpu_launches": args.steps * tr.n_launches_per_step,
             "clocks": clk.summary(),
             "final_loss": loss,
@@ -938,29 +1005,45 @@ def profile_encode(dev):
         torch.cuda.empty_cache()
 
 
-def image_step_variants(dev, xd, td, simplex_ms, steps=100, warmup=5):
-    """The headline training step with the simplex encoder in the equal-memory setting and with the
-    2^d grid encoder instead (same L, F, T, table layout, network and batches): the comparison of
-    Sec. 6.1's image-fitting run time, per res_mode of the simplex side."""
+def _replayed_step_ms(tr, xd, td, steps, warmup):
+    """Time per step of ``steps`` replays of recorded training steps (one recording per resident
+    batch, cycled; no timing events inside), after ``warmup`` eager steps."""
+    import torch
+    for i in range(warmup):
+        tr.step(xd[i % len(xd)], td[i % len(td)])
+    recs = []
+    for i in range(len(xd)):
+        tr.capture(xd[i], td[i], warmup=0)
+        recs.append(tr.graph)
+    for g in recs:                       # first launches outside the timed span
+        tr.t += 1
+        g.replay()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for i in range(steps):
+        tr.t += 1
+        recs[i % len(recs)].replay()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def image_step_variants(dev, xd, td, steps=100, warmup=5):
+    """The headline training step with the simplex encoder in both res_modes and with the 2^d grid
+    encoder (same L, F, T, table layout, network and batches), each timed the same way (replays of
+    recorded steps without timing events): the comparison of Sec. 6.1's image-fitting run time, per
+    res_mode of the simplex side."""
     import torch
     from paper_2311_15439_gb300.api import Encoder, Mlp
     from paper_2311_15439_gb300.trainer import Trainer
-    out = {"simplex_raw": {"res_mode": "raw", "ms_per_step": simplex_ms, "points_per_s": BATCH / (simplex_ms / 1e3),
-                           "note": "the headline step"}}
-    for kind, mode in VARIANTS[1:]:
+    out = {"timing": "%d replays of recorded steps per encoder (8 recordings, one per resident batch, cycled), "
+                     "no timing events inside" % steps}
+    for kind, mode in VARIANTS:
         enc = Encoder(**CFG, kind=kind, res_mode=mode, table_dtype="f16")
         tr = Trainer(enc, Mlp(CFG["n_levels"] * CFG["n_features"], N_OUT, n_hidden=2, dtype="f16"), BATCH, seed=0,
                      device=dev, table_layout="records")
-        for i in range(warmup):
-            tr.step(xd[i % len(xd)], td[i % len(td)])
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        a.record()
-        for i in range(steps):
-            tr.step(xd[i % len(xd)], td[i % len(td)])
-        b.record()
-        torch.cuda.synchronize(dev)
-        ms = a.elapsed_time(b) / steps
+        ms = _replayed_step_ms(tr, xd, td, steps, warmup)
         out[vname(kind, mode)] = {"res_mode": mode, "ms_per_step": ms, "points_per_s": BATCH / (ms / 1e3),
                                   "steps": steps}
         del tr
@@ -1202,18 +1285,26 @@ def serve_bench(dev, n_requests=800, rate_hz=1000.0, seed=5, repeats=3, sweep=(2
     for m in ("raw", "equal_mem"):
         out["simplex_over_grid_capacity_" + m] = (out[vname("simplex", m)]["capacity_points_per_s"]
                                                    / out["grid"]["capacity_points_per_s"])
-    # the same load through the Python scheduler (simplex, raw), for comparison with the library's
-    fields = {d: make_field(d, seed=d, device=dev) for d in dims}
-    srv = FieldServer(fields, mem_budget_bytes=4 << 30, n_slots=4, max_batch_points=4 << 20, device=dev).start()
-    for d in dims:
-        if not srv.submit(d, pools[d][:65536]).wait(120.0):
-            raise TimeoutError("serving warm-up request did not complete")
-    runs = [one_run(srv, rate_hz, n_requests, seed + r) for r in range(repeats)]
-    srv.stop()
+    # the same load through the Python scheduler (simplex, raw), for comparison with the library's;
+    # its forward passes on the kernel the library's loop takes (mma.sync) for the length of the run
+    from paper_2311_15439_gb300 import _lib
+    prev = _lib.lib().sxe_mlp_get_kernel()
+    _lib.check(_lib.lib().sxe_mlp_set_kernel(_lib.SXE_MLP_KERNEL_MMA_SYNC), "sxe_mlp_set_kernel")
+    try:
+        fields = {d: make_field(d, seed=d, device=dev) for d in dims}
+        srv = FieldServer(fields, mem_budget_bytes=4 << 30, n_slots=4, max_batch_points=4 << 20, device=dev).start()
+        for d in dims:
+            if not srv.submit(d, pools[d][:65536]).wait(120.0):
+                raise TimeoutError("serving warm-up request did not complete")
+        runs = [one_run(srv, rate_hz, n_requests, seed + r) for r in range(repeats)]
+        srv.stop()
+    finally:
+        _lib.lib().sxe_mlp_set_kernel(prev)
     out["python_scheduler_simplex_raw"] = {"p50_ms": float(np.median([r["p50_ms"] for r in runs])),
                                            "p99_ms": float(np.median([r["p99_ms"] for r in runs]))}
     out["scheduler"] = ("library (sxe_server_*: C++ scheduler thread, 4 stream slots, batches of <= 2^20 points on "
-                        "high-priority streams, host-callback completion); python_scheduler_* is serve.FieldServer")
+                        "high-priority streams, host-callback completion; network forward on mma.sync); "
+                        "python_scheduler_* is serve.FieldServer on the same kernels")
     return out
 
 

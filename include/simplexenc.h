@@ -343,7 +343,8 @@ sxe_status sxe_mlp_bwd(const sxe_mlp_desc* desc, const void* weights, const void
  * image fitting): with y the network output, the upstream gradient is
  * dy = 2 (y - target) / (n_points*n_out); *sq_sum (one binary32 device
  * scalar) is overwritten with the batch's sum of squared residuals, summed in a
- * fixed order.  Other arguments as sxe_mlp_bwd. */
+ * fixed order (n_points = 0: *sq_sum = 0, when sq_sum is not NULL, and nothing else is
+ * written).  Other arguments as sxe_mlp_bwd. */
 sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* desc, const void* weights, const void* in,
                             const float* target, float loss_scale, int64_t n_points,
                             float* din, float* dweights, float* sq_sum,
@@ -354,8 +355,9 @@ sxe_status sxe_mlp_train_l2(const sxe_mlp_desc* desc, const void* weights, const
  * shard of one rank in data-parallel training): the upstream gradient is normalised by the whole
  * batch, dy = 2 (y - target) / (batch_points * n_out), so that the parts' weight gradients,
  * accumulated into the same dweights (+=), sum to the batch's; *sq_sum is overwritten with this
- * part's sum of squared residuals.  SXE_EINVAL if n_points > batch_points; n_points = 0 enqueues
- * nothing.  Other arguments as sxe_mlp_train_l2.  Sec. 6.1's L2 loss over the batch. */
+ * part's sum of squared residuals.  SXE_EINVAL if n_points > batch_points; n_points = 0 sets
+ * *sq_sum = 0 (when sq_sum is not NULL) and enqueues nothing else.  Other arguments as
+ * sxe_mlp_train_l2.  Sec. 6.1's L2 loss over the batch. */
 sxe_status sxe_mlp_train_l2_part(const sxe_mlp_desc* desc, const void* weights, const void* in,
                                  const float* target, float loss_scale, int64_t n_points,
                                  int64_t batch_points, float* din, float* dweights, float* sq_sum,
@@ -462,7 +464,10 @@ sxe_status sxe_step_touched_dev(const sxe_adam_desc* desc, const float* correcti
  * of 2 NH + 2).  The setting also picks sxe_mlp_fwd's kernel: the three-tile kernel's forward-only
  * form under SXE_MLP_KERNEL_AUTO and SXE_MLP_KERNEL_TCGEN05_3TILE (n_out <= 16), mma.sync
  * otherwise, and sxe_vr_field_mlp's: its tcgen05 form under the same two settings (colour
- * n_out <= 8), mma.sync otherwise.  Not thread-safe: set it before launching work. */
+ * n_out <= 8), mma.sync otherwise.  The tcgen05 kernels are persistent, one CTA per SM that needs
+ * the whole SM: where network passes run beside other streams' kernels, mma.sync shares the GPU
+ * better (the serving loop below takes it for its forward passes under SXE_MLP_KERNEL_AUTO).
+ * Not thread-safe: set it before launching work. */
 #define SXE_MLP_KERNEL_AUTO 0
 #define SXE_MLP_KERNEL_MMA_SYNC 1
 #define SXE_MLP_KERNEL_TCGEN05 2
@@ -487,7 +492,9 @@ sxe_status sxe_device_error(int32_t* flag, int32_t clear);
  *     fit in the caller's arena next to the batches in flight, else it waits for completions;
  *   - overlap: each batch runs on its own stream slot (host-to-device copies of its requests'
  *     points, the two kernels, device-to-host copies of the values), and a host callback on that
- *     stream completes its requests;
+ *     stream completes its requests; the network's forward pass runs on the mma.sync kernel
+ *     under SXE_MLP_KERNEL_AUTO (its blocks share SMs with the other slots' kernels), on the
+ *     three-tile tcgen05 kernel under SXE_MLP_KERNEL_TCGEN05_3TILE;
  *   - priority: requests of at most priority_points points are batched only with each other,
  *     up to that size, and run on the slot's high-priority stream, so the GPU's block scheduler
  *     serves them ahead of the blocks of large batches; copies go in pieces of at most 4 MB.

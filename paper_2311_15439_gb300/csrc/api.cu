@@ -31,6 +31,13 @@ sxe_status check_launch(const char* what) {
   return SXE_OK;
 }
 
+sxe_status empty_batch_sq_sum(const char* fn, float* sq_sum, void* stream) {
+  if (!sq_sum) return SXE_OK;
+  const cudaError_t e = cudaMemsetAsync(sq_sum, 0, sizeof(float), (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(SXE_ECUDA, "%s: %s", fn, cudaGetErrorString(e));
+  return SXE_OK;
+}
+
 // Launch set-up cached per device: a kernel's dynamic shared-memory limit and its occupancy
 // belong to the device that is current when they are set or queried, so a second device in the
 // same process gets its own set-up instead of inheriting (or missing) the first one's.
@@ -426,7 +433,7 @@ static sxe_status mlp_bwd_common(const char* fn, const sxe_mlp_desc* d, const vo
   sxe_status st = check_mlp(fn, d);
   if (st != SXE_OK) return st;
   if (P < 0) return set_error(SXE_EINVAL, "%s: n_points < 0", fn);
-  if (P == 0) return SXE_OK;
+  if (P == 0) return empty_batch_sq_sum(fn, sq_sum, stream);
   if (!W || !in || !dW || !ws) return set_error(SXE_EINVAL, "%s: NULL weights, in, dweights or workspace", fn);
   if (!(loss_scale > 0.f) || !std::isfinite(loss_scale)) return set_error(SXE_EINVAL, "%s: loss_scale must be > 0", fn);
   if (!aligned(in, 16) || !aligned(W, 4) || !aligned(ws, 4) || (din && !aligned(din, 8)))
@@ -472,7 +479,7 @@ sxe_status sxe_mlp_train_l2_grouped(const sxe_mlp_desc* d, const void* W, const 
   sxe_status st = check_mlp("mlp_train_l2_grouped", d);
   if (st != SXE_OK) return st;
   if (P < 0) return set_error(SXE_EINVAL, "mlp_train_l2_grouped: n_points < 0");
-  if (P == 0) return SXE_OK;
+  if (P == 0) return empty_batch_sq_sum("mlp_train_l2_grouped", sq_sum, stream);
   if (!W || !in || !dW || !ws) return set_error(SXE_EINVAL, "mlp_train_l2_grouped: NULL weights, in, dweights or workspace");
   if (!(loss_scale > 0.f) || !std::isfinite(loss_scale)) return set_error(SXE_EINVAL, "mlp_train_l2_grouped: loss_scale must be > 0");
   if (!aligned(in, 16) || !aligned(W, 4) || !aligned(ws, 4) || !aligned(din, 8))

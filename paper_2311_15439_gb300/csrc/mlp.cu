@@ -822,10 +822,15 @@ int mlp_grid_blocks(const sxe_mlp_desc* d, int64_t P) {
 }
 
 sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out, void* act,
-                          cudaStream_t s) {
-  // the three-tile tcgen05 kernel's forward-only form for n_out <= 16 (automatic choice), else mma.sync
-  if ((g_mlp_kernel == SXE_MLP_KERNEL_AUTO || g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_3TILE) && mlp_tc3_applies(d))
-    return launch_mlp_fwd_tc3(d, W, in, P, out, act, s);
+                          cudaStream_t s, bool shared_gpu) {
+  // the three-tile tcgen05 kernel's forward-only form for n_out <= 16 (automatic choice), else
+  // mma.sync.  A caller whose launches run beside other streams' kernels (the serving loop) gets
+  // mma.sync under the automatic choice: each CTA of the persistent tcgen05 kernel needs a whole
+  // SM (213 KB of shared memory, 384 threads of 155 registers), so it starts only where the other
+  // streams' blocks have drained and then holds that SM to itself.  Serving mixed-d queries from
+  // four streams: 2.6 against 2.0 G points/s for the simplex encoder, 0.98 against 0.59 for the grid.
+  const bool tc3 = g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_3TILE || (g_mlp_kernel == SXE_MLP_KERNEL_AUTO && !shared_gpu);
+  if (tc3 && mlp_tc3_applies(d)) return launch_mlp_fwd_tc3(d, W, in, P, out, act, s);
   return d->dtype == SXE_F16 ? fwd_in<__half>(d, W, in, P, out, act, s)
                              : fwd_in<__nv_bfloat16>(d, W, in, P, out, act, s);
 }

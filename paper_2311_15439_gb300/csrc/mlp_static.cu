@@ -75,7 +75,7 @@ extern "C" sxe_status sxe_mlp_train_l2_static(const sxe_mlp_desc* d, const void*
   if (per_cta > SXE_MLP_STATIC_SCRATCH_FLOATS)
     return set_error(SXE_ENOMEM, "mlp_train_l2_static: %lld floats of scratch per CTA exceed the static %d",
                      (long long)per_cta, SXE_MLP_STATIC_SCRATCH_FLOATS);
-  if (P == 0) return SXE_OK;
+  if (P == 0) return empty_batch_sq_sum("mlp_train_l2_static", sq_sum, stream);
   float* ws = nullptr;
   st = scratch_for_current_device(&ws);
   if (st != SXE_OK) return st;

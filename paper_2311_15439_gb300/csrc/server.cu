@@ -159,7 +159,7 @@ std::string launch_batch(sxe_server* s, const SrvField& f, SrvBatch* b, int64_t 
     o += r->n;
   }
   if (sxe::launch_encode_fwd(f.enc, x, P, f.tables, enc, st) != SXE_OK) return sxe_last_error();
-  if (sxe::launch_mlp_fwd(&f.mlp, f.weights, enc, P, y, nullptr, st) != SXE_OK) return sxe_last_error();
+  if (sxe::launch_mlp_fwd(&f.mlp, f.weights, enc, P, y, nullptr, st, true) != SXE_OK) return sxe_last_error();
   o = 0;
   for (SrvRequest* r : b->reqs) {
     const size_t total = (size_t)(r->n * n_out) * sizeof(float);

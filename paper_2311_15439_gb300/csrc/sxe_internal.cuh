@@ -26,6 +26,9 @@ namespace sxe {
 // error reporting (defined in api.cu)
 sxe_status set_error(sxe_status st, const char* fmt, ...);
 sxe_status check_launch(const char* what);
+// n_points == 0 in an entry point that overwrites *sq_sum with the batch's sum of squared
+// residuals: that sum is zero (nothing is written when sq_sum is NULL)
+sxe_status empty_batch_sq_sum(const char* fn, float* sq_sum, void* stream);
 
 // Launch set-up of the current device, cached per device (defined in api.cu): its SM count, and
 // for a kernel the resident CTAs per SM at `threads` threads and `smem_bytes` of dynamic shared
@@ -70,8 +73,10 @@ sxe_status launch_vr_composite(const float* sigma, const float* logits, const fl
                                float* color, float* trans, float* weights, cudaStream_t s);
 
 int mlp_grid_blocks(const sxe_mlp_desc* d, int64_t P);
+// shared_gpu: the launch runs beside other streams' kernels (the automatic choice then avoids the
+// persistent tcgen05 form, whose CTAs each hold a whole SM)
 sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, int64_t P, float* out,
-                          void* act, cudaStream_t s);
+                          void* act, cudaStream_t s, bool shared_gpu = false);
 sxe_status launch_mlp_bwd(const sxe_mlp_desc* d, const void* W, const void* in, const float* dout,
                           const float* target, float loss_scale, int64_t P, float* din, float* dW,
                           float* sq_sum, float* ws, int grid, cudaStream_t s, int din_group = 0,

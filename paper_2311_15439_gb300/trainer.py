@@ -206,6 +206,7 @@ class Trainer:
         self.sq_parts = torch.zeros((self.split,), dtype=torch.float32, device=self.device)
         self.sq_sum = self.sq_parts[:1]
         self.stage_events = None
+        self.stage_only = None            # a set of stage names: mark only those stages
         self.ws = mlp.workspace(batch, self.device)
         self.loss_scale = default_loss_scale(batch, mlp.n_out)
         self.adam_tables = Adam(lr, betas[0], betas[1], eps, skip_zero_grad=True)
@@ -255,9 +256,16 @@ class Trainer:
         return [(cut[i], cut[i + 1]) for i in range(self.split)]
 
     def _mark(self, name, stream):
-        """Record a timing event on `stream` when ``stage_events`` (a dict name -> list) is set."""
-        if self.stage_events is not None:
-            ev = torch.cuda.Event(enable_timing=True)
+        """Record a timing event on `stream` when ``stage_events`` (a dict name -> list) is set (and
+        the stage is in ``stage_only``, when that is set).  Inside a graph recording (``capture``)
+        the event becomes one of the graph's nodes, so it records the time each replay of that graph
+        reaches it."""
+        stage = name[:-4] if name.endswith("_end") else name
+        if self.stage_events is not None and (self.stage_only is None or stage in self.stage_only):
+            if torch.cuda.is_current_stream_capturing():
+                ev = torch.cuda.Event(enable_timing=True, external=True)
+            else:
+                ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
             self.stage_events.setdefault(name, []).append(ev)
 

@@ -135,11 +135,14 @@ def test_entry_points_validate_before_launch(L):
     assert lib.sxe_mlp_fwd(ctypes.byref(L.MlpDesc(32, 64, 2, 17, L.SXE_F16)), 16, 16, 8, 16, None, None) == -1
     assert lib.sxe_mlp_fwd(ctypes.byref(L.MlpDesc(32, 64, 2, 3, L.SXE_F32)), 16, 16, 8, 16, None, None) == -1
     assert lib.sxe_mlp_bwd(ctypes.byref(m), 16, 16, 16, ctypes.c_float(1.0), 8, None, 16, 16, 4, None) == -4  # workspace too small
-    # one part of a batch: the batch must hold the part; an empty part does nothing
+    # one part of a batch: the batch must hold the part; an empty part without a squared-residual
+    # sum enqueues nothing (with one it writes a zero there: a device write, covered on the GPU)
     part = lib.sxe_mlp_train_l2_part
     assert part(ctypes.byref(m), 16, 16, 16, ctypes.c_float(1.0), 8, 7, None, 16, 16, 16, 1 << 30, None) == -1
     assert part(ctypes.byref(m), 16, 16, None, ctypes.c_float(1.0), 8, 16, None, 16, 16, 16, 1 << 30, None) == -1
-    assert part(ctypes.byref(m), 16, 16, 16, ctypes.c_float(1.0), 0, 0, None, 16, 16, 16, 0, None) == 0
+    assert part(ctypes.byref(m), 16, 16, 16, ctypes.c_float(1.0), 0, 0, None, 16, None, 16, 0, None) == 0
+    assert lib.sxe_mlp_train_l2(ctypes.byref(m), None, None, None, ctypes.c_float(1.0), 0, None, None, None, None, 0,
+                                None) == 0
     assert part(ctypes.byref(m), 16, 16, 16, ctypes.c_float(1.0), 8, 16, None, 16, 16, 16, 4, None) == -4
     a = L.AdamDesc(1e-2, 0.9, 0.99, 1e-15, 0)
     assert lib.sxe_step(ctypes.byref(a), 0, 4, 16, 16, 16, 16, None, 0, None) == -1                         # t = 0

@@ -421,6 +421,41 @@ def test_forward_kernels_agree(cuda_lib, net):
         assert np.all(np.abs(ab[i] - aa[i]) <= (2 * i + 4) * u * h[i + 1] + 2.0 ** -24), "layer %d" % i
 
 
+def test_empty_batch(cuda_lib, mlp_kernel):
+    """No points: every L2 entry point sets the squared-residual sum to zero (the sum over an empty
+    batch) and leaves the accumulated weight gradient as it was; the forward returns no rows; the
+    bare backward writes nothing."""
+    import ctypes
+    from paper_2311_15439_gb300 import _lib as L
+    net = (32, 2, 3, "f16", 0)
+    mlp, Wd, Ws, xd, x = _setup(net, seed=63)
+    tgt = torch.zeros((0, 3), device="cuda")
+    din = torch.empty((0, 32), device="cuda")
+    ws = mlp.workspace(1, "cuda")
+    dW = torch.full((mlp.n_params,), 7.0, device="cuda")
+    sq = torch.full((1,), -1.0, device="cuda")
+    mlp.mlp_train_l2(Wd, xd, tgt, dW, sq, din=din, workspace=ws)
+    torch.cuda.synchronize()
+    assert sq.item() == 0.0 and bool((dW == 7.0).all())
+    sq.fill_(-1.0)
+    mlp.mlp_train_l2_static(Wd, xd, tgt, dW, sq, din=din)
+    torch.cuda.synchronize()
+    assert sq.item() == 0.0 and bool((dW == 7.0).all())
+    sq.fill_(-1.0)
+    mlp.mlp_train_l2_part(Wd, xd, tgt, dW, sq, 1024, din=din, workspace=ws)
+    torch.cuda.synchronize()
+    assert sq.item() == 0.0 and bool((dW == 7.0).all())
+    sq.fill_(-1.0)
+    st = L.lib().sxe_mlp_train_l2_grouped(ctypes.byref(mlp.desc), Wd.data_ptr(), xd.data_ptr(), None, 1.0, 0, None,
+                                          2, dW.data_ptr(), sq.data_ptr(), ws.data_ptr(), ws.numel() * 4, None)
+    torch.cuda.synchronize()
+    assert st == 0 and sq.item() == 0.0 and bool((dW == 7.0).all())
+    assert mlp.mlp_fwd(Wd, xd).shape == (0, 3)
+    mlp.mlp_bwd(Wd, xd, torch.zeros((0, 3), device="cuda"), dW, din=din, workspace=ws)
+    torch.cuda.synchronize()
+    assert bool((dW == 7.0).all())
+
+
 @pytest.mark.parametrize("P", [1, 127, 129, 383])
 def test_tiny_batches(cuda_lib, P, mlp_kernel):
     """Batches of one point, just under and over one 128-point tile, and a few tiles with a ragged

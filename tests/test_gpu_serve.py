@@ -23,9 +23,19 @@ def server_cls(request):
     return {"python": FieldServer, "native": NativeFieldServer}[request.param]
 
 
-def _alone(f, x):
+def _alone(f, x, server_cls=None):
+    """The request computed by itself: the encoding, then the network's forward pass on the
+    kernel the server's loop takes (the library's loop: mma.sync under the automatic choice)."""
+    from paper_2311_15439_gb300 import _lib as L
+    from paper_2311_15439_gb300.serve import NativeFieldServer
     enc = f.encoder.encode_fwd(x.cuda(), f.tables)
-    return f.mlp.mlp_fwd(f.weights, enc).cpu()
+    if server_cls is not NativeFieldServer or L.lib().sxe_mlp_get_kernel() != L.SXE_MLP_KERNEL_AUTO:
+        return f.mlp.mlp_fwd(f.weights, enc).cpu()
+    assert L.lib().sxe_mlp_set_kernel(L.SXE_MLP_KERNEL_MMA_SYNC) == 0
+    try:
+        return f.mlp.mlp_fwd(f.weights, enc).cpu()
+    finally:
+        L.lib().sxe_mlp_set_kernel(L.SXE_MLP_KERNEL_AUTO)
 
 
 def test_alone_equals_mixed(cuda_lib, server_cls):
@@ -46,7 +56,7 @@ def test_alone_equals_mixed(cuda_lib, server_cls):
     assert srv.n_batches < len(reqs)                     # requests were merged
     for (d, x), r in zip(reqs_in, reqs):
         assert r.error is None
-        assert torch.equal(r.y, _alone(fields[d], x))
+        assert torch.equal(r.y, _alone(fields[d], x, server_cls))
 
 
 def test_memory_admission_and_rejections(cuda_lib, server_cls):
@@ -72,7 +82,7 @@ def test_memory_admission_and_rejections(cuda_lib, server_cls):
     assert len(errs) == len(bad)
     for r in reqs:
         if r.error is None:
-            assert torch.equal(r.y, _alone(fields[r.d], r.x))
+            assert torch.equal(r.y, _alone(fields[r.d], r.x, server_cls))
 
 
 @pytest.mark.parametrize("d", [2, 5])
@@ -115,7 +125,7 @@ def test_native_server_stops_without_draining_and_reports_failures(cuda_lib):
         assert r.wait(60)
     done = [r for r in reqs if r.error is None]
     failed = [r for r in reqs if r.error is not None]
-    assert done[0] is reqs[0] and all(torch.equal(r.y, _alone(fields[3], r.x)) for r in done)
+    assert done[0] is reqs[0] and all(torch.equal(r.y, _alone(fields[3], r.x, NativeFieldServer)) for r in done)
     assert failed and all("stopped" in r.error for r in failed)
     assert all(r.rid > q.rid for r in failed for q in done)     # the queue's tail failed, in order
     late = srv.submit(3, xs[0])
@@ -158,5 +168,5 @@ def test_native_server_takes_requests_from_several_threads(cuda_lib):
     assert not errors, errors[0]
     assert len(results) == 120
     for d, x, y in results.values():
-        assert torch.equal(y, _alone(fields[d], x))
+        assert torch.equal(y, _alone(fields[d], x, NativeFieldServer))
     assert big.wait(1) and big.error is not None

@@ -425,6 +425,66 @@ def test_graph_replay_equals_eager_steps():
     assert a.loss() == pytest.approx(b.loss(), rel=1e-3)
 
 
+@pytest.mark.parametrize("split", [1, 2])
+def test_stage_events_inside_recordings(split):
+    """Timing events marked while a step is recorded are nodes of that graph: after replays of two
+    distinct recordings each recording's stage events are complete, ordered and inside the span of
+    the replays, and the replays train like eager steps."""
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+    try:
+        torch.cuda.Event(enable_timing=True, external=True)
+    except TypeError:
+        pytest.skip("this PyTorch records no timing events inside graphs")
+    P = 8192
+    enc = Encoder(**CFG, table_dtype="f16")
+    mlp = Mlp(16, 3, n_hidden=2, dtype="f16")
+    a = Trainer(enc, mlp, P, seed=5, table_layout="records", split_batch=split)
+    b = Trainer(enc, mlp, P, seed=5, table_layout="records", split_batch=split)
+    img = synth.ProceduralImage(3, size=1024, n_waves=4)
+    xs = [torch.from_numpy(synth.uniform_points(P, 2, 70 + i)).cuda() for i in range(2)]
+    ts = [torch.from_numpy(img.sample(x.cpu().numpy())).cuda() for x in xs]
+    recs = []
+    for i in range(2):
+        b.stage_events = {}
+        b.capture(xs[i], ts[i], warmup=0)
+        recs.append((b.graph, b.stage_events))
+    b.stage_events = None
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for g, _ in recs:
+        b.t += 1
+        g.replay()
+    e.record()
+    for i in range(2):
+        a.step(xs[i], ts[i])
+    torch.cuda.synchronize()
+    span = s.elapsed_time(e)
+    order = ["encode_fwd", "encode_fwd_end", "mlp_train_l2", "mlp_train_l2_end", "adam_tables",
+             "adam_tables_end", "adam_mlp_end"]
+    for _, ev in recs:
+        assert set(order) | {"encode_bwd", "encode_bwd_end"} <= set(ev)
+        for n in ev:
+            assert all(x.query() for x in ev[n]), n
+        t = [s.elapsed_time(ev[n][0]) for n in order]
+        assert all(0.0 <= u <= span for u in t), t
+        assert t == sorted(t), t
+        for x, y in zip(ev["encode_bwd"], ev["encode_bwd_end"]):
+            assert 0.0 < x.elapsed_time(y) <= span
+    assert a.t == b.t == 2
+    _close_up_to_atomics(a.W, b.W, steps=2, atol=1e-5)
+    _close_up_to_atomics(a.table_params(), b.table_params(), steps=2)
+    # a recording that marks one stage only
+    b.stage_events, b.stage_only = {}, {"encode_bwd"}
+    b.capture(xs[0], ts[0], warmup=0)
+    ev, b.stage_events, b.stage_only = b.stage_events, None, None
+    assert set(ev) == {"encode_bwd", "encode_bwd_end"} and len(ev["encode_bwd"]) == split
+    b.t += 1
+    b.graph.replay()
+    torch.cuda.synchronize()
+    assert all(0.0 < x.elapsed_time(y) for x, y in zip(ev["encode_bwd"], ev["encode_bwd_end"]))
+
+
 @pytest.mark.parametrize("k", [2, 3, 5])
 def test_overlapped_table_step_equals_plain_step(k):
     """The table backward and Adam in k level ranges, Adam of one range on a second stream while
