@@ -42,7 +42,8 @@ typedef enum {
   SXE_EINVAL = -1,        /* an argument is out of range or NULL where required */
   SXE_EUNSUPPORTED = -2,  /* valid but not implemented (e.g. d = 7)            */
   SXE_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed        */
-  SXE_ENOMEM = -4         /* a caller-provided workspace is too small           */
+  SXE_ENOMEM = -4         /* a caller-provided workspace or buffer is too small,
+                             or the host could not allocate (serving requests)  */
 } sxe_status;
 
 typedef enum { SXE_SIMPLEX = 0, SXE_GRID = 1 } sxe_kind;
@@ -519,12 +520,15 @@ sxe_status sxe_server_create(const sxe_server_desc* desc, sxe_server** out);
  * outlive the server. */
 sxe_status sxe_server_add_field(sxe_server* srv, const sxe_encoder* enc, const void* tables,
                                 const sxe_mlp_desc* mlp, const void* weights);
+/* Starts the scheduler thread (SXE_ENOMEM if it cannot be created); SXE_EINVAL if the server
+ * is already running or has no field.  A stopped server may be started again. */
 sxe_status sxe_server_start(sxe_server* srv);
 /* Queues a request: n_points points x_host [n][d] binary32 and their values y_host [n][n_out]
  * binary32, both host memory (pinned for asynchronous copies) that must stay valid until the
  * request completes.  *request_id receives its id.  SXE_EINVAL (and no request) for a stopped
  * server, an unknown d, n_points < 1 or above max_batch_points, a request whose buffers could
- * never fit in the arena, or NULL buffers.  Thread-safe. */
+ * never fit in the arena, or NULL buffers; SXE_ENOMEM if the host cannot hold the request.
+ * Thread-safe. */
 sxe_status sxe_server_submit(sxe_server* srv, int32_t d, const float* x_host, int64_t n_points,
                              float* y_host, int64_t* request_id);
 /* Waits up to timeout_us microseconds (0: just polls) for a request.  *state: 0 still pending,
@@ -534,11 +538,13 @@ sxe_status sxe_server_submit(sxe_server* srv, int32_t d, const float* x_host, in
 sxe_status sxe_server_wait(sxe_server* srv, int64_t request_id, int64_t timeout_us, int32_t* state,
                            double* latency_s);
 /* Stops the scheduler: with drain != 0 after every queued request has run, else queued
- * requests fail; batches in flight always complete. */
+ * requests fail; batches in flight always complete.  Thread-safe: a second caller returns once
+ * the first has stopped the server. */
 sxe_status sxe_server_stop(sxe_server* srv, int32_t drain);
 /* Batches launched so far and the largest arena footprint in flight. */
 sxe_status sxe_server_stats(const sxe_server* srv, int64_t* n_batches, int64_t* peak_bytes);
-/* Stops (draining) if running, waits for its streams and releases the server. */
+/* Stops (draining) if running, waits for its streams and releases the server.  No other call
+ * on the same server may run concurrently with it or follow it. */
 sxe_status sxe_server_destroy(sxe_server* srv);
 
 /* Diagnostic of the bounded waits: runs, on `stream`, one mbarrier wait of the kind every

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <exception>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -64,6 +65,7 @@ struct sxe_server {
   int inflight = 0;
   bool running = false, stopping = false, drain = true;
   std::mutex mu;
+  std::mutex stop_mu;            // serialises sxe_server_stop calls (one of them joins the thread)
   std::condition_variable cv_sched, cv_done;
   std::thread thread;
 };
@@ -313,7 +315,12 @@ sxe_status sxe_server_start(sxe_server* s) {
   if (!any) return set_error(SXE_EINVAL, "server_start: no field registered");
   s->running = true;
   s->stopping = false;
-  s->thread = std::thread(serve_loop, s);
+  try {
+    s->thread = std::thread(serve_loop, s);
+  } catch (const std::exception& e) {
+    s->running = false;
+    return set_error(SXE_ENOMEM, "server_start: no scheduler thread (%s)", e.what());
+  }
   return SXE_OK;
 }
 
@@ -327,16 +334,26 @@ sxe_status sxe_server_submit(sxe_server* s, int32_t d, const float* x, int64_t n
     return set_error(SXE_EINVAL, "server_submit: %lld points outside 1..max_batch_points", (long long)n);
   if (batch_bytes(s->fields[d], n) > s->desc.arena_bytes)
     return set_error(SXE_EINVAL, "server_submit: %lld points need more than the arena", (long long)n);
-  std::unique_ptr<SrvRequest> r(new SrvRequest);
-  r->id = s->next_id++;
-  r->d = d;
-  r->x = x;
-  r->y = y;
-  r->n = n;
-  r->t_arrival = Clock::now();
-  *request_id = r->id;
-  s->queue.push_back(r.get());
-  s->requests.emplace(r->id, std::move(r));
+  try {
+    std::unique_ptr<SrvRequest> r(new SrvRequest);
+    r->id = s->next_id;
+    r->d = d;
+    r->x = x;
+    r->y = y;
+    r->n = n;
+    r->t_arrival = Clock::now();
+    SrvRequest* q = r.get();
+    s->requests.emplace(r->id, std::move(r));
+    try {
+      s->queue.push_back(q);
+    } catch (...) {
+      s->requests.erase(q->id);
+      throw;
+    }
+    *request_id = s->next_id++;
+  } catch (const std::exception& e) {
+    return set_error(SXE_ENOMEM, "server_submit: %s", e.what());
+  }
   lock.unlock();
   s->cv_sched.notify_all();
   return SXE_OK;
@@ -362,6 +379,7 @@ sxe_status sxe_server_wait(sxe_server* s, int64_t id, int64_t timeout_us, int32_
 
 sxe_status sxe_server_stop(sxe_server* s, int32_t drain) {
   if (!s) return sxe::set_error(SXE_EINVAL, "server_stop: NULL server");
+  std::lock_guard<std::mutex> one_stop(s->stop_mu);
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (!s->running) return SXE_OK;

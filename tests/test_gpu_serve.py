@@ -170,3 +170,35 @@ def test_native_server_takes_requests_from_several_threads(cuda_lib):
     for d, x, y in results.values():
         assert torch.equal(y, _alone(fields[d], x, NativeFieldServer))
     assert big.wait(1) and big.error is not None
+
+
+def test_native_server_concurrent_stops_and_restart(cuda_lib):
+    """Two threads stop a draining server at once: both calls return, every queued request has
+    run; the server then starts again and answers as before."""
+    import threading
+    from paper_2311_15439_gb300.serve import NativeFieldServer
+    fields = _fields()
+    srv = NativeFieldServer(fields, mem_budget_bytes=16 << 20, n_slots=2, max_batch_points=1 << 16).start()
+    xs = [torch.from_numpy(synth.uniform_points(20000, 3, 300 + i)).pin_memory() for i in range(40)]
+    reqs = [srv.submit(3, x) for x in xs]
+    errors = []
+
+    def stopper():
+        try:
+            srv.stop(drain=True)
+        except Exception as exc:         # surfaced in the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=stopper) for _ in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(60)
+    assert not any(t.is_alive() for t in threads) and not errors, errors
+    assert all(r.wait(1) and r.error is None for r in reqs)
+    assert all(torch.equal(r.y, _alone(fields[3], x, NativeFieldServer)) for r, x in zip(reqs, xs))
+    srv.start()
+    again = srv.submit(2, xs[0][:, :2].contiguous().pin_memory())
+    assert again.wait(60) and again.error is None
+    srv.stop()
+    assert torch.equal(again.y, _alone(fields[2], xs[0][:, :2].contiguous(), NativeFieldServer))
