@@ -425,6 +425,50 @@ def test_graph_replay_equals_eager_steps():
     assert a.loss() == pytest.approx(b.loss(), rel=1e-3)
 
 
+def test_full_size_image_step_replayed_equals_eager():
+    """The image workload at full size (d = 2, L = 16, F = 2, T = 2^22 fp16 tables, 2 GiB of state
+    records, network 32-64-64-3, 2^18 points per step), trained the way the benchmark times it:
+    one recording of the step per resident batch, replayed.  Three replayed steps give the
+    parameters of three eager steps (up to the order of the table backward's atomics), over every
+    table entry either run moved and every network weight."""
+    from paper_2311_15439_gb300.api import Encoder, Mlp
+    from paper_2311_15439_gb300.trainer import Trainer
+    P = 1 << 18
+    cfg = dict(d=2, n_levels=16, n_features=2, log2_T=22, base_res=16.0, growth=2.0)
+    img = synth.ProceduralImage(3, size=16384, n_waves=64)
+    xs = [torch.from_numpy(synth.uniform_points(P, 2, 80 + i)).cuda() for i in range(3)]
+    ts = [torch.from_numpy(img.sample(x.cpu().numpy())).cuda() for x in xs]
+
+    def make():
+        enc = Encoder(**cfg, table_dtype="f16")
+        return Trainer(enc, Mlp(32, 3, n_hidden=2, dtype="f16"), P, seed=3, table_layout="records")
+
+    a = make()
+    init = a.table_params().clone()
+    for x, t in zip(xs, ts):
+        a.step(x, t)
+    pa, Wa = a.table_params().clone(), a.W.clone()
+    del a
+    torch.cuda.empty_cache()
+    b = make()
+    graphs = []
+    for x, t in zip(xs, ts):
+        b.capture(x, t, warmup=0)
+        graphs.append(b.graph)
+    for g in graphs:
+        b.t += 1
+        g.replay()
+    torch.cuda.synchronize()
+    assert b.t == 3 and int(b.t_dev.item()) == 3
+    pb = b.table_params()
+    moved = (pa != init) | (pb != init)
+    assert int(moved.sum()) > 1_000_000                  # millions of touched entries compared
+    # (the fraction is taken over the moved entries only, not diluted by the untouched majority;
+    # a replay on the wrong batch or step count moves most of them differently)
+    _close_up_to_atomics(pa[moved], pb[moved], steps=3, max_frac=1e-2)
+    _close_up_to_atomics(Wa, b.W, steps=3, atol=1e-5)
+
+
 @pytest.mark.parametrize("split", [1, 2])
 def test_stage_events_inside_recordings(split):
     """Timing events marked while a step is recorded are nodes of that graph: after replays of two
