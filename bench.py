@@ -43,7 +43,7 @@ N_POOL = 8   # distinct resident batches cycled through the timed steps
 # kernels in one ncu capture of this workload, profiles/train_step_image2d_L16_T2^22_P2^18_dram_traffic.md),
 # with the SHA-1 of the kernel sources it was taken on: reported only while those sources are unchanged.
 TRAFFIC = {
-    "encode_bwd": (35.8e6 + 755.5e6, "ce99299f167c65a5c0953733d60d2fe2ffe4879f",
+    "encode_bwd": (35.8e6 + 755.7e6, "b8bc06d238dec3bd0fd796c812d8e2ac3a899f34",
                    ("encode.cu", "encode_common.cuh", "lattice.cuh")),
 }
 
@@ -652,62 +652,62 @@ PER_CONFIG = [
 # ``bench.py --profile-encode`` (the volumetric configuration at 2^16 rays x 64 samples there):
 # L2 sector throughput and DRAM throughput as a percentage of their peaks, L2 hit rate, DRAM bytes
 # per point.  Reported only while the kernel sources hash to ENCODE_NCU_SHA.
-ENCODE_NCU_SHA = 'ce99299f167c65a5c0953733d60d2fe2ffe4879f'
+ENCODE_NCU_SHA = 'b8bc06d238dec3bd0fd796c812d8e2ac3a899f34'
 ENCODE_NCU = {
  "plain_fp32_2d_L8_T2^14_P2^16/simplex_raw/fwd": {
-  "l2_throughput_pct": 21.2,
-  "l2_sectors_pct": 9.1,
-  "dram_throughput_pct": 1.3,
-  "l2_hit_pct": 66.4,
-  "dram_bytes_per_point": 13.9,
+  "l2_throughput_pct": 21.8,
+  "l2_sectors_pct": 9.4,
+  "dram_throughput_pct": 1.4,
+  "l2_hit_pct": 66.1,
+  "dram_bytes_per_point": 14.0,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/simplex_raw/bwd": {
   "l2_throughput_pct": 16.6,
   "l2_sectors_pct": 7.9,
   "dram_throughput_pct": 4.9,
-  "l2_hit_pct": 47.1,
-  "dram_bytes_per_point": 150.0,
+  "l2_hit_pct": 47.0,
+  "dram_bytes_per_point": 150.1,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/simplex_equal_mem/fwd": {
-  "l2_throughput_pct": 24.4,
+  "l2_throughput_pct": 24.7,
   "l2_sectors_pct": 10.3,
   "dram_throughput_pct": 1.5,
-  "l2_hit_pct": 69.0,
+  "l2_hit_pct": 69.5,
   "dram_bytes_per_point": 15.3,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/simplex_equal_mem/bwd": {
-  "l2_throughput_pct": 16.1,
+  "l2_throughput_pct": 16.2,
   "l2_sectors_pct": 7.7,
   "dram_throughput_pct": 4.7,
-  "l2_hit_pct": 47.2,
+  "l2_hit_pct": 46.9,
   "dram_bytes_per_point": 151.4,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/grid/fwd": {
-  "l2_throughput_pct": 24.2,
-  "l2_sectors_pct": 10.0,
-  "dram_throughput_pct": 1.3,
-  "l2_hit_pct": 71.0,
+  "l2_throughput_pct": 24.9,
+  "l2_sectors_pct": 10.3,
+  "dram_throughput_pct": 1.4,
+  "l2_hit_pct": 70.9,
   "dram_bytes_per_point": 14.9,
   "points_captured": 65536
  },
  "plain_fp32_2d_L8_T2^14_P2^16/grid/bwd": {
-  "l2_throughput_pct": 20.4,
-  "l2_sectors_pct": 9.1,
-  "dram_throughput_pct": 4.7,
-  "l2_hit_pct": 48.8,
+  "l2_throughput_pct": 20.7,
+  "l2_sectors_pct": 9.2,
+  "dram_throughput_pct": 4.8,
+  "l2_hit_pct": 48.7,
   "dram_bytes_per_point": 151.0,
   "points_captured": 65536
  },
  "image_2d_L16_T2^22_fp16_P2^18/simplex_raw/fwd": {
-  "l2_throughput_pct": 50.4,
-  "l2_sectors_pct": 37.0,
-  "dram_throughput_pct": 70.6,
-  "l2_hit_pct": 28.6,
-  "dram_bytes_per_point": 1224.7,
+  "l2_throughput_pct": 58.7,
+  "l2_sectors_pct": 38.3,
+  "dram_throughput_pct": 36.8,
+  "l2_hit_pct": 51.4,
+  "dram_bytes_per_point": 594.7,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/simplex_raw/bwd": {
@@ -715,51 +715,51 @@ ENCODE_NCU = {
   "l2_sectors_pct": 11.9,
   "dram_throughput_pct": 33.2,
   "l2_hit_pct": 29.6,
-  "dram_bytes_per_point": 1967.3,
+  "dram_bytes_per_point": 1968.1,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/simplex_equal_mem/fwd": {
-  "l2_throughput_pct": 50.0,
-  "l2_sectors_pct": 37.0,
-  "dram_throughput_pct": 72.2,
-  "l2_hit_pct": 27.5,
-  "dram_bytes_per_point": 1318.8,
+  "l2_throughput_pct": 58.8,
+  "l2_sectors_pct": 38.4,
+  "dram_throughput_pct": 38.0,
+  "l2_hit_pct": 51.0,
+  "dram_bytes_per_point": 632.0,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/simplex_equal_mem/bwd": {
-  "l2_throughput_pct": 24.4,
+  "l2_throughput_pct": 24.2,
   "l2_sectors_pct": 11.9,
-  "dram_throughput_pct": 34.2,
-  "l2_hit_pct": 29.0,
-  "dram_bytes_per_point": 2063.8,
+  "dram_throughput_pct": 34.0,
+  "l2_hit_pct": 28.9,
+  "dram_bytes_per_point": 2062.9,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/grid/fwd": {
-  "l2_throughput_pct": 49.4,
-  "l2_sectors_pct": 35.8,
-  "dram_throughput_pct": 68.7,
-  "l2_hit_pct": 28.8,
-  "dram_bytes_per_point": 1351.2,
+  "l2_throughput_pct": 59.0,
+  "l2_sectors_pct": 37.5,
+  "dram_throughput_pct": 35.7,
+  "l2_hit_pct": 52.1,
+  "dram_bytes_per_point": 627.5,
   "points_captured": 262144
  },
  "image_2d_L16_T2^22_fp16_P2^18/grid/bwd": {
-  "l2_throughput_pct": 26.4,
+  "l2_throughput_pct": 26.6,
   "l2_sectors_pct": 12.6,
-  "dram_throughput_pct": 31.8,
+  "dram_throughput_pct": 32.1,
   "l2_hit_pct": 33.7,
-  "dram_bytes_per_point": 2196.5,
+  "dram_bytes_per_point": 2197.0,
   "points_captured": 262144
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/simplex_raw/fwd": {
-  "l2_throughput_pct": 63.0,
-  "l2_sectors_pct": 22.8,
-  "dram_throughput_pct": 3.5,
+  "l2_throughput_pct": 64.6,
+  "l2_sectors_pct": 23.4,
+  "dram_throughput_pct": 3.6,
   "l2_hit_pct": 90.0,
-  "dram_bytes_per_point": 54.6,
+  "dram_bytes_per_point": 54.5,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/simplex_raw/bwd": {
-  "l2_throughput_pct": 70.8,
+  "l2_throughput_pct": 70.9,
   "l2_sectors_pct": 25.7,
   "dram_throughput_pct": 11.5,
   "l2_hit_pct": 55.2,
@@ -767,27 +767,27 @@ ENCODE_NCU = {
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/simplex_equal_mem/fwd": {
-  "l2_throughput_pct": 64.6,
-  "l2_sectors_pct": 23.3,
-  "dram_throughput_pct": 3.8,
+  "l2_throughput_pct": 66.0,
+  "l2_sectors_pct": 23.8,
+  "dram_throughput_pct": 3.9,
   "l2_hit_pct": 90.3,
-  "dram_bytes_per_point": 60.7,
+  "dram_bytes_per_point": 60.8,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/simplex_equal_mem/bwd": {
-  "l2_throughput_pct": 77.0,
-  "l2_sectors_pct": 27.1,
+  "l2_throughput_pct": 76.7,
+  "l2_sectors_pct": 27.0,
   "dram_throughput_pct": 7.2,
   "l2_hit_pct": 61.4,
-  "dram_bytes_per_point": 193.7,
+  "dram_bytes_per_point": 193.8,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/grid/fwd": {
-  "l2_throughput_pct": 67.7,
-  "l2_sectors_pct": 23.6,
+  "l2_throughput_pct": 65.1,
+  "l2_sectors_pct": 22.8,
   "dram_throughput_pct": 2.2,
-  "l2_hit_pct": 94.4,
-  "dram_bytes_per_point": 59.2,
+  "l2_hit_pct": 94.2,
+  "dram_bytes_per_point": 59.3,
   "points_captured": 1048576
  },
  "sdf_3d_L16_T2^19_bf16_P2^20/grid/bwd": {
@@ -795,15 +795,15 @@ ENCODE_NCU = {
   "l2_sectors_pct": 25.9,
   "dram_throughput_pct": 6.3,
   "l2_hit_pct": 59.4,
-  "dram_bytes_per_point": 335.6,
+  "dram_bytes_per_point": 335.5,
   "points_captured": 1048576
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_raw/fwd": {
-  "l2_throughput_pct": 58.9,
-  "l2_sectors_pct": 21.2,
-  "dram_throughput_pct": 5.5,
+  "l2_throughput_pct": 58.3,
+  "l2_sectors_pct": 21.0,
+  "dram_throughput_pct": 5.4,
   "l2_hit_pct": 89.9,
-  "dram_bytes_per_point": 70.6,
+  "dram_bytes_per_point": 70.7,
   "points_captured": 4194304
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_raw/bwd": {
@@ -811,12 +811,12 @@ ENCODE_NCU = {
   "l2_sectors_pct": 23.1,
   "dram_throughput_pct": 9.4,
   "l2_hit_pct": 54.5,
-  "dram_bytes_per_point": 293.0,
+  "dram_bytes_per_point": 293.1,
   "points_captured": 4194304
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/simplex_equal_mem/fwd": {
-  "l2_throughput_pct": 61.4,
-  "l2_sectors_pct": 22.0,
+  "l2_throughput_pct": 60.8,
+  "l2_sectors_pct": 21.8,
   "dram_throughput_pct": 5.2,
   "l2_hit_pct": 90.8,
   "dram_bytes_per_point": 71.9,
@@ -827,15 +827,15 @@ ENCODE_NCU = {
   "l2_sectors_pct": 27.3,
   "dram_throughput_pct": 5.9,
   "l2_hit_pct": 62.1,
-  "dram_bytes_per_point": 153.8,
+  "dram_bytes_per_point": 153.7,
   "points_captured": 4194304
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/grid/fwd": {
-  "l2_throughput_pct": 60.0,
-  "l2_sectors_pct": 21.0,
-  "dram_throughput_pct": 3.4,
-  "l2_hit_pct": 93.7,
-  "dram_bytes_per_point": 71.7,
+  "l2_throughput_pct": 60.3,
+  "l2_sectors_pct": 21.1,
+  "dram_throughput_pct": 3.3,
+  "l2_hit_pct": 93.9,
+  "dram_bytes_per_point": 71.8,
   "points_captured": 4194304
  },
  "volume_3d_L16_T2^19_fp16_2^16rays_x1024/grid/bwd": {

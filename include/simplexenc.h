@@ -118,6 +118,21 @@ sxe_status sxe_encoder_level_index(const sxe_encoder* enc, int32_t* box_width);
  * same encoder. */
 sxe_status sxe_encoder_set_bwd_aggregation(sxe_encoder* enc, int32_t on);
 
+/* Work-item order of the forward encoding (sxe_encode_fwd, sxe_encode_fwd_marked).  The
+ * outputs are the same bit for bit in every order (each (point, level) item computes alone);
+ * only the memory traffic differs.  SXE_FWD_ORDER_POINT_MAJOR: consecutive threads take the
+ * levels of one point, then the next point, so every level's table is read at the same time.
+ * SXE_FWD_ORDER_LEVEL_MAJOR: blocks take consecutive points of one level, the levels in turn, so
+ * one or two levels' tables are read at a time; where all the tables exceed L2 but one level's
+ * fits, a table sector fetched for one point stays in L2 for the later points of its level.
+ * SXE_FWD_ORDER_AUTO (the default): level-major when L tables of T entries exceed the device's
+ * L2 and one of them takes at most half of it, else point-major.  SXE_EINVAL for a NULL
+ * encoder or another value.  Not thread-safe with concurrent calls on the same encoder. */
+#define SXE_FWD_ORDER_AUTO 0
+#define SXE_FWD_ORDER_POINT_MAJOR 1
+#define SXE_FWD_ORDER_LEVEL_MAJOR 2
+sxe_status sxe_encoder_set_fwd_order(sxe_encoder* enc, int32_t order);
+
 /* Forward encoding, Sec. 5 steps (a)-(d): for every point and level, scale and skew
  * (Eq. 2) the point, find its simplex by sorting the fractional parts (Sec. 4.2),
  * weight its n+1 vertices barycentrically (Sec. 4.3), hash each vertex into that

@@ -19,11 +19,12 @@ SXE_INDEX_HASH, SXE_INDEX_DENSE_COARSE = 0, 1
 SXE_MAX_LEVELS = 32
 SXE_MLP_KERNEL_AUTO, SXE_MLP_KERNEL_MMA_SYNC, SXE_MLP_KERNEL_TCGEN05, SXE_MLP_KERNEL_TCGEN05_PIPELINED = 0, 1, 2, 3
 SXE_MLP_KERNEL_TCGEN05_3TILE = 4
+SXE_FWD_ORDER_AUTO, SXE_FWD_ORDER_POINT_MAJOR, SXE_FWD_ORDER_LEVEL_MAJOR = 0, 1, 2
 
 #: every function the header declares (checked by the export test)
 EXPORTS = (
     "sxe_encoder_create", "sxe_encoder_destroy", "sxe_encoder_level_params", "sxe_encoder_level_index",
-    "sxe_encoder_set_bwd_aggregation",
+    "sxe_encoder_set_bwd_aggregation", "sxe_encoder_set_fwd_order",
     "sxe_encode_fwd", "sxe_encode_fwd_marked", "sxe_encode_bwd", "sxe_encode_bwd_levels", "sxe_encode_bwd_kernel_count",
     "sxe_encode_bwd_levels_kernel_count", "sxe_encode_bwd_coarse_levels", "sxe_encode_bwd_input",
     "sxe_encode_vertices",
@@ -75,6 +76,7 @@ def _declare(L):
         "sxe_encoder_level_params": (i32, [vp, vp, vp]),
         "sxe_encoder_level_index": (i32, [vp, vp]),
         "sxe_encoder_set_bwd_aggregation": (i32, [vp, i32]),
+        "sxe_encoder_set_fwd_order": (i32, [vp, i32]),
         "sxe_encode_fwd": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_encode_fwd_marked": (i32, [vp, vp, i64, vp, vp, vp, vp]),
         "sxe_encode_bwd": (i32, [vp, vp, i64, vp, vp, i64, vp, vp]),

@@ -148,6 +148,14 @@ class Encoder:
         coherent, such as the samples along rays."""
         L.check(L.lib().sxe_encoder_set_bwd_aggregation(self._h, 1 if on else 0), "sxe_encoder_set_bwd_aggregation")
 
+    def set_fwd_order(self, order: str) -> None:
+        """Work-item order of the forward encoding (``sxe_encoder_set_fwd_order``): "auto"
+        (level-major where the tables exceed L2 but one level's fits), "point" or "level"; the
+        outputs are the same bit for bit."""
+        code = {"auto": L.SXE_FWD_ORDER_AUTO, "point": L.SXE_FWD_ORDER_POINT_MAJOR,
+                "level": L.SXE_FWD_ORDER_LEVEL_MAJOR}[order]
+        L.check(L.lib().sxe_encoder_set_fwd_order(self._h, code), "sxe_encoder_set_fwd_order")
+
     def bwd_kernel_count(self, n_points: int, levels: tuple[int, int] | None = None) -> int:
         """Kernels one ``encode_bwd`` call launches for this many points (0, 1 or 2)."""
         if levels is None:

@@ -43,6 +43,7 @@ sxe_status empty_batch_sq_sum(const char* fn, float* sq_sum, void* stream) {
 // same process gets its own set-up instead of inheriting (or missing) the first one's.
 static std::mutex g_setup_mu;
 static std::map<int, int> g_sms;
+static std::map<int, int64_t> g_l2;
 static std::map<std::tuple<int, const void*, int, int>, int> g_ctas;
 static std::map<std::pair<int, const void*>, int> g_smem_limit;   // dynamic shared-memory limit set per kernel
 
@@ -60,6 +61,17 @@ int device_sm_count() {
   int n = 0;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
   g_sms[dev] = n;
+  return n;
+}
+
+int64_t device_l2_bytes() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  auto it = g_l2.find(dev);
+  if (it != g_l2.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev) != cudaSuccess || n < 1) n = 96 << 20;
+  g_l2[dev] = n;
   return n;
 }
 
@@ -176,6 +188,14 @@ sxe_status sxe_encoder_set_bwd_aggregation(sxe_encoder* e, int32_t on) {
   if (!e) return set_error(SXE_EINVAL, "encoder_set_bwd_aggregation: NULL encoder");
   if (on != 0 && on != 1) return set_error(SXE_EINVAL, "encoder_set_bwd_aggregation: on=%d is not 0 or 1", on);
   e->bwd_aggregate = on;
+  return SXE_OK;
+}
+
+sxe_status sxe_encoder_set_fwd_order(sxe_encoder* e, int32_t order) {
+  if (!e) return set_error(SXE_EINVAL, "encoder_set_fwd_order: NULL encoder");
+  if (order < SXE_FWD_ORDER_AUTO || order > SXE_FWD_ORDER_LEVEL_MAJOR)
+    return set_error(SXE_EINVAL, "encoder_set_fwd_order: order=%d is not 0, 1 or 2", order);
+  e->fwd_order = order;
   return SXE_OK;
 }
 

@@ -3,8 +3,9 @@
 //
 // Work item = one (point, level) pair, flattened as i = p * L + l so that consecutive
 // threads write consecutive F-feature groups of the [P][L*F] output (coalesced) and
-// read consecutive groups of dout.  Every item issues its V = d+1 (simplex) or 2^d
-// (grid) independent gathers before it consumes any of them.
+// read consecutive groups of dout; the forward can also take the items level by level
+// (fwd_level_major below).  Every item issues its V = d+1 (simplex) or 2^d (grid)
+// independent gathers before it consumes any of them.
 #include <algorithm>
 
 #include "encode_common.cuh"
@@ -17,7 +18,7 @@ using namespace encode_detail;
 template <bool SIMPLEX, int D, int F, typename TT>
 __global__ void __launch_bounds__(kThreads)
 encode_fwd_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__ tables, int64_t tstride,
-                  void* __restrict__ out, const EncParams prm, uint32_t* __restrict__ touched) {
+                  void* __restrict__ out, const EncParams prm, uint32_t* __restrict__ touched, int bpl) {
   constexpr int V = Verts<SIMPLEX, D>::V;
   __shared__ float s_scale[SXE_MAX_LEVELS];
   __shared__ uint32_t s_width[SXE_MAX_LEVELS];
@@ -27,7 +28,7 @@ encode_fwd_kernel(const float* __restrict__ x, int64_t P, const TT* __restrict__
   }
   __syncthreads();
   const int L = prm.n_levels;
-  const Item it = item_of(L);
+  const Item it = bpl ? item_level_major(bpl) : item_of(L);
   if (it.p >= P) return;
   float xv[D];
   load_point<D>(x, it.p, xv);
@@ -512,14 +513,30 @@ sxe_status launch_encode_bwd_input(const sxe_encoder* enc, const float* x, int64
 
 namespace {
 
+// The forward's work-item order.  Point-major (the level fastest) keeps every level's table in use
+// at once, which suits tables that L2 holds.  Level-major (blocks of consecutive points of one
+// level, the levels in turn) keeps one or two levels' tables in use at a time, so that where the
+// tables together exceed L2 but one level's fits, a sector fetched for one point stays in L2 for
+// the later points of its level: image workload (16 levels of 16 MB fp16) 71 -> 60 us per
+// forward; the SDF-style workload (32 MB of tables in all) 0.750 -> 0.764 ms per step the other
+// way.  The backward keeps the point-major order (level-major re-reads each dout sector once per
+// level: image 313 -> 324 us).
+bool fwd_level_major(const sxe_encoder* enc, int64_t entry_stride) {
+  if (enc->fwd_order != SXE_FWD_ORDER_AUTO) return enc->fwd_order == SXE_FWD_ORDER_LEVEL_MAJOR;
+  const int64_t level_bytes = (entry_stride << enc->desc.log2_T) * (enc->desc.table_dtype == SXE_F32 ? 4 : 2);
+  const int64_t l2 = device_l2_bytes();
+  return level_bytes * enc->desc.n_levels > l2 && 2 * level_bytes <= l2;
+}
+
 template <bool SIMPLEX, int D, int F>
 sxe_status fwd_tt(const sxe_encoder* enc, const float* x, int64_t P, const void* tab, int64_t ts, void* out,
                   uint32_t* touched, cudaStream_t s) {
-  const unsigned g = grid_for(P, enc->prm.n_levels);
+  const int bpl = fwd_level_major(enc, ts) ? (int)((P + kThreads - 1) / kThreads) : 0;
+  const unsigned g = bpl ? (unsigned)bpl * enc->prm.n_levels : grid_for(P, enc->prm.n_levels);
   switch (enc->desc.table_dtype) {
-    case SXE_F32: encode_fwd_kernel<SIMPLEX, D, F, float><<<g, kThreads, 0, s>>>(x, P, (const float*)tab, ts, out, enc->prm, touched); break;
-    case SXE_F16: encode_fwd_kernel<SIMPLEX, D, F, __half><<<g, kThreads, 0, s>>>(x, P, (const __half*)tab, ts, out, enc->prm, touched); break;
-    default: encode_fwd_kernel<SIMPLEX, D, F, __nv_bfloat16><<<g, kThreads, 0, s>>>(x, P, (const __nv_bfloat16*)tab, ts, out, enc->prm, touched); break;
+    case SXE_F32: encode_fwd_kernel<SIMPLEX, D, F, float><<<g, kThreads, 0, s>>>(x, P, (const float*)tab, ts, out, enc->prm, touched, bpl); break;
+    case SXE_F16: encode_fwd_kernel<SIMPLEX, D, F, __half><<<g, kThreads, 0, s>>>(x, P, (const __half*)tab, ts, out, enc->prm, touched, bpl); break;
+    default: encode_fwd_kernel<SIMPLEX, D, F, __nv_bfloat16><<<g, kThreads, 0, s>>>(x, P, (const __nv_bfloat16*)tab, ts, out, enc->prm, touched, bpl); break;
   }
   return check_launch("encode_fwd");
 }

@@ -1,5 +1,5 @@
 // Work-item helpers shared by the encoding kernels (forward, backward, input gradient, table
-// step): one thread per (point, level) pair, the level fastest.
+// step): one thread per (point, level) pair, the level fastest (or, for the forward, level-major).
 #pragma once
 
 #include "sxe_internal.cuh"
@@ -22,6 +22,13 @@ __device__ __forceinline__ void lattice(const float (&x)[D], float s, float skew
 // with 32-bit divisions only: blockIdx.x = qb L + rb gives i = qb kThreads L + j with
 // j = rb kThreads + threadIdx.x < L kThreads, so i / L = qb kThreads + j / L.
 struct Item { int64_t p; int l; };
+// Level-major decode: blocks [l bpl, (l + 1) bpl) take level l of the points (blockIdx.x - l bpl)
+// kThreads + threadIdx.x, so that the blocks in flight at any time read one or two levels' tables.
+__device__ __forceinline__ Item item_level_major(int bpl) {
+  const uint32_t l = blockIdx.x / (uint32_t)bpl;
+  return Item{(int64_t)(blockIdx.x - l * (uint32_t)bpl) * kThreads + threadIdx.x, (int)l};
+}
+
 __device__ __forceinline__ Item item_of(int L) {
   if ((L & (L - 1)) == 0) {                          // L a power of two: shifts
     const int sh = __ffs(L) - 1;

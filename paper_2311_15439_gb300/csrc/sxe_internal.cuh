@@ -19,6 +19,7 @@ struct sxe_encoder {
   uint32_t box_width[SXE_MAX_LEVELS];   // lattice coordinates per axis of [0,1]^d at each level
   sxe::EncParams prm;
   int32_t bwd_aggregate = 0;            // backward: warp-level sum of colliding terms (coherent batches)
+  int32_t fwd_order = 0;                // forward work-item order, SXE_FWD_ORDER_*
 };
 
 namespace sxe {
@@ -34,6 +35,7 @@ sxe_status empty_batch_sq_sum(const char* fn, float* sq_sum, void* stream);
 // for a kernel the resident CTAs per SM at `threads` threads and `smem_bytes` of dynamic shared
 // memory, after raising the kernel's dynamic shared-memory limit to `smem_bytes` on that device.
 int device_sm_count();
+int64_t device_l2_bytes();   // L2 size of the current device (cached per device)
 int kernel_ctas_per_sm(const void* kernel, int threads, int smem_bytes);
 // 2 / (P n_out), the factor of the L2 loss's gradient dy = 2 (y - t) / (P n_out), rounded on the
 // host so that no kernel needs FP64 to form it exactly (P n_out exceeds 2^24).

@@ -124,6 +124,12 @@ def test_entry_points_validate_before_launch(L):
         assert lib.sxe_encoder_set_bwd_aggregation(h, 2) == -1
         assert lib.sxe_encoder_set_bwd_aggregation(h, 1) == 0
         assert lib.sxe_encoder_set_bwd_aggregation(h, 0) == 0
+        # forward work-item order: 0 (automatic), 1 (point-major) or 2 (level-major)
+        assert lib.sxe_encoder_set_fwd_order(None, 1) == -1
+        assert lib.sxe_encoder_set_fwd_order(h, 3) == -1
+        assert lib.sxe_encoder_set_fwd_order(h, -1) == -1
+        for order in (2, 1, 0):
+            assert lib.sxe_encoder_set_fwd_order(h, order) == 0
         # zero points: nothing to do, no pointer needed
         assert lib.sxe_encode_fwd(h, None, 0, None, None, None) == 0
         assert lib.sxe_encode_bwd(h, None, 0, None, None, 2, None, None) == 0
