@@ -344,7 +344,7 @@ def run_gpu(args):
     ms = start.elapsed_time(stop)
     ms = max_over_ranks(ms, world, dev)
     loss = tr.loss()
-    n_touched, n_sectors = count_touched(tr, xd[0])
+    n_touched, _ = count_touched(tr, xd[0])
 
     # ---- end to end through the public API (HostFeed): every step copies its batch from pinned
     # host memory to the device (copy stream, double-buffered), replays the recorded step and reads
@@ -427,15 +427,6 @@ def run_gpu(args):
             "predicted_ms": pred_bwd * 1e3, "measured_ms": per_kernel["encode_bwd"],
             "frac": pred_bwd * 1e3 / per_kernel["encode_bwd"],
             "model": "first touch of an entry = one random float2 reduction missing L2; later ones hit"}
-        gathers = contrib
-        pred_fwd = n_sectors / peaks_ra["gather_4B_table"] + (gathers - n_sectors) / peaks_ra["gather_4B_l2"]
-        line["gather_roofline"] = {
-            "kernel": "encode_fwd", "gathers": gathers, "table_sectors_touched": n_sectors,
-            "achieved_gathers_per_s": gathers / (per_kernel["encode_fwd"] / 1e3),
-            "predicted_ms": pred_fwd * 1e3, "measured_ms": per_kernel["encode_fwd"],
-            "frac": pred_fwd * 1e3 / per_kernel["encode_fwd"],
-            "model": "first gather from a 32-byte table sector = one random 4-byte gather missing L2 "
-                     "(probe over the fp16 tables); later ones hit (probe over 8 MiB)"}
         if comparators is not None:
             line["comparators"] = comparators
         if quality is not None:
