@@ -41,6 +41,32 @@ def _alone(f, x, server_cls=None):
 def test_alone_equals_mixed(cuda_lib, server_cls):
     """Each request's values are bitwise the same when merged with others (continuous batching
     over 4 stream slots) as when computed alone."""
+    _alone_equals_mixed(server_cls, server_cls)
+
+
+@pytest.mark.parametrize("priority_points", [0, 1 << 12])
+def test_native_size_classes_alone_equal_mixed(cuda_lib, priority_points):
+    """The library's loop with one size class (priority_points 0: every batch at normal priority)
+    and with a small class of at most 4096 points: merged values equal those computed alone."""
+    import functools
+    from paper_2311_15439_gb300.serve import NativeFieldServer
+    _alone_equals_mixed(functools.partial(NativeFieldServer, priority_points=priority_points), NativeFieldServer)
+
+
+def test_native_server_on_the_tcgen05_forward(cuda_lib):
+    """Under SXE_MLP_KERNEL_TCGEN05_3TILE the library's loop runs its network forward on the
+    three-tile tcgen05 kernel: merged values equal that kernel's values alone."""
+    from paper_2311_15439_gb300 import _lib as L
+    from paper_2311_15439_gb300.serve import NativeFieldServer
+    prev = L.lib().sxe_mlp_get_kernel()
+    assert L.lib().sxe_mlp_set_kernel(L.SXE_MLP_KERNEL_TCGEN05_3TILE) == 0
+    try:
+        _alone_equals_mixed(NativeFieldServer, NativeFieldServer)
+    finally:
+        L.lib().sxe_mlp_set_kernel(prev)
+
+
+def _alone_equals_mixed(make_server, server_cls):
     fields = _fields()
     g = synth.rng(1)
     reqs_in = []
@@ -48,7 +74,7 @@ def test_alone_equals_mixed(cuda_lib, server_cls):
         d = int(g.choice([2, 3, 4, 5]))
         P = int(np.exp(g.uniform(np.log(100), np.log(70000))))
         reqs_in.append((d, torch.from_numpy(synth.uniform_points(P, d, 100 + i)).pin_memory()))
-    srv = server_cls(fields, mem_budget_bytes=64 << 20, n_slots=4, max_batch_points=1 << 18).start()
+    srv = make_server(fields, mem_budget_bytes=64 << 20, n_slots=4, max_batch_points=1 << 18).start()
     reqs = [srv.submit(d, x) for d, x in reqs_in]
     for r in reqs:
         assert r.wait(60)
