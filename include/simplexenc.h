@@ -337,6 +337,16 @@ sxe_status sxe_vr_field_mlp(const sxe_mlp_desc* density, const void* Wd,
                             const float* dirs, int64_t n_rays, int32_t n_samples, float* sigma,
                             float* logits, void* stream);
 
+/* sxe_vr_field_mlp that also writes the intermediates a training step's backward reads: the
+ * density network's 16 outputs density_out [n_rays*S][16] binary32 (as sxe_mlp_fwd writes them)
+ * and the colour network's input color_in [n_rays*S][32] of the network dtype (as sxe_vr_field
+ * writes it), both 16-byte aligned and required when n_rays > 0.  Every output equals that of the
+ * three launches bit for bit (which is what runs where the fused kernel does not apply). */
+sxe_status sxe_vr_field_mlp_saved(const sxe_mlp_desc* density, const void* Wd,
+                                  const sxe_mlp_desc* color, const void* Wc, const void* enc,
+                                  const float* dirs, int64_t n_rays, int32_t n_samples, float* sigma,
+                                  float* logits, float* density_out, void* color_in, void* stream);
+
 /* Size in bytes of the workspace sxe_mlp_bwd needs for n_points (host). */
 int64_t sxe_mlp_bwd_workspace_bytes(const sxe_mlp_desc* desc, int64_t n_points);
 

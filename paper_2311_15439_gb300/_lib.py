@@ -28,7 +28,7 @@ EXPORTS = (
     "sxe_encode_fwd", "sxe_encode_fwd_marked", "sxe_encode_bwd", "sxe_encode_bwd_levels", "sxe_encode_bwd_kernel_count",
     "sxe_encode_bwd_levels_kernel_count", "sxe_encode_bwd_coarse_levels", "sxe_encode_bwd_input",
     "sxe_encode_vertices",
-    "sxe_encode_plain_fwd", "sxe_encode_plain_bwd", "sxe_vr_samples", "sxe_vr_field", "sxe_vr_field_mlp", "sxe_vr_composite",
+    "sxe_encode_plain_fwd", "sxe_encode_plain_bwd", "sxe_vr_samples", "sxe_vr_field", "sxe_vr_field_mlp", "sxe_vr_field_mlp_saved", "sxe_vr_composite",
     "sxe_vr_composite_bwd", "sxe_vr_field_bwd",
     "sxe_adam_advance", "sxe_step_dev", "sxe_step_touched_dev",
     "sxe_mlp_n_params", "sxe_mlp_fwd", "sxe_mlp_bwd_workspace_bytes", "sxe_mlp_bwd", "sxe_mlp_train_l2",
@@ -95,6 +95,7 @@ def _declare(L):
         "sxe_vr_composite_bwd": (i32, [vp, vp, vp, vp, vp, i64, i32, vp, vp, vp]),
         "sxe_vr_field_bwd": (i32, [vp, vp, vp, vp, i64, i32, vp, vp]),
         "sxe_vr_field_mlp": (i32, [M, vp, M, vp, vp, vp, i64, i32, vp, vp, vp]),
+        "sxe_vr_field_mlp_saved": (i32, [M, vp, M, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp]),
         "sxe_vr_composite": (i32, [vp, vp, vp, i64, i32, vp, vp, vp, vp]),
         "sxe_encode_plain_bwd": (i32, [vp, vp, i64, vp, vp, vp]),
         "sxe_mlp_n_params": (i64, [M]),

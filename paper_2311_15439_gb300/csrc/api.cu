@@ -406,22 +406,40 @@ sxe_status sxe_encode_plain_bwd(const sxe_encoder* e, const float* x, int64_t P,
 }
 
 // ---------------------------------------------------------------------------
+static sxe_status vr_field_mlp(const char* fn, const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc,
+                               const void* Wc, const void* enc, const float* dirs, int64_t R, int32_t S, float* sigma,
+                               float* logits, float* dens_out, void* color_in, void* stream) {
+  sxe_status st = check_rays(fn, R, S);
+  if (st != SXE_OK) return st;
+  if (!dd || !dc) return set_error(SXE_EINVAL, "%s: NULL network description", fn);
+  if ((st = check_mlp(fn, dd)) != SXE_OK || (st = check_mlp(fn, dc)) != SXE_OK) return st;
+  if (dd->n_hidden != 1 || dd->n_out != 16 || dc->n_in != 32 || dc->dtype != dd->dtype)
+    return set_error(SXE_EUNSUPPORTED, "%s: needs a density network n_in -> 64 -> 16 and a colour "
+                     "network 32 -> ... of the same dtype", fn);
+  if (R == 0) return SXE_OK;
+  if (!Wd || !Wc || !enc || !dirs || !sigma || !logits) return set_error(SXE_EINVAL, "%s: NULL buffer", fn);
+  if (!aligned(enc, 16) || !aligned(Wd, 4) || !aligned(Wc, 4) || !aligned(dirs, 4) || !aligned(sigma, 4) ||
+      !aligned(logits, 4))
+    return set_error(SXE_EINVAL, "%s: misaligned buffer (encoding rows need 16 bytes)", fn);
+  if ((dens_out && !aligned(dens_out, 16)) || (color_in && !aligned(color_in, 16)))
+    return set_error(SXE_EINVAL, "%s: density_out and color_in must be 16-byte aligned", fn);
+  return launch_vr_field_mlp(dd, Wd, dc, Wc, enc, dirs, R, S, sigma, logits, dens_out, color_in,
+                             (cudaStream_t)stream);
+}
+
 sxe_status sxe_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
                             const void* enc, const float* dirs, int64_t R, int32_t S, float* sigma, float* logits,
                             void* stream) {
-  sxe_status st = check_rays("vr_field_mlp", R, S);
-  if (st != SXE_OK) return st;
-  if (!dd || !dc) return set_error(SXE_EINVAL, "vr_field_mlp: NULL network description");
-  if ((st = check_mlp("vr_field_mlp", dd)) != SXE_OK || (st = check_mlp("vr_field_mlp", dc)) != SXE_OK) return st;
-  if (dd->n_hidden != 1 || dd->n_out != 16 || dc->n_in != 32 || dc->dtype != dd->dtype)
-    return set_error(SXE_EUNSUPPORTED, "vr_field_mlp: needs a density network n_in -> 64 -> 16 and a colour "
-                     "network 32 -> ... of the same dtype");
-  if (R == 0) return SXE_OK;
-  if (!Wd || !Wc || !enc || !dirs || !sigma || !logits) return set_error(SXE_EINVAL, "vr_field_mlp: NULL buffer");
-  if (!aligned(enc, 16) || !aligned(Wd, 4) || !aligned(Wc, 4) || !aligned(dirs, 4) || !aligned(sigma, 4) ||
-      !aligned(logits, 4))
-    return set_error(SXE_EINVAL, "vr_field_mlp: misaligned buffer (encoding rows need 16 bytes)");
-  return launch_vr_field_mlp(dd, Wd, dc, Wc, enc, dirs, R, S, sigma, logits, (cudaStream_t)stream);
+  return vr_field_mlp("vr_field_mlp", dd, Wd, dc, Wc, enc, dirs, R, S, sigma, logits, nullptr, nullptr, stream);
+}
+
+sxe_status sxe_vr_field_mlp_saved(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
+                                  const void* enc, const float* dirs, int64_t R, int32_t S, float* sigma,
+                                  float* logits, float* density_out, void* color_in, void* stream) {
+  if (R > 0 && (!density_out || !color_in))
+    return set_error(SXE_EINVAL, "vr_field_mlp_saved: NULL density_out or color_in");
+  return vr_field_mlp("vr_field_mlp_saved", dd, Wd, dc, Wc, enc, dirs, R, S, sigma, logits, density_out, color_in,
+                      stream);
 }
 
 int64_t sxe_mlp_n_params(const sxe_mlp_desc* d) {

@@ -837,11 +837,17 @@ sxe_status launch_mlp_fwd(const sxe_mlp_desc* d, const void* W, const void* in, 
 
 sxe_status launch_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
                                const void* enc, const float* dirs, int64_t R, int S, float* sigma, float* logits,
-                               cudaStream_t s) {
+                               float* dens_out, void* color_in, cudaStream_t s) {
   // the tcgen05 form (three sample tiles per SM) under the automatic and three-tile settings
   if ((g_mlp_kernel == SXE_MLP_KERNEL_AUTO || g_mlp_kernel == SXE_MLP_KERNEL_TCGEN05_3TILE) && dc->n_out <= 8)
-    return launch_vr_field_tc3(dd, Wd, dc, Wc, enc, dirs, R, S, sigma, logits, s);
+    return launch_vr_field_tc3(dd, Wd, dc, Wc, enc, dirs, R, S, sigma, logits, dens_out, color_in, s);
   const int64_t P = R * S;
+  if (dens_out && color_in) {      // the intermediates asked for: the three launches, which write them
+    sxe_status st = launch_mlp_fwd(dd, Wd, enc, P, dens_out, nullptr, s);
+    if (st == SXE_OK) st = launch_vr_field(dens_out, dirs, R, S, dd->dtype, sigma, color_in, s);
+    if (st == SXE_OK) st = launch_mlp_fwd(dc, Wc, color_in, P, logits, nullptr, s);
+    return st;
+  }
   return dd->dtype == SXE_F16
              ? field_in<__half>(dd->n_in, dc->n_hidden, Wd, Wc, enc, dirs, P, S, dc->n_out, sigma, logits, s)
              : field_in<__nv_bfloat16>(dd->n_in, dc->n_hidden, Wd, Wc, enc, dirs, P, S, dc->n_out, sigma, logits, s);

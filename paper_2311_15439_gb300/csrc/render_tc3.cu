@@ -6,7 +6,9 @@
 // narrow output layers run on warp-level mma.sync in the epilogues, each warp on its own 32 rows.
 // Per tile: density hidden layer, colour hidden layers on tcgen05; density outputs, sigma and
 // the colour input's first 16 columns from the first epilogue (the spherical-harmonics half is
-// written at the tile's start); the colour logits from the last.  Every wait is bounded.
+// written at the tile's start); the colour logits from the last.  On request the density outputs
+// (binary32) and the colour input rows are written out too, for a backward pass that reads them.
+// Every wait is bounded.
 #include "mlp_tc3.cuh"
 
 namespace sxe {
@@ -49,7 +51,8 @@ template <typename T, int N_IN, int NHC>
 __global__ void __launch_bounds__(Fd3<N_IN, NHC>::THREADS, 1)
 vr_field_tc3_kernel(const T* __restrict__ Wd, const T* __restrict__ Wc, const T* __restrict__ enc,
                     const float* __restrict__ dirs, int64_t P, int S_, int n_out_c, float* __restrict__ sigma,
-                    float* __restrict__ logits, int* __restrict__ err) {
+                    float* __restrict__ logits, float* __restrict__ dens_out, T* __restrict__ color_in,
+                    int* __restrict__ err) {
   using S = Fd3<N_IN, NHC>;
   constexpr int G = S::G;
   constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
@@ -182,10 +185,29 @@ vr_field_tc3_kernel(const T* __restrict__ Wd, const T* __restrict__ Wc, const T*
             if (rl < rows) sigma[row0 + rl] = vr_density(y[0][2 * half]);
           }
         }
+        if (dens_out) {                                 // the 16 outputs in binary32, if asked
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const int rl = 32 * q + 16 * mt + gq + 8 * half;
+            if (rl < rows)
+#pragma unroll
+              for (int nt = 0; nt < 2; ++nt)
+                *reinterpret_cast<float2*>(dens_out + (row0 + rl) * 16 + 8 * nt + 2 * t4) =
+                    make_float2(y[nt][2 * half], y[nt][2 * half + 1]);
+          }
+        }
         // the 16 outputs, rounded, are the colour input's columns 0-15
         stsm_x4(tc::smem_u32(gs + S::X2) + lm_x2 + 1024u * mt, pack2<T>(y[0][0], y[0][1]), pack2<T>(y[0][2], y[0][3]),
                 pack2<T>(y[1][0], y[1][1]), pack2<T>(y[1][2], y[1][3]));
       }
+    }
+    if (color_in) {                                     // the colour input row, if asked (this warp's rows)
+      __syncwarp();
+      if (r < rows)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          *reinterpret_cast<uint4*>(color_in + (row0 + r) * 32 + 8 * j) =
+              *reinterpret_cast<const uint4*>(gs + S::X2 + tc::cm_offset(r, 8 * j, 32));
     }
     // ---- colour network: hidden layers on tcgen05 (HA, HB alternating), outputs on mma.sync
     issue(gs + S::X2, sm + S::W0C, 32);
@@ -228,29 +250,32 @@ vr_field_tc3_kernel(const T* __restrict__ Wd, const T* __restrict__ Wc, const T*
 
 template <typename T, int N_IN, int NHC>
 sxe_status field_tc3_launch(const void* Wd, const void* Wc, const void* enc, const float* dirs, int64_t P, int S_,
-                            int n_out_c, float* sigma, float* logits, cudaStream_t s) {
+                            int n_out_c, float* sigma, float* logits, float* dens_out, void* color_in,
+                            cudaStream_t s) {
   using S = Fd3<N_IN, NHC>;
   const int64_t n_tiles = (P + kM - 1) / kM;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)device_sm_count(), (n_tiles + S::G - 1) / S::G));
   kernel_ctas_per_sm((const void*)vr_field_tc3_kernel<T, N_IN, NHC>, S::THREADS, S::SMEM);
   vr_field_tc3_kernel<T, N_IN, NHC><<<grid, S::THREADS, S::SMEM, s>>>((const T*)Wd, (const T*)Wc, (const T*)enc, dirs,
-                                                                       P, S_, n_out_c, sigma, logits, tc3_error_word());
+                                                                       P, S_, n_out_c, sigma, logits, dens_out,
+                                                                       (T*)color_in, tc3_error_word());
   return check_launch("vr_field_tc3");
 }
 
 template <typename T>
 sxe_status field_tc3_in(int n_in, int nhc, const void* Wd, const void* Wc, const void* enc, const float* dirs,
-                        int64_t P, int S_, int n_out_c, float* sigma, float* logits, cudaStream_t s) {
+                        int64_t P, int S_, int n_out_c, float* sigma, float* logits, float* dens_out,
+                        void* color_in, cudaStream_t s) {
   switch (n_in * 4 + nhc) {
-    case 16 * 4 + 1: return field_tc3_launch<T, 16, 1>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
-    case 16 * 4 + 2: return field_tc3_launch<T, 16, 2>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
-    case 16 * 4 + 3: return field_tc3_launch<T, 16, 3>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
-    case 32 * 4 + 1: return field_tc3_launch<T, 32, 1>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
-    case 32 * 4 + 2: return field_tc3_launch<T, 32, 2>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
-    case 32 * 4 + 3: return field_tc3_launch<T, 32, 3>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
-    case 64 * 4 + 1: return field_tc3_launch<T, 64, 1>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
-    case 64 * 4 + 2: return field_tc3_launch<T, 64, 2>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
-    default: return field_tc3_launch<T, 64, 3>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, s);
+    case 16 * 4 + 1: return field_tc3_launch<T, 16, 1>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
+    case 16 * 4 + 2: return field_tc3_launch<T, 16, 2>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
+    case 16 * 4 + 3: return field_tc3_launch<T, 16, 3>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
+    case 32 * 4 + 1: return field_tc3_launch<T, 32, 1>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
+    case 32 * 4 + 2: return field_tc3_launch<T, 32, 2>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
+    case 32 * 4 + 3: return field_tc3_launch<T, 32, 3>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
+    case 64 * 4 + 1: return field_tc3_launch<T, 64, 1>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
+    case 64 * 4 + 2: return field_tc3_launch<T, 64, 2>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
+    default: return field_tc3_launch<T, 64, 3>(Wd, Wc, enc, dirs, P, S_, n_out_c, sigma, logits, dens_out, color_in, s);
   }
 }
 
@@ -258,13 +283,14 @@ sxe_status field_tc3_in(int n_in, int nhc, const void* Wd, const void* Wc, const
 
 sxe_status launch_vr_field_tc3(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
                                const void* enc, const float* dirs, int64_t R, int S_, float* sigma, float* logits,
-                               cudaStream_t s) {
+                               float* dens_out, void* color_in, cudaStream_t s) {
   if (dc->n_out > 8) return set_error(SXE_EUNSUPPORTED, "vr_field_tc3: colour n_out=%d > 8", dc->n_out);
   const int64_t P = R * S_;
   return dd->dtype == SXE_F16
-             ? field_tc3_in<__half>(dd->n_in, dc->n_hidden, Wd, Wc, enc, dirs, P, S_, dc->n_out, sigma, logits, s)
+             ? field_tc3_in<__half>(dd->n_in, dc->n_hidden, Wd, Wc, enc, dirs, P, S_, dc->n_out, sigma, logits,
+                                    dens_out, color_in, s)
              : field_tc3_in<__nv_bfloat16>(dd->n_in, dc->n_hidden, Wd, Wc, enc, dirs, P, S_, dc->n_out, sigma, logits,
-                                           s);
+                                           dens_out, color_in, s);
 }
 
 }  // namespace sxe

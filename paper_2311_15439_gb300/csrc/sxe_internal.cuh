@@ -65,7 +65,7 @@ sxe_status launch_vr_field(const float* dens, const float* dirs, int64_t R, int 
                            void* cin, cudaStream_t s);
 sxe_status launch_vr_field_mlp(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
                                const void* enc, const float* dirs, int64_t R, int S, float* sigma, float* logits,
-                               cudaStream_t s);
+                               float* dens_out, void* color_in, cudaStream_t s);
 sxe_status launch_vr_composite_bwd(const float* sigma, const float* logits, const float* delta, const float* color,
                                    const float* dcolor, int64_t R, int S, float* dsigma, float* dlogits,
                                    cudaStream_t s);
@@ -102,7 +102,7 @@ sxe_status launch_mlp_fwd_tc3(const sxe_mlp_desc* d, const void* W, const void* 
                               void* act, cudaStream_t s);
 sxe_status launch_vr_field_tc3(const sxe_mlp_desc* dd, const void* Wd, const sxe_mlp_desc* dc, const void* Wc,
                                const void* enc, const float* dirs, int64_t R, int S, float* sigma, float* logits,
-                               cudaStream_t s);   // colour n_out <= 8 (render_tc3.cu)
+                               float* dens_out, void* color_in, cudaStream_t s);   // colour n_out <= 8 (render_tc3.cu)
 int* tc_error_word();   // device address of the tcgen05 kernels' error word (current device)
 sxe_status launch_mlp_reduce(const float* ws, int nb, int64_t n_params, float inv_scale, float* dW, float* sq_sum,
                              cudaStream_t s);

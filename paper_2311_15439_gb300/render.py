@@ -10,8 +10,10 @@ A ``Renderer`` renders a batch of rays through the library's kernels only:
 4. ``sxe_vr_composite`` -- sigmoid colours composited front to back (Eq. 5).
 
 With ``fused=False`` step 3 is three launches (``sxe_mlp_fwd``, ``sxe_vr_field``,
-``sxe_mlp_fwd``) with the same results.  All buffers are allocated once for the largest ray
-batch and reused; every launch is asynchronous on one stream.
+``sxe_mlp_fwd``) with the same results; with ``keep_intermediates`` the fused step is
+``sxe_vr_field_mlp_saved``, which also writes the density outputs and the colour input that a
+training step's backward reads.  All buffers are allocated once for the largest ray batch and
+reused; every launch is asynchronous on one stream.
 """
 from __future__ import annotations
 
@@ -29,12 +31,13 @@ class Renderer:
     """Renders rays of a field = (encoder, density network, colour network)."""
 
     def __init__(self, encoder: Encoder, max_rays: int, n_samples: int, *, dtype: str = "f16", device="cuda",
-                 fused: bool = True):
+                 fused: bool = True, keep_intermediates: bool = False):
         if encoder.d != 3:
             raise ValueError("volumetric rendering needs a 3-D encoder")
         if encoder.out_dtype != dtype:
             raise ValueError("encoder output dtype %s != network dtype %s" % (encoder.out_dtype, dtype))
         self.enc, self.S, self.max_rays, self.dtype, self.fused = encoder, n_samples, max_rays, dtype, fused
+        self.keep = bool(keep_intermediates)
         self.density = Mlp(encoder.n_out, 16, n_hidden=1, dtype=dtype)
         self.color = Mlp(32, 3, n_hidden=2, dtype=dtype)
         dev = torch.device(device)
@@ -81,9 +84,17 @@ class Renderer:
         if self.fused:
             for W, m, nm in ((W_density, self.density, "W_density"), (W_color, self.color, "W_color")):
                 _need(W, torch_dtype(self.dtype), nm, (m.n_params,))
-            L.check(lib.sxe_vr_field_mlp(ctypes.byref(self.density.desc), _ptr(W_density), ctypes.byref(self.color.desc),
-                                         _ptr(W_color), _ptr(self.enc_out), _ptr(dirs), R, S, _ptr(self.sigma),
-                                         _ptr(self.logits), st), "sxe_vr_field_mlp")
+            if self.keep:
+                L.check(lib.sxe_vr_field_mlp_saved(ctypes.byref(self.density.desc), _ptr(W_density),
+                                                   ctypes.byref(self.color.desc), _ptr(W_color), _ptr(self.enc_out),
+                                                   _ptr(dirs), R, S, _ptr(self.sigma), _ptr(self.logits),
+                                                   _ptr(self.dens_out), _ptr(self.color_in), st),
+                        "sxe_vr_field_mlp_saved")
+            else:
+                L.check(lib.sxe_vr_field_mlp(ctypes.byref(self.density.desc), _ptr(W_density),
+                                             ctypes.byref(self.color.desc), _ptr(W_color), _ptr(self.enc_out),
+                                             _ptr(dirs), R, S, _ptr(self.sigma), _ptr(self.logits), st),
+                        "sxe_vr_field_mlp")
         else:
             self.density.mlp_fwd(W_density, self.enc_out[:P], out=self.dens_out[:P], stream=stream)
             L.check(lib.sxe_vr_field(_ptr(self.dens_out), _ptr(dirs), R, S, _VR_DTYPES[self.dtype],
@@ -113,7 +124,9 @@ class VolumeTrainer:
         from .api import Adam
         from .trainer import TableState, choose_table_layout, default_loss_scale
         self.enc, self.R, self.S = encoder, max_rays, n_samples
-        self.rr = Renderer(encoder, max_rays, n_samples, dtype=dtype, device=device, fused=False)
+        # the fused field, keeping the density outputs and colour input the backward reads
+        self.rr = Renderer(encoder, max_rays, n_samples, dtype=dtype, device=device, fused=True,
+                           keep_intermediates=True)
         dev = self.rr.x.device
         F, n_entries = encoder.n_features, encoder.n_levels * encoder.T
         vals = synth.uniform_tables(encoder.n_levels, encoder.T, F, seed, dtype="f32", scale=table_init)[0]

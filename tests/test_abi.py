@@ -209,3 +209,13 @@ def test_render_entries_validate_before_launch(L):
     assert lib.sxe_vr_composite(None, 16, 16, 4, 8, 16, None, None, None) == L.SXE_EINVAL
     assert lib.sxe_vr_composite(16, 16, 16, 0, 8, 16, None, None, None) == L.SXE_OK       # no rays: nothing
     assert lib.sxe_encode_bwd_input(None, 16, 4, 16, 16, 16, None) == L.SXE_EINVAL         # NULL encoder
+    # the fused field: the saved form needs both intermediate buffers, 16-byte aligned
+    import ctypes
+    dd, dc = L.MlpDesc(32, 64, 1, 16, L.SXE_F16), L.MlpDesc(32, 64, 2, 3, L.SXE_F16)
+    args = (ctypes.byref(dd), 16, ctypes.byref(dc), 16, 16, 16, 4, 8, 16, 16)
+    assert lib.sxe_vr_field_mlp_saved(*args, None, 16, None) == L.SXE_EINVAL              # no density_out
+    assert lib.sxe_vr_field_mlp_saved(*args, 16, None, None) == L.SXE_EINVAL              # no color_in
+    assert lib.sxe_vr_field_mlp_saved(*args, 8, 16, None) == L.SXE_EINVAL                 # misaligned
+    assert lib.sxe_vr_field_mlp_saved(*args[:6], 0, 8, 16, 16, None, None, None) == L.SXE_OK   # no rays
+    bad = L.MlpDesc(32, 64, 2, 16, L.SXE_F16)                                               # 2 hidden layers
+    assert lib.sxe_vr_field_mlp_saved(ctypes.byref(bad), *args[1:], 16, 16, None) == L.SXE_EUNSUPPORTED

@@ -160,6 +160,44 @@ def test_fused_field_equals_three_launches(cuda_lib, kind, dtype, L):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("kernel", ["auto", "mma_sync"])
+@pytest.mark.parametrize("kind,dtype,L", [("simplex", "f16", 16), ("grid", "bf16", 8)])
+def test_fused_field_with_saved_intermediates(cuda_lib, kernel, kind, dtype, L):
+    """sxe_vr_field_mlp_saved: sigma, colour logits and colours as the one-kernel field, and the
+    density outputs and colour input it keeps for the backward equal those the three separate
+    launches write, bit for bit (the tcgen05 kernel under the automatic choice; the three launches
+    themselves under mma.sync); ragged last tile."""
+    from paper_2311_15439_gb300 import _lib as Lb
+    from paper_2311_15439_gb300.api import Encoder
+    from paper_2311_15439_gb300.render import Renderer
+    R, S = 333, 7
+    enc = Encoder(3, L, 2, 14, 16.0, 1.4, kind=kind, table_dtype=dtype)
+    _, store = synth.uniform_tables(L, 1 << 14, 2, 43, dtype=dtype, scale=1.0)
+    t = torch.from_numpy(store.astype(np.int16) if dtype == "bf16" else store).cuda()
+    if dtype == "bf16":
+        t = t.view(torch.bfloat16)
+    rays = [torch.from_numpy(a).cuda() for a in synth.camera_rays(R, 44)]
+    prev = Lb.lib().sxe_mlp_get_kernel()
+    code = {"auto": Lb.SXE_MLP_KERNEL_AUTO, "mma_sync": Lb.SXE_MLP_KERNEL_MMA_SYNC}[kernel]
+    assert Lb.lib().sxe_mlp_set_kernel(code) == 0
+    try:
+        out = []
+        for fused, keep in ((False, False), (True, True)):
+            rr = Renderer(enc, R, S, dtype=dtype, fused=fused, keep_intermediates=keep)
+            Wd, Wc = rr.init_weights(45)
+            rr.dens_out.fill_(float("nan"))
+            rr.color_in.fill_(float("nan"))
+            C = rr.render(*rays, t, Wd, Wc)
+            P = R * S
+            out.append((C.clone(), rr.sigma[:P].clone(), rr.logits[:P].clone(), rr.dens_out[:P].clone(),
+                        rr.color_in[:P].clone()))
+        torch.cuda.synchronize()
+    finally:
+        Lb.lib().sxe_mlp_set_kernel(prev)
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("R,S", [(129, 1), (129, 33), (129, 100), (129, 1024), (1 << 16, 64)])
 def test_composite_bwd_matches_oracle(cuda_lib, R, S):
     """dL/dsigma and dL/dlogits of the compositing against the FP64 chain rule, within a bound
